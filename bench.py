@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GPU partitioned-network-expansion path.
+
+Default workload: 2D random-tensor networks, 16x16 open lattice, bond
+dimension D=4, entries U[0,1)+0.1 (SplitMix64 seeds), expansion order K=8 in
+LOOP mode; one step = one full pass (BP partition, gauge, cluster and term
+enumeration, cluster contractions, FP64 term sums) over a batch of 32
+networks.  Metric: PNE terms contracted per second (whole job, all ranks).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pne|reference]
+                  [--dtype f64|f32|tf32|bf16] [--workload random16|ising4|ising3d]
+
+Under torchrun each rank works on its own 32 networks (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2512_10910_gb300 import inputs as I  # noqa: E402
+
+WORKLOADS = {
+    "random16": dict(desc="2D random-tensor network 16x16 open, D=4, U[0,1)+0.1, K=8 LOOP, 32 networks per step",
+                     kind="random2d", L=16, D=4, K=8, batch=32, mode=0),
+    "ising4": dict(desc="2D Ising 4x4 open, D=2, beta=0.40, full order K=24 LOOP, 32 copies per step",
+                   kind="ising2d", L=4, D=2, K=24, batch=32, mode=0, beta=0.40),
+    "ising3d": dict(desc="3D Ising 8x8x8 open, D=2, beta in {0.20,0.2217,0.25}, K=8 LOOP",
+                    kind="ising3d", L=8, D=2, K=8, batch=3, mode=0),
+}
+
+
+def make_networks(wl, rank):
+    if wl["kind"] == "random2d":
+        g = I.square_lattice(wl["L"], wl["L"], wl["D"])
+        seeds = range(rank * wl["batch"], (rank + 1) * wl["batch"])
+        return g, [I.random_tensors(g, s) for s in seeds]
+    if wl["kind"] == "ising2d":
+        g = I.square_lattice(wl["L"], wl["L"], 2)
+        return g, [I.ising_tensors(g, wl["beta"]) for _ in range(wl["batch"])]
+    if wl["kind"] == "ising3d":
+        g = I.cubic_lattice(wl["L"], wl["L"], wl["L"], 2)
+        return g, [I.ising_tensors(g, b) for b in (0.20, 0.2217, 0.25)]
+    raise ValueError(wl["kind"])
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle baseline
+def oracle_step(wl, net):
+    """The oracle as it stands on one network of the workload; returns
+    (n_terms, seconds, result)."""
+    from oracle import enumerate as E
+    from oracle import expansion as X
+    t0 = time.perf_counter()
+    r = X.pne(net, wl["K"], E.LOOP if wl["mode"] == 0 else E.ALL)
+    return r.n_terms, time.perf_counter() - t0, r
+
+
+def algorithmic_bp_flops(g, iters):
+    """FP64 flops of one BP sweep-set: per site and sweep, the two half
+    contractions touch every tensor entry once with one multiply-add each
+    (4 flops per entry); times the sweeps each tensor set took."""
+    per_sweep = 0
+    for v in range(g.n_sites):
+        per_sweep += 4 * int(np.prod(g.leg_dims(v)))
+    return per_sweep * float(sum(iters))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="pne", choices=["pne", "reference"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "tf32", "bf16"])
+    ap.add_argument("--workload", default="random16", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, wl, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2512_10910_gb300 import pne
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    sh = ctypes_stream = stream.cuda_stream
+
+    g, nets = make_networks(wl, rank)
+    B = len(nets)
+    flat = np.concatenate([n.flat_data()[0] for n in nets])
+    data_dev = torch.from_numpy(flat).to(dev)
+    data_host = torch.from_numpy(flat).pin_memory()
+    ctx = pne.Context(local_rank)
+    K, mode = wl["K"], wl["mode"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
+
+    def step(data, dtype):
+        ns, keep = pne.network_struct(g, data=data, n_batch=B)
+        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0), ctypes_stream)
+        try:
+            terms, nc, nt = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, mode, 0), ctypes_stream)
+            try:
+                pne.pne_contract_terms(ctx.h, terms, dtype, ctypes_stream)
+                res = pne.pne_sum(ctx.h, terms, ctypes_stream)
+            finally:
+                pne.pne_terms_destroy(terms)
+        finally:
+            pne.pne_partition_destroy(part)
+        del keep
+        return res
+
+    def timed(data, dtype, steps, warmup, profile=False):
+        for _ in range(warmup):
+            step(data, dtype)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        if profile:
+            pne.pne_ctx_profile(ctx.h, True)
+        total = 0.0
+        res = None
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = step(data, dtype)
+            b.record(stream)
+            b.synchronize()
+            total += a.elapsed_time(b)
+        torch.cuda.synchronize(dev)
+        prof = pne.pne_ctx_profile_read(ctx.h) if profile else None
+        if profile:
+            pne.pne_ctx_profile(ctx.h, False)
+        if world > 1:
+            t = torch.tensor([total], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total, res, prof
+
+    dtype = pne.DTYPES[args.dtype]
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    total_ms, res, prof = timed(data_dev, dtype, args.steps, args.warmup, profile=True)
+    clk = clocks.stop()
+    n_terms = res[0]["n_terms"]
+    terms_per_step = n_terms * B
+    ms_per_step = total_ms / args.steps
+    value = terms_per_step * world / (ms_per_step * 1e-3)
+
+    # end to end: host (pinned) input copied inside the call, results read back
+    e2e_ms, _, _ = timed(data_host, dtype, max(5, args.steps // 5), 2)
+    e2e_ms /= max(5, args.steps // 5)
+    geom_bytes = 2 * ((g.n_sites + 1) * 8 + (3 * g.n_bonds + g.n_sites + 1 + len(g.site_bonds) + 2 * g.n_bonds
+                                              + len(g.site_bonds) + 64 * g.n_sites) * 4)
+    h2d = int(flat.nbytes + geom_bytes)
+    d2h = int(B * (K + 1) * 2 * 8 + B * 3 * 8 + B * 12 + 64)
+
+    # variants in the other precisions (fewer steps)
+    variants = {}
+    if not args.no_variants:
+        for dn in ("f64", "f32", "tf32", "bf16"):
+            if dn == args.dtype:
+                continue
+            tv, rv, _ = timed(data_dev, pne.DTYPES[dn], max(5, args.steps // 5), 2)
+            msv = tv / max(5, args.steps // 5)
+            variants[dn] = {"value": terms_per_step * world / (msv * 1e-3), "ms_per_step": msv,
+                            "log_abs_first": rv[0]["log_abs"], "err_bound_first": rv[0]["err_bound"]}
+
+    # roofline of the dominant kernel (largest event-timed share of the step)
+    fam, (launches, tot) = max(prof.items(), key=lambda kv: kv[1][1])
+    avg_ms = tot / max(launches, 1)
+    gpu_launches = int(sum(v[0] for v in prof.values()))
+    peak_f64 = pne.pne_measure_fma_peak(ctx.h, pne.PNE_F64, ctypes_stream)
+    peak_f32 = pne.pne_measure_fma_peak(ctx.h, pne.PNE_F32, ctypes_stream)
+    roof = {"kernel": fam, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s",
+            "frac": None, "traffic": None}
+    if fam == "bp_sweeps":
+        iters = [r["bp_iters"] for r in res[:B]]
+        flops = algorithmic_bp_flops(g, iters)
+        roof.update(achieved=flops / (avg_ms * 1e-3) / 1e12, peak=peak_f64 / 1e12,
+                    peak_source="measured FP64 FMA-chain kernel (pne_measure_fma_peak)",
+                    work=f"4 flops per tensor entry per site per sweep; {sum(iters)} sweeps over {B} sets")
+    elif fam == "contract":
+        ns, keep = pne.network_struct(g, data=data_dev, n_batch=B)
+        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0), ctypes_stream)
+        terms, _, _ = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, mode, 0), ctypes_stream)
+        fma = pne.pne_terms_work(ctx.h, terms, ctypes_stream)
+        pne.pne_terms_destroy(terms); pne.pne_partition_destroy(part)
+        pk = peak_f64 if args.dtype == "f64" else peak_f32
+        roof.update(achieved=2.0 * fma * B / (avg_ms * 1e-3) / 1e12, peak=pk / 1e12,
+                    peak_source="measured FMA-chain kernel (pne_measure_fma_peak)",
+                    work=f"2 flops per plan multiply-add; {fma} multiply-adds per network")
+    if roof["achieved"] is not None and roof["peak"]:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["avg_launch_ms"] = avg_ms
+    roof["kernel_shares"] = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()}
+
+    out = {
+        "metric": "PNE terms contracted/sec",
+        "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": wl["desc"], "networks_per_step_per_gpu": B, "terms_per_network": n_terms,
+                   "clusters_per_network": res[0]["n_clusters"], "K": K,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "enumeration": "recomputed every step (cache off)",
+                   "parallelism": f"independent networks per GPU x{world}"},
+        "e2e": {"value": terms_per_step * world / (e2e_ms * 1e-3), "unit": "terms/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": gpu_launches,
+        "roofline": roof,
+        "clocks": clk,
+        "variants": variants,
+        "peaks_measured": {"fp64_tflops": peak_f64 / 1e12, "fp32_tflops": peak_f32 / 1e12},
+    }
+
+    # CPU baseline: the oracle on a bounded sample (rank 0, single GPU only)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nt, secs, r = oracle_step(wl, nets[0])
+        out["cpu_baseline"] = {"value": nt / secs, "unit": "terms/s", "cores": 1, "kind": "oracle",
+                               "sample": f"network 0 of the {B} per step, full oracle pipeline "
+                                         f"({nt} terms in {secs:.1f} s, single thread)"}
+        # time to 1e-6: cheapest dtype whose result is within 1e-6 of the oracle
+        ttt = {}
+        for dn in ("bf16", "tf32", "f32", "f64"):
+            (rr,) = ctx.expand(nets[0], K, mode, pne.DTYPES[dn])
+            err = abs(math.expm1(rr["log_abs"] - r.log_abs))
+            ms = ms_per_step if dn == args.dtype else variants.get(dn, {}).get("ms_per_step")
+            ttt[dn] = {"rel_err_vs_oracle": err, "ms_per_step": ms, "reached_1e-6": bool(err <= 1e-6)}
+        ok = [d for d in ("bf16", "tf32", "f32", "f64") if ttt[d]["reached_1e-6"]]
+        out["time_to_1e-6"] = {"cheapest_dtype": ok[0] if ok else None,
+                               "ms_per_step": ttt[ok[0]]["ms_per_step"] if ok else None, "by_dtype": ttt}
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args, wl, rank, world):
+    """The oracle as the reference arm, on this arm's workload and metric.
+    Each step is a bounded sample: the full oracle pipeline on one network;
+    the run stops early when the steps would exceed about three minutes."""
+    if rank != 0:
+        return 0
+    g, nets = make_networks(wl, rank)
+    for i in range(min(args.warmup, 1)):
+        oracle_step(wl, nets[i % len(nets)])
+    total_terms, total_s, steps = 0, 0.0, 0
+    budget = 180.0
+    for i in range(args.steps):
+        nt, secs, _ = oracle_step(wl, nets[i % len(nets)])
+        total_terms += nt; total_s += secs; steps += 1
+        if total_s + secs > budget:
+            break
+    value = total_terms / total_s
+    out = {"impl": "reference", "metric": "PNE terms contracted/sec", "value": value, "unit": "terms/s",
+           "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl["desc"], "sample_per_step": "one network, full oracle pipeline"},
+           "cpu_baseline": {"value": value, "unit": "terms/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{steps} networks, one per step, single thread"},
+           "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main() or 0)

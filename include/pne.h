@@ -1,0 +1,214 @@
+/*
+ * pne.h -- C ABI of the GB300 partitioned-network-expansion (PNE) library.
+ *
+ * The library evaluates the truncated linear form of the partitioned network
+ * expansion (Evenbly, Gray & Chan, "Partitioned Expansions for Approximate
+ * Tensor Network Contractions", Sec. II.A, Eq. A2-A4) with every bond
+ * partitioned by a rank-1 projector built from belief-propagation messages
+ * (Sec. II.B, Eq. A7, symmetrised as in App. B).  A term is the network with
+ * Q = I - P on a set E of bonds and P on the rest; it factorises into the
+ * capped sites and one local contraction per connected cluster of E.  Terms
+ * of order |E| <= K are summed with unit weights; higher orders and the
+ * residue (Eq. res) are neglected.
+ *
+ * Conventions shared by every call
+ *   - Every call returns a pne_status; none aborts the process.  After an
+ *     error, pne_last_error(ctx) holds a one-line message (per thread).
+ *   - Inputs are borrowed for the duration of the call and copied.
+ *   - Handles (pne_ctx, pne_partition, pne_terms) are owned by the caller once
+ *     returned and released with the matching *_destroy call; device memory
+ *     they hold is freed there (stream-ordered on the stream last used).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on it unless stated otherwise.
+ *   - One context serves one device and one host thread at a time.
+ *   - Floating point: partitions (messages, gauge, site values) are FP64;
+ *     cluster contractions run in the pne_dtype given; term products and the
+ *     per-order sums are FP64.
+ */
+#ifndef PNE_H
+#define PNE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pne_ctx pne_ctx;             /* device, allocator, enumeration cache */
+typedef struct pne_partition pne_partition; /* messages, gauged site tensors, z_v  */
+typedef struct pne_terms pne_terms;         /* clusters, terms, cluster values     */
+
+typedef enum {
+    PNE_OK = 0,
+    PNE_EINVAL = 1,       /* malformed input or unsupported size              */
+    PNE_ENOMEM = 2,       /* device or host allocation failed                 */
+    PNE_ECUDA = 3,        /* a CUDA runtime call failed                       */
+    PNE_ENOCONV = 4,      /* BP did not reach tol within max_iter sweeps      */
+    PNE_EDEGENERATE = 5,  /* |<m_s0|m_s1>| below 1e-300 on some bond, or a
+                             message of zero norm                             */
+    PNE_ETIMEOUT = 6,     /* a bounded device-side wait gave up               */
+    PNE_EOVERFLOW = 7,    /* a per-cluster or per-term buffer limit exceeded  */
+    PNE_EBUSY = 8         /* resource in use (e.g. scratch of another call)   */
+} pne_status;
+
+typedef enum { PNE_F64 = 0, PNE_F32 = 1, PNE_TF32 = 2, PNE_BF16 = 3 } pne_dtype;
+/* LOOP: clusters with a site of cluster-degree one ("dangling excitation",
+ *       Sec. III.A) are dropped -- they vanish at a BP fixed point.
+ * ALL:  every bond subset is a term (networks with <= 30 closed bonds). */
+typedef enum { PNE_MODE_LOOP = 0, PNE_MODE_ALL = 1 } pne_mode;
+
+/* Library limits (checked; violations return PNE_EINVAL). */
+#define PNE_MAX_DEG 6        /* legs per site                                */
+#define PNE_MAX_DIM 8        /* bond dimension                               */
+#define PNE_MAX_ORDER 32     /* expansion order K                            */
+
+/*
+ * A network of tensors (Eq. A1).  Sites 0..n_sites-1, bonds 0..n_bonds-1.
+ *   bond_site  [n_bonds][2] host: the two sites of each bond; the second is -1
+ *              for an open index (Sec. III.D).  No bond joins a site to itself.
+ *   bond_dim   [n_bonds] host: index dimension, 2..PNE_MAX_DIM.
+ *   site_ptr   [n_sites+1], site_bonds [site_ptr[n_sites]] host: each site's
+ *              legs = its bonds in ascending bond id (CSR).
+ *   data       site tensors, FP64, row-major over the site's legs in the order
+ *              above; n_batch consecutive tensor sets of identical geometry,
+ *              set b at data + b * data_off[n_sites].  Host pointer, or device
+ *              pointer when data_on_device != 0.
+ *   data_off   [n_sites+1] host: start of each site's tensor within a set.
+ */
+typedef struct {
+    int32_t n_sites, n_bonds;
+    const int32_t *bond_site;
+    const int32_t *bond_dim;
+    const int32_t *site_ptr, *site_bonds;
+    const double *data;
+    const int64_t *data_off;
+    int32_t data_on_device;
+    int32_t n_batch;
+} pne_network;
+
+/* BP options (the paper leaves the schedule open): Jacobi sweeps from the
+ * uniform message 1/sqrt(d); each message normalised to unit 2-norm with its
+ * largest-magnitude entry positive; stop when the largest entry change in a
+ * sweep is below tol.  damping in [0,1) mixes the previous message in. */
+typedef struct {
+    double tol;          /* default 1e-13 when <= 0 */
+    int32_t max_iter;    /* default 10000 when <= 0 */
+    double damping;      /* default 0 */
+} pne_partition_opts;
+
+typedef struct {
+    int32_t max_order;   /* K: keep terms with |E| <= K                      */
+    int32_t mode;        /* pne_mode                                          */
+    int32_t use_cache;   /* reuse a cached enumeration of the same geometry  */
+} pne_enum_opts;
+
+/* Result for one network (one tensor set, one open-index assignment). */
+typedef struct {
+    int32_t sign;            /* sign of Z_K                                   */
+    double log_abs;          /* ln|Z_K|                                       */
+    double value;            /* Z_K as a double (+-inf when out of range)     */
+    double c[PNE_MAX_ORDER + 1];     /* c_k = (sum of order-k terms) / Z_ref  */
+    double abs_c[PNE_MAX_ORDER + 1]; /* same with |term|                      */
+    int32_t n_orders;        /* K + 1                                         */
+    double log_abs_zref;     /* ln|Z_ref|, Z_ref = prod of nonzero z_v        */
+    int32_t sign_zref;
+    int32_t n_zero_sites;    /* sites with z_v == 0                            */
+    double log_series;       /* ln|Z_ref| + sum_{k=1..K} [x^k] ln(sum_j c_j x^j);
+                                NaN when undefined (not part of the paper)    */
+    double err_bound;        /* rounding bound of the dtype on Z_K, relative  */
+    uint64_t n_terms, n_clusters;
+    int32_t bp_iters;        /* sweeps BP took for this tensor set            */
+    double bp_residual;      /* last sweep's largest message change           */
+} pne_result;
+
+/* ---- context ------------------------------------------------------------ */
+pne_status pne_ctx_create(int device, pne_ctx **out);
+void pne_ctx_destroy(pne_ctx *ctx);
+const char *pne_last_error(pne_ctx *ctx);
+
+/* Optional device allocator (e.g. a framework's caching allocator).  Without
+ * one the library uses cudaMallocAsync / cudaFreeAsync on the call's stream. */
+typedef void *(*pne_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*pne_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+pne_status pne_ctx_set_allocator(pne_ctx *ctx, pne_alloc_fn alloc, pne_free_fn free_fn, void *user);
+
+/* ---- the four calls of the hot path ------------------------------------- */
+
+/* Build the bond partitions (Sec. II.B, Eq. A7, App. B): BP to a fixed point
+ * (boundary reflection on open indices, Sec. III.D), normalise each bond's
+ * messages to unit overlap, gauge every closed bond so that P = e0 e0^T and
+ * Q = diag(0,1,..,1), and keep the gauged site tensors, z_v and the vacuum
+ * value on the device.  Synchronises `stream` once at the end to read the
+ * convergence record.  Returns PNE_ENOCONV (handle still returned, usable)
+ * when some tensor set did not converge, PNE_EDEGENERATE on a zero overlap. */
+pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net,
+                               const pne_partition_opts *opts, void *stream,
+                               pne_partition **out);
+void pne_partition_destroy(pne_partition *p);
+
+/* Enumerate the clusters (connected bond sets with |C| <= K, LOOP or ALL
+ * mode) and the terms (vertex-disjoint cluster tuples with total size <= K,
+ * Eq. A4).  Geometry only: the lists are shared by every tensor set and
+ * cached in the context when use_cache != 0.  Synchronises `stream` (the
+ * counts size the buffers).  n_clusters / n_terms may be NULL. */
+pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part,
+                               const pne_enum_opts *opts, void *stream,
+                               pne_terms **out, uint64_t *n_clusters, uint64_t *n_terms);
+void pne_terms_destroy(pne_terms *t);
+
+/* Contract every cluster of every tensor set in `dtype`: w(C) = Z'_C /
+ * prod_{v in C, z_v != 0} z_v with a per-cluster power-of-two exponent carried
+ * through the contraction.  Asynchronous. */
+pne_status pne_contract_terms(pne_ctx *ctx, pne_terms *t, pne_dtype dtype, void *stream);
+
+/* Form every term's value (product of its clusters' w) and sum by order in
+ * FP64 with a fixed reduction tree; write one pne_result per tensor set and
+ * open-index assignment into out[] (pne_terms_n_results entries, set-major,
+ * assignments row-major over the open bonds in ascending id).  Synchronises
+ * `stream`. */
+pne_status pne_sum(pne_ctx *ctx, const pne_terms *t, void *stream, pne_result *out);
+
+/* Number of pne_result entries pne_sum writes (= n_batch * prod of open dims). */
+int64_t pne_terms_n_results(const pne_terms *t);
+
+/* Copy the cluster list and the contracted cluster values to host memory, for
+ * inspection and element-by-element checks.  LOOP mode only.
+ *   edges  [n_clusters][max_order] int32: each cluster's bond ids (ids of the
+ *          network as given), ascending, padded with -1; may be NULL.
+ *   w      [pne_terms_n_results][n_clusters] double: w(C) per tensor set and
+ *          open-index assignment (needs pne_contract_terms first); may be NULL.
+ * Clusters are listed grouped by size.  Synchronises `stream`. */
+pne_status pne_terms_export(pne_ctx *ctx, const pne_terms *t, void *stream, int32_t *edges, double *w);
+
+/* ---- measurement --------------------------------------------------------- */
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+ * every kernel the library launches (no effect on results).  enable != 0
+ * turns it on and clears the record; 0 turns it off. */
+pne_status pne_ctx_profile(pne_ctx *ctx, int enable);
+
+typedef struct {
+    char name[32];        /* kernel family, e.g. "bp_sweep", "contract"       */
+    int64_t launches;
+    double total_ms;      /* sum of event-timed launch durations              */
+} pne_profile_entry;
+
+/* Waits for the recorded events, then writes up to max entries (sorted by
+ * total time, largest first); returns the number of kernel families. */
+int pne_ctx_profile_read(pne_ctx *ctx, pne_profile_entry *out, int max);
+
+/* Multiply-adds of every cluster's contraction plan, summed over clusters (one
+ * tensor set): the algorithmic work of pne_contract_terms per tensor set.
+ * LOOP mode.  Synchronises `stream`. */
+pne_status pne_terms_work(pne_ctx *ctx, const pne_terms *t, void *stream, uint64_t *fma_per_set);
+
+/* Sustained fused multiply-add throughput of this GPU's CUDA cores in FLOP/s
+ * (2 per FMA) for PNE_F64 or PNE_F32, measured with an FMA-chain kernel; the
+ * denominator of the ALU roofline.  Synchronises `stream`. */
+pne_status pne_measure_fma_peak(pne_ctx *ctx, pne_dtype dtype, void *stream, double *flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PNE_H */

@@ -84,6 +84,28 @@ def clusters_bitmask(net, K, mode=LOOP) -> list:
     return _canonical(out[:n])
 
 
+def count_clusters_bitmask(net, K, mode=LOOP) -> int:
+    """Number of clusters by the bitmask scan, without listing them."""
+    lib = _get_lib()
+    bs = np.ascontiguousarray(net.bond_site, dtype=np.int32)
+    n = lib.oracle_enum_bitmask(net.n_sites, net.n_bonds, _p32(bs), K, mode, max(1, K), None, 0)
+    if n < 0:
+        raise ValueError("bitmask scan needs <= 30 closed bonds and <= 64 sites")
+    return int(n)
+
+
+def count_clusters_grow(net, K, mode=LOOP) -> int:
+    """Number of clusters by per-anchor growth, without listing them."""
+    lib = _get_lib()
+    bs = np.ascontiguousarray(net.bond_site, dtype=np.int32)
+    sp = np.ascontiguousarray(net.site_ptr, dtype=np.int32)
+    sb = np.ascontiguousarray(net.site_bonds, dtype=np.int32)
+    n = lib.oracle_enum_grow(net.n_sites, net.n_bonds, _p32(bs), _p32(sp), _p32(sb), K, mode, max(1, K), None, 0)
+    if n < 0:
+        raise MemoryError("oracle_enum_grow failed")
+    return int(n)
+
+
 def clusters_grow(net, K, mode=LOOP) -> list:
     """Per-anchor level growth with sort/unique de-duplication (any size)."""
     lib = _get_lib()
@@ -130,6 +152,8 @@ def clusters_python(net, K, mode=LOOP) -> list:
 
 def enumerate_clusters(net, K, mode=LOOP) -> list:
     """Canonical cluster list; bitmask scan when it applies, growth otherwise."""
+    if K < 1:
+        return []
     n_closed = int(np.sum(net.bond_site[:, 1] >= 0))
     if n_closed <= 30 and net.n_sites <= 64 and (n_closed <= 22 or mode == ALL or K >= n_closed - 4):
         return clusters_bitmask(net, K, mode)

@@ -1,0 +1,672 @@
+// Bond partitions on the GPU: belief propagation, the symmetrising gauge and
+// the excitation-blocked layout of the gauged site tensors.  All FP64.
+//
+// * BP (Sec. I, Sec. II.B): Jacobi sweeps; each outgoing message of a site is
+//   its tensor contracted with the messages arriving on its other legs,
+//   normalised to unit 2-norm with the largest-magnitude entry positive.  An
+//   open index reflects the site's own outgoing message back (Sec. III.D).
+//   One persistent cooperative launch runs every sweep of every tensor set,
+//   with a bounded grid barrier between sweeps.
+// * Gauge (App. B): for bond b = (s0, s1) with outgoing messages m0 (of s0)
+//   and m1 (of s1), n = <m0|m1>.  x = [m0^T / n ; R_perp] where R_perp holds
+//   d-1 orthonormal rows orthogonal to m1 (rows 1.. of the Householder
+//   reflector that maps m1 to a multiple of e0).  Then x m1 = e0 and
+//   e0^T x = m0^T / n, so in the new basis P_b = e0 e0^T (Eq. A7) and
+//   Q_b = diag(0, 1, .., 1).  x^{-1} has the closed form
+//   [m1 | R_perp^T - m1 (R_perp m0)^T / n].
+//   s0's leg is multiplied by x^{-1}, s1's leg by x^T (from the left).
+// * Blocked layout: entries of a gauged site tensor are grouped by the set S
+//   of legs whose index is >= 1 ("excited"); block S is the dense sub-tensor
+//   over those legs with index values 1..d-1.  A cluster contraction reads
+//   exactly one block per site.  Each site is divided by z_v (its all-zero
+//   entry) when z_v != 0, else by a power of two.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "pne_internal.h"
+
+namespace pne {
+
+namespace {
+
+constexpr int kBpWarps = 8;              // warps per block in the BP kernel
+constexpr long long kBarrierSpinLimit = 1ll << 25;
+
+struct BPParams {
+    int n_sets, n_sites, n_legs;
+    const int32_t *site_ptr, *site_bonds, *bond_dim, *inc_slot;
+    const int64_t *tens_off;
+    int64_t set_stride;
+    const double *T;
+    double *msg;                  // [2][n_sets][n_legs][8]
+    double tol, damping;
+    int max_iter;
+    unsigned long long *res;      // [4][n_sets] residual of sweep it in slot it % 4
+    int32_t *done_it;             // [n_sets] iteration of convergence (0: not yet)
+    int32_t *iters_out;           // [n_sets]
+    double *res_out;              // [n_sets]
+    int32_t *final_buf;           // [n_sets]
+    int32_t *flags;               // [0] barrier timeout, [1] degenerate message
+    unsigned int *bar;            // [0] count, [1] generation
+    int smem_per_warp;            // doubles
+    int tabA, tabC;               // table sizes (max over sites)
+};
+
+// Grid-wide barrier for a cooperative launch.  The wait is bounded: on timeout
+// flags[0] is set and every block leaves its loop at the next check.
+__device__ bool grid_barrier(unsigned int *bar, int32_t *flags, unsigned int nblocks)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = bar + 1;
+        unsigned int g = *gen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(bar, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g) {
+                if (++spins > kBarrierSpinLimit) { atomicExch(flags, 1); break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *((volatile int32_t *)flags) == 0;
+}
+
+// All outgoing messages of one site, warp-cooperative.
+// The legs are split in two halves H1 = [0,h), H2 = [h,k).  X1 = T contracted
+// with the incoming messages on H2 (a tensor over H1), X2 = T contracted on H1
+// (over H2).  An output on a leg of H1 is X1 contracted with the messages on
+// the other legs of H1, and likewise for H2.
+__device__ void site_messages(const double *__restrict__ T, int k, const int *dims,
+                              const double *in, double *u, double *w, double *x1, double *x2,
+                              double *out, int lane)
+{
+    int h = k / 2;
+    int A = 1, C = 1;
+    for (int i = 0; i < h; ++i) A *= dims[i];
+    for (int i = h; i < k; ++i) C *= dims[i];
+    // outer-product weight tables
+    for (int c = lane; c < C; c += 32) {
+        int r = c;
+        double p = 1.0;
+        for (int i = k - 1; i >= h; --i) { p *= in[i * kMsgStride + r % dims[i]]; r /= dims[i]; }
+        w[c] = p;
+    }
+    for (int a = lane; a < A; a += 32) {
+        int r = a;
+        double p = 1.0;
+        for (int i = h - 1; i >= 0; --i) { p *= in[i * kMsgStride + r % dims[i]]; r /= dims[i]; }
+        u[a] = p;
+    }
+    __syncwarp();
+    for (int a = lane; a < A; a += 32) {
+        double s = 0.0;
+        const double *row = T + (int64_t)a * C;
+        for (int c = 0; c < C; ++c) s = fma(row[c], w[c], s);
+        x1[a] = s;
+    }
+    for (int c = lane; c < C; c += 32) {
+        double s = 0.0;
+        for (int a = 0; a < A; ++a) s = fma(u[a], T[(int64_t)a * C + c], s);
+        x2[c] = s;
+    }
+    __syncwarp();
+    // outputs: one (leg, value) pair per lane
+    int n_items = 0;
+    for (int j = 0; j < k; ++j) n_items += dims[j];
+    for (int it = lane; it < n_items; it += 32) {
+        int j = 0, x = it;
+        while (x >= dims[j]) { x -= dims[j]; ++j; }
+        const double *X = (j < h) ? x1 : x2;
+        int lo = (j < h) ? 0 : h, hi = (j < h) ? h : k;
+        int size = (j < h) ? A : C;
+        int stride = 1;
+        for (int i = hi - 1; i > j; --i) stride *= dims[i];
+        int rest = size / dims[j];
+        double s = 0.0;
+        for (int r = 0; r < rest; ++r) {
+            int a = (r / stride) * (stride * dims[j]) + x * stride + (r % stride);
+            double p = X[a];
+            int rr = a;
+            for (int i = hi - 1; i >= lo; --i) {
+                int dgt = rr % dims[i];
+                rr /= dims[i];
+                if (i != j) p *= in[i * kMsgStride + dgt];
+            }
+            s += p;
+        }
+        out[j * kMsgStride + x] = s;
+    }
+    __syncwarp();
+}
+
+__global__ void bp_init_kernel(double *msg, const int32_t *site_ptr, const int32_t *site_bonds,
+                               const int32_t *bond_dim, int n_sites, int n_legs, int n_sets)
+{
+    int64_t total = (int64_t)n_sets * n_legs;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int slot = (int)(i % n_legs);
+        int d = bond_dim[site_bonds[slot]];
+        double v = 1.0 / sqrt((double)d);
+        for (int a = 0; a < kMsgStride; ++a) msg[i * kMsgStride + a] = (a < d) ? v : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(kBpWarps * 32) bp_persistent_kernel(BPParams p)
+{
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double *ws = smem + wib * p.smem_per_warp;
+    double *in = ws;                       // [6][8]
+    double *out = in + kMaxDeg * kMsgStride;  // [6][8]
+    double *u = out + kMaxDeg * kMsgStride;
+    double *w = u + p.tabA;
+    double *x1 = w + p.tabC;
+    double *x2 = x1 + p.tabA;
+    const unsigned int nblocks = gridDim.x;
+    const int64_t items = (int64_t)p.n_sets * p.n_sites;
+    const int64_t gwarp = (int64_t)blockIdx.x * kBpWarps + wib;
+    const int64_t nwarps = (int64_t)nblocks * kBpWarps;
+    const int64_t msg_set = (int64_t)p.n_legs * kMsgStride;
+    const int64_t msg_buf = (int64_t)p.n_sets * msg_set;
+
+    for (int it = 1; it <= p.max_iter; ++it) {
+        const int src = (it - 1) & 1, dst = it & 1;
+        // Slots it%4 (this sweep) and (it-1)%4 are live here; a slower block may
+        // still read (it-2)%4 in its bookkeeping of the previous sweep.  Slot
+        // (it+1)%4 was last read before the previous barrier: clear it now.
+        unsigned long long *res_cur = p.res + (int64_t)(it % 4) * p.n_sets;
+        unsigned long long *res_prev = p.res + (int64_t)((it + 3) % 4) * p.n_sets;
+        if (blockIdx.x == 0) {
+            unsigned long long *res_next = p.res + (int64_t)((it + 1) % 4) * p.n_sets;
+            for (int s = threadIdx.x; s < p.n_sets; s += blockDim.x) res_next[s] = 0ull;
+        }
+        for (int64_t item = gwarp; item < items; item += nwarps) {
+            const int set = (int)(item / p.n_sites), v = (int)(item % p.n_sites);
+            if (p.done_it[set] != 0) continue;
+            if (it > 1 && __longlong_as_double((long long)res_prev[set]) < p.tol) continue;
+            const int l0 = p.site_ptr[v], k = p.site_ptr[v + 1] - l0;
+            int dims[kMaxDeg];
+            for (int i = 0; i < kMaxDeg; ++i) dims[i] = (i < k) ? p.bond_dim[p.site_bonds[l0 + i]] : 1;
+            const double *msrc = p.msg + src * msg_buf + set * msg_set;
+            double *mdst = p.msg + dst * msg_buf + set * msg_set;
+            for (int e = lane; e < k * kMsgStride; e += 32) {
+                int i = e / kMsgStride, a = e % kMsgStride;
+                in[e] = msrc[(int64_t)p.inc_slot[l0 + i] * kMsgStride + a];
+            }
+            __syncwarp();
+            const double *T = p.T + set * p.set_stride + p.tens_off[v];
+            site_messages(T, k, dims, in, u, w, x1, x2, out, lane);
+            double r = 0.0;
+            if (lane < k) {
+                const int d = dims[lane];
+                double *o = out + lane * kMsgStride;
+                const double *old = msrc + (int64_t)(l0 + lane) * kMsgStride;
+                double nrm = 0.0, big = -1.0;
+                int arg = 0;
+                for (int a = 0; a < d; ++a) nrm = fma(o[a], o[a], nrm);
+                nrm = sqrt(nrm);
+                if (!(nrm > 0.0)) { atomicExch(p.flags + 1, 1); nrm = 1.0; }
+                for (int a = 0; a < d; ++a) {
+                    double m = fabs(o[a]);
+                    if (m > big) { big = m; arg = a; }
+                }
+                double sg = (o[arg] < 0.0) ? -1.0 : 1.0;
+                double f = sg / nrm;
+                if (p.damping > 0.0) {
+                    double n2 = 0.0;
+                    for (int a = 0; a < d; ++a) { o[a] = (1.0 - p.damping) * (o[a] * f) + p.damping * old[a]; n2 = fma(o[a], o[a], n2); }
+                    n2 = sqrt(n2);
+                    if (!(n2 > 0.0)) { atomicExch(p.flags + 1, 1); n2 = 1.0; }
+                    big = -1.0; arg = 0;
+                    for (int a = 0; a < d; ++a) { double m = fabs(o[a]); if (m > big) { big = m; arg = a; } }
+                    f = ((o[arg] < 0.0) ? -1.0 : 1.0) / n2;
+                }
+                double *dm = mdst + (int64_t)(l0 + lane) * kMsgStride;
+                for (int a = 0; a < d; ++a) {
+                    double nv = o[a] * f;
+                    r = fmax(r, fabs(nv - old[a]));
+                    dm[a] = nv;
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, off));
+            if (lane == 0) atomicMax(res_cur + set, (unsigned long long)__double_as_longlong(r));
+            __syncwarp();
+        }
+        if (!grid_barrier(p.bar, p.flags, nblocks)) return;
+        // convergence bookkeeping (every block reaches the same decision)
+        bool all_done = true;
+        for (int s = 0; s < p.n_sets; ++s) {
+            bool was = p.done_it[s] != 0 ||
+                       (it > 1 && __longlong_as_double((long long)res_prev[s]) < p.tol);
+            if (was) continue;
+            double rs = __longlong_as_double((long long)res_cur[s]);
+            if (rs < p.tol) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    p.done_it[s] = it; p.iters_out[s] = it; p.res_out[s] = rs; p.final_buf[s] = dst;
+                }
+            } else {
+                all_done = false;
+                if (it == p.max_iter && blockIdx.x == 0 && threadIdx.x == 0) {
+                    p.iters_out[s] = 0; p.res_out[s] = rs; p.final_buf[s] = dst;
+                }
+            }
+        }
+        if (all_done) return;
+    }
+}
+
+// ---------------------------------------------------------------- gauge
+struct GaugeParams {
+    int n_sets, n_bonds, n_legs;
+    const int32_t *bond_site, *bond_dim, *bond_leg, *site_ptr;
+    const double *msg;           // [2][n_sets][n_legs][8]
+    const int32_t *final_buf;    // [n_sets]
+    double *gauge;               // [n_sets][n_bonds][2][64]
+    int32_t *flags;              // [1] degenerate
+};
+
+__global__ void gauge_kernel(GaugeParams p)
+{
+    int64_t total = (int64_t)p.n_sets * p.n_bonds;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int set = (int)(i / p.n_bonds), b = (int)(i % p.n_bonds);
+        double *G0 = p.gauge + (i * 2) * 64, *G1 = G0 + 64;
+        const int d = p.bond_dim[b];
+        const int s0 = p.bond_site[2 * b], s1 = p.bond_site[2 * b + 1];
+        if (s1 < 0) {                      // open index: not partitioned
+            for (int e = 0; e < 64; ++e) { G0[e] = (e / 8 == e % 8) ? 1.0 : 0.0; G1[e] = G0[e]; }
+            continue;
+        }
+        const double *base = p.msg + ((int64_t)p.final_buf[set] * p.n_sets + set) * p.n_legs * kMsgStride;
+        const double *m0 = base + (int64_t)(p.site_ptr[s0] + p.bond_leg[2 * b]) * kMsgStride;
+        const double *m1 = base + (int64_t)(p.site_ptr[s1] + p.bond_leg[2 * b + 1]) * kMsgStride;
+        double n = 0.0, nm1 = 0.0;
+        for (int a = 0; a < d; ++a) { n = fma(m0[a], m1[a], n); nm1 = fma(m1[a], m1[a], nm1); }
+        if (!(fabs(n) >= 1e-300) || !(nm1 > 0.0)) { atomicExch(p.flags + 1, 1); n = 1.0; nm1 = 1.0; }
+        nm1 = sqrt(nm1);
+        // Householder vector: v = m1/|m1| + sign(m1[0]) e0
+        double v[kMaxDim], vv = 0.0;
+        for (int a = 0; a < d; ++a) v[a] = m1[a] / nm1;
+        v[0] += (v[0] < 0.0) ? -1.0 : 1.0;
+        for (int a = 0; a < d; ++a) vv = fma(v[a], v[a], vv);
+        // B = [m0^T / n ; H[1..d-1, :]],  H = I - 2 v v^T / (v^T v)
+        double B[kMaxDim][kMaxDim];
+        for (int c = 0; c < d; ++c) B[0][c] = m0[c] / n;
+        for (int r = 1; r < d; ++r)
+            for (int c = 0; c < d; ++c) B[r][c] = ((r == c) ? 1.0 : 0.0) - 2.0 * v[r] * v[c] / vv;
+        // A = B^{-1}: column 0 = m1; column l = R_l^T - m1 (R_l . m0) / n
+        double Ainv[kMaxDim][kMaxDim];
+        for (int a = 0; a < d; ++a) Ainv[a][0] = m1[a];
+        for (int l = 1; l < d; ++l) {
+            double rm = 0.0;
+            for (int c = 0; c < d; ++c) rm = fma(B[l][c], m0[c], rm);
+            for (int a = 0; a < d; ++a) Ainv[a][l] = B[l][a] - m1[a] * rm / n;
+        }
+        for (int e = 0; e < 64; ++e) { G0[e] = 0.0; G1[e] = 0.0; }
+        for (int a = 0; a < d; ++a)
+            for (int c = 0; c < d; ++c) {
+                G0[a * 8 + c] = Ainv[a][c];      // s0: T'[.., c, ..] = sum_a T[.., a, ..] A[a][c]
+                G1[a * 8 + c] = B[c][a];         // s1: T'[.., c, ..] = sum_a T[.., a, ..] B[c][a]
+            }
+    }
+}
+
+
+// ---------------------------------------------------------------- gauged, sliced, blocked tensors
+struct BlockParams {
+    int n_sets, n_slices, n_sites, n_bonds_full, n_open;
+    const int32_t *open_dims;          // [n_open]
+    const int32_t *open_pos;           // [n_bonds_full]: position among open bonds, or -1
+    const int32_t *f_site_ptr, *f_site_bonds, *f_bond_dim, *f_bond_site;
+    const int64_t *f_tens_off;
+    int64_t f_stride;
+    const int64_t *c_tens_off;
+    int64_t c_stride;
+    const int32_t *c_blk_off;          // [n_sites][64]
+    const double *T;                   // [n_sets][f_stride] raw tensors
+    const double *gauge;               // [n_sets][n_bonds_full][2][64]
+    double *Mb;                        // [members][c_stride]
+    double *z, *scale;                 // [members][n_sites]
+    int8_t *zero;                      // [members][n_sites]
+    int half;                          // doubles per buffer (two buffers per warp)
+};
+
+__global__ void block_kernel(BlockParams p)
+{
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    double *bufA = smem + (int64_t)wib * 2 * p.half;
+    double *bufB = bufA + p.half;
+    const int64_t members = (int64_t)p.n_sets * p.n_slices;
+    const int64_t items = members * p.n_sites;
+    for (int64_t item = (int64_t)blockIdx.x * wpb + wib; item < items;
+         item += (int64_t)gridDim.x * wpb) {
+        const int64_t member = item / p.n_sites;
+        const int v = (int)(item % p.n_sites);
+        const int set = (int)(member / p.n_slices), slice = (int)(member % p.n_slices);
+        const int l0 = p.f_site_ptr[v], k = p.f_site_ptr[v + 1] - l0;
+        int fdims[kMaxDeg], cdims[kMaxDeg], fixed[kMaxDeg], bonds[kMaxDeg], side[kMaxDeg];
+        int kc = 0;
+        for (int i = 0; i < k; ++i) {
+            const int b = p.f_site_bonds[l0 + i];
+            fdims[i] = p.f_bond_dim[b];
+            bonds[i] = b;
+            side[i] = (p.f_bond_site[2 * b] == v) ? 0 : 1;
+            const int op = p.open_pos[b];
+            if (op >= 0) {                      // slice index: row-major, last open bond fastest
+                int r = slice;
+                for (int q = p.n_open - 1; q > op; --q) r /= p.open_dims[q];
+                fixed[i] = r % p.open_dims[op];
+            } else {
+                fixed[i] = -1;
+                cdims[kc++] = fdims[i];
+            }
+        }
+        int n = 1;
+        for (int i = 0; i < kc; ++i) n *= cdims[i];
+        // gather the slice (closed legs only) into bufA
+        const double *T = p.T + set * p.f_stride + p.f_tens_off[v];
+        for (int e = lane; e < n; e += 32) {
+            int r = e, src = 0, mul = 1, ci = kc - 1;
+            for (int i = k - 1; i >= 0; --i) {
+                int dgt;
+                if (fixed[i] >= 0) dgt = fixed[i];
+                else { dgt = r % cdims[ci]; r /= cdims[ci]; --ci; }
+                src += dgt * mul;
+                mul *= fdims[i];
+            }
+            bufA[e] = T[src];
+        }
+        __syncwarp();
+        // multiply each closed leg by its gauge matrix: out[.., c, ..] = sum_a in[.., a, ..] G[a][c]
+        double *cur = bufA, *nxt = bufB;
+        int ci = 0, post = n;
+        for (int i = 0; i < k; ++i) {
+            if (fixed[i] >= 0) continue;
+            const int d = cdims[ci++];
+            post /= d;
+            const double *G = p.gauge + (((int64_t)set * p.n_bonds_full + bonds[i]) * 2 + side[i]) * 64;
+            for (int e = lane; e < n; e += 32) {
+                const int lo = e % post, c = (e / post) % d, hi = e / (post * d);
+                const double *src = cur + (int64_t)hi * d * post + lo;
+                double s = 0.0;
+                for (int a = 0; a < d; ++a) s = fma(src[(int64_t)a * post], G[a * 8 + c], s);
+                nxt[e] = s;
+            }
+            __syncwarp();
+            double *t = cur; cur = nxt; nxt = t;
+        }
+        // z_v, scale, blocked write
+        const double zv = cur[0];
+        double mx = 0.0;
+        for (int e = lane; e < n; e += 32) mx = fmax(mx, fabs(cur[e]));
+        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        double s;
+        if (zv != 0.0) s = zv;
+        else if (mx > 0.0) { int ex; frexp(mx, &ex); s = ldexp(1.0, ex); }
+        else s = 1.0;
+        const double inv = 1.0 / s;
+        double *M = p.Mb + member * p.c_stride + p.c_tens_off[v];
+        const int32_t *boff = p.c_blk_off + (int64_t)v * kBlkStride;
+        for (int e = lane; e < n; e += 32) {
+            int r = e, mask = 0, pos = 0, mul = 1;
+            for (int i = kc - 1; i >= 0; --i) {
+                const int dgt = r % cdims[i];
+                r /= cdims[i];
+                if (dgt > 0) { mask |= 1 << i; pos += (dgt - 1) * mul; mul *= cdims[i] - 1; }
+            }
+            M[boff[mask] + pos] = (zv != 0.0) ? cur[e] / zv : cur[e] * inv;
+        }
+        if (lane == 0) {
+            p.z[member * p.n_sites + v] = zv;
+            p.scale[member * p.n_sites + v] = (zv != 0.0) ? 1.0 : s;
+            p.zero[member * p.n_sites + v] = (zv == 0.0) ? 1 : 0;
+        }
+        __syncwarp();
+    }
+}
+
+// ln|Z_ref|, sign(Z_ref) and the number of zero sites, one warp per member.
+__global__ void vacuum_kernel(const double *z, int n_sites, int64_t members, double *vac)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (m >= members) return;
+    double lg = 0.0;
+    int neg = 0, nz = 0;
+    for (int v = lane; v < n_sites; v += 32) {
+        const double x = z[m * n_sites + v];
+        if (x == 0.0) { ++nz; continue; }
+        lg += log(fabs(x));
+        neg += (x < 0.0);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        lg += __shfl_xor_sync(0xffffffffu, lg, off);
+        neg += __shfl_xor_sync(0xffffffffu, neg, off);
+        nz += __shfl_xor_sync(0xffffffffu, nz, off);
+    }
+    if (lane == 0) {
+        vac[3 * m] = lg;
+        vac[3 * m + 1] = (neg & 1) ? -1.0 : 1.0;
+        vac[3 * m + 2] = (double)nz;
+    }
+}
+
+__device__ __forceinline__ float round_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void convert_kernel(const double *src, int64_t n, int dtype, float *dst32, __nv_bfloat16 *dst16)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float f = (float)src[i];
+        if (dtype == PNE_BF16) dst16[i] = __float2bfloat16_rn(f);
+        else dst32[i] = (dtype == PNE_TF32) ? round_tf32(f) : f;
+    }
+}
+
+int grid_for(int64_t n, int block, int n_sm)
+{
+    int64_t g = (n + block - 1) / block;
+    int64_t cap = (int64_t)n_sm * 32;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host launchers
+pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, double damping,
+                     cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags)
+{
+    const Geometry &g = p->full;
+    const int n_sets = p->n_sets;
+    // table sizes: halves of the largest site
+    int tabA = 1, tabC = 1;
+    for (int v = 0; v < g.n_sites; ++v) {
+        const int k = g.site_ptr[v + 1] - g.site_ptr[v], h = k / 2;
+        int A = 1, C = 1;
+        for (int i = 0; i < k; ++i) {
+            const int d = g.bond_dim[g.site_bonds[g.site_ptr[v] + i]];
+            if (i < h) A *= d; else C *= d;
+        }
+        tabA = tabA > A ? tabA : A;
+        tabC = tabC > C ? tabC : C;
+    }
+    const int per_warp = 2 * kMaxDeg * kMsgStride + 2 * tabA + 2 * tabC;
+    const size_t smem = (size_t)per_warp * kBpWarps * sizeof(double);
+    if (smem > 200 * 1024) {
+        set_error(ctx, PNE_EINVAL, "site tensor too large for the BP kernel");
+        return PNE_EINVAL;
+    }
+    // scratch: res[4][n_sets] u64, res_out [n_sets] f64, done/iters/final [n_sets] i32,
+    // flags[4] i32, barrier[2] u32
+    DevBuf scratch;
+    const size_t bytes = 4 * n_sets * 8 + n_sets * 8 + 3 * n_sets * 4 + 16 + 8 + 64;
+    pne_status st = dev_alloc(ctx, scratch, bytes, s);
+    if (st) return st;
+    char *base = (char *)scratch.ptr;
+    unsigned long long *res = (unsigned long long *)base;
+    double *res_out = (double *)(base + 4 * n_sets * 8);
+    int32_t *done = (int32_t *)(base + 5 * n_sets * 8);
+    int32_t *iters = done + n_sets;
+    int32_t *finalb = iters + n_sets;
+    int32_t *flags = finalb + n_sets;
+    unsigned int *bar = (unsigned int *)(flags + 4);
+    cudaError_t e = cudaMemsetAsync(scratch.ptr, 0, bytes, s);
+    if (e != cudaSuccess) { dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, e); }
+
+    double *msg = (double *)p->msg.ptr;
+    {
+        ProfScope ps(ctx, s, "bp_init");
+        bp_init_kernel<<<grid_for((int64_t)n_sets * g.n_legs, 256, ctx->n_sm), 256, 0, s>>>(
+            msg, g.d_site_ptr, g.d_site_bonds, g.d_bond_dim, g.n_sites, g.n_legs, n_sets);
+    }
+
+    BPParams prm;
+    prm.n_sets = n_sets; prm.n_sites = g.n_sites; prm.n_legs = g.n_legs;
+    prm.site_ptr = g.d_site_ptr; prm.site_bonds = g.d_site_bonds; prm.bond_dim = g.d_bond_dim;
+    prm.inc_slot = g.d_inc_slot; prm.tens_off = g.d_tens_off; prm.set_stride = g.tens_off[g.n_sites];
+    prm.T = (const double *)p->T.ptr; prm.msg = msg;
+    prm.tol = tol; prm.damping = damping; prm.max_iter = max_iter;
+    prm.res = res; prm.done_it = done; prm.iters_out = iters; prm.res_out = res_out;
+    prm.final_buf = finalb; prm.flags = flags; prm.bar = bar;
+    prm.smem_per_warp = per_warp; prm.tabA = tabA; prm.tabC = tabC;
+
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(bp_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bp_persistent_kernel,
+                                                                     kBpWarps * 32, smem));
+    if (per_sm < 1) { dev_free(ctx, scratch, s); set_error(ctx, PNE_EINVAL, "BP kernel does not fit"); return PNE_EINVAL; }
+    const int64_t items = (int64_t)n_sets * g.n_sites;
+    int64_t want = (items + kBpWarps - 1) / kBpWarps;
+    int64_t cap = (int64_t)per_sm * ctx->n_sm;
+    int nblocks = (int)(want < cap ? want : cap);
+    if (nblocks < 1) nblocks = 1;
+    void *args[] = {&prm};
+    {
+        ProfScope ps(ctx, s, "bp_sweeps");
+        e = cudaLaunchCooperativeKernel((void *)bp_persistent_kernel, dim3(nblocks), dim3(kBpWarps * 32),
+                                        args, smem, s);
+    }
+    if (e != cudaSuccess) { dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, e); }
+    // copy out the convergence record
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_iters, iters, n_sets * 4, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_res, res_out, n_sets * 8, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_flags, flags, 8, cudaMemcpyDeviceToHost, s));
+    // the final-buffer index stays on the device for the gauge kernel
+    if (p->gauge.ptr == nullptr) { dev_free(ctx, scratch, s); return PNE_EINVAL; }
+    GaugeParams gp;
+    gp.n_sets = n_sets; gp.n_bonds = g.n_bonds; gp.n_legs = g.n_legs;
+    gp.bond_site = g.d_bond_site; gp.bond_dim = g.d_bond_dim; gp.bond_leg = g.d_bond_leg;
+    gp.site_ptr = g.d_site_ptr; gp.msg = msg; gp.final_buf = finalb;
+    gp.gauge = (double *)p->gauge.ptr; gp.flags = flags;
+    {
+        ProfScope ps(ctx, s, "gauge");
+        gauge_kernel<<<grid_for((int64_t)n_sets * g.n_bonds, 128, ctx->n_sm), 128, 0, s>>>(gp);
+    }
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_flags + 2, flags, 8, cudaMemcpyDeviceToHost, s));
+    dev_free(ctx, scratch, s);
+    return PNE_OK;
+}
+
+pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t *h_flag)
+{
+    (void)h_flag;
+    const Geometry &f = p->full, &c = p->closed;
+    int nmax = 1;
+    for (int v = 0; v < f.n_sites; ++v) {
+        int n = 1;
+        for (int i = f.site_ptr[v]; i < f.site_ptr[v + 1]; ++i) n *= f.bond_dim[f.site_bonds[i]];
+        nmax = nmax > n ? nmax : n;
+    }
+    if (nmax > 4096) { set_error(ctx, PNE_EINVAL, "site tensor larger than 4096 entries"); return PNE_EINVAL; }
+    const int half = nmax < 32 ? 32 : nmax;
+    int wpb = (int)((48 * 1024) / (2 * half * sizeof(double)));
+    if (wpb > 8) wpb = 8;
+    if (wpb < 1) wpb = 1;
+    const size_t smem = (size_t)wpb * 2 * half * sizeof(double);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // device table of open positions and dims
+    std::vector<int32_t> open_pos(f.n_bonds, -1);
+    for (size_t q = 0; q < p->open_bonds.size(); ++q) open_pos[p->open_bonds[q]] = (int32_t)q;
+    DevBuf tab;
+    const size_t tb = (f.n_bonds + p->open_dims.size() + 1) * 4;
+    pne_status st = dev_alloc(ctx, tab, tb, s);
+    if (st) return st;
+    int32_t *d_open_pos = (int32_t *)tab.ptr, *d_open_dims = d_open_pos + f.n_bonds;
+    std::vector<int32_t> h(open_pos);
+    h.insert(h.end(), p->open_dims.begin(), p->open_dims.end());
+    h.push_back(0);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(tab.ptr, h.data(), tb, cudaMemcpyHostToDevice, s));
+    BlockParams bp;
+    bp.n_sets = p->n_sets; bp.n_slices = p->n_slices; bp.n_sites = f.n_sites;
+    bp.n_bonds_full = f.n_bonds; bp.n_open = (int)p->open_bonds.size();
+    bp.open_dims = d_open_dims; bp.open_pos = d_open_pos;
+    bp.f_site_ptr = f.d_site_ptr; bp.f_site_bonds = f.d_site_bonds; bp.f_bond_dim = f.d_bond_dim;
+    bp.f_bond_site = f.d_bond_site; bp.f_tens_off = f.d_tens_off; bp.f_stride = f.tens_off[f.n_sites];
+    bp.c_tens_off = c.d_tens_off; bp.c_stride = c.tens_off[c.n_sites]; bp.c_blk_off = c.d_blk_off;
+    bp.T = (const double *)p->T.ptr; bp.gauge = (const double *)p->gauge.ptr;
+    bp.Mb = (double *)p->Mb.ptr;
+    bp.z = (double *)p->site_info.ptr; bp.scale = (double *)p->site_scale.ptr;
+    bp.zero = (int8_t *)p->site_zero.ptr;
+    bp.half = half;
+    const int64_t items = (int64_t)p->n_members * f.n_sites;
+    int64_t g = (items + wpb - 1) / wpb;
+    if (g > (int64_t)ctx->n_sm * 16) g = (int64_t)ctx->n_sm * 16;
+    {
+        ProfScope ps(ctx, s, "gauge_block");
+        block_kernel<<<(int)g, wpb * 32, smem, s>>>(bp);
+    }
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    const int vwarps = 8;
+    {
+        ProfScope ps(ctx, s, "vacuum");
+        vacuum_kernel<<<(int)((p->n_members + vwarps - 1) / vwarps), vwarps * 32, 0, s>>>(
+            (const double *)p->site_info.ptr, f.n_sites, p->n_members, (double *)p->vac.ptr);
+    }
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    dev_free(ctx, tab, s);
+    return PNE_OK;
+}
+
+pne_status launch_convert(pne_ctx *ctx, pne_partition *p, int dtype, cudaStream_t s)
+{
+    if (dtype == PNE_F64 || p->mb32_dtype == dtype) return PNE_OK;
+    const int64_t n = (int64_t)p->n_members * p->closed.tens_off[p->closed.n_sites];
+    pne_status st;
+    if (dtype == PNE_BF16) {
+        if (!p->Mb16.ptr && (st = dev_alloc(ctx, p->Mb16, n * 2, s))) return st;
+        ProfScope ps(ctx, s, "convert");
+        convert_kernel<<<grid_for(n, 256, ctx->n_sm), 256, 0, s>>>(
+            (const double *)p->Mb.ptr, n, dtype, nullptr, (__nv_bfloat16 *)p->Mb16.ptr);
+    } else {
+        if (!p->Mb32.ptr && (st = dev_alloc(ctx, p->Mb32, n * 4, s))) return st;
+        ProfScope ps(ctx, s, "convert");
+        convert_kernel<<<grid_for(n, 256, ctx->n_sm), 256, 0, s>>>(
+            (const double *)p->Mb.ptr, n, dtype, (float *)p->Mb32.ptr, nullptr);
+        p->mb32_dtype = dtype;
+    }
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    return PNE_OK;
+}
+
+}  // namespace pne

@@ -1,0 +1,735 @@
+// Cluster contractions and the per-order term sums.
+//
+// In the symmetrised gauge (App. B) every partitioned bond has P = e0 e0^T and
+// Q = diag(0, 1, .., 1).  A cluster C (a connected set of excited bonds)
+// therefore contracts to
+//     Z'_C = sum over excited values alpha_e in 1..d_e-1 on C's bonds of
+//            prod_{v in C} T'_v[alpha on v's C-legs, 0 on its other legs],
+// i.e. one dense excitation block per site (the blocked layout).  Each site
+// tensor is pre-divided by z_v (its all-zero entry), so the contraction gives
+// w(C) = Z'_C / prod z_v directly (Sec. III.A: the term of a P/Q string is the
+// vacuum times one factor per excited cluster).
+//
+// General clusters: one warp per cluster.  Sites are absorbed one at a time in
+// a greedy order that keeps the open frontier (bonds with exactly one absorbed
+// end) small; the intermediate tensor over the frontier lives in shared memory
+// and is renormalised by a power of two after every step, the exponent being
+// carried separately (a per-cluster log scale).  Precision: FP64, or FP32 /
+// TF32-rounded / BF16 inputs with FP32 accumulation.
+// Bond dimension 2 everywhere (one excited value per bond): each site
+// contributes one number and a cluster is a plain product, one thread each.
+//
+// Term sums (Eq. A4, truncated at order K): a term is a tuple of vertex-
+// disjoint clusters; its value divided by the vacuum is the product of their
+// w.  Terms are stored grouped by order, and each order's sum is formed in
+// FP64 by a fixed reduction tree (chunks of a fixed size, then chunk partials
+// in index order), so results do not depend on scheduling.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "pne_internal.h"
+
+namespace pne {
+
+namespace {
+
+constexpr int kCtWarps = 4;          // warps per block, general contraction
+constexpr int kMaxSteps = 32;        // sites per cluster in the general kernel
+constexpr int kMaxFront = 12;        // frontier bonds
+constexpr int kMaxClose = kMaxDeg;
+constexpr int kStepInts = 8 + 3 * kMaxFront + 3 * kMaxClose;
+
+struct ContractParams {
+    int64_t n_clusters;
+    int n_members, n_sites;
+    int width, vwidth;
+    const int32_t *cl_edges, *cl_verts, *cl_size;
+    const int32_t *bond_site, *bond_dim, *bond_leg;   // closed geometry
+    const int32_t *blk_off;                           // [n_sites][64]
+    const int64_t *tens_off;
+    int64_t stride;                                   // entries per member
+    const void *M;                                    // double / float / bf16
+    const double *scale;                              // [members][n_sites]
+    const int8_t *zero;                               // [members][n_sites]
+    double *w;                                        // [members][n_clusters]
+    int32_t *nzc;                                     // [members][n_clusters]
+    int32_t *status;                                  // [0] buffer overflow
+};
+
+template <typename T> struct Load;
+template <> struct Load<double> {
+    static __device__ __forceinline__ double get(const void *p, int64_t i) { return ((const double *)p)[i]; }
+};
+template <> struct Load<float> {
+    static __device__ __forceinline__ float get(const void *p, int64_t i) { return ((const float *)p)[i]; }
+};
+struct LoadBF16 {
+    static __device__ __forceinline__ float get(const void *p, int64_t i)
+    {
+        return __bfloat162float(((const __nv_bfloat16 *)p)[i]);
+    }
+};
+
+__device__ __forceinline__ float rnd_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// operand rounding of the intermediate tensor: 0 none, 1 TF32, 2 BF16
+template <int R> __device__ __forceinline__ float rnd(float x)
+{
+    if (R == 1) return rnd_tf32(x);
+    if (R == 2) return __bfloat162float(__float2bfloat16_rn(x));
+    return x;
+}
+template <int R> __device__ __forceinline__ double rnd(double x) { return x; }
+
+__device__ __forceinline__ double pow2(int e) { return ldexp(1.0, e); }
+
+// ---------------------------------------------------------------- plan
+// Step layout (ints): [0] site, [1] mask, [2] nF (size of the new frontier),
+// [3] nC (closing bonds), [4] out_size, [5] close_size, [6..7] spare,
+// then dimsF[kMaxFront], sxF[kMaxFront], smF[kMaxFront],
+// dimsC[kMaxClose], sxC[kMaxClose], smC[kMaxClose].
+// Builds the elimination plan of one cluster (single thread).  Returns the
+// number of steps, or -1 when a limit is exceeded.
+__device__ int build_plan(const ContractParams &P, int64_t c, int *plan, int *sites_out,
+                          int maxT)
+{
+    const int32_t *E = P.cl_edges + c * P.width;
+    const int32_t *V = P.cl_verts + c * P.vwidth;
+    int s = 0;
+    while (s < P.width && E[s] >= 0) ++s;
+    int nv = 0;
+    while (nv < P.vwidth && V[nv] >= 0) ++nv;
+    if (nv > kMaxSteps) return -1;
+    // per vertex: leg -> local edge index
+    int legedge[kMaxSteps][kMaxDeg];
+    int mask[kMaxSteps];
+    for (int i = 0; i < nv; ++i) { mask[i] = 0; for (int l = 0; l < kMaxDeg; ++l) legedge[i][l] = -1; }
+    int ends[32][2];
+    int qd[32];
+    for (int k = 0; k < s; ++k) {
+        const int e = E[k];
+        qd[k] = P.bond_dim[e] - 1;
+        for (int side = 0; side < 2; ++side) {
+            const int x = P.bond_site[2 * e + side];
+            int lo = 0, hi = nv - 1, slot = -1;
+            while (lo <= hi) { int mid = (lo + hi) >> 1; if (V[mid] == x) { slot = mid; break; } if (V[mid] < x) lo = mid + 1; else hi = mid - 1; }
+            if (slot < 0) return -1;
+            ends[k][side] = slot;
+            const int leg = P.bond_leg[2 * e + side];
+            legedge[slot][leg] = k;
+            mask[slot] |= 1 << leg;
+        }
+    }
+    bool visited[kMaxSteps];
+    for (int i = 0; i < nv; ++i) visited[i] = false;
+    int F[kMaxFront], nF = 0;
+    for (int t = 0; t < nv; ++t) {
+        // greedy choice: smallest new frontier, then smallest work, then lowest slot
+        int best = -1, bestF = 1 << 30, bestW = 1 << 30;
+        for (int i = 0; i < nv; ++i) {
+            if (visited[i]) continue;
+            int closing = 0, nnew = 0;
+            for (int l = 0; l < kMaxDeg; ++l) {
+                const int k = legedge[i][l];
+                if (k < 0) continue;
+                const int other = ends[k][0] == i ? ends[k][1] : ends[k][0];
+                if (visited[other]) ++closing; else ++nnew;
+            }
+            const int f = nF - closing + nnew, wk = nF + nnew;
+            if (f < bestF || (f == bestF && wk < bestW)) { best = i; bestF = f; bestW = wk; }
+        }
+        const int v = best;
+        visited[v] = true;
+        int *st = plan + t * kStepInts;
+        int *dimsF = st + 8, *sxF = dimsF + kMaxFront, *smF = sxF + kMaxFront;
+        int *dimsC = smF + kMaxFront, *sxC = dimsC + kMaxClose, *smC = sxC + kMaxClose;
+        // strides of v's block: row-major over its C-legs, ascending leg order
+        int mstride[kMaxDeg];
+        {
+            int mul = 1;
+            for (int l = kMaxDeg - 1; l >= 0; --l)
+                if (legedge[v][l] >= 0) { mstride[l] = mul; mul *= qd[legedge[v][l]]; }
+        }
+        // strides of the current X: row-major over F
+        int xstride[kMaxFront];
+        {
+            int mul = 1;
+            for (int i = nF - 1; i >= 0; --i) { xstride[i] = mul; mul *= qd[F[i]]; }
+        }
+        int F2[kMaxFront], n2 = 0, nC = 0;
+        for (int i = 0; i < nF; ++i) {
+            const int k = F[i];
+            int leg = -1;
+            for (int l = 0; l < kMaxDeg; ++l) if (legedge[v][l] == k) leg = l;
+            if (leg >= 0) {                       // closing
+                dimsC[nC] = qd[k]; sxC[nC] = xstride[i]; smC[nC] = mstride[leg]; ++nC;
+            } else {                              // kept
+                if (n2 >= kMaxFront) return -1;
+                F2[n2] = k; dimsF[n2] = qd[k]; sxF[n2] = xstride[i]; smF[n2] = 0; ++n2;
+            }
+        }
+        for (int l = 0; l < kMaxDeg; ++l) {
+            const int k = legedge[v][l];
+            if (k < 0) continue;
+            const int other = ends[k][0] == v ? ends[k][1] : ends[k][0];
+            if (visited[other] && other != v) continue;   // already closed above
+            if (n2 >= kMaxFront) return -1;
+            F2[n2] = k; dimsF[n2] = qd[k]; sxF[n2] = 0; smF[n2] = mstride[l]; ++n2;
+        }
+        int outsz = 1, closz = 1;
+        for (int i = 0; i < n2; ++i) outsz *= dimsF[i];
+        for (int i = 0; i < nC; ++i) closz *= dimsC[i];
+        if (outsz > maxT) return -1;
+        st[0] = P.cl_verts[c * P.vwidth + v];
+        st[1] = mask[v];
+        st[2] = n2; st[3] = nC; st[4] = outsz; st[5] = closz;
+        sites_out[t] = v;
+        for (int i = 0; i < n2; ++i) F[i] = F2[i];
+        nF = n2;
+    }
+    return nv;
+}
+
+template <typename T, typename L, int R>
+__global__ void __launch_bounds__(kCtWarps * 32) contract_general_kernel(ContractParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *plan = (int *)smem_raw + wib * (kMaxSteps * kStepInts + kMaxSteps + 4);
+    int *sites = plan + kMaxSteps * kStepInts;
+    int *hdr = sites + kMaxSteps;
+    T *bufs = (T *)((int *)smem_raw + kCtWarps * (kMaxSteps * kStepInts + kMaxSteps + 4));
+    T *X0 = bufs + (int64_t)wib * 2 * kWarpTensorMax;
+    T *X1 = X0 + kWarpTensorMax;
+    for (int64_t c = (int64_t)blockIdx.x * kCtWarps + wib; c < P.n_clusters; c += (int64_t)gridDim.x * kCtWarps) {
+        if (lane == 0) hdr[0] = build_plan(P, c, plan, sites, kWarpTensorMax);
+        __syncwarp();
+        const int nsteps = hdr[0];
+        if (nsteps < 0) {
+            if (lane == 0) atomicExch(P.status, 1);
+            for (int b = lane; b < P.n_members; b += 32) {
+                P.w[(int64_t)b * P.n_clusters + c] = 0.0;
+                P.nzc[(int64_t)b * P.n_clusters + c] = 0;
+            }
+            continue;
+        }
+        for (int b = 0; b < P.n_members; ++b) {
+            T *X = X0, *Y = X1;
+            if (lane == 0) X[0] = (T)1;
+            __syncwarp();
+            int expo = 0;
+            for (int t = 0; t < nsteps; ++t) {
+                const int *st = plan + t * kStepInts;
+                const int site = st[0], mask = st[1], nF = st[2], nC = st[3], outsz = st[4], closz = st[5];
+                const int *dimsF = st + 8, *sxF = dimsF + kMaxFront, *smF = sxF + kMaxFront;
+                const int *dimsC = smF + kMaxFront, *sxC = dimsC + kMaxClose, *smC = sxC + kMaxClose;
+                const int64_t mbase = (int64_t)b * P.stride + P.tens_off[site] + P.blk_off[site * kBlkStride + mask];
+                T mx = (T)0;
+                for (int o = lane; o < outsz; o += 32) {
+                    int r = o, xb = 0, mb = 0;
+                    for (int i = nF - 1; i >= 0; --i) { const int d = r % dimsF[i]; r /= dimsF[i]; xb += d * sxF[i]; mb += d * smF[i]; }
+                    T acc = (T)0;
+                    for (int cc = 0; cc < closz; ++cc) {
+                        int rc = cc, xi = xb, mi = mb;
+                        for (int i = nC - 1; i >= 0; --i) { const int d = rc % dimsC[i]; rc /= dimsC[i]; xi += d * sxC[i]; mi += d * smC[i]; }
+                        acc = fma(rnd<R>(X[xi]), (T)L::get(P.M, mbase + mi), acc);
+                    }
+                    Y[o] = acc;
+                    mx = fmax(mx, fabs(acc));
+                }
+                for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+                __syncwarp();
+                if (mx > (T)0) {
+                    int e;
+                    frexp((double)mx, &e);
+                    const T sc = (T)pow2(-e);
+                    for (int o = lane; o < outsz; o += 32) Y[o] *= sc;
+                    expo += e;
+                }
+                __syncwarp();
+                T *tmp = X; X = Y; Y = tmp;
+            }
+            if (lane == 0) {
+                double wv = ldexp((double)X[0], expo);
+                int nz = 0;
+                for (int t = 0; t < nsteps; ++t) {
+                    const int site = plan[t * kStepInts];
+                    if (P.zero[(int64_t)b * P.n_sites + site]) { ++nz; wv *= P.scale[(int64_t)b * P.n_sites + site]; }
+                }
+                P.w[(int64_t)b * P.n_clusters + c] = wv;
+                P.nzc[(int64_t)b * P.n_clusters + c] = nz;
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Bond dimension 2: one excited value per bond, one number per site.
+template <typename T, typename L>
+__global__ void contract_q1_kernel(ContractParams P)
+{
+    const int64_t total = P.n_clusters * P.n_members;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i % P.n_clusters;
+        const int b = (int)(i / P.n_clusters);
+        const int32_t *E = P.cl_edges + c * P.width;
+        const int32_t *V = P.cl_verts + c * P.vwidth;
+        T prod = (T)1;
+        int expo = 0, nz = 0;
+        double zs = 1.0;
+        for (int j = 0; j < P.vwidth && V[j] >= 0; ++j) {
+            const int x = V[j];
+            int mask = 0;
+            for (int k = 0; k < P.width && E[k] >= 0; ++k) {
+                const int e = E[k];
+                if (P.bond_site[2 * e] == x) mask |= 1 << P.bond_leg[2 * e];
+                if (P.bond_site[2 * e + 1] == x) mask |= 1 << P.bond_leg[2 * e + 1];
+            }
+            const T m = (T)L::get(P.M, (int64_t)b * P.stride + P.tens_off[x] + P.blk_off[x * kBlkStride + mask]);
+            prod *= m;
+            if (prod != (T)0) { int e; frexp((double)prod, &e); prod *= (T)pow2(-e); expo += e; }
+            if (P.zero[(int64_t)b * P.n_sites + x]) { ++nz; zs *= P.scale[(int64_t)b * P.n_sites + x]; }
+        }
+        P.w[(int64_t)b * P.n_clusters + c] = ldexp((double)prod, expo) * zs;
+        P.nzc[(int64_t)b * P.n_clusters + c] = nz;
+    }
+}
+
+// ---------------------------------------------------------------- sums
+struct SumDesc {
+    int32_t level;       // 0: single clusters, l >= 1: rec.levels[l-1]
+    int32_t order;
+    int64_t begin, end;
+};
+
+struct SumParams {
+    const SumDesc *desc;
+    int n_desc;
+    int n_members;
+    int64_t n_clusters;
+    const double *w;
+    const int32_t *nzc;
+    const double *vac;        // [members][3]
+    const int32_t *lvl_idx[8];
+    int lvl_m[8];
+    double *partial;          // [members][n_desc][2]
+};
+
+constexpr int kSumThreads = 256;
+constexpr int64_t kSumChunk = 4096;
+
+__global__ void __launch_bounds__(kSumThreads) term_sum_kernel(SumParams P)
+{
+    __shared__ double sh[2][kSumThreads];
+    const int di = blockIdx.x, b = blockIdx.y;
+    const SumDesc d = P.desc[di];
+    const int nzero = (int)P.vac[3 * b + 2];
+    const double *w = P.w + (int64_t)b * P.n_clusters;
+    const int32_t *nz = P.nzc + (int64_t)b * P.n_clusters;
+    double s = 0.0, a = 0.0;
+    if (d.level == 0) {
+        for (int64_t i = d.begin + threadIdx.x; i < d.end; i += kSumThreads) {
+            const double v = (nz[i] == nzero) ? w[i] : 0.0;
+            s += v; a += fabs(v);
+        }
+    } else {
+        const int m = P.lvl_m[d.level - 1];
+        const int32_t *idx = P.lvl_idx[d.level - 1];
+        for (int64_t i = d.begin + threadIdx.x; i < d.end; i += kSumThreads) {
+            const int32_t *tp = idx + i * m;
+            double v = 1.0;
+            int z = 0;
+            for (int q = 0; q < m; ++q) { v *= w[tp[q]]; z += nz[tp[q]]; }
+            if (z != nzero) v = 0.0;
+            s += v; a += fabs(v);
+        }
+    }
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = a;
+    __syncthreads();
+    for (int off = kSumThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + off];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        P.partial[((int64_t)b * P.n_desc + di) * 2] = sh[0][0];
+        P.partial[((int64_t)b * P.n_desc + di) * 2 + 1] = sh[1][0];
+    }
+}
+
+// per (member, order): partials of that order in descriptor order
+__global__ void finalize_kernel(const double *partial, const SumDesc *desc, int n_desc, int n_members, int K,
+                                double *out /* [members][K+1][2] */)
+{
+    const int64_t total = (int64_t)n_members * (K + 1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / (K + 1)), k = (int)(i % (K + 1));
+        double s = 0.0, a = 0.0;
+        for (int d = 0; d < n_desc; ++d)
+            if (desc[d].order == k) {
+                s += partial[((int64_t)b * n_desc + d) * 2];
+                a += partial[((int64_t)b * n_desc + d) * 2 + 1];
+            }
+        out[i * 2] = s;
+        out[i * 2 + 1] = a;
+    }
+}
+
+// ---------------------------------------------------------------- ALL mode
+// Every subset E of the closed bonds (at most 30) with |E| <= K is a term.
+// Subsets of size k are visited by unranking k-combinations (colexicographic
+// order of the combinatorial number system).  Bond dimension 2 only: the term
+// divided by the vacuum is prod_v M_v[excited legs of v] over touched sites.
+struct AllParams {
+    int n_members, n_sites, Mc, K;
+    const int32_t *site_ptr, *site_bonds;  // closed geometry
+    const int32_t *blk_off;
+    const int64_t *tens_off;
+    int64_t stride;
+    const void *M;
+    const double *scale;
+    const int8_t *zero;
+    const double *vac;
+    const int64_t *binom;                  // [31][31]
+    const SumDesc *desc;                   // order, rank range [begin, end)
+    int n_desc;
+    double *partial;                       // [members][n_desc][2]
+    int64_t *conn_count;                   // [n_desc]: connected subsets (member 0 only)
+    const int32_t *bond_site;
+};
+
+__device__ uint32_t unrank_comb(int64_t r, int k, const int64_t *binom)
+{
+    uint32_t mask = 0;
+    for (int i = k; i >= 1; --i) {
+        int c = i - 1;
+        while (binom[(c + 1) * 31 + i] <= r) ++c;
+        r -= binom[c * 31 + i];
+        mask |= 1u << c;
+    }
+    return mask;
+}
+
+template <typename T, typename L>
+__global__ void __launch_bounds__(kSumThreads) all_q1_kernel(AllParams P)
+{
+    __shared__ double sh[2][kSumThreads];
+    __shared__ long long shc[kSumThreads];
+    const int di = blockIdx.x, b = blockIdx.y;
+    const SumDesc d = P.desc[di];
+    const int nzero = (int)P.vac[3 * b + 2];
+    double s = 0.0, a = 0.0;
+    long long conn = 0;
+    for (int64_t r = d.begin + threadIdx.x; r < d.end; r += kSumThreads) {
+        const uint32_t E = unrank_comb(r, d.order, P.binom);
+        T prod = (T)1;
+        int expo = 0, cover = 0;
+        double zs = 1.0;
+        for (int v = 0; v < P.n_sites; ++v) {
+            int mask = 0;
+            for (int p = P.site_ptr[v]; p < P.site_ptr[v + 1]; ++p)
+                if ((E >> P.site_bonds[p]) & 1u) mask |= 1 << (p - P.site_ptr[v]);
+            if (mask == 0) continue;
+            prod *= (T)L::get(P.M, (int64_t)b * P.stride + P.tens_off[v] + P.blk_off[v * kBlkStride + mask]);
+            if (prod != (T)0) { int e; frexp((double)prod, &e); prod *= (T)pow2(-e); expo += e; }
+            if (P.zero[(int64_t)b * P.n_sites + v]) { ++cover; zs *= P.scale[(int64_t)b * P.n_sites + v]; }
+        }
+        double val = (cover == nzero) ? ldexp((double)prod, expo) * zs : 0.0;
+        if (d.order == 0) val = (nzero == 0) ? 1.0 : 0.0;
+        s += val; a += fabs(val);
+        if (b == 0 && E != 0) {
+            // connectivity of E by vertex-set growth
+            uint32_t left = E & ~(E & (0u - E));
+            uint64_t cov = 0;
+            {
+                const int e0 = __ffs(E) - 1;
+                cov = (1ull << P.bond_site[2 * e0]) | (1ull << P.bond_site[2 * e0 + 1]);
+            }
+            bool grew = true;
+            while (grew && left) {
+                grew = false;
+                for (uint32_t rr = left; rr; rr &= rr - 1) {
+                    const int e = __ffs(rr) - 1;
+                    const uint64_t vm = (1ull << P.bond_site[2 * e]) | (1ull << P.bond_site[2 * e + 1]);
+                    if (vm & cov) { cov |= vm; left &= ~(1u << e); grew = true; }
+                }
+            }
+            if (!left) ++conn;
+        }
+    }
+    sh[0][threadIdx.x] = s; sh[1][threadIdx.x] = a; shc[threadIdx.x] = conn;
+    __syncthreads();
+    for (int off = kSumThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + off];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + off];
+            shc[threadIdx.x] += shc[threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        P.partial[((int64_t)b * P.n_desc + di) * 2] = sh[0][0];
+        P.partial[((int64_t)b * P.n_desc + di) * 2 + 1] = sh[1][0];
+        if (b == 0) P.conn_count[di] = shc[0];
+    }
+}
+
+int grid_for(int64_t n, int block, int n_sm, int per_sm = 32)
+{
+    int64_t g = (n + block - 1) / block;
+    const int64_t cap = (int64_t)n_sm * per_sm;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+bool all_dims_two(const Geometry &g)
+{
+    for (int b = 0; b < g.n_bonds; ++b) if (g.bond_dim[b] != 2) return false;
+    return true;
+}
+
+template <typename KERN>
+pne_status run_general(pne_ctx *ctx, KERN kern, const ContractParams &cp, size_t elem, cudaStream_t s)
+{
+    const size_t smem = (size_t)kCtWarps * ((kMaxSteps * kStepInts + kMaxSteps + 4) * 4 + 2 * kWarpTensorMax * elem);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int g = grid_for(cp.n_clusters, kCtWarps, ctx->n_sm, 16);
+    kern<<<g, kCtWarps * 32, smem, s>>>(cp);
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    return PNE_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Multiply-adds of each cluster's plan (the algorithmic work of the contraction).
+__global__ void __launch_bounds__(kCtWarps * 32) plan_work_kernel(ContractParams P, unsigned long long *total)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *plan = (int *)smem_raw + wib * (kMaxSteps * kStepInts + kMaxSteps + 4);
+    int *sites = plan + kMaxSteps * kStepInts;
+    for (int64_t c = (int64_t)blockIdx.x * kCtWarps + wib; c < P.n_clusters; c += (int64_t)gridDim.x * kCtWarps) {
+        if (lane == 0) {
+            const int n = build_plan(P, c, plan, sites, kWarpTensorMax);
+            unsigned long long f = 0;
+            for (int t = 0; t < n; ++t) f += (unsigned long long)plan[t * kStepInts + 4] * plan[t * kStepInts + 5];
+            atomicAdd(total, f);
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+pne_status launch_plan_work(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, uint64_t *fma)
+{
+    const pne_partition *p = t->part;
+    const EnumRecord &rec = *t->rec;
+    *fma = 0;
+    if (rec.n_clusters == 0) return PNE_OK;
+    ContractParams cp;
+    cp.n_clusters = (int64_t)rec.n_clusters; cp.n_members = 1; cp.n_sites = p->closed.n_sites;
+    cp.width = rec.width; cp.vwidth = rec.vwidth;
+    cp.cl_edges = (const int32_t *)rec.cl_edges.ptr; cp.cl_verts = (const int32_t *)rec.cl_verts.ptr;
+    cp.cl_size = (const int32_t *)rec.cl_size.ptr;
+    cp.bond_site = p->closed.d_bond_site; cp.bond_dim = p->closed.d_bond_dim; cp.bond_leg = p->closed.d_bond_leg;
+    DevBuf tot;
+    pne_status st = dev_alloc(ctx, tot, 8, s);
+    if (st) return st;
+    PNE_CUDA_TRY(ctx, cudaMemsetAsync(tot.ptr, 0, 8, s));
+    const size_t smem = (size_t)kCtWarps * (kMaxSteps * kStepInts + kMaxSteps + 4) * 4;
+    plan_work_kernel<<<grid_for(cp.n_clusters, kCtWarps, ctx->n_sm, 16), kCtWarps * 32, smem, s>>>(
+        cp, (unsigned long long *)tot.ptr);
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    unsigned long long h = 0;
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(&h, tot.ptr, 8, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    dev_free(ctx, tot, s);
+    *fma = h;
+    return PNE_OK;
+}
+
+pne_status launch_contract(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s)
+{
+    const pne_partition *p = t->part;
+    EnumRecord &rec = *t->rec;
+    if (rec.n_clusters == 0) return PNE_OK;
+    pne_status st = launch_convert(ctx, const_cast<pne_partition *>(p), dtype, s);
+    if (st) return st;
+    ContractParams cp;
+    cp.n_clusters = (int64_t)rec.n_clusters; cp.n_members = p->n_members; cp.n_sites = p->closed.n_sites;
+    cp.width = rec.width; cp.vwidth = rec.vwidth;
+    cp.cl_edges = (const int32_t *)rec.cl_edges.ptr; cp.cl_verts = (const int32_t *)rec.cl_verts.ptr;
+    cp.cl_size = (const int32_t *)rec.cl_size.ptr;
+    cp.bond_site = p->closed.d_bond_site; cp.bond_dim = p->closed.d_bond_dim; cp.bond_leg = p->closed.d_bond_leg;
+    cp.blk_off = p->closed.d_blk_off; cp.tens_off = p->closed.d_tens_off;
+    cp.stride = p->closed.tens_off[p->closed.n_sites];
+    cp.scale = (const double *)p->site_scale.ptr; cp.zero = (const int8_t *)p->site_zero.ptr;
+    cp.w = (double *)t->w.ptr; cp.nzc = (int32_t *)t->nzc.ptr; cp.status = (int32_t *)t->status.ptr;
+    const bool q1 = all_dims_two(p->closed);
+    ProfScope ps__(ctx, s, "contract");
+    if (dtype == PNE_F64) {
+        cp.M = p->Mb.ptr;
+        if (q1) contract_q1_kernel<double, Load<double>><<<grid_for(cp.n_clusters * cp.n_members, 256, ctx->n_sm), 256, 0, s>>>(cp);
+        else return run_general(ctx, contract_general_kernel<double, Load<double>, 0>, cp, 8, s);
+    } else if (dtype == PNE_BF16) {
+        cp.M = p->Mb16.ptr;
+        if (q1) contract_q1_kernel<float, LoadBF16><<<grid_for(cp.n_clusters * cp.n_members, 256, ctx->n_sm), 256, 0, s>>>(cp);
+        else return run_general(ctx, contract_general_kernel<float, LoadBF16, 2>, cp, 4, s);
+    } else {
+        cp.M = p->Mb32.ptr;
+        if (q1) contract_q1_kernel<float, Load<float>><<<grid_for(cp.n_clusters * cp.n_members, 256, ctx->n_sm), 256, 0, s>>>(cp);
+        else if (dtype == PNE_TF32) return run_general(ctx, contract_general_kernel<float, Load<float>, 1>, cp, 4, s);
+        else return run_general(ctx, contract_general_kernel<float, Load<float>, 0>, cp, 4, s);
+    }
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    return PNE_OK;
+}
+
+pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, std::vector<double> &c,
+                       std::vector<double> &abs_c, int32_t *h_status)
+{
+    const pne_partition *p = t->part;
+    const int K = t->K, B = p->n_members;
+    std::vector<SumDesc> desc;
+    if (t->mode == PNE_MODE_ALL) {
+        // handled by launch_all_mode; sums were written into t->sums
+        std::vector<double> buf((size_t)B * (K + 1) * 2);
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(buf.data(), t->sums.ptr, buf.size() * 8, cudaMemcpyDeviceToHost, s));
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_status, t->status.ptr, 4, cudaMemcpyDeviceToHost, s));
+        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        c.assign((size_t)B * (K + 1), 0.0); abs_c.assign((size_t)B * (K + 1), 0.0);
+        for (size_t i = 0; i < c.size(); ++i) { c[i] = buf[2 * i]; abs_c[i] = buf[2 * i + 1]; }
+        return PNE_OK;
+    }
+    const EnumRecord &rec = *t->rec;
+    for (int k = 1; k <= K; ++k)
+        for (int64_t b0 = rec.size_start[k]; b0 < rec.size_start[k + 1]; b0 += kSumChunk)
+            desc.push_back({0, k, b0, std::min<int64_t>(b0 + kSumChunk, rec.size_start[k + 1])});
+    if (rec.levels.size() > 8) { set_error(ctx, PNE_EOVERFLOW, "too many tuple levels"); return PNE_EOVERFLOW; }
+    for (size_t l = 0; l < rec.levels.size(); ++l)
+        for (int k = 0; k <= K; ++k)
+            for (int64_t b0 = rec.levels[l].order_start[k]; b0 < rec.levels[l].order_start[k + 1]; b0 += kSumChunk)
+                desc.push_back({(int32_t)l + 1, k, b0, std::min<int64_t>(b0 + kSumChunk, rec.levels[l].order_start[k + 1])});
+    const int nd = (int)desc.size();
+    DevBuf dd, part, out;
+    pne_status st;
+    if ((st = dev_alloc(ctx, dd, std::max(nd, 1) * sizeof(SumDesc), s))) return st;
+    if ((st = dev_alloc(ctx, part, (size_t)B * std::max(nd, 1) * 16, s))) return st;
+    if ((st = dev_alloc(ctx, out, (size_t)B * (K + 1) * 16, s))) return st;
+    if (nd > 0) {
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dd.ptr, desc.data(), nd * sizeof(SumDesc), cudaMemcpyHostToDevice, s));
+        SumParams sp;
+        sp.desc = (const SumDesc *)dd.ptr; sp.n_desc = nd; sp.n_members = B;
+        sp.n_clusters = (int64_t)rec.n_clusters;
+        sp.w = (const double *)t->w.ptr; sp.nzc = (const int32_t *)t->nzc.ptr;
+        sp.vac = (const double *)p->vac.ptr;
+        for (int l = 0; l < 8; ++l) { sp.lvl_idx[l] = nullptr; sp.lvl_m[l] = 0; }
+        for (size_t l = 0; l < rec.levels.size(); ++l) {
+            sp.lvl_idx[l] = (const int32_t *)rec.levels[l].idx.ptr;
+            sp.lvl_m[l] = rec.levels[l].m;
+        }
+        sp.partial = (double *)part.ptr;
+        if (B > 65535) { set_error(ctx, PNE_EINVAL, "too many tensor sets"); return PNE_EINVAL; }
+        {
+            ProfScope ps__(ctx, s, "term_sum");
+            term_sum_kernel<<<dim3(nd, B), kSumThreads, 0, s>>>(sp);
+        }
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+        {
+            ProfScope ps__(ctx, s, "term_sum");
+            finalize_kernel<<<grid_for((int64_t)B * (K + 1), 128, ctx->n_sm), 128, 0, s>>>(
+            (const double *)part.ptr, (const SumDesc *)dd.ptr, nd, B, K, (double *)out.ptr);
+        }
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+    } else {
+        PNE_CUDA_TRY(ctx, cudaMemsetAsync(out.ptr, 0, (size_t)B * (K + 1) * 16, s));
+    }
+    std::vector<double> buf((size_t)B * (K + 1) * 2);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(buf.data(), out.ptr, buf.size() * 8, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_status, t->status.ptr, 4, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    dev_free(ctx, dd, s); dev_free(ctx, part, s); dev_free(ctx, out, s);
+    c.assign((size_t)B * (K + 1), 0.0); abs_c.assign((size_t)B * (K + 1), 0.0);
+    for (size_t i = 0; i < c.size(); ++i) { c[i] = buf[2 * i]; abs_c[i] = buf[2 * i + 1]; }
+    return PNE_OK;
+}
+
+pne_status launch_all_mode(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s)
+{
+    const pne_partition *p = t->part;
+    const Geometry &g = p->closed;
+    const int K = t->K, B = p->n_members, Mc = g.n_bonds;
+    if (Mc > kMaxAllBonds || g.n_sites > 64) {
+        set_error(ctx, PNE_EINVAL, "ALL mode needs <= 30 closed bonds and <= 64 sites"); return PNE_EINVAL;
+    }
+    if (!all_dims_two(g)) {
+        set_error(ctx, PNE_EINVAL, "ALL mode on the GPU needs bond dimension 2"); return PNE_EINVAL;
+    }
+    pne_status st = launch_convert(ctx, const_cast<pne_partition *>(p), dtype, s);
+    if (st) return st;
+    std::vector<int64_t> binom(31 * 31, 0);
+    for (int n = 0; n <= 30; ++n) {
+        binom[n * 31] = 1;
+        for (int k = 1; k <= n; ++k) binom[n * 31 + k] = binom[(n - 1) * 31 + k - 1] + (k <= n - 1 ? binom[(n - 1) * 31 + k] : 0);
+    }
+    std::vector<SumDesc> desc;
+    for (int k = 0; k <= std::min(K, Mc); ++k) {
+        const int64_t nk = binom[Mc * 31 + k];
+        for (int64_t b0 = 0; b0 < nk; b0 += kSumChunk) desc.push_back({0, k, b0, std::min<int64_t>(b0 + kSumChunk, nk)});
+    }
+    const int nd = (int)desc.size();
+    DevBuf dd, bn, part, conn;
+    if ((st = dev_alloc(ctx, dd, nd * sizeof(SumDesc), s))) return st;
+    if ((st = dev_alloc(ctx, bn, binom.size() * 8, s))) return st;
+    if ((st = dev_alloc(ctx, part, (size_t)B * nd * 16, s))) return st;
+    if ((st = dev_alloc(ctx, conn, (size_t)nd * 8, s))) return st;
+    if (!t->sums.ptr && (st = dev_alloc(ctx, t->sums, (size_t)B * (K + 1) * 16, s))) return st;
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dd.ptr, desc.data(), nd * sizeof(SumDesc), cudaMemcpyHostToDevice, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bn.ptr, binom.data(), binom.size() * 8, cudaMemcpyHostToDevice, s));
+    AllParams ap;
+    ap.n_members = B; ap.n_sites = g.n_sites; ap.Mc = Mc; ap.K = K;
+    ap.site_ptr = g.d_site_ptr; ap.site_bonds = g.d_site_bonds; ap.blk_off = g.d_blk_off;
+    ap.tens_off = g.d_tens_off; ap.stride = g.tens_off[g.n_sites];
+    ap.scale = (const double *)p->site_scale.ptr; ap.zero = (const int8_t *)p->site_zero.ptr;
+    ap.vac = (const double *)p->vac.ptr; ap.binom = (const int64_t *)bn.ptr;
+    ap.desc = (const SumDesc *)dd.ptr; ap.n_desc = nd; ap.partial = (double *)part.ptr;
+    ap.conn_count = (int64_t *)conn.ptr; ap.bond_site = g.d_bond_site;
+    {
+        ProfScope ps_all__(ctx, s, "all_terms");
+        if (dtype == PNE_F64) { ap.M = p->Mb.ptr; all_q1_kernel<double, Load<double>><<<dim3(nd, B), kSumThreads, 0, s>>>(ap); }
+        else if (dtype == PNE_BF16) { ap.M = p->Mb16.ptr; all_q1_kernel<float, LoadBF16><<<dim3(nd, B), kSumThreads, 0, s>>>(ap); }
+        else { ap.M = p->Mb32.ptr; all_q1_kernel<float, Load<float>><<<dim3(nd, B), kSumThreads, 0, s>>>(ap); }
+    }
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    {
+        ProfScope ps__(ctx, s, "term_sum");
+        finalize_kernel<<<grid_for((int64_t)B * (K + 1), 128, ctx->n_sm), 128, 0, s>>>(
+        (const double *)part.ptr, (const SumDesc *)dd.ptr, nd, B, K, (double *)t->sums.ptr);
+    }
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    std::vector<int64_t> hc(nd);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(hc.data(), conn.ptr, nd * 8, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    uint64_t nconn = 0;
+    for (int i = 0; i < nd; ++i) nconn += (uint64_t)hc[i];
+    t->rec->n_clusters = nconn;
+    dev_free(ctx, dd, s); dev_free(ctx, bn, s); dev_free(ctx, part, s); dev_free(ctx, conn, s);
+    return PNE_OK;
+}
+
+}  // namespace pne

@@ -1,0 +1,773 @@
+// Cluster and term enumeration on the GPU (integer work only).
+//
+// Clusters (Sec. III.A): connected sets C of closed bonds with |C| <= K.  In
+// LOOP mode no site of C may have C-degree one (a dangling excitation, which
+// vanishes at a BP fixed point).  Each connected set is generated exactly once
+// from its smallest bond (the anchor) by a Redelmeier-style search: a node of
+// the search tree is (S, U), S the current set and U the ordered list of
+// candidate bonds still to try; taking U[i] gives the child
+// (S + U[i], U[i+1..] ++ new), where `new` are the bonds at the site U[i]
+// brings in (if any), larger than the anchor, whose other end is not yet in S.
+// In LOOP mode a subtree is skipped when its set cannot be completed: more
+// degree-one sites than 2 (K - |S|) (each further bond repairs at most two),
+// or a degree-one site none of whose bonds is in the candidate list -- every
+// bond that touches a site of S is either in S, in the list, or was already
+// tried and is excluded from the subtree, and bonds found later join new
+// sites only.
+//
+// Parallel schedule: the first levels of every anchor's tree are expanded
+// level by level (one thread per node); each node of the last prefix level is
+// then searched depth-first by one thread.  Every unit first counts what it
+// emits per cluster size; an exclusive scan over (size, unit) gives each unit
+// its output slots, and a second pass writes.  The output is grouped by size
+// and deterministic.
+//
+// Terms (Eq. A4): a term is a set of pairwise vertex-disjoint clusters with
+// total size <= K (the connected components of one P/Q string).  Tuples
+// (i_1 < i_2 < ...) of cluster ids are built one length at a time, each
+// extended by every larger id whose size fits and whose sites are disjoint.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "pne_internal.h"
+
+namespace pne {
+
+namespace {
+
+constexpr int kPrefixMax = 5;     // deepest prefix level kept as explicit nodes
+constexpr int kNodeU = 32;        // candidate-list capacity of a prefix node
+constexpr int64_t kPrefixTarget = 65536;   // expand while a level has fewer nodes
+
+struct Node {
+    int32_t S[kPrefixMax];
+    int32_t U[kNodeU];
+    int32_t nU;
+    int32_t t;
+};
+
+struct GeomView {
+    const int32_t *bond_site;     // closed geometry [Mc][2]
+    const int32_t *site_ptr, *site_bonds;
+};
+
+struct Emit {
+    int32_t *edges;               // [n][width]
+    int32_t *verts;               // [n][vwidth]
+    int32_t *size;                // [n]
+    int width, vwidth;
+};
+
+// Vertex multiset of a bond set, with the number of degree-one vertices.
+template <int NV>
+struct VSet {
+    int32_t v[NV];
+    int32_t d[NV];
+    int n = 0;
+    int dang = 0;
+    __device__ int find(int x) const {
+        for (int i = 0; i < n; ++i) if (v[i] == x) return i;
+        return -1;
+    }
+    __device__ void inc(int x) {
+        int i = find(x);
+        if (i < 0) { i = n++; v[i] = x; d[i] = 0; }
+        int o = d[i]++;
+        if (o == 0) ++dang; else if (o == 1) --dang;
+    }
+    __device__ void dec(int x) {
+        int i = find(x);
+        int o = d[i]--;
+        if (o == 1) { --dang; --n; }          // the vertex was the last one added
+        else if (o == 2) ++dang;
+    }
+};
+
+__device__ __forceinline__ bool valid_set(int mode, int dang) { return mode == PNE_MODE_ALL || dang == 0; }
+__device__ __forceinline__ bool may_grow(int mode, int s, int K, int dang)
+{
+    return s < K && (mode == PNE_MODE_ALL || dang <= 2 * (K - s));
+}
+
+// every degree-one site of V has a bond among the candidates U[lo..hi)
+template <int NV>
+__device__ bool repairable(const VSet<NV> &V, const int32_t *UA, const int32_t *UB, int lo, int hi)
+{
+    if (V.dang == 0) return true;
+    for (int i = 0; i < V.n; ++i) {
+        if (V.d[i] != 1) continue;
+        const int x = V.v[i];
+        bool found = false;
+        for (int q = lo; q < hi; ++q)
+            if (UA[q] == x || UB[q] == x) { found = true; break; }
+        if (!found) return false;
+    }
+    return true;
+}
+
+template <int NV>
+__device__ void write_cluster(const Emit &o, int64_t slot, const int32_t *S, int s, const VSet<NV> &V)
+{
+    int32_t *e = o.edges + slot * o.width;
+    for (int i = 0; i < s; ++i) {            // insertion sort into the row
+        int x = S[i], j = i;
+        while (j > 0 && e[j - 1] > x) { e[j] = e[j - 1]; --j; }
+        e[j] = x;
+    }
+    for (int i = s; i < o.width; ++i) e[i] = -1;
+    int32_t *vv = o.verts + slot * o.vwidth;
+    for (int i = 0; i < V.n; ++i) {
+        int x = V.v[i], j = i;
+        while (j > 0 && vv[j - 1] > x) { vv[j] = vv[j - 1]; --j; }
+        vv[j] = x;
+    }
+    for (int i = V.n; i < o.vwidth; ++i) vv[i] = -1;
+    o.size[slot] = s;
+}
+
+// Bonds at new vertex b (> anchor, other end not in V), appended to U.
+template <int NV>
+__device__ int append_new(const GeomView &g, int b, int e, int anchor, const VSet<NV> &V,
+                          int32_t *U, int32_t *UA, int32_t *UB, int ne, int cap, int32_t *overflow)
+{
+    for (int p = g.site_ptr[b]; p < g.site_ptr[b + 1]; ++p) {
+        const int f = g.site_bonds[p];
+        if (f == e || f <= anchor) continue;
+        const int c = g.bond_site[2 * f] == b ? g.bond_site[2 * f + 1] : g.bond_site[2 * f];
+        if (V.find(c) >= 0) continue;
+        if (ne >= cap) { atomicExch(overflow, 1); return ne; }
+        U[ne] = f; UA[ne] = b; UB[ne] = c;
+        ++ne;
+    }
+    return ne;
+}
+
+// ---------------------------------------------------------------- roots
+__global__ void roots_kernel(GeomView g, int n_closed, int K, int mode, Node *nodes,
+                             int32_t *counts /* [K+1][n_closed] */, Emit out, const int64_t *base,
+                             int write, int32_t *overflow)
+{
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n_closed; a += gridDim.x * blockDim.x) {
+        const int x0 = g.bond_site[2 * a], x1 = g.bond_site[2 * a + 1];
+        if (!write) {
+            Node nd;
+            nd.S[0] = a; nd.t = 1;
+            int n = 0;
+            for (int p = g.site_ptr[x0]; p < g.site_ptr[x0 + 1]; ++p) {
+                int f = g.site_bonds[p];
+                if (f > a) { if (n < kNodeU) nd.U[n++] = f; else atomicExch(overflow, 1); }
+            }
+            for (int p = g.site_ptr[x1]; p < g.site_ptr[x1 + 1]; ++p) {
+                int f = g.site_bonds[p];
+                if (f <= a) continue;
+                const int c = g.bond_site[2 * f] == x1 ? g.bond_site[2 * f + 1] : g.bond_site[2 * f];
+                if (c == x0) continue;                 // parallel bond, already listed at x0
+                if (n < kNodeU) nd.U[n++] = f; else atomicExch(overflow, 1);
+            }
+            nd.nU = n;
+            nodes[a] = nd;
+            counts[1 * n_closed + a] = (mode == PNE_MODE_ALL) ? 1 : 0;
+        } else if (mode == PNE_MODE_ALL) {
+            VSet<2> V;
+            V.inc(x0); V.inc(x1);
+            int32_t S[1] = {a};
+            write_cluster(out, base[1 * n_closed + a], S, 1, V);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- prefix expansion
+// pass 0: count child nodes and emissions; pass 1: write child nodes;
+// pass 2: write emitted clusters.
+__global__ void expand_kernel(GeomView g, const Node *nodes, int64_t n_nodes, int K, int mode, int pass,
+                              int32_t *child_count, const int64_t *child_off, Node *children,
+                              int32_t *counts /* [K+1][n_nodes] */, Emit out, const int64_t *base,
+                              int32_t *overflow)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n_nodes;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const Node nd = nodes[u];
+        const int t = nd.t, anchor = nd.S[0];
+        VSet<kPrefixMax + 2> V;
+        for (int i = 0; i < t; ++i) { V.inc(g.bond_site[2 * nd.S[i]]); V.inc(g.bond_site[2 * nd.S[i] + 1]); }
+        int32_t S[kPrefixMax + 1];
+        for (int i = 0; i < t; ++i) S[i] = nd.S[i];
+        int32_t U[kNodeU], UA[kNodeU], UB[kNodeU];
+        for (int i = 0; i < nd.nU; ++i) {
+            U[i] = nd.U[i]; UA[i] = g.bond_site[2 * U[i]]; UB[i] = g.bond_site[2 * U[i] + 1];
+        }
+        int n_child = 0, n_emit = 0;
+        int64_t child_slot = (pass == 1) ? child_off[u] : 0;
+        int64_t emit_slot = (pass == 2) ? base[(int64_t)(t + 1) * n_nodes + u] : 0;
+        for (int i = 0; i < nd.nU; ++i) {
+            const int e = nd.U[i];
+            const int a0 = g.bond_site[2 * e], a1 = g.bond_site[2 * e + 1];
+            const int b = V.find(a0) < 0 ? a0 : (V.find(a1) < 0 ? a1 : -1);
+            V.inc(a0); V.inc(a1);
+            S[t] = e;
+            if (valid_set(mode, V.dang)) {
+                if (pass == 2) write_cluster(out, emit_slot, S, t + 1, V);
+                ++emit_slot; ++n_emit;
+            }
+            if (may_grow(mode, t + 1, K, V.dang)) {
+                int ne = nd.nU;
+                if (b >= 0) ne = append_new(g, b, e, anchor, V, U, UA, UB, ne, kNodeU, overflow);
+                if (mode == PNE_MODE_ALL || repairable(V, UA, UB, i + 1, ne)) {
+                    if (pass == 1) {
+                        Node c;
+                        for (int q = 0; q <= t; ++q) c.S[q] = S[q];
+                        c.t = t + 1;
+                        int m = 0;
+                        for (int q = i + 1; q < ne; ++q) c.U[m++] = U[q];
+                        c.nU = m;
+                        children[child_slot] = c;
+                    }
+                    ++child_slot; ++n_child;
+                }
+            }
+            V.dec(a1); V.dec(a0);
+        }
+        if (pass == 0) {
+            child_count[u] = n_child;
+            counts[(int64_t)(t + 1) * n_nodes + u] = n_emit;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- depth-first tasks
+template <int KMAX, int UMAX>
+__global__ void __launch_bounds__(128) dfs_kernel(GeomView g, const Node *nodes, int64_t n_nodes, int K,
+                                                  int mode, int write, int32_t *counts /* [K+1][n_nodes] */,
+                                                  Emit out, const int64_t *base, int32_t *overflow)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n_nodes;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const Node &nd = nodes[u];
+        const int t0 = nd.t, anchor = nd.S[0];
+        VSet<KMAX + 1> V;
+        int32_t S[KMAX];
+        int s = t0;
+        for (int i = 0; i < t0; ++i) {
+            S[i] = nd.S[i];
+            V.inc(g.bond_site[2 * S[i]]); V.inc(g.bond_site[2 * S[i] + 1]);
+        }
+        int32_t U[UMAX], UA[UMAX], UB[UMAX];
+        for (int i = 0; i < nd.nU; ++i) {
+            U[i] = nd.U[i]; UA[i] = g.bond_site[2 * U[i]]; UB[i] = g.bond_site[2 * U[i] + 1];
+        }
+        int32_t pos[KMAX], end[KMAX];
+        int32_t cnt[KMAX + 1];
+        int64_t slot[KMAX + 1];
+        for (int q = 0; q <= KMAX; ++q) {
+            cnt[q] = 0;
+            slot[q] = (write && q <= K) ? base[(int64_t)q * n_nodes + u] : 0;
+        }
+        int lvl = 0;
+        pos[0] = 0; end[0] = nd.nU;
+        for (;;) {
+            if (pos[lvl] >= end[lvl]) {
+                if (lvl == 0) break;
+                --lvl;
+                const int e = S[--s];
+                V.dec(g.bond_site[2 * e + 1]); V.dec(g.bond_site[2 * e]);
+                ++pos[lvl];
+                continue;
+            }
+            const int e = U[pos[lvl]];
+            const int a0 = g.bond_site[2 * e], a1 = g.bond_site[2 * e + 1];
+            const int b = V.find(a0) < 0 ? a0 : (V.find(a1) < 0 ? a1 : -1);
+            V.inc(a0); V.inc(a1);
+            S[s++] = e;
+            if (valid_set(mode, V.dang)) {
+                if (write) write_cluster(out, slot[s]++, S, s, V);
+                else ++cnt[s];
+            }
+            if (may_grow(mode, s, K, V.dang)) {
+                int ne = end[lvl];
+                if (b >= 0) ne = append_new(g, b, e, anchor, V, U, UA, UB, ne, UMAX, overflow);
+                if (mode == PNE_MODE_ALL || repairable(V, UA, UB, pos[lvl] + 1, ne)) {
+                    ++lvl;
+                    pos[lvl] = pos[lvl - 1] + 1;
+                    end[lvl] = ne;
+                    continue;
+                }
+            }
+            --s;
+            V.dec(a1); V.dec(a0);
+            ++pos[lvl];
+        }
+        if (!write)
+            for (int q = t0 + 1; q <= K; ++q) counts[(int64_t)q * n_nodes + u] = cnt[q];
+    }
+}
+
+// ---------------------------------------------------------------- scan
+constexpr int kScanBlock = 1024;
+
+__global__ void scan_block_kernel(int64_t *data, int64_t n, int64_t *block_sums)
+{
+    __shared__ int64_t sh[kScanBlock];
+    const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    int64_t x = (i < n) ? data[i] : 0;
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int off = 1; off < kScanBlock; off <<= 1) {
+        int64_t y = (threadIdx.x >= (unsigned)off) ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += y;
+        __syncthreads();
+    }
+    if (i < n) data[i] = sh[threadIdx.x] - x;       // exclusive
+    if (threadIdx.x == kScanBlock - 1) block_sums[blockIdx.x] = sh[threadIdx.x];
+}
+
+__global__ void scan_add_kernel(int64_t *data, int64_t n, const int64_t *block_offsets)
+{
+    const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    if (i < n) data[i] += block_offsets[blockIdx.x];
+}
+
+__global__ void widen_kernel(const int32_t *src, int64_t *dst, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// ---------------------------------------------------------------- tuples
+struct TupleParams {
+    const int32_t *verts;     // [n][vwidth] sorted, -1 pad
+    const int32_t *size;      // [n]
+    int vwidth, K, m;         // m: length of the input tuples
+    const int32_t *in;        // [n_in][m] input tuples (m == 1: the anchors are cluster ids)
+    const int32_t *in_order;  // [n_in] order of each input tuple
+    int64_t n_in;
+    const int64_t *size_end;  // [K+2]: first cluster index with size > s  (size_end[s])
+    const int64_t *unit_off;  // [n_in + 1] chunk offsets
+    int64_t n_units;
+    int32_t *counts;          // [K+1][n_units]
+    const int64_t *base;      // [K+1][n_units]
+    int32_t *out;             // [n_out][m+1]
+    int32_t *out_order;
+};
+
+constexpr int kTupleChunk = 128;
+
+__device__ __forceinline__ bool disjoint_sorted(const int32_t *a, const int32_t *b, int w)
+{
+    // both sorted ascending, -1 padded at the end
+    int i = 0, j = 0;
+    while (i < w && j < w && a[i] >= 0 && b[j] >= 0) {
+        if (a[i] == b[j]) return false;
+        if (a[i] < b[j]) ++i; else ++j;
+    }
+    return true;
+}
+
+__global__ void tuple_chunks_kernel(TupleParams p, int64_t *n_chunks)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < p.n_in;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t *tp = p.in + t * p.m;
+        const int last = tp[p.m - 1];
+        const int o = p.in_order[t];
+        int64_t lo = (int64_t)last + 1, hi = (o < p.K) ? p.size_end[p.K - o] : lo;
+        int64_t nc = hi > lo ? (hi - lo + kTupleChunk - 1) / kTupleChunk : 0;
+        n_chunks[t] = nc;
+    }
+}
+
+__global__ void tuple_kernel(TupleParams p, int write)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < p.n_units;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        // locate the input tuple of this unit (binary search in unit_off)
+        int64_t lo = 0, hi = p.n_in;
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) / 2;
+            if (p.unit_off[mid] <= u) lo = mid; else hi = mid;
+        }
+        const int64_t t = lo;
+        const int64_t chunk = u - p.unit_off[t];
+        const int32_t *tp = p.in + t * p.m;
+        const int last = tp[p.m - 1];
+        const int o = p.in_order[t];
+        const int64_t j0 = (int64_t)last + 1 + chunk * kTupleChunk;
+        int64_t j1 = p.size_end[p.K - o];
+        if (j1 > j0 + kTupleChunk) j1 = j0 + kTupleChunk;
+        int32_t cnt[kMaxOrder + 1];
+        int64_t slot[kMaxOrder + 1];
+        for (int q = 0; q <= p.K; ++q) {
+            cnt[q] = 0;
+            slot[q] = write ? p.base[(int64_t)q * p.n_units + u] : 0;
+        }
+        for (int64_t j = j0; j < j1; ++j) {
+            const int32_t *vj = p.verts + j * p.vwidth;
+            bool ok = true;
+            for (int q = 0; q < p.m && ok; ++q) ok = disjoint_sorted(p.verts + (int64_t)tp[q] * p.vwidth, vj, p.vwidth);
+            if (!ok) continue;
+            const int ord = o + p.size[j];
+            if (write) {
+                const int64_t s = slot[ord]++;
+                int32_t *dst = p.out + s * (p.m + 1);
+                for (int q = 0; q < p.m; ++q) dst[q] = tp[q];
+                dst[p.m] = (int32_t)j;
+                p.out_order[s] = ord;
+            } else {
+                ++cnt[ord];
+            }
+        }
+        if (!write)
+            for (int q = 0; q <= p.K; ++q) p.counts[(int64_t)q * p.n_units + u] = cnt[q];
+    }
+}
+
+__global__ void iota_order_kernel(int32_t *idx, int32_t *ord, const int32_t *size, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        idx[i] = (int32_t)i;
+        ord[i] = size[i];
+    }
+}
+
+int grid1(int64_t n, int block, int n_sm)
+{
+    int64_t g = (n + block - 1) / block;
+    const int64_t cap = (int64_t)n_sm * 64;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+// exclusive scan (in place) of n int64 values; the total is returned on the host
+pne_status device_exclusive_scan(pne_ctx *ctx, int64_t *d, int64_t n, int64_t *h_total, cudaStream_t s)
+{
+    if (n == 0) { *h_total = 0; return PNE_OK; }
+    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    DevBuf sums;
+    pne_status st = dev_alloc(ctx, sums, (size_t)(nb + 1) * 8, s);
+    if (st) return st;
+    int64_t *bs = (int64_t *)sums.ptr;
+    {
+        ProfScope ps__(ctx, s, "scan");
+        scan_block_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(d, n, bs);
+    }
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    int64_t tot = 0;
+    if (nb > 1) {
+        st = device_exclusive_scan(ctx, bs, nb, &tot, s);
+        if (st) { dev_free(ctx, sums, s); return st; }
+        {
+            ProfScope ps__(ctx, s, "scan");
+            scan_add_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(d, n, bs);
+        }
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+    } else {
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(&tot, bs, 8, cudaMemcpyDeviceToHost, s));
+        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    }
+    *h_total = tot;
+    dev_free(ctx, sums, s);
+    return PNE_OK;
+}
+
+namespace {
+
+// counts [rows][cols] int32 -> base (exclusive scan, row-major) int64; per-row totals
+pne_status scan_counts(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t cols, DevBuf &base,
+                       std::vector<int64_t> &row_tot, cudaStream_t s)
+{
+    const int64_t n = (int64_t)rows * cols;
+    pne_status st = dev_alloc(ctx, base, (size_t)std::max<int64_t>(n, 1) * 8, s);
+    if (st) return st;
+    int64_t *b = (int64_t *)base.ptr;
+    if (n > 0) {
+        ProfScope ps__(ctx, s, "scan");
+        widen_kernel<<<grid1(n, 256, ctx->n_sm), 256, 0, s>>>(d_counts, b, n);
+    }
+    // per-row totals come from the scanned values at row boundaries
+    int64_t total = 0;
+    st = device_exclusive_scan(ctx, b, n, &total, s);
+    if (st) return st;
+    std::vector<int64_t> starts(rows + 1, 0);
+    for (int r = 0; r < rows; ++r)
+        if (cols > 0 && r * cols < n)
+            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(&starts[r], b + (int64_t)r * cols, 8, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    starts[rows] = total;
+    if (cols == 0) for (int r = 0; r <= rows; ++r) starts[r] = 0;
+    row_tot.assign(rows, 0);
+    for (int r = 0; r < rows; ++r) row_tot[r] = starts[r + 1] - starts[r];
+    return PNE_OK;
+}
+
+}  // namespace
+
+pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, EnumRecord &rec,
+                              cudaStream_t s)
+{
+    const int Mc = g.n_bonds;
+    rec.K = K; rec.mode = mode; rec.n_closed = Mc;
+    rec.width = std::max(1, K);
+    rec.vwidth = K + 1;
+    int maxdeg = g.max_deg;
+    const int umax_need = 2 * (maxdeg - 1) + K * (maxdeg - 1) + 2;
+    if (K > 32 || umax_need > 128) {
+        set_error(ctx, PNE_EINVAL, "expansion order too large for the cluster search");
+        return PNE_EINVAL;
+    }
+    if ((kPrefixMax + 1) * (maxdeg - 1) > kNodeU) { set_error(ctx, PNE_EINVAL, "site degree too large"); return PNE_EINVAL; }
+    GeomView gv{g.d_bond_site, g.d_site_ptr, g.d_site_bonds};
+    DevBuf flag;
+    pne_status st = dev_alloc(ctx, flag, 8, s);
+    if (st) return st;
+    int32_t *overflow = (int32_t *)flag.ptr;
+    PNE_CUDA_TRY(ctx, cudaMemsetAsync(overflow, 0, 8, s));
+
+    // levels of prefix nodes
+    struct Level { DevBuf nodes; int64_t n = 0; DevBuf counts; DevBuf base; std::vector<int64_t> tot; };
+    std::vector<Level> lv(1);
+    lv[0].n = Mc;
+    if ((st = dev_alloc(ctx, lv[0].nodes, sizeof(Node) * std::max(Mc, 1), s))) return st;
+    if ((st = dev_alloc(ctx, lv[0].counts, (size_t)(K + 1) * std::max(Mc, 1) * 4, s))) return st;
+    PNE_CUDA_TRY(ctx, cudaMemsetAsync(lv[0].counts.ptr, 0, (size_t)(K + 1) * std::max(Mc, 1) * 4, s));
+    Emit none{nullptr, nullptr, nullptr, rec.width, rec.vwidth};
+    if (Mc > 0)
+        {
+            ProfScope ps__(ctx, s, "enum_roots");
+            roots_kernel<<<grid1(Mc, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, K, mode, (Node *)lv[0].nodes.ptr,
+                                                              (int32_t *)lv[0].counts.ptr, none, nullptr, 0, overflow);
+        }
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    // expand while the tree is narrow
+    int depth = 1;
+    while (depth < kPrefixMax && depth < K - 1 && lv.back().n > 0 && lv.back().n < kPrefixTarget) {
+        Level &cur = lv.back();
+        DevBuf cc;
+        if ((st = dev_alloc(ctx, cc, (size_t)cur.n * 8, s))) return st;
+        int32_t *child_count = (int32_t *)cc.ptr;
+        int32_t *cnts = (int32_t *)cur.counts.ptr;
+        {
+            ProfScope ps__(ctx, s, "enum_expand");
+            expand_kernel<<<grid1(cur.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)cur.nodes.ptr, cur.n, K, mode, 0,
+                                                                  child_count, nullptr, nullptr, cnts, none, nullptr, overflow);
+        }
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+        DevBuf coff;
+        if ((st = dev_alloc(ctx, coff, (size_t)(cur.n + 1) * 8, s))) return st;
+        {
+            ProfScope ps__(ctx, s, "scan");
+            widen_kernel<<<grid1(cur.n, 256, ctx->n_sm), 256, 0, s>>>(child_count, (int64_t *)coff.ptr, cur.n);
+        }
+        int64_t n_child = 0;
+        if ((st = device_exclusive_scan(ctx, (int64_t *)coff.ptr, cur.n, &n_child, s))) return st;
+        Level nxt;
+        nxt.n = n_child;
+        if ((st = dev_alloc(ctx, nxt.nodes, sizeof(Node) * std::max<int64_t>(n_child, 1), s))) return st;
+        if ((st = dev_alloc(ctx, nxt.counts, (size_t)(K + 1) * std::max<int64_t>(n_child, 1) * 4, s))) return st;
+        PNE_CUDA_TRY(ctx, cudaMemsetAsync(nxt.counts.ptr, 0, (size_t)(K + 1) * std::max<int64_t>(n_child, 1) * 4, s));
+        {
+            ProfScope ps__(ctx, s, "enum_expand");
+            expand_kernel<<<grid1(cur.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)cur.nodes.ptr, cur.n, K, mode, 1,
+                                                                  nullptr, (const int64_t *)coff.ptr, (Node *)nxt.nodes.ptr,
+                                                                  nullptr, none, nullptr, overflow);
+        }
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+        dev_free(ctx, cc, s);
+        dev_free(ctx, coff, s);
+        lv.push_back(std::move(nxt));
+        ++depth;
+    }
+    // depth-first counts from the last level
+    Level &last = lv.back();
+    const bool small = (K <= 12 && umax_need <= 64);
+    if (last.n > 0) {
+        if (small)
+            {
+                ProfScope ps__(ctx, s, "enum_dfs");
+                dfs_kernel<12, 64><<<grid1(last.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)last.nodes.ptr, last.n, K, mode, 0,
+                                                                            (int32_t *)last.counts.ptr, none, nullptr, overflow);
+            }
+        else
+            {
+                ProfScope ps__(ctx, s, "enum_dfs");
+                dfs_kernel<32, 128><<<grid1(last.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)last.nodes.ptr, last.n, K, mode, 0,
+                                                                             (int32_t *)last.counts.ptr, none, nullptr, overflow);
+            }
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    // one (size, unit) table over all levels: concatenate per size
+    int64_t n_units = 0;
+    for (auto &L : lv) n_units += L.n;
+    DevBuf all_counts;
+    if ((st = dev_alloc(ctx, all_counts, (size_t)(K + 1) * std::max<int64_t>(n_units, 1) * 4, s))) return st;
+    {
+        int64_t col = 0;
+        for (auto &L : lv) {
+            if (L.n > 0)
+                PNE_CUDA_TRY(ctx, cudaMemcpy2DAsync((int32_t *)all_counts.ptr + col, n_units * 4, L.counts.ptr, L.n * 4,
+                                                     L.n * 4, K + 1, cudaMemcpyDeviceToDevice, s));
+            col += L.n;
+        }
+    }
+    DevBuf base;
+    std::vector<int64_t> per_size;
+    if ((st = scan_counts(ctx, (const int32_t *)all_counts.ptr, K + 1, n_units, base, per_size, s))) return st;
+    int32_t h_over = 0;
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(&h_over, overflow, 4, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (h_over) { set_error(ctx, PNE_EOVERFLOW, "candidate list overflow in the cluster search"); return PNE_EOVERFLOW; }
+    uint64_t n_cl = 0;
+    rec.size_start.assign(K + 2, 0);
+    for (int q = 0; q <= K; ++q) { rec.size_start[q] = (int64_t)n_cl; n_cl += per_size[q]; }
+    rec.size_start[K + 1] = (int64_t)n_cl;
+    rec.n_clusters = n_cl;
+    const size_t nn = std::max<uint64_t>(n_cl, 1);
+    if ((st = dev_alloc(ctx, rec.cl_edges, nn * rec.width * 4, s))) return st;
+    if ((st = dev_alloc(ctx, rec.cl_verts, nn * rec.vwidth * 4, s))) return st;
+    if ((st = dev_alloc(ctx, rec.cl_size, nn * 4, s))) return st;
+    Emit out{(int32_t *)rec.cl_edges.ptr, (int32_t *)rec.cl_verts.ptr, (int32_t *)rec.cl_size.ptr, rec.width, rec.vwidth};
+    // write passes; each level reads its slice of the base table
+    {
+        // base is [K+1][n_units]; the kernels index base[q * n_level + u] of their own
+        // table, so each level gets a compact copy
+        int64_t col = 0;
+        for (size_t li = 0; li < lv.size(); ++li) {
+            Level &L = lv[li];
+            if (L.n == 0) { col += L.n; continue; }
+            if ((st = dev_alloc(ctx, L.base, (size_t)(K + 1) * L.n * 8, s))) return st;
+            PNE_CUDA_TRY(ctx, cudaMemcpy2DAsync(L.base.ptr, L.n * 8, (int64_t *)base.ptr + col, n_units * 8,
+                                                 L.n * 8, K + 1, cudaMemcpyDeviceToDevice, s));
+            const int64_t *lb = (const int64_t *)L.base.ptr;
+            if (li == 0)
+                {
+                    ProfScope ps__(ctx, s, "enum_roots");
+                    roots_kernel<<<grid1(L.n, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, K, mode, nullptr, nullptr, out, lb, 1, overflow);
+                }
+            if (li + 1 < lv.size())
+                {
+                    ProfScope ps__(ctx, s, "enum_expand");
+                    expand_kernel<<<grid1(L.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)L.nodes.ptr, L.n, K, mode, 2,
+                                                                        nullptr, nullptr, nullptr, nullptr, out, lb, overflow);
+                }
+            else if (small)
+                {
+                    ProfScope ps__(ctx, s, "enum_dfs");
+                    dfs_kernel<12, 64><<<grid1(L.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)L.nodes.ptr, L.n, K, mode, 1,
+                                                                              nullptr, out, lb, overflow);
+                }
+            else
+                {
+                    ProfScope ps__(ctx, s, "enum_dfs");
+                    dfs_kernel<32, 128><<<grid1(L.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)L.nodes.ptr, L.n, K, mode, 1,
+                                                                               nullptr, out, lb, overflow);
+                }
+            PNE_CUDA_TRY(ctx, cudaGetLastError());
+            col += L.n;
+        }
+    }
+    for (auto &L : lv) { dev_free(ctx, L.nodes, s); dev_free(ctx, L.counts, s); dev_free(ctx, L.base, s); }
+    dev_free(ctx, all_counts, s);
+    dev_free(ctx, base, s);
+    dev_free(ctx, flag, s);
+    return PNE_OK;
+}
+
+pne_status enumerate_tuples(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s)
+{
+    const int K = rec.K;
+    rec.levels.clear();
+    rec.terms_by_order.assign(K + 1, 0);
+    rec.terms_by_order[0] = 1;
+    for (int q = 1; q <= K; ++q) rec.terms_by_order[q] += rec.size_start[q + 1] - rec.size_start[q];
+    int s_min = 0;
+    for (int q = 1; q <= K; ++q) if (rec.size_start[q + 1] > rec.size_start[q]) { s_min = q; break; }
+    rec.n_terms = 1 + rec.n_clusters;
+    if (s_min == 0 || rec.n_clusters == 0) return PNE_OK;
+    // size_end[q] = first cluster index with size > q
+    std::vector<int64_t> size_end(K + 2, 0);
+    for (int q = 0; q <= K; ++q) size_end[q] = rec.size_start[q + 1];
+    size_end[K + 1] = rec.size_start[K + 1];
+    DevBuf d_size_end;
+    pne_status st = dev_alloc(ctx, d_size_end, (K + 2) * 8, s);
+    if (st) return st;
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(d_size_end.ptr, size_end.data(), (K + 2) * 8, cudaMemcpyHostToDevice, s));
+    // first round: every cluster that can start a pair (size <= K - s_min)
+    int64_t n_in = (K - s_min >= s_min) ? size_end[K - s_min] : 0;
+    DevBuf in_idx, in_ord;
+    bool in_owned = true;
+    int m = 1;
+    if (n_in > 0) {
+        if ((st = dev_alloc(ctx, in_idx, n_in * 4, s))) return st;
+        if ((st = dev_alloc(ctx, in_ord, n_in * 4, s))) return st;
+        {
+            ProfScope ps__(ctx, s, "enum_terms");
+            iota_order_kernel<<<grid1(n_in, 256, ctx->n_sm), 256, 0, s>>>((int32_t *)in_idx.ptr, (int32_t *)in_ord.ptr,
+                                                                       (const int32_t *)rec.cl_size.ptr, n_in);
+        }
+    }
+    while (n_in > 0 && (m + 1) * s_min <= K) {
+        TupleParams p;
+        p.verts = (const int32_t *)rec.cl_verts.ptr; p.size = (const int32_t *)rec.cl_size.ptr;
+        p.vwidth = rec.vwidth; p.K = K; p.m = m;
+        p.in = (const int32_t *)in_idx.ptr; p.in_order = (const int32_t *)in_ord.ptr; p.n_in = n_in;
+        p.size_end = (const int64_t *)d_size_end.ptr;
+        p.counts = nullptr; p.base = nullptr; p.out = nullptr; p.out_order = nullptr;
+        DevBuf uoff;
+        if ((st = dev_alloc(ctx, uoff, (n_in + 1) * 8, s))) return st;
+        {
+            ProfScope ps__(ctx, s, "enum_terms");
+            tuple_chunks_kernel<<<grid1(n_in, 256, ctx->n_sm), 256, 0, s>>>(p, (int64_t *)uoff.ptr);
+        }
+        int64_t n_units = 0;
+        if ((st = device_exclusive_scan(ctx, (int64_t *)uoff.ptr, n_in, &n_units, s))) return st;
+        p.unit_off = (const int64_t *)uoff.ptr; p.n_units = n_units;
+        EnumRecord::Level L;
+        L.m = m + 1;
+        L.order_start.assign(K + 2, 0);
+        DevBuf counts, base, out_ord;
+        std::vector<int64_t> per_order(K + 1, 0);
+        if (n_units > 0) {
+            if ((st = dev_alloc(ctx, counts, (size_t)(K + 1) * n_units * 4, s))) return st;
+            p.counts = (int32_t *)counts.ptr;
+            {
+                ProfScope ps__(ctx, s, "enum_terms");
+                tuple_kernel<<<grid1(n_units, 128, ctx->n_sm), 128, 0, s>>>(p, 0);
+            }
+            PNE_CUDA_TRY(ctx, cudaGetLastError());
+            if ((st = scan_counts(ctx, (const int32_t *)counts.ptr, K + 1, n_units, base, per_order, s))) return st;
+        }
+        int64_t n_out = 0;
+        for (int q = 0; q <= K; ++q) { L.order_start[q] = n_out; n_out += per_order[q]; }
+        L.order_start[K + 1] = n_out;
+        L.n = (uint64_t)n_out;
+        if (n_out > 0) {
+            if ((st = dev_alloc(ctx, L.idx, (size_t)n_out * (m + 1) * 4, s))) return st;
+            if ((st = dev_alloc(ctx, out_ord, (size_t)n_out * 4, s))) return st;
+            p.base = (const int64_t *)base.ptr;
+            p.out = (int32_t *)L.idx.ptr; p.out_order = (int32_t *)out_ord.ptr;
+            {
+                ProfScope ps__(ctx, s, "enum_terms");
+                tuple_kernel<<<grid1(n_units, 128, ctx->n_sm), 128, 0, s>>>(p, 1);
+            }
+            PNE_CUDA_TRY(ctx, cudaGetLastError());
+        }
+        for (int q = 0; q <= K; ++q) rec.terms_by_order[q] += per_order[q];
+        rec.n_terms += (uint64_t)n_out;
+        dev_free(ctx, uoff, s); dev_free(ctx, counts, s); dev_free(ctx, base, s);
+        if (in_owned) dev_free(ctx, in_idx, s);
+        dev_free(ctx, in_ord, s);
+        if (n_out > 0) rec.levels.push_back(L);
+        in_idx = L.idx; in_owned = false;     // the level keeps ownership
+        in_ord = out_ord;
+        n_in = n_out;
+        m += 1;
+    }
+    if (in_owned) dev_free(ctx, in_idx, s);
+    dev_free(ctx, in_ord, s);
+    dev_free(ctx, d_size_end, s);
+    return PNE_OK;
+}
+
+}  // namespace pne

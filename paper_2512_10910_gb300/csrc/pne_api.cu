@@ -1,0 +1,612 @@
+// Host side of libpne: the C ABI of include/pne.h.
+//
+// Validation of the network, geometry tables (leg positions, incoming-message
+// slots, row-major and excitation-blocked offsets), device memory through the
+// context's allocator, the enumeration cache, and the final FP64 assembly of
+// each result (Z_K = Z_ref * sum_k c_k, Sec. II.B truncation of Eq. A4).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "pne_internal.h"
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+namespace pne {
+
+void set_error(pne_ctx *ctx, pne_status st, const std::string &msg)
+{
+    (void)ctx;
+    g_last_error = std::string("pne status ") + std::to_string((int)st) + ": " + msg;
+}
+
+pne_status dev_alloc(pne_ctx *ctx, DevBuf &b, size_t bytes, cudaStream_t s)
+{
+    if (bytes < 16) bytes = 16;
+    b.bytes = bytes;
+    if (ctx->alloc) {
+        b.ptr = ctx->alloc(bytes, (void *)s, ctx->alloc_user);
+        if (!b.ptr) { set_error(ctx, PNE_ENOMEM, "allocator callback returned NULL"); return PNE_ENOMEM; }
+        return PNE_OK;
+    }
+    cudaError_t e = cudaMallocAsync(&b.ptr, bytes, s);
+    if (e != cudaSuccess) {
+        b.ptr = nullptr;
+        set_error(ctx, PNE_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+        return PNE_ENOMEM;
+    }
+    return PNE_OK;
+}
+
+void dev_free(pne_ctx *ctx, DevBuf &b, cudaStream_t s)
+{
+    if (!b.ptr) return;
+    if (ctx->free_fn) ctx->free_fn(b.ptr, b.bytes, (void *)s, ctx->alloc_user);
+    else cudaFreeAsync(b.ptr, s);
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+ProfScope::ProfScope(pne_ctx *c, cudaStream_t st, const char *n) : ctx(c), s(st), name(n)
+{
+    if (!ctx || !ctx->prof.on) return;
+    auto take = [&]() {
+        cudaEvent_t e;
+        if (!ctx->prof.pool.empty()) { e = ctx->prof.pool.back(); ctx->prof.pool.pop_back(); }
+        else cudaEventCreate(&e);
+        return e;
+    };
+    a = take();
+    b = take();
+    cudaEventRecord(a, s);
+}
+
+ProfScope::~ProfScope()
+{
+    if (!a) return;
+    cudaEventRecord(b, s);
+    ctx->prof.pending.push_back({name, a, b});
+}
+
+EnumRecord::~EnumRecord()
+{
+    if (!ctx) return;
+    dev_free(ctx, cl_edges, nullptr);
+    dev_free(ctx, cl_verts, nullptr);
+    dev_free(ctx, cl_size, nullptr);
+    for (auto &L : levels) dev_free(ctx, L.idx, nullptr);
+}
+
+namespace {
+
+uint64_t fnv(uint64_t h, const void *p, size_t n)
+{
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+// Derived tables of a geometry given bond_site, bond_dim, site_ptr, site_bonds.
+pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
+{
+    const int N = g.n_sites, M = g.n_bonds;
+    g.n_legs = g.site_ptr[N];
+    g.bond_leg.assign(2 * M, -1);
+    g.max_deg = 0; g.max_dim = 0;
+    for (int v = 0; v < N; ++v) {
+        const int k = g.site_ptr[v + 1] - g.site_ptr[v];
+        g.max_deg = std::max(g.max_deg, k);
+        for (int i = 0; i < k; ++i) {
+            const int b = g.site_bonds[g.site_ptr[v] + i];
+            const int side = (g.bond_site[2 * b] == v) ? 0 : 1;
+            g.bond_leg[2 * b + side] = i;
+        }
+    }
+    for (int b = 0; b < M; ++b) g.max_dim = std::max(g.max_dim, g.bond_dim[b]);
+    g.inc_slot.assign(g.n_legs, 0);
+    for (int v = 0; v < N; ++v)
+        for (int i = g.site_ptr[v]; i < g.site_ptr[v + 1]; ++i) {
+            const int b = g.site_bonds[i];
+            const int s0 = g.bond_site[2 * b], s1 = g.bond_site[2 * b + 1];
+            if (s1 < 0) { g.inc_slot[i] = i; continue; }         // boundary reflection
+            const int u = (s0 == v) ? s1 : s0, side = (s0 == v) ? 1 : 0;
+            g.inc_slot[i] = g.site_ptr[u] + g.bond_leg[2 * b + side];
+        }
+    g.tens_off.assign(N + 1, 0);
+    g.blk_off.assign((size_t)N * kBlkStride, 0);
+    for (int v = 0; v < N; ++v) {
+        const int k = g.site_ptr[v + 1] - g.site_ptr[v];
+        int64_t n = 1;
+        int q[kMaxDeg];
+        for (int i = 0; i < k; ++i) { const int d = g.bond_dim[g.site_bonds[g.site_ptr[v] + i]]; n *= d; q[i] = d - 1; }
+        g.tens_off[v + 1] = g.tens_off[v] + n;
+        int32_t off = 0;
+        for (int m = 0; m < (1 << k); ++m) {
+            g.blk_off[(size_t)v * kBlkStride + m] = off;
+            int32_t sz = 1;
+            for (int i = 0; i < k; ++i) if (m >> i & 1) sz *= q[i];
+            off += sz;
+        }
+    }
+    uint64_t h = 1469598103934665603ull;
+    h = fnv(h, &N, sizeof N);
+    h = fnv(h, g.bond_site.data(), g.bond_site.size() * 4);
+    h = fnv(h, g.bond_dim.data(), g.bond_dim.size() * 4);
+    g.hash = h;
+    // one device buffer for every table
+    const size_t n_i32 = g.bond_site.size() + g.bond_dim.size() + g.site_ptr.size() + g.site_bonds.size() +
+                         g.bond_leg.size() + g.inc_slot.size() + g.blk_off.size();
+    const size_t bytes = g.tens_off.size() * 8 + n_i32 * 4 + 64;
+    pne_status st = dev_alloc(ctx, g.storage, bytes, s);
+    if (st) return st;
+    std::vector<char> host(bytes, 0);
+    size_t off = 0;
+    auto put = [&](const void *src, size_t nb) { size_t o = off; std::memcpy(host.data() + off, src, nb); off += nb; return o; };
+    const size_t o_tens = put(g.tens_off.data(), g.tens_off.size() * 8);
+    const size_t o_bs = put(g.bond_site.data(), g.bond_site.size() * 4);
+    const size_t o_bd = put(g.bond_dim.data(), g.bond_dim.size() * 4);
+    const size_t o_sp = put(g.site_ptr.data(), g.site_ptr.size() * 4);
+    const size_t o_sb = put(g.site_bonds.data(), g.site_bonds.size() * 4);
+    const size_t o_bl = put(g.bond_leg.data(), g.bond_leg.size() * 4);
+    const size_t o_is = put(g.inc_slot.data(), g.inc_slot.size() * 4);
+    const size_t o_bo = put(g.blk_off.data(), g.blk_off.size() * 4);
+    char *d = (char *)g.storage.ptr;
+    g.d_tens_off = (int64_t *)(d + o_tens);
+    g.d_bond_site = (int32_t *)(d + o_bs);
+    g.d_bond_dim = (int32_t *)(d + o_bd);
+    g.d_site_ptr = (int32_t *)(d + o_sp);
+    g.d_site_bonds = (int32_t *)(d + o_sb);
+    g.d_bond_leg = (int32_t *)(d + o_bl);
+    g.d_inc_slot = (int32_t *)(d + o_is);
+    g.d_blk_off = (int32_t *)(d + o_bo);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(g.storage.ptr, host.data(), bytes, cudaMemcpyHostToDevice, s));
+    // the host copy must stay alive until the copy ran
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return PNE_OK;
+}
+
+pne_status validate(pne_ctx *ctx, const pne_network *n)
+{
+    auto bad = [&](const std::string &m) { set_error(ctx, PNE_EINVAL, m); return PNE_EINVAL; };
+    if (!n || n->n_sites < 1 || n->n_bonds < 0) return bad("empty or malformed network");
+    if (!n->bond_site || !n->bond_dim || !n->site_ptr || !n->site_bonds || !n->data || !n->data_off)
+        return bad("null array in pne_network");
+    if (n->n_batch < 1) return bad("n_batch must be >= 1");
+    const int N = n->n_sites, M = n->n_bonds;
+    std::vector<int> seen(M, 0);
+    for (int b = 0; b < M; ++b) {
+        const int s0 = n->bond_site[2 * b], s1 = n->bond_site[2 * b + 1];
+        if (s0 < 0 || s0 >= N || s1 >= N || s1 < -1 || s0 == s1) return bad("bond " + std::to_string(b) + " has invalid sites");
+        if (n->bond_dim[b] < 2 || n->bond_dim[b] > kMaxDim) return bad("bond dimension must be in 2..8");
+    }
+    if (n->site_ptr[0] != 0) return bad("site_ptr[0] must be 0");
+    for (int v = 0; v < N; ++v) {
+        const int a = n->site_ptr[v], e = n->site_ptr[v + 1];
+        if (e < a || e - a > kMaxDeg) return bad("site degree must be in 0..6");
+        int64_t size = 1;
+        for (int i = a; i < e; ++i) {
+            const int b = n->site_bonds[i];
+            if (b < 0 || b >= M) return bad("site_bonds out of range");
+            if (i > a && n->site_bonds[i - 1] >= b) return bad("legs must be in ascending bond id");
+            if (n->bond_site[2 * b] != v && n->bond_site[2 * b + 1] != v) return bad("leg not incident to its site");
+            seen[b]++;
+            size *= n->bond_dim[b];
+        }
+        if (n->data_off[v + 1] - n->data_off[v] != size) return bad("data_off inconsistent with leg dimensions");
+        if (size > 4096) return bad("site tensor larger than 4096 entries");
+    }
+    if (n->data_off[0] != 0) return bad("data_off[0] must be 0");
+    for (int b = 0; b < M; ++b) {
+        const int want = (n->bond_site[2 * b + 1] < 0) ? 1 : 2;
+        if (seen[b] != want) return bad("bond " + std::to_string(b) + " not listed at both of its sites");
+    }
+    return PNE_OK;
+}
+
+double gamma_n(int n, double u) { return (n * u) / (1.0 - n * u); }
+
+}  // namespace
+}  // namespace pne
+
+using namespace pne;
+
+extern "C" {
+
+pne_status pne_ctx_create(int device, pne_ctx **out)
+{
+    if (!out) return PNE_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || device < 0 || device >= n) {
+        g_last_error = std::string("no CUDA device ") + std::to_string(device) +
+                       (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : std::string());
+        return PNE_ECUDA;
+    }
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) { g_last_error = cudaGetErrorString(e); return PNE_ECUDA; }
+    pne_ctx *c = new pne_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+    // keep stream-ordered allocations pooled inside this process
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = std::numeric_limits<uint64_t>::max();
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = c;
+    return PNE_OK;
+}
+
+void pne_ctx_destroy(pne_ctx *ctx)
+{
+    if (!ctx) return;
+    ctx->enum_cache.clear();
+    cudaDeviceSynchronize();
+    delete ctx;
+}
+
+const char *pne_last_error(pne_ctx *ctx)
+{
+    (void)ctx;
+    return g_last_error.c_str();
+}
+
+pne_status pne_ctx_set_allocator(pne_ctx *ctx, pne_alloc_fn alloc, pne_free_fn free_fn, void *user)
+{
+    if (!ctx || (!alloc) != (!free_fn)) return PNE_EINVAL;
+    ctx->alloc = alloc; ctx->free_fn = free_fn; ctx->alloc_user = user;
+    return PNE_OK;
+}
+
+pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_partition_opts *opts,
+                               void *stream, pne_partition **out)
+{
+    if (!ctx || !out) return PNE_EINVAL;
+    *out = nullptr;
+    pne_status st = validate(ctx, net);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double tol = (opts && opts->tol > 0) ? opts->tol : 1e-13;
+    int max_iter = (opts && opts->max_iter > 0) ? opts->max_iter : 10000;
+    double damping = opts ? opts->damping : 0.0;
+    if (!(damping >= 0.0 && damping < 1.0)) { set_error(ctx, PNE_EINVAL, "damping must be in [0,1)"); return PNE_EINVAL; }
+
+    pne_partition *p = new pne_partition();
+    p->ctx = ctx;
+    p->last_stream = s;
+    const int N = net->n_sites, M = net->n_bonds;
+    Geometry &f = p->full;
+    f.n_sites = N; f.n_bonds = M;
+    f.bond_site.assign(net->bond_site, net->bond_site + 2 * M);
+    f.bond_dim.assign(net->bond_dim, net->bond_dim + M);
+    f.site_ptr.assign(net->site_ptr, net->site_ptr + N + 1);
+    f.site_bonds.assign(net->site_bonds, net->site_bonds + net->site_ptr[N]);
+    // closed geometry: open bonds removed, remaining bonds renumbered in order
+    p->closed_of_full.assign(M, -1);
+    Geometry &c = p->closed;
+    c.n_sites = N;
+    int mc = 0;
+    for (int b = 0; b < M; ++b) {
+        if (f.bond_site[2 * b + 1] < 0) { p->open_bonds.push_back(b); p->open_dims.push_back(f.bond_dim[b]); continue; }
+        p->closed_of_full[b] = mc++;
+        c.bond_site.push_back(f.bond_site[2 * b]); c.bond_site.push_back(f.bond_site[2 * b + 1]);
+        c.bond_dim.push_back(f.bond_dim[b]);
+    }
+    c.n_bonds = mc;
+    c.site_ptr.assign(N + 1, 0);
+    for (int v = 0; v < N; ++v) {
+        for (int i = f.site_ptr[v]; i < f.site_ptr[v + 1]; ++i) {
+            const int cb = p->closed_of_full[f.site_bonds[i]];
+            if (cb >= 0) c.site_bonds.push_back(cb);
+        }
+        c.site_ptr[v + 1] = (int32_t)c.site_bonds.size();
+    }
+    int64_t slices = 1;
+    for (int d : p->open_dims) slices *= d;
+    if (slices > 4096) { delete p; set_error(ctx, PNE_EINVAL, "more than 4096 open-index assignments"); return PNE_EINVAL; }
+    p->n_sets = net->n_batch;
+    p->n_slices = (int)slices;
+    p->n_members = p->n_sets * p->n_slices;
+    if ((st = finish_geometry(ctx, f, s)) || (st = finish_geometry(ctx, c, s))) { pne_partition_destroy(p); return st; }
+    const int64_t fstride = f.tens_off[N], cstride = c.tens_off[N];
+    const size_t B = p->n_sets, Bm = p->n_members;
+    if ((st = dev_alloc(ctx, p->T, B * fstride * 8, s)) ||
+        (st = dev_alloc(ctx, p->msg, 2 * B * f.n_legs * kMsgStride * 8, s)) ||
+        (st = dev_alloc(ctx, p->gauge, B * std::max(M, 1) * 2 * 64 * 8, s)) ||
+        (st = dev_alloc(ctx, p->Mb, Bm * cstride * 8, s)) ||
+        (st = dev_alloc(ctx, p->site_info, Bm * N * 8, s)) ||
+        (st = dev_alloc(ctx, p->site_scale, Bm * N * 8, s)) ||
+        (st = dev_alloc(ctx, p->site_zero, Bm * N, s)) ||
+        (st = dev_alloc(ctx, p->vac, Bm * 3 * 8, s))) {
+        pne_partition_destroy(p);
+        return st;
+    }
+    // input tensors: a host or device source, in one copy
+    {
+        const size_t bytes = B * fstride * 8;
+        cudaError_t e = cudaMemcpyAsync(p->T.ptr, net->data, bytes,
+                                        net->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { pne_partition_destroy(p); set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return PNE_ECUDA; }
+    }
+    p->bp_iters.assign(B, 0);
+    p->bp_residual.assign(B, 0.0);
+    int32_t flags[4] = {0, 0, 0, 0};
+    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, p->bp_iters.data(), p->bp_residual.data(), flags)) ||
+        (st = launch_gauge(ctx, p, s, nullptr))) {
+        pne_partition_destroy(p);
+        return st;
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { pne_partition_destroy(p); set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return PNE_ECUDA; }
+    if (flags[0] || flags[2]) { pne_partition_destroy(p); set_error(ctx, PNE_ETIMEOUT, "grid barrier timed out in BP"); return PNE_ETIMEOUT; }
+    if (flags[1] || flags[3]) { pne_partition_destroy(p); set_error(ctx, PNE_EDEGENERATE, "zero message or zero message overlap"); return PNE_EDEGENERATE; }
+    *out = p;
+    for (size_t b = 0; b < B; ++b)
+        if (p->bp_iters[b] == 0) {
+            set_error(ctx, PNE_ENOCONV, "BP did not converge for tensor set " + std::to_string(b));
+            return PNE_ENOCONV;
+        }
+    return PNE_OK;
+}
+
+void pne_partition_destroy(pne_partition *p)
+{
+    if (!p) return;
+    pne_ctx *ctx = p->ctx;
+    cudaStream_t s = p->last_stream;
+    DevBuf *bufs[] = {&p->T, &p->msg, &p->gauge, &p->Mb, &p->site_info, &p->site_scale, &p->site_zero,
+                      &p->vac, &p->Mb32, &p->Mb16, &p->full.storage, &p->closed.storage};
+    for (DevBuf *b : bufs) dev_free(ctx, *b, s);
+    delete p;
+}
+
+pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pne_enum_opts *opts,
+                               void *stream, pne_terms **out, uint64_t *n_clusters, uint64_t *n_terms)
+{
+    if (!ctx || !part || !opts || !out) return PNE_EINVAL;
+    *out = nullptr;
+    const int K = opts->max_order, mode = opts->mode;
+    if (K < 0 || K > kMaxOrder) { set_error(ctx, PNE_EINVAL, "max_order must be in 0..32"); return PNE_EINVAL; }
+    if (mode != PNE_MODE_LOOP && mode != PNE_MODE_ALL) { set_error(ctx, PNE_EINVAL, "unknown mode"); return PNE_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Geometry &g = part->closed;
+    std::string key = std::to_string(g.hash) + ":" + std::to_string(g.n_sites) + ":" + std::to_string(g.n_bonds) +
+                      ":" + std::to_string(K) + ":" + std::to_string(mode);
+    std::shared_ptr<EnumRecord> rec;
+    if (opts->use_cache) {
+        auto it = ctx->enum_cache.find(key);
+        if (it != ctx->enum_cache.end()) rec = it->second;
+    }
+    pne_status st;
+    if (!rec) {
+        rec = std::make_shared<EnumRecord>();
+        rec->ctx = ctx;
+        if (mode == PNE_MODE_ALL) {
+            if (g.n_bonds > kMaxAllBonds || g.n_sites > 64) {
+                set_error(ctx, PNE_EINVAL, "ALL mode needs <= 30 closed bonds and <= 64 sites"); return PNE_EINVAL;
+            }
+            rec->K = K; rec->mode = mode; rec->n_closed = g.n_bonds;
+            rec->size_start.assign(K + 2, 0);
+            rec->terms_by_order.assign(K + 1, 0);
+            uint64_t tot = 0;
+            for (int k = 0; k <= K && k <= g.n_bonds; ++k) {
+                double bn = 1.0;
+                for (int i = 1; i <= k; ++i) bn = bn * (g.n_bonds - k + i) / i;
+                rec->terms_by_order[k] = (uint64_t)llround(bn);
+                tot += rec->terms_by_order[k];
+            }
+            rec->n_terms = tot;
+        } else {
+            if (K == 0) {
+                rec->K = 0; rec->mode = mode; rec->size_start.assign(2, 0);
+                rec->terms_by_order.assign(1, 1); rec->n_terms = 1;
+                rec->width = 1; rec->vwidth = 1;
+            } else {
+                if ((st = enumerate_clusters(ctx, g, K, mode, *rec, s))) return st;
+                if ((st = enumerate_tuples(ctx, *rec, s))) return st;
+            }
+        }
+        if (opts->use_cache) ctx->enum_cache[key] = rec;
+    }
+    pne_terms *t = new pne_terms();
+    t->ctx = ctx; t->part = part; t->rec = rec; t->K = K; t->mode = mode;
+    const size_t Bm = part->n_members;
+    const size_t ncl = std::max<uint64_t>(rec->n_clusters, 1);
+    if ((st = dev_alloc(ctx, t->status, 16, s))) { delete t; return st; }
+    cudaMemsetAsync(t->status.ptr, 0, 16, s);
+    if (mode == PNE_MODE_LOOP) {
+        if ((st = dev_alloc(ctx, t->w, Bm * ncl * 8, s)) || (st = dev_alloc(ctx, t->nzc, Bm * ncl * 4, s))) {
+            pne_terms_destroy(t); return st;
+        }
+    }
+    *out = t;
+    if (n_clusters) *n_clusters = rec->n_clusters;
+    if (n_terms) *n_terms = rec->n_terms;
+    return PNE_OK;
+}
+
+void pne_terms_destroy(pne_terms *t)
+{
+    if (!t) return;
+    cudaStream_t s = t->part ? t->part->last_stream : nullptr;
+    dev_free(t->ctx, t->w, s);
+    dev_free(t->ctx, t->nzc, s);
+    dev_free(t->ctx, t->sums, s);
+    dev_free(t->ctx, t->status, s);
+    delete t;
+}
+
+pne_status pne_contract_terms(pne_ctx *ctx, pne_terms *t, pne_dtype dtype, void *stream)
+{
+    if (!ctx || !t) return PNE_EINVAL;
+    if (dtype < PNE_F64 || dtype > PNE_BF16) { set_error(ctx, PNE_EINVAL, "unknown dtype"); return PNE_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    pne_status st = (t->mode == PNE_MODE_ALL) ? launch_all_mode(ctx, t, dtype, s) : launch_contract(ctx, t, dtype, s);
+    if (st) return st;
+    t->dtype = dtype;
+    t->contracted = true;
+    return PNE_OK;
+}
+
+int64_t pne_terms_n_results(const pne_terms *t)
+{
+    return t && t->part ? (int64_t)t->part->n_members : 0;
+}
+
+pne_status pne_terms_export(pne_ctx *ctx, const pne_terms *t, void *stream, int32_t *edges, double *w)
+{
+    if (!ctx || !t) return PNE_EINVAL;
+    if (t->mode != PNE_MODE_LOOP) { set_error(ctx, PNE_EINVAL, "export needs LOOP mode"); return PNE_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const EnumRecord &rec = *t->rec;
+    const size_t n = rec.n_clusters;
+    if (n == 0) return PNE_OK;
+    if (edges) {
+        std::vector<int32_t> buf(n * rec.width);
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(buf.data(), rec.cl_edges.ptr, buf.size() * 4, cudaMemcpyDeviceToHost, s));
+        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        std::vector<int32_t> full_of_closed;
+        for (size_t b = 0; b < t->part->closed_of_full.size(); ++b)
+            if (t->part->closed_of_full[b] >= 0) full_of_closed.push_back((int32_t)b);
+        for (size_t i = 0; i < n; ++i)
+            for (int j = 0; j < t->K; ++j) {
+                const int32_t e = (j < rec.width) ? buf[i * rec.width + j] : -1;
+                edges[i * t->K + j] = (e >= 0) ? full_of_closed[e] : -1;
+            }
+    }
+    if (w) {
+        if (!t->contracted) { set_error(ctx, PNE_EINVAL, "contract before exporting values"); return PNE_EINVAL; }
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(w, t->w.ptr, n * t->part->n_members * 8, cudaMemcpyDeviceToHost, s));
+        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    }
+    return PNE_OK;
+}
+
+pne_status pne_sum(pne_ctx *ctx, const pne_terms *t, void *stream, pne_result *out)
+{
+    if (!ctx || !t || !out) return PNE_EINVAL;
+    if (!t->contracted) { set_error(ctx, PNE_EINVAL, "pne_contract_terms must run before pne_sum"); return PNE_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const pne_partition *p = t->part;
+    const int K = t->K, B = p->n_members;
+    std::vector<double> c, a;
+    int32_t status = 0;
+    pne_status st = launch_sums(ctx, t, s, c, a, &status);
+    if (st) return st;
+    if (status) { set_error(ctx, PNE_EOVERFLOW, "a cluster exceeded the contraction buffer"); return PNE_EOVERFLOW; }
+    std::vector<double> vac((size_t)B * 3);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(vac.data(), p->vac.ptr, vac.size() * 8, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    static const double unit[4] = {0x1p-53, 0x1p-24, 0x1p-11, 0x1p-8};
+    const double u = unit[t->dtype < 0 ? 0 : t->dtype];
+    // first-order rounding count per term: every site factor and every
+    // intermediate of a cluster contraction is rounded once in the working
+    // dtype (at most 2 (K + 1) roundings along a term's product)
+    const int nops = 2 * (K + 1);
+    for (int b = 0; b < B; ++b) {
+        pne_result &r = out[b];
+        std::memset(&r, 0, sizeof r);
+        const double lz = vac[3 * b], sz = vac[3 * b + 1];
+        const int nzero = (int)vac[3 * b + 2];
+        r.n_orders = K + 1;
+        for (int k = 0; k <= K; ++k) { r.c[k] = c[(size_t)b * (K + 1) + k]; r.abs_c[k] = a[(size_t)b * (K + 1) + k]; }
+        if (t->mode == PNE_MODE_LOOP && nzero == 0) { r.c[0] += 1.0; r.abs_c[0] += 1.0; }
+        // Neumaier sum over orders
+        double sum = 0.0, comp = 0.0, asum = 0.0;
+        for (int k = 0; k <= K; ++k) {
+            const double x = r.c[k], tt = sum + x;
+            comp += (std::fabs(sum) >= std::fabs(x)) ? (sum - tt) + x : (x - tt) + sum;
+            sum = tt;
+            asum += r.abs_c[k];
+        }
+        sum += comp;
+        r.log_abs_zref = lz;
+        r.sign_zref = sz < 0 ? -1 : 1;
+        r.n_zero_sites = nzero;
+        r.sign = (sum < 0 ? -1 : 1) * r.sign_zref;
+        r.log_abs = (sum != 0.0) ? lz + std::log(std::fabs(sum)) : -std::numeric_limits<double>::infinity();
+        r.value = (sum == 0.0) ? 0.0 : (r.log_abs > 709.7 ? r.sign * std::numeric_limits<double>::infinity()
+                                                           : r.sign * std::exp(r.log_abs));
+        // truncated power-series logarithm of sum_k c_k x^k (x -> 1)
+        if (nzero == 0 && r.c[0] != 0.0) {
+            std::vector<double> cc(K + 1), l(K + 1, 0.0);
+            for (int k = 0; k <= K; ++k) cc[k] = r.c[k] / r.c[0];
+            double ls = 0.0;
+            for (int k = 1; k <= K; ++k) {
+                double acc = k * cc[k];
+                for (int j = 1; j < k; ++j) acc -= j * l[j] * cc[k - j];
+                l[k] = acc / k;
+                ls += l[k];
+            }
+            r.log_series = lz + std::log(std::fabs(r.c[0])) + ls;
+        } else {
+            r.log_series = std::numeric_limits<double>::quiet_NaN();
+        }
+        r.err_bound = (sum != 0.0) ? gamma_n(nops, u) * asum / std::fabs(sum) : std::numeric_limits<double>::infinity();
+        r.n_terms = t->rec->n_terms;
+        r.n_clusters = t->rec->n_clusters;
+        const int set = b / p->n_slices;
+        r.bp_iters = p->bp_iters[set];
+        r.bp_residual = p->bp_residual[set];
+    }
+    return PNE_OK;
+}
+
+pne_status pne_ctx_profile(pne_ctx *ctx, int enable)
+{
+    if (!ctx) return PNE_EINVAL;
+    for (auto &r : ctx->prof.pending) { cudaEventSynchronize(r.b); ctx->prof.pool.push_back(r.a); ctx->prof.pool.push_back(r.b); }
+    ctx->prof.pending.clear();
+    ctx->prof.acc.clear();
+    ctx->prof.on = enable != 0;
+    return PNE_OK;
+}
+
+int pne_ctx_profile_read(pne_ctx *ctx, pne_profile_entry *out, int max)
+{
+    if (!ctx) return 0;
+    for (auto &r : ctx->prof.pending) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto &e = ctx->prof.acc[r.name];
+        e.first += 1;
+        e.second += ms;
+        ctx->prof.pool.push_back(r.a);
+        ctx->prof.pool.push_back(r.b);
+    }
+    ctx->prof.pending.clear();
+    std::vector<std::pair<std::string, std::pair<int64_t, double>>> v(ctx->prof.acc.begin(), ctx->prof.acc.end());
+    std::sort(v.begin(), v.end(), [](const auto &x, const auto &y) { return x.second.second > y.second.second; });
+    const int n = (int)v.size();
+    for (int i = 0; i < n && i < max && out; ++i) {
+        std::memset(out[i].name, 0, sizeof out[i].name);
+        std::strncpy(out[i].name, v[i].first.c_str(), sizeof out[i].name - 1);
+        out[i].launches = v[i].second.first;
+        out[i].total_ms = v[i].second.second;
+    }
+    return n;
+}
+
+pne_status pne_terms_work(pne_ctx *ctx, const pne_terms *t, void *stream, uint64_t *fma_per_set)
+{
+    if (!ctx || !t || !fma_per_set) return PNE_EINVAL;
+    if (t->mode != PNE_MODE_LOOP) { set_error(ctx, PNE_EINVAL, "work count needs LOOP mode"); return PNE_EINVAL; }
+    return launch_plan_work(ctx, t, (cudaStream_t)stream, fma_per_set);
+}
+
+pne_status pne_measure_fma_peak(pne_ctx *ctx, pne_dtype dtype, void *stream, double *flops_per_s)
+{
+    if (!ctx || !flops_per_s || (dtype != PNE_F64 && dtype != PNE_F32)) return PNE_EINVAL;
+    return launch_fma_peak(ctx, dtype, (cudaStream_t)stream, flops_per_s);
+}
+
+}  // extern "C"

@@ -1,0 +1,205 @@
+// Internal declarations shared by the translation units of libpne.
+// Not part of the public ABI (include/pne.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+#include <memory>
+#include <map>
+
+#include "pne.h"
+
+namespace pne {
+
+constexpr int kMaxDeg = PNE_MAX_DEG;
+constexpr int kMaxDim = PNE_MAX_DIM;
+constexpr int kMaxOrder = PNE_MAX_ORDER;
+constexpr int kMsgStride = 8;            // doubles per stored message (>= kMaxDim)
+constexpr int kBlkStride = 64;           // 2^kMaxDeg excitation masks per site
+constexpr int kMaxAllBonds = 30;         // ALL mode: bitmask terms
+constexpr int kWarpTensorMax = 1024;     // entries of one intermediate tensor per warp
+
+// ------------------------------------------------------------------ errors
+struct Error {
+    pne_status st;
+    std::string msg;
+};
+
+void set_error(pne_ctx *ctx, pne_status st, const std::string &msg);
+
+#define PNE_CUDA_TRY(ctx, expr)                                                   \
+    do {                                                                          \
+        cudaError_t e__ = (expr);                                                 \
+        if (e__ != cudaSuccess) {                                                 \
+            ::pne::set_error((ctx), PNE_ECUDA,                                    \
+                             std::string(#expr) + ": " + cudaGetErrorString(e__)); \
+            return PNE_ECUDA;                                                     \
+        }                                                                         \
+    } while (0)
+
+// ------------------------------------------------------------------ memory
+// Device buffer owned through the context's allocator.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+pne_status dev_alloc(pne_ctx *ctx, DevBuf &b, size_t bytes, cudaStream_t s);
+void dev_free(pne_ctx *ctx, DevBuf &b, cudaStream_t s);
+
+// ------------------------------------------------------------------ geometry
+// Host + device copy of one network geometry (closed or with open bonds).
+struct Geometry {
+    int n_sites = 0, n_bonds = 0, n_legs = 0;
+    std::vector<int32_t> bond_site, bond_dim, site_ptr, site_bonds;
+    std::vector<int32_t> bond_leg;      // [n_bonds][2] leg index at each end (-1 open)
+    std::vector<int32_t> inc_slot;      // [n_legs] slot whose message arrives here
+    std::vector<int64_t> tens_off;      // [n_sites+1] row-major tensor offsets
+    std::vector<int32_t> blk_off;       // [n_sites][64] excitation-block offsets
+    int max_deg = 0, max_dim = 0;
+    uint64_t hash = 0;
+    // device mirrors
+    int32_t *d_bond_site = nullptr, *d_bond_dim = nullptr, *d_site_ptr = nullptr,
+            *d_site_bonds = nullptr, *d_bond_leg = nullptr, *d_inc_slot = nullptr,
+            *d_blk_off = nullptr;
+    int64_t *d_tens_off = nullptr;
+    DevBuf storage;
+};
+
+// ------------------------------------------------------------------ handles
+struct EnumRecord;  // cluster and term lists of one closed geometry
+
+}  // namespace pne
+
+namespace pne {
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+struct Profiler {
+    bool on = false;
+    std::vector<ProfRec> pending;
+    std::vector<cudaEvent_t> pool;
+    std::map<std::string, std::pair<int64_t, double>> acc;
+};
+}  // namespace pne
+
+struct pne_ctx {
+    pne::Profiler prof;
+    int device = 0;
+    int n_sm = 0;
+    pne_alloc_fn alloc = nullptr;
+    pne_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
+    std::map<std::string, std::shared_ptr<pne::EnumRecord>> enum_cache;
+    // scratch for small device-side status words
+    int32_t *d_status = nullptr;
+};
+
+struct pne_partition {
+    pne_ctx *ctx = nullptr;
+    pne::Geometry full;              // as given (may have open bonds)
+    pne::Geometry closed;            // open bonds removed, bonds renumbered
+    std::vector<int32_t> closed_of_full;  // full bond id -> closed id (-1 open)
+    std::vector<int32_t> open_bonds;      // full ids of open bonds, ascending
+    std::vector<int32_t> open_dims;
+    int n_sets = 1;                  // tensor sets (n_batch)
+    int n_slices = 1;                // prod of open dims
+    int n_members = 1;               // n_sets * n_slices
+    pne::DevBuf T;                   // [n_sets][full.tens_off[N]] raw FP64
+    pne::DevBuf msg;                 // [2][n_sets][full.n_legs][8]
+    pne::DevBuf gauge;               // [n_sets][full.n_bonds][2][64] leg matrices
+    pne::DevBuf Mb;                  // [n_members][closed.tens_off[N]] blocked, FP64
+    pne::DevBuf site_info;           // [n_members][N] double: z_v (raw)
+    pne::DevBuf site_scale;          // [n_members][N] double: 1 or 2^e for zero sites
+    pne::DevBuf site_zero;           // [n_members][N] int8
+    pne::DevBuf vac;                 // [n_members] {log|Zref|, sign, n_zero} as 3 doubles
+    pne::DevBuf Mb32;                // FP32/TF32 copy (lazy)
+    pne::DevBuf Mb16;                // BF16 copy (lazy)
+    int mb32_dtype = -1;
+    std::vector<int32_t> bp_iters;   // per set
+    std::vector<double> bp_residual; // per set
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace pne {
+
+// Cluster/term lists of one closed geometry at one (K, mode).
+struct EnumRecord {
+    pne_ctx *ctx = nullptr;
+    int K = 0, mode = 0, width = 0, vwidth = 0;
+    int n_closed = 0;
+    uint64_t n_clusters = 0;
+    std::vector<int64_t> size_start;            // [K+2] clusters sorted by size
+    DevBuf cl_edges;                            // [n][width] int32 (closed ids)
+    DevBuf cl_verts;                            // [n][vwidth] int32 sorted, -1 pad
+    DevBuf cl_size;                             // [n] int32
+    // tuples of >= 2 clusters, one list per tuple length, sorted by order
+    struct Level {
+        int m = 0;
+        uint64_t n = 0;
+        DevBuf idx;                             // [n][m] int32
+        std::vector<int64_t> order_start;       // [K+2]
+    };
+    std::vector<Level> levels;
+    uint64_t n_terms = 0;                       // including the empty term
+    std::vector<uint64_t> terms_by_order;       // [K+1]
+    ~EnumRecord();
+};
+
+}  // namespace pne
+
+struct pne_terms {
+    pne_ctx *ctx = nullptr;
+    const pne_partition *part = nullptr;
+    std::shared_ptr<pne::EnumRecord> rec;
+    int K = 0, mode = 0;
+    int dtype = -1;                      // dtype of the last contraction
+    pne::DevBuf w;                       // [n_members][n_clusters] double
+    pne::DevBuf nzc;                     // [n_members][n_clusters] int32
+    pne::DevBuf sums;                    // ALL mode / reduction partials
+    pne::DevBuf status;                  // int32 error flags
+    bool contracted = false;
+};
+
+namespace pne {
+
+// ------------------------------------------------------------------ profiling
+// Records CUDA events around one launch when the context's profiler is on.
+struct ProfScope {
+    pne_ctx *ctx;
+    cudaStream_t s;
+    const char *name;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(pne_ctx *c, cudaStream_t st, const char *n);
+    ~ProfScope();
+};
+
+// ------------------------------------------------------------------ kernels
+// BP, gauge, blocked layout (bp.cu)
+pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, double damping,
+                     cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags);
+pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t *h_flag);
+pne_status launch_convert(pne_ctx *ctx, pne_partition *p, int dtype, cudaStream_t s);
+
+// enumeration (enumerate.cu)
+pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode,
+                              EnumRecord &rec, cudaStream_t s);
+pne_status enumerate_tuples(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s);
+
+// contraction and sums (contract.cu)
+pne_status launch_contract(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s);
+pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s,
+                       std::vector<double> &c, std::vector<double> &abs_c, int32_t *h_status);
+pne_status launch_all_mode(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s);
+pne_status launch_plan_work(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, uint64_t *fma);
+pne_status launch_fma_peak(pne_ctx *ctx, int dtype, cudaStream_t s, double *flops);
+
+// exclusive scan of int64 counts on the device; total returned on the host
+pne_status device_exclusive_scan(pne_ctx *ctx, int64_t *d_counts, int64_t n, int64_t *h_total,
+                                 cudaStream_t s);
+
+}  // namespace pne

@@ -1,0 +1,361 @@
+"""ctypes binding of libpne (include/pne.h): the same calls, argument marshalling only.
+
+Every step of the expansion runs inside the CUDA library; this module only
+packs arrays, pointers and streams.  It raises if the compiled library is
+missing -- there is no fallback path.
+
+Low-level names mirror the C ABI (``pne_ctx_create``, ``pne_build_partition``,
+``pne_enumerate_terms``, ``pne_contract_terms``, ``pne_sum`` ...).  ``Context``
+and ``run`` wrap one full pass for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+__all__ = [
+    "PNE_OK", "PNE_F64", "PNE_F32", "PNE_TF32", "PNE_BF16", "PNE_MODE_LOOP", "PNE_MODE_ALL",
+    "PneError", "load_library", "lib_path", "exported_symbols",
+    "pne_ctx_create", "pne_ctx_destroy", "pne_last_error", "pne_ctx_set_allocator",
+    "pne_build_partition", "pne_partition_destroy", "pne_enumerate_terms", "pne_terms_destroy",
+    "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_terms_export",
+    "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak",
+    "Network", "PartitionOpts", "EnumOpts", "Result", "Context", "run", "network_struct",
+]
+
+PNE_OK, PNE_EINVAL, PNE_ENOMEM, PNE_ECUDA, PNE_ENOCONV, PNE_EDEGENERATE, PNE_ETIMEOUT, PNE_EOVERFLOW, PNE_EBUSY = range(9)
+PNE_F64, PNE_F32, PNE_TF32, PNE_BF16 = range(4)
+PNE_MODE_LOOP, PNE_MODE_ALL = 0, 1
+MAX_ORDER = 32
+DTYPES = {"f64": PNE_F64, "f32": PNE_F32, "tf32": PNE_TF32, "bf16": PNE_BF16}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libpne.so")
+_lib = None
+
+
+class PneError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class Network(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int32), ("n_bonds", ctypes.c_int32),
+                ("bond_site", ctypes.POINTER(ctypes.c_int32)),
+                ("bond_dim", ctypes.POINTER(ctypes.c_int32)),
+                ("site_ptr", ctypes.POINTER(ctypes.c_int32)),
+                ("site_bonds", ctypes.POINTER(ctypes.c_int32)),
+                ("data", ctypes.c_void_p),
+                ("data_off", ctypes.POINTER(ctypes.c_int64)),
+                ("data_on_device", ctypes.c_int32),
+                ("n_batch", ctypes.c_int32)]
+
+
+class PartitionOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("damping", ctypes.c_double)]
+
+
+class EnumOpts(ctypes.Structure):
+    _fields_ = [("max_order", ctypes.c_int32), ("mode", ctypes.c_int32), ("use_cache", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("sign", ctypes.c_int32), ("log_abs", ctypes.c_double), ("value", ctypes.c_double),
+                ("c", ctypes.c_double * (MAX_ORDER + 1)), ("abs_c", ctypes.c_double * (MAX_ORDER + 1)),
+                ("n_orders", ctypes.c_int32), ("log_abs_zref", ctypes.c_double), ("sign_zref", ctypes.c_int32),
+                ("n_zero_sites", ctypes.c_int32), ("log_series", ctypes.c_double),
+                ("err_bound", ctypes.c_double), ("n_terms", ctypes.c_uint64), ("n_clusters", ctypes.c_uint64),
+                ("bp_iters", ctypes.c_int32), ("bp_residual", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        n = self.n_orders
+        return dict(sign=self.sign, log_abs=self.log_abs, value=self.value,
+                    c=np.array(self.c[:n]), abs_c=np.array(self.abs_c[:n]),
+                    log_abs_zref=self.log_abs_zref, sign_zref=self.sign_zref,
+                    n_zero_sites=self.n_zero_sites, log_series=self.log_series,
+                    err_bound=self.err_bound, n_terms=int(self.n_terms), n_clusters=int(self.n_clusters),
+                    bp_iters=self.bp_iters, bp_residual=self.bp_residual)
+
+
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libpne.so; raise if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libpne.so not built at {_LIB_PATH}; run paper_2512_10910_gb300.build.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp = ctypes.c_void_p
+    lib.pne_ctx_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp)]
+    lib.pne_ctx_create.restype = ctypes.c_int
+    lib.pne_ctx_destroy.argtypes = [vp]
+    lib.pne_ctx_destroy.restype = None
+    lib.pne_last_error.argtypes = [vp]
+    lib.pne_last_error.restype = ctypes.c_char_p
+    lib.pne_ctx_set_allocator.argtypes = [vp, ALLOC_FN, FREE_FN, vp]
+    lib.pne_ctx_set_allocator.restype = ctypes.c_int
+    lib.pne_build_partition.argtypes = [vp, ctypes.POINTER(Network), ctypes.POINTER(PartitionOpts), vp, ctypes.POINTER(vp)]
+    lib.pne_build_partition.restype = ctypes.c_int
+    lib.pne_partition_destroy.argtypes = [vp]
+    lib.pne_partition_destroy.restype = None
+    lib.pne_enumerate_terms.argtypes = [vp, vp, ctypes.POINTER(EnumOpts), vp, ctypes.POINTER(vp),
+                                        ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+    lib.pne_enumerate_terms.restype = ctypes.c_int
+    lib.pne_terms_destroy.argtypes = [vp]
+    lib.pne_terms_destroy.restype = None
+    lib.pne_contract_terms.argtypes = [vp, vp, ctypes.c_int, vp]
+    lib.pne_contract_terms.restype = ctypes.c_int
+    lib.pne_sum.argtypes = [vp, vp, vp, ctypes.POINTER(Result)]
+    lib.pne_sum.restype = ctypes.c_int
+    lib.pne_terms_n_results.argtypes = [vp]
+    lib.pne_terms_n_results.restype = ctypes.c_int64
+    lib.pne_terms_export.argtypes = [vp, vp, vp, ctypes.c_void_p, ctypes.c_void_p]
+    lib.pne_terms_export.restype = ctypes.c_int
+    lib.pne_ctx_profile.argtypes = [vp, ctypes.c_int]
+    lib.pne_ctx_profile.restype = ctypes.c_int
+    lib.pne_ctx_profile_read.argtypes = [vp, ctypes.POINTER(ProfileEntry), ctypes.c_int]
+    lib.pne_ctx_profile_read.restype = ctypes.c_int
+    lib.pne_terms_work.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.pne_terms_work.restype = ctypes.c_int
+    lib.pne_measure_fma_peak.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.pne_measure_fma_peak.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list:
+    """Names of the ``pne_*`` functions ``include/pne.h`` declares, found in the library."""
+    lib = load_library()
+    names = ["pne_ctx_create", "pne_ctx_destroy", "pne_last_error", "pne_ctx_set_allocator",
+             "pne_build_partition", "pne_partition_destroy", "pne_enumerate_terms", "pne_terms_destroy",
+             "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_terms_export",
+    "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak",
+             "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak"]
+    return [n for n in names if hasattr(lib, n)]
+
+
+def _check(st, ctx=None):
+    if st != PNE_OK:
+        msg = load_library().pne_last_error(ctx).decode() if ctx is not None else "pne call failed"
+        raise PneError(st, msg)
+
+
+# ------------------------------------------------------------------ the C calls
+def pne_ctx_create(device=0):
+    h = ctypes.c_void_p()
+    _check(load_library().pne_ctx_create(int(device), ctypes.byref(h)))
+    return h
+
+
+def pne_ctx_destroy(ctx):
+    load_library().pne_ctx_destroy(ctx)
+
+
+def pne_last_error(ctx=None) -> str:
+    return load_library().pne_last_error(ctx).decode()
+
+
+def pne_ctx_set_allocator(ctx, alloc_fn, free_fn, user=None):
+    _check(load_library().pne_ctx_set_allocator(ctx, alloc_fn, free_fn, user), ctx)
+
+
+def pne_build_partition(ctx, net: Network, opts: PartitionOpts, stream=None, allow_noconv=False):
+    h = ctypes.c_void_p()
+    st = load_library().pne_build_partition(ctx, ctypes.byref(net), ctypes.byref(opts), stream, ctypes.byref(h))
+    if st == PNE_ENOCONV and allow_noconv:
+        return h, st
+    _check(st, ctx)
+    return h, st
+
+
+def pne_partition_destroy(p):
+    load_library().pne_partition_destroy(p)
+
+
+def pne_enumerate_terms(ctx, part, opts: EnumOpts, stream=None):
+    h = ctypes.c_void_p()
+    nc, nt = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load_library().pne_enumerate_terms(ctx, part, ctypes.byref(opts), stream, ctypes.byref(h),
+                                              ctypes.byref(nc), ctypes.byref(nt)), ctx)
+    return h, nc.value, nt.value
+
+
+def pne_terms_destroy(t):
+    load_library().pne_terms_destroy(t)
+
+
+def pne_contract_terms(ctx, terms, dtype, stream=None):
+    _check(load_library().pne_contract_terms(ctx, terms, int(dtype), stream), ctx)
+
+
+def pne_terms_n_results(terms) -> int:
+    return int(load_library().pne_terms_n_results(terms))
+
+
+def pne_terms_export(ctx, terms, n_clusters, K, with_values=True, stream=None):
+    """(edges [n_clusters, K] int32, w [n_results, n_clusters] float64 or None)."""
+    edges = np.full((max(n_clusters, 1), max(K, 1)), -1, dtype=np.int32)
+    w = np.zeros((pne_terms_n_results(terms), max(n_clusters, 1))) if with_values else None
+    _check(load_library().pne_terms_export(ctx, terms, stream, edges.ctypes.data,
+                                           w.ctypes.data if w is not None else None), ctx)
+    return edges[:n_clusters], (w[:, :n_clusters] if w is not None else None)
+
+
+def pne_ctx_profile(ctx, enable=True):
+    _check(load_library().pne_ctx_profile(ctx, int(bool(enable))), ctx)
+
+
+def pne_ctx_profile_read(ctx) -> dict:
+    """{kernel family: (launches, total_ms)}, largest total first."""
+    lib = load_library()
+    buf = (ProfileEntry * 64)()
+    n = lib.pne_ctx_profile_read(ctx, buf, 64)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n, 64))}
+
+
+def pne_terms_work(ctx, terms, stream=None) -> int:
+    v = ctypes.c_uint64()
+    _check(load_library().pne_terms_work(ctx, terms, stream, ctypes.byref(v)), ctx)
+    return int(v.value)
+
+
+def pne_measure_fma_peak(ctx, dtype, stream=None) -> float:
+    v = ctypes.c_double()
+    _check(load_library().pne_measure_fma_peak(ctx, int(dtype), stream, ctypes.byref(v)), ctx)
+    return float(v.value)
+
+
+def pne_sum(ctx, terms, stream=None):
+    n = pne_terms_n_results(terms)
+    out = (Result * n)()
+    _check(load_library().pne_sum(ctx, terms, stream, out), ctx)
+    return [r.as_dict() for r in out]
+
+
+# ------------------------------------------------------------------ marshalling helpers
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def network_struct(net, data=None, n_batch=1, data_on_device=False):
+    """pne_network for an ``inputs.Network``.  ``data``: a flat FP64 array of
+    n_batch tensor sets (numpy for host, a torch CUDA tensor for device), or
+    None to use the network's own tensors.  Returns (struct, keepalive)."""
+    bs, p_bs = _i32(net.bond_site.reshape(-1))
+    bd, p_bd = _i32(net.bond_dim)
+    sp, p_sp = _i32(net.site_ptr)
+    sb, p_sb = _i32(net.site_bonds)
+    if data is None:
+        flat, off = net.flat_data()
+        data = flat
+    else:
+        _, off = _offsets(net)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    if hasattr(data, "data_ptr"):
+        ptr = data.data_ptr()
+        data_on_device = bool(data.is_cuda)
+    else:
+        data = np.ascontiguousarray(data, dtype=np.float64)
+        ptr = data.ctypes.data
+    s = Network(net.n_sites, net.n_bonds, p_bs, p_bd, p_sp, p_sb, ctypes.c_void_p(ptr),
+                off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(data_on_device), int(n_batch))
+    return s, (bs, bd, sp, sb, off, data)
+
+
+def _offsets(net):
+    sizes = [int(np.prod(net.leg_dims(v))) for v in range(net.n_sites)]
+    off = np.zeros(net.n_sites + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    return sizes, off
+
+
+class Context:
+    """Owns a pne_ctx on one device.  ``torch_alloc=True`` routes the library's
+    device memory through PyTorch's caching allocator."""
+
+    def __init__(self, device=0, torch_alloc=False):
+        self.device = device
+        self.h = pne_ctx_create(device)
+        self._cbs = None
+        if torch_alloc:
+            import torch
+
+            def _alloc(nbytes, stream, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0)
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, stream, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cbs = (ALLOC_FN(_alloc), FREE_FN(_free))
+            pne_ctx_set_allocator(self.h, self._cbs[0], self._cbs[1], None)
+
+    def close(self):
+        if self.h is not None:
+            pne_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def expand(self, net, K, mode=PNE_MODE_LOOP, dtype=PNE_F64, data=None, n_batch=1, stream=None,
+               tol=1e-13, max_iter=10000, damping=0.0, use_cache=True, allow_noconv=False,
+               export=False):
+        """One pass: partition -> enumerate -> contract -> sum.  Returns the
+        list of result dicts (one per tensor set and open-index assignment);
+        with export=True also (edges, w) of the clusters."""
+        if isinstance(dtype, str):
+            dtype = DTYPES[dtype]
+        ns, keep = network_struct(net, data=data, n_batch=n_batch)
+        part, st = pne_build_partition(self.h, ns, PartitionOpts(tol, max_iter, damping), stream, allow_noconv)
+        try:
+            terms, nc, nt = pne_enumerate_terms(self.h, part, EnumOpts(K, mode, int(use_cache)), stream)
+            try:
+                pne_contract_terms(self.h, terms, dtype, stream)
+                res = pne_sum(self.h, terms, stream)
+                if export:
+                    res = (res, pne_terms_export(self.h, terms, nc, K, True, stream))
+            finally:
+                pne_terms_destroy(terms)
+        finally:
+            pne_partition_destroy(part)
+        del keep
+        return res
+
+
+def run(net, K, mode=PNE_MODE_LOOP, dtype=PNE_F64, device=0, **kw):
+    ctx = Context(device)
+    try:
+        return ctx.expand(net, K, mode, dtype, **kw)
+    finally:
+        ctx.close()
+
+
+def open_tensor(results, open_dims, n_sets=1):
+    """Assemble the open-index tensors from pne_sum's results (set-major,
+    assignments row-major over the open bonds in ascending id)."""
+    vals = np.array([r["sign"] * math.exp(r["log_abs"]) if r["sign"] != 0 and np.isfinite(r["log_abs"]) else 0.0
+                     for r in results])
+    return vals.reshape((n_sets,) + tuple(open_dims))

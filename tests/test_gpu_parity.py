@@ -1,0 +1,220 @@
+"""GPU path (C ABI) vs the FP64 CPU oracle, element by element.
+
+Tolerances: counts and cluster lists bit-exact; FP64 values within 1e-10
+relative on Z_K (|d ln Z| <= 1e-10) and per order within 1e-10 of sum_k |c_k|;
+cluster weights within rtol 1e-9 (both sides converge BP to 1e-13).  Reduced
+precisions are checked against the library's own a-priori bound err_bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2512_10910_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2512_10910_gb300 import pne  # noqa: E402
+from oracle import enumerate as E  # noqa: E402
+from oracle import exact as Ex  # noqa: E402
+from oracle import expansion as X  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2512_10910_gb300 import build
+    build.build()
+    c = pne.Context(0)
+    yield c
+    c.close()
+
+
+def _canon(edges, w):
+    tuples = [tuple(int(x) for x in r if x >= 0) for r in edges]
+    order = sorted(range(len(tuples)), key=lambda i: (len(tuples[i]), tuples[i]))
+    return [tuples[i] for i in order], (w[:, order] if w is not None else None)
+
+
+def _check_values(res, ref, tol=1e-10):
+    assert abs(res["log_abs"] - ref.log_abs) <= tol, (res["log_abs"], ref.log_abs)
+    assert res["sign"] == ref.sign
+    scale = float(np.sum(np.abs(ref.c)))
+    np.testing.assert_allclose(res["c"], ref.c, rtol=0, atol=tol * scale)
+
+
+# ---------------------------------------------------------------- closed-form pins
+def test_ising_4x4_full_order_loop_equals_brute_force(ctx):
+    net = I.ising_tensors(I.square_lattice(4, 4, 2), 0.40)
+    (res,), (edges, w) = ctx.expand(net, 24, pne.PNE_MODE_LOOP, pne.PNE_F64, export=True)
+    z = Ex.ising_spin_sum(net, 0.40)
+    assert res["value"] == pytest.approx(z, rel=1e-12)
+    assert res["n_clusters"] == 15593 and res["n_terms"] == 16372
+    cl, _ = _canon(edges, None)
+    assert cl == E.clusters_bitmask(net, 24, E.LOOP)
+    cnt = E.even_subsets_by_size(net)
+    t = math.tanh(0.40)
+    np.testing.assert_allclose(res["c"], [cnt[k] * t ** k for k in range(25)], atol=1e-13)
+
+
+def test_ising_4x4_full_order_all_mode(ctx):
+    net = I.ising_tensors(I.square_lattice(4, 4, 2), 0.40)
+    (res,) = ctx.expand(net, 24, pne.PNE_MODE_ALL, pne.PNE_F64)
+    assert res["value"] == pytest.approx(Ex.ising_spin_sum(net, 0.40), rel=1e-12)
+    assert res["n_terms"] == 2 ** 24
+    assert res["n_clusters"] == E.count_clusters_bitmask(net, 24, E.ALL)
+
+
+def test_all_mode_random_full_order_is_exact(ctx):
+    # Eq. A2-A4: summing every P/Q string reproduces the network, whatever P is.
+    net = I.random_tensors(I.square_lattice(3, 3, 2), 4, "bias:0.2")
+    (res,) = ctx.expand(net, 12, pne.PNE_MODE_ALL, pne.PNE_F64)
+    assert res["value"] == pytest.approx(float(Ex.contract_einsum(net)), rel=1e-11)
+    ref = X.pne(net, 12, E.ALL)
+    _check_values(res, ref)
+
+
+@pytest.mark.parametrize("shape,D,seed", [((3, 3), 3, 1), ((2, 3), 3, 2), ((3, 3), 2, 3), ((2, 4), 4, 5)])
+def test_loop_full_order_is_exact_at_fixed_point(ctx, shape, D, seed):
+    net = I.random_tensors(I.square_lattice(shape[0], shape[1], D), seed)
+    M = net.n_bonds
+    (res,) = ctx.expand(net, M, pne.PNE_MODE_LOOP, pne.PNE_F64)
+    assert res["value"] == pytest.approx(float(Ex.contract_einsum(net)), rel=1e-10)
+    _check_values(res, X.pne(net, M, E.LOOP))
+
+
+# ---------------------------------------------------------------- oracle parity
+@pytest.mark.parametrize("L,D,K,seed", [(6, 4, 8, 0), (5, 3, 10, 7), (7, 5, 6, 3), (16, 4, 8, 0)])
+def test_random_2d_parity_f64(ctx, L, D, K, seed):
+    net = I.random_tensors(I.square_lattice(L, L, D), seed)
+    ref = X.pne(net, K, E.LOOP)
+    (res,), (edges, w) = ctx.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64, export=True)
+    assert res["n_clusters"] == ref.n_clusters and res["n_terms"] == ref.n_terms
+    cl, wc = _canon(edges, w)
+    assert cl == list(ref.clusters)
+    np.testing.assert_allclose(wc[0], ref.w, rtol=1e-9, atol=1e-13)
+    _check_values(res, ref)
+
+
+def test_cubic_parity_and_batch(ctx):
+    g = I.cubic_lattice(3, 3, 3, 2)
+    nets = [I.ising_tensors(g, b) for b in (0.20, 0.2217, 0.25)] + [I.random_tensors(g, 9, "n1,0.3")]
+    data = np.concatenate([n.flat_data()[0] for n in nets])
+    res = ctx.expand(nets[0], 8, pne.PNE_MODE_LOOP, pne.PNE_F64, data=data, n_batch=len(nets))
+    for r, n in zip(res, nets):
+        ref = X.pne(n, 8, E.LOOP)
+        assert r["n_clusters"] == ref.n_clusters and r["n_terms"] == ref.n_terms
+        _check_values(r, ref)
+
+
+def test_batch_equals_individual_bitwise(ctx):
+    g = I.square_lattice(6, 5, 4)
+    nets = [I.random_tensors(g, s) for s in (11, 12, 13)]
+    data = np.concatenate([n.flat_data()[0] for n in nets])
+    batch = ctx.expand(nets[0], 8, pne.PNE_MODE_LOOP, pne.PNE_F64, data=data, n_batch=3)
+    for r, n in zip(batch, nets):
+        (one,) = ctx.expand(n, 8, pne.PNE_MODE_LOOP, pne.PNE_F64)
+        assert np.array_equal(one["c"], r["c"]) and one["log_abs"] == r["log_abs"]
+
+
+def test_deterministic_and_device_input(ctx):
+    net = I.random_tensors(I.square_lattice(8, 8, 4), 21)
+    flat, _ = net.flat_data()
+    (a,) = ctx.expand(net, 8, pne.PNE_MODE_LOOP, pne.PNE_F64)
+    (b,) = ctx.expand(net, 8, pne.PNE_MODE_LOOP, pne.PNE_F64, data=torch.from_numpy(flat).cuda())
+    assert np.array_equal(a["c"], b["c"]) and a["log_abs"] == b["log_abs"]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "tf32", "bf16"])
+def test_reduced_precision_within_stated_bound(ctx, dtype):
+    net = I.random_tensors(I.square_lattice(8, 8, 4), 3)
+    ref = X.pne(net, 8, E.LOOP)
+    (res,) = ctx.expand(net, 8, pne.PNE_MODE_LOOP, dtype)
+    rel = abs(math.expm1(res["log_abs"] - ref.log_abs))
+    assert rel <= res["err_bound"], (rel, res["err_bound"])
+    assert res["err_bound"] < {"f32": 1e-4, "tf32": 0.1, "bf16": 0.5}[dtype]
+    print(dtype, "rel err", rel, "bound", res["err_bound"])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "tf32", "bf16"])
+def test_reduced_precision_ising_cubic(ctx, dtype):
+    net = I.ising_tensors(I.cubic_lattice(4, 4, 4, 2), 0.2217)
+    ref = X.pne(net, 8, E.LOOP)
+    (res,) = ctx.expand(net, 8, pne.PNE_MODE_LOOP, dtype)
+    rel = abs(math.expm1(res["log_abs"] - ref.log_abs))
+    assert rel <= res["err_bound"], (rel, res["err_bound"])
+
+
+# ---------------------------------------------------------------- open indices
+def test_open_output_all_mode_exact(ctx):
+    go = I.with_open_legs(I.square_lattice(3, 2, 2), [(0, 2), (2, 2), (4, 2)])
+    net = I.random_tensors(go, 12)
+    res = ctx.expand(net, 7, pne.PNE_MODE_ALL, pne.PNE_F64)      # 7 closed bonds: full order
+    T = pne.open_tensor(res, [2, 2, 2])[0]
+    assert Ex.eps2(Ex.contract_einsum(net), T) < 1e-12
+
+
+def test_open_output_loop_parity(ctx):
+    go = I.with_open_legs(I.square_lattice(4, 3, 3), [(0, 2), (5, 3), (11, 2)])
+    net = I.random_tensors(go, 5)
+    ref, entries, _ = X.pne_open(net, 8, E.LOOP)
+    res = ctx.expand(net, 8, pne.PNE_MODE_LOOP, pne.PNE_F64)
+    T = pne.open_tensor(res, [2, 3, 2])[0]
+    np.testing.assert_allclose(T, ref, rtol=1e-10)
+
+
+# ---------------------------------------------------------------- edge cases
+def test_low_orders_and_trees(ctx):
+    net = I.random_tensors(I.square_lattice(5, 4, 3), 2)
+    ref0 = X.pne(net, 0, E.LOOP)
+    for K in (0, 1, 2, 3):
+        (r,) = ctx.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64)
+        assert r["n_clusters"] == 0 and r["n_terms"] == 1
+        assert abs(r["log_abs"] - ref0.log_abs) < 1e-10
+    tree = I.random_tensors(I.grid_graph(6, [(0, 1), (1, 2), (1, 3), (3, 4), (4, 5)], [3, 2, 4, 2, 3]), 8)
+    (r,) = ctx.expand(tree, 10, pne.PNE_MODE_LOOP, pne.PNE_F64)
+    assert r["n_clusters"] == 0
+    assert r["value"] == pytest.approx(float(Ex.contract_einsum(tree)), rel=1e-12)
+    single = I.grid_graph(1, [], [])
+    single = single.with_tensors([np.array(3.25)])
+    (r,) = ctx.expand(single, 4, pne.PNE_MODE_LOOP, pne.PNE_F64)
+    assert r["value"] == pytest.approx(3.25, rel=1e-15)
+
+
+def test_multi_edges_and_irregular_graph(ctx):
+    g = I.grid_graph(5, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 2), (0, 1), (3, 1)], [2, 3, 2, 2, 3, 2, 2, 3])
+    net = I.random_tensors(g, 4)
+    for K in (3, 5, 8):
+        ref = X.pne(net, K, E.LOOP)
+        (res,), (edges, w) = ctx.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64, export=True)
+        cl, wc = _canon(edges, w)
+        assert cl == list(ref.clusters)
+        np.testing.assert_allclose(wc[0], ref.w, rtol=1e-9, atol=1e-13)
+        _check_values(res, ref)
+
+
+def test_invalid_input_is_rejected(ctx):
+    net = I.random_tensors(I.square_lattice(3, 3, 2), 1)
+    bad = I.Network(net.n_sites, net.bond_site, np.full(net.n_bonds, 9, dtype=np.int32), net.site_ptr,
+                    net.site_bonds, net.leg_dir, net.tensors)
+    with pytest.raises(pne.PneError) as ei:
+        ctx.expand(bad, 4, data=np.zeros(10 ** 5))
+    assert ei.value.status == pne.PNE_EINVAL
+    with pytest.raises(pne.PneError):
+        ctx.expand(net, 40)           # order above the limit
+
+
+def test_torch_allocator_gives_identical_results():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    net = I.random_tensors(I.square_lattice(6, 6, 3), 4)
+    c1 = pne.Context(0)
+    c2 = pne.Context(0, torch_alloc=True)
+    try:
+        (a,) = c1.expand(net, 8)
+        (b,) = c2.expand(net, 8)
+    finally:
+        c1.close(); c2.close()
+    assert np.array_equal(a["c"], b["c"])

@@ -1,0 +1,53 @@
+"""CPU-side checks of the C-ABI library: it builds for sm_103a, loads, and
+exports every function include/pne.h declares.  No GPU compute is issued."""
+import os
+import re
+
+import pytest
+
+from paper_2512_10910_gb300 import build as B
+from paper_2512_10910_gb300 import pne
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(pne_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = B.build()
+    assert os.path.exists(path)
+    lib = pne.load_library()
+    declared = _declared()
+    assert len(declared) >= 12
+    missing = [n for n in declared if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_the_header():
+    for n in _declared():
+        assert hasattr(pne, n), n
+
+
+def test_ctx_create_without_a_device_reports_an_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(pne.PneError) as ei:
+        pne.pne_ctx_create(0)
+    assert ei.value.status == pne.PNE_ECUDA
+
+
+def test_struct_layouts():
+    import ctypes
+    # pne_network: 2 ints, 4 pointers, data, data_off, 2 ints (LP64)
+    assert ctypes.sizeof(pne.Network) == 8 + 4 * 8 + 8 + 8 + 8
+    assert ctypes.sizeof(pne.PartitionOpts) == 24
+    assert ctypes.sizeof(pne.EnumOpts) == 12
