@@ -29,6 +29,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <unordered_map>
 
 #include "pne_internal.h"
 
@@ -93,7 +94,7 @@ __device__ __forceinline__ double pow2(int e) { return ldexp(1.0, e); }
 
 // ---------------------------------------------------------------- plan
 // Step layout (ints): [0] site, [1] mask, [2] nF (size of the new frontier),
-// [3] nC (closing bonds), [4] out_size, [5] close_size, [6..7] spare,
+// [3] nC (closing bonds), [4] out_size, [5] close_size, [6] slot, [7] spare,
 // then dimsF[kMaxFront], sxF[kMaxFront], smF[kMaxFront],
 // dimsC[kMaxClose], sxC[kMaxClose], smC[kMaxClose].
 // Builds the elimination plan of one cluster (single thread).  Returns the
@@ -191,6 +192,7 @@ __device__ int build_plan(const ContractParams &P, int64_t c, int *plan, int *si
         st[0] = P.cl_verts[c * P.vwidth + v];
         st[1] = mask[v];
         st[2] = n2; st[3] = nC; st[4] = outsz; st[5] = closz;
+        st[6] = v;                              // slot of the site in the cluster's vertex list
         sites_out[t] = v;
         for (int i = 0; i < n2; ++i) F[i] = F2[i];
         nF = n2;
@@ -515,6 +517,271 @@ pne_status run_general(pne_ctx *ctx, KERN kern, const ContractParams &cp, size_t
 
 namespace {
 
+constexpr int kPlanInts = kMaxSteps * kStepInts;
+
+// Local structure of a cluster, independent of where it sits: site slots
+// (rank in the sorted vertex list), the leg of each bond end and each bond's
+// excited dimension.  Clusters with equal keys have equal plans.
+__device__ int cluster_key(const ContractParams &P, int64_t c, int32_t *key, int cap)
+{
+    const int32_t *E = P.cl_edges + c * P.width;
+    const int32_t *V = P.cl_verts + c * P.vwidth;
+    int s = 0, nv = 0;
+    while (s < P.width && E[s] >= 0) ++s;
+    while (nv < P.vwidth && V[nv] >= 0) ++nv;
+    int n = 0;
+    key[n++] = nv; key[n++] = s;
+    for (int k = 0; k < s && n + 5 <= cap; ++k) {
+        const int e = E[k];
+        for (int side = 0; side < 2; ++side) {
+            const int x = P.bond_site[2 * e + side];
+            int slot = 0;
+            while (slot < nv && V[slot] != x) ++slot;
+            key[n++] = slot;
+            key[n++] = P.bond_leg[2 * e + side];
+        }
+        key[n++] = P.bond_dim[e];
+    }
+    return n;
+}
+
+__global__ void shape_hash_kernel(ContractParams P, unsigned long long *hash)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < P.n_clusters;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int32_t key[2 + 5 * 32];
+        const int n = cluster_key(P, c, key, 2 + 5 * 32);
+        unsigned long long h = 1469598103934665603ull;
+        for (int i = 0; i < n; ++i) {
+            h ^= (unsigned long long)(uint32_t)key[i];
+            h *= 1099511628211ull;
+            h ^= h >> 29;
+        }
+        hash[c] = h;
+    }
+}
+
+// 1 where a cluster's key differs from its shape representative's (a hash collision)
+__global__ void shape_verify_kernel(ContractParams P, const int32_t *shape_of, const int32_t *rep, int32_t *bad)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < P.n_clusters;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a[2 + 5 * 32], b[2 + 5 * 32];
+        const int na = cluster_key(P, c, a, 2 + 5 * 32);
+        const int nb = cluster_key(P, rep[shape_of[c]], b, 2 + 5 * 32);
+        int d = (na != nb);
+        for (int i = 0; i < na && !d; ++i) d = (a[i] != b[i]);
+        bad[c] = d;
+    }
+}
+
+__global__ void shape_plan_kernel(ContractParams P, const int32_t *rep, int n_shapes, int32_t *plans,
+                                  int32_t *steps)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *plan = (int *)smem_raw + wib * (kMaxSteps * kStepInts + kMaxSteps + 4);
+    int *sites = plan + kMaxSteps * kStepInts;
+    for (int sh = blockIdx.x * kCtWarps + wib; sh < n_shapes; sh += gridDim.x * kCtWarps) {
+        if (lane == 0) steps[sh] = build_plan(P, rep[sh], plan, sites, kWarpTensorMax);
+        __syncwarp();
+        const int n = steps[sh];
+        for (int i = lane; i < (n > 0 ? n : 0) * kStepInts; i += 32) plans[(int64_t)sh * kPlanInts + i] = plan[i];
+        __syncwarp();
+    }
+}
+
+// One cluster per lane; the 32 lanes of a warp take consecutive clusters in
+// shape order and run the same plan on their own sites.  Lane l keeps its
+// intermediate tensor at X[j * 32 + l] (conflict-free shared memory).
+template <typename T, typename L, int R, int XMAX>
+__global__ void __launch_bounds__(128) contract_shaped_kernel(ContractParams P, const int32_t *perm,
+                                                              const int32_t *shape_of, const int32_t *plans,
+                                                              const int32_t *plan_steps)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    T *X0 = (T *)smem_raw + (int64_t)wib * 2 * XMAX * 32 + lane;
+    T *X1 = X0 + XMAX * 32;
+    const int64_t groups = (P.n_clusters + 31) / 32;
+    const int64_t items = groups * P.n_members;
+    for (int64_t it = (int64_t)blockIdx.x * wpb + wib; it < items; it += (int64_t)gridDim.x * wpb) {
+        const int b = (int)(it / groups);
+        const int64_t i = (it % groups) * 32 + lane;
+        if (i >= P.n_clusters) continue;
+        const int64_t c = perm[i];
+        const int sh = shape_of[c];
+        const int *plan = plans + (int64_t)sh * kPlanInts;
+        const int nsteps = plan_steps[sh];
+        const int32_t *V = P.cl_verts + c * P.vwidth;
+        T *X = X0, *Y = X1;
+        X[0] = (T)1;
+        int expo = 0, nz = 0;
+        double zs = 1.0;
+        for (int t = 0; t < nsteps; ++t) {
+            const int *st = plan + t * kStepInts;
+            const int mask = st[1], nF = st[2], nC = st[3], outsz = st[4], closz = st[5];
+            const int site = V[st[6]];
+            const int *dimsF = st + 8, *sxF = dimsF + kMaxFront, *smF = sxF + kMaxFront;
+            const int *dimsC = smF + kMaxFront, *sxC = dimsC + kMaxClose, *smC = sxC + kMaxClose;
+            const int64_t mbase = (int64_t)b * P.stride + P.tens_off[site] + P.blk_off[site * kBlkStride + mask];
+            T mx = (T)0;
+            for (int o = 0; o < outsz; ++o) {
+                int r = o, xb = 0, mb = 0;
+                for (int q = nF - 1; q >= 0; --q) { const int d = r % dimsF[q]; r /= dimsF[q]; xb += d * sxF[q]; mb += d * smF[q]; }
+                T acc = (T)0;
+                for (int cc = 0; cc < closz; ++cc) {
+                    int rc = cc, xi = xb, mi = mb;
+                    for (int q = nC - 1; q >= 0; --q) { const int d = rc % dimsC[q]; rc /= dimsC[q]; xi += d * sxC[q]; mi += d * smC[q]; }
+                    acc = fma(rnd<R>(X[xi * 32]), (T)L::get(P.M, mbase + mi), acc);
+                }
+                Y[o * 32] = acc;
+                mx = fmax(mx, fabs(acc));
+            }
+            if (mx > (T)0) {
+                int e;
+                frexp((double)mx, &e);
+                const T sc = (T)pow2(-e);
+                for (int o = 0; o < outsz; ++o) Y[o * 32] *= sc;
+                expo += e;
+            }
+            T *tmp = X; X = Y; Y = tmp;
+            if (P.zero[(int64_t)b * P.n_sites + site]) { ++nz; zs *= P.scale[(int64_t)b * P.n_sites + site]; }
+        }
+        P.w[(int64_t)b * P.n_clusters + c] = ldexp((double)X[0], expo) * zs;
+        P.nzc[(int64_t)b * P.n_clusters + c] = nz;
+    }
+}
+
+template <typename T, typename L, int R, int XMAX>
+pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &rec, cudaStream_t s)
+{
+    auto kern = contract_shaped_kernel<T, L, R, XMAX>;
+    const int per_warp = 2 * XMAX * 32 * (int)sizeof(T);
+    int wpb = (96 * 1024) / per_warp;
+    if (wpb > 4) wpb = 4;
+    if (wpb < 1) wpb = 1;
+    const size_t smem = (size_t)wpb * per_warp;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t items = ((cp.n_clusters + 31) / 32) * cp.n_members;
+    int64_t g = (items + wpb - 1) / wpb;
+    const int64_t cap = (int64_t)ctx->n_sm * 16;
+    if (g > cap) g = cap;
+    kern<<<(int)g, wpb * 32, smem, s>>>(cp, (const int32_t *)rec.perm.ptr, (const int32_t *)rec.shape_of.ptr,
+                                        (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr);
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    return PNE_OK;
+}
+
+template <typename T, typename L, int R>
+pne_status dispatch_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &rec, cudaStream_t s)
+{
+    if (rec.max_out <= 16) return run_shaped<T, L, R, 16>(ctx, cp, rec, s);
+    if (rec.max_out <= 64) return run_shaped<T, L, R, 64>(ctx, cp, rec, s);
+    return run_shaped<T, L, R, 256>(ctx, cp, rec, s);
+}
+
+}  // namespace
+
+pne_status prepare_shapes(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, cudaStream_t s)
+{
+    rec.shaped = false;
+    if (rec.n_clusters == 0 || all_dims_two(g)) return PNE_OK;
+    const int64_t n = (int64_t)rec.n_clusters;
+    ContractParams cp;
+    cp.n_clusters = n; cp.n_members = 1; cp.n_sites = g.n_sites;
+    cp.width = rec.width; cp.vwidth = rec.vwidth;
+    cp.cl_edges = (const int32_t *)rec.cl_edges.ptr; cp.cl_verts = (const int32_t *)rec.cl_verts.ptr;
+    cp.cl_size = (const int32_t *)rec.cl_size.ptr;
+    cp.bond_site = g.d_bond_site; cp.bond_dim = g.d_bond_dim; cp.bond_leg = g.d_bond_leg;
+    DevBuf dh;
+    pne_status st = dev_alloc(ctx, dh, n * 8, s);
+    if (st) return st;
+    {
+        ProfScope ps(ctx, s, "shapes");
+        shape_hash_kernel<<<grid_for(n, 128, ctx->n_sm), 128, 0, s>>>(cp, (unsigned long long *)dh.ptr);
+    }
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    std::vector<unsigned long long> h(n);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), dh.ptr, n * 8, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    // shape ids in order of first appearance (deterministic)
+    std::unordered_map<unsigned long long, int32_t> id;
+    id.reserve(1024);
+    std::vector<int32_t> shape(n), rep;
+    for (int64_t c = 0; c < n; ++c) {
+        auto it = id.find(h[c]);
+        if (it == id.end()) { it = id.emplace(h[c], (int32_t)rep.size()).first; rep.push_back((int32_t)c); }
+        shape[c] = it->second;
+    }
+    // exact key check against the representative; a mismatch gets its own shape
+    DevBuf dshape, drep, dbad;
+    if ((st = dev_alloc(ctx, dshape, n * 4, s)) || (st = dev_alloc(ctx, drep, rep.size() * 4, s)) ||
+        (st = dev_alloc(ctx, dbad, n * 4, s)))
+        return st;
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dshape.ptr, shape.data(), n * 4, cudaMemcpyHostToDevice, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(drep.ptr, rep.data(), rep.size() * 4, cudaMemcpyHostToDevice, s));
+    shape_verify_kernel<<<grid_for(n, 128, ctx->n_sm), 128, 0, s>>>(cp, (const int32_t *)dshape.ptr,
+                                                                  (const int32_t *)drep.ptr, (int32_t *)dbad.ptr);
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    std::vector<int32_t> bad(n);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bad.data(), dbad.ptr, n * 4, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    bool any_bad = false;
+    for (int64_t c = 0; c < n; ++c)
+        if (bad[c]) { shape[c] = (int32_t)rep.size(); rep.push_back((int32_t)c); any_bad = true; }
+    const int ns = (int)rep.size();
+    if (any_bad) {
+        dev_free(ctx, drep, s);
+        if ((st = dev_alloc(ctx, drep, ns * 4, s))) return st;
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(drep.ptr, rep.data(), ns * 4, cudaMemcpyHostToDevice, s));
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dshape.ptr, shape.data(), n * 4, cudaMemcpyHostToDevice, s));
+    }
+    // plans of the representatives
+    if ((st = dev_alloc(ctx, rec.plans, (size_t)ns * kPlanInts * 4, s)) ||
+        (st = dev_alloc(ctx, rec.plan_steps, (size_t)ns * 4, s)))
+        return st;
+    {
+        const size_t smem = (size_t)kCtWarps * (kMaxSteps * kStepInts + kMaxSteps + 4) * 4;
+        shape_plan_kernel<<<grid_for(ns, kCtWarps, ctx->n_sm, 16), kCtWarps * 32, smem, s>>>(
+            cp, (const int32_t *)drep.ptr, ns, (int32_t *)rec.plans.ptr, (int32_t *)rec.plan_steps.ptr);
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    std::vector<int32_t> steps(ns), plans((size_t)ns * kPlanInts);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(steps.data(), rec.plan_steps.ptr, ns * 4, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(plans.data(), rec.plans.ptr, plans.size() * 4, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    rec.shape_fma.assign(ns, 0);
+    rec.shape_count.assign(ns, 0);
+    int max_out = 1;
+    bool ok = true;
+    for (int i = 0; i < ns; ++i) {
+        if (steps[i] < 0) { ok = false; break; }
+        for (int t = 0; t < steps[i]; ++t) {
+            const int32_t *stp = plans.data() + (size_t)i * kPlanInts + t * kStepInts;
+            rec.shape_fma[i] += (uint64_t)stp[4] * stp[5];
+            max_out = std::max(max_out, (int)stp[4]);
+        }
+    }
+    for (int64_t c = 0; c < n; ++c) rec.shape_count[shape[c]]++;
+    // clusters in shape order (stable)
+    std::vector<int64_t> start(ns + 1, 0);
+    for (int i = 0; i < ns; ++i) start[i + 1] = start[i] + rec.shape_count[i];
+    std::vector<int32_t> perm(n);
+    for (int64_t c = 0; c < n; ++c) perm[start[shape[c]]++] = (int32_t)c;
+    if ((st = dev_alloc(ctx, rec.perm, n * 4, s))) return st;
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(rec.perm.ptr, perm.data(), n * 4, cudaMemcpyHostToDevice, s));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    rec.shape_of = dshape;
+    rec.n_shapes = ns;
+    rec.max_out = max_out;
+    rec.shaped = ok && max_out <= 256;
+    dev_free(ctx, dh, s); dev_free(ctx, drep, s); dev_free(ctx, dbad, s);
+    return PNE_OK;
+}
+
+namespace {
+
 // Multiply-adds of each cluster's plan (the algorithmic work of the contraction).
 __global__ void __launch_bounds__(kCtWarps * 32) plan_work_kernel(ContractParams P, unsigned long long *total)
 {
@@ -582,6 +849,13 @@ pne_status launch_contract(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s
     cp.w = (double *)t->w.ptr; cp.nzc = (int32_t *)t->nzc.ptr; cp.status = (int32_t *)t->status.ptr;
     const bool q1 = all_dims_two(p->closed);
     ProfScope ps__(ctx, s, "contract");
+    if (!q1 && rec.shaped) {
+        if (dtype == PNE_F64) { cp.M = p->Mb.ptr; return dispatch_shaped<double, Load<double>, 0>(ctx, cp, rec, s); }
+        if (dtype == PNE_BF16) { cp.M = p->Mb16.ptr; return dispatch_shaped<float, LoadBF16, 2>(ctx, cp, rec, s); }
+        cp.M = p->Mb32.ptr;
+        if (dtype == PNE_TF32) return dispatch_shaped<float, Load<float>, 1>(ctx, cp, rec, s);
+        return dispatch_shaped<float, Load<float>, 0>(ctx, cp, rec, s);
+    }
     if (dtype == PNE_F64) {
         cp.M = p->Mb.ptr;
         if (q1) contract_q1_kernel<double, Load<double>><<<grid_for(cp.n_clusters * cp.n_members, 256, ctx->n_sm), 256, 0, s>>>(cp);

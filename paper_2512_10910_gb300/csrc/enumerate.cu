@@ -36,9 +36,10 @@ namespace pne {
 
 namespace {
 
-constexpr int kPrefixMax = 5;     // deepest prefix level kept as explicit nodes
-constexpr int kNodeU = 32;        // candidate-list capacity of a prefix node
-constexpr int64_t kPrefixTarget = 65536;   // expand while a level has fewer nodes
+constexpr int kPrefixMax = 8;     // deepest prefix level kept as explicit nodes
+constexpr int kNodeU = 48;        // candidate-list capacity of a prefix node
+constexpr int64_t kPrefixTarget = 1 << 20;  // expand breadth-first while a level is smaller
+constexpr int64_t kNodeCap = 1 << 22;       // never materialise a larger level
 
 struct Node {
     int32_t S[kPrefixMax];
@@ -562,6 +563,11 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         }
         int64_t n_child = 0;
         if ((st = device_exclusive_scan(ctx, (int64_t *)coff.ptr, cur.n, &n_child, s))) return st;
+        if (n_child > kNodeCap) {             // too wide: search depth-first from this level
+            dev_free(ctx, cc, s);
+            dev_free(ctx, coff, s);
+            break;
+        }
         Level nxt;
         nxt.n = n_child;
         if ((st = dev_alloc(ctx, nxt.nodes, sizeof(Node) * std::max<int64_t>(n_child, 1), s))) return st;

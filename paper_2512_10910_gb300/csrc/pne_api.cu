@@ -82,6 +82,10 @@ EnumRecord::~EnumRecord()
     dev_free(ctx, cl_verts, nullptr);
     dev_free(ctx, cl_size, nullptr);
     for (auto &L : levels) dev_free(ctx, L.idx, nullptr);
+    dev_free(ctx, shape_of, nullptr);
+    dev_free(ctx, perm, nullptr);
+    dev_free(ctx, plans, nullptr);
+    dev_free(ctx, plan_steps, nullptr);
 }
 
 namespace {
@@ -412,6 +416,7 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
             } else {
                 if ((st = enumerate_clusters(ctx, g, K, mode, *rec, s))) return st;
                 if ((st = enumerate_tuples(ctx, *rec, s))) return st;
+                if ((st = prepare_shapes(ctx, g, *rec, s))) return st;
             }
         }
         if (opts->use_cache) ctx->enum_cache[key] = rec;
@@ -600,6 +605,12 @@ pne_status pne_terms_work(pne_ctx *ctx, const pne_terms *t, void *stream, uint64
 {
     if (!ctx || !t || !fma_per_set) return PNE_EINVAL;
     if (t->mode != PNE_MODE_LOOP) { set_error(ctx, PNE_EINVAL, "work count needs LOOP mode"); return PNE_EINVAL; }
+    if (t->rec->shaped) {
+        uint64_t f = 0;
+        for (int i = 0; i < t->rec->n_shapes; ++i) f += t->rec->shape_fma[i] * (uint64_t)t->rec->shape_count[i];
+        *fma_per_set = f;
+        return PNE_OK;
+    }
     return launch_plan_work(ctx, t, (cudaStream_t)stream, fma_per_set);
 }
 

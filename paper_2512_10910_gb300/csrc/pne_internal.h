@@ -147,6 +147,15 @@ struct EnumRecord {
     std::vector<Level> levels;
     uint64_t n_terms = 0;                       // including the empty term
     std::vector<uint64_t> terms_by_order;       // [K+1]
+    // per-shape contraction plans (bond dimension > 2 somewhere)
+    bool shaped = false;
+    int n_shapes = 0, max_out = 0;
+    DevBuf shape_of;                            // [n] int32 shape id per cluster
+    DevBuf perm;                                // [n] int32 clusters ordered by shape
+    DevBuf plans;                               // [n_shapes][plan ints]
+    DevBuf plan_steps;                          // [n_shapes] int32
+    std::vector<uint64_t> shape_fma;            // [n_shapes] multiply-adds of the plan
+    std::vector<int64_t> shape_count;           // [n_shapes] clusters per shape
     ~EnumRecord();
 };
 
@@ -196,6 +205,7 @@ pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s,
                        std::vector<double> &c, std::vector<double> &abs_c, int32_t *h_status);
 pne_status launch_all_mode(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s);
 pne_status launch_plan_work(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, uint64_t *fma);
+pne_status prepare_shapes(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, cudaStream_t s);
 pne_status launch_fma_peak(pne_ctx *ctx, int dtype, cudaStream_t s, double *flops);
 
 // exclusive scan of int64 counts on the device; total returned on the host
