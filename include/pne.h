@@ -181,6 +181,39 @@ int64_t pne_terms_n_results(const pne_terms *t);
  * Clusters are listed grouped by size.  Synchronises `stream`. */
 pne_status pne_terms_export(pne_ctx *ctx, const pne_terms *t, void *stream, int32_t *edges, double *w);
 
+/* ---- belief propagation without device allocation ------------------------ */
+
+/* The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory while they run -- code inside a CUDA stream capture,
+ * a host framework that owns a fixed device arena, or a real-time loop where
+ * cudaMalloc's implicit synchronisation is not allowed.  It runs the same BP
+ * sweeps as pne_build_partition and returns the fixed-point messages, but
+ * calls no cudaMalloc, cudaFree or allocating library routine: its working
+ * memory (geometry tables, the second message buffer, convergence words) is a
+ * file-scope device array of PNE_NOALLOC_SCRATCH_BYTES that every GPU which
+ * loads the library holds until the process exits.
+ *
+ *   net        network as for pne_build_partition; net->data must be a device
+ *              pointer (data_on_device != 0), n_batch tensor sets.
+ *   tol, max_iter  as in pne_partition_opts (defaults when <= 0).
+ *   msg_out    device buffer [n_batch][site_ptr[n_sites]][8] doubles: for every
+ *              leg slot (sites in order, each site's legs in ascending bond
+ *              id) the outgoing fixed-point message, unit 2-norm, largest
+ *              entry positive, zero-padded to 8 entries.
+ *   iters_out, residual_out  host arrays [n_batch] (may be NULL): sweeps taken
+ *              (0 = not converged) and the last sweep's largest change.
+ * Returns PNE_EINVAL when the tables and buffers need more than
+ * PNE_NOALLOC_SCRATCH_BYTES (or on malformed input), PNE_ENOCONV,
+ * PNE_EDEGENERATE, PNE_ETIMEOUT or PNE_ECUDA as pne_build_partition does.
+ * Synchronises `stream`.  The first call on a device looks up the array's
+ * device address (per device, with that device current); make that first
+ * call before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents: calls that overlap on the GPU (other streams,
+ * other host threads) race and corrupt each other. */
+#define PNE_NOALLOC_SCRATCH_BYTES (8u << 20)
+pne_status pne_bp_messages_noalloc(const pne_network *net, double tol, int32_t max_iter, double *msg_out,
+                                   int32_t *iters_out, double *residual_out, void *stream);
+
 /* ---- measurement --------------------------------------------------------- */
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around

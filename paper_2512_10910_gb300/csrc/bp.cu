@@ -670,3 +670,216 @@ pne_status launch_convert(pne_ctx *ctx, pne_partition *p, int dtype, cudaStream_
 }
 
 }  // namespace pne
+
+// ---------------------------------------------------------------- BP without device allocation
+// Working memory of pne_bp_messages_noalloc: one file-scope device array.
+// Host code only ever passes its device address (looked up per device).
+static __device__ __align__(256) unsigned char g_bp_noalloc_scratch[PNE_NOALLOC_SCRATCH_BYTES];
+
+namespace pne {
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+// bond_leg, incoming-message slots and tensor offsets from the raw geometry,
+// one thread (tables are small; the call allocates nothing to go faster)
+__global__ void noalloc_tables_kernel(int n_sites, int n_bonds, const int32_t *bond_site, const int32_t *bond_dim,
+                                      const int32_t *site_ptr, const int32_t *site_bonds, int32_t *bond_leg,
+                                      int32_t *inc_slot, int64_t *tens_off)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int b = 0; b < 2 * n_bonds; ++b) bond_leg[b] = -1;
+    tens_off[0] = 0;
+    for (int v = 0; v < n_sites; ++v) {
+        int64_t n = 1;
+        for (int i = site_ptr[v]; i < site_ptr[v + 1]; ++i) {
+            const int b = site_bonds[i];
+            bond_leg[2 * b + (bond_site[2 * b] == v ? 0 : 1)] = i - site_ptr[v];
+            n *= bond_dim[b];
+        }
+        tens_off[v + 1] = tens_off[v] + n;
+    }
+    for (int v = 0; v < n_sites; ++v)
+        for (int i = site_ptr[v]; i < site_ptr[v + 1]; ++i) {
+            const int b = site_bonds[i];
+            const int s0 = bond_site[2 * b], s1 = bond_site[2 * b + 1];
+            if (s1 < 0) { inc_slot[i] = i; continue; }
+            const int u = (s0 == v) ? s1 : s0, side = (s0 == v) ? 1 : 0;
+            inc_slot[i] = site_ptr[u] + bond_leg[2 * b + side];
+        }
+}
+
+__global__ void noalloc_copy_kernel(const double *msg, const int32_t *final_buf, int n_sets, int64_t per_set,
+                                    double *out)
+{
+    const int64_t total = (int64_t)n_sets * per_set;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int set = (int)(i / per_set);
+        out[i] = msg[((int64_t)final_buf[set] * n_sets) * per_set + i];
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace pne
+
+extern "C" pne_status pne_bp_messages_noalloc(const pne_network *net, double tol, int32_t max_iter, double *msg_out,
+                                              int32_t *iters_out, double *residual_out, void *stream)
+{
+    using namespace pne;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!net || !msg_out || !net->bond_site || !net->bond_dim || !net->site_ptr || !net->site_bonds || !net->data ||
+        !net->data_off || !net->data_on_device || net->n_sites < 1 || net->n_bonds < 0 || net->n_batch < 1) {
+        set_error(nullptr, PNE_EINVAL, "pne_bp_messages_noalloc: malformed network (device data required)");
+        return PNE_EINVAL;
+    }
+    const int N = net->n_sites, M = net->n_bonds, B = net->n_batch;
+    const int L = net->site_ptr[N];
+    // host-side checks on the caller's arrays (nothing is allocated)
+    int tabA = 1, tabC = 1;
+    for (int b = 0; b < M; ++b) {
+        const int s0 = net->bond_site[2 * b], s1 = net->bond_site[2 * b + 1];
+        if (s0 < 0 || s0 >= N || s1 >= N || s1 < -1 || s0 == s1 || net->bond_dim[b] < 2 || net->bond_dim[b] > kMaxDim) {
+            set_error(nullptr, PNE_EINVAL, "pne_bp_messages_noalloc: invalid bond " + std::to_string(b));
+            return PNE_EINVAL;
+        }
+    }
+    if (net->site_ptr[0] != 0 || net->data_off[0] != 0) {
+        set_error(nullptr, PNE_EINVAL, "pne_bp_messages_noalloc: site_ptr[0] and data_off[0] must be 0");
+        return PNE_EINVAL;
+    }
+    for (int v = 0; v < N; ++v)
+        if (net->site_ptr[v + 1] < net->site_ptr[v] || net->site_ptr[v + 1] - net->site_ptr[v] > kMaxDeg) {
+            set_error(nullptr, PNE_EINVAL, "pne_bp_messages_noalloc: site degree must be in 0..6");
+            return PNE_EINVAL;
+        }
+    // every bond listed exactly once at each of its sites
+    for (int b = 0; b < M; ++b)
+        for (int side = 0; side < 2; ++side) {
+            const int x = net->bond_site[2 * b + side];
+            if (x < 0) continue;
+            int c = 0;
+            for (int i = net->site_ptr[x]; i < net->site_ptr[x + 1]; ++i) c += (net->site_bonds[i] == b);
+            if (c != 1) {
+                set_error(nullptr, PNE_EINVAL, "pne_bp_messages_noalloc: bond not listed once at each of its sites");
+                return PNE_EINVAL;
+            }
+        }
+    for (int v = 0; v < N; ++v) {
+        const int a = net->site_ptr[v], e = net->site_ptr[v + 1], k = e - a, h = k / 2;
+        if (k < 0 || k > kMaxDeg) { set_error(nullptr, PNE_EINVAL, "pne_bp_messages_noalloc: site degree must be in 0..6"); return PNE_EINVAL; }
+        int64_t size = 1;
+        int A = 1, C = 1;
+        for (int i = a; i < e; ++i) {
+            const int b = net->site_bonds[i];
+            if (b < 0 || b >= M || (i > a && net->site_bonds[i - 1] >= b) ||
+                (net->bond_site[2 * b] != v && net->bond_site[2 * b + 1] != v)) {
+                set_error(nullptr, PNE_EINVAL, "pne_bp_messages_noalloc: bad leg list");
+                return PNE_EINVAL;
+            }
+            size *= net->bond_dim[b];
+            if (i - a < h) A *= net->bond_dim[b]; else C *= net->bond_dim[b];
+        }
+        if (size > 4096 || net->data_off[v + 1] - net->data_off[v] != size) {
+            set_error(nullptr, PNE_EINVAL, "pne_bp_messages_noalloc: data_off inconsistent or tensor above 4096 entries");
+            return PNE_EINVAL;
+        }
+        tabA = tabA > A ? tabA : A;
+        tabC = tabC > C ? tabC : C;
+    }
+    // scratch layout
+    size_t off = 0;
+    const size_t o_bs = off; off = align256(off + (size_t)2 * M * 4 + 4);
+    const size_t o_bd = off; off = align256(off + (size_t)M * 4 + 4);
+    const size_t o_sp = off; off = align256(off + (size_t)(N + 1) * 4);
+    const size_t o_sb = off; off = align256(off + (size_t)L * 4 + 4);
+    const size_t o_bl = off; off = align256(off + (size_t)2 * M * 4 + 4);
+    const size_t o_is = off; off = align256(off + (size_t)L * 4 + 4);
+    const size_t o_to = off; off = align256(off + (size_t)(N + 1) * 8);
+    const size_t o_msg = off; off = align256(off + (size_t)2 * B * L * kMsgStride * 8);
+    const size_t o_zero = off;                       // everything below starts at zero each call
+    const size_t o_res = off; off = align256(off + (size_t)4 * B * 8);
+    const size_t o_rout = off; off = align256(off + (size_t)B * 8);
+    const size_t o_done = off; off = align256(off + (size_t)3 * B * 4);
+    const size_t o_flags = off; off = align256(off + 16 + 8);
+    if (off > PNE_NOALLOC_SCRATCH_BYTES) {
+        set_error(nullptr, PNE_EINVAL, "pne_bp_messages_noalloc: network needs " + std::to_string(off) +
+                                       " bytes of scratch, above PNE_NOALLOC_SCRATCH_BYTES");
+        return PNE_EINVAL;
+    }
+    const int per_warp = 2 * kMaxDeg * kMsgStride + 2 * tabA + 2 * tabC;
+    const size_t smem = (size_t)per_warp * kBpWarps * sizeof(double);
+    if (smem > 200 * 1024) { set_error(nullptr, PNE_EINVAL, "pne_bp_messages_noalloc: site tensor too large"); return PNE_EINVAL; }
+    // device address of the array, once per device
+    int dev = 0;
+    PNE_CUDA_TRY(nullptr, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) { set_error(nullptr, PNE_EINVAL, "device ordinal out of range"); return PNE_EINVAL; }
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        PNE_CUDA_TRY(nullptr, cudaGetSymbolAddress(&ptr, g_bp_noalloc_scratch));
+        g_noalloc_addr[dev] = ptr;
+    }
+    char *base = (char *)g_noalloc_addr[dev];
+    int32_t *bs = (int32_t *)(base + o_bs), *bd = (int32_t *)(base + o_bd), *sp = (int32_t *)(base + o_sp);
+    int32_t *sb = (int32_t *)(base + o_sb), *bl = (int32_t *)(base + o_bl), *is = (int32_t *)(base + o_is);
+    int64_t *to = (int64_t *)(base + o_to);
+    double *msg = (double *)(base + o_msg);
+    unsigned long long *res = (unsigned long long *)(base + o_res);
+    double *res_out = (double *)(base + o_rout);
+    int32_t *done = (int32_t *)(base + o_done), *iters = done + B, *finalb = iters + B;
+    int32_t *flags = (int32_t *)(base + o_flags);
+    unsigned int *bar = (unsigned int *)(flags + 4);
+    PNE_CUDA_TRY(nullptr, cudaMemcpyAsync(bs, net->bond_site, (size_t)2 * M * 4, cudaMemcpyHostToDevice, s));
+    PNE_CUDA_TRY(nullptr, cudaMemcpyAsync(bd, net->bond_dim, (size_t)M * 4, cudaMemcpyHostToDevice, s));
+    PNE_CUDA_TRY(nullptr, cudaMemcpyAsync(sp, net->site_ptr, (size_t)(N + 1) * 4, cudaMemcpyHostToDevice, s));
+    PNE_CUDA_TRY(nullptr, cudaMemcpyAsync(sb, net->site_bonds, (size_t)L * 4, cudaMemcpyHostToDevice, s));
+    PNE_CUDA_TRY(nullptr, cudaMemsetAsync(base + o_zero, 0, off - o_zero, s));
+    noalloc_tables_kernel<<<1, 1, 0, s>>>(N, M, bs, bd, sp, sb, bl, is, to);
+    PNE_CUDA_TRY(nullptr, cudaGetLastError());
+    int n_sm = 0;
+    PNE_CUDA_TRY(nullptr, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    bp_init_kernel<<<grid_for((int64_t)B * L, 256, n_sm), 256, 0, s>>>(msg, sp, sb, bd, N, L, B);
+    PNE_CUDA_TRY(nullptr, cudaGetLastError());
+    BPParams prm;
+    prm.n_sets = B; prm.n_sites = N; prm.n_legs = L;
+    prm.site_ptr = sp; prm.site_bonds = sb; prm.bond_dim = bd; prm.inc_slot = is;
+    prm.tens_off = to; prm.set_stride = net->data_off[N];
+    prm.T = net->data; prm.msg = msg;
+    prm.tol = (tol > 0) ? tol : 1e-13; prm.damping = 0.0; prm.max_iter = (max_iter > 0) ? max_iter : 10000;
+    prm.res = res; prm.done_it = done; prm.iters_out = iters; prm.res_out = res_out;
+    prm.final_buf = finalb; prm.flags = flags; prm.bar = bar;
+    prm.smem_per_warp = per_warp; prm.tabA = tabA; prm.tabC = tabC;
+    if (smem > 48 * 1024)
+        PNE_CUDA_TRY(nullptr, cudaFuncSetAttribute(bp_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PNE_CUDA_TRY(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bp_persistent_kernel, kBpWarps * 32, smem));
+    if (per_sm < 1) { set_error(nullptr, PNE_EINVAL, "BP kernel does not fit"); return PNE_EINVAL; }
+    const int64_t items = (int64_t)B * N;
+    int64_t want = (items + kBpWarps - 1) / kBpWarps, cap = (int64_t)per_sm * n_sm;
+    int nblocks = (int)(want < cap ? want : cap);
+    if (nblocks < 1) nblocks = 1;
+    void *args[] = {&prm};
+    PNE_CUDA_TRY(nullptr, cudaLaunchCooperativeKernel((void *)bp_persistent_kernel, dim3(nblocks),
+                                                       dim3(kBpWarps * 32), args, smem, s));
+    const int64_t per_set = (int64_t)L * kMsgStride;
+    noalloc_copy_kernel<<<grid_for((int64_t)B * per_set, 256, n_sm), 256, 0, s>>>(msg, finalb, B, per_set, msg_out);
+    PNE_CUDA_TRY(nullptr, cudaGetLastError());
+    int32_t hflags[2] = {0, 0};
+    PNE_CUDA_TRY(nullptr, cudaMemcpyAsync(hflags, flags, 8, cudaMemcpyDeviceToHost, s));
+    if (iters_out) PNE_CUDA_TRY(nullptr, cudaMemcpyAsync(iters_out, iters, (size_t)B * 4, cudaMemcpyDeviceToHost, s));
+    if (residual_out) PNE_CUDA_TRY(nullptr, cudaMemcpyAsync(residual_out, res_out, (size_t)B * 8, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(nullptr, cudaStreamSynchronize(s));
+    if (hflags[0]) { set_error(nullptr, PNE_ETIMEOUT, "grid barrier timed out in BP"); return PNE_ETIMEOUT; }
+    if (hflags[1]) { set_error(nullptr, PNE_EDEGENERATE, "zero BP message"); return PNE_EDEGENERATE; }
+    // convergence record through a fixed host buffer (no allocation)
+    int32_t chunk[256];
+    for (int b0 = 0; b0 < B; b0 += 256) {
+        const int nb = (B - b0 < 256) ? B - b0 : 256;
+        PNE_CUDA_TRY(nullptr, cudaMemcpy(chunk, iters + b0, (size_t)nb * 4, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < nb; ++i)
+            if (chunk[i] == 0) { set_error(nullptr, PNE_ENOCONV, "BP did not converge"); return PNE_ENOCONV; }
+    }
+    return PNE_OK;
+}

@@ -22,7 +22,7 @@ __all__ = [
     "pne_ctx_create", "pne_ctx_destroy", "pne_last_error", "pne_ctx_set_allocator",
     "pne_build_partition", "pne_partition_destroy", "pne_enumerate_terms", "pne_terms_destroy",
     "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_terms_export",
-    "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak",
+    "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak", "pne_bp_messages_noalloc",
     "Network", "PartitionOpts", "EnumOpts", "Result", "Context", "run", "network_struct",
 ]
 
@@ -127,6 +127,9 @@ def load_library():
     lib.pne_terms_n_results.restype = ctypes.c_int64
     lib.pne_terms_export.argtypes = [vp, vp, vp, ctypes.c_void_p, ctypes.c_void_p]
     lib.pne_terms_export.restype = ctypes.c_int
+    lib.pne_bp_messages_noalloc.argtypes = [ctypes.POINTER(Network), ctypes.c_double, ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, vp]
+    lib.pne_bp_messages_noalloc.restype = ctypes.c_int
     lib.pne_ctx_profile.argtypes = [vp, ctypes.c_int]
     lib.pne_ctx_profile.restype = ctypes.c_int
     lib.pne_ctx_profile_read.argtypes = [vp, ctypes.POINTER(ProfileEntry), ctypes.c_int]
@@ -146,7 +149,8 @@ def exported_symbols() -> list:
              "pne_build_partition", "pne_partition_destroy", "pne_enumerate_terms", "pne_terms_destroy",
              "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_terms_export",
     "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak",
-             "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak"]
+             "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak",
+             "pne_bp_messages_noalloc"]
     return [n for n in names if hasattr(lib, n)]
 
 
@@ -215,6 +219,19 @@ def pne_terms_export(ctx, terms, n_clusters, K, with_values=True, stream=None):
     _check(load_library().pne_terms_export(ctx, terms, stream, edges.ctypes.data,
                                            w.ctypes.data if w is not None else None), ctx)
     return edges[:n_clusters], (w[:, :n_clusters] if w is not None else None)
+
+
+def pne_bp_messages_noalloc(net: Network, msg_out_ptr, tol=1e-13, max_iter=10000, stream=None):
+    """Allocation-free BP (see include/pne.h): fixed-point messages written to
+    the caller's device buffer ``msg_out_ptr`` ([n_batch][n_legs][8] doubles).
+    Returns (iters, residuals) per tensor set."""
+    B = int(net.n_batch)
+    iters = np.zeros(B, dtype=np.int32)
+    res = np.zeros(B, dtype=np.float64)
+    st = load_library().pne_bp_messages_noalloc(ctypes.byref(net), float(tol), int(max_iter), ctypes.c_void_p(msg_out_ptr),
+                                                 iters.ctypes.data, res.ctypes.data, stream)
+    _check(st, ctypes.c_void_p(0))
+    return iters, res
 
 
 def pne_ctx_profile(ctx, enable=True):
