@@ -39,6 +39,12 @@ WORKLOADS = {
                    kind="ising2d", L=4, D=2, K=24, batch=32, mode=0, beta=0.40),
     "ising3d": dict(desc="3D Ising 8x8x8 open, D=2, beta in {0.20,0.2217,0.25}, K=8 LOOP",
                     kind="ising3d", L=8, D=2, K=8, batch=3, mode=0),
+    "batched": dict(desc="4096 independent 2D networks LxL, L~U{6..24}, D~U{2..6}, half random U[0,1)+0.1, "
+                         "half Ising beta~U[0.3,0.5] (D=2), seed 1234, K=8 LOOP, one persistent fused launch "
+                         "replayed from a CUDA graph", kind="batched", n=4096, K=8, mode=0),
+    "serve": dict(desc="served: Poisson arrivals mean 2000 req/s, seed 7; 1/2 AKLT norm networks LxL, L~U{8..32} "
+                       "(D=4), 1/2 3D random networks L^3, L~U{6..12}, D~U{2..4}, N(1,0.3^2); K~U{4..8}; "
+                       "continuous batching with memory admission", kind="serve", rate=2000.0, mode=0),
 }
 
 
@@ -150,6 +156,10 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, wl, rank, world)
+    if wl["kind"] == "batched":
+        return run_batched(args, wl, rank, world, local_rank)
+    if wl["kind"] == "serve":
+        return run_serve(args, wl, rank, world, local_rank)
 
     import torch
     import torch.distributed as dist
@@ -313,6 +323,201 @@ def main():
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batched(args, wl, rank, world, local_rank):
+    """cfg4: networks grouped by geometry; one partition and one enumeration
+    per group (enumeration is geometry-only and built once), one batch over all
+    groups.  A step re-runs every partition on its tensors (BP, gauge) and
+    replays the batch's graph (conversion, fused contraction + term sums,
+    per-order reduction, copy-back)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2512_10910_gb300 import pne
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    dtype = pne.DTYPES[args.dtype]
+    t0 = time.time()
+    work = I.batched_workload(wl["n"], 1234 + 1000003 * rank)
+    groups = {}
+    for kind, L, D, beta, net in work:
+        groups.setdefault((L, D), []).append(net)
+    ctx = pne.Context(local_rank)
+    parts, terms, datas, keep = [], [], [], []
+    for (L, D), nets in sorted(groups.items()):
+        g = nets[0]
+        flat = np.concatenate([n.flat_data()[0] for n in nets])
+        data = torch.from_numpy(flat).to(dev)
+        ns, kp = pne.network_struct(g, data=data, n_batch=len(nets))
+        p, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0), sh)
+        t, _, _ = pne.pne_enumerate_terms(ctx.h, p, pne.EnumOpts(wl["K"], wl["mode"], 1), sh)
+        parts.append(p); terms.append(t); datas.append(data); keep.append((ns, kp))
+    batch = pne.pne_batch_create(ctx.h, terms, dtype, None, sh)
+    wpb, bps, tuned = pne.pne_batch_config(batch)
+    setup_s = time.time() - t0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        for p, d in zip(parts, datas):
+            pne.pne_partition_update(ctx.h, p, d, None, sh)
+        return pne.pne_batch_run(ctx.h, batch, sh)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    pne.pne_ctx_profile(ctx.h, True)
+    total = 0.0
+    res = None
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True); e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res = step()
+        e.record(stream); e.synchronize()
+        total += a.elapsed_time(e)
+    prof = pne.pne_ctx_profile_read(ctx.h)
+    pne.pne_ctx_profile(ctx.h, False)
+    clk = clocks.stop()
+    if world > 1:
+        tt = torch.tensor([total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = float(tt.item())
+    ms = total / args.steps
+    n_terms = sum(r["n_terms"] for r in res)
+    n_clusters = sum(r["n_clusters"] for r in res)
+    fam, (launches, tot) = max(prof.items(), key=lambda kv: kv[1][1])
+    out = {"metric": "PNE terms contracted/sec", "value": n_terms * world / (ms * 1e-3), "unit": "terms/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+           "config": {"workload": wl["desc"], "networks": len(work), "geometry_groups": len(groups),
+                      "terms_per_step": n_terms, "clusters_per_step": n_clusters,
+                      "launch_shape": {"warps_per_block": wpb, "blocks_per_sm": bps, "tuned_ms": tuned},
+                      "setup_s": setup_s, "enumeration": "per geometry, built once at setup",
+                      "l2": "flushed between timed steps (256 MB write)"},
+           "gpu_launches": int(sum(v[0] for v in prof.values())),
+           "kernel_shares": {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()},
+           "kernel_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in prof.items()},
+           "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out))
+    pne.pne_batch_destroy(batch)
+    for t in terms:
+        pne.pne_terms_destroy(t)
+    for p in parts:
+        pne.pne_partition_destroy(p)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    del fam, launches, tot
+
+
+def serve_trace(n, rate, seed):
+    """Arrival times and request descriptors of the served workload."""
+    u = I.splitmix64_uniform(seed, 6 * n).reshape(n, 6)
+    gaps = -np.log(1.0 - u[:, 0]) / rate
+    t = np.cumsum(gaps)
+    reqs = []
+    for i in range(n):
+        K = 4 + min(4, int(u[i, 1] * 5))
+        if u[i, 2] < 0.5:
+            reqs.append(("aklt", 8 + min(24, int(u[i, 3] * 25)), 4, K, None))
+        else:
+            reqs.append(("rand3d", 6 + min(6, int(u[i, 3] * 7)), 2 + min(2, int(u[i, 4] * 3)), K,
+                         seed * 1000003 + i))
+    return t, reqs
+
+
+def run_serve(args, wl, rank, world, local_rank):
+    """cfg5: requests replayed in real time against the library's server.
+    Geometries (and their enumerations) are warmed once before the trace."""
+    import torch
+    from paper_2512_10910_gb300 import pne
+    torch.cuda.set_device(local_rank)
+    duration = max(0.5, args.steps / 10.0)            # --steps 20 -> a 2 s trace
+    n = int(wl["rate"] * duration)
+    t_arr, reqs = serve_trace(n, wl["rate"], 7 + rank)
+    geoms, flats = {}, {}
+
+    def build(kind, L, D, K, seed):
+        key = (kind, L, D)
+        if key not in geoms:
+            g = I.square_lattice(L, L, 4) if kind == "aklt" else I.cubic_lattice(L, L, L, D)
+            if kind == "aklt":
+                flats[key] = I.aklt_tensors(g).flat_data()[0]
+            geoms[key] = g
+        g = geoms[key]
+        if kind == "aklt":
+            flat = flats[key]
+        else:
+            size = int(sum(np.prod(g.leg_dims(v)) for v in range(g.n_sites))) if key not in flats else flats[key]
+            flats[key] = size
+            flat = I.splitmix64_normal(seed, size, 1.0, 0.3)     # the random_tensors layout, sites in order
+        return pne.network_struct(g, data=flat)
+
+    t0 = time.time()
+    structs = [build(*r) for r in reqs]
+    build_s = time.time() - t0
+    dtype = pne.DTYPES[args.dtype]
+    ctx = pne.Context(local_rank)
+    opts = pne.ServerOpts(64 << 30, 512, 6, 512, dtype, 0, 0)
+    srv = pne.pne_server_create(ctx.h, opts)
+    # warm the geometry cache: one request per distinct (geometry, K)
+    seen, warm = set(), []
+    for (ns, keep), r in zip(structs, reqs):
+        key = (r[0], r[1], r[2], r[3])
+        if key not in seen:
+            seen.add(key)
+            warm.append(pne.pne_server_submit(srv, ns, r[3]))
+    pne.pne_server_drain(srv)
+    for rid in warm:
+        pne.pne_server_poll(srv, rid)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ids = []
+    start = time.perf_counter()
+    for (ns, keep), r, ta in zip(structs, reqs, t_arr):
+        delay = ta - (time.perf_counter() - start)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(pne.pne_server_submit(srv, ns, r[3]))
+    pne.pne_server_drain(srv)
+    wall = time.perf_counter() - start
+    clk = clocks.stop()
+    lat, terms, batch, first, last = [], 0, [], None, None
+    for rid in ids:
+        st, res, info = pne.pne_server_poll(srv, rid)
+        if st != pne.PNE_OK:
+            continue
+        lat.append(info["t_done"] - info["t_arrival"])
+        terms += res["n_terms"]
+        batch.append(info["batch_size"])
+        first = info["t_arrival"] if first is None else min(first, info["t_arrival"])
+        last = info["t_done"] if last is None else max(last, info["t_done"])
+    peak, _ = pne.pne_server_stats(srv)
+    pne.pne_server_destroy(srv)
+    ctx.close()
+    lat = np.array(lat)
+    span = last - first
+    out = {"metric": "PNE terms contracted/sec", "value": terms / span, "unit": "terms/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * span, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+           "config": {"workload": wl["desc"], "requests": len(ids), "completed": int(len(lat)),
+                      "offered_rate_req_s": wl["rate"], "trace_s": float(t_arr[-1]),
+                      "served_req_s": len(lat) / span, "geometries_warmed": len(seen),
+                      "device_budget_bytes": int(opts.device_budget_bytes), "peak_admitted_bytes": peak,
+                      "input_build_s": build_s},
+           "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
+                          "mean": 1e3 * float(lat.mean()), "max": 1e3 * float(lat.max())},
+           "batch_size": {"mean": float(np.mean(batch)), "max": int(np.max(batch))},
+           "wall_s": wall, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out))
 
 
 def run_reference(args, wl, rank, world):

@@ -181,6 +181,91 @@ int64_t pne_terms_n_results(const pne_terms *t);
  * Clusters are listed grouped by size.  Synchronises `stream`. */
 pne_status pne_terms_export(pne_ctx *ctx, const pne_terms *t, void *stream, int32_t *edges, double *w);
 
+/* Re-run the partition of an existing handle on new tensors of the same
+ * geometry and batch size (BP, gauge, blocked tensors), reusing its device
+ * buffers, so that enumerations and batches built on the handle stay valid.
+ * `data` holds n_batch tensor sets laid out as in pne_network; host pointer,
+ * or device pointer when data_on_device != 0.  Synchronises `stream`. */
+pne_status pne_partition_update(pne_ctx *ctx, pne_partition *p, const double *data, int32_t data_on_device,
+                                const pne_partition_opts *opts, void *stream);
+
+/* ---- batched form: one persistent launch over many networks -------------- */
+
+/* A batch fuses the cluster contractions (pne_contract_terms) and the term
+ * sums (pne_sum) of many handles -- networks of different sizes and bond
+ * dimensions, each with its own partition -- into one persistent kernel that
+ * takes work from a single queue (Sec. II.D: every term can be evaluated in
+ * parallel).  Contraction items of a handle come before its sum items; a sum
+ * item waits (bounded) for its handle's contractions.  The launch sequence
+ * (dtype conversion, fused kernel, per-order reduction, copy of the results)
+ * is captured once in a CUDA graph and replayed by pne_batch_run. */
+typedef struct pne_batch pne_batch;
+
+typedef struct {
+    int32_t warps_per_block;   /* 0: autotune (with blocks_per_sm)            */
+    int32_t blocks_per_sm;     /* 0: autotune                                 */
+    int32_t use_graph;         /* capture and replay a CUDA graph             */
+} pne_batch_opts;
+
+/* terms[i] must be LOOP-mode handles whose partitions stay alive as long as
+ * the batch.  Autotuning times each candidate launch shape on this batch and
+ * caches the winner (in memory, and in the file named by the environment
+ * variable PNE_AUTOTUNE_CACHE when set).  Synchronises `stream`. */
+pne_status pne_batch_create(pne_ctx *ctx, int32_t n, pne_terms *const *terms, pne_dtype dtype,
+                            const pne_batch_opts *opts, void *stream, pne_batch **out);
+/* Replay: writes sum_i pne_terms_n_results(terms[i]) results, handle-major.
+ * Synchronises `stream`. */
+pne_status pne_batch_run(pne_ctx *ctx, pne_batch *b, void *stream, pne_result *out);
+int64_t pne_batch_n_results(const pne_batch *b);
+/* Chosen launch shape and its timed duration (ms) from the autotuner. */
+pne_status pne_batch_config(const pne_batch *b, int32_t *warps_per_block, int32_t *blocks_per_sm, double *tuned_ms);
+void pne_batch_destroy(pne_batch *b);
+
+/* ---- served form: continuous batching of requests ------------------------- */
+
+/* A server owns worker threads on the context's device.  Requests (one network,
+ * any size, bond dimension and order) are admitted in arrival order while the
+ * estimated device bytes of the admitted-but-unfinished requests stay within
+ * device_budget_bytes and their number within max_inflight.  Admitted
+ * requests are prepared concurrently (partition, enumeration -- the latter
+ * from the context's geometry cache when present) on n_prep_streams streams;
+ * a launcher merges every prepared request into the next fused persistent
+ * launch (see pne_batch_*) while later arrivals keep being prepared, so work
+ * of different requests overlaps on the device.  A request's result does not
+ * depend on which other requests share its launch.  Clusters, partitions and
+ * cluster values stay on the device until the request completes. */
+typedef struct pne_server pne_server;
+
+typedef struct {
+    uint64_t device_budget_bytes;   /* admission limit (0: 8 GiB)              */
+    int32_t max_inflight;           /* admitted, unfinished requests (0: 256)  */
+    int32_t n_prep_streams;         /* preparing threads/streams (0: 4)        */
+    int32_t max_batch;              /* requests per fused launch (0: 256)      */
+    int32_t dtype;                  /* pne_dtype of the cluster contractions   */
+    int32_t warps_per_block;        /* fused-launch shape (0: 4)               */
+    int32_t blocks_per_sm;          /* (0: 2)                                  */
+} pne_server_opts;
+
+typedef struct {
+    double t_arrival, t_admit, t_ready, t_done;  /* seconds since server start */
+    uint64_t device_bytes;                        /* admission estimate        */
+    int32_t batch_size;                           /* requests in its launch    */
+} pne_request_info;
+
+pne_status pne_server_create(pne_ctx *ctx, const pne_server_opts *opts, pne_server **out);
+/* Copies the network (host tensors; n_batch must be 1, no open indices) and
+ * queues it; returns at once with the request id. */
+pne_status pne_server_submit(pne_server *s, const pne_network *net, int32_t max_order, uint64_t *id);
+/* PNE_OK and the result when the request is done (its record is then
+ * released), PNE_EBUSY while it is queued or running, PNE_EINVAL for an
+ * unknown id; a request that failed returns its error status. */
+pne_status pne_server_poll(pne_server *s, uint64_t id, pne_result *out, pne_request_info *info);
+/* Blocks until every submitted request is done. */
+pne_status pne_server_drain(pne_server *s);
+/* Largest admitted estimate seen at once, and the server clock (seconds). */
+pne_status pne_server_stats(pne_server *s, uint64_t *peak_inflight_bytes, double *now);
+void pne_server_destroy(pne_server *s);
+
 /* ---- belief propagation without device allocation ------------------------ */
 
 /* The paper has no counterpart to this call; it exists for callers that cannot

@@ -107,16 +107,37 @@ __device__ void site_messages(const double *__restrict__ T, int k, const int *di
         u[a] = p;
     }
     __syncwarp();
-    for (int a = lane; a < A; a += 32) {
-        double s = 0.0;
-        const double *row = T + (int64_t)a * C;
-        for (int c = 0; c < C; ++c) s = fma(row[c], w[c], s);
-        x1[a] = s;
+    // X1[a] = sum_c T[a][c] w[c]: lpr lanes share a row (consecutive lanes),
+    // each summing a strided part of it, then a fixed shuffle tree
+    {
+        int lpr = 1;
+        while (lpr * 2 * A <= 32) lpr *= 2;
+        const int rows_per_pass = 32 / lpr, sub = lane % lpr;
+        for (int a0 = 0; a0 < A; a0 += rows_per_pass) {
+            const int a = a0 + lane / lpr;
+            double s = 0.0;
+            if (a < A) {
+                const double *row = T + (int64_t)a * C;
+                for (int c = sub; c < C; c += lpr) s = fma(row[c], w[c], s);
+            }
+            for (int off = lpr / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (a < A && sub == 0) x1[a] = s;
+        }
     }
-    for (int c = lane; c < C; c += 32) {
-        double s = 0.0;
-        for (int a = 0; a < A; ++a) s = fma(u[a], T[(int64_t)a * C + c], s);
-        x2[c] = s;
+    // X2[c] = sum_a u[a] T[a][c]: lpc lanes share a column, split over a
+    {
+        int lpc = 1;
+        while (lpc * 2 * C <= 32) lpc *= 2;
+        const int cols_per_pass = 32 / lpc;
+        const int sub = lane / cols_per_pass;           // lanes of one column are cols_per_pass apart
+        for (int c0 = 0; c0 < C; c0 += cols_per_pass) {
+            const int c = c0 + lane % cols_per_pass;
+            double s = 0.0;
+            if (c < C)
+                for (int a = sub; a < A; a += lpc) s = fma(u[a], T[(int64_t)a * C + c], s);
+            for (int off = 16; off >= cols_per_pass; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (c < C && sub == 0) x2[c] = s;
+        }
     }
     __syncwarp();
     // outputs: one (leg, value) pair per lane
@@ -206,36 +227,46 @@ __global__ void __launch_bounds__(kBpWarps * 32) bp_persistent_kernel(BPParams p
             __syncwarp();
             const double *T = p.T + set * p.set_stride + p.tens_off[v];
             site_messages(T, k, dims, in, u, w, x1, x2, out, lane);
+            // normalise every message in parallel: lane = (leg j, entry a), 8 lanes per leg
             double r = 0.0;
-            if (lane < k) {
-                const int d = dims[lane];
-                double *o = out + lane * kMsgStride;
-                const double *old = msrc + (int64_t)(l0 + lane) * kMsgStride;
-                double nrm = 0.0, big = -1.0;
-                int arg = 0;
-                for (int a = 0; a < d; ++a) nrm = fma(o[a], o[a], nrm);
-                nrm = sqrt(nrm);
-                if (!(nrm > 0.0)) { atomicExch(p.flags + 1, 1); nrm = 1.0; }
-                for (int a = 0; a < d; ++a) {
-                    double m = fabs(o[a]);
-                    if (m > big) { big = m; arg = a; }
+            for (int j0 = 0; j0 < k; j0 += 4) {
+                const int j = j0 + (lane >> 3), a = lane & 7;
+                const bool live = (j < k) && (a < dims[j < k ? j : 0]);
+                const double o = live ? out[j * kMsgStride + a] : 0.0;
+                const double old = live ? msrc[(int64_t)(l0 + j) * kMsgStride + a] : 0.0;
+                double n2 = o * o;
+                for (int off = 4; off > 0; off >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+                // sign: the entry of largest magnitude, first index on ties
+                double big = live ? fabs(o) : -1.0;
+                int arg = a;
+                for (int off = 4; off > 0; off >>= 1) {
+                    const double ob = __shfl_xor_sync(0xffffffffu, big, off);
+                    const int oa = __shfl_xor_sync(0xffffffffu, arg, off);
+                    if (ob > big || (ob == big && oa < arg)) { big = ob; arg = oa; }
                 }
-                double sg = (o[arg] < 0.0) ? -1.0 : 1.0;
-                double f = sg / nrm;
+                const double oarg = __shfl_sync(0xffffffffu, o, (lane & ~7) | arg);
+                double nrm = sqrt(n2);
+                if (j < k && !(nrm > 0.0)) { atomicExch(p.flags + 1, 1); nrm = 1.0; }
+                double nv = (oarg < 0.0 ? -o : o) / nrm;
                 if (p.damping > 0.0) {
-                    double n2 = 0.0;
-                    for (int a = 0; a < d; ++a) { o[a] = (1.0 - p.damping) * (o[a] * f) + p.damping * old[a]; n2 = fma(o[a], o[a], n2); }
-                    n2 = sqrt(n2);
-                    if (!(n2 > 0.0)) { atomicExch(p.flags + 1, 1); n2 = 1.0; }
-                    big = -1.0; arg = 0;
-                    for (int a = 0; a < d; ++a) { double m = fabs(o[a]); if (m > big) { big = m; arg = a; } }
-                    f = ((o[arg] < 0.0) ? -1.0 : 1.0) / n2;
+                    double m = (1.0 - p.damping) * nv + p.damping * old;
+                    double m2 = live ? m * m : 0.0;
+                    for (int off = 4; off > 0; off >>= 1) m2 += __shfl_xor_sync(0xffffffffu, m2, off);
+                    double bg = live ? fabs(m) : -1.0;
+                    int ag = a;
+                    for (int off = 4; off > 0; off >>= 1) {
+                        const double ob = __shfl_xor_sync(0xffffffffu, bg, off);
+                        const int oa = __shfl_xor_sync(0xffffffffu, ag, off);
+                        if (ob > bg || (ob == bg && oa < ag)) { bg = ob; ag = oa; }
+                    }
+                    const double marg = __shfl_sync(0xffffffffu, m, (lane & ~7) | ag);
+                    double n3 = sqrt(m2);
+                    if (j < k && !(n3 > 0.0)) { atomicExch(p.flags + 1, 1); n3 = 1.0; }
+                    nv = (marg < 0.0 ? -m : m) / n3;
                 }
-                double *dm = mdst + (int64_t)(l0 + lane) * kMsgStride;
-                for (int a = 0; a < d; ++a) {
-                    double nv = o[a] * f;
-                    r = fmax(r, fabs(nv - old[a]));
-                    dm[a] = nv;
+                if (live) {
+                    mdst[(int64_t)(l0 + j) * kMsgStride + a] = nv;
+                    r = fmax(r, fabs(nv - old));
                 }
             }
             for (int off = 16; off > 0; off >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, off));
@@ -645,6 +676,22 @@ pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t 
     }
     PNE_CUDA_TRY(ctx, cudaGetLastError());
     dev_free(ctx, tab, s);
+    return PNE_OK;
+}
+
+// conversion only, into buffers that already exist (safe inside stream capture)
+pne_status launch_convert_only(pne_ctx *ctx, const pne_partition *p, int dtype, cudaStream_t s)
+{
+    if (dtype == PNE_F64) return PNE_OK;
+    const int64_t n = (int64_t)p->n_members * p->closed.tens_off[p->closed.n_sites];
+    ProfScope ps(ctx, s, "convert");
+    if (dtype == PNE_BF16)
+        convert_kernel<<<grid_for(n, 256, ctx->n_sm), 256, 0, s>>>((const double *)p->Mb.ptr, n, dtype, nullptr,
+                                                                   (__nv_bfloat16 *)p->Mb16.ptr);
+    else
+        convert_kernel<<<grid_for(n, 256, ctx->n_sm), 256, 0, s>>>((const double *)p->Mb.ptr, n, dtype,
+                                                                   (float *)p->Mb32.ptr, nullptr);
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
     return PNE_OK;
 }
 

@@ -1007,3 +1007,400 @@ pne_status launch_all_mode(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s
 }
 
 }  // namespace pne
+
+
+// ====================================================================== batched form
+namespace pne {
+namespace {
+
+struct BatchGroup {
+    ContractParams cp;
+    int shaped;
+    const int32_t *perm, *shape_of, *plans, *plan_steps;
+    const double *vac;
+    const int32_t *lvl_idx[8];
+    int lvl_m[8];
+    int K;
+    int n_desc;
+    int64_t desc_off, part_off, out_off;
+};
+
+struct BatchItem {
+    int32_t g, kind, member, aux;   // kind 0: 32 clusters; kind 1: one sum descriptor (aux)
+    int64_t start;
+};
+
+constexpr long long kBatchSpinLimit = 1ll << 26;
+
+template <typename T, typename L, int R>
+__device__ void lane_contract(const BatchGroup &G, int64_t i, int b, T *X0, T *X1)
+{
+    const ContractParams &P = G.cp;
+    if (!G.shaped) {                                  // bond dimension 2: a plain product
+        const int64_t c = i;
+        const int32_t *E = P.cl_edges + c * P.width;
+        const int32_t *V = P.cl_verts + c * P.vwidth;
+        T prod = (T)1;
+        int expo = 0, nz = 0;
+        double zs = 1.0;
+        for (int j = 0; j < P.vwidth && V[j] >= 0; ++j) {
+            const int x = V[j];
+            int mask = 0;
+            for (int k = 0; k < P.width && E[k] >= 0; ++k) {
+                const int e = E[k];
+                if (P.bond_site[2 * e] == x) mask |= 1 << P.bond_leg[2 * e];
+                if (P.bond_site[2 * e + 1] == x) mask |= 1 << P.bond_leg[2 * e + 1];
+            }
+            prod *= (T)L::get(P.M, (int64_t)b * P.stride + P.tens_off[x] + P.blk_off[x * kBlkStride + mask]);
+            if (prod != (T)0) { int e; frexp((double)prod, &e); prod *= (T)pow2(-e); expo += e; }
+            if (P.zero[(int64_t)b * P.n_sites + x]) { ++nz; zs *= P.scale[(int64_t)b * P.n_sites + x]; }
+        }
+        P.w[(int64_t)b * P.n_clusters + c] = ldexp((double)prod, expo) * zs;
+        P.nzc[(int64_t)b * P.n_clusters + c] = nz;
+        return;
+    }
+    const int64_t c = G.perm[i];
+    const int sh = G.shape_of[c];
+    const int *plan = G.plans + (int64_t)sh * kPlanInts;
+    const int nsteps = G.plan_steps[sh];
+    const int32_t *V = P.cl_verts + c * P.vwidth;
+    T *X = X0, *Y = X1;
+    X[0] = (T)1;
+    int expo = 0, nz = 0;
+    double zs = 1.0;
+    for (int t = 0; t < nsteps; ++t) {
+        const int *st = plan + t * kStepInts;
+        const int mask = st[1], nF = st[2], nC = st[3], outsz = st[4], closz = st[5];
+        const int site = V[st[6]];
+        const int *dimsF = st + 8, *sxF = dimsF + kMaxFront, *smF = sxF + kMaxFront;
+        const int *dimsC = smF + kMaxFront, *sxC = dimsC + kMaxClose, *smC = sxC + kMaxClose;
+        const int64_t mbase = (int64_t)b * P.stride + P.tens_off[site] + P.blk_off[site * kBlkStride + mask];
+        T mx = (T)0;
+        for (int o = 0; o < outsz; ++o) {
+            int r = o, xb = 0, mb = 0;
+            for (int q = nF - 1; q >= 0; --q) { const int d = r % dimsF[q]; r /= dimsF[q]; xb += d * sxF[q]; mb += d * smF[q]; }
+            T acc = (T)0;
+            for (int cc = 0; cc < closz; ++cc) {
+                int rc = cc, xi = xb, mi = mb;
+                for (int q = nC - 1; q >= 0; --q) { const int d = rc % dimsC[q]; rc /= dimsC[q]; xi += d * sxC[q]; mi += d * smC[q]; }
+                acc = fma(rnd<R>(X[xi * 32]), (T)L::get(P.M, mbase + mi), acc);
+            }
+            Y[o * 32] = acc;
+            mx = fmax(mx, fabs(acc));
+        }
+        if (mx > (T)0) {
+            int e;
+            frexp((double)mx, &e);
+            const T sc = (T)pow2(-e);
+            for (int o = 0; o < outsz; ++o) Y[o * 32] *= sc;
+            expo += e;
+        }
+        T *tmp = X; X = Y; Y = tmp;
+        if (P.zero[(int64_t)b * P.n_sites + site]) { ++nz; zs *= P.scale[(int64_t)b * P.n_sites + site]; }
+    }
+    P.w[(int64_t)b * P.n_clusters + c] = ldexp((double)X[0], expo) * zs;
+    P.nzc[(int64_t)b * P.n_clusters + c] = nz;
+}
+
+// One persistent launch: warps take items from one queue in order.  A sum item
+// of handle g waits until every contraction item of g has been counted done;
+// those items were taken earlier by running warps, so the wait ends.  It is
+// bounded anyway: on timeout status[0] is set and the warp moves on.
+template <typename T, typename L, int R>
+__global__ void fused_batch_kernel(const BatchGroup *groups, const BatchItem *items, int64_t n_items,
+                                   const SumDesc *descs, double *partials, unsigned long long *next,
+                                   unsigned int *done, const unsigned int *need, int xmax, int32_t *status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    T *X0 = (T *)smem_raw + (int64_t)wib * 2 * xmax * 32 + lane;
+    T *X1 = X0 + (int64_t)xmax * 32;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(next, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= (unsigned long long)n_items) break;
+        const BatchItem wi = items[it];
+        const BatchGroup &G = groups[wi.g];
+        if (wi.kind == 0) {
+            const int64_t i = wi.start + lane;
+            if (i < G.cp.n_clusters) lane_contract<T, L, R>(G, i, wi.member, X0, X1);
+            __syncwarp();
+            if (lane == 0) { __threadfence(); atomicAdd(done + wi.g, 1u); }
+        } else {
+            if (lane == 0) {
+                long long spins = 0;
+                while (*((volatile unsigned int *)(done + wi.g)) < need[wi.g]) {
+                    if (++spins > kBatchSpinLimit) { atomicExch(status + 1, 1); break; }
+                    __nanosleep(100);
+                }
+                __threadfence();
+            }
+            __syncwarp();
+            const SumDesc d = descs[G.desc_off + wi.aux];
+            const int b = wi.member;
+            const double *w = G.cp.w + (int64_t)b * G.cp.n_clusters;
+            const int32_t *nzc = G.cp.nzc + (int64_t)b * G.cp.n_clusters;
+            const int nzero = (int)G.vac[3 * b + 2];
+            double sv = 0.0, av = 0.0;
+            if (d.level == 0) {
+                for (int64_t i = d.begin + lane; i < d.end; i += 32) {
+                    const double v = (nzc[i] == nzero) ? w[i] : 0.0;
+                    sv += v; av += fabs(v);
+                }
+            } else {
+                const int m = G.lvl_m[d.level - 1];
+                const int32_t *idx = G.lvl_idx[d.level - 1];
+                for (int64_t i = d.begin + lane; i < d.end; i += 32) {
+                    const int32_t *tp = idx + i * m;
+                    double v = 1.0;
+                    int z = 0;
+                    for (int q = 0; q < m; ++q) { v *= w[tp[q]]; z += nzc[tp[q]]; }
+                    if (z != nzero) v = 0.0;
+                    sv += v; av += fabs(v);
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                sv += __shfl_xor_sync(0xffffffffu, sv, off);
+                av += __shfl_xor_sync(0xffffffffu, av, off);
+            }
+            if (lane == 0) {
+                double *p = partials + G.part_off + ((int64_t)b * G.n_desc + wi.aux) * 2;
+                p[0] = sv; p[1] = av;
+            }
+        }
+    }
+}
+
+__global__ void batch_finalize_kernel(const BatchGroup *groups, int G, const int64_t *fin_start,
+                                      const SumDesc *descs, const double *partials, double *out)
+{
+    const int64_t total = fin_start[G];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = G;
+        while (hi - lo > 1) { const int mid = (lo + hi) / 2; if (fin_start[mid] <= i) lo = mid; else hi = mid; }
+        const BatchGroup &g = groups[lo];
+        const int64_t r = i - fin_start[lo];
+        const int b = (int)(r / (g.K + 1)), k = (int)(r % (g.K + 1));
+        double sv = 0.0, av = 0.0;
+        for (int d = 0; d < g.n_desc; ++d)
+            if (descs[g.desc_off + d].order == k) {
+                const double *p = partials + g.part_off + ((int64_t)b * g.n_desc + d) * 2;
+                sv += p[0]; av += p[1];
+            }
+        double *o = out + g.out_off + (int64_t)b * ((g.K + 1) * 2 + 3);
+        o[2 * k] = sv;
+        o[2 * k + 1] = av;
+        if (k == 0) { o[(g.K + 1) * 2] = g.vac[3 * b]; o[(g.K + 1) * 2 + 1] = g.vac[3 * b + 1]; o[(g.K + 1) * 2 + 2] = g.vac[3 * b + 2]; }
+    }
+}
+
+}  // namespace
+
+// counters block: next item (u64) | done[G] (u32) | need[G] (u32) | status[4] (i32, 16-aligned)
+size_t status_offset(int G) { return ((size_t)8 + (size_t)8 * G + 15) & ~(size_t)15; }
+
+struct BatchPlan {
+    int dtype = 0, G = 0, xmax = 1;
+    int64_t n_items = 0, n_desc = 0, n_partials = 0, n_fin = 0, out_doubles = 0;
+    std::vector<pne_terms *> terms;
+    std::vector<int64_t> out_off;
+    DevBuf groups, items, descs, partials, fin_start, counters, d_out;
+    double *h_out = nullptr;
+    size_t smem_per_warp = 0;
+};
+
+double *batch_host_out(BatchPlan *bp) { return bp->h_out; }
+const std::vector<int64_t> &batch_out_offsets(BatchPlan *bp) { return bp->out_off; }
+
+int32_t batch_status_host(BatchPlan *bp)
+{
+    int32_t st[2] = {0, 0};
+    cudaMemcpy(st, (char *)bp->counters.ptr + status_offset(bp->G), 8, cudaMemcpyDeviceToHost);
+    return st[0] | st[1];
+}
+
+pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms, int dtype, cudaStream_t s,
+                             BatchPlan **out)
+{
+    BatchPlan *bp = new BatchPlan();
+    bp->dtype = dtype;
+    bp->terms = terms;
+    bp->G = (int)terms.size();
+    std::vector<BatchGroup> groups(bp->G);
+    std::vector<BatchItem> items;
+    std::vector<SumDesc> descs;
+    std::vector<int64_t> fin_start(bp->G + 1, 0);
+    std::vector<unsigned int> need(bp->G, 0);
+    std::vector<BatchItem> sum_items;
+    int64_t part_off = 0, out_off = 0;
+    pne_status st;
+    for (int g = 0; g < bp->G; ++g) {
+        pne_terms *t = terms[g];
+        const pne_partition *p = t->part;
+        const EnumRecord &rec = *t->rec;
+        if (t->mode != PNE_MODE_LOOP) { delete bp; set_error(ctx, PNE_EINVAL, "batches take LOOP-mode handles"); return PNE_EINVAL; }
+        const bool q1 = all_dims_two(p->closed);
+        if (!q1 && !rec.shaped && rec.n_clusters > 0) {
+            delete bp; set_error(ctx, PNE_EINVAL, "a cluster exceeds the batched kernel's limits"); return PNE_EINVAL;
+        }
+        if ((st = launch_convert(ctx, const_cast<pne_partition *>(p), dtype, s))) { delete bp; return st; }
+        BatchGroup &G = groups[g];
+        ContractParams &cp = G.cp;
+        cp.n_clusters = (int64_t)rec.n_clusters; cp.n_members = p->n_members; cp.n_sites = p->closed.n_sites;
+        cp.width = rec.width; cp.vwidth = rec.vwidth;
+        cp.cl_edges = (const int32_t *)rec.cl_edges.ptr; cp.cl_verts = (const int32_t *)rec.cl_verts.ptr;
+        cp.cl_size = (const int32_t *)rec.cl_size.ptr;
+        cp.bond_site = p->closed.d_bond_site; cp.bond_dim = p->closed.d_bond_dim; cp.bond_leg = p->closed.d_bond_leg;
+        cp.blk_off = p->closed.d_blk_off; cp.tens_off = p->closed.d_tens_off; cp.stride = p->closed.tens_off[p->closed.n_sites];
+        cp.M = dtype == PNE_F64 ? p->Mb.ptr : (dtype == PNE_BF16 ? p->Mb16.ptr : p->Mb32.ptr);
+        cp.scale = (const double *)p->site_scale.ptr; cp.zero = (const int8_t *)p->site_zero.ptr;
+        cp.w = (double *)t->w.ptr; cp.nzc = (int32_t *)t->nzc.ptr; cp.status = (int32_t *)t->status.ptr;
+        G.shaped = (!q1 && rec.shaped) ? 1 : 0;
+        G.perm = (const int32_t *)rec.perm.ptr; G.shape_of = (const int32_t *)rec.shape_of.ptr;
+        G.plans = (const int32_t *)rec.plans.ptr; G.plan_steps = (const int32_t *)rec.plan_steps.ptr;
+        G.vac = (const double *)p->vac.ptr;
+        for (int l = 0; l < 8; ++l) { G.lvl_idx[l] = nullptr; G.lvl_m[l] = 0; }
+        if (rec.levels.size() > 8) { delete bp; set_error(ctx, PNE_EOVERFLOW, "too many tuple levels"); return PNE_EOVERFLOW; }
+        for (size_t l = 0; l < rec.levels.size(); ++l) { G.lvl_idx[l] = (const int32_t *)rec.levels[l].idx.ptr; G.lvl_m[l] = rec.levels[l].m; }
+        G.K = t->K;
+        if (G.shaped) bp->xmax = std::max(bp->xmax, rec.max_out);
+        // descriptors of this handle
+        G.desc_off = (int64_t)descs.size();
+        for (int k = 1; k <= t->K; ++k)
+            for (int64_t b0 = rec.size_start[k]; b0 < rec.size_start[k + 1]; b0 += kSumChunk)
+                descs.push_back({0, k, b0, std::min<int64_t>(b0 + kSumChunk, rec.size_start[k + 1])});
+        for (size_t l = 0; l < rec.levels.size(); ++l)
+            for (int k = 0; k <= t->K; ++k)
+                for (int64_t b0 = rec.levels[l].order_start[k]; b0 < rec.levels[l].order_start[k + 1]; b0 += kSumChunk)
+                    descs.push_back({(int32_t)l + 1, k, b0, std::min<int64_t>(b0 + kSumChunk, rec.levels[l].order_start[k + 1])});
+        G.n_desc = (int)((int64_t)descs.size() - G.desc_off);
+        G.part_off = part_off;
+        part_off += (int64_t)p->n_members * G.n_desc * 2;
+        G.out_off = out_off;
+        bp->out_off.push_back(out_off);
+        out_off += (int64_t)p->n_members * ((t->K + 1) * 2 + 3);
+        fin_start[g + 1] = fin_start[g] + (int64_t)p->n_members * (t->K + 1);
+        // items: contraction chunks of 32 clusters, then (later) the sums
+        const int64_t chunks = (cp.n_clusters + 31) / 32;
+        for (int b = 0; b < p->n_members; ++b)
+            for (int64_t c = 0; c < chunks; ++c) items.push_back({g, 0, b, 0, c * 32});
+        need[g] = (unsigned int)(chunks * p->n_members);
+        for (int b = 0; b < p->n_members; ++b)
+            for (int d = 0; d < G.n_desc; ++d) sum_items.push_back({g, 1, b, d, 0});
+    }
+    items.insert(items.end(), sum_items.begin(), sum_items.end());
+    bp->n_items = (int64_t)items.size();
+    bp->n_desc = (int64_t)descs.size();
+    bp->n_partials = part_off;
+    bp->out_doubles = out_off;
+    bp->n_fin = fin_start[bp->G];
+    // counters: next (u64), done[G] (u32), need[G] (u32), status[2] (i32, 16-aligned)
+    const size_t cnt_bytes = status_offset(bp->G) + 16;
+    if ((st = dev_alloc(ctx, bp->groups, groups.size() * sizeof(BatchGroup), s)) ||
+        (st = dev_alloc(ctx, bp->items, std::max<size_t>(items.size(), 1) * sizeof(BatchItem), s)) ||
+        (st = dev_alloc(ctx, bp->descs, std::max<size_t>(descs.size(), 1) * sizeof(SumDesc), s)) ||
+        (st = dev_alloc(ctx, bp->partials, std::max<int64_t>(part_off, 1) * 8, s)) ||
+        (st = dev_alloc(ctx, bp->fin_start, fin_start.size() * 8, s)) ||
+        (st = dev_alloc(ctx, bp->counters, cnt_bytes, s)) ||
+        (st = dev_alloc(ctx, bp->d_out, std::max<int64_t>(out_off, 1) * 8, s))) {
+        batch_plan_destroy(ctx, bp);
+        return st;
+    }
+    PNE_CUDA_TRY(ctx, cudaMallocHost((void **)&bp->h_out, std::max<int64_t>(out_off, 1) * 8));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->groups.ptr, groups.data(), groups.size() * sizeof(BatchGroup), cudaMemcpyHostToDevice, s));
+    if (!items.empty()) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->items.ptr, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s));
+    if (!descs.empty()) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->descs.ptr, descs.data(), descs.size() * sizeof(SumDesc), cudaMemcpyHostToDevice, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->fin_start.ptr, fin_start.data(), fin_start.size() * 8, cudaMemcpyHostToDevice, s));
+    // need[] sits after next and done[]
+    char *cb = (char *)bp->counters.ptr;
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(cb + 8 + (size_t)bp->G * 4, need.data(), (size_t)bp->G * 4, cudaMemcpyHostToDevice, s));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    const size_t elem = (dtype == PNE_F64) ? 8 : 4;
+    bp->smem_per_warp = 2 * (size_t)bp->xmax * 32 * elem;
+    *out = bp;
+    return PNE_OK;
+}
+
+namespace {
+template <typename T, typename L, int R>
+pne_status launch_fused(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStream_t s)
+{
+    auto kern = fused_batch_kernel<T, L, R>;
+    const size_t smem = bp->smem_per_warp * wpb;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    char *cb = (char *)bp->counters.ptr;
+    unsigned long long *next = (unsigned long long *)cb;
+    unsigned int *done = (unsigned int *)(cb + 8);
+    const unsigned int *need = (const unsigned int *)(cb + 8 + (size_t)bp->G * 4);
+    int32_t *status = (int32_t *)(cb + status_offset(bp->G));
+    kern<<<bps * ctx->n_sm, wpb * 32, smem, s>>>((const BatchGroup *)bp->groups.ptr, (const BatchItem *)bp->items.ptr,
+                                                 bp->n_items, (const SumDesc *)bp->descs.ptr, (double *)bp->partials.ptr,
+                                                 next, done, need, bp->xmax, status);
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    return PNE_OK;
+}
+}  // namespace
+
+int batch_max_blocks_per_sm(BatchPlan *bp, int wpb)
+{
+    int n = 0;
+    const size_t smem = bp->smem_per_warp * wpb;
+    if (smem > 200 * 1024) return 0;
+    cudaError_t e;
+    if (bp->dtype == PNE_F64) {
+        cudaFuncSetAttribute(fused_batch_kernel<double, Load<double>, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_batch_kernel<double, Load<double>, 0>, wpb * 32, smem);
+    } else if (bp->dtype == PNE_BF16) {
+        cudaFuncSetAttribute(fused_batch_kernel<float, LoadBF16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_batch_kernel<float, LoadBF16, 2>, wpb * 32, smem);
+    } else {
+        cudaFuncSetAttribute(fused_batch_kernel<float, Load<float>, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_batch_kernel<float, Load<float>, 0>, wpb * 32, smem);
+    }
+    return e == cudaSuccess ? n : 0;
+}
+
+pne_status batch_enqueue(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStream_t s)
+{
+    pne_status st;
+    // conversions of updated partitions (each partition once)
+    std::vector<const pne_partition *> seen;
+    for (pne_terms *t : bp->terms) {
+        if (std::find(seen.begin(), seen.end(), t->part) != seen.end()) continue;
+        seen.push_back(t->part);
+        if ((st = launch_convert_only(ctx, t->part, bp->dtype, s))) return st;
+    }
+    char *cb = (char *)bp->counters.ptr;
+    PNE_CUDA_TRY(ctx, cudaMemsetAsync(cb, 0, 8 + (size_t)bp->G * 4, s));
+    PNE_CUDA_TRY(ctx, cudaMemsetAsync(cb + status_offset(bp->G), 0, 16, s));
+    {
+        ProfScope ps(ctx, s, "batch_fused");
+        if (bp->dtype == PNE_F64) st = launch_fused<double, Load<double>, 0>(ctx, bp, wpb, bps, s);
+        else if (bp->dtype == PNE_BF16) st = launch_fused<float, LoadBF16, 2>(ctx, bp, wpb, bps, s);
+        else if (bp->dtype == PNE_TF32) st = launch_fused<float, Load<float>, 1>(ctx, bp, wpb, bps, s);
+        else st = launch_fused<float, Load<float>, 0>(ctx, bp, wpb, bps, s);
+        if (st) return st;
+    }
+    {
+        ProfScope ps(ctx, s, "batch_finalize");
+        batch_finalize_kernel<<<grid_for(bp->n_fin, 128, ctx->n_sm), 128, 0, s>>>(
+            (const BatchGroup *)bp->groups.ptr, bp->G, (const int64_t *)bp->fin_start.ptr, (const SumDesc *)bp->descs.ptr,
+            (const double *)bp->partials.ptr, (double *)bp->d_out.ptr);
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->h_out, bp->d_out.ptr, std::max<int64_t>(bp->out_doubles, 1) * 8,
+                                      cudaMemcpyDeviceToHost, s));
+    return PNE_OK;
+}
+
+void batch_plan_destroy(pne_ctx *ctx, BatchPlan *bp)
+{
+    if (!bp) return;
+    DevBuf *bufs[] = {&bp->groups, &bp->items, &bp->descs, &bp->partials, &bp->fin_start, &bp->counters, &bp->d_out};
+    for (DevBuf *b : bufs) dev_free(ctx, *b, nullptr);
+    if (bp->h_out) cudaFreeHost(bp->h_out);
+    delete bp;
+}
+
+}  // namespace pne

@@ -8,6 +8,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <string>
@@ -57,6 +59,7 @@ void dev_free(pne_ctx *ctx, DevBuf &b, cudaStream_t s)
 ProfScope::ProfScope(pne_ctx *c, cudaStream_t st, const char *n) : ctx(c), s(st), name(n)
 {
     if (!ctx || !ctx->prof.on) return;
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
     auto take = [&]() {
         cudaEvent_t e;
         if (!ctx->prof.pool.empty()) { e = ctx->prof.pool.back(); ctx->prof.pool.pop_back(); }
@@ -72,6 +75,7 @@ ProfScope::~ProfScope()
 {
     if (!a) return;
     cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
     ctx->prof.pending.push_back({name, a, b});
 }
 
@@ -217,6 +221,58 @@ pne_status validate(pne_ctx *ctx, const pne_network *n)
 double gamma_n(int n, double u) { return (n * u) / (1.0 - n * u); }
 
 }  // namespace
+
+void finalize_result(pne_result &r, int K, int mode, int dtype, const double *c, const double *abs_c,
+                     const double *vac, uint64_t n_terms, uint64_t n_clusters, int bp_iters, double bp_residual)
+{
+    static const double unit[4] = {0x1p-53, 0x1p-24, 0x1p-11, 0x1p-8};
+    const double u = unit[dtype < 0 ? 0 : dtype];
+    // first-order rounding count per term: every site factor and every
+    // intermediate of a cluster contraction is rounded once in the working
+    // dtype (at most 2 (K + 1) roundings along a term's product)
+    const int nops = 2 * (K + 1);
+    std::memset(&r, 0, sizeof r);
+    const double lz = vac[0], sz = vac[1];
+    const int nzero = (int)vac[2];
+    r.n_orders = K + 1;
+    for (int k = 0; k <= K; ++k) { r.c[k] = c[k]; r.abs_c[k] = abs_c[k]; }
+    if (mode == PNE_MODE_LOOP && nzero == 0) { r.c[0] += 1.0; r.abs_c[0] += 1.0; }
+    double sum = 0.0, comp = 0.0, asum = 0.0;            // Neumaier over orders
+    for (int k = 0; k <= K; ++k) {
+        const double x = r.c[k], tt = sum + x;
+        comp += (std::fabs(sum) >= std::fabs(x)) ? (sum - tt) + x : (x - tt) + sum;
+        sum = tt;
+        asum += r.abs_c[k];
+    }
+    sum += comp;
+    r.log_abs_zref = lz;
+    r.sign_zref = sz < 0 ? -1 : 1;
+    r.n_zero_sites = nzero;
+    r.sign = (sum < 0 ? -1 : 1) * r.sign_zref;
+    r.log_abs = (sum != 0.0) ? lz + std::log(std::fabs(sum)) : -std::numeric_limits<double>::infinity();
+    r.value = (sum == 0.0) ? 0.0 : (r.log_abs > 709.7 ? r.sign * std::numeric_limits<double>::infinity()
+                                                       : r.sign * std::exp(r.log_abs));
+    if (nzero == 0 && r.c[0] != 0.0) {                    // truncated power-series logarithm
+        double cc[kMaxOrder + 1], l[kMaxOrder + 1];
+        for (int k = 0; k <= K; ++k) { cc[k] = r.c[k] / r.c[0]; l[k] = 0.0; }
+        double ls = 0.0;
+        for (int k = 1; k <= K; ++k) {
+            double acc = k * cc[k];
+            for (int j = 1; j < k; ++j) acc -= j * l[j] * cc[k - j];
+            l[k] = acc / k;
+            ls += l[k];
+        }
+        r.log_series = lz + std::log(std::fabs(r.c[0])) + ls;
+    } else {
+        r.log_series = std::numeric_limits<double>::quiet_NaN();
+    }
+    r.err_bound = (sum != 0.0) ? gamma_n(nops, u) * asum / std::fabs(sum) : std::numeric_limits<double>::infinity();
+    r.n_terms = n_terms;
+    r.n_clusters = n_clusters;
+    r.bp_iters = bp_iters;
+    r.bp_residual = bp_residual;
+}
+
 }  // namespace pne
 
 using namespace pne;
@@ -252,7 +308,10 @@ pne_status pne_ctx_create(int device, pne_ctx **out)
 void pne_ctx_destroy(pne_ctx *ctx)
 {
     if (!ctx) return;
-    ctx->enum_cache.clear();
+    {
+        std::lock_guard<std::mutex> lk(ctx->cache_mu);
+        ctx->enum_cache.clear();
+    }
     cudaDeviceSynchronize();
     delete ctx;
 }
@@ -386,6 +445,7 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
                       ":" + std::to_string(K) + ":" + std::to_string(mode);
     std::shared_ptr<EnumRecord> rec;
     if (opts->use_cache) {
+        std::lock_guard<std::mutex> lk(ctx->cache_mu);
         auto it = ctx->enum_cache.find(key);
         if (it != ctx->enum_cache.end()) rec = it->second;
     }
@@ -419,7 +479,10 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
                 if ((st = prepare_shapes(ctx, g, *rec, s))) return st;
             }
         }
-        if (opts->use_cache) ctx->enum_cache[key] = rec;
+        if (opts->use_cache) {
+            std::lock_guard<std::mutex> lk(ctx->cache_mu);
+            ctx->enum_cache[key] = rec;
+        }
     }
     pne_terms *t = new pne_terms();
     t->ctx = ctx; t->part = part; t->rec = rec; t->K = K; t->mode = mode;
@@ -510,64 +573,44 @@ pne_status pne_sum(pne_ctx *ctx, const pne_terms *t, void *stream, pne_result *o
     std::vector<double> vac((size_t)B * 3);
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(vac.data(), p->vac.ptr, vac.size() * 8, cudaMemcpyDeviceToHost, s));
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    static const double unit[4] = {0x1p-53, 0x1p-24, 0x1p-11, 0x1p-8};
-    const double u = unit[t->dtype < 0 ? 0 : t->dtype];
-    // first-order rounding count per term: every site factor and every
-    // intermediate of a cluster contraction is rounded once in the working
-    // dtype (at most 2 (K + 1) roundings along a term's product)
-    const int nops = 2 * (K + 1);
     for (int b = 0; b < B; ++b) {
-        pne_result &r = out[b];
-        std::memset(&r, 0, sizeof r);
-        const double lz = vac[3 * b], sz = vac[3 * b + 1];
-        const int nzero = (int)vac[3 * b + 2];
-        r.n_orders = K + 1;
-        for (int k = 0; k <= K; ++k) { r.c[k] = c[(size_t)b * (K + 1) + k]; r.abs_c[k] = a[(size_t)b * (K + 1) + k]; }
-        if (t->mode == PNE_MODE_LOOP && nzero == 0) { r.c[0] += 1.0; r.abs_c[0] += 1.0; }
-        // Neumaier sum over orders
-        double sum = 0.0, comp = 0.0, asum = 0.0;
-        for (int k = 0; k <= K; ++k) {
-            const double x = r.c[k], tt = sum + x;
-            comp += (std::fabs(sum) >= std::fabs(x)) ? (sum - tt) + x : (x - tt) + sum;
-            sum = tt;
-            asum += r.abs_c[k];
-        }
-        sum += comp;
-        r.log_abs_zref = lz;
-        r.sign_zref = sz < 0 ? -1 : 1;
-        r.n_zero_sites = nzero;
-        r.sign = (sum < 0 ? -1 : 1) * r.sign_zref;
-        r.log_abs = (sum != 0.0) ? lz + std::log(std::fabs(sum)) : -std::numeric_limits<double>::infinity();
-        r.value = (sum == 0.0) ? 0.0 : (r.log_abs > 709.7 ? r.sign * std::numeric_limits<double>::infinity()
-                                                           : r.sign * std::exp(r.log_abs));
-        // truncated power-series logarithm of sum_k c_k x^k (x -> 1)
-        if (nzero == 0 && r.c[0] != 0.0) {
-            std::vector<double> cc(K + 1), l(K + 1, 0.0);
-            for (int k = 0; k <= K; ++k) cc[k] = r.c[k] / r.c[0];
-            double ls = 0.0;
-            for (int k = 1; k <= K; ++k) {
-                double acc = k * cc[k];
-                for (int j = 1; j < k; ++j) acc -= j * l[j] * cc[k - j];
-                l[k] = acc / k;
-                ls += l[k];
-            }
-            r.log_series = lz + std::log(std::fabs(r.c[0])) + ls;
-        } else {
-            r.log_series = std::numeric_limits<double>::quiet_NaN();
-        }
-        r.err_bound = (sum != 0.0) ? gamma_n(nops, u) * asum / std::fabs(sum) : std::numeric_limits<double>::infinity();
-        r.n_terms = t->rec->n_terms;
-        r.n_clusters = t->rec->n_clusters;
         const int set = b / p->n_slices;
-        r.bp_iters = p->bp_iters[set];
-        r.bp_residual = p->bp_residual[set];
+        finalize_result(out[b], K, t->mode, t->dtype, &c[(size_t)b * (K + 1)], &a[(size_t)b * (K + 1)], &vac[3 * (size_t)b],
+                        t->rec->n_terms, t->rec->n_clusters, p->bp_iters[set], p->bp_residual[set]);
     }
+    return PNE_OK;
+}
+
+pne_status pne_partition_update(pne_ctx *ctx, pne_partition *p, const double *data, int32_t data_on_device,
+                                const pne_partition_opts *opts, void *stream)
+{
+    if (!ctx || !p || !data) return PNE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    const double tol = (opts && opts->tol > 0) ? opts->tol : 1e-13;
+    const int max_iter = (opts && opts->max_iter > 0) ? opts->max_iter : 10000;
+    const double damping = opts ? opts->damping : 0.0;
+    if (!(damping >= 0.0 && damping < 1.0)) { set_error(ctx, PNE_EINVAL, "damping must be in [0,1)"); return PNE_EINVAL; }
+    const size_t bytes = (size_t)p->n_sets * p->full.tens_off[p->full.n_sites] * 8;
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(p->T.ptr, data, bytes, data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    int32_t flags[4] = {0, 0, 0, 0};
+    pne_status st;
+    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, p->bp_iters.data(), p->bp_residual.data(), flags)) ||
+        (st = launch_gauge(ctx, p, s, nullptr)))
+        return st;
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    p->mb32_dtype = -1;
+    if (flags[0] || flags[2]) { set_error(ctx, PNE_ETIMEOUT, "grid barrier timed out in BP"); return PNE_ETIMEOUT; }
+    if (flags[1] || flags[3]) { set_error(ctx, PNE_EDEGENERATE, "zero message or zero message overlap"); return PNE_EDEGENERATE; }
+    for (int b = 0; b < p->n_sets; ++b)
+        if (p->bp_iters[b] == 0) { set_error(ctx, PNE_ENOCONV, "BP did not converge for tensor set " + std::to_string(b)); return PNE_ENOCONV; }
     return PNE_OK;
 }
 
 pne_status pne_ctx_profile(pne_ctx *ctx, int enable)
 {
     if (!ctx) return PNE_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
     for (auto &r : ctx->prof.pending) { cudaEventSynchronize(r.b); ctx->prof.pool.push_back(r.a); ctx->prof.pool.push_back(r.b); }
     ctx->prof.pending.clear();
     ctx->prof.acc.clear();
@@ -578,6 +621,7 @@ pne_status pne_ctx_profile(pne_ctx *ctx, int enable)
 int pne_ctx_profile_read(pne_ctx *ctx, pne_profile_entry *out, int max)
 {
     if (!ctx) return 0;
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
     for (auto &r : ctx->prof.pending) {
         cudaEventSynchronize(r.b);
         float ms = 0.f;
@@ -618,6 +662,189 @@ pne_status pne_measure_fma_peak(pne_ctx *ctx, pne_dtype dtype, void *stream, dou
 {
     if (!ctx || !flops_per_s || (dtype != PNE_F64 && dtype != PNE_F32)) return PNE_EINVAL;
     return launch_fma_peak(ctx, dtype, (cudaStream_t)stream, flops_per_s);
+}
+
+}  // extern "C"
+
+struct pne_batch {
+    pne_ctx *ctx = nullptr;
+    pne::BatchPlan *plan = nullptr;
+    std::vector<pne_terms *> terms;
+    int dtype = 0, wpb = 4, bps = 1;
+    double tuned_ms = 0.0;
+    bool use_graph = false;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t n_results = 0;
+};
+
+namespace {
+
+std::map<std::string, std::pair<std::pair<int, int>, double>> g_tune_cache;
+
+void tune_cache_load()
+{
+    const char *path = std::getenv("PNE_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char key[512];
+    int w, b;
+    double ms;
+    while (std::fscanf(f, "%511s %d %d %lf", key, &w, &b, &ms) == 4) g_tune_cache[key] = {{w, b}, ms};
+    std::fclose(f);
+}
+
+void tune_cache_store(const std::string &key, int w, int b, double ms)
+{
+    g_tune_cache[key] = {{w, b}, ms};
+    const char *path = std::getenv("PNE_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d %.6f\n", key.c_str(), w, b, ms);
+    std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
+pne_status pne_batch_create(pne_ctx *ctx, int32_t n, pne_terms *const *terms, pne_dtype dtype,
+                            const pne_batch_opts *opts, void *stream, pne_batch **out)
+{
+    if (!ctx || n < 1 || !terms || !out) return PNE_EINVAL;
+    if (dtype < PNE_F64 || dtype > PNE_BF16) { set_error(ctx, PNE_EINVAL, "unknown dtype"); return PNE_EINVAL; }
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    pne_batch *b = new pne_batch();
+    b->ctx = ctx;
+    b->dtype = dtype;
+    b->terms.assign(terms, terms + n);
+    for (pne_terms *t : b->terms) {
+        if (!t) { delete b; return PNE_EINVAL; }
+        b->n_results += t->part->n_members;
+    }
+    pne_status st = batch_plan_create(ctx, b->terms, dtype, s, &b->plan);
+    if (st) { delete b; return st; }
+    // launch shape: given, cached, or tuned by timing every candidate
+    int w0 = opts ? opts->warps_per_block : 0, b0 = opts ? opts->blocks_per_sm : 0;
+    const bool prof = ctx->prof.on;
+    ctx->prof.on = false;
+    if (w0 > 0 && b0 > 0) {
+        if (w0 > 32 || batch_max_blocks_per_sm(b->plan, w0) < b0) {
+            ctx->prof.on = prof;
+            pne_batch_destroy(b);
+            set_error(ctx, PNE_EINVAL, "launch shape does not fit (shared memory or occupancy)");
+            return PNE_EINVAL;
+        }
+        b->wpb = w0; b->bps = b0;
+    } else {
+        static bool loaded = false;
+        if (!loaded) { tune_cache_load(); loaded = true; }
+        uint64_t ncl = 0, nmem = 0;
+        for (pne_terms *t : b->terms) { ncl += t->rec->n_clusters; nmem += t->part->n_members; }
+        const std::string key = "d" + std::to_string(dtype) + "_g" + std::to_string(n) + "_c" + std::to_string(ncl) +
+                                "_m" + std::to_string(nmem) + "_sm" + std::to_string(ctx->n_sm);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            b->wpb = it->second.first.first; b->bps = it->second.first.second; b->tuned_ms = it->second.second;
+        } else {
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0); cudaEventCreate(&e1);
+            double best = 1e300;
+            const int wcand[4] = {1, 2, 4, 8}, bcand[4] = {1, 2, 4, 8};
+            for (int wi = 0; wi < 4; ++wi) {
+                const int maxb = batch_max_blocks_per_sm(b->plan, wcand[wi]);
+                for (int bi = 0; bi < 4; ++bi) {
+                    if (bcand[bi] > maxb) continue;
+                    double t_best = 1e300;
+                    for (int rep = 0; rep < 3; ++rep) {
+                        cudaEventRecord(e0, s);
+                        st = batch_enqueue(ctx, b->plan, wcand[wi], bcand[bi], s);
+                        cudaEventRecord(e1, s);
+                        if (st || cudaEventSynchronize(e1) != cudaSuccess) { ctx->prof.on = prof; pne_batch_destroy(b); return st ? st : PNE_ECUDA; }
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (rep > 0 && ms < t_best) t_best = ms;
+                    }
+                    if (t_best < best) { best = t_best; b->wpb = wcand[wi]; b->bps = bcand[bi]; }
+                }
+            }
+            cudaEventDestroy(e0); cudaEventDestroy(e1);
+            if (best >= 1e300) { ctx->prof.on = prof; pne_batch_destroy(b); set_error(ctx, PNE_EINVAL, "no launch shape fits"); return PNE_EINVAL; }
+            b->tuned_ms = best;
+            tune_cache_store(key, b->wpb, b->bps, best);
+        }
+    }
+    b->use_graph = !opts || opts->use_graph;
+    if (b->use_graph) {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { ctx->prof.on = prof; pne_batch_destroy(b); set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return PNE_ECUDA; }
+        st = batch_enqueue(ctx, b->plan, b->wpb, b->bps, b->cap);
+        e = cudaStreamEndCapture(b->cap, &b->graph);
+        if (st || e != cudaSuccess) { ctx->prof.on = prof; pne_batch_destroy(b); if (!st) set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return st ? st : PNE_ECUDA; }
+        e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess) { ctx->prof.on = prof; pne_batch_destroy(b); set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return PNE_ECUDA; }
+    }
+    ctx->prof.on = prof;
+    *out = b;
+    return PNE_OK;
+}
+
+pne_status pne_batch_run(pne_ctx *ctx, pne_batch *b, void *stream, pne_result *out)
+{
+    if (!ctx || !b || !out) return PNE_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->use_graph) {
+        ProfScope ps(ctx, s, "batch_graph");
+        PNE_CUDA_TRY(ctx, cudaGraphLaunch(b->exec, s));
+    } else {
+        pne_status st = batch_enqueue(ctx, b->plan, b->wpb, b->bps, s);
+        if (st) return st;
+    }
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (batch_status_host(b->plan)) { set_error(ctx, PNE_ETIMEOUT, "a batched sum waited too long"); return PNE_ETIMEOUT; }
+    const double *h = batch_host_out(b->plan);
+    const std::vector<int64_t> &off = batch_out_offsets(b->plan);
+    int64_t r = 0;
+    for (size_t g = 0; g < b->terms.size(); ++g) {
+        const pne_terms *t = b->terms[g];
+        const pne_partition *p = t->part;
+        const int K = t->K;
+        for (int m = 0; m < p->n_members; ++m) {
+            const double *row = h + off[g] + (int64_t)m * ((K + 1) * 2 + 3);
+            double c[kMaxOrder + 1], a[kMaxOrder + 1];
+            for (int k = 0; k <= K; ++k) { c[k] = row[2 * k]; a[k] = row[2 * k + 1]; }
+            const int set = m / p->n_slices;
+            finalize_result(out[r++], K, t->mode, b->dtype, c, a, row + (K + 1) * 2, t->rec->n_terms, t->rec->n_clusters,
+                            p->bp_iters[set], p->bp_residual[set]);
+        }
+    }
+    return PNE_OK;
+}
+
+int64_t pne_batch_n_results(const pne_batch *b) { return b ? b->n_results : 0; }
+
+pne_status pne_batch_config(const pne_batch *b, int32_t *warps_per_block, int32_t *blocks_per_sm, double *tuned_ms)
+{
+    if (!b) return PNE_EINVAL;
+    if (warps_per_block) *warps_per_block = b->wpb;
+    if (blocks_per_sm) *blocks_per_sm = b->bps;
+    if (tuned_ms) *tuned_ms = b->tuned_ms;
+    return PNE_OK;
+}
+
+void pne_batch_destroy(pne_batch *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->plan) batch_plan_destroy(b->ctx, b->plan);
+    delete b;
 }
 
 }  // extern "C"

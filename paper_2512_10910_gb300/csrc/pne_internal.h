@@ -9,6 +9,7 @@
 #include <vector>
 #include <memory>
 #include <map>
+#include <mutex>
 
 #include "pne.h"
 
@@ -80,6 +81,7 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 struct Profiler {
+    std::mutex mu;
     bool on = false;
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> pool;
@@ -95,6 +97,7 @@ struct pne_ctx {
     pne_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
     std::map<std::string, std::shared_ptr<pne::EnumRecord>> enum_cache;
+    std::mutex cache_mu;
     // scratch for small device-side status words
     int32_t *d_status = nullptr;
 };
@@ -206,6 +209,22 @@ pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s,
 pne_status launch_all_mode(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s);
 pne_status launch_plan_work(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, uint64_t *fma);
 pne_status prepare_shapes(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, cudaStream_t s);
+pne_status launch_convert_only(pne_ctx *ctx, const pne_partition *p, int dtype, cudaStream_t s);
+
+// batched form (contract.cu)
+struct BatchPlan;
+pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms, int dtype, cudaStream_t s,
+                             BatchPlan **out);
+pne_status batch_enqueue(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStream_t s);
+int batch_max_blocks_per_sm(BatchPlan *bp, int wpb);
+void batch_plan_destroy(pne_ctx *ctx, BatchPlan *bp);
+double *batch_host_out(BatchPlan *bp);
+const std::vector<int64_t> &batch_out_offsets(BatchPlan *bp);
+int32_t batch_status_host(BatchPlan *bp);
+
+// result assembly shared by pne_sum and pne_batch_run
+void finalize_result(pne_result &r, int K, int mode, int dtype, const double *c, const double *abs_c,
+                     const double *vac, uint64_t n_terms, uint64_t n_clusters, int bp_iters, double bp_residual);
 pne_status launch_fma_peak(pne_ctx *ctx, int dtype, cudaStream_t s, double *flops);
 
 // exclusive scan of int64 counts on the device; total returned on the host

@@ -30,7 +30,7 @@ import numpy as np
 __all__ = [
     "Network", "square_lattice", "cubic_lattice", "grid_graph", "with_open_legs",
     "splitmix64_uniform", "splitmix64_normal",
-    "ising_tensors", "random_tensors", "aklt_tensors", "slice_open",
+    "ising_tensors", "random_tensors", "aklt_tensors", "slice_open", "batched_workload",
 ]
 
 # leg direction tags stored beside ``site_bonds`` (used by the AKLT builder)
@@ -290,6 +290,27 @@ def aklt_tensors(net: Network) -> Network:
         perm = [present.index(d) for d in dirs]
         tensors.append(np.ascontiguousarray(np.transpose(t, perm)))
     return net.with_tensors(tensors, name=net.name + "_aklt")
+
+
+def batched_workload(n: int = 4096, seed: int = 1234):
+    """The uneven batch: n independent open L x L square-lattice networks,
+    L uniform in 6..24 and D uniform in 2..6; with probability 1/2 a network is
+    random U[0,1)+0.1 at that D, otherwise Ising at D=2 with beta uniform in
+    [0.3, 0.5].  Drawn from one SplitMix64 stream; network i's tensors use
+    seed + 1 + i.  Returns a list of (kind, L, D, beta or None, Network)."""
+    u = splitmix64_uniform(seed, 4 * n).reshape(n, 4)
+    out = []
+    for i in range(n):
+        L = 6 + min(18, int(u[i, 0] * 19))
+        D = 2 + min(4, int(u[i, 1] * 5))
+        if u[i, 2] < 0.5:
+            g = square_lattice(L, L, D)
+            out.append(("random", L, D, None, random_tensors(g, seed + 1 + i)))
+        else:
+            beta = 0.3 + 0.2 * float(u[i, 3])
+            g = square_lattice(L, L, 2)
+            out.append(("ising", L, 2, beta, ising_tensors(g, beta)))
+    return out
 
 
 def slice_open(net: Network, assignment) -> Network:

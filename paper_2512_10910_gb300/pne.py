@@ -23,6 +23,9 @@ __all__ = [
     "pne_build_partition", "pne_partition_destroy", "pne_enumerate_terms", "pne_terms_destroy",
     "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_terms_export",
     "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak", "pne_bp_messages_noalloc",
+    "pne_partition_update", "pne_batch_create", "pne_batch_run", "pne_batch_n_results", "pne_batch_config",
+    "pne_batch_destroy", "BatchOpts", "pne_server_create", "pne_server_submit", "pne_server_poll",
+    "pne_server_drain", "pne_server_stats", "pne_server_destroy", "ServerOpts", "RequestInfo",
     "Network", "PartitionOpts", "EnumOpts", "Result", "Context", "run", "network_struct",
 ]
 
@@ -81,6 +84,24 @@ class Result(ctypes.Structure):
                     bp_iters=self.bp_iters, bp_residual=self.bp_residual)
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int32),
+                ("n_prep_streams", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("t_arrival", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_ready", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("device_bytes", ctypes.c_uint64), ("batch_size", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class ProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -130,6 +151,32 @@ def load_library():
     lib.pne_bp_messages_noalloc.argtypes = [ctypes.POINTER(Network), ctypes.c_double, ctypes.c_int32, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p, vp]
     lib.pne_bp_messages_noalloc.restype = ctypes.c_int
+    lib.pne_partition_update.argtypes = [vp, vp, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(PartitionOpts), vp]
+    lib.pne_partition_update.restype = ctypes.c_int
+    lib.pne_batch_create.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(BatchOpts), vp,
+                                     ctypes.POINTER(vp)]
+    lib.pne_batch_create.restype = ctypes.c_int
+    lib.pne_batch_run.argtypes = [vp, vp, vp, ctypes.POINTER(Result)]
+    lib.pne_batch_run.restype = ctypes.c_int
+    lib.pne_batch_n_results.argtypes = [vp]
+    lib.pne_batch_n_results.restype = ctypes.c_int64
+    lib.pne_batch_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_double)]
+    lib.pne_batch_config.restype = ctypes.c_int
+    lib.pne_batch_destroy.argtypes = [vp]
+    lib.pne_batch_destroy.restype = None
+    lib.pne_server_create.argtypes = [vp, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+    lib.pne_server_create.restype = ctypes.c_int
+    lib.pne_server_submit.argtypes = [vp, ctypes.POINTER(Network), ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.pne_server_submit.restype = ctypes.c_int
+    lib.pne_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result), ctypes.POINTER(RequestInfo)]
+    lib.pne_server_poll.restype = ctypes.c_int
+    lib.pne_server_drain.argtypes = [vp]
+    lib.pne_server_drain.restype = ctypes.c_int
+    lib.pne_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]
+    lib.pne_server_stats.restype = ctypes.c_int
+    lib.pne_server_destroy.argtypes = [vp]
+    lib.pne_server_destroy.restype = None
     lib.pne_ctx_profile.argtypes = [vp, ctypes.c_int]
     lib.pne_ctx_profile.restype = ctypes.c_int
     lib.pne_ctx_profile_read.argtypes = [vp, ctypes.POINTER(ProfileEntry), ctypes.c_int]
@@ -150,7 +197,9 @@ def exported_symbols() -> list:
              "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_terms_export",
     "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak",
              "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak",
-             "pne_bp_messages_noalloc"]
+             "pne_bp_messages_noalloc", "pne_partition_update", "pne_batch_create", "pne_batch_run",
+             "pne_batch_n_results", "pne_batch_config", "pne_batch_destroy", "pne_server_create",
+             "pne_server_submit", "pne_server_poll", "pne_server_drain", "pne_server_stats", "pne_server_destroy"]
     return [n for n in names if hasattr(lib, n)]
 
 
@@ -232,6 +281,81 @@ def pne_bp_messages_noalloc(net: Network, msg_out_ptr, tol=1e-13, max_iter=10000
                                                  iters.ctypes.data, res.ctypes.data, stream)
     _check(st, ctypes.c_void_p(0))
     return iters, res
+
+
+def pne_partition_update(ctx, part, data, opts: PartitionOpts = None, stream=None):
+    """Re-run a partition on new tensors (host numpy or device torch tensor)."""
+    opts = opts or PartitionOpts(1e-13, 10000, 0.0)
+    if hasattr(data, "data_ptr"):
+        ptr, dev = data.data_ptr(), int(bool(data.is_cuda))
+    else:
+        data = np.ascontiguousarray(data, dtype=np.float64)
+        ptr, dev = data.ctypes.data, 0
+    _check(load_library().pne_partition_update(ctx, part, ctypes.c_void_p(ptr), dev, ctypes.byref(opts), stream), ctx)
+
+
+def pne_batch_create(ctx, terms_list, dtype, opts: BatchOpts = None, stream=None):
+    arr = (ctypes.c_void_p * len(terms_list))(*[t.value if isinstance(t, ctypes.c_void_p) else t for t in terms_list])
+    h = ctypes.c_void_p()
+    _check(load_library().pne_batch_create(ctx, len(terms_list), arr, int(dtype),
+                                           ctypes.byref(opts) if opts is not None else None, stream, ctypes.byref(h)), ctx)
+    return h
+
+
+def pne_batch_n_results(b) -> int:
+    return int(load_library().pne_batch_n_results(b))
+
+
+def pne_batch_run(ctx, b, stream=None):
+    n = pne_batch_n_results(b)
+    out = (Result * n)()
+    _check(load_library().pne_batch_run(ctx, b, stream, out), ctx)
+    return [r.as_dict() for r in out]
+
+
+def pne_batch_config(b):
+    w, k, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(load_library().pne_batch_config(b, ctypes.byref(w), ctypes.byref(k), ctypes.byref(ms)))
+    return int(w.value), int(k.value), float(ms.value)
+
+
+def pne_batch_destroy(b):
+    load_library().pne_batch_destroy(b)
+
+
+def pne_server_create(ctx, opts: ServerOpts = None):
+    h = ctypes.c_void_p()
+    _check(load_library().pne_server_create(ctx, ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)), ctx)
+    return h
+
+
+def pne_server_submit(srv, net: Network, max_order) -> int:
+    i = ctypes.c_uint64()
+    _check(load_library().pne_server_submit(srv, ctypes.byref(net), int(max_order), ctypes.byref(i)))
+    return int(i.value)
+
+
+def pne_server_poll(srv, rid):
+    """(status, result dict or None, info dict or None); status PNE_EBUSY while pending."""
+    r, info = Result(), RequestInfo()
+    st = load_library().pne_server_poll(srv, ctypes.c_uint64(rid), ctypes.byref(r), ctypes.byref(info))
+    if st == PNE_EBUSY:
+        return st, None, None
+    return st, (r.as_dict() if st == PNE_OK else None), info.as_dict()
+
+
+def pne_server_drain(srv):
+    _check(load_library().pne_server_drain(srv))
+
+
+def pne_server_stats(srv):
+    b, t = ctypes.c_uint64(), ctypes.c_double()
+    _check(load_library().pne_server_stats(srv, ctypes.byref(b), ctypes.byref(t)))
+    return int(b.value), float(t.value)
+
+
+def pne_server_destroy(srv):
+    load_library().pne_server_destroy(srv)
 
 
 def pne_ctx_profile(ctx, enable=True):

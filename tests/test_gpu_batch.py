@@ -1,0 +1,129 @@
+"""Batched form: one persistent fused launch over many networks (uneven sizes
+and bond dimensions), replayed from a CUDA graph, against the per-network
+path and the oracle."""
+import numpy as np
+import pytest
+
+from paper_2512_10910_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2512_10910_gb300 import pne  # noqa: E402
+from oracle import enumerate as E  # noqa: E402
+from oracle import expansion as X  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2512_10910_gb300 import build
+    build.build()
+    c = pne.Context(0)
+    yield c
+    c.close()
+
+
+def _groups():
+    """(geometry, list of networks) groups of several sizes and dimensions."""
+    out = []
+    for (L, D, seeds) in [(6, 2, (1, 2)), (7, 3, (3,)), (5, 4, (4, 5, 6)), (8, 5, (7,)), (6, 6, (8,))]:
+        g = I.square_lattice(L, L, D)
+        out.append((g, [I.random_tensors(g, s) for s in seeds]))
+    g = I.square_lattice(7, 6, 2)
+    out.append((g, [I.ising_tensors(g, b) for b in (0.3, 0.45)]))
+    return out
+
+
+def _make(ctx, groups, K=8):
+    parts, terms, keep = [], [], []
+    for g, nets in groups:
+        data = np.concatenate([n.flat_data()[0] for n in nets])
+        ns, kp = pne.network_struct(g, data=data, n_batch=len(nets))
+        p, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0))
+        t, _, _ = pne.pne_enumerate_terms(ctx.h, p, pne.EnumOpts(K, 0, 1))
+        parts.append(p); terms.append(t); keep.append((ns, kp))
+    return parts, terms, keep
+
+
+def _free(parts, terms):
+    for t in terms:
+        pne.pne_terms_destroy(t)
+    for p in parts:
+        pne.pne_partition_destroy(p)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batch_matches_per_network_path_and_oracle(ctx, dtype):
+    groups = _groups()
+    parts, terms, keep = _make(ctx, groups)
+    try:
+        b = pne.pne_batch_create(ctx.h, terms, pne.DTYPES[dtype])
+        got = pne.pne_batch_run(ctx.h, b)
+        w, k, ms = pne.pne_batch_config(b)
+        assert w in (1, 2, 4, 8) and k >= 1 and ms > 0
+        pne.pne_batch_destroy(b)
+        r = 0
+        for (g, nets), t in zip(groups, terms):
+            pne.pne_contract_terms(ctx.h, t, pne.DTYPES[dtype])
+            single = pne.pne_sum(ctx.h, t)
+            for j, net in enumerate(nets):
+                one, ref = got[r], single[j]
+                assert one["n_terms"] == ref["n_terms"] and one["n_clusters"] == ref["n_clusters"]
+                tol = 1e-12 if dtype == "f64" else 1e-6
+                assert abs(one["log_abs"] - ref["log_abs"]) <= tol
+                np.testing.assert_allclose(one["c"], ref["c"], rtol=0, atol=tol * np.sum(np.abs(ref["c"])))
+                if dtype == "f64":
+                    orc = X.pne(net, 8, E.LOOP)
+                    assert abs(one["log_abs"] - orc.log_abs) <= 1e-10
+                r += 1
+        assert r == len(got)
+    finally:
+        _free(parts, terms)
+
+
+def test_batch_results_identical_across_launch_shapes_and_graph(ctx):
+    groups = _groups()
+    parts, terms, keep = _make(ctx, groups)
+    try:
+        runs = []
+        for opts in (pne.BatchOpts(1, 1, 1), pne.BatchOpts(2, 1, 1), pne.BatchOpts(1, 2, 0), None):
+            b = pne.pne_batch_create(ctx.h, terms, pne.PNE_F64, opts)
+            runs.append([(r["log_abs"], tuple(r["c"])) for r in pne.pne_batch_run(ctx.h, b)])
+            runs.append([(r["log_abs"], tuple(r["c"])) for r in pne.pne_batch_run(ctx.h, b)])   # replay
+            pne.pne_batch_destroy(b)
+        for other in runs[1:]:
+            assert other == runs[0]
+    finally:
+        _free(parts, terms)
+
+
+def test_batch_rejects_a_shape_that_does_not_fit(ctx):
+    groups = _groups()
+    parts, terms, keep = _make(ctx, groups)
+    try:
+        with pytest.raises(pne.PneError) as ei:
+            pne.pne_batch_create(ctx.h, terms, pne.PNE_F64, pne.BatchOpts(32, 8, 1))
+        assert ei.value.status == pne.PNE_EINVAL
+    finally:
+        _free(parts, terms)
+
+
+def test_batch_after_partition_update(ctx):
+    g = I.square_lattice(6, 6, 3)
+    nets_a = [I.random_tensors(g, s) for s in (1, 2)]
+    nets_b = [I.random_tensors(g, s) for s in (3, 4)]
+    parts, terms, keep = _make(ctx, [(g, nets_a)])
+    try:
+        b = pne.pne_batch_create(ctx.h, terms, pne.PNE_F64)
+        pne.pne_batch_run(ctx.h, b)
+        data = torch.from_numpy(np.concatenate([n.flat_data()[0] for n in nets_b])).cuda()
+        pne.pne_partition_update(ctx.h, parts[0], data)
+        got = pne.pne_batch_run(ctx.h, b)
+        pne.pne_batch_destroy(b)
+        for r, net in zip(got, nets_b):
+            (fresh,) = ctx.expand(net, 8)
+            assert abs(r["log_abs"] - fresh["log_abs"]) <= 1e-12
+    finally:
+        _free(parts, terms)
