@@ -32,6 +32,8 @@ import numpy as np  # noqa: E402
 
 from paper_2512_10910_gb300 import inputs as I  # noqa: E402
 
+BP_ARITH = {"fp64": 0, "ff": 1}
+
 WORKLOADS = {
     "random16": dict(desc="2D random-tensor network 16x16 open, D=4, U[0,1)+0.1, K=8 LOOP, 32 networks per step",
                      kind="random2d", L=16, D=4, K=8, batch=32, mode=0),
@@ -147,6 +149,8 @@ def main():
     ap.add_argument("--workload", default="random16", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--bp", default="ff", choices=["fp64", "ff"],
+                    help="BP sweep arithmetic: FP64, or float-float pairs on the FP32 pipes")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
 
@@ -183,7 +187,7 @@ def main():
 
     def step(data, dtype):
         ns, keep = pne.network_struct(g, data=data, n_batch=B)
-        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0), ctypes_stream)
+        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0, BP_ARITH[args.bp]), ctypes_stream)
         try:
             terms, nc, nt = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, mode, 0), ctypes_stream)
             try:
@@ -270,7 +274,7 @@ def main():
                     work=f"4 flops per tensor entry per site per sweep; {sum(iters)} sweeps over {B} sets")
     elif fam == "contract":
         ns, keep = pne.network_struct(g, data=data_dev, n_batch=B)
-        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0), ctypes_stream)
+        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0, BP_ARITH[args.bp]), ctypes_stream)
         terms, _, _ = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, mode, 0), ctypes_stream)
         fma = pne.pne_terms_work(ctx.h, terms, ctypes_stream)
         pne.pne_terms_destroy(terms); pne.pne_partition_destroy(part)
@@ -353,7 +357,7 @@ def run_batched(args, wl, rank, world, local_rank):
         flat = np.concatenate([n.flat_data()[0] for n in nets])
         data = torch.from_numpy(flat).to(dev)
         ns, kp = pne.network_struct(g, data=data, n_batch=len(nets))
-        p, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0), sh)
+        p, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0, BP_ARITH[args.bp]), sh)
         t, _, _ = pne.pne_enumerate_terms(ctx.h, p, pne.EnumOpts(wl["K"], wl["mode"], 1), sh)
         parts.append(p); terms.append(t); datas.append(data); keep.append((ns, kp))
     batch = pne.pne_batch_create(ctx.h, terms, dtype, None, sh)
@@ -363,7 +367,7 @@ def run_batched(args, wl, rank, world, local_rank):
 
     def step():
         for p, d in zip(parts, datas):
-            pne.pne_partition_update(ctx.h, p, d, None, sh)
+            pne.pne_partition_update(ctx.h, p, d, pne.PartitionOpts(1e-13, 10000, 0.0, BP_ARITH[args.bp]), sh)
         return pne.pne_batch_run(ctx.h, batch, sh)
 
     for _ in range(args.warmup):

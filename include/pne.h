@@ -95,6 +95,10 @@ typedef struct {
     double tol;          /* default 1e-13 when <= 0 */
     int32_t max_iter;    /* default 10000 when <= 0 */
     double damping;      /* default 0 */
+    int32_t arithmetic;  /* sweeps in 0: FP64, 1: float-float (pairs of FP32
+                            with error-free sums and products, ~2^-48 relative
+                            precision per operation, on the FP32 pipes); the
+                            messages handed to the gauge are FP64 either way */
 } pne_partition_opts;
 
 typedef struct {

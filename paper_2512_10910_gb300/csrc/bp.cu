@@ -24,6 +24,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "pne_internal.h"
 
 namespace pne {
@@ -94,16 +96,18 @@ __device__ void site_messages(const double *__restrict__ T, int k, const int *di
     for (int i = 0; i < h; ++i) A *= dims[i];
     for (int i = h; i < k; ++i) C *= dims[i];
     // outer-product weight tables
+    float inv[kMaxDeg];
+    for (int i = 0; i < k; ++i) inv[i] = 1.0f / (float)dims[i];
     for (int c = lane; c < C; c += 32) {
-        int r = c;
+        int r = c, m;
         double p = 1.0;
-        for (int i = k - 1; i >= h; --i) { p *= in[i * kMsgStride + r % dims[i]]; r /= dims[i]; }
+        for (int i = k - 1; i >= h; --i) { r = fdivmod(r, dims[i], inv[i], m); p *= in[i * kMsgStride + m]; }
         w[c] = p;
     }
     for (int a = lane; a < A; a += 32) {
-        int r = a;
+        int r = a, m;
         double p = 1.0;
-        for (int i = h - 1; i >= 0; --i) { p *= in[i * kMsgStride + r % dims[i]]; r /= dims[i]; }
+        for (int i = h - 1; i >= 0; --i) { r = fdivmod(r, dims[i], inv[i], m); p *= in[i * kMsgStride + m]; }
         u[a] = p;
     }
     __syncwarp();
@@ -152,14 +156,16 @@ __device__ void site_messages(const double *__restrict__ T, int k, const int *di
         int stride = 1;
         for (int i = hi - 1; i > j; --i) stride *= dims[i];
         int rest = size / dims[j];
+        const float inv_stride = 1.0f / (float)stride;
         double s = 0.0;
         for (int r = 0; r < rest; ++r) {
-            int a = (r / stride) * (stride * dims[j]) + x * stride + (r % stride);
+            int rs;
+            const int qs = fdivmod(r, stride, inv_stride, rs);
+            int a = qs * (stride * dims[j]) + x * stride + rs;
             double p = X[a];
-            int rr = a;
+            int rr = a, dgt;
             for (int i = hi - 1; i >= lo; --i) {
-                int dgt = rr % dims[i];
-                rr /= dims[i];
+                rr = fdivmod(rr, dims[i], inv[i], dgt);
                 if (i != j) p *= in[i * kMsgStride + dgt];
             }
             s += p;
@@ -293,6 +299,331 @@ __global__ void __launch_bounds__(kBpWarps * 32) bp_persistent_kernel(BPParams p
             }
         }
         if (all_done) return;
+    }
+}
+
+// ---------------------------------------------------------------- float-float sweeps
+// The same Jacobi sweeps with every multiply and add carried as an unevaluated
+// sum of two FP32 numbers (hi + lo): products by Dekker's error-free product
+// (one FMA recovers the rounding error of a*b), sums by Knuth's error-free
+// two-sum, dot products accumulated with a compensation term.  About 2^-48
+// relative precision per operation, on the FP32 pipes (64x the FP64 rate of
+// this part).  Site tensors are pre-scaled by a power of two per site (the
+// normalised messages do not change); messages live as (hi, lo) pairs.
+struct ff { float h, l; };
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ff ff_fast(float a, float b)        // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y)
+{
+    const float p = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -p);
+    e = __fadd_rn(e, __fmaf_rn(x.h, y.l, __fmul_rn(x.l, y.h)));
+    return ff_fast(p, e);
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y)
+{
+    const ff s = ff_two_sum(x.h, y.h), t = ff_two_sum(x.l, y.l);
+    const ff v = ff_fast(s.h, __fadd_rn(s.l, t.h));
+    return ff_fast(v.h, __fadd_rn(t.l, v.l));
+}
+// compensated accumulator: value = h + c
+struct ffacc {
+    float h = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(ff p)
+    {
+        const ff s = ff_two_sum(h, p.h);
+        h = s.h;
+        c = __fadd_rn(c, __fadd_rn(s.l, p.l));
+    }
+    __device__ __forceinline__ ff get() const { return ff_fast(h, c); }
+};
+__device__ __forceinline__ ff ff_shfl_xor(ff x, int off)
+{
+    return {__shfl_xor_sync(0xffffffffu, x.h, off), __shfl_xor_sync(0xffffffffu, x.l, off)};
+}
+__device__ __forceinline__ ff ff_sqrt(ff x)
+{
+    if (!(x.h > 0.f)) return {0.f, 0.f};
+    const float s = sqrtf(x.h);
+    const float r = __fadd_rn(__fmaf_rn(-s, s, x.h), x.l);
+    return ff_fast(s, __fdiv_rn(r, __fmul_rn(2.f, s)));
+}
+__device__ __forceinline__ ff ff_div(ff x, ff y)
+{
+    const float q1 = __fdiv_rn(x.h, y.h);
+    const ff r = ff_add(x, ff_mul({-q1, 0.f}, y));
+    return ff_fast(q1, __fdiv_rn(r.h, y.h));
+}
+// |x| > |y| (lexicographic on the normalised pair)
+__device__ __forceinline__ bool ff_abs_gt(ff x, ff y)
+{
+    if (x.h < 0.f) { x.h = -x.h; x.l = -x.l; }
+    if (y.h < 0.f) { y.h = -y.h; y.l = -y.l; }
+    return x.h > y.h || (x.h == y.h && x.l > y.l);
+}
+
+struct BPFFParams {
+    int n_sets, n_sites, n_legs;
+    const int32_t *site_ptr, *site_bonds, *bond_dim, *inc_slot;
+    const int64_t *tens_off;
+    int64_t set_stride;
+    const ff *T;                  // [n_sets][stride] scaled, float-float
+    ff *msg;                      // [2][n_sets][n_legs][8]
+    float tol;
+    double damping;
+    int max_iter;
+    unsigned int *res;            // [4][n_sets] float bits
+    int32_t *done_it, *iters_out, *final_buf, *flags;
+    double *res_out;
+    unsigned int *bar;
+    int smem_per_warp;            // ff entries
+    int tabA, tabC;
+};
+
+__device__ void site_messages_ff(const ff *__restrict__ T, int k, const int *dims, const ff *in, ff *u, ff *w,
+                                 ff *x1, ff *x2, ff *out, int lane)
+{
+    const int h = k / 2;
+    int A = 1, C = 1;
+    for (int i = 0; i < h; ++i) A *= dims[i];
+    for (int i = h; i < k; ++i) C *= dims[i];
+    float inv[kMaxDeg];
+    for (int i = 0; i < k; ++i) inv[i] = 1.0f / (float)dims[i];
+    for (int c = lane; c < C; c += 32) {
+        int r = c, m;
+        ff p = {1.f, 0.f};
+        for (int i = k - 1; i >= h; --i) { r = fdivmod(r, dims[i], inv[i], m); p = ff_mul(p, in[i * kMsgStride + m]); }
+        w[c] = p;
+    }
+    for (int a = lane; a < A; a += 32) {
+        int r = a, m;
+        ff p = {1.f, 0.f};
+        for (int i = h - 1; i >= 0; --i) { r = fdivmod(r, dims[i], inv[i], m); p = ff_mul(p, in[i * kMsgStride + m]); }
+        u[a] = p;
+    }
+    __syncwarp();
+    {
+        int lpr = 1;
+        while (lpr * 2 * A <= 32) lpr *= 2;
+        const int rows_per_pass = 32 / lpr, sub = lane % lpr;
+        for (int a0 = 0; a0 < A; a0 += rows_per_pass) {
+            const int a = a0 + lane / lpr;
+            ffacc acc;
+            if (a < A) {
+                const ff *row = T + (int64_t)a * C;
+                for (int c = sub; c < C; c += lpr) acc.add(ff_mul(row[c], w[c]));
+            }
+            ff s = acc.get();
+            for (int off = lpr / 2; off > 0; off >>= 1) s = ff_add(s, ff_shfl_xor(s, off));
+            if (a < A && sub == 0) x1[a] = s;
+        }
+    }
+    {
+        int lpc = 1;
+        while (lpc * 2 * C <= 32) lpc *= 2;
+        const int cols_per_pass = 32 / lpc, sub = lane / cols_per_pass;
+        for (int c0 = 0; c0 < C; c0 += cols_per_pass) {
+            const int c = c0 + lane % cols_per_pass;
+            ffacc acc;
+            if (c < C)
+                for (int a = sub; a < A; a += lpc) acc.add(ff_mul(u[a], T[(int64_t)a * C + c]));
+            ff s = acc.get();
+            for (int off = 16; off >= cols_per_pass; off >>= 1) s = ff_add(s, ff_shfl_xor(s, off));
+            if (c < C && sub == 0) x2[c] = s;
+        }
+    }
+    __syncwarp();
+    int n_items = 0;
+    for (int j = 0; j < k; ++j) n_items += dims[j];
+    for (int it = lane; it < n_items; it += 32) {
+        int j = 0, x = it;
+        while (x >= dims[j]) { x -= dims[j]; ++j; }
+        const ff *X = (j < h) ? x1 : x2;
+        const int lo = (j < h) ? 0 : h, hi = (j < h) ? h : k, size = (j < h) ? A : C;
+        int stride = 1;
+        for (int i = hi - 1; i > j; --i) stride *= dims[i];
+        const int rest = size / dims[j];
+        const float inv_stride = 1.0f / (float)stride;
+        ffacc acc;
+        for (int r = 0; r < rest; ++r) {
+            int rs;
+            const int qs = fdivmod(r, stride, inv_stride, rs);
+            const int a = qs * (stride * dims[j]) + x * stride + rs;
+            ff p = X[a];
+            int rr = a, dgt;
+            for (int i = hi - 1; i >= lo; --i) {
+                rr = fdivmod(rr, dims[i], inv[i], dgt);
+                if (i != j) p = ff_mul(p, in[i * kMsgStride + dgt]);
+            }
+            acc.add(p);
+        }
+        out[j * kMsgStride + x] = acc.get();
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kBpWarps * 32) bp_ff_kernel(BPFFParams p)
+{
+    extern __shared__ ff ffsmem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    ff *ws = ffsmem + wib * p.smem_per_warp;
+    ff *in = ws;
+    ff *out = in + kMaxDeg * kMsgStride;
+    ff *u = out + kMaxDeg * kMsgStride;
+    ff *w = u + p.tabA;
+    ff *x1 = w + p.tabC;
+    ff *x2 = x1 + p.tabA;
+    const unsigned int nblocks = gridDim.x;
+    const int64_t items = (int64_t)p.n_sets * p.n_sites;
+    const int64_t gwarp = (int64_t)blockIdx.x * kBpWarps + wib, nwarps = (int64_t)nblocks * kBpWarps;
+    const int64_t msg_set = (int64_t)p.n_legs * kMsgStride, msg_buf = (int64_t)p.n_sets * msg_set;
+    for (int it = 1; it <= p.max_iter; ++it) {
+        const int src = (it - 1) & 1, dst = it & 1;
+        unsigned int *res_cur = p.res + (int64_t)(it % 4) * p.n_sets;
+        unsigned int *res_prev = p.res + (int64_t)((it + 3) % 4) * p.n_sets;
+        if (blockIdx.x == 0) {
+            unsigned int *res_next = p.res + (int64_t)((it + 1) % 4) * p.n_sets;
+            for (int s = threadIdx.x; s < p.n_sets; s += blockDim.x) res_next[s] = 0u;
+        }
+        for (int64_t item = gwarp; item < items; item += nwarps) {
+            const int set = (int)(item / p.n_sites), v = (int)(item % p.n_sites);
+            if (p.done_it[set] != 0) continue;
+            if (it > 1 && __uint_as_float(res_prev[set]) < p.tol) continue;
+            const int l0 = p.site_ptr[v], k = p.site_ptr[v + 1] - l0;
+            int dims[kMaxDeg];
+            for (int i = 0; i < kMaxDeg; ++i) dims[i] = (i < k) ? p.bond_dim[p.site_bonds[l0 + i]] : 1;
+            const ff *msrc = p.msg + src * msg_buf + set * msg_set;
+            ff *mdst = p.msg + dst * msg_buf + set * msg_set;
+            for (int e = lane; e < k * kMsgStride; e += 32)
+                in[e] = msrc[(int64_t)p.inc_slot[l0 + e / kMsgStride] * kMsgStride + e % kMsgStride];
+            __syncwarp();
+            site_messages_ff(p.T + set * p.set_stride + p.tens_off[v], k, dims, in, u, w, x1, x2, out, lane);
+            float r = 0.f;
+            for (int j0 = 0; j0 < k; j0 += 4) {
+                const int j = j0 + (lane >> 3), a = lane & 7;
+                const bool live = (j < k) && (a < dims[j < k ? j : 0]);
+                const ff o = live ? out[j * kMsgStride + a] : ff{0.f, 0.f};
+                const ff old = live ? msrc[(int64_t)(l0 + j) * kMsgStride + a] : ff{0.f, 0.f};
+                ff n2 = ff_mul(o, o);
+                for (int off = 4; off > 0; off >>= 1) n2 = ff_add(n2, ff_shfl_xor(n2, off));
+                ff big = live ? o : ff{-1.f, 0.f};
+                bool has = live;
+                int arg = a;
+                for (int off = 4; off > 0; off >>= 1) {
+                    const ff ob = ff_shfl_xor(big, off);
+                    const int oa = __shfl_xor_sync(0xffffffffu, arg, off);
+                    const bool oh = __shfl_xor_sync(0xffffffffu, has, off);
+                    const bool take = oh && (!has || ff_abs_gt(ob, big) || (!ff_abs_gt(big, ob) && oa < arg));
+                    if (take) { big = ob; arg = oa; has = true; }
+                }
+                const float oarg = __shfl_sync(0xffffffffu, o.h, (lane & ~7) | arg);
+                ff nrm = ff_sqrt(n2);
+                if (j < k && !(nrm.h > 0.f)) { atomicExch(p.flags + 1, 1); nrm = {1.f, 0.f}; }
+                ff nv = ff_div(oarg < 0.f ? ff{-o.h, -o.l} : o, nrm);
+                if (p.damping > 0.0) {
+                    const float dm = (float)p.damping;
+                    ff m = ff_add(ff_mul(nv, {1.f - dm, 0.f}), ff_mul(old, {dm, 0.f}));
+                    ff m2 = live ? ff_mul(m, m) : ff{0.f, 0.f};
+                    for (int off = 4; off > 0; off >>= 1) m2 = ff_add(m2, ff_shfl_xor(m2, off));
+                    ff bg = live ? m : ff{-1.f, 0.f};
+                    bool hs = live;
+                    int ag = a;
+                    for (int off = 4; off > 0; off >>= 1) {
+                        const ff ob = ff_shfl_xor(bg, off);
+                        const int oa = __shfl_xor_sync(0xffffffffu, ag, off);
+                        const bool oh = __shfl_xor_sync(0xffffffffu, hs, off);
+                        const bool take = oh && (!hs || ff_abs_gt(ob, bg) || (!ff_abs_gt(bg, ob) && oa < ag));
+                        if (take) { bg = ob; ag = oa; hs = true; }
+                    }
+                    const float marg = __shfl_sync(0xffffffffu, m.h, (lane & ~7) | ag);
+                    ff n3 = ff_sqrt(m2);
+                    if (j < k && !(n3.h > 0.f)) { atomicExch(p.flags + 1, 1); n3 = {1.f, 0.f}; }
+                    nv = ff_div(marg < 0.f ? ff{-m.h, -m.l} : m, n3);
+                }
+                if (live) {
+                    mdst[(int64_t)(l0 + j) * kMsgStride + a] = nv;
+                    r = fmaxf(r, fabsf(__fadd_rn(__fsub_rn(nv.h, old.h), __fsub_rn(nv.l, old.l))));
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
+            if (lane == 0) atomicMax(res_cur + set, __float_as_uint(r));
+            __syncwarp();
+        }
+        if (!grid_barrier(p.bar, p.flags, nblocks)) return;
+        bool all_done = true;
+        for (int s = 0; s < p.n_sets; ++s) {
+            const bool was = p.done_it[s] != 0 || (it > 1 && __uint_as_float(res_prev[s]) < p.tol);
+            if (was) continue;
+            const float rs = __uint_as_float(res_cur[s]);
+            if (rs < p.tol) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    p.done_it[s] = it; p.iters_out[s] = it; p.res_out[s] = (double)rs; p.final_buf[s] = dst;
+                }
+            } else {
+                all_done = false;
+                if (it == p.max_iter && blockIdx.x == 0 && threadIdx.x == 0) {
+                    p.iters_out[s] = 0; p.res_out[s] = (double)rs; p.final_buf[s] = dst;
+                }
+            }
+        }
+        if (all_done) return;
+    }
+}
+
+// site tensors -> scaled float-float, one warp per (set, site)
+__global__ void ff_tensor_kernel(const double *T, ff *out, const int64_t *tens_off, int n_sites, int n_sets, int64_t stride)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t items = (int64_t)n_sets * n_sites;
+    for (int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < items;
+         item += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int set = (int)(item / n_sites), v = (int)(item % n_sites);
+        const double *t = T + set * stride + tens_off[v];
+        ff *o = out + set * stride + tens_off[v];
+        const int64_t n = tens_off[v + 1] - tens_off[v];
+        double mx = 0.0;
+        for (int64_t e = lane; e < n; e += 32) mx = fmax(mx, fabs(t[e]));
+        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        int ex = 0;
+        if (mx > 0.0) frexp(mx, &ex);
+        for (int64_t e = lane; e < n; e += 32) {
+            const double x = ldexp(t[e], -ex);
+            const float hi = __double2float_rn(x);
+            o[e] = {hi, __double2float_rn(x - (double)hi)};
+        }
+    }
+}
+
+__global__ void ff_init_kernel(ff *msg, const int32_t *site_bonds, const int32_t *bond_dim, int n_legs, int n_sets)
+{
+    const int64_t total = (int64_t)n_sets * n_legs;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int d = bond_dim[site_bonds[i % n_legs]];
+        const double v = 1.0 / sqrt((double)d);
+        const float hi = __double2float_rn(v);
+        const float lo = __double2float_rn(v - (double)hi);
+        for (int a = 0; a < kMsgStride; ++a) msg[i * kMsgStride + a] = (a < d) ? ff{hi, lo} : ff{0.f, 0.f};
+    }
+}
+
+// final float-float messages -> the FP64 message buffer the gauge reads
+__global__ void ff_export_kernel(const ff *msg_ff, double *msg, const int32_t *final_buf, int n_sets, int64_t per_set)
+{
+    const int64_t total = (int64_t)n_sets * per_set;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int set = (int)(i / per_set);
+        const int64_t at = ((int64_t)final_buf[set] * n_sets) * per_set + i;
+        msg[at] = (double)msg_ff[at].h + (double)msg_ff[at].l;
     }
 }
 
@@ -523,7 +854,7 @@ int grid_for(int64_t n, int block, int n_sm)
 
 // ---------------------------------------------------------------- host launchers
 pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, double damping,
-                     cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags)
+                     cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags, int arithmetic)
 {
     const Geometry &g = p->full;
     const int n_sets = p->n_sets;
@@ -563,6 +894,54 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
     if (e != cudaSuccess) { dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, e); }
 
     double *msg = (double *)p->msg.ptr;
+    DevBuf ffbuf;
+    if (arithmetic == 1) {
+        // float-float sweeps: pair tensors and pair messages in scratch, the
+        // final messages exported to the FP64 buffer for the gauge
+        const int64_t stride = g.tens_off[g.n_sites];
+        const size_t tbytes = (size_t)n_sets * stride * sizeof(ff);
+        const size_t mbytes = (size_t)2 * n_sets * g.n_legs * kMsgStride * sizeof(ff);
+        if ((st = dev_alloc(ctx, ffbuf, tbytes + mbytes, s))) { dev_free(ctx, scratch, s); return st; }
+        ff *Tff = (ff *)ffbuf.ptr;
+        ff *mff = (ff *)((char *)ffbuf.ptr + tbytes);
+        {
+            ProfScope ps(ctx, s, "bp_init");
+            ff_tensor_kernel<<<grid_for((int64_t)n_sets * g.n_sites * 32, 256, ctx->n_sm), 256, 0, s>>>(
+                (const double *)p->T.ptr, Tff, g.d_tens_off, g.n_sites, n_sets, stride);
+            ff_init_kernel<<<grid_for((int64_t)n_sets * g.n_legs, 256, ctx->n_sm), 256, 0, s>>>(
+                mff, g.d_site_bonds, g.d_bond_dim, g.n_legs, n_sets);
+        }
+        BPFFParams fp;
+        fp.n_sets = n_sets; fp.n_sites = g.n_sites; fp.n_legs = g.n_legs;
+        fp.site_ptr = g.d_site_ptr; fp.site_bonds = g.d_site_bonds; fp.bond_dim = g.d_bond_dim;
+        fp.inc_slot = g.d_inc_slot; fp.tens_off = g.d_tens_off; fp.set_stride = stride;
+        fp.T = Tff; fp.msg = mff; fp.tol = (float)tol; fp.damping = damping; fp.max_iter = max_iter;
+        fp.res = (unsigned int *)res; fp.done_it = done; fp.iters_out = iters; fp.final_buf = finalb;
+        fp.flags = flags; fp.res_out = res_out; fp.bar = bar;
+        fp.smem_per_warp = per_warp; fp.tabA = tabA; fp.tabC = tabC;
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(bp_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm_ff = 0;
+        PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_ff, bp_ff_kernel, kBpWarps * 32, smem));
+        if (per_sm_ff < 1) { dev_free(ctx, ffbuf, s); dev_free(ctx, scratch, s); set_error(ctx, PNE_EINVAL, "BP kernel does not fit"); return PNE_EINVAL; }
+        const int64_t items_ff = (int64_t)n_sets * g.n_sites;
+        const int64_t want_ff = (items_ff + kBpWarps - 1) / kBpWarps, cap_ff = (int64_t)per_sm_ff * ctx->n_sm;
+        const int nb_ff = (int)std::max<int64_t>(1, want_ff < cap_ff ? want_ff : cap_ff);
+        void *fargs[] = {&fp};
+        cudaError_t fe;
+        {
+            ProfScope ps(ctx, s, "bp_sweeps");
+            fe = cudaLaunchCooperativeKernel((void *)bp_ff_kernel, dim3(nb_ff), dim3(kBpWarps * 32), fargs, smem, s);
+        }
+        if (fe != cudaSuccess) { dev_free(ctx, ffbuf, s); dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, fe); }
+        {
+            ProfScope ps(ctx, s, "bp_export");
+            ff_export_kernel<<<grid_for((int64_t)n_sets * g.n_legs * kMsgStride, 256, ctx->n_sm), 256, 0, s>>>(
+                mff, msg, finalb, n_sets, (int64_t)g.n_legs * kMsgStride);
+        }
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    if (arithmetic != 1) {
     {
         ProfScope ps(ctx, s, "bp_init");
         bp_init_kernel<<<grid_for((int64_t)n_sets * g.n_legs, 256, ctx->n_sm), 256, 0, s>>>(
@@ -597,6 +976,7 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
                                         args, smem, s);
     }
     if (e != cudaSuccess) { dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, e); }
+    }
     // copy out the convergence record
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_iters, iters, n_sets * 4, cudaMemcpyDeviceToHost, s));
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_res, res_out, n_sets * 8, cudaMemcpyDeviceToHost, s));
@@ -614,6 +994,7 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
     }
     PNE_CUDA_TRY(ctx, cudaGetLastError());
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_flags + 2, flags, 8, cudaMemcpyDeviceToHost, s));
+    dev_free(ctx, ffbuf, s);
     dev_free(ctx, scratch, s);
     return PNE_OK;
 }

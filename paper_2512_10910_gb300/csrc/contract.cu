@@ -41,7 +41,7 @@ constexpr int kCtWarps = 4;          // warps per block, general contraction
 constexpr int kMaxSteps = 32;        // sites per cluster in the general kernel
 constexpr int kMaxFront = 12;        // frontier bonds
 constexpr int kMaxClose = kMaxDeg;
-constexpr int kStepInts = 8 + 3 * kMaxFront + 3 * kMaxClose;
+constexpr int kStepInts = 8 + 4 * kMaxFront + 4 * kMaxClose;   // + float reciprocals of the dims
 
 struct ContractParams {
     int64_t n_clusters;
@@ -96,7 +96,8 @@ __device__ __forceinline__ double pow2(int e) { return ldexp(1.0, e); }
 // Step layout (ints): [0] site, [1] mask, [2] nF (size of the new frontier),
 // [3] nC (closing bonds), [4] out_size, [5] close_size, [6] slot, [7] spare,
 // then dimsF[kMaxFront], sxF[kMaxFront], smF[kMaxFront],
-// dimsC[kMaxClose], sxC[kMaxClose], smC[kMaxClose].
+// dimsC[kMaxClose], sxC[kMaxClose], smC[kMaxClose], then the float bits of
+// 1/dimsF[kMaxFront] and 1/dimsC[kMaxClose] for divide-free decoding.
 // Builds the elimination plan of one cluster (single thread).  Returns the
 // number of steps, or -1 when a limit is exceeded.
 __device__ int build_plan(const ContractParams &P, int64_t c, int *plan, int *sites_out,
@@ -188,6 +189,9 @@ __device__ int build_plan(const ContractParams &P, int64_t c, int *plan, int *si
         int outsz = 1, closz = 1;
         for (int i = 0; i < n2; ++i) outsz *= dimsF[i];
         for (int i = 0; i < nC; ++i) closz *= dimsC[i];
+        int *invF = smC + kMaxClose, *invC = invF + kMaxFront;
+        for (int i = 0; i < n2; ++i) invF[i] = __float_as_int(1.0f / (float)dimsF[i]);
+        for (int i = 0; i < nC; ++i) invC[i] = __float_as_int(1.0f / (float)dimsC[i]);
         if (outsz > maxT) return -1;
         st[0] = P.cl_verts[c * P.vwidth + v];
         st[1] = mask[v];
@@ -233,15 +237,16 @@ __global__ void __launch_bounds__(kCtWarps * 32) contract_general_kernel(Contrac
                 const int site = st[0], mask = st[1], nF = st[2], nC = st[3], outsz = st[4], closz = st[5];
                 const int *dimsF = st + 8, *sxF = dimsF + kMaxFront, *smF = sxF + kMaxFront;
                 const int *dimsC = smF + kMaxFront, *sxC = dimsC + kMaxClose, *smC = sxC + kMaxClose;
+            const int *invF = smC + kMaxClose, *invC = invF + kMaxFront;
                 const int64_t mbase = (int64_t)b * P.stride + P.tens_off[site] + P.blk_off[site * kBlkStride + mask];
                 T mx = (T)0;
                 for (int o = lane; o < outsz; o += 32) {
                     int r = o, xb = 0, mb = 0;
-                    for (int i = nF - 1; i >= 0; --i) { const int d = r % dimsF[i]; r /= dimsF[i]; xb += d * sxF[i]; mb += d * smF[i]; }
+                    for (int i = nF - 1; i >= 0; --i) { int d; r = fdivmod(r, dimsF[i], __int_as_float(invF[i]), d); xb += d * sxF[i]; mb += d * smF[i]; }
                     T acc = (T)0;
                     for (int cc = 0; cc < closz; ++cc) {
                         int rc = cc, xi = xb, mi = mb;
-                        for (int i = nC - 1; i >= 0; --i) { const int d = rc % dimsC[i]; rc /= dimsC[i]; xi += d * sxC[i]; mi += d * smC[i]; }
+                        for (int i = nC - 1; i >= 0; --i) { int d; rc = fdivmod(rc, dimsC[i], __int_as_float(invC[i]), d); xi += d * sxC[i]; mi += d * smC[i]; }
                         acc = fma(rnd<R>(X[xi]), (T)L::get(P.M, mbase + mi), acc);
                     }
                     Y[o] = acc;
@@ -594,15 +599,15 @@ __global__ void shape_plan_kernel(ContractParams P, const int32_t *rep, int n_sh
 // One cluster per lane; the 32 lanes of a warp take consecutive clusters in
 // shape order and run the same plan on their own sites.  Lane l keeps its
 // intermediate tensor at X[j * 32 + l] (conflict-free shared memory).
-template <typename T, typename L, int R, int XMAX>
-__global__ void __launch_bounds__(128) contract_shaped_kernel(ContractParams P, const int32_t *perm,
+template <typename T, typename L, int R>
+__global__ void __launch_bounds__(256) contract_shaped_kernel(ContractParams P, const int32_t *perm,
                                                               const int32_t *shape_of, const int32_t *plans,
-                                                              const int32_t *plan_steps)
+                                                              const int32_t *plan_steps, int xmax)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    T *X0 = (T *)smem_raw + (int64_t)wib * 2 * XMAX * 32 + lane;
-    T *X1 = X0 + XMAX * 32;
+    T *X0 = (T *)smem_raw + (int64_t)wib * 2 * xmax * 32 + lane;
+    T *X1 = X0 + (int64_t)xmax * 32;
     const int64_t groups = (P.n_clusters + 31) / 32;
     const int64_t items = groups * P.n_members;
     for (int64_t it = (int64_t)blockIdx.x * wpb + wib; it < items; it += (int64_t)gridDim.x * wpb) {
@@ -624,15 +629,16 @@ __global__ void __launch_bounds__(128) contract_shaped_kernel(ContractParams P, 
             const int site = V[st[6]];
             const int *dimsF = st + 8, *sxF = dimsF + kMaxFront, *smF = sxF + kMaxFront;
             const int *dimsC = smF + kMaxFront, *sxC = dimsC + kMaxClose, *smC = sxC + kMaxClose;
+            const int *invF = smC + kMaxClose, *invC = invF + kMaxFront;
             const int64_t mbase = (int64_t)b * P.stride + P.tens_off[site] + P.blk_off[site * kBlkStride + mask];
             T mx = (T)0;
             for (int o = 0; o < outsz; ++o) {
                 int r = o, xb = 0, mb = 0;
-                for (int q = nF - 1; q >= 0; --q) { const int d = r % dimsF[q]; r /= dimsF[q]; xb += d * sxF[q]; mb += d * smF[q]; }
+                for (int q = nF - 1; q >= 0; --q) { int d; r = fdivmod(r, dimsF[q], __int_as_float(invF[q]), d); xb += d * sxF[q]; mb += d * smF[q]; }
                 T acc = (T)0;
                 for (int cc = 0; cc < closz; ++cc) {
                     int rc = cc, xi = xb, mi = mb;
-                    for (int q = nC - 1; q >= 0; --q) { const int d = rc % dimsC[q]; rc /= dimsC[q]; xi += d * sxC[q]; mi += d * smC[q]; }
+                    for (int q = nC - 1; q >= 0; --q) { int d; rc = fdivmod(rc, dimsC[q], __int_as_float(invC[q]), d); xi += d * sxC[q]; mi += d * smC[q]; }
                     acc = fma(rnd<R>(X[xi * 32]), (T)L::get(P.M, mbase + mi), acc);
                 }
                 Y[o * 32] = acc;
@@ -653,13 +659,14 @@ __global__ void __launch_bounds__(128) contract_shaped_kernel(ContractParams P, 
     }
 }
 
-template <typename T, typename L, int R, int XMAX>
+template <typename T, typename L, int R>
 pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &rec, cudaStream_t s)
 {
-    auto kern = contract_shaped_kernel<T, L, R, XMAX>;
-    const int per_warp = 2 * XMAX * 32 * (int)sizeof(T);
-    int wpb = (96 * 1024) / per_warp;
-    if (wpb > 4) wpb = 4;
+    auto kern = contract_shaped_kernel<T, L, R>;
+    const int xmax = rec.max_out;
+    const int per_warp = 2 * xmax * 32 * (int)sizeof(T);
+    int wpb = (100 * 1024) / per_warp;           // about two blocks per SM
+    if (wpb > 8) wpb = 8;
     if (wpb < 1) wpb = 1;
     const size_t smem = (size_t)wpb * per_warp;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -668,7 +675,7 @@ pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &
     const int64_t cap = (int64_t)ctx->n_sm * 16;
     if (g > cap) g = cap;
     kern<<<(int)g, wpb * 32, smem, s>>>(cp, (const int32_t *)rec.perm.ptr, (const int32_t *)rec.shape_of.ptr,
-                                        (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr);
+                                        (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr, xmax);
     PNE_CUDA_TRY(ctx, cudaGetLastError());
     return PNE_OK;
 }
@@ -676,9 +683,7 @@ pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &
 template <typename T, typename L, int R>
 pne_status dispatch_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &rec, cudaStream_t s)
 {
-    if (rec.max_out <= 16) return run_shaped<T, L, R, 16>(ctx, cp, rec, s);
-    if (rec.max_out <= 64) return run_shaped<T, L, R, 64>(ctx, cp, rec, s);
-    return run_shaped<T, L, R, 256>(ctx, cp, rec, s);
+    return run_shaped<T, L, R>(ctx, cp, rec, s);
 }
 
 }  // namespace
@@ -1074,15 +1079,16 @@ __device__ void lane_contract(const BatchGroup &G, int64_t i, int b, T *X0, T *X
         const int site = V[st[6]];
         const int *dimsF = st + 8, *sxF = dimsF + kMaxFront, *smF = sxF + kMaxFront;
         const int *dimsC = smF + kMaxFront, *sxC = dimsC + kMaxClose, *smC = sxC + kMaxClose;
+            const int *invF = smC + kMaxClose, *invC = invF + kMaxFront;
         const int64_t mbase = (int64_t)b * P.stride + P.tens_off[site] + P.blk_off[site * kBlkStride + mask];
         T mx = (T)0;
         for (int o = 0; o < outsz; ++o) {
             int r = o, xb = 0, mb = 0;
-            for (int q = nF - 1; q >= 0; --q) { const int d = r % dimsF[q]; r /= dimsF[q]; xb += d * sxF[q]; mb += d * smF[q]; }
+            for (int q = nF - 1; q >= 0; --q) { int d; r = fdivmod(r, dimsF[q], __int_as_float(invF[q]), d); xb += d * sxF[q]; mb += d * smF[q]; }
             T acc = (T)0;
             for (int cc = 0; cc < closz; ++cc) {
                 int rc = cc, xi = xb, mi = mb;
-                for (int q = nC - 1; q >= 0; --q) { const int d = rc % dimsC[q]; rc /= dimsC[q]; xi += d * sxC[q]; mi += d * smC[q]; }
+                for (int q = nC - 1; q >= 0; --q) { int d; rc = fdivmod(rc, dimsC[q], __int_as_float(invC[q]), d); xi += d * sxC[q]; mi += d * smC[q]; }
                 acc = fma(rnd<R>(X[xi * 32]), (T)L::get(P.M, mbase + mi), acc);
             }
             Y[o * 32] = acc;

@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "pne_internal.h"
 
@@ -329,6 +330,16 @@ __global__ void scan_add_kernel(int64_t *data, int64_t n, const int64_t *block_o
     if (i < n) data[i] += block_offsets[blockIdx.x];
 }
 
+// starts[r] = scanned[r * cols] (or the total at r == rows), one thread per row
+__global__ void row_starts_kernel(const int64_t *scanned, int rows, int64_t cols, int64_t n, int64_t *starts,
+                                  const int64_t *total)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r > rows) return;
+    const int64_t at = (int64_t)r * cols;
+    starts[r] = (r == rows || at >= n) ? *total : scanned[at];
+}
+
 __global__ void widen_kernel(const int32_t *src, int64_t *dst, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -441,10 +452,11 @@ int grid1(int64_t n, int block, int n_sm)
 
 }  // namespace
 
-// exclusive scan (in place) of n int64 values; the total is returned on the host
-pne_status device_exclusive_scan(pne_ctx *ctx, int64_t *d, int64_t n, int64_t *h_total, cudaStream_t s)
+// exclusive scan (in place) of n int64 values; the total is written to d_total
+// on the device (no synchronisation)
+pne_status device_exclusive_scan_to(pne_ctx *ctx, int64_t *d, int64_t n, int64_t *d_total, cudaStream_t s)
 {
-    if (n == 0) { *h_total = 0; return PNE_OK; }
+    if (n == 0) { PNE_CUDA_TRY(ctx, cudaMemsetAsync(d_total, 0, 8, s)); return PNE_OK; }
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
     DevBuf sums;
     pne_status st = dev_alloc(ctx, sums, (size_t)(nb + 1) * 8, s);
@@ -455,51 +467,65 @@ pne_status device_exclusive_scan(pne_ctx *ctx, int64_t *d, int64_t n, int64_t *h
         scan_block_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(d, n, bs);
     }
     PNE_CUDA_TRY(ctx, cudaGetLastError());
-    int64_t tot = 0;
     if (nb > 1) {
-        st = device_exclusive_scan(ctx, bs, nb, &tot, s);
-        if (st) { dev_free(ctx, sums, s); return st; }
+        if ((st = device_exclusive_scan_to(ctx, bs, nb, d_total, s))) { dev_free(ctx, sums, s); return st; }
         {
             ProfScope ps__(ctx, s, "scan");
             scan_add_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(d, n, bs);
         }
         PNE_CUDA_TRY(ctx, cudaGetLastError());
     } else {
-        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(&tot, bs, 8, cudaMemcpyDeviceToHost, s));
-        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(d_total, bs, 8, cudaMemcpyDeviceToDevice, s));
     }
-    *h_total = tot;
     dev_free(ctx, sums, s);
+    return PNE_OK;
+}
+
+// exclusive scan (in place) of n int64 values; the total is returned on the host
+pne_status device_exclusive_scan(pne_ctx *ctx, int64_t *d, int64_t n, int64_t *h_total, cudaStream_t s)
+{
+    if (n == 0) { *h_total = 0; return PNE_OK; }
+    DevBuf tot;
+    pne_status st = dev_alloc(ctx, tot, 8, s);
+    if (st) return st;
+    if ((st = device_exclusive_scan_to(ctx, d, n, (int64_t *)tot.ptr, s))) { dev_free(ctx, tot, s); return st; }
+    int64_t *h = pinned_i64(ctx, 1);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h, tot.ptr, 8, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    *h_total = *h;
+    dev_free(ctx, tot, s);
     return PNE_OK;
 }
 
 namespace {
 
 // counts [rows][cols] int32 -> base (exclusive scan, row-major) int64; per-row totals
+// (the row starts are gathered on the device and read back in one copy)
 pne_status scan_counts(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t cols, DevBuf &base,
                        std::vector<int64_t> &row_tot, cudaStream_t s)
 {
     const int64_t n = (int64_t)rows * cols;
-    pne_status st = dev_alloc(ctx, base, (size_t)std::max<int64_t>(n, 1) * 8, s);
+    pne_status st = dev_alloc(ctx, base, (size_t)(std::max<int64_t>(n, 1) + rows + 3) * 8, s);
     if (st) return st;
     int64_t *b = (int64_t *)base.ptr;
+    int64_t *starts = b + std::max<int64_t>(n, 1);          // [rows + 1]
+    int64_t *tot = starts + rows + 1;                       // [1]
     if (n > 0) {
         ProfScope ps__(ctx, s, "scan");
         widen_kernel<<<grid1(n, 256, ctx->n_sm), 256, 0, s>>>(d_counts, b, n);
     }
-    // per-row totals come from the scanned values at row boundaries
+    // exclusive scan; its total lands in tot
     int64_t total = 0;
-    st = device_exclusive_scan(ctx, b, n, &total, s);
-    if (st) return st;
-    std::vector<int64_t> starts(rows + 1, 0);
-    for (int r = 0; r < rows; ++r)
-        if (cols > 0 && r * cols < n)
-            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(&starts[r], b + (int64_t)r * cols, 8, cudaMemcpyDeviceToHost, s));
+    if ((st = device_exclusive_scan_to(ctx, b, n, tot, s))) return st;
+    row_starts_kernel<<<(rows + 1 + 127) / 128, 128, 0, s>>>(b, rows, cols, n, starts, tot);
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    std::vector<int64_t> h(rows + 1, 0);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(pinned_i64(ctx, rows + 1), starts, (rows + 1) * 8, cudaMemcpyDeviceToHost, s));
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    starts[rows] = total;
-    if (cols == 0) for (int r = 0; r <= rows; ++r) starts[r] = 0;
+    std::memcpy(h.data(), pinned_i64(ctx, rows + 1), (rows + 1) * 8);
+    (void)total;
     row_tot.assign(rows, 0);
-    for (int r = 0; r < rows; ++r) row_tot[r] = starts[r + 1] - starts[r];
+    for (int r = 0; r < rows; ++r) row_tot[r] = h[r + 1] - h[r];
     return PNE_OK;
 }
 

@@ -47,6 +47,20 @@ pne_status dev_alloc(pne_ctx *ctx, DevBuf &b, size_t bytes, cudaStream_t s)
     return PNE_OK;
 }
 
+int64_t *pinned_i64(pne_ctx *ctx, size_t n)
+{
+    (void)ctx;
+    thread_local int64_t *buf = nullptr;
+    thread_local size_t cap = 0;
+    thread_local int64_t fallback[64];          // pageable, if pinned memory is unavailable
+    if (n > cap) {
+        if (buf) cudaFreeHost(buf);
+        cap = n < 64 ? 64 : n;
+        if (cudaMallocHost((void **)&buf, cap * 8) != cudaSuccess) { buf = nullptr; cap = 0; }
+    }
+    return buf ? buf : (n <= 64 ? fallback : nullptr);
+}
+
 void dev_free(pne_ctx *ctx, DevBuf &b, cudaStream_t s)
 {
     if (!b.ptr) return;
@@ -402,7 +416,10 @@ pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_p
     p->bp_iters.assign(B, 0);
     p->bp_residual.assign(B, 0.0);
     int32_t flags[4] = {0, 0, 0, 0};
-    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, p->bp_iters.data(), p->bp_residual.data(), flags)) ||
+    const int arith = opts ? opts->arithmetic : 0;
+    if (arith != 0 && arith != 1) { pne_partition_destroy(p); set_error(ctx, PNE_EINVAL, "arithmetic must be 0 or 1"); return PNE_EINVAL; }
+    p->arithmetic = arith;
+    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, p->bp_iters.data(), p->bp_residual.data(), flags, arith)) ||
         (st = launch_gauge(ctx, p, s, nullptr))) {
         pne_partition_destroy(p);
         return st;
@@ -495,6 +512,10 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
             pne_terms_destroy(t); return st;
         }
     }
+    // the lists were written by kernels on `stream`; callers may use them from
+    // other streams (the server's launcher does), so finish them here
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { pne_terms_destroy(t); set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return PNE_ECUDA; }
     *out = t;
     if (n_clusters) *n_clusters = rec->n_clusters;
     if (n_terms) *n_terms = rec->n_terms;
@@ -595,7 +616,8 @@ pne_status pne_partition_update(pne_ctx *ctx, pne_partition *p, const double *da
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(p->T.ptr, data, bytes, data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     int32_t flags[4] = {0, 0, 0, 0};
     pne_status st;
-    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, p->bp_iters.data(), p->bp_residual.data(), flags)) ||
+    const int arith = opts ? opts->arithmetic : p->arithmetic;
+    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, p->bp_iters.data(), p->bp_residual.data(), flags, arith)) ||
         (st = launch_gauge(ctx, p, s, nullptr)))
         return st;
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));

@@ -23,6 +23,18 @@ constexpr int kBlkStride = 64;           // 2^kMaxDeg excitation masks per site
 constexpr int kMaxAllBonds = 30;         // ALL mode: bitmask terms
 constexpr int kWarpTensorMax = 1024;     // entries of one intermediate tensor per warp
 
+// ------------------------------------------------------------------ index arithmetic
+// q = r / d and m = r % d for 0 <= r < 2^22 - 1 and any d >= 1, without an
+// integer divide: (r + 1/2) / d lies at least 1/(2d) from an integer, while the
+// float product (r + 1/2) * fl(1/d) is off by under (r + 1/2) / d * 2^-23 <
+// 1/(2d); truncation therefore gives q exactly.
+__device__ __forceinline__ int fdivmod(int r, int d, float inv_d, int &m)
+{
+    const int q = __float2int_rz(__fmul_rn(__int2float_rn(r) + 0.5f, inv_d));
+    m = r - q * d;
+    return q;
+}
+
 // ------------------------------------------------------------------ errors
 struct Error {
     pne_status st;
@@ -49,6 +61,8 @@ struct DevBuf {
 };
 
 pne_status dev_alloc(pne_ctx *ctx, DevBuf &b, size_t bytes, cudaStream_t s);
+// small pinned host buffer for device-to-host reads of counts (per thread)
+int64_t *pinned_i64(pne_ctx *ctx, size_t n);
 void dev_free(pne_ctx *ctx, DevBuf &b, cudaStream_t s);
 
 // ------------------------------------------------------------------ geometry
@@ -123,6 +137,7 @@ struct pne_partition {
     pne::DevBuf Mb32;                // FP32/TF32 copy (lazy)
     pne::DevBuf Mb16;                // BF16 copy (lazy)
     int mb32_dtype = -1;
+    int arithmetic = 0;              // BP sweeps: 0 FP64, 1 float-float
     std::vector<int32_t> bp_iters;   // per set
     std::vector<double> bp_residual; // per set
     cudaStream_t last_stream = nullptr;
@@ -193,7 +208,7 @@ struct ProfScope {
 // ------------------------------------------------------------------ kernels
 // BP, gauge, blocked layout (bp.cu)
 pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, double damping,
-                     cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags);
+                     cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags, int arithmetic = 0);
 pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t *h_flag);
 pne_status launch_convert(pne_ctx *ctx, pne_partition *p, int dtype, cudaStream_t s);
 
@@ -230,5 +245,6 @@ pne_status launch_fma_peak(pne_ctx *ctx, int dtype, cudaStream_t s, double *flop
 // exclusive scan of int64 counts on the device; total returned on the host
 pne_status device_exclusive_scan(pne_ctx *ctx, int64_t *d_counts, int64_t n, int64_t *h_total,
                                  cudaStream_t s);
+pne_status device_exclusive_scan_to(pne_ctx *ctx, int64_t *d, int64_t n, int64_t *d_total, cudaStream_t s);
 
 }  // namespace pne

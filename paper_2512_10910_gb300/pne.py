@@ -59,7 +59,8 @@ class Network(ctypes.Structure):
 
 
 class PartitionOpts(ctypes.Structure):
-    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("damping", ctypes.c_double)]
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("damping", ctypes.c_double),
+                ("arithmetic", ctypes.c_int32)]
 
 
 class EnumOpts(ctypes.Structure):
@@ -463,14 +464,15 @@ class Context:
 
     def expand(self, net, K, mode=PNE_MODE_LOOP, dtype=PNE_F64, data=None, n_batch=1, stream=None,
                tol=1e-13, max_iter=10000, damping=0.0, use_cache=True, allow_noconv=False,
-               export=False):
+               export=False, arithmetic=0):
         """One pass: partition -> enumerate -> contract -> sum.  Returns the
         list of result dicts (one per tensor set and open-index assignment);
         with export=True also (edges, w) of the clusters."""
         if isinstance(dtype, str):
             dtype = DTYPES[dtype]
         ns, keep = network_struct(net, data=data, n_batch=n_batch)
-        part, st = pne_build_partition(self.h, ns, PartitionOpts(tol, max_iter, damping), stream, allow_noconv)
+        part, st = pne_build_partition(self.h, ns, PartitionOpts(tol, max_iter, damping, arithmetic), stream,
+                                       allow_noconv)
         try:
             terms, nc, nt = pne_enumerate_terms(self.h, part, EnumOpts(K, mode, int(use_cache)), stream)
             try:

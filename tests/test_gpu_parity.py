@@ -218,3 +218,27 @@ def test_torch_allocator_gives_identical_results():
     finally:
         c1.close(); c2.close()
     assert np.array_equal(a["c"], b["c"])
+
+
+# ---------------------------------------------------------------- float-float BP sweeps
+FF_CASES = [
+    ("random2d_D4", lambda: I.random_tensors(I.square_lattice(8, 8, 4), 3), 8),
+    ("random2d_D5", lambda: I.random_tensors(I.square_lattice(6, 7, 5), 4), 6),
+    ("random3d_D3", lambda: I.random_tensors(I.cubic_lattice(3, 3, 3, 3), 5, "n1,0.3"), 6),
+    ("aklt", lambda: I.aklt_tensors(I.square_lattice(6, 6, 4)), 8),
+    ("ising3d_ordered", lambda: I.ising_tensors(I.cubic_lattice(4, 4, 4, 2), 0.25), 8),
+    ("ising2d", lambda: I.ising_tensors(I.square_lattice(4, 4, 2), 0.40), 24),
+    ("bias_signed", lambda: I.random_tensors(I.square_lattice(5, 5, 3), 7, "bias:0.5"), 8),
+]
+
+
+@pytest.mark.parametrize("name,make,K", FF_CASES, ids=[c[0] for c in FF_CASES])
+def test_float_float_bp_matches_oracle(ctx, name, make, K):
+    net = make()
+    ref = X.pne(net, K, E.LOOP)
+    (ff,) = ctx.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64, arithmetic=1)
+    (d64,) = ctx.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64, arithmetic=0)
+    assert ff["n_terms"] == ref.n_terms
+    _check_values(ff, ref)
+    assert abs(ff["log_abs"] - d64["log_abs"]) <= 1e-10
+    assert ff["bp_iters"] > 0

@@ -49,5 +49,5 @@ def test_struct_layouts():
     import ctypes
     # pne_network: 2 ints, 4 pointers, data, data_off, 2 ints (LP64)
     assert ctypes.sizeof(pne.Network) == 8 + 4 * 8 + 8 + 8 + 8
-    assert ctypes.sizeof(pne.PartitionOpts) == 24
+    assert ctypes.sizeof(pne.PartitionOpts) == 32
     assert ctypes.sizeof(pne.EnumOpts) == 12
