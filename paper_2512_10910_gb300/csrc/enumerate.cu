@@ -16,8 +16,9 @@
 // sites only.
 //
 // Parallel schedule: the first levels of every anchor's tree are expanded
-// level by level (one thread per node); each node of the last prefix level is
-// then searched depth-first by one thread.  Every unit first counts what it
+// level by level (one warp per node, one lane per candidate); each node of the
+// last prefix level is then searched depth-first by one thread, unless the
+// prefix already reaches size K - 1 and one more warp-parallel step ends it.  Every unit first counts what it
 // emits per cluster size; an exclusive scan over (size, unit) gives each unit
 // its output slots, and a second pass writes.  The output is grouped by size
 // and deterministic.
@@ -180,60 +181,103 @@ __global__ void roots_kernel(GeomView g, int n_closed, int K, int mode, Node *no
 }
 
 // ---------------------------------------------------------------- prefix expansion
-// pass 0: count child nodes and emissions; pass 1: write child nodes;
-// pass 2: write emitted clusters.
-__global__ void expand_kernel(GeomView g, const Node *nodes, int64_t n_nodes, int K, int mode, int pass,
-                              int32_t *child_count, const int64_t *child_off, Node *children,
-                              int32_t *counts /* [K+1][n_nodes] */, Emit out, const int64_t *base,
-                              int32_t *overflow)
+// One warp per node, one lane per candidate U[i] (two rounds when the list is
+// longer than a warp).  Each lane forms S + U[i] on its own, so a node costs a
+// few hundred instructions of latency instead of a serial walk over its list;
+// ballots give every child and every emitted set its rank within the node, so
+// the output order is the candidate order, as in the serial search.
+// pass 0: count child nodes (child_count may be null) and emissions;
+// pass 1: write child nodes; pass 2: write emitted clusters.
+constexpr int kExpandWarps = 4;
+constexpr int kMaxNew = kNodeU / (kPrefixMax + 1);   // new candidates per step (site degree - 1)
+constexpr int kNodeWords = (int)(sizeof(Node) / 4);
+
+// every degree-one site of V has a bond among U[lo..hi) (endpoints UA/UB) or the
+// new candidates (endpoints NA/NB)
+template <int NV>
+__device__ bool repairable_split(const VSet<NV> &V, const int32_t *UA, const int32_t *UB, int lo, int hi,
+                                 const int32_t *NA, const int32_t *NB, int nn)
 {
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n_nodes;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        const Node nd = nodes[u];
-        const int t = nd.t, anchor = nd.S[0];
-        VSet<kPrefixMax + 2> V;
-        for (int i = 0; i < t; ++i) { V.inc(g.bond_site[2 * nd.S[i]]); V.inc(g.bond_site[2 * nd.S[i] + 1]); }
-        int32_t S[kPrefixMax + 1];
-        for (int i = 0; i < t; ++i) S[i] = nd.S[i];
-        int32_t U[kNodeU], UA[kNodeU], UB[kNodeU];
-        for (int i = 0; i < nd.nU; ++i) {
-            U[i] = nd.U[i]; UA[i] = g.bond_site[2 * U[i]]; UB[i] = g.bond_site[2 * U[i] + 1];
+    if (V.dang == 0) return true;
+    for (int i = 0; i < V.n; ++i) {
+        if (V.d[i] != 1) continue;
+        const int x = V.v[i];
+        bool found = false;
+        for (int q = lo; q < hi && !found; ++q) found = (UA[q] == x || UB[q] == x);
+        for (int q = 0; q < nn && !found; ++q) found = (NA[q] == x || NB[q] == x);
+        if (!found) return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(32 * kExpandWarps)
+expand_kernel(GeomView g, const Node *nodes, int64_t n_nodes, int K, int mode, int pass,
+              int32_t *child_count, const int64_t *child_off, Node *children,
+              int32_t *counts /* [K+1][n_nodes] */, Emit out, const int64_t *base, int32_t *overflow)
+{
+    __shared__ Node sh_node[kExpandWarps];
+    __shared__ int32_t sh_a[kExpandWarps][kNodeU], sh_b[kExpandWarps][kNodeU];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    Node &nd = sh_node[w];
+    int32_t *UA = sh_a[w], *UB = sh_b[w];
+    for (int64_t u = (int64_t)blockIdx.x * kExpandWarps + w; u < n_nodes; u += (int64_t)gridDim.x * kExpandWarps) {
+        const int32_t *src = reinterpret_cast<const int32_t *>(nodes + u);
+        for (int q = lane; q < kNodeWords; q += 32) reinterpret_cast<int32_t *>(&nd)[q] = src[q];
+        __syncwarp();
+        const int nU = nd.nU, t = nd.t, anchor = nd.S[0];
+        for (int q = lane; q < nU; q += 32) {
+            const int e = nd.U[q];
+            UA[q] = g.bond_site[2 * e]; UB[q] = g.bond_site[2 * e + 1];
         }
+        __syncwarp();
         int n_child = 0, n_emit = 0;
-        int64_t child_slot = (pass == 1) ? child_off[u] : 0;
-        int64_t emit_slot = (pass == 2) ? base[(int64_t)(t + 1) * n_nodes + u] : 0;
-        for (int i = 0; i < nd.nU; ++i) {
-            const int e = nd.U[i];
-            const int a0 = g.bond_site[2 * e], a1 = g.bond_site[2 * e + 1];
-            const int b = V.find(a0) < 0 ? a0 : (V.find(a1) < 0 ? a1 : -1);
-            V.inc(a0); V.inc(a1);
-            S[t] = e;
-            if (valid_set(mode, V.dang)) {
-                if (pass == 2) write_cluster(out, emit_slot, S, t + 1, V);
-                ++emit_slot; ++n_emit;
-            }
-            if (may_grow(mode, t + 1, K, V.dang)) {
-                int ne = nd.nU;
-                if (b >= 0) ne = append_new(g, b, e, anchor, V, U, UA, UB, ne, kNodeU, overflow);
-                if (mode == PNE_MODE_ALL || repairable(V, UA, UB, i + 1, ne)) {
-                    if (pass == 1) {
-                        Node c;
-                        for (int q = 0; q <= t; ++q) c.S[q] = S[q];
-                        c.t = t + 1;
-                        int m = 0;
-                        for (int q = i + 1; q < ne; ++q) c.U[m++] = U[q];
-                        c.nU = m;
-                        children[child_slot] = c;
-                    }
-                    ++child_slot; ++n_child;
+        const int64_t cbase = (pass == 1) ? child_off[u] : 0;
+        const int64_t ebase = (pass == 2) ? base[(int64_t)(t + 1) * n_nodes + u] : 0;
+        for (int i0 = 0; i0 < nU; i0 += 32) {
+            const int i = i0 + lane;
+            bool emit = false, grow = false;
+            VSet<kPrefixMax + 2> V;
+            int32_t NU[kMaxNew], NA[kMaxNew], NB[kMaxNew];
+            int nn = 0;
+            if (i < nU) {
+                for (int q = 0; q < t; ++q) { V.inc(g.bond_site[2 * nd.S[q]]); V.inc(g.bond_site[2 * nd.S[q] + 1]); }
+                const int e = nd.U[i], a0 = UA[i], a1 = UB[i];
+                const int b = V.find(a0) < 0 ? a0 : (V.find(a1) < 0 ? a1 : -1);
+                V.inc(a0); V.inc(a1);
+                emit = valid_set(mode, V.dang);
+                if (may_grow(mode, t + 1, K, V.dang)) {
+                    if (b >= 0) nn = append_new(g, b, e, anchor, V, NU, NA, NB, 0, kMaxNew, overflow);
+                    grow = mode == PNE_MODE_ALL || repairable_split(V, UA, UB, i + 1, nU, NA, NB, nn);
                 }
             }
-            V.dec(a1); V.dec(a0);
+            const unsigned gm = __ballot_sync(0xffffffffu, grow), em = __ballot_sync(0xffffffffu, emit);
+            if (pass == 1 && grow) {
+                Node *c = children + cbase + n_child + __popc(gm & lt);
+                for (int q = 0; q < t; ++q) c->S[q] = nd.S[q];
+                c->S[t] = nd.U[i];
+                c->t = t + 1;
+                int m = 0;
+                for (int q = i + 1; q < nU; ++q) c->U[m++] = nd.U[q];
+                for (int q = 0; q < nn; ++q) {
+                    if (m < kNodeU) c->U[m++] = NU[q]; else atomicExch(overflow, 1);
+                }
+                c->nU = m;
+            }
+            if (pass == 2 && emit) {
+                int32_t S[kPrefixMax + 1];
+                for (int q = 0; q < t; ++q) S[q] = nd.S[q];
+                S[t] = nd.U[i];
+                write_cluster(out, ebase + n_emit + __popc(em & lt), S, t + 1, V);
+            }
+            n_child += __popc(gm);
+            n_emit += __popc(em);
         }
-        if (pass == 0) {
-            child_count[u] = n_child;
+        if (pass == 0 && lane == 0) {
+            if (child_count) child_count[u] = n_child;
             counts[(int64_t)(t + 1) * n_nodes + u] = n_emit;
         }
+        __syncwarp();
     }
 }
 
@@ -577,7 +621,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         int32_t *cnts = (int32_t *)cur.counts.ptr;
         {
             ProfScope ps__(ctx, s, "enum_expand");
-            expand_kernel<<<grid1(cur.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)cur.nodes.ptr, cur.n, K, mode, 0,
+            expand_kernel<<<grid1(cur.n, kExpandWarps, ctx->n_sm), 32 * kExpandWarps, 0, s>>>(gv, (const Node *)cur.nodes.ptr, cur.n, K, mode, 0,
                                                                   child_count, nullptr, nullptr, cnts, none, nullptr, overflow);
         }
         PNE_CUDA_TRY(ctx, cudaGetLastError());
@@ -601,7 +645,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         PNE_CUDA_TRY(ctx, cudaMemsetAsync(nxt.counts.ptr, 0, (size_t)(K + 1) * std::max<int64_t>(n_child, 1) * 4, s));
         {
             ProfScope ps__(ctx, s, "enum_expand");
-            expand_kernel<<<grid1(cur.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)cur.nodes.ptr, cur.n, K, mode, 1,
+            expand_kernel<<<grid1(cur.n, kExpandWarps, ctx->n_sm), 32 * kExpandWarps, 0, s>>>(gv, (const Node *)cur.nodes.ptr, cur.n, K, mode, 1,
                                                                   nullptr, (const int64_t *)coff.ptr, (Node *)nxt.nodes.ptr,
                                                                   nullptr, none, nullptr, overflow);
         }
@@ -611,10 +655,19 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         lv.push_back(std::move(nxt));
         ++depth;
     }
-    // depth-first counts from the last level
+    // the last level: nodes of size K - 1 only emit (one more warp-parallel
+    // step); shallower nodes are searched depth-first; nodes of size K (K == 1)
+    // have nothing left to add
     Level &last = lv.back();
     const bool small = (K <= 12 && umax_need <= 64);
-    if (last.n > 0) {
+    const int final_kind = (depth >= K) ? 0 : (depth == K - 1 ? 1 : 2);
+    if (last.n > 0 && final_kind == 1) {
+        ProfScope ps__(ctx, s, "enum_expand");
+        expand_kernel<<<grid1(last.n, kExpandWarps, ctx->n_sm), 32 * kExpandWarps, 0, s>>>(
+            gv, (const Node *)last.nodes.ptr, last.n, K, mode, 0, nullptr, nullptr, nullptr,
+            (int32_t *)last.counts.ptr, none, nullptr, overflow);
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+    } else if (last.n > 0 && final_kind == 2) {
         if (small)
             {
                 ProfScope ps__(ctx, s, "enum_dfs");
@@ -677,19 +730,19 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
                     ProfScope ps__(ctx, s, "enum_roots");
                     roots_kernel<<<grid1(L.n, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, K, mode, nullptr, nullptr, out, lb, 1, overflow);
                 }
-            if (li + 1 < lv.size())
+            if (li + 1 < lv.size() || final_kind == 1)
                 {
                     ProfScope ps__(ctx, s, "enum_expand");
-                    expand_kernel<<<grid1(L.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)L.nodes.ptr, L.n, K, mode, 2,
+                    expand_kernel<<<grid1(L.n, kExpandWarps, ctx->n_sm), 32 * kExpandWarps, 0, s>>>(gv, (const Node *)L.nodes.ptr, L.n, K, mode, 2,
                                                                         nullptr, nullptr, nullptr, nullptr, out, lb, overflow);
                 }
-            else if (small)
+            else if (final_kind == 2 && small)
                 {
                     ProfScope ps__(ctx, s, "enum_dfs");
                     dfs_kernel<12, 64><<<grid1(L.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)L.nodes.ptr, L.n, K, mode, 1,
                                                                               nullptr, out, lb, overflow);
                 }
-            else
+            else if (final_kind == 2)
                 {
                     ProfScope ps__(ctx, s, "enum_dfs");
                     dfs_kernel<32, 128><<<grid1(L.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)L.nodes.ptr, L.n, K, mode, 1,
