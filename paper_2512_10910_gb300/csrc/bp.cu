@@ -280,23 +280,27 @@ __global__ void __launch_bounds__(kBpWarps * 32) bp_persistent_kernel(BPParams p
             __syncwarp();
         }
         if (!grid_barrier(p.bar, p.flags, nblocks)) return;
-        // convergence bookkeeping (every block reaches the same decision)
+        // convergence bookkeeping: every warp reads the residuals one set per
+        // lane and reaches the same decision; warp 0 of block 0 records
         bool all_done = true;
-        for (int s = 0; s < p.n_sets; ++s) {
-            bool was = p.done_it[s] != 0 ||
-                       (it > 1 && __longlong_as_double((long long)res_prev[s]) < p.tol);
-            if (was) continue;
-            double rs = __longlong_as_double((long long)res_cur[s]);
-            if (rs < p.tol) {
-                if (blockIdx.x == 0 && threadIdx.x == 0) {
-                    p.done_it[s] = it; p.iters_out[s] = it; p.res_out[s] = rs; p.final_buf[s] = dst;
-                }
-            } else {
-                all_done = false;
-                if (it == p.max_iter && blockIdx.x == 0 && threadIdx.x == 0) {
-                    p.iters_out[s] = 0; p.res_out[s] = rs; p.final_buf[s] = dst;
+        const bool recorder = blockIdx.x == 0 && threadIdx.x < 32;
+        for (int s0 = 0; s0 < p.n_sets; s0 += 32) {
+            const int s = s0 + (threadIdx.x & 31);
+            bool pending = false;
+            if (s < p.n_sets) {
+                const bool was = p.done_it[s] != 0 ||
+                                 (it > 1 && __longlong_as_double((long long)res_prev[s]) < p.tol);
+                if (!was) {
+                    const double rs = __longlong_as_double((long long)res_cur[s]);
+                    if (rs < p.tol) {
+                        if (recorder) { p.done_it[s] = it; p.iters_out[s] = it; p.res_out[s] = rs; p.final_buf[s] = dst; }
+                    } else {
+                        pending = true;
+                        if (it == p.max_iter && recorder) { p.iters_out[s] = 0; p.res_out[s] = rs; p.final_buf[s] = dst; }
+                    }
                 }
             }
+            if (__any_sync(0xffffffffu, pending)) all_done = false;
         }
         if (all_done) return;
     }
@@ -560,21 +564,25 @@ __global__ void __launch_bounds__(kBpWarps * 32) bp_ff_kernel(BPFFParams p)
             __syncwarp();
         }
         if (!grid_barrier(p.bar, p.flags, nblocks)) return;
+        // convergence bookkeeping, one set per lane (as in the FP64 kernel)
         bool all_done = true;
-        for (int s = 0; s < p.n_sets; ++s) {
-            const bool was = p.done_it[s] != 0 || (it > 1 && __uint_as_float(res_prev[s]) < p.tol);
-            if (was) continue;
-            const float rs = __uint_as_float(res_cur[s]);
-            if (rs < p.tol) {
-                if (blockIdx.x == 0 && threadIdx.x == 0) {
-                    p.done_it[s] = it; p.iters_out[s] = it; p.res_out[s] = (double)rs; p.final_buf[s] = dst;
-                }
-            } else {
-                all_done = false;
-                if (it == p.max_iter && blockIdx.x == 0 && threadIdx.x == 0) {
-                    p.iters_out[s] = 0; p.res_out[s] = (double)rs; p.final_buf[s] = dst;
+        const bool recorder = blockIdx.x == 0 && threadIdx.x < 32;
+        for (int s0 = 0; s0 < p.n_sets; s0 += 32) {
+            const int s = s0 + lane;
+            bool pending = false;
+            if (s < p.n_sets) {
+                const bool was = p.done_it[s] != 0 || (it > 1 && __uint_as_float(res_prev[s]) < p.tol);
+                if (!was) {
+                    const float rs = __uint_as_float(res_cur[s]);
+                    if (rs < p.tol) {
+                        if (recorder) { p.done_it[s] = it; p.iters_out[s] = it; p.res_out[s] = (double)rs; p.final_buf[s] = dst; }
+                    } else {
+                        pending = true;
+                        if (it == p.max_iter && recorder) { p.iters_out[s] = 0; p.res_out[s] = (double)rs; p.final_buf[s] = dst; }
+                    }
                 }
             }
+            if (__any_sync(0xffffffffu, pending)) all_done = false;
         }
         if (all_done) return;
     }

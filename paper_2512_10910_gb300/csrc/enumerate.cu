@@ -63,26 +63,40 @@ struct Emit {
 };
 
 // Vertex multiset of a bond set, with the number of degree-one vertices.
+// Every loop runs over the fixed capacity NV with a guard on n, so after
+// unrolling all indices are constants and the set lives in registers.
 template <int NV>
 struct VSet {
     int32_t v[NV];
     int32_t d[NV];
     int n = 0;
     int dang = 0;
-    __device__ int find(int x) const {
-        for (int i = 0; i < n; ++i) if (v[i] == x) return i;
-        return -1;
+    __device__ __forceinline__ bool has(int x) const {
+        bool r = false;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) r |= (i < n && v[i] == x);
+        return r;
     }
-    __device__ void inc(int x) {
-        int i = find(x);
-        if (i < 0) { i = n++; v[i] = x; d[i] = 0; }
-        int o = d[i]++;
+    __device__ __forceinline__ void inc(int x) {
+        int o = -1;
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < n && v[i] == x) { o = d[i]; d[i] = o + 1; }
+        if (o < 0) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                if (i == n) { v[i] = x; d[i] = 1; }
+            ++n;
+            o = 0;
+        }
         if (o == 0) ++dang; else if (o == 1) --dang;
     }
-    __device__ void dec(int x) {
-        int i = find(x);
-        int o = d[i]--;
-        if (o == 1) { --dang; --n; }          // the vertex was the last one added
+    __device__ __forceinline__ void dec(int x) {       // x was the last vertex added if its degree drops to 0
+        int o = 0;
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i < n && v[i] == x) { o = d[i]; d[i] = o - 1; }
+        if (o == 1) { --dang; --n; }
         else if (o == 2) ++dang;
     }
 };
@@ -98,7 +112,9 @@ template <int NV>
 __device__ bool repairable(const VSet<NV> &V, const int32_t *UA, const int32_t *UB, int lo, int hi)
 {
     if (V.dang == 0) return true;
-    for (int i = 0; i < V.n; ++i) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        if (i >= V.n) break;
         if (V.d[i] != 1) continue;
         const int x = V.v[i];
         bool found = false;
@@ -120,7 +136,9 @@ __device__ void write_cluster(const Emit &o, int64_t slot, const int32_t *S, int
     }
     for (int i = s; i < o.width; ++i) e[i] = -1;
     int32_t *vv = o.verts + slot * o.vwidth;
-    for (int i = 0; i < V.n; ++i) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        if (i >= V.n) break;
         int x = V.v[i], j = i;
         while (j > 0 && vv[j - 1] > x) { vv[j] = vv[j - 1]; --j; }
         vv[j] = x;
@@ -138,7 +156,7 @@ __device__ int append_new(const GeomView &g, int b, int e, int anchor, const VSe
         const int f = g.site_bonds[p];
         if (f == e || f <= anchor) continue;
         const int c = g.bond_site[2 * f] == b ? g.bond_site[2 * f + 1] : g.bond_site[2 * f];
-        if (V.find(c) >= 0) continue;
+        if (V.has(c)) continue;
         if (ne >= cap) { atomicExch(overflow, 1); return ne; }
         U[ne] = f; UA[ne] = b; UB[ne] = c;
         ++ne;
@@ -199,7 +217,9 @@ __device__ bool repairable_split(const VSet<NV> &V, const int32_t *UA, const int
                                  const int32_t *NA, const int32_t *NB, int nn)
 {
     if (V.dang == 0) return true;
-    for (int i = 0; i < V.n; ++i) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        if (i >= V.n) break;
         if (V.d[i] != 1) continue;
         const int x = V.v[i];
         bool found = false;
@@ -243,7 +263,7 @@ expand_kernel(GeomView g, const Node *nodes, int64_t n_nodes, int K, int mode, i
             if (i < nU) {
                 for (int q = 0; q < t; ++q) { V.inc(g.bond_site[2 * nd.S[q]]); V.inc(g.bond_site[2 * nd.S[q] + 1]); }
                 const int e = nd.U[i], a0 = UA[i], a1 = UB[i];
-                const int b = V.find(a0) < 0 ? a0 : (V.find(a1) < 0 ? a1 : -1);
+                const int b = !V.has(a0) ? a0 : (!V.has(a1) ? a1 : -1);
                 V.inc(a0); V.inc(a1);
                 emit = valid_set(mode, V.dang);
                 if (may_grow(mode, t + 1, K, V.dang)) {
@@ -322,7 +342,7 @@ __global__ void __launch_bounds__(128) dfs_kernel(GeomView g, const Node *nodes,
             }
             const int e = U[pos[lvl]];
             const int a0 = g.bond_site[2 * e], a1 = g.bond_site[2 * e + 1];
-            const int b = V.find(a0) < 0 ? a0 : (V.find(a1) < 0 ? a1 : -1);
+            const int b = !V.has(a0) ? a0 : (!V.has(a1) ? a1 : -1);
             V.inc(a0); V.inc(a1);
             S[s++] = e;
             if (valid_set(mode, V.dang)) {
@@ -349,29 +369,91 @@ __global__ void __launch_bounds__(128) dfs_kernel(GeomView g, const Node *nodes,
 }
 
 // ---------------------------------------------------------------- scan
-constexpr int kScanBlock = 1024;
+// Exclusive prefix sums of int32 or int64 tables into int64.  A tile is 8192
+// values scanned by one block of 1024 threads: warp w owns kScanItems
+// consecutive rows of 32 values, lane l column l, so loads and stores are
+// coalesced; all loads of a tile are issued before the first shuffle, rows are
+// scanned across lanes and chained through the last lane, and the warp totals
+// are scanned by warp 0.  Small tables are scanned by one block walking the
+// tiles with a running carry (one launch); larger ones by one block per tile,
+// a scan of the tile totals, and an add pass.  `in` may alias `out`.
+constexpr int kScanItems = 8;
+constexpr int kScanTile = 1024 * kScanItems;
+constexpr int64_t kOneBlockTiles = 4;
 
-__global__ void scan_block_kernel(int64_t *data, int64_t n, int64_t *block_sums)
+template <typename T>
+__device__ __forceinline__ int64_t tile_scan(const T *in, int64_t *out, int64_t n, int64_t t0, int64_t carry,
+                                             int64_t *wsum /* shared [32] */)
 {
-    __shared__ int64_t sh[kScanBlock];
-    const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    int64_t x = (i < n) ? data[i] : 0;
-    sh[threadIdx.x] = x;
-    __syncthreads();
-    for (int off = 1; off < kScanBlock; off <<= 1) {
-        int64_t y = (threadIdx.x >= (unsigned)off) ? sh[threadIdx.x - off] : 0;
-        __syncthreads();
-        sh[threadIdx.x] += y;
-        __syncthreads();
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t b = t0 + (int64_t)wid * (32 * kScanItems) + lane;
+    int64_t v[kScanItems], x[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t at = b + 32 * k;
+        v[k] = (at < n) ? (int64_t)in[at] : 0;
     }
-    if (i < n) data[i] = sh[threadIdx.x] - x;       // exclusive
-    if (threadIdx.x == kScanBlock - 1) block_sums[blockIdx.x] = sh[threadIdx.x];
+    int64_t run = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t y = v[k];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t z = __shfl_up_sync(0xffffffffu, y, off);
+            if (lane >= off) y += z;
+        }
+        x[k] = run + y - v[k];
+        run += __shfl_sync(0xffffffffu, y, 31);
+    }
+    if (lane == 0) wsum[wid] = run;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t ws = wsum[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t z = __shfl_up_sync(0xffffffffu, ws, off);
+            if (lane >= off) ws += z;
+        }
+        wsum[lane] = ws;
+    }
+    __syncthreads();
+    const int64_t before = carry + (wid > 0 ? wsum[wid - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t at = b + 32 * k;
+        if (at < n) out[at] = before + x[k];
+    }
+    const int64_t total = wsum[31];
+    __syncthreads();
+    return total;
 }
 
-__global__ void scan_add_kernel(int64_t *data, int64_t n, const int64_t *block_offsets)
+template <typename T>
+__global__ void __launch_bounds__(1024) scan_one_block_kernel(const T *in, int64_t *out, int64_t n, int64_t *total)
 {
-    const int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    if (i < n) data[i] += block_offsets[blockIdx.x];
+    __shared__ int64_t wsum[32];
+    int64_t carry = 0;
+    for (int64_t t0 = 0; t0 < n; t0 += kScanTile) carry += tile_scan(in, out, n, t0, carry, wsum);
+    if (threadIdx.x == 0) *total = carry;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) scan_tiles_kernel(const T *in, int64_t *out, int64_t n, int64_t *tile_sums)
+{
+    __shared__ int64_t wsum[32];
+    const int64_t t = tile_scan(in, out, n, (int64_t)blockIdx.x * kScanTile, 0, wsum);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(1024) scan_add_tiles_kernel(int64_t *out, int64_t n, const int64_t *tile_off)
+{
+    const int64_t add = tile_off[blockIdx.x];
+    const int64_t b = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t at = b + 1024 * k;
+        if (at < n) out[at] += add;
+    }
 }
 
 // starts[r] = scanned[r * cols] (or the total at r == rows), one thread per row
@@ -384,11 +466,6 @@ __global__ void row_starts_kernel(const int64_t *scanned, int rows, int64_t cols
     starts[r] = (r == rows || at >= n) ? *total : scanned[at];
 }
 
-__global__ void widen_kernel(const int32_t *src, int64_t *dst, int64_t n)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = src[i];
-}
 
 // ---------------------------------------------------------------- tuples
 struct TupleParams {
@@ -433,10 +510,22 @@ __global__ void tuple_chunks_kernel(TupleParams p, int64_t *n_chunks)
     }
 }
 
-__global__ void tuple_kernel(TupleParams p, int write)
+// One warp per unit (an input tuple and a chunk of up to kTupleChunk candidate
+// clusters), one lane per candidate.  A candidate's order is the tuple's order
+// plus its size; lanes with the same order are ranked by __match_any_sync, and
+// the per-order running counts of the warp sit in shared memory, so the output
+// keeps candidate order within every (order, unit) slot range.
+constexpr int kTupleWarps = 4;
+
+__global__ void __launch_bounds__(32 * kTupleWarps) tuple_kernel(TupleParams p, int write)
 {
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < p.n_units;
-         u += (int64_t)gridDim.x * blockDim.x) {
+    extern __shared__ int32_t tsh[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int tv_words = p.m * p.vwidth;
+    int32_t *tv = tsh + w * (tv_words + kMaxOrder + 1);     // the tuple's sorted vertex lists
+    int32_t *cnt = tv + tv_words;                            // [K+1] running counts per order
+    for (int64_t u = (int64_t)blockIdx.x * kTupleWarps + w; u < p.n_units; u += (int64_t)gridDim.x * kTupleWarps) {
         // locate the input tuple of this unit (binary search in unit_off)
         int64_t lo = 0, hi = p.n_in;
         while (hi - lo > 1) {
@@ -448,33 +537,39 @@ __global__ void tuple_kernel(TupleParams p, int write)
         const int32_t *tp = p.in + t * p.m;
         const int last = tp[p.m - 1];
         const int o = p.in_order[t];
+        for (int q = lane; q < tv_words; q += 32) tv[q] = p.verts[(int64_t)tp[q / p.vwidth] * p.vwidth + q % p.vwidth];
+        for (int q = lane; q <= p.K; q += 32) cnt[q] = 0;
+        __syncwarp();
         const int64_t j0 = (int64_t)last + 1 + chunk * kTupleChunk;
         int64_t j1 = p.size_end[p.K - o];
         if (j1 > j0 + kTupleChunk) j1 = j0 + kTupleChunk;
-        int32_t cnt[kMaxOrder + 1];
-        int64_t slot[kMaxOrder + 1];
-        for (int q = 0; q <= p.K; ++q) {
-            cnt[q] = 0;
-            slot[q] = write ? p.base[(int64_t)q * p.n_units + u] : 0;
-        }
-        for (int64_t j = j0; j < j1; ++j) {
-            const int32_t *vj = p.verts + j * p.vwidth;
-            bool ok = true;
-            for (int q = 0; q < p.m && ok; ++q) ok = disjoint_sorted(p.verts + (int64_t)tp[q] * p.vwidth, vj, p.vwidth);
-            if (!ok) continue;
-            const int ord = o + p.size[j];
-            if (write) {
-                const int64_t s = slot[ord]++;
-                int32_t *dst = p.out + s * (p.m + 1);
-                for (int q = 0; q < p.m; ++q) dst[q] = tp[q];
-                dst[p.m] = (int32_t)j;
-                p.out_order[s] = ord;
-            } else {
-                ++cnt[ord];
+        for (int64_t jb = j0; jb < j1; jb += 32) {
+            const int64_t j = jb + lane;
+            bool ok = j < j1;
+            int ord = -1;
+            if (ok) {
+                const int32_t *vj = p.verts + j * p.vwidth;
+                for (int q = 0; q < p.m && ok; ++q) ok = disjoint_sorted(tv + q * p.vwidth, vj, p.vwidth);
+                if (ok) ord = o + p.size[j];
             }
+            const unsigned same = __match_any_sync(0xffffffffu, ord);
+            const int before = ok ? cnt[ord] : 0;
+            __syncwarp();
+            if (ok) {
+                if (write) {
+                    const int64_t sl = p.base[(int64_t)ord * p.n_units + u] + before + __popc(same & lt);
+                    int32_t *dst = p.out + sl * (p.m + 1);
+                    for (int q = 0; q < p.m; ++q) dst[q] = tp[q];
+                    dst[p.m] = (int32_t)j;
+                    p.out_order[sl] = ord;
+                }
+                if ((same & lt) == 0) cnt[ord] = before + __popc(same);   // group leader
+            }
+            __syncwarp();
         }
         if (!write)
-            for (int q = 0; q <= p.K; ++q) p.counts[(int64_t)q * p.n_units + u] = cnt[q];
+            for (int q = lane; q <= p.K; q += 32) p.counts[(int64_t)q * p.n_units + u] = cnt[q];
+        __syncwarp();
     }
 }
 
@@ -496,33 +591,47 @@ int grid1(int64_t n, int block, int n_sm)
 
 }  // namespace
 
+namespace {
+
+template <typename T>
+pne_status scan_to(pne_ctx *ctx, const T *src, int64_t *dst, int64_t n, int64_t *d_total, cudaStream_t s)
+{
+    if (n <= 0) { PNE_CUDA_TRY(ctx, cudaMemsetAsync(d_total, 0, 8, s)); return PNE_OK; }
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb <= kOneBlockTiles) {
+        {
+            ProfScope ps__(ctx, s, "scan");
+            scan_one_block_kernel<T><<<1, 1024, 0, s>>>(src, dst, n, d_total);
+        }
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+        return PNE_OK;
+    }
+    DevBuf sums;
+    pne_status st = dev_alloc(ctx, sums, (size_t)nb * 8, s);
+    if (st) return st;
+    int64_t *ts = (int64_t *)sums.ptr;
+    {
+        ProfScope ps__(ctx, s, "scan");
+        scan_tiles_kernel<T><<<(unsigned)nb, 1024, 0, s>>>(src, dst, n, ts);
+    }
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    if ((st = scan_to<int64_t>(ctx, ts, ts, nb, d_total, s))) { dev_free(ctx, sums, s); return st; }
+    {
+        ProfScope ps__(ctx, s, "scan");
+        scan_add_tiles_kernel<<<(unsigned)nb, 1024, 0, s>>>(dst, n, ts);
+    }
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    dev_free(ctx, sums, s);
+    return PNE_OK;
+}
+
+}  // namespace
+
 // exclusive scan (in place) of n int64 values; the total is written to d_total
 // on the device (no synchronisation)
 pne_status device_exclusive_scan_to(pne_ctx *ctx, int64_t *d, int64_t n, int64_t *d_total, cudaStream_t s)
 {
-    if (n == 0) { PNE_CUDA_TRY(ctx, cudaMemsetAsync(d_total, 0, 8, s)); return PNE_OK; }
-    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
-    DevBuf sums;
-    pne_status st = dev_alloc(ctx, sums, (size_t)(nb + 1) * 8, s);
-    if (st) return st;
-    int64_t *bs = (int64_t *)sums.ptr;
-    {
-        ProfScope ps__(ctx, s, "scan");
-        scan_block_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(d, n, bs);
-    }
-    PNE_CUDA_TRY(ctx, cudaGetLastError());
-    if (nb > 1) {
-        if ((st = device_exclusive_scan_to(ctx, bs, nb, d_total, s))) { dev_free(ctx, sums, s); return st; }
-        {
-            ProfScope ps__(ctx, s, "scan");
-            scan_add_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(d, n, bs);
-        }
-        PNE_CUDA_TRY(ctx, cudaGetLastError());
-    } else {
-        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(d_total, bs, 8, cudaMemcpyDeviceToDevice, s));
-    }
-    dev_free(ctx, sums, s);
-    return PNE_OK;
+    return scan_to<int64_t>(ctx, d, d, n, d_total, s);
 }
 
 // exclusive scan (in place) of n int64 values; the total is returned on the host
@@ -543,6 +652,12 @@ pne_status device_exclusive_scan(pne_ctx *ctx, int64_t *d, int64_t n, int64_t *h
 
 namespace {
 
+// exclusive scan of n int32 counts into int64 dst; the total lands in d_total
+pne_status scan_i32_to(pne_ctx *ctx, const int32_t *src, int64_t *dst, int64_t n, int64_t *d_total, cudaStream_t s)
+{
+    return scan_to<int32_t>(ctx, src, dst, n, d_total, s);
+}
+
 // counts [rows][cols] int32 -> base (exclusive scan, row-major) int64; per-row totals
 // (the row starts are gathered on the device and read back in one copy)
 pne_status scan_counts(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t cols, DevBuf &base,
@@ -554,20 +669,14 @@ pne_status scan_counts(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t 
     int64_t *b = (int64_t *)base.ptr;
     int64_t *starts = b + std::max<int64_t>(n, 1);          // [rows + 1]
     int64_t *tot = starts + rows + 1;                       // [1]
-    if (n > 0) {
-        ProfScope ps__(ctx, s, "scan");
-        widen_kernel<<<grid1(n, 256, ctx->n_sm), 256, 0, s>>>(d_counts, b, n);
-    }
     // exclusive scan; its total lands in tot
-    int64_t total = 0;
-    if ((st = device_exclusive_scan_to(ctx, b, n, tot, s))) return st;
+    if ((st = scan_i32_to(ctx, d_counts, b, n, tot, s))) return st;
     row_starts_kernel<<<(rows + 1 + 127) / 128, 128, 0, s>>>(b, rows, cols, n, starts, tot);
     PNE_CUDA_TRY(ctx, cudaGetLastError());
     std::vector<int64_t> h(rows + 1, 0);
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(pinned_i64(ctx, rows + 1), starts, (rows + 1) * 8, cudaMemcpyDeviceToHost, s));
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     std::memcpy(h.data(), pinned_i64(ctx, rows + 1), (rows + 1) * 8);
-    (void)total;
     row_tot.assign(rows, 0);
     for (int r = 0; r < rows; ++r) row_tot[r] = h[r + 1] - h[r];
     return PNE_OK;
@@ -627,12 +736,12 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         PNE_CUDA_TRY(ctx, cudaGetLastError());
         DevBuf coff;
         if ((st = dev_alloc(ctx, coff, (size_t)(cur.n + 1) * 8, s))) return st;
-        {
-            ProfScope ps__(ctx, s, "scan");
-            widen_kernel<<<grid1(cur.n, 256, ctx->n_sm), 256, 0, s>>>(child_count, (int64_t *)coff.ptr, cur.n);
-        }
-        int64_t n_child = 0;
-        if ((st = device_exclusive_scan(ctx, (int64_t *)coff.ptr, cur.n, &n_child, s))) return st;
+        int64_t *d_n_child = (int64_t *)coff.ptr + cur.n;
+        if ((st = scan_i32_to(ctx, child_count, (int64_t *)coff.ptr, cur.n, d_n_child, s))) return st;
+        int64_t *h_n_child = pinned_i64(ctx, 1);
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_n_child, d_n_child, 8, cudaMemcpyDeviceToHost, s));
+        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        const int64_t n_child = *h_n_child;
         if (n_child > kNodeCap) {             // too wide: search depth-first from this level
             dev_free(ctx, cc, s);
             dev_free(ctx, coff, s);
@@ -808,6 +917,7 @@ pne_status enumerate_tuples(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s)
         int64_t n_units = 0;
         if ((st = device_exclusive_scan(ctx, (int64_t *)uoff.ptr, n_in, &n_units, s))) return st;
         p.unit_off = (const int64_t *)uoff.ptr; p.n_units = n_units;
+        const size_t tsmem = (size_t)kTupleWarps * (m * rec.vwidth + kMaxOrder + 1) * 4;
         EnumRecord::Level L;
         L.m = m + 1;
         L.order_start.assign(K + 2, 0);
@@ -818,7 +928,7 @@ pne_status enumerate_tuples(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s)
             p.counts = (int32_t *)counts.ptr;
             {
                 ProfScope ps__(ctx, s, "enum_terms");
-                tuple_kernel<<<grid1(n_units, 128, ctx->n_sm), 128, 0, s>>>(p, 0);
+                tuple_kernel<<<grid1(n_units, kTupleWarps, ctx->n_sm), 32 * kTupleWarps, tsmem, s>>>(p, 0);
             }
             PNE_CUDA_TRY(ctx, cudaGetLastError());
             if ((st = scan_counts(ctx, (const int32_t *)counts.ptr, K + 1, n_units, base, per_order, s))) return st;
@@ -834,7 +944,7 @@ pne_status enumerate_tuples(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s)
             p.out = (int32_t *)L.idx.ptr; p.out_order = (int32_t *)out_ord.ptr;
             {
                 ProfScope ps__(ctx, s, "enum_terms");
-                tuple_kernel<<<grid1(n_units, 128, ctx->n_sm), 128, 0, s>>>(p, 1);
+                tuple_kernel<<<grid1(n_units, kTupleWarps, ctx->n_sm), 32 * kTupleWarps, tsmem, s>>>(p, 1);
             }
             PNE_CUDA_TRY(ctx, cudaGetLastError());
         }

@@ -422,7 +422,14 @@ def network_struct(net, data=None, n_batch=1, data_on_device=False):
 
 
 def _offsets(net):
-    sizes = [int(np.prod(net.leg_dims(v))) for v in range(net.n_sites)]
+    """Per-site tensor sizes (product of the leg dimensions) and their offsets,
+    vectorised: one segmented product over the CSR legs."""
+    ptr = np.asarray(net.site_ptr, dtype=np.int64)
+    dims = np.asarray(net.bond_dim, dtype=np.int64)[np.asarray(net.site_bonds, dtype=np.int64)]
+    sizes = np.ones(net.n_sites, dtype=np.int64)
+    nonempty = np.diff(ptr) > 0
+    if dims.size:
+        sizes[nonempty] = np.multiply.reduceat(dims, ptr[:-1][nonempty])
     off = np.zeros(net.n_sites + 1, dtype=np.int64)
     off[1:] = np.cumsum(sizes)
     return sizes, off

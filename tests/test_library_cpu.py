@@ -51,3 +51,21 @@ def test_struct_layouts():
     assert ctypes.sizeof(pne.Network) == 8 + 4 * 8 + 8 + 8 + 8
     assert ctypes.sizeof(pne.PartitionOpts) == 32
     assert ctypes.sizeof(pne.EnumOpts) == 12
+
+
+def test_tensor_offsets_match_per_site_leg_products():
+    # the binding packs data_off from a segmented product over the CSR legs;
+    # it must equal the per-site product of leg dimensions, including sites
+    # without legs and open legs
+    import numpy as np
+    from paper_2512_10910_gb300 import inputs as I
+    graphs = [I.square_lattice(6, 5, 3), I.cubic_lattice(3, 3, 3, 2), I.grid_graph(1, [], []),
+              I.grid_graph(4, [(0, 1), (1, 2)], [2, 5]),          # site 3 has no legs
+              I.grid_graph(5, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 2), (0, 1), (3, 1)],
+                           [2, 3, 2, 2, 3, 2, 2, 3]),
+              I.with_open_legs(I.square_lattice(3, 3, 2), [(0, 3), (4, 2)])]
+    for g in graphs:
+        sizes, off = pne._offsets(g)
+        want = [int(np.prod(g.leg_dims(v))) for v in range(g.n_sites)]
+        assert list(sizes) == want
+        assert off[0] == 0 and list(np.diff(off)) == want
