@@ -51,6 +51,8 @@ struct BPParams {
     int32_t *final_buf;           // [n_sets]
     int32_t *flags;               // [0] barrier timeout, [1] degenerate message
     unsigned int *bar;            // [0] count, [1] generation
+    int n_colors;                 // > 0: colour-ordered sweeps, in place; 0: Jacobi, two buffers
+    const int32_t *color_ptr, *color_sites;
     int smem_per_warp;            // doubles
     int tabA, tabC;               // table sizes (max over sites)
 };
@@ -200,14 +202,15 @@ __global__ void __launch_bounds__(kBpWarps * 32) bp_persistent_kernel(BPParams p
     double *x1 = w + p.tabC;
     double *x2 = x1 + p.tabA;
     const unsigned int nblocks = gridDim.x;
-    const int64_t items = (int64_t)p.n_sets * p.n_sites;
     const int64_t gwarp = (int64_t)blockIdx.x * kBpWarps + wib;
     const int64_t nwarps = (int64_t)nblocks * kBpWarps;
     const int64_t msg_set = (int64_t)p.n_legs * kMsgStride;
     const int64_t msg_buf = (int64_t)p.n_sets * msg_set;
+    const bool colored = p.n_colors > 0;
+    const int phases = colored ? p.n_colors : 1;
 
     for (int it = 1; it <= p.max_iter; ++it) {
-        const int src = (it - 1) & 1, dst = it & 1;
+        const int src = colored ? 0 : (it - 1) & 1, dst = colored ? 0 : it & 1;
         // Slots it%4 (this sweep) and (it-1)%4 are live here; a slower block may
         // still read (it-2)%4 in its bookkeeping of the previous sweep.  Slot
         // (it+1)%4 was last read before the previous barrier: clear it now.
@@ -217,8 +220,13 @@ __global__ void __launch_bounds__(kBpWarps * 32) bp_persistent_kernel(BPParams p
             unsigned long long *res_next = p.res + (int64_t)((it + 1) % 4) * p.n_sets;
             for (int s = threadIdx.x; s < p.n_sets; s += blockDim.x) res_next[s] = 0ull;
         }
+        for (int ph = 0; ph < phases; ++ph) {
+        const int c0 = colored ? p.color_ptr[ph] : 0;
+        const int nc = colored ? p.color_ptr[ph + 1] - c0 : p.n_sites;
+        const int64_t items = (int64_t)p.n_sets * nc;
         for (int64_t item = gwarp; item < items; item += nwarps) {
-            const int set = (int)(item / p.n_sites), v = (int)(item % p.n_sites);
+            const int set = (int)(item / nc), q = (int)(item % nc);
+            const int v = colored ? p.color_sites[c0 + q] : q;
             if (p.done_it[set] != 0) continue;
             if (it > 1 && __longlong_as_double((long long)res_prev[set]) < p.tol) continue;
             const int l0 = p.site_ptr[v], k = p.site_ptr[v + 1] - l0;
@@ -278,6 +286,8 @@ __global__ void __launch_bounds__(kBpWarps * 32) bp_persistent_kernel(BPParams p
             for (int off = 16; off > 0; off >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, off));
             if (lane == 0) atomicMax(res_cur + set, (unsigned long long)__double_as_longlong(r));
             __syncwarp();
+        }
+        if (ph + 1 < phases && !grid_barrier(p.bar, p.flags, nblocks)) return;
         }
         if (!grid_barrier(p.bar, p.flags, nblocks)) return;
         // convergence bookkeeping: every warp reads the residuals one set per
@@ -390,6 +400,8 @@ struct BPFFParams {
     int32_t *done_it, *iters_out, *final_buf, *flags;
     double *res_out;
     unsigned int *bar;
+    int n_colors;                 // as in BPParams
+    const int32_t *color_ptr, *color_sites;
     int smem_per_warp;            // ff entries
     int tabA, tabC;
 };
@@ -488,19 +500,25 @@ __global__ void __launch_bounds__(kBpWarps * 32) bp_ff_kernel(BPFFParams p)
     ff *x1 = w + p.tabC;
     ff *x2 = x1 + p.tabA;
     const unsigned int nblocks = gridDim.x;
-    const int64_t items = (int64_t)p.n_sets * p.n_sites;
     const int64_t gwarp = (int64_t)blockIdx.x * kBpWarps + wib, nwarps = (int64_t)nblocks * kBpWarps;
     const int64_t msg_set = (int64_t)p.n_legs * kMsgStride, msg_buf = (int64_t)p.n_sets * msg_set;
+    const bool colored = p.n_colors > 0;
+    const int phases = colored ? p.n_colors : 1;
     for (int it = 1; it <= p.max_iter; ++it) {
-        const int src = (it - 1) & 1, dst = it & 1;
+        const int src = colored ? 0 : (it - 1) & 1, dst = colored ? 0 : it & 1;
         unsigned int *res_cur = p.res + (int64_t)(it % 4) * p.n_sets;
         unsigned int *res_prev = p.res + (int64_t)((it + 3) % 4) * p.n_sets;
         if (blockIdx.x == 0) {
             unsigned int *res_next = p.res + (int64_t)((it + 1) % 4) * p.n_sets;
             for (int s = threadIdx.x; s < p.n_sets; s += blockDim.x) res_next[s] = 0u;
         }
+        for (int ph = 0; ph < phases; ++ph) {
+        const int c0 = colored ? p.color_ptr[ph] : 0;
+        const int nc = colored ? p.color_ptr[ph + 1] - c0 : p.n_sites;
+        const int64_t items = (int64_t)p.n_sets * nc;
         for (int64_t item = gwarp; item < items; item += nwarps) {
-            const int set = (int)(item / p.n_sites), v = (int)(item % p.n_sites);
+            const int set = (int)(item / nc), q = (int)(item % nc);
+            const int v = colored ? p.color_sites[c0 + q] : q;
             if (p.done_it[set] != 0) continue;
             if (it > 1 && __uint_as_float(res_prev[set]) < p.tol) continue;
             const int l0 = p.site_ptr[v], k = p.site_ptr[v + 1] - l0;
@@ -562,6 +580,8 @@ __global__ void __launch_bounds__(kBpWarps * 32) bp_ff_kernel(BPFFParams p)
             for (int off = 16; off > 0; off >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
             if (lane == 0) atomicMax(res_cur + set, __float_as_uint(r));
             __syncwarp();
+        }
+        if (ph + 1 < phases && !grid_barrier(p.bar, p.flags, nblocks)) return;
         }
         if (!grid_barrier(p.bar, p.flags, nblocks)) return;
         // convergence bookkeeping, one set per lane (as in the FP64 kernel)
@@ -927,6 +947,7 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         fp.res = (unsigned int *)res; fp.done_it = done; fp.iters_out = iters; fp.final_buf = finalb;
         fp.flags = flags; fp.res_out = res_out; fp.bar = bar;
         fp.smem_per_warp = per_warp; fp.tabA = tabA; fp.tabC = tabC;
+        fp.n_colors = g.n_colors; fp.color_ptr = g.d_color_ptr; fp.color_sites = g.d_color_sites;
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(bp_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm_ff = 0;
@@ -965,6 +986,7 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
     prm.res = res; prm.done_it = done; prm.iters_out = iters; prm.res_out = res_out;
     prm.final_buf = finalb; prm.flags = flags; prm.bar = bar;
     prm.smem_per_warp = per_warp; prm.tabA = tabA; prm.tabC = tabC;
+    prm.n_colors = g.n_colors; prm.color_ptr = g.d_color_ptr; prm.color_sites = g.d_color_sites;
 
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(bp_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1287,6 +1309,7 @@ extern "C" pne_status pne_bp_messages_noalloc(const pne_network *net, double tol
     prm.res = res; prm.done_it = done; prm.iters_out = iters; prm.res_out = res_out;
     prm.final_buf = finalb; prm.flags = flags; prm.bar = bar;
     prm.smem_per_warp = per_warp; prm.tabA = tabA; prm.tabC = tabC;
+    prm.n_colors = 0; prm.color_ptr = nullptr; prm.color_sites = nullptr;   // Jacobi sweeps, two buffers
     if (smem > 48 * 1024)
         PNE_CUDA_TRY(nullptr, cudaFuncSetAttribute(bp_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;

@@ -157,6 +157,35 @@ pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
             off += sz;
         }
     }
+    // greedy colouring in site order over the closed bonds: every site takes the
+    // smallest colour none of its earlier neighbours has (a checkerboard on
+    // the square and cubic lattices)
+    {
+        std::vector<int32_t> col(N, -1);
+        std::vector<char> used;
+        int nc = 0;
+        for (int v = 0; v < N; ++v) {
+            used.assign(nc + 1, 0);
+            for (int i = g.site_ptr[v]; i < g.site_ptr[v + 1]; ++i) {
+                const int b = g.site_bonds[i];
+                const int s0 = g.bond_site[2 * b], s1 = g.bond_site[2 * b + 1];
+                if (s1 < 0) continue;
+                const int u = (s0 == v) ? s1 : s0;
+                if (col[u] >= 0) used[col[u]] = 1;
+            }
+            int c = 0;
+            while (used[c]) ++c;
+            col[v] = c;
+            nc = std::max(nc, c + 1);
+        }
+        g.n_colors = nc;
+        g.color_ptr.assign(nc + 1, 0);
+        for (int v = 0; v < N; ++v) ++g.color_ptr[col[v] + 1];
+        for (int c = 0; c < nc; ++c) g.color_ptr[c + 1] += g.color_ptr[c];
+        g.color_sites.assign(N, 0);
+        std::vector<int32_t> fill(g.color_ptr.begin(), g.color_ptr.end() - 1);
+        for (int v = 0; v < N; ++v) g.color_sites[fill[col[v]]++] = v;
+    }
     uint64_t h = 1469598103934665603ull;
     h = fnv(h, &N, sizeof N);
     h = fnv(h, g.bond_site.data(), g.bond_site.size() * 4);
@@ -164,7 +193,8 @@ pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
     g.hash = h;
     // one device buffer for every table
     const size_t n_i32 = g.bond_site.size() + g.bond_dim.size() + g.site_ptr.size() + g.site_bonds.size() +
-                         g.bond_leg.size() + g.inc_slot.size() + g.blk_off.size();
+                         g.bond_leg.size() + g.inc_slot.size() + g.blk_off.size() + g.color_ptr.size() +
+                         g.color_sites.size();
     const size_t bytes = g.tens_off.size() * 8 + n_i32 * 4 + 64;
     pne_status st = dev_alloc(ctx, g.storage, bytes, s);
     if (st) return st;
@@ -179,6 +209,8 @@ pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
     const size_t o_bl = put(g.bond_leg.data(), g.bond_leg.size() * 4);
     const size_t o_is = put(g.inc_slot.data(), g.inc_slot.size() * 4);
     const size_t o_bo = put(g.blk_off.data(), g.blk_off.size() * 4);
+    const size_t o_cp = put(g.color_ptr.data(), g.color_ptr.size() * 4);
+    const size_t o_cs = put(g.color_sites.data(), g.color_sites.size() * 4);
     char *d = (char *)g.storage.ptr;
     g.d_tens_off = (int64_t *)(d + o_tens);
     g.d_bond_site = (int32_t *)(d + o_bs);
@@ -188,6 +220,8 @@ pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
     g.d_bond_leg = (int32_t *)(d + o_bl);
     g.d_inc_slot = (int32_t *)(d + o_is);
     g.d_blk_off = (int32_t *)(d + o_bo);
+    g.d_color_ptr = (int32_t *)(d + o_cp);
+    g.d_color_sites = (int32_t *)(d + o_cs);
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(g.storage.ptr, host.data(), bytes, cudaMemcpyHostToDevice, s));
     // the host copy must stay alive until the copy ran
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));

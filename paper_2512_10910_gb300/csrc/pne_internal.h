@@ -74,12 +74,15 @@ struct Geometry {
     std::vector<int32_t> inc_slot;      // [n_legs] slot whose message arrives here
     std::vector<int64_t> tens_off;      // [n_sites+1] row-major tensor offsets
     std::vector<int32_t> blk_off;       // [n_sites][64] excitation-block offsets
+    std::vector<int32_t> color_ptr;     // [n_colors+1] proper colouring of the sites (closed bonds)
+    std::vector<int32_t> color_sites;   // [n_sites] sites grouped by colour, ascending within a colour
+    int n_colors = 0;
     int max_deg = 0, max_dim = 0;
     uint64_t hash = 0;
     // device mirrors
     int32_t *d_bond_site = nullptr, *d_bond_dim = nullptr, *d_site_ptr = nullptr,
             *d_site_bonds = nullptr, *d_bond_leg = nullptr, *d_inc_slot = nullptr,
-            *d_blk_off = nullptr;
+            *d_blk_off = nullptr, *d_color_ptr = nullptr, *d_color_sites = nullptr;
     int64_t *d_tens_off = nullptr;
     DevBuf storage;
 };
