@@ -40,14 +40,21 @@ namespace {
 
 constexpr int kPrefixMax = 8;     // deepest prefix level kept as explicit nodes
 constexpr int kNodeU = 48;        // candidate-list capacity of a prefix node
-constexpr int64_t kPrefixTarget = 1 << 20;  // expand breadth-first while a level is smaller
-constexpr int64_t kNodeCap = 1 << 22;       // never materialise a larger level
+constexpr int64_t kArenaFirst = 1 << 16;    // arena size of a first search (nodes), grown on demand
+constexpr int64_t kNodeCap = 1 << 22;       // largest arena; beyond it the deepest level that fits is searched depth-first
 
+constexpr int kNodeV = kPrefixMax + 2;   // vertex capacity of S plus one bond
+
+// A node of the search tree: the set S (t bonds), its candidate list U, and the
+// vertex multiset of S (vertices, C-degrees, count, degree-one count), so a
+// child's multiset is its parent's plus the endpoints of one bond.
 struct Node {
     int32_t S[kPrefixMax];
     int32_t U[kNodeU];
     int32_t nU;
     int32_t t;
+    int32_t vn, vdang;
+    int32_t vv[kNodeV], vd[kNodeV];
 };
 
 struct GeomView {
@@ -100,6 +107,22 @@ struct VSet {
         else if (o == 2) ++dang;
     }
 };
+
+template <int NV>
+__device__ __forceinline__ void load_vset(VSet<NV> &V, const Node &nd)
+{
+    V.n = nd.vn; V.dang = nd.vdang;
+#pragma unroll
+    for (int i = 0; i < (NV < kNodeV ? NV : kNodeV); ++i) { V.v[i] = nd.vv[i]; V.d[i] = nd.vd[i]; }
+}
+
+template <int NV>
+__device__ __forceinline__ void store_vset(Node *nd, const VSet<NV> &V)
+{
+    nd->vn = V.n; nd->vdang = V.dang;
+#pragma unroll
+    for (int i = 0; i < (NV < kNodeV ? NV : kNodeV); ++i) { nd->vv[i] = V.v[i]; nd->vd[i] = V.d[i]; }
+}
 
 __device__ __forceinline__ bool valid_set(int mode, int dang) { return mode == PNE_MODE_ALL || dang == 0; }
 __device__ __forceinline__ bool may_grow(int mode, int s, int K, int dang)
@@ -164,10 +187,147 @@ __device__ int append_new(const GeomView &g, int b, int e, int anchor, const VSe
     return ne;
 }
 
+// ---------------------------------------------------------------- scan
+// Exclusive prefix sums of int32 or int64 values into int64.  A tile is
+// THREADS * kScanItems values scanned by one block: warp w owns kScanItems
+// consecutive rows of 32 values, lane l column l, so loads and stores are
+// coalesced; all loads of a tile are issued before the first shuffle, rows are
+// scanned across lanes and chained through the last lane, and the warp totals
+// are scanned by warp 0.  Small tables are scanned by one block walking the
+// tiles with a running carry (one launch); larger ones by one block per tile,
+// a scan of the tile totals, and an add pass.  `in` may alias `out`.
+constexpr int kScanItems = 8;
+constexpr int kScanTile = 1024 * kScanItems;
+constexpr int64_t kOneBlockTiles = 4;
+
+template <int THREADS, typename T>
+__device__ __forceinline__ int64_t tile_scan(const T *in, int64_t *out, int64_t n, int64_t t0, int64_t carry,
+                                             int64_t *wsum /* shared [THREADS / 32] */)
+{
+    constexpr int W = THREADS / 32;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t b = t0 + (int64_t)wid * (32 * kScanItems) + lane;
+    int64_t v[kScanItems], x[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t at = b + 32 * k;
+        v[k] = (at < n) ? (int64_t)in[at] : 0;
+    }
+    int64_t run = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t y = v[k];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t z = __shfl_up_sync(0xffffffffu, y, off);
+            if (lane >= off) y += z;
+        }
+        x[k] = run + y - v[k];
+        run += __shfl_sync(0xffffffffu, y, 31);
+    }
+    if (lane == 0) wsum[wid] = run;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t ws = (lane < W) ? wsum[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t z = __shfl_up_sync(0xffffffffu, ws, off);
+            if (lane >= off) ws += z;
+        }
+        if (lane < W) wsum[lane] = ws;
+    }
+    __syncthreads();
+    const int64_t before = carry + (wid > 0 ? wsum[wid - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t at = b + 32 * k;
+        if (at < n) out[at] = before + x[k];
+    }
+    const int64_t total = wsum[W - 1];
+    __syncthreads();
+    return total;
+}
+
+// exclusive scan of in[0, n) by the whole block, tile after tile; returns the total
+template <int THREADS, typename T>
+__device__ int64_t block_scan_range(const T *in, int64_t *out, int64_t n, int64_t *wsum)
+{
+    int64_t carry = 0;
+    for (int64_t t0 = 0; t0 < n; t0 += THREADS * kScanItems) carry += tile_scan<THREADS>(in, out, n, t0, carry, wsum);
+    return carry;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) scan_one_block_kernel(const T *in, int64_t *out, int64_t n, int64_t *total)
+{
+    __shared__ int64_t wsum[32];
+    const int64_t t = block_scan_range<1024>(in, out, n, wsum);
+    if (threadIdx.x == 0) *total = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) scan_tiles_kernel(const T *in, int64_t *out, int64_t n, int64_t *tile_sums)
+{
+    __shared__ int64_t wsum[32];
+    const int64_t t = tile_scan<1024>(in, out, n, (int64_t)blockIdx.x * kScanTile, 0, wsum);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(1024) scan_add_tiles_kernel(int64_t *out, int64_t n, const int64_t *tile_off)
+{
+    const int64_t add = tile_off[blockIdx.x];
+    const int64_t b = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t at = b + 1024 * k;
+        if (at < n) out[at] += add;
+    }
+}
+
+// starts[r] = scanned[r * cols] (or the total at r == rows), one thread per row
+__global__ void row_starts_kernel(const int64_t *scanned, int rows, int64_t cols, int64_t n, int64_t *starts,
+                                  const int64_t *total)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r > rows) return;
+    const int64_t at = (int64_t)r * cols;
+    starts[r] = (r == rows || at >= n) ? *total : scanned[at];
+}
+
+
+// ---------------------------------------------------------------- search arena
+// Every prefix level lives in one node arena: level d (d = 1: the anchors,
+// one node per bond) is nodes[lv[d-1], lv[d]).  Level sizes stay on the
+// device, so the levels are expanded without a host round trip.  A level
+// whose children would not fit stops the search (ctl->stop = d, ctl->need =
+// the size it asked for) and every deeper level is left empty.  Count and
+// slot tables are [K+1][cap], indexed by arena position.
+struct SearchCtl {
+    int32_t cand_overflow;        // a candidate list outgrew kNodeU
+    int32_t stop;                 // first level whose children did not fit (0: none)
+    int64_t need;                 // arena size that level asked for
+};
+
+struct Arena {
+    Node *nodes;
+    int64_t cap;
+    int64_t *lv;                  // [kPrefixMax + 2] level boundaries
+    int32_t *child_cnt;           // [cap] children per node
+    int64_t *child_off;           // [cap] child offset within the node's chunk
+    int64_t *chunk_tot;           // [grid] children per chunk, then their exclusive scan
+    int32_t *counts;              // [K+1][cap] clusters emitted per (size, node)
+    const int64_t *base;          // [K+1][cap] first output slot per (size, node)
+    SearchCtl *ctl;
+};
+
+__global__ void arena_init_kernel(Arena a, int n_roots)
+{
+    if (threadIdx.x <= kPrefixMax + 1) a.lv[threadIdx.x] = threadIdx.x == 0 ? 0 : n_roots;
+    if (threadIdx.x == 0) { a.ctl->cand_overflow = 0; a.ctl->stop = 0; a.ctl->need = 0; }
+}
+
 // ---------------------------------------------------------------- roots
-__global__ void roots_kernel(GeomView g, int n_closed, int K, int mode, Node *nodes,
-                             int32_t *counts /* [K+1][n_closed] */, Emit out, const int64_t *base,
-                             int write, int32_t *overflow)
+__global__ void roots_kernel(GeomView g, int n_closed, int mode, Arena A, Emit out, int write)
 {
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n_closed; a += gridDim.x * blockDim.x) {
         const int x0 = g.bond_site[2 * a], x1 = g.bond_site[2 * a + 1];
@@ -177,23 +337,26 @@ __global__ void roots_kernel(GeomView g, int n_closed, int K, int mode, Node *no
             int n = 0;
             for (int p = g.site_ptr[x0]; p < g.site_ptr[x0 + 1]; ++p) {
                 int f = g.site_bonds[p];
-                if (f > a) { if (n < kNodeU) nd.U[n++] = f; else atomicExch(overflow, 1); }
+                if (f > a) { if (n < kNodeU) nd.U[n++] = f; else atomicExch(&A.ctl->cand_overflow, 1); }
             }
             for (int p = g.site_ptr[x1]; p < g.site_ptr[x1 + 1]; ++p) {
                 int f = g.site_bonds[p];
                 if (f <= a) continue;
                 const int c = g.bond_site[2 * f] == x1 ? g.bond_site[2 * f + 1] : g.bond_site[2 * f];
                 if (c == x0) continue;                 // parallel bond, already listed at x0
-                if (n < kNodeU) nd.U[n++] = f; else atomicExch(overflow, 1);
+                if (n < kNodeU) nd.U[n++] = f; else atomicExch(&A.ctl->cand_overflow, 1);
             }
             nd.nU = n;
-            nodes[a] = nd;
-            counts[1 * n_closed + a] = (mode == PNE_MODE_ALL) ? 1 : 0;
+            VSet<kNodeV> V;
+            V.inc(x0); V.inc(x1);
+            store_vset(&nd, V);
+            A.nodes[a] = nd;
+            A.counts[1 * A.cap + a] = (mode == PNE_MODE_ALL) ? 1 : 0;
         } else if (mode == PNE_MODE_ALL) {
             VSet<2> V;
             V.inc(x0); V.inc(x1);
             int32_t S[1] = {a};
-            write_cluster(out, base[1 * n_closed + a], S, 1, V);
+            write_cluster(out, A.base[1 * A.cap + a], S, 1, V);
         }
     }
 }
@@ -204,8 +367,14 @@ __global__ void roots_kernel(GeomView g, int n_closed, int K, int mode, Node *no
 // few hundred instructions of latency instead of a serial walk over its list;
 // ballots give every child and every emitted set its rank within the node, so
 // the output order is the candidate order, as in the serial search.
-// pass 0: count child nodes (child_count may be null) and emissions;
-// pass 1: write child nodes; pass 2: write emitted clusters.
+// Block b takes the b-th contiguous chunk of the node range, its warps
+// striding through it.
+//   kCount:     children and emissions of level lo == hi; the block then scans
+//               its chunk's child counts (offsets within the chunk, chunk total)
+//   kEmitCount: emissions only (the last level)
+//   kChildren:  write the children of level lo == hi, unless the search stopped
+//   kEmit:      write the emitted clusters of levels lo..hi
+enum ExpandPass { kCount = 0, kChildren = 1, kEmit = 2, kEmitCount = 3 };
 constexpr int kExpandWarps = 4;
 constexpr int kMaxNew = kNodeU / (kPrefixMax + 1);   // new candidates per step (site degree - 1)
 constexpr int kNodeWords = (int)(sizeof(Node) / 4);
@@ -231,18 +400,24 @@ __device__ bool repairable_split(const VSet<NV> &V, const int32_t *UA, const int
 }
 
 __global__ void __launch_bounds__(32 * kExpandWarps)
-expand_kernel(GeomView g, const Node *nodes, int64_t n_nodes, int K, int mode, int pass,
-              int32_t *child_count, const int64_t *child_off, Node *children,
-              int32_t *counts /* [K+1][n_nodes] */, Emit out, const int64_t *base, int32_t *overflow)
+expand_kernel(GeomView g, Arena A, int lo_level, int hi_level, int K, int mode, int pass, Emit out)
 {
     __shared__ Node sh_node[kExpandWarps];
     __shared__ int32_t sh_a[kExpandWarps][kNodeU], sh_b[kExpandWarps][kNodeU];
+    __shared__ int64_t wsum[kExpandWarps];
+    if (pass == kChildren && A.ctl->stop != 0) return;              // uniform over the grid
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     Node &nd = sh_node[w];
     int32_t *UA = sh_a[w], *UB = sh_b[w];
-    for (int64_t u = (int64_t)blockIdx.x * kExpandWarps + w; u < n_nodes; u += (int64_t)gridDim.x * kExpandWarps) {
-        const int32_t *src = reinterpret_cast<const int32_t *>(nodes + u);
+    const int64_t r0 = A.lv[lo_level - 1], r1 = A.lv[hi_level];
+    const int64_t chunk = (r1 - r0 + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = r0 + (int64_t)blockIdx.x * chunk;
+    const int64_t c1 = c0 + chunk < r1 ? c0 + chunk : r1;
+    const int64_t next = A.lv[hi_level];                              // first child slot (kChildren)
+    const int64_t cbase_chunk = (pass == kChildren) ? A.chunk_tot[blockIdx.x] : 0;
+    for (int64_t u = c0 + w; u < c1; u += kExpandWarps) {
+        const int32_t *src = reinterpret_cast<const int32_t *>(A.nodes + u);
         for (int q = lane; q < kNodeWords; q += 32) reinterpret_cast<int32_t *>(&nd)[q] = src[q];
         __syncwarp();
         const int nU = nd.nU, t = nd.t, anchor = nd.S[0];
@@ -252,8 +427,8 @@ expand_kernel(GeomView g, const Node *nodes, int64_t n_nodes, int K, int mode, i
         }
         __syncwarp();
         int n_child = 0, n_emit = 0;
-        const int64_t cbase = (pass == 1) ? child_off[u] : 0;
-        const int64_t ebase = (pass == 2) ? base[(int64_t)(t + 1) * n_nodes + u] : 0;
+        const int64_t cbase = (pass == kChildren) ? next + cbase_chunk + A.child_off[u] : 0;
+        const int64_t ebase = (pass == kEmit) ? A.base[(int64_t)(t + 1) * A.cap + u] : 0;
         for (int i0 = 0; i0 < nU; i0 += 32) {
             const int i = i0 + lane;
             bool emit = false, grow = false;
@@ -261,30 +436,31 @@ expand_kernel(GeomView g, const Node *nodes, int64_t n_nodes, int K, int mode, i
             int32_t NU[kMaxNew], NA[kMaxNew], NB[kMaxNew];
             int nn = 0;
             if (i < nU) {
-                for (int q = 0; q < t; ++q) { V.inc(g.bond_site[2 * nd.S[q]]); V.inc(g.bond_site[2 * nd.S[q] + 1]); }
+                load_vset(V, nd);
                 const int e = nd.U[i], a0 = UA[i], a1 = UB[i];
                 const int b = !V.has(a0) ? a0 : (!V.has(a1) ? a1 : -1);
                 V.inc(a0); V.inc(a1);
                 emit = valid_set(mode, V.dang);
-                if (may_grow(mode, t + 1, K, V.dang)) {
-                    if (b >= 0) nn = append_new(g, b, e, anchor, V, NU, NA, NB, 0, kMaxNew, overflow);
+                if ((pass == kCount || pass == kChildren) && may_grow(mode, t + 1, K, V.dang)) {
+                    if (b >= 0) nn = append_new(g, b, e, anchor, V, NU, NA, NB, 0, kMaxNew, &A.ctl->cand_overflow);
                     grow = mode == PNE_MODE_ALL || repairable_split(V, UA, UB, i + 1, nU, NA, NB, nn);
                 }
             }
             const unsigned gm = __ballot_sync(0xffffffffu, grow), em = __ballot_sync(0xffffffffu, emit);
-            if (pass == 1 && grow) {
-                Node *c = children + cbase + n_child + __popc(gm & lt);
+            if (pass == kChildren && grow) {
+                Node *c = A.nodes + cbase + n_child + __popc(gm & lt);
                 for (int q = 0; q < t; ++q) c->S[q] = nd.S[q];
                 c->S[t] = nd.U[i];
                 c->t = t + 1;
                 int m = 0;
                 for (int q = i + 1; q < nU; ++q) c->U[m++] = nd.U[q];
                 for (int q = 0; q < nn; ++q) {
-                    if (m < kNodeU) c->U[m++] = NU[q]; else atomicExch(overflow, 1);
+                    if (m < kNodeU) c->U[m++] = NU[q]; else atomicExch(&A.ctl->cand_overflow, 1);
                 }
                 c->nU = m;
+                store_vset(c, V);
             }
-            if (pass == 2 && emit) {
+            if (pass == kEmit && emit) {
                 int32_t S[kPrefixMax + 1];
                 for (int q = 0; q < t; ++q) S[q] = nd.S[q];
                 S[t] = nd.U[i];
@@ -293,31 +469,53 @@ expand_kernel(GeomView g, const Node *nodes, int64_t n_nodes, int K, int mode, i
             n_child += __popc(gm);
             n_emit += __popc(em);
         }
-        if (pass == 0 && lane == 0) {
-            if (child_count) child_count[u] = n_child;
-            counts[(int64_t)(t + 1) * n_nodes + u] = n_emit;
+        if ((pass == kCount || pass == kEmitCount) && lane == 0) {
+            A.counts[(int64_t)(t + 1) * A.cap + u] = n_emit;
+            if (pass == kCount) A.child_cnt[u] = n_child;
         }
         __syncwarp();
+    }
+    if (pass == kCount) {
+        __syncthreads();
+        const int64_t len = c1 > c0 ? c1 - c0 : 0;
+        const int64_t tot = block_scan_range<32 * kExpandWarps>(A.child_cnt + c0, A.child_off + c0, len, wsum);
+        if (threadIdx.x == 0) A.chunk_tot[blockIdx.x] = tot;
+    }
+}
+
+// After the kCount pass of level d: scan the chunk totals in place and place
+// level d + 1, or stop the search if it does not fit.
+__global__ void __launch_bounds__(1024) level_close_kernel(Arena A, int d, int n_chunks)
+{
+    __shared__ int64_t wsum[32];
+    const int64_t tot = block_scan_range<1024>(A.chunk_tot, A.chunk_tot, n_chunks, wsum);
+    if (threadIdx.x == 0) {
+        const int64_t end = A.lv[d];
+        if (A.ctl->stop == 0 && end + tot <= A.cap) {
+            for (int e = d + 1; e <= kPrefixMax + 1; ++e) A.lv[e] = end + tot;
+        } else {
+            if (A.ctl->stop == 0) { A.ctl->stop = d; A.ctl->need = end + tot; }
+            for (int e = d + 1; e <= kPrefixMax + 1; ++e) A.lv[e] = end;
+        }
     }
 }
 
 // ---------------------------------------------------------------- depth-first tasks
+// One thread searches the whole subtree below one node of `level`; counts go
+// to rows t0 + 1 .. K of its arena column, writes to the slots those rows give.
 template <int KMAX, int UMAX>
-__global__ void __launch_bounds__(128) dfs_kernel(GeomView g, const Node *nodes, int64_t n_nodes, int K,
-                                                  int mode, int write, int32_t *counts /* [K+1][n_nodes] */,
-                                                  Emit out, const int64_t *base, int32_t *overflow)
+__global__ void __launch_bounds__(128) dfs_kernel(GeomView g, Arena A, int level, int K, int mode, int write, Emit out)
 {
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n_nodes;
+    const int64_t r0 = A.lv[level - 1], r1 = A.lv[level];
+    for (int64_t u = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < r1;
          u += (int64_t)gridDim.x * blockDim.x) {
-        const Node &nd = nodes[u];
+        const Node &nd = A.nodes[u];
         const int t0 = nd.t, anchor = nd.S[0];
         VSet<KMAX + 1> V;
+        load_vset(V, nd);
         int32_t S[KMAX];
         int s = t0;
-        for (int i = 0; i < t0; ++i) {
-            S[i] = nd.S[i];
-            V.inc(g.bond_site[2 * S[i]]); V.inc(g.bond_site[2 * S[i] + 1]);
-        }
+        for (int i = 0; i < t0; ++i) S[i] = nd.S[i];
         int32_t U[UMAX], UA[UMAX], UB[UMAX];
         for (int i = 0; i < nd.nU; ++i) {
             U[i] = nd.U[i]; UA[i] = g.bond_site[2 * U[i]]; UB[i] = g.bond_site[2 * U[i] + 1];
@@ -327,7 +525,7 @@ __global__ void __launch_bounds__(128) dfs_kernel(GeomView g, const Node *nodes,
         int64_t slot[KMAX + 1];
         for (int q = 0; q <= KMAX; ++q) {
             cnt[q] = 0;
-            slot[q] = (write && q <= K) ? base[(int64_t)q * n_nodes + u] : 0;
+            slot[q] = (write && q <= K) ? A.base[(int64_t)q * A.cap + u] : 0;
         }
         int lvl = 0;
         pos[0] = 0; end[0] = nd.nU;
@@ -351,7 +549,7 @@ __global__ void __launch_bounds__(128) dfs_kernel(GeomView g, const Node *nodes,
             }
             if (may_grow(mode, s, K, V.dang)) {
                 int ne = end[lvl];
-                if (b >= 0) ne = append_new(g, b, e, anchor, V, U, UA, UB, ne, UMAX, overflow);
+                if (b >= 0) ne = append_new(g, b, e, anchor, V, U, UA, UB, ne, UMAX, &A.ctl->cand_overflow);
                 if (mode == PNE_MODE_ALL || repairable(V, UA, UB, pos[lvl] + 1, ne)) {
                     ++lvl;
                     pos[lvl] = pos[lvl - 1] + 1;
@@ -364,108 +562,9 @@ __global__ void __launch_bounds__(128) dfs_kernel(GeomView g, const Node *nodes,
             ++pos[lvl];
         }
         if (!write)
-            for (int q = t0 + 1; q <= K; ++q) counts[(int64_t)q * n_nodes + u] = cnt[q];
+            for (int q = t0 + 1; q <= K; ++q) A.counts[(int64_t)q * A.cap + u] = cnt[q];
     }
 }
-
-// ---------------------------------------------------------------- scan
-// Exclusive prefix sums of int32 or int64 tables into int64.  A tile is 8192
-// values scanned by one block of 1024 threads: warp w owns kScanItems
-// consecutive rows of 32 values, lane l column l, so loads and stores are
-// coalesced; all loads of a tile are issued before the first shuffle, rows are
-// scanned across lanes and chained through the last lane, and the warp totals
-// are scanned by warp 0.  Small tables are scanned by one block walking the
-// tiles with a running carry (one launch); larger ones by one block per tile,
-// a scan of the tile totals, and an add pass.  `in` may alias `out`.
-constexpr int kScanItems = 8;
-constexpr int kScanTile = 1024 * kScanItems;
-constexpr int64_t kOneBlockTiles = 4;
-
-template <typename T>
-__device__ __forceinline__ int64_t tile_scan(const T *in, int64_t *out, int64_t n, int64_t t0, int64_t carry,
-                                             int64_t *wsum /* shared [32] */)
-{
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t b = t0 + (int64_t)wid * (32 * kScanItems) + lane;
-    int64_t v[kScanItems], x[kScanItems];
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int64_t at = b + 32 * k;
-        v[k] = (at < n) ? (int64_t)in[at] : 0;
-    }
-    int64_t run = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        int64_t y = v[k];
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int64_t z = __shfl_up_sync(0xffffffffu, y, off);
-            if (lane >= off) y += z;
-        }
-        x[k] = run + y - v[k];
-        run += __shfl_sync(0xffffffffu, y, 31);
-    }
-    if (lane == 0) wsum[wid] = run;
-    __syncthreads();
-    if (wid == 0) {
-        int64_t ws = wsum[lane];
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int64_t z = __shfl_up_sync(0xffffffffu, ws, off);
-            if (lane >= off) ws += z;
-        }
-        wsum[lane] = ws;
-    }
-    __syncthreads();
-    const int64_t before = carry + (wid > 0 ? wsum[wid - 1] : 0);
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int64_t at = b + 32 * k;
-        if (at < n) out[at] = before + x[k];
-    }
-    const int64_t total = wsum[31];
-    __syncthreads();
-    return total;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(1024) scan_one_block_kernel(const T *in, int64_t *out, int64_t n, int64_t *total)
-{
-    __shared__ int64_t wsum[32];
-    int64_t carry = 0;
-    for (int64_t t0 = 0; t0 < n; t0 += kScanTile) carry += tile_scan(in, out, n, t0, carry, wsum);
-    if (threadIdx.x == 0) *total = carry;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(1024) scan_tiles_kernel(const T *in, int64_t *out, int64_t n, int64_t *tile_sums)
-{
-    __shared__ int64_t wsum[32];
-    const int64_t t = tile_scan(in, out, n, (int64_t)blockIdx.x * kScanTile, 0, wsum);
-    if (threadIdx.x == 0) tile_sums[blockIdx.x] = t;
-}
-
-__global__ void __launch_bounds__(1024) scan_add_tiles_kernel(int64_t *out, int64_t n, const int64_t *tile_off)
-{
-    const int64_t add = tile_off[blockIdx.x];
-    const int64_t b = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int64_t at = b + 1024 * k;
-        if (at < n) out[at] += add;
-    }
-}
-
-// starts[r] = scanned[r * cols] (or the total at r == rows), one thread per row
-__global__ void row_starts_kernel(const int64_t *scanned, int rows, int64_t cols, int64_t n, int64_t *starts,
-                                  const int64_t *total)
-{
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r > rows) return;
-    const int64_t at = (int64_t)r * cols;
-    starts[r] = (r == rows || at >= n) ? *total : scanned[at];
-}
-
 
 // ---------------------------------------------------------------- tuples
 struct TupleParams {
@@ -658,10 +757,12 @@ pne_status scan_i32_to(pne_ctx *ctx, const int32_t *src, int64_t *dst, int64_t n
     return scan_to<int32_t>(ctx, src, dst, n, d_total, s);
 }
 
-// counts [rows][cols] int32 -> base (exclusive scan, row-major) int64; per-row totals
-// (the row starts are gathered on the device and read back in one copy)
+// counts [rows][cols] int32 -> base (exclusive scan, row-major) int64; per-row totals.
+// The row starts are gathered on the device and read back in one copy, together
+// with `extra_bytes` from `extra_dev` (a multiple of 8) into `extra_host`.
 pne_status scan_counts(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t cols, DevBuf &base,
-                       std::vector<int64_t> &row_tot, cudaStream_t s)
+                       std::vector<int64_t> &row_tot, cudaStream_t s, const void *extra_dev = nullptr,
+                       size_t extra_bytes = 0, void *extra_host = nullptr)
 {
     const int64_t n = (int64_t)rows * cols;
     pne_status st = dev_alloc(ctx, base, (size_t)(std::max<int64_t>(n, 1) + rows + 3) * 8, s);
@@ -673,12 +774,15 @@ pne_status scan_counts(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t 
     if ((st = scan_i32_to(ctx, d_counts, b, n, tot, s))) return st;
     row_starts_kernel<<<(rows + 1 + 127) / 128, 128, 0, s>>>(b, rows, cols, n, starts, tot);
     PNE_CUDA_TRY(ctx, cudaGetLastError());
-    std::vector<int64_t> h(rows + 1, 0);
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(pinned_i64(ctx, rows + 1), starts, (rows + 1) * 8, cudaMemcpyDeviceToHost, s));
+    const size_t words = (size_t)(rows + 1) + extra_bytes / 8;
+    int64_t *h = pinned_i64(ctx, words);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h, starts, (rows + 1) * 8, cudaMemcpyDeviceToHost, s));
+    if (extra_bytes)
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h + rows + 1, extra_dev, extra_bytes, cudaMemcpyDeviceToHost, s));
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    std::memcpy(h.data(), pinned_i64(ctx, rows + 1), (rows + 1) * 8);
     row_tot.assign(rows, 0);
     for (int r = 0; r < rows; ++r) row_tot[r] = h[r + 1] - h[r];
+    if (extra_bytes) std::memcpy(extra_host, h + rows + 1, extra_bytes);
     return PNE_OK;
 }
 
@@ -699,119 +803,107 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     }
     if ((kPrefixMax + 1) * (maxdeg - 1) > kNodeU) { set_error(ctx, PNE_EINVAL, "site degree too large"); return PNE_EINVAL; }
     GeomView gv{g.d_bond_site, g.d_site_ptr, g.d_site_bonds};
-    DevBuf flag;
-    pne_status st = dev_alloc(ctx, flag, 8, s);
-    if (st) return st;
-    int32_t *overflow = (int32_t *)flag.ptr;
-    PNE_CUDA_TRY(ctx, cudaMemsetAsync(overflow, 0, 8, s));
-
-    // levels of prefix nodes
-    struct Level { DevBuf nodes; int64_t n = 0; DevBuf counts; DevBuf base; std::vector<int64_t> tot; };
-    std::vector<Level> lv(1);
-    lv[0].n = Mc;
-    if ((st = dev_alloc(ctx, lv[0].nodes, sizeof(Node) * std::max(Mc, 1), s))) return st;
-    if ((st = dev_alloc(ctx, lv[0].counts, (size_t)(K + 1) * std::max(Mc, 1) * 4, s))) return st;
-    PNE_CUDA_TRY(ctx, cudaMemsetAsync(lv[0].counts.ptr, 0, (size_t)(K + 1) * std::max(Mc, 1) * 4, s));
+    // prefix levels 1..D are expanded breadth-first; the last one either only
+    // emits (D == K - 1) or is searched depth-first (K - 1 > kPrefixMax)
+    const int D = (K <= 1) ? 1 : std::min(kPrefixMax, K - 1);
+    const int final_kind = (K <= 1) ? 0 : (D == K - 1 ? 1 : 2);
+    const bool small = (K <= 12 && umax_need <= 64);
+    // chunks of the blocked passes: one wave of resident blocks
+    int per_sm = 0;
+    PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel, 32 * kExpandWarps, 0));
+    const int G = ctx->n_sm * std::max(1, per_sm);
+    const int Gd = grid1(1 << 20, 128, ctx->n_sm);    // grid of the depth-first kernel
+    const std::string hint_key = std::to_string(g.hash) + ":" + std::to_string(Mc) + ":" + std::to_string(K) + ":" +
+                                 std::to_string(mode);
+    int64_t cap = kArenaFirst;
+    {
+        std::lock_guard<std::mutex> lk(ctx->cache_mu);
+        auto it = ctx->arena_hint.find(hint_key);
+        if (it != ctx->arena_hint.end()) cap = it->second;
+    }
+    const int64_t cap_max = ctx->arena_max > 0 ? std::max<int64_t>(ctx->arena_max, Mc) : kNodeCap;
+    cap = std::min(cap_max, std::max<int64_t>(cap, Mc));
     Emit none{nullptr, nullptr, nullptr, rec.width, rec.vwidth};
-    if (Mc > 0)
+    auto dfs = [&](const Arena &A, int level, int write, const Emit &o) {
+        ProfScope ps__(ctx, s, "enum_dfs");
+        if (small) dfs_kernel<12, 64><<<Gd, 128, 0, s>>>(gv, A, level, K, mode, write, o);
+        else dfs_kernel<32, 128><<<Gd, 128, 0, s>>>(gv, A, level, K, mode, write, o);
+    };
+    struct Readback { int64_t lv[kPrefixMax + 2]; SearchCtl ctl; } hb;
+    DevBuf nodes, tables, counts, base;
+    Arena A{};
+    std::vector<int64_t> per_size;
+    int dfs_level = 0;
+    pne_status st;
+    for (;;) {
+        // arena: nodes, then [lv | ctl | child_cnt | child_off | chunk_tot], then counts
+        if ((st = dev_alloc(ctx, nodes, sizeof(Node) * (size_t)cap, s))) return st;
+        const size_t tab_bytes = sizeof(Readback) + (size_t)cap * 4 + (size_t)cap * 8 + (size_t)G * 8 + 64;
+        if ((st = dev_alloc(ctx, tables, tab_bytes, s))) return st;
+        if ((st = dev_alloc(ctx, counts, (size_t)(K + 1) * cap * 4, s))) return st;
+        char *tb = (char *)tables.ptr;
+        A.nodes = (Node *)nodes.ptr;
+        A.cap = cap;
+        A.lv = (int64_t *)tb;
+        A.ctl = (SearchCtl *)(tb + offsetof(Readback, ctl));
+        A.child_off = (int64_t *)(tb + sizeof(Readback));
+        A.chunk_tot = A.child_off + cap;
+        A.child_cnt = (int32_t *)(A.chunk_tot + G);
+        A.counts = (int32_t *)counts.ptr;
+        A.base = nullptr;
+        PNE_CUDA_TRY(ctx, cudaMemsetAsync(counts.ptr, 0, (size_t)(K + 1) * cap * 4, s));
+        arena_init_kernel<<<1, 32, 0, s>>>(A, Mc);
         {
             ProfScope ps__(ctx, s, "enum_roots");
-            roots_kernel<<<grid1(Mc, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, K, mode, (Node *)lv[0].nodes.ptr,
-                                                              (int32_t *)lv[0].counts.ptr, none, nullptr, 0, overflow);
+            roots_kernel<<<grid1(Mc, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, mode, A, none, 0);
         }
-    PNE_CUDA_TRY(ctx, cudaGetLastError());
-    // expand while the tree is narrow
-    int depth = 1;
-    while (depth < kPrefixMax && depth < K - 1 && lv.back().n > 0 && lv.back().n < kPrefixTarget) {
-        Level &cur = lv.back();
-        DevBuf cc;
-        if ((st = dev_alloc(ctx, cc, (size_t)cur.n * 8, s))) return st;
-        int32_t *child_count = (int32_t *)cc.ptr;
-        int32_t *cnts = (int32_t *)cur.counts.ptr;
-        {
-            ProfScope ps__(ctx, s, "enum_expand");
-            expand_kernel<<<grid1(cur.n, kExpandWarps, ctx->n_sm), 32 * kExpandWarps, 0, s>>>(gv, (const Node *)cur.nodes.ptr, cur.n, K, mode, 0,
-                                                                  child_count, nullptr, nullptr, cnts, none, nullptr, overflow);
-        }
-        PNE_CUDA_TRY(ctx, cudaGetLastError());
-        DevBuf coff;
-        if ((st = dev_alloc(ctx, coff, (size_t)(cur.n + 1) * 8, s))) return st;
-        int64_t *d_n_child = (int64_t *)coff.ptr + cur.n;
-        if ((st = scan_i32_to(ctx, child_count, (int64_t *)coff.ptr, cur.n, d_n_child, s))) return st;
-        int64_t *h_n_child = pinned_i64(ctx, 1);
-        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_n_child, d_n_child, 8, cudaMemcpyDeviceToHost, s));
-        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-        const int64_t n_child = *h_n_child;
-        if (n_child > kNodeCap) {             // too wide: search depth-first from this level
-            dev_free(ctx, cc, s);
-            dev_free(ctx, coff, s);
-            break;
-        }
-        Level nxt;
-        nxt.n = n_child;
-        if ((st = dev_alloc(ctx, nxt.nodes, sizeof(Node) * std::max<int64_t>(n_child, 1), s))) return st;
-        if ((st = dev_alloc(ctx, nxt.counts, (size_t)(K + 1) * std::max<int64_t>(n_child, 1) * 4, s))) return st;
-        PNE_CUDA_TRY(ctx, cudaMemsetAsync(nxt.counts.ptr, 0, (size_t)(K + 1) * std::max<int64_t>(n_child, 1) * 4, s));
-        {
-            ProfScope ps__(ctx, s, "enum_expand");
-            expand_kernel<<<grid1(cur.n, kExpandWarps, ctx->n_sm), 32 * kExpandWarps, 0, s>>>(gv, (const Node *)cur.nodes.ptr, cur.n, K, mode, 1,
-                                                                  nullptr, (const int64_t *)coff.ptr, (Node *)nxt.nodes.ptr,
-                                                                  nullptr, none, nullptr, overflow);
-        }
-        PNE_CUDA_TRY(ctx, cudaGetLastError());
-        dev_free(ctx, cc, s);
-        dev_free(ctx, coff, s);
-        lv.push_back(std::move(nxt));
-        ++depth;
-    }
-    // the last level: nodes of size K - 1 only emit (one more warp-parallel
-    // step); shallower nodes are searched depth-first; nodes of size K (K == 1)
-    // have nothing left to add
-    Level &last = lv.back();
-    const bool small = (K <= 12 && umax_need <= 64);
-    const int final_kind = (depth >= K) ? 0 : (depth == K - 1 ? 1 : 2);
-    if (last.n > 0 && final_kind == 1) {
-        ProfScope ps__(ctx, s, "enum_expand");
-        expand_kernel<<<grid1(last.n, kExpandWarps, ctx->n_sm), 32 * kExpandWarps, 0, s>>>(
-            gv, (const Node *)last.nodes.ptr, last.n, K, mode, 0, nullptr, nullptr, nullptr,
-            (int32_t *)last.counts.ptr, none, nullptr, overflow);
-        PNE_CUDA_TRY(ctx, cudaGetLastError());
-    } else if (last.n > 0 && final_kind == 2) {
-        if (small)
+        for (int d = 1; d < D; ++d) {
             {
-                ProfScope ps__(ctx, s, "enum_dfs");
-                dfs_kernel<12, 64><<<grid1(last.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)last.nodes.ptr, last.n, K, mode, 0,
-                                                                            (int32_t *)last.counts.ptr, none, nullptr, overflow);
+                ProfScope ps__(ctx, s, "enum_expand");
+                expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, d, K, mode, kCount, none);
             }
-        else
+            level_close_kernel<<<1, 1024, 0, s>>>(A, d, G);
             {
-                ProfScope ps__(ctx, s, "enum_dfs");
-                dfs_kernel<32, 128><<<grid1(last.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)last.nodes.ptr, last.n, K, mode, 0,
-                                                                             (int32_t *)last.counts.ptr, none, nullptr, overflow);
+                ProfScope ps__(ctx, s, "enum_expand");
+                expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, d, K, mode, kChildren, none);
             }
+        }
+        if (final_kind == 1) {
+            ProfScope ps__(ctx, s, "enum_expand");
+            expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, D, D, K, mode, kEmitCount, none);
+        } else if (final_kind == 2) {
+            dfs(A, D, 0, none);
+        }
         PNE_CUDA_TRY(ctx, cudaGetLastError());
+        // one (size, node) table over the arena; the same round trip brings the
+        // level bounds and the stop record
+        if ((st = scan_counts(ctx, A.counts, K + 1, cap, base, per_size, s, A.lv, sizeof(Readback), &hb))) return st;
+        if (hb.ctl.cand_overflow) {
+            set_error(ctx, PNE_EOVERFLOW, "candidate list overflow in the cluster search");
+            return PNE_EOVERFLOW;
+        }
+        if (hb.ctl.stop == 0) { dfs_level = (final_kind == 2) ? D : 0; break; }
+        if (cap < cap_max) {
+            // the tree outgrew the arena: grow it and search again
+            cap = std::min(cap_max, std::max(4 * cap, 2 * hb.ctl.need));
+            dev_free(ctx, nodes, s); dev_free(ctx, tables, s); dev_free(ctx, counts, s); dev_free(ctx, base, s);
+            continue;
+        }
+        // the largest arena holds levels 1..stop: search below level `stop` depth-first
+        dfs_level = hb.ctl.stop;
+        dfs(A, dfs_level, 0, none);
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+        dev_free(ctx, base, s);
+        if ((st = scan_counts(ctx, A.counts, K + 1, cap, base, per_size, s))) return st;
+        break;
     }
-    // one (size, unit) table over all levels: concatenate per size
-    int64_t n_units = 0;
-    for (auto &L : lv) n_units += L.n;
-    DevBuf all_counts;
-    if ((st = dev_alloc(ctx, all_counts, (size_t)(K + 1) * std::max<int64_t>(n_units, 1) * 4, s))) return st;
     {
-        int64_t col = 0;
-        for (auto &L : lv) {
-            if (L.n > 0)
-                PNE_CUDA_TRY(ctx, cudaMemcpy2DAsync((int32_t *)all_counts.ptr + col, n_units * 4, L.counts.ptr, L.n * 4,
-                                                     L.n * 4, K + 1, cudaMemcpyDeviceToDevice, s));
-            col += L.n;
-        }
+        // the next search of this geometry starts with an arena that fits
+        const int last = hb.ctl.stop ? hb.ctl.stop : D;
+        const int64_t used = ((hb.lv[last] + 1023) / 1024) * 1024;
+        std::lock_guard<std::mutex> lk(ctx->cache_mu);
+        ctx->arena_hint[hint_key] = std::min(cap_max, std::max<int64_t>(used, 1024));
     }
-    DevBuf base;
-    std::vector<int64_t> per_size;
-    if ((st = scan_counts(ctx, (const int32_t *)all_counts.ptr, K + 1, n_units, base, per_size, s))) return st;
-    int32_t h_over = 0;
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(&h_over, overflow, 4, cudaMemcpyDeviceToHost, s));
-    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    if (h_over) { set_error(ctx, PNE_EOVERFLOW, "candidate list overflow in the cluster search"); return PNE_EOVERFLOW; }
     uint64_t n_cl = 0;
     rec.size_start.assign(K + 2, 0);
     for (int q = 0; q <= K; ++q) { rec.size_start[q] = (int64_t)n_cl; n_cl += per_size[q]; }
@@ -822,49 +914,24 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     if ((st = dev_alloc(ctx, rec.cl_verts, nn * rec.vwidth * 4, s))) return st;
     if ((st = dev_alloc(ctx, rec.cl_size, nn * 4, s))) return st;
     Emit out{(int32_t *)rec.cl_edges.ptr, (int32_t *)rec.cl_verts.ptr, (int32_t *)rec.cl_size.ptr, rec.width, rec.vwidth};
-    // write passes; each level reads its slice of the base table
-    {
-        // base is [K+1][n_units]; the kernels index base[q * n_level + u] of their own
-        // table, so each level gets a compact copy
-        int64_t col = 0;
-        for (size_t li = 0; li < lv.size(); ++li) {
-            Level &L = lv[li];
-            if (L.n == 0) { col += L.n; continue; }
-            if ((st = dev_alloc(ctx, L.base, (size_t)(K + 1) * L.n * 8, s))) return st;
-            PNE_CUDA_TRY(ctx, cudaMemcpy2DAsync(L.base.ptr, L.n * 8, (int64_t *)base.ptr + col, n_units * 8,
-                                                 L.n * 8, K + 1, cudaMemcpyDeviceToDevice, s));
-            const int64_t *lb = (const int64_t *)L.base.ptr;
-            if (li == 0)
-                {
-                    ProfScope ps__(ctx, s, "enum_roots");
-                    roots_kernel<<<grid1(L.n, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, K, mode, nullptr, nullptr, out, lb, 1, overflow);
-                }
-            if (li + 1 < lv.size() || final_kind == 1)
-                {
-                    ProfScope ps__(ctx, s, "enum_expand");
-                    expand_kernel<<<grid1(L.n, kExpandWarps, ctx->n_sm), 32 * kExpandWarps, 0, s>>>(gv, (const Node *)L.nodes.ptr, L.n, K, mode, 2,
-                                                                        nullptr, nullptr, nullptr, nullptr, out, lb, overflow);
-                }
-            else if (final_kind == 2 && small)
-                {
-                    ProfScope ps__(ctx, s, "enum_dfs");
-                    dfs_kernel<12, 64><<<grid1(L.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)L.nodes.ptr, L.n, K, mode, 1,
-                                                                              nullptr, out, lb, overflow);
-                }
-            else if (final_kind == 2)
-                {
-                    ProfScope ps__(ctx, s, "enum_dfs");
-                    dfs_kernel<32, 128><<<grid1(L.n, 128, ctx->n_sm), 128, 0, s>>>(gv, (const Node *)L.nodes.ptr, L.n, K, mode, 1,
-                                                                               nullptr, out, lb, overflow);
-                }
-            PNE_CUDA_TRY(ctx, cudaGetLastError());
-            col += L.n;
-        }
+    A.base = (const int64_t *)base.ptr;
+    // write passes: the anchors (ALL mode), the breadth-first emissions of
+    // levels 1..last_bfs, and the depth-first subtrees
+    const int last_bfs = dfs_level ? dfs_level - 1 : (final_kind == 1 ? D : 0);
+    if (mode == PNE_MODE_ALL) {
+        ProfScope ps__(ctx, s, "enum_roots");
+        roots_kernel<<<grid1(Mc, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, mode, A, out, 1);
     }
-    for (auto &L : lv) { dev_free(ctx, L.nodes, s); dev_free(ctx, L.counts, s); dev_free(ctx, L.base, s); }
-    dev_free(ctx, all_counts, s);
+    if (last_bfs >= 1) {
+        ProfScope ps__(ctx, s, "enum_expand");
+        expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, 1, last_bfs, K, mode, kEmit, out);
+    }
+    if (dfs_level) dfs(A, dfs_level, 1, out);
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    dev_free(ctx, nodes, s);
+    dev_free(ctx, tables, s);
+    dev_free(ctx, counts, s);
     dev_free(ctx, base, s);
-    dev_free(ctx, flag, s);
     return PNE_OK;
 }
 

@@ -343,6 +343,10 @@ pne_status pne_ctx_create(int device, pne_ctx **out)
     pne_ctx *c = new pne_ctx();
     c->device = device;
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+    // PNE_SEARCH_ARENA_MAX (nodes) lowers the node-arena limit of the cluster
+    // search, so that the depth-first completion below the deepest level that
+    // fits can be exercised on small networks
+    if (const char *lim = std::getenv("PNE_SEARCH_ARENA_MAX")) c->arena_max = std::max(0LL, std::atoll(lim));
     // keep stream-ordered allocations pooled inside this process
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {

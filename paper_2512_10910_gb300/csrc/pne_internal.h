@@ -110,10 +110,12 @@ struct pne_ctx {
     pne::Profiler prof;
     int device = 0;
     int n_sm = 0;
+    int64_t arena_max = 0;        // node-arena limit of the cluster search (0: the built-in limit)
     pne_alloc_fn alloc = nullptr;
     pne_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
     std::map<std::string, std::shared_ptr<pne::EnumRecord>> enum_cache;
+    std::map<std::string, int64_t> arena_hint;   // search-arena size that fitted, per (geometry, K, mode)
     std::mutex cache_mu;
     // scratch for small device-side status words
     int32_t *d_status = nullptr;

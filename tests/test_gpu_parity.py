@@ -243,3 +243,35 @@ def test_float_float_bp_matches_oracle(ctx, name, make, K):
     _check_values(ff, ref)
     assert abs(ff["log_abs"] - d64["log_abs"]) <= 1e-10
     assert ff["bp_iters"] > 0
+
+
+# ---------------------------------------------------------------- search schedule
+@pytest.mark.parametrize("shape,D,K,limit", [((8, 8), 3, 8, 1), ((8, 8), 3, 8, 700), ((8, 8), 3, 8, 6000),
+                                             ((6, 5), 2, 10, 0), ((6, 5), 2, 10, 500)])
+def test_search_arena_limit_gives_identical_lists(ctx, monkeypatch, shape, D, K, limit):
+    """The breadth-first prefix stops where its node arena is full and the rest
+    of the tree is searched depth-first (limit 1: depth-first from the anchors;
+    limit 0: the default arena, and K = 10 ends depth-first from level 8).  The
+    cluster list, its order and every value must not depend on where the
+    search switches."""
+    net = I.random_tensors(I.square_lattice(shape[0], shape[1], D), 5)
+    (ref,), (e0, w0) = ctx.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64, export=True, use_cache=False)
+    if limit:
+        monkeypatch.setenv("PNE_SEARCH_ARENA_MAX", str(limit))
+    c2 = pne.Context(0)
+    monkeypatch.delenv("PNE_SEARCH_ARENA_MAX", raising=False)
+    try:
+        (res,), (e1, w1) = c2.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64, export=True, use_cache=False)
+        # a second search on the same context starts from the arena size that fitted
+        (res2,), (e2, _) = c2.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64, export=True, use_cache=False)
+    finally:
+        c2.close()
+    assert np.array_equal(e0, e1) and np.array_equal(e0, e2)
+    assert np.array_equal(w0, w1)
+    assert res["n_terms"] == ref["n_terms"] == res2["n_terms"]
+    assert res["log_abs"] == ref["log_abs"]
+    if K == 10:
+        refo = X.pne(net, K, E.LOOP)
+        cl, _ = _canon(e1, None)
+        assert cl == list(refo.clusters)
+        _check_values(res, refo)
