@@ -237,7 +237,9 @@ def main():
     # per-kernel event timings come from a separate pass, so that the timed
     # steps carry no profiling events
     prof_steps = max(5, args.steps // 4)
-    _, _, prof = timed(data_dev, dtype, prof_steps, 1, profile=True)
+    _, _, prof_all = timed(data_dev, dtype, prof_steps, 1, profile=True)
+    prof = {k: v for k, v in prof_all.items() if not k.startswith("host:")}
+    host_ms = {k[5:]: round(v[1] / prof_steps, 4) for k, v in prof_all.items() if k.startswith("host:")}
     n_terms = res[0]["n_terms"]
     terms_per_step = n_terms * B
     ms_per_step = total_ms / args.steps
@@ -306,6 +308,7 @@ def main():
         "e2e": {"value": terms_per_step * world / (e2e_ms * 1e-3), "unit": "terms/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": gpu_launches,
+        "host_ms_per_step": host_ms,
         "roofline": roof,
         "clocks": clk,
         "variants": variants,
@@ -391,7 +394,7 @@ def run_batched(args, wl, rank, world, local_rank):
         res = step()
         e.record(stream); e.synchronize()
         total += a.elapsed_time(e)
-    prof = pne.pne_ctx_profile_read(ctx.h)
+    prof = {k: v for k, v in pne.pne_ctx_profile_read(ctx.h).items() if not k.startswith("host:")}
     pne.pne_ctx_profile(ctx.h, False)
     clk = clocks.stop()
     if world > 1:

@@ -87,18 +87,23 @@ typedef struct {
     int32_t n_batch;
 } pne_network;
 
-/* BP options (the paper leaves the schedule open): Jacobi sweeps from the
- * uniform message 1/sqrt(d); each message normalised to unit 2-norm with its
+/* BP options (the paper leaves the schedule open): sweeps from the uniform
+ * message 1/sqrt(d) in colour order (the sites of one colour of a greedy
+ * proper colouring update together from the latest messages: red-black on
+ * bipartite lattices); each message normalised to unit 2-norm with its
  * largest-magnitude entry positive; stop when the largest entry change in a
- * sweep is below tol.  damping in [0,1) mixes the previous message in. */
+ * sweep is below tol.  The fixed point is the one Jacobi sweeps reach.
+ * damping in [0,1) mixes the previous message in. */
 typedef struct {
     double tol;          /* default 1e-13 when <= 0 */
     int32_t max_iter;    /* default 10000 when <= 0 */
     double damping;      /* default 0 */
-    int32_t arithmetic;  /* sweeps in 0: FP64, 1: float-float (pairs of FP32
+    int32_t arithmetic;  /* the BP sweeps and the gauge transform of the site
+                            tensors in 0: FP64, 1: float-float (pairs of FP32
                             with error-free sums and products, ~2^-48 relative
                             precision per operation, on the FP32 pipes); the
-                            messages handed to the gauge are FP64 either way */
+                            messages, projectors and blocked tensors handed on
+                            are FP64 either way */
 } pne_partition_opts;
 
 typedef struct {
@@ -154,8 +159,12 @@ void pne_partition_destroy(pne_partition *p);
 /* Enumerate the clusters (connected bond sets with |C| <= K, LOOP or ALL
  * mode) and the terms (vertex-disjoint cluster tuples with total size <= K,
  * Eq. A4).  Geometry only: the lists are shared by every tensor set and
- * cached in the context when use_cache != 0.  Synchronises `stream` (the
- * counts size the buffers).  n_clusters / n_terms may be NULL. */
+ * cached in the context when use_cache != 0.  Synchronises `stream` while it
+ * searches (the counts size the buffers).  With use_cache != 0 the returned
+ * lists and buffers are complete on return and may be used from any stream;
+ * with use_cache == 0 their last writes are still queued on `stream`, so use
+ * them on `stream` or after it (an event or a synchronisation).  n_clusters /
+ * n_terms may be NULL. */
 pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part,
                                const pne_enum_opts *opts, void *stream,
                                pne_terms **out, uint64_t *n_clusters, uint64_t *n_terms);

@@ -827,29 +827,171 @@ __global__ void block_kernel(BlockParams p)
     }
 }
 
-// ln|Z_ref|, sign(Z_ref) and the number of zero sites, one warp per member.
-__global__ void vacuum_kernel(const double *z, int n_sites, int64_t members, double *vac)
+// The same gauge transform and blocked write in float-float pairs on the FP32
+// pipes (the partition's float-float option).  The slice is scaled by a power
+// of two (its largest binary exponent, found with integer operations) before
+// the split into pairs, so the pair range covers any FP64 input; the blocked
+// tensor M = T' / z_v does not depend on that scale, and z_v and the scale of a
+// zero site are returned to the input's scale exactly.
+__global__ void block_ff_kernel(BlockParams p)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    ff *bufA = reinterpret_cast<ff *>(smem + (int64_t)wib * 2 * p.half);
+    ff *bufB = bufA + p.half;
+    ff *Gs = reinterpret_cast<ff *>(smem + (int64_t)wpb * 2 * p.half) + wib * 64;   // one leg's gauge matrix
+    const int64_t members = (int64_t)p.n_sets * p.n_slices;
+    const int64_t items = members * p.n_sites;
+    for (int64_t item = (int64_t)blockIdx.x * wpb + wib; item < items;
+         item += (int64_t)gridDim.x * wpb) {
+        const int64_t member = item / p.n_sites;
+        const int v = (int)(item % p.n_sites);
+        const int set = (int)(member / p.n_slices), slice = (int)(member % p.n_slices);
+        const int l0 = p.f_site_ptr[v], k = p.f_site_ptr[v + 1] - l0;
+        int cdims[kMaxDeg], bonds[kMaxDeg], side[kMaxDeg], cstr[kMaxDeg];
+        float cinv[kMaxDeg];
+        int kc = 0, fixed_off = 0, mul = 1;
+        // strides of the closed legs in the raw tensor, and the offset of the
+        // fixed open-leg digits of this slice
+        for (int i = k - 1; i >= 0; --i) {
+            const int b = p.f_site_bonds[l0 + i];
+            const int d = p.f_bond_dim[b];
+            const int op = p.open_pos[b];
+            if (op >= 0) {
+                int r = slice;
+                for (int q = p.n_open - 1; q > op; --q) r /= p.open_dims[q];
+                fixed_off += (r % p.open_dims[op]) * mul;
+            } else {
+                ++kc;
+            }
+            mul *= d;
+        }
+        {
+            int ci = kc, m2 = 1;
+            for (int i = k - 1; i >= 0; --i) {
+                const int b = p.f_site_bonds[l0 + i];
+                const int d = p.f_bond_dim[b];
+                if (p.open_pos[b] < 0) {
+                    --ci;
+                    cdims[ci] = d; cinv[ci] = 1.0f / (float)d; cstr[ci] = m2;
+                    bonds[ci] = b; side[ci] = (p.f_bond_site[2 * b] == v) ? 0 : 1;
+                }
+                m2 *= d;
+            }
+        }
+        int n = 1;
+        for (int i = 0; i < kc; ++i) n *= cdims[i];
+        const double *T = p.T + set * p.f_stride + p.f_tens_off[v] + fixed_off;
+        auto src_of = [&](int e) {
+            int r = e, src = 0;
+            for (int i = kc - 1; i >= 0; --i) { int dgt; r = fdivmod(r, cdims[i], cinv[i], dgt); src += dgt * cstr[i]; }
+            return src;
+        };
+        // largest biased exponent of the slice, then the scaled pairs
+        int mxb = 0;
+        for (int e = lane; e < n; e += 32)
+            mxb = max(mxb, (int)((__double_as_longlong(T[src_of(e)]) >> 52) & 0x7FF));
+        for (int off = 16; off > 0; off >>= 1) mxb = max(mxb, __shfl_xor_sync(0xffffffffu, mxb, off));
+        const int ex = mxb > 0 ? min(mxb - 1022, 1022) : 0;        // slice values are below 2^ex
+        const double down = __longlong_as_double((long long)(1023 - ex) << 52);   // 2^-ex
+        for (int e = lane; e < n; e += 32) {
+            const double x = T[src_of(e)] * down;
+            const float hi = __double2float_rn(x);
+            bufA[e] = {hi, __double2float_rn(x - (double)hi)};
+        }
+        __syncwarp();
+        ff *cur = bufA, *nxt = bufB;
+        int post = n;
+        for (int i = 0; i < kc; ++i) {
+            const int d = cdims[i];
+            post /= d;
+            const double *G = p.gauge + (((int64_t)set * p.n_bonds_full + bonds[i]) * 2 + side[i]) * 64;
+            for (int q = lane; q < d * 8; q += 32) {
+                const double g = G[q];
+                const float gh = __double2float_rn(g);
+                Gs[q] = {gh, __double2float_rn(g - (double)gh)};
+            }
+            __syncwarp();
+            const float inv_post = 1.0f / (float)post;
+            for (int e = lane; e < n; e += 32) {
+                int lo, c;
+                const int rest = fdivmod(e, post, inv_post, lo);
+                const int hi = fdivmod(rest, d, cinv[i], c);
+                const ff *src = cur + (int64_t)hi * d * post + lo;
+                ffacc acc;
+                for (int a = 0; a < d; ++a) acc.add(ff_mul(src[(int64_t)a * post], Gs[a * 8 + c]));
+                nxt[e] = acc.get();
+            }
+            __syncwarp();
+            ff *t = cur; cur = nxt; nxt = t;
+        }
+        // z_v, scale, blocked write (in the slice's scale, returned to the input's)
+        const ff zv = cur[0];
+        const bool zero_site = (zv.h == 0.f);
+        int mob = 0;
+        for (int e = lane; e < n; e += 32) mob = max(mob, (__float_as_int(cur[e].h) >> 23) & 0xFF);
+        for (int off = 16; off > 0; off >>= 1) mob = max(mob, __shfl_xor_sync(0xffffffffu, mob, off));
+        // scale of a zero site: 2^e with e the frexp exponent of its largest entry
+        const int se = mob > 0 ? mob - 126 : 0;
+        const ff inv_s = {__int_as_float((127 - se) << 23), 0.f};   // 2^-se
+        double *M = p.Mb + member * p.c_stride + p.c_tens_off[v];
+        const int32_t *boff = p.c_blk_off + (int64_t)v * kBlkStride;
+        const ff f = zero_site ? inv_s : ff_div({1.f, 0.f}, zv);
+        for (int e = lane; e < n; e += 32) {
+            int r = e, mask = 0, pos = 0, bm = 1;
+            for (int i = kc - 1; i >= 0; --i) {
+                int dgt;
+                r = fdivmod(r, cdims[i], cinv[i], dgt);
+                if (dgt > 0) { mask |= 1 << i; pos += (dgt - 1) * bm; bm *= cdims[i] - 1; }
+            }
+            const ff m = ff_mul(cur[e], f);
+            M[boff[mask] + pos] = (double)m.h + (double)m.l;
+        }
+        if (lane == 0) {
+            const double up = __longlong_as_double((long long)(1023 + ex) << 52);   // 2^ex
+            const double zt = ((double)zv.h + (double)zv.l) * up;
+            p.z[member * p.n_sites + v] = zt;
+            p.scale[member * p.n_sites + v] = zero_site ? ldexp(1.0, se) * up : 1.0;
+            p.zero[member * p.n_sites + v] = zero_site ? 1 : 0;
+        }
+        __syncwarp();
+    }
+}
+
+// ln|Z_ref|, sign(Z_ref) and the number of zero sites, one block per member:
+// per-thread partials over a fixed stride, then a fixed shared-memory tree, so
+// the sum order depends only on the site count.  (The FP64 logarithm is long;
+// a block per member spreads it over the SMs.)
+constexpr int kVacThreads = 256;
+
+__global__ void __launch_bounds__(kVacThreads) vacuum_kernel(const double *z, int n_sites, int64_t members, double *vac)
+{
+    __shared__ double s_lg[kVacThreads];
+    __shared__ int s_neg[kVacThreads], s_nz[kVacThreads];
+    const int64_t m = blockIdx.x;
     if (m >= members) return;
     double lg = 0.0;
     int neg = 0, nz = 0;
-    for (int v = lane; v < n_sites; v += 32) {
+    for (int v = threadIdx.x; v < n_sites; v += kVacThreads) {
         const double x = z[m * n_sites + v];
         if (x == 0.0) { ++nz; continue; }
         lg += log(fabs(x));
         neg += (x < 0.0);
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        lg += __shfl_xor_sync(0xffffffffu, lg, off);
-        neg += __shfl_xor_sync(0xffffffffu, neg, off);
-        nz += __shfl_xor_sync(0xffffffffu, nz, off);
+    s_lg[threadIdx.x] = lg; s_neg[threadIdx.x] = neg; s_nz[threadIdx.x] = nz;
+    __syncthreads();
+    for (int h = kVacThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s_lg[threadIdx.x] += s_lg[threadIdx.x + h];
+            s_neg[threadIdx.x] += s_neg[threadIdx.x + h];
+            s_nz[threadIdx.x] += s_nz[threadIdx.x + h];
+        }
+        __syncthreads();
     }
-    if (lane == 0) {
-        vac[3 * m] = lg;
-        vac[3 * m + 1] = (neg & 1) ? -1.0 : 1.0;
-        vac[3 * m + 2] = (double)nz;
+    if (threadIdx.x == 0) {
+        vac[3 * m] = s_lg[0];
+        vac[3 * m + 1] = (s_neg[0] & 1) ? -1.0 : 1.0;
+        vac[3 * m + 2] = (double)s_nz[0];
     }
 }
 
@@ -884,7 +1026,7 @@ int grid_for(int64_t n, int block, int n_sm)
 pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, double damping,
                      cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags, int arithmetic)
 {
-    const Geometry &g = p->full;
+    const Geometry &g = p->geo->full;
     const int n_sets = p->n_sets;
     // table sizes: halves of the largest site
     int tabA = 1, tabC = 1;
@@ -1032,7 +1174,7 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
 pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t *h_flag)
 {
     (void)h_flag;
-    const Geometry &f = p->full, &c = p->closed;
+    const Geometry &f = p->geo->full, &c = p->geo->closed;
     int nmax = 1;
     for (int v = 0; v < f.n_sites; ++v) {
         int n = 1;
@@ -1049,19 +1191,19 @@ pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t 
         cudaFuncSetAttribute(block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // device table of open positions and dims
     std::vector<int32_t> open_pos(f.n_bonds, -1);
-    for (size_t q = 0; q < p->open_bonds.size(); ++q) open_pos[p->open_bonds[q]] = (int32_t)q;
+    for (size_t q = 0; q < p->geo->open_bonds.size(); ++q) open_pos[p->geo->open_bonds[q]] = (int32_t)q;
     DevBuf tab;
-    const size_t tb = (f.n_bonds + p->open_dims.size() + 1) * 4;
+    const size_t tb = (f.n_bonds + p->geo->open_dims.size() + 1) * 4;
     pne_status st = dev_alloc(ctx, tab, tb, s);
     if (st) return st;
     int32_t *d_open_pos = (int32_t *)tab.ptr, *d_open_dims = d_open_pos + f.n_bonds;
     std::vector<int32_t> h(open_pos);
-    h.insert(h.end(), p->open_dims.begin(), p->open_dims.end());
+    h.insert(h.end(), p->geo->open_dims.begin(), p->geo->open_dims.end());
     h.push_back(0);
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(tab.ptr, h.data(), tb, cudaMemcpyHostToDevice, s));
+    if ((st = upload(ctx, tab.ptr, h.data(), tb, s))) return st;
     BlockParams bp;
     bp.n_sets = p->n_sets; bp.n_slices = p->n_slices; bp.n_sites = f.n_sites;
-    bp.n_bonds_full = f.n_bonds; bp.n_open = (int)p->open_bonds.size();
+    bp.n_bonds_full = f.n_bonds; bp.n_open = (int)p->geo->open_bonds.size();
     bp.open_dims = d_open_dims; bp.open_pos = d_open_pos;
     bp.f_site_ptr = f.d_site_ptr; bp.f_site_bonds = f.d_site_bonds; bp.f_bond_dim = f.d_bond_dim;
     bp.f_bond_site = f.d_bond_site; bp.f_tens_off = f.d_tens_off; bp.f_stride = f.tens_off[f.n_sites];
@@ -1076,14 +1218,19 @@ pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t 
     if (g > (int64_t)ctx->n_sm * 16) g = (int64_t)ctx->n_sm * 16;
     {
         ProfScope ps(ctx, s, "gauge_block");
-        block_kernel<<<(int)g, wpb * 32, smem, s>>>(bp);
+        if (p->arithmetic == 1) {
+            const size_t smem_ff = smem + (size_t)wpb * 64 * sizeof(ff);   // plus one gauge matrix per warp
+            if (smem_ff > 48 * 1024) cudaFuncSetAttribute(block_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ff);
+            block_ff_kernel<<<(int)g, wpb * 32, smem_ff, s>>>(bp);
+        } else {
+            block_kernel<<<(int)g, wpb * 32, smem, s>>>(bp);
+        }
     }
     PNE_CUDA_TRY(ctx, cudaGetLastError());
-    const int vwarps = 8;
     {
         ProfScope ps(ctx, s, "vacuum");
-        vacuum_kernel<<<(int)((p->n_members + vwarps - 1) / vwarps), vwarps * 32, 0, s>>>(
-            (const double *)p->site_info.ptr, f.n_sites, p->n_members, (double *)p->vac.ptr);
+        vacuum_kernel<<<(unsigned)p->n_members, kVacThreads, 0, s>>>((const double *)p->site_info.ptr, f.n_sites,
+                                                                    p->n_members, (double *)p->vac.ptr);
     }
     PNE_CUDA_TRY(ctx, cudaGetLastError());
     dev_free(ctx, tab, s);
@@ -1094,7 +1241,7 @@ pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t 
 pne_status launch_convert_only(pne_ctx *ctx, const pne_partition *p, int dtype, cudaStream_t s)
 {
     if (dtype == PNE_F64) return PNE_OK;
-    const int64_t n = (int64_t)p->n_members * p->closed.tens_off[p->closed.n_sites];
+    const int64_t n = (int64_t)p->n_members * p->geo->closed.tens_off[p->geo->closed.n_sites];
     ProfScope ps(ctx, s, "convert");
     if (dtype == PNE_BF16)
         convert_kernel<<<grid_for(n, 256, ctx->n_sm), 256, 0, s>>>((const double *)p->Mb.ptr, n, dtype, nullptr,
@@ -1109,7 +1256,7 @@ pne_status launch_convert_only(pne_ctx *ctx, const pne_partition *p, int dtype, 
 pne_status launch_convert(pne_ctx *ctx, pne_partition *p, int dtype, cudaStream_t s)
 {
     if (dtype == PNE_F64 || p->mb32_dtype == dtype) return PNE_OK;
-    const int64_t n = (int64_t)p->n_members * p->closed.tens_off[p->closed.n_sites];
+    const int64_t n = (int64_t)p->n_members * p->geo->closed.tens_off[p->geo->closed.n_sites];
     pne_status st;
     if (dtype == PNE_BF16) {
         if (!p->Mb16.ptr && (st = dev_alloc(ctx, p->Mb16, n * 2, s))) return st;

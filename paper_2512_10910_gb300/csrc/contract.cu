@@ -29,6 +29,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
 #include <unordered_map>
 
 #include "pne_internal.h"
@@ -523,6 +524,7 @@ pne_status run_general(pne_ctx *ctx, KERN kern, const ContractParams &cp, size_t
 namespace {
 
 constexpr int kPlanInts = kMaxSteps * kStepInts;
+constexpr int kClassMin = 8;           // smallest running-tensor class of the shaped contraction
 
 // Local structure of a cluster, independent of where it sits: site slots
 // (rank in the sorted vertex list), the leg of each bond end and each bond's
@@ -596,66 +598,161 @@ __global__ void shape_plan_kernel(ContractParams P, const int32_t *rep, int n_sh
     }
 }
 
+// The multiply-adds of every step of a shape's plan, in the order the
+// contraction runs them (step, output entry o, closed entry cc), each packed as
+// (xi << 16) | mi: xi indexes the running tensor, mi the site's excited block.
+// One warp per shape; the plan's digit decoding is done here once instead of
+// per cluster and per multiply-add.
+__global__ void shape_ops_kernel(const int32_t *plans, const int32_t *plan_steps, const int64_t *op_off, int n_shapes,
+                                 int32_t *ops)
+{
+    const int lane = threadIdx.x & 31;
+    for (int sh = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sh < n_shapes; sh += (gridDim.x * blockDim.x) >> 5) {
+        const int *plan = plans + (int64_t)sh * kPlanInts;
+        int64_t at = op_off[sh];
+        for (int t = 0; t < plan_steps[sh]; ++t) {
+            const int *st = plan + t * kStepInts;
+            const int nF = st[2], nC = st[3], outsz = st[4], closz = st[5];
+            const int *dimsF = st + 8, *sxF = dimsF + kMaxFront, *smF = sxF + kMaxFront;
+            const int *dimsC = smF + kMaxFront, *sxC = dimsC + kMaxClose, *smC = sxC + kMaxClose;
+            for (int idx = lane; idx < outsz * closz; idx += 32) {
+                int r = idx / closz, rc = idx % closz, xi = 0, mi = 0;
+                for (int q = nF - 1; q >= 0; --q) { const int d = r % dimsF[q]; r /= dimsF[q]; xi += d * sxF[q]; mi += d * smF[q]; }
+                for (int q = nC - 1; q >= 0; --q) { const int d = rc % dimsC[q]; rc /= dimsC[q]; xi += d * sxC[q]; mi += d * smC[q]; }
+                // xi < 256 (shaped plans keep every running tensor within 256
+                // entries) and mi < 4096 (site tensors hold at most 4096 entries)
+                ops[at + idx] = (xi << 16) | mi;
+            }
+            at += (int64_t)outsz * closz;
+        }
+    }
+}
+
+// Per cluster and plan step: the site and the offset of its excited block
+// within one tensor set (geometry only), so that the contraction reads each
+// step's block base with one independent load.
+__global__ void cluster_steps_kernel(ContractParams P, const int32_t *shape_of, const int32_t *plans,
+                                     const int32_t *plan_steps, int stride, int32_t *step_off, int32_t *step_site)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < P.n_clusters;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int sh = shape_of[c];
+        const int *plan = plans + (int64_t)sh * kPlanInts;
+        const int32_t *V = P.cl_verts + c * P.vwidth;
+        for (int t = 0; t < plan_steps[sh]; ++t) {
+            const int site = V[plan[t * kStepInts + 6]];
+            step_site[c * stride + t] = site;
+            step_off[c * stride + t] = (int32_t)(P.tens_off[site] + P.blk_off[site * kBlkStride + plan[t * kStepInts + 1]]);
+        }
+    }
+}
+
+// Exponent handling of the running tensor on the integer pipes: the biased
+// exponent of a value, and 2^-e built from bits.  Rescaling by a power of two is
+// exact, so when it happens does not change a single bit of the result (short of
+// overflow or subnormals): FP64 rescales only when the largest entry leaves
+// 2^[-64, 64], the FP32 family after every step.
+template <typename T> struct Expo;
+template <> struct Expo<double> {
+    static constexpr int kBias = 1023, kWindow = 64;
+    __device__ static int biased(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+    __device__ static double inv_pow2(int e) { return __longlong_as_double((long long)(kBias - e) << 52); }   // e < kBias
+};
+template <> struct Expo<float> {
+    static constexpr int kBias = 127, kWindow = 0;
+    __device__ static int biased(float x) { return (__float_as_int(x) >> 23) & 0xFF; }
+    __device__ static float inv_pow2(int e) { return __int_as_float((kBias - e) << 23); }   // e < kBias
+};
+
+// One cluster c of tensor set b by its shape's plan.  The lane keeps its
+// running tensor at X[j * 32] (interleaved with the other lanes, so shared
+// memory is conflict-free).  Each output entry is a chain of fused
+// multiply-adds in the plan's order; the multiply-add list is walked eight at a
+// time with all loads of a group issued before its chain, so the latency of
+// the site-tensor loads overlaps.  Every contraction path (one network, the
+// fused batch) runs this routine, so their values agree bit for bit.
+template <typename T, typename L, int R>
+__device__ __forceinline__ void shaped_cluster(const ContractParams &P, const int *plan, int nsteps, const int32_t *ops,
+                                               const int32_t *soff, const int32_t *ssite, int64_t c, int b, T *X, T *Y)
+{
+    X[0] = (T)1;
+    int expo = 0, nz = 0;
+    double zs = 1.0;
+    for (int t = 0; t < nsteps; ++t) {
+        const int *st = plan + t * kStepInts;
+        const int outsz = st[4], closz = st[5];
+        const int64_t mbase = (int64_t)b * P.stride + __ldg(soff + t);
+        int mxb = 0;                                   // largest biased exponent among the outputs
+        // the step's (o, cc) list walked flat, eight multiply-adds at a time:
+        // a group's loads are issued together even when it spans outputs
+        const int n_ops = outsz * closz;
+        T acc = (T)0;
+        int cc = 0, o = 0;
+        for (int k0 = 0; k0 < n_ops; k0 += 8) {
+            const int m = min(8, n_ops - k0);
+            int32_t pk[8];
+            T xv[8], mv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) pk[k] = (k < m) ? __ldg(ops + k0 + k) : 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                xv[k] = rnd<R>(X[(pk[k] >> 16) * 32]);
+                mv[k] = (k < m) ? (T)L::get(P.M, mbase + (pk[k] & 0xffff)) : (T)0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (k < m) {
+                    acc = fma(xv[k], mv[k], acc);
+                    if (++cc == closz) {
+                        Y[o * 32] = acc;
+                        mxb = max(mxb, Expo<T>::biased(acc));
+                        acc = (T)0; cc = 0; ++o;
+                    }
+                }
+            }
+        }
+        ops += n_ops;
+        if (mxb > 0) {
+            const int e = mxb - (Expo<T>::kBias - 1);      // the frexp exponent of the largest entry
+            if (e > Expo<T>::kWindow || e < -Expo<T>::kWindow) {
+                const T sc = (e < Expo<T>::kBias) ? Expo<T>::inv_pow2(e) : (T)ldexp(1.0, -e);   // 2^-e
+                for (int o = 0; o < outsz; ++o) Y[o * 32] *= sc;
+                expo += e;
+            }
+        }
+        T *tmp = X; X = Y; Y = tmp;
+        const int site = __ldg(ssite + t);
+        if (P.zero[(int64_t)b * P.n_sites + site]) { ++nz; zs *= P.scale[(int64_t)b * P.n_sites + site]; }
+    }
+    P.w[(int64_t)b * P.n_clusters + c] = ldexp((double)X[0], expo) * zs;
+    P.nzc[(int64_t)b * P.n_clusters + c] = nz;
+}
+
 // One cluster per lane; the 32 lanes of a warp take consecutive clusters in
-// shape order and run the same plan on their own sites.  Lane l keeps its
-// intermediate tensor at X[j * 32 + l] (conflict-free shared memory).
+// shape order and run the same plan on their own sites.
+// Clusters perm[i0, i1) (one running-tensor class) of every tensor set.
 template <typename T, typename L, int R>
 __global__ void __launch_bounds__(256) contract_shaped_kernel(ContractParams P, const int32_t *perm,
                                                               const int32_t *shape_of, const int32_t *plans,
-                                                              const int32_t *plan_steps, int xmax)
+                                                              const int32_t *plan_steps, const int32_t *ops,
+                                                              const int64_t *op_off, const int32_t *step_off,
+                                                              const int32_t *step_site, int sstride, int xmax,
+                                                              int64_t i0, int64_t i1)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     T *X0 = (T *)smem_raw + (int64_t)wib * 2 * xmax * 32 + lane;
     T *X1 = X0 + (int64_t)xmax * 32;
-    const int64_t groups = (P.n_clusters + 31) / 32;
+    const int64_t groups = (i1 - i0 + 31) / 32;
     const int64_t items = groups * P.n_members;
     for (int64_t it = (int64_t)blockIdx.x * wpb + wib; it < items; it += (int64_t)gridDim.x * wpb) {
         const int b = (int)(it / groups);
-        const int64_t i = (it % groups) * 32 + lane;
-        if (i >= P.n_clusters) continue;
+        const int64_t i = i0 + (it % groups) * 32 + lane;
+        if (i >= i1) continue;
         const int64_t c = perm[i];
         const int sh = shape_of[c];
-        const int *plan = plans + (int64_t)sh * kPlanInts;
-        const int nsteps = plan_steps[sh];
-        const int32_t *V = P.cl_verts + c * P.vwidth;
-        T *X = X0, *Y = X1;
-        X[0] = (T)1;
-        int expo = 0, nz = 0;
-        double zs = 1.0;
-        for (int t = 0; t < nsteps; ++t) {
-            const int *st = plan + t * kStepInts;
-            const int mask = st[1], nF = st[2], nC = st[3], outsz = st[4], closz = st[5];
-            const int site = V[st[6]];
-            const int *dimsF = st + 8, *sxF = dimsF + kMaxFront, *smF = sxF + kMaxFront;
-            const int *dimsC = smF + kMaxFront, *sxC = dimsC + kMaxClose, *smC = sxC + kMaxClose;
-            const int *invF = smC + kMaxClose, *invC = invF + kMaxFront;
-            const int64_t mbase = (int64_t)b * P.stride + P.tens_off[site] + P.blk_off[site * kBlkStride + mask];
-            T mx = (T)0;
-            for (int o = 0; o < outsz; ++o) {
-                int r = o, xb = 0, mb = 0;
-                for (int q = nF - 1; q >= 0; --q) { int d; r = fdivmod(r, dimsF[q], __int_as_float(invF[q]), d); xb += d * sxF[q]; mb += d * smF[q]; }
-                T acc = (T)0;
-                for (int cc = 0; cc < closz; ++cc) {
-                    int rc = cc, xi = xb, mi = mb;
-                    for (int q = nC - 1; q >= 0; --q) { int d; rc = fdivmod(rc, dimsC[q], __int_as_float(invC[q]), d); xi += d * sxC[q]; mi += d * smC[q]; }
-                    acc = fma(rnd<R>(X[xi * 32]), (T)L::get(P.M, mbase + mi), acc);
-                }
-                Y[o * 32] = acc;
-                mx = fmax(mx, fabs(acc));
-            }
-            if (mx > (T)0) {
-                int e;
-                frexp((double)mx, &e);
-                const T sc = (T)pow2(-e);
-                for (int o = 0; o < outsz; ++o) Y[o * 32] *= sc;
-                expo += e;
-            }
-            T *tmp = X; X = Y; Y = tmp;
-            if (P.zero[(int64_t)b * P.n_sites + site]) { ++nz; zs *= P.scale[(int64_t)b * P.n_sites + site]; }
-        }
-        P.w[(int64_t)b * P.n_clusters + c] = ldexp((double)X[0], expo) * zs;
-        P.nzc[(int64_t)b * P.n_clusters + c] = nz;
+        shaped_cluster<T, L, R>(P, plans + (int64_t)sh * kPlanInts, plan_steps[sh], ops + op_off[sh],
+                                step_off + c * sstride, step_site + c * sstride, c, b, X0, X1);
     }
 }
 
@@ -663,20 +760,32 @@ template <typename T, typename L, int R>
 pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &rec, cudaStream_t s)
 {
     auto kern = contract_shaped_kernel<T, L, R>;
-    const int xmax = rec.max_out;
-    const int per_warp = 2 * xmax * 32 * (int)sizeof(T);
-    int wpb = (100 * 1024) / per_warp;           // about two blocks per SM
-    if (wpb > 8) wpb = 8;
-    if (wpb < 1) wpb = 1;
-    const size_t smem = (size_t)wpb * per_warp;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int64_t items = ((cp.n_clusters + 31) / 32) * cp.n_members;
-    int64_t g = (items + wpb - 1) / wpb;
-    const int64_t cap = (int64_t)ctx->n_sm * 16;
-    if (g > cap) g = cap;
-    kern<<<(int)g, wpb * 32, smem, s>>>(cp, (const int32_t *)rec.perm.ptr, (const int32_t *)rec.shape_of.ptr,
-                                        (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr, xmax);
-    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    // one launch per running-tensor class, each with buffers (and so an
+    // occupancy) sized for its own class
+    const size_t smem_cap = 200 * 1024;
+    bool attr_set = false;
+    for (size_t q = 0; q + 1 < rec.class_start.size(); ++q) {
+        const int64_t i0 = rec.class_start[q], i1 = rec.class_start[q + 1];
+        if (i1 <= i0) continue;
+        const int xmax = std::min(rec.class_xmax[q], std::max(rec.max_out, 1));
+        const int per_warp = 2 * xmax * 32 * (int)sizeof(T);
+        int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (smem_cap / 4) / per_warp));   // about four blocks per SM
+        const size_t smem = (size_t)wpb * per_warp;
+        if (smem > 48 * 1024 && !attr_set) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
+            attr_set = true;
+        }
+        const int64_t items = ((i1 - i0 + 31) / 32) * cp.n_members;
+        int64_t g = (items + wpb - 1) / wpb;
+        const int64_t cap = (int64_t)ctx->n_sm * 32;
+        if (g > cap) g = cap;
+        kern<<<(int)g, wpb * 32, smem, s>>>(cp, (const int32_t *)rec.perm.ptr, (const int32_t *)rec.shape_of.ptr,
+                                            (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr,
+                                            (const int32_t *)rec.ops.ptr, (const int64_t *)rec.op_off.ptr,
+                                            (const int32_t *)rec.step_off.ptr, (const int32_t *)rec.step_site.ptr,
+                                            rec.step_stride, xmax, i0, i1);
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+    }
     return PNE_OK;
 }
 
@@ -688,9 +797,13 @@ pne_status dispatch_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRec
 
 }  // namespace
 
-pne_status prepare_shapes(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, cudaStream_t s)
+// Shape preparation, first half: hash every cluster's local structure and
+// queue the hashes' readback (no synchronisation; the caller's next
+// synchronisation of `s` brings them).
+pne_status shapes_begin(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s)
 {
     rec.shaped = false;
+    sp.active = false;
     if (rec.n_clusters == 0 || all_dims_two(g)) return PNE_OK;
     const int64_t n = (int64_t)rec.n_clusters;
     ContractParams cp;
@@ -699,17 +812,43 @@ pne_status prepare_shapes(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, cuda
     cp.cl_edges = (const int32_t *)rec.cl_edges.ptr; cp.cl_verts = (const int32_t *)rec.cl_verts.ptr;
     cp.cl_size = (const int32_t *)rec.cl_size.ptr;
     cp.bond_site = g.d_bond_site; cp.bond_dim = g.d_bond_dim; cp.bond_leg = g.d_bond_leg;
-    DevBuf dh;
-    pne_status st = dev_alloc(ctx, dh, n * 8, s);
+    pne_status st = dev_alloc(ctx, sp.dh, n * 8, s);
     if (st) return st;
     {
         ProfScope ps(ctx, s, "shapes");
-        shape_hash_kernel<<<grid_for(n, 128, ctx->n_sm), 128, 0, s>>>(cp, (unsigned long long *)dh.ptr);
+        shape_hash_kernel<<<grid_for(n, 128, ctx->n_sm), 128, 0, s>>>(cp, (unsigned long long *)sp.dh.ptr);
     }
     PNE_CUDA_TRY(ctx, cudaGetLastError());
+    sp.h_pinned = pinned_slot(3, n * 8);
+    if (sp.h_pinned) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(sp.h_pinned, sp.dh.ptr, n * 8, cudaMemcpyDeviceToHost, s));
+    sp.active = true;
+    return PNE_OK;
+}
+
+// Second half: shape ids, exact-key verification, one plan per shape, and the
+// clusters grouped by shape.
+pne_status shapes_finish(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s)
+{
+    if (!sp.active) return PNE_OK;
+    sp.active = false;
+    const int64_t n = (int64_t)rec.n_clusters;
+    ContractParams cp;
+    cp.n_clusters = n; cp.n_members = 1; cp.n_sites = g.n_sites;
+    cp.width = rec.width; cp.vwidth = rec.vwidth;
+    cp.cl_edges = (const int32_t *)rec.cl_edges.ptr; cp.cl_verts = (const int32_t *)rec.cl_verts.ptr;
+    cp.cl_size = (const int32_t *)rec.cl_size.ptr;
+    cp.bond_site = g.d_bond_site; cp.bond_dim = g.d_bond_dim; cp.bond_leg = g.d_bond_leg;
+    DevBuf &dh = sp.dh;
+    pne_status st;
     std::vector<unsigned long long> h(n);
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), dh.ptr, n * 8, cudaMemcpyDeviceToHost, s));
-    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (sp.h_pinned) {
+        HostScope hw__(ctx, "sync_shapes");
+        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));        // returns at once when the caller already did
+        std::memcpy(h.data(), sp.h_pinned, n * 8);
+    } else {
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), dh.ptr, n * 8, cudaMemcpyDeviceToHost, s));
+        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    }
     // shape ids in order of first appearance (deterministic)
     std::unordered_map<unsigned long long, int32_t> id;
     id.reserve(1024);
@@ -719,64 +858,135 @@ pne_status prepare_shapes(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, cuda
         if (it == id.end()) { it = id.emplace(h[c], (int32_t)rep.size()).first; rep.push_back((int32_t)c); }
         shape[c] = it->second;
     }
-    // exact key check against the representative; a mismatch gets its own shape
+    // exact key check against the representative (a mismatch gets its own
+    // shape) and the plans of the representatives, read back together
     DevBuf dshape, drep, dbad;
     if ((st = dev_alloc(ctx, dshape, n * 4, s)) || (st = dev_alloc(ctx, drep, rep.size() * 4, s)) ||
         (st = dev_alloc(ctx, dbad, n * 4, s)))
         return st;
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dshape.ptr, shape.data(), n * 4, cudaMemcpyHostToDevice, s));
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(drep.ptr, rep.data(), rep.size() * 4, cudaMemcpyHostToDevice, s));
+    if ((st = upload(ctx, dshape.ptr, shape.data(), n * 4, s)) ||
+        (st = upload(ctx, drep.ptr, rep.data(), rep.size() * 4, s)))
+        return st;
     shape_verify_kernel<<<grid_for(n, 128, ctx->n_sm), 128, 0, s>>>(cp, (const int32_t *)dshape.ptr,
                                                                   (const int32_t *)drep.ptr, (int32_t *)dbad.ptr);
     PNE_CUDA_TRY(ctx, cudaGetLastError());
-    std::vector<int32_t> bad(n);
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bad.data(), dbad.ptr, n * 4, cudaMemcpyDeviceToHost, s));
-    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    bool any_bad = false;
-    for (int64_t c = 0; c < n; ++c)
-        if (bad[c]) { shape[c] = (int32_t)rep.size(); rep.push_back((int32_t)c); any_bad = true; }
-    const int ns = (int)rep.size();
-    if (any_bad) {
-        dev_free(ctx, drep, s);
-        if ((st = dev_alloc(ctx, drep, ns * 4, s))) return st;
-        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(drep.ptr, rep.data(), ns * 4, cudaMemcpyHostToDevice, s));
-        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dshape.ptr, shape.data(), n * 4, cudaMemcpyHostToDevice, s));
-    }
-    // plans of the representatives
-    if ((st = dev_alloc(ctx, rec.plans, (size_t)ns * kPlanInts * 4, s)) ||
-        (st = dev_alloc(ctx, rec.plan_steps, (size_t)ns * 4, s)))
-        return st;
-    {
+    int ns = (int)rep.size();
+    std::vector<int32_t> bad(n), steps, plans;
+    auto make_plans = [&](bool with_bad) -> pne_status {
+        dev_free(ctx, rec.plans, s);
+        dev_free(ctx, rec.plan_steps, s);
+        pne_status e;
+        if ((e = dev_alloc(ctx, rec.plans, (size_t)ns * kPlanInts * 4, s)) ||
+            (e = dev_alloc(ctx, rec.plan_steps, (size_t)ns * 4, s)))
+            return e;
         const size_t smem = (size_t)kCtWarps * (kMaxSteps * kStepInts + kMaxSteps + 4) * 4;
         shape_plan_kernel<<<grid_for(ns, kCtWarps, ctx->n_sm, 16), kCtWarps * 32, smem, s>>>(
             cp, (const int32_t *)drep.ptr, ns, (int32_t *)rec.plans.ptr, (int32_t *)rec.plan_steps.ptr);
         PNE_CUDA_TRY(ctx, cudaGetLastError());
+        steps.assign(ns, 0);
+        plans.assign((size_t)ns * kPlanInts, 0);
+        const size_t nb = with_bad ? (size_t)n * 4 : 0, sb = (size_t)ns * 4, pb = plans.size() * 4;
+        char *hp = (char *)pinned_slot(3, nb + sb + pb);
+        if (hp) {
+            if (nb) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(hp, dbad.ptr, nb, cudaMemcpyDeviceToHost, s));
+            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(hp + nb, rec.plan_steps.ptr, sb, cudaMemcpyDeviceToHost, s));
+            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(hp + nb + sb, rec.plans.ptr, pb, cudaMemcpyDeviceToHost, s));
+            HostScope hw__(ctx, "sync_plans");
+            PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+            if (nb) std::memcpy(bad.data(), hp, nb);
+            std::memcpy(steps.data(), hp + nb, sb);
+            std::memcpy(plans.data(), hp + nb + sb, pb);
+        } else {
+            if (nb) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bad.data(), dbad.ptr, nb, cudaMemcpyDeviceToHost, s));
+            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(steps.data(), rec.plan_steps.ptr, sb, cudaMemcpyDeviceToHost, s));
+            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(plans.data(), rec.plans.ptr, pb, cudaMemcpyDeviceToHost, s));
+            PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        }
+        return PNE_OK;
+    };
+    if ((st = make_plans(true))) return st;
+    bool any_bad = false;
+    for (int64_t c = 0; c < n; ++c)
+        if (bad[c]) { shape[c] = (int32_t)rep.size(); rep.push_back((int32_t)c); any_bad = true; }
+    if (any_bad) {
+        // hash collisions (rare): the split-off clusters become representatives
+        ns = (int)rep.size();
+        dev_free(ctx, drep, s);
+        if ((st = dev_alloc(ctx, drep, ns * 4, s))) return st;
+        if ((st = upload(ctx, drep.ptr, rep.data(), ns * 4, s)) ||
+            (st = upload(ctx, dshape.ptr, shape.data(), n * 4, s)))
+            return st;
+        if ((st = make_plans(false))) return st;
     }
-    std::vector<int32_t> steps(ns), plans((size_t)ns * kPlanInts);
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(steps.data(), rec.plan_steps.ptr, ns * 4, cudaMemcpyDeviceToHost, s));
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(plans.data(), rec.plans.ptr, plans.size() * 4, cudaMemcpyDeviceToHost, s));
-    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     rec.shape_fma.assign(ns, 0);
     rec.shape_count.assign(ns, 0);
     int max_out = 1;
     bool ok = true;
+    std::vector<int> shape_cls(ns, 0);
     for (int i = 0; i < ns; ++i) {
         if (steps[i] < 0) { ok = false; break; }
+        int mo = 1;
         for (int t = 0; t < steps[i]; ++t) {
             const int32_t *stp = plans.data() + (size_t)i * kPlanInts + t * kStepInts;
             rec.shape_fma[i] += (uint64_t)stp[4] * stp[5];
-            max_out = std::max(max_out, (int)stp[4]);
+            mo = std::max(mo, (int)stp[4]);
         }
+        max_out = std::max(max_out, mo);
+        while ((kClassMin << shape_cls[i]) < mo) ++shape_cls[i];
+    }
+    // the multiply-add lists of every shape
+    if (ok) {
+        std::vector<int64_t> off(ns + 1, 0);
+        for (int i = 0; i < ns; ++i) off[i + 1] = off[i] + (int64_t)rec.shape_fma[i];
+        dev_free(ctx, rec.ops, s);
+        dev_free(ctx, rec.op_off, s);
+        if ((st = dev_alloc(ctx, rec.ops, (size_t)std::max<int64_t>(off[ns], 1) * 4, s)) ||
+            (st = dev_alloc(ctx, rec.op_off, (size_t)(ns + 1) * 8, s)) ||
+            (st = upload(ctx, rec.op_off.ptr, off.data(), (size_t)(ns + 1) * 8, s)))
+            return st;
+        shape_ops_kernel<<<grid_for((int64_t)ns * 32, 128, ctx->n_sm), 128, 0, s>>>(
+            (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr, (const int64_t *)rec.op_off.ptr, ns,
+            (int32_t *)rec.ops.ptr);
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
     }
     for (int64_t c = 0; c < n; ++c) rec.shape_count[shape[c]]++;
-    // clusters in shape order (stable)
-    std::vector<int64_t> start(ns + 1, 0);
-    for (int i = 0; i < ns; ++i) start[i + 1] = start[i] + rec.shape_count[i];
+    // clusters by class, then shape (stable within a shape)
+    const int n_cls = ok ? 1 + *std::max_element(shape_cls.begin(), shape_cls.end()) : 1;
+    std::vector<int64_t> start(ns, 0);
+    rec.class_start.assign(n_cls + 1, 0);
+    rec.class_xmax.assign(n_cls, 0);
+    {
+        int64_t at = 0;
+        for (int q = 0; q < n_cls; ++q) {
+            rec.class_start[q] = at;
+            rec.class_xmax[q] = kClassMin << q;
+            for (int i = 0; i < ns; ++i)
+                if (!ok || shape_cls[i] == q) { start[i] = at; at += rec.shape_count[i]; }
+            if (!ok) break;
+        }
+        rec.class_start[n_cls] = at;
+    }
     std::vector<int32_t> perm(n);
     for (int64_t c = 0; c < n; ++c) perm[start[shape[c]]++] = (int32_t)c;
     if ((st = dev_alloc(ctx, rec.perm, n * 4, s))) return st;
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(rec.perm.ptr, perm.data(), n * 4, cudaMemcpyHostToDevice, s));
-    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if ((st = upload(ctx, rec.perm.ptr, perm.data(), n * 4, s))) return st;
+    // per-cluster step tables
+    if (ok) {
+        int max_steps = 1;
+        for (int i = 0; i < ns; ++i) max_steps = std::max(max_steps, steps[i]);
+        rec.step_stride = max_steps;
+        dev_free(ctx, rec.step_off, s);
+        dev_free(ctx, rec.step_site, s);
+        if ((st = dev_alloc(ctx, rec.step_off, (size_t)n * max_steps * 4, s)) ||
+            (st = dev_alloc(ctx, rec.step_site, (size_t)n * max_steps * 4, s)))
+            return st;
+        ContractParams cq = cp;
+        cq.tens_off = g.d_tens_off; cq.blk_off = g.d_blk_off;
+        cluster_steps_kernel<<<grid_for(n, 128, ctx->n_sm), 128, 0, s>>>(
+            cq, (const int32_t *)dshape.ptr, (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr,
+            max_steps, (int32_t *)rec.step_off.ptr, (int32_t *)rec.step_site.ptr);
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+    }
     rec.shape_of = dshape;
     rec.n_shapes = ns;
     rec.max_out = max_out;
@@ -814,11 +1024,11 @@ pne_status launch_plan_work(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, ui
     *fma = 0;
     if (rec.n_clusters == 0) return PNE_OK;
     ContractParams cp;
-    cp.n_clusters = (int64_t)rec.n_clusters; cp.n_members = 1; cp.n_sites = p->closed.n_sites;
+    cp.n_clusters = (int64_t)rec.n_clusters; cp.n_members = 1; cp.n_sites = p->geo->closed.n_sites;
     cp.width = rec.width; cp.vwidth = rec.vwidth;
     cp.cl_edges = (const int32_t *)rec.cl_edges.ptr; cp.cl_verts = (const int32_t *)rec.cl_verts.ptr;
     cp.cl_size = (const int32_t *)rec.cl_size.ptr;
-    cp.bond_site = p->closed.d_bond_site; cp.bond_dim = p->closed.d_bond_dim; cp.bond_leg = p->closed.d_bond_leg;
+    cp.bond_site = p->geo->closed.d_bond_site; cp.bond_dim = p->geo->closed.d_bond_dim; cp.bond_leg = p->geo->closed.d_bond_leg;
     DevBuf tot;
     pne_status st = dev_alloc(ctx, tot, 8, s);
     if (st) return st;
@@ -843,16 +1053,16 @@ pne_status launch_contract(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s
     pne_status st = launch_convert(ctx, const_cast<pne_partition *>(p), dtype, s);
     if (st) return st;
     ContractParams cp;
-    cp.n_clusters = (int64_t)rec.n_clusters; cp.n_members = p->n_members; cp.n_sites = p->closed.n_sites;
+    cp.n_clusters = (int64_t)rec.n_clusters; cp.n_members = p->n_members; cp.n_sites = p->geo->closed.n_sites;
     cp.width = rec.width; cp.vwidth = rec.vwidth;
     cp.cl_edges = (const int32_t *)rec.cl_edges.ptr; cp.cl_verts = (const int32_t *)rec.cl_verts.ptr;
     cp.cl_size = (const int32_t *)rec.cl_size.ptr;
-    cp.bond_site = p->closed.d_bond_site; cp.bond_dim = p->closed.d_bond_dim; cp.bond_leg = p->closed.d_bond_leg;
-    cp.blk_off = p->closed.d_blk_off; cp.tens_off = p->closed.d_tens_off;
-    cp.stride = p->closed.tens_off[p->closed.n_sites];
+    cp.bond_site = p->geo->closed.d_bond_site; cp.bond_dim = p->geo->closed.d_bond_dim; cp.bond_leg = p->geo->closed.d_bond_leg;
+    cp.blk_off = p->geo->closed.d_blk_off; cp.tens_off = p->geo->closed.d_tens_off;
+    cp.stride = p->geo->closed.tens_off[p->geo->closed.n_sites];
     cp.scale = (const double *)p->site_scale.ptr; cp.zero = (const int8_t *)p->site_zero.ptr;
     cp.w = (double *)t->w.ptr; cp.nzc = (int32_t *)t->nzc.ptr; cp.status = (int32_t *)t->status.ptr;
-    const bool q1 = all_dims_two(p->closed);
+    const bool q1 = all_dims_two(p->geo->closed);
     ProfScope ps__(ctx, s, "contract");
     if (!q1 && rec.shaped) {
         if (dtype == PNE_F64) { cp.M = p->Mb.ptr; return dispatch_shaped<double, Load<double>, 0>(ctx, cp, rec, s); }
@@ -911,7 +1121,7 @@ pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, std::ve
     if ((st = dev_alloc(ctx, part, (size_t)B * std::max(nd, 1) * 16, s))) return st;
     if ((st = dev_alloc(ctx, out, (size_t)B * (K + 1) * 16, s))) return st;
     if (nd > 0) {
-        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dd.ptr, desc.data(), nd * sizeof(SumDesc), cudaMemcpyHostToDevice, s));
+        if ((st = upload(ctx, dd.ptr, desc.data(), nd * sizeof(SumDesc), s))) return st;
         SumParams sp;
         sp.desc = (const SumDesc *)dd.ptr; sp.n_desc = nd; sp.n_members = B;
         sp.n_clusters = (int64_t)rec.n_clusters;
@@ -938,11 +1148,18 @@ pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, std::ve
     } else {
         PNE_CUDA_TRY(ctx, cudaMemsetAsync(out.ptr, 0, (size_t)B * (K + 1) * 16, s));
     }
-    std::vector<double> buf((size_t)B * (K + 1) * 2);
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(buf.data(), out.ptr, buf.size() * 8, cudaMemcpyDeviceToHost, s));
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_status, t->status.ptr, 4, cudaMemcpyDeviceToHost, s));
-    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    std::vector<double> buf((size_t)B * (K + 1) * 2 + 1);
+    double *hb = (double *)pinned_slot(1, buf.size() * 8);
+    double *dst = hb ? hb : buf.data();
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dst, out.ptr, (buf.size() - 1) * 8, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dst + buf.size() - 1, t->status.ptr, 4, cudaMemcpyDeviceToHost, s));
     dev_free(ctx, dd, s); dev_free(ctx, part, s); dev_free(ctx, out, s);
+    {
+        HostScope hw__(ctx, "sync_sum");
+        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    }
+    if (hb) std::memcpy(buf.data(), hb, buf.size() * 8);
+    std::memcpy(h_status, buf.data() + buf.size() - 1, 4);
     c.assign((size_t)B * (K + 1), 0.0); abs_c.assign((size_t)B * (K + 1), 0.0);
     for (size_t i = 0; i < c.size(); ++i) { c[i] = buf[2 * i]; abs_c[i] = buf[2 * i + 1]; }
     return PNE_OK;
@@ -951,7 +1168,7 @@ pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, std::ve
 pne_status launch_all_mode(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s)
 {
     const pne_partition *p = t->part;
-    const Geometry &g = p->closed;
+    const Geometry &g = p->geo->closed;
     const int K = t->K, B = p->n_members, Mc = g.n_bonds;
     if (Mc > kMaxAllBonds || g.n_sites > 64) {
         set_error(ctx, PNE_EINVAL, "ALL mode needs <= 30 closed bonds and <= 64 sites"); return PNE_EINVAL;
@@ -1021,7 +1238,9 @@ namespace {
 struct BatchGroup {
     ContractParams cp;
     int shaped;
-    const int32_t *perm, *shape_of, *plans, *plan_steps;
+    const int32_t *perm, *shape_of, *plans, *plan_steps, *ops, *step_off, *step_site;
+    const int64_t *op_off;
+    int step_stride;
     const double *vac;
     const int32_t *lvl_idx[8];
     int lvl_m[8];
@@ -1066,46 +1285,8 @@ __device__ void lane_contract(const BatchGroup &G, int64_t i, int b, T *X0, T *X
     }
     const int64_t c = G.perm[i];
     const int sh = G.shape_of[c];
-    const int *plan = G.plans + (int64_t)sh * kPlanInts;
-    const int nsteps = G.plan_steps[sh];
-    const int32_t *V = P.cl_verts + c * P.vwidth;
-    T *X = X0, *Y = X1;
-    X[0] = (T)1;
-    int expo = 0, nz = 0;
-    double zs = 1.0;
-    for (int t = 0; t < nsteps; ++t) {
-        const int *st = plan + t * kStepInts;
-        const int mask = st[1], nF = st[2], nC = st[3], outsz = st[4], closz = st[5];
-        const int site = V[st[6]];
-        const int *dimsF = st + 8, *sxF = dimsF + kMaxFront, *smF = sxF + kMaxFront;
-        const int *dimsC = smF + kMaxFront, *sxC = dimsC + kMaxClose, *smC = sxC + kMaxClose;
-            const int *invF = smC + kMaxClose, *invC = invF + kMaxFront;
-        const int64_t mbase = (int64_t)b * P.stride + P.tens_off[site] + P.blk_off[site * kBlkStride + mask];
-        T mx = (T)0;
-        for (int o = 0; o < outsz; ++o) {
-            int r = o, xb = 0, mb = 0;
-            for (int q = nF - 1; q >= 0; --q) { int d; r = fdivmod(r, dimsF[q], __int_as_float(invF[q]), d); xb += d * sxF[q]; mb += d * smF[q]; }
-            T acc = (T)0;
-            for (int cc = 0; cc < closz; ++cc) {
-                int rc = cc, xi = xb, mi = mb;
-                for (int q = nC - 1; q >= 0; --q) { int d; rc = fdivmod(rc, dimsC[q], __int_as_float(invC[q]), d); xi += d * sxC[q]; mi += d * smC[q]; }
-                acc = fma(rnd<R>(X[xi * 32]), (T)L::get(P.M, mbase + mi), acc);
-            }
-            Y[o * 32] = acc;
-            mx = fmax(mx, fabs(acc));
-        }
-        if (mx > (T)0) {
-            int e;
-            frexp((double)mx, &e);
-            const T sc = (T)pow2(-e);
-            for (int o = 0; o < outsz; ++o) Y[o * 32] *= sc;
-            expo += e;
-        }
-        T *tmp = X; X = Y; Y = tmp;
-        if (P.zero[(int64_t)b * P.n_sites + site]) { ++nz; zs *= P.scale[(int64_t)b * P.n_sites + site]; }
-    }
-    P.w[(int64_t)b * P.n_clusters + c] = ldexp((double)X[0], expo) * zs;
-    P.nzc[(int64_t)b * P.n_clusters + c] = nz;
+    shaped_cluster<T, L, R>(P, G.plans + (int64_t)sh * kPlanInts, G.plan_steps[sh], G.ops + G.op_off[sh],
+                            G.step_off + c * G.step_stride, G.step_site + c * G.step_stride, c, b, X0, X1);
 }
 
 // One persistent launch: warps take items from one queue in order.  A sum item
@@ -1246,25 +1427,28 @@ pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms
         const pne_partition *p = t->part;
         const EnumRecord &rec = *t->rec;
         if (t->mode != PNE_MODE_LOOP) { delete bp; set_error(ctx, PNE_EINVAL, "batches take LOOP-mode handles"); return PNE_EINVAL; }
-        const bool q1 = all_dims_two(p->closed);
+        const bool q1 = all_dims_two(p->geo->closed);
         if (!q1 && !rec.shaped && rec.n_clusters > 0) {
             delete bp; set_error(ctx, PNE_EINVAL, "a cluster exceeds the batched kernel's limits"); return PNE_EINVAL;
         }
         if ((st = launch_convert(ctx, const_cast<pne_partition *>(p), dtype, s))) { delete bp; return st; }
         BatchGroup &G = groups[g];
         ContractParams &cp = G.cp;
-        cp.n_clusters = (int64_t)rec.n_clusters; cp.n_members = p->n_members; cp.n_sites = p->closed.n_sites;
+        cp.n_clusters = (int64_t)rec.n_clusters; cp.n_members = p->n_members; cp.n_sites = p->geo->closed.n_sites;
         cp.width = rec.width; cp.vwidth = rec.vwidth;
         cp.cl_edges = (const int32_t *)rec.cl_edges.ptr; cp.cl_verts = (const int32_t *)rec.cl_verts.ptr;
         cp.cl_size = (const int32_t *)rec.cl_size.ptr;
-        cp.bond_site = p->closed.d_bond_site; cp.bond_dim = p->closed.d_bond_dim; cp.bond_leg = p->closed.d_bond_leg;
-        cp.blk_off = p->closed.d_blk_off; cp.tens_off = p->closed.d_tens_off; cp.stride = p->closed.tens_off[p->closed.n_sites];
+        cp.bond_site = p->geo->closed.d_bond_site; cp.bond_dim = p->geo->closed.d_bond_dim; cp.bond_leg = p->geo->closed.d_bond_leg;
+        cp.blk_off = p->geo->closed.d_blk_off; cp.tens_off = p->geo->closed.d_tens_off; cp.stride = p->geo->closed.tens_off[p->geo->closed.n_sites];
         cp.M = dtype == PNE_F64 ? p->Mb.ptr : (dtype == PNE_BF16 ? p->Mb16.ptr : p->Mb32.ptr);
         cp.scale = (const double *)p->site_scale.ptr; cp.zero = (const int8_t *)p->site_zero.ptr;
         cp.w = (double *)t->w.ptr; cp.nzc = (int32_t *)t->nzc.ptr; cp.status = (int32_t *)t->status.ptr;
         G.shaped = (!q1 && rec.shaped) ? 1 : 0;
         G.perm = (const int32_t *)rec.perm.ptr; G.shape_of = (const int32_t *)rec.shape_of.ptr;
         G.plans = (const int32_t *)rec.plans.ptr; G.plan_steps = (const int32_t *)rec.plan_steps.ptr;
+        G.ops = (const int32_t *)rec.ops.ptr; G.op_off = (const int64_t *)rec.op_off.ptr;
+        G.step_off = (const int32_t *)rec.step_off.ptr; G.step_site = (const int32_t *)rec.step_site.ptr;
+        G.step_stride = rec.step_stride;
         G.vac = (const double *)p->vac.ptr;
         for (int l = 0; l < 8; ++l) { G.lvl_idx[l] = nullptr; G.lvl_m[l] = 0; }
         if (rec.levels.size() > 8) { delete bp; set_error(ctx, PNE_EOVERFLOW, "too many tuple levels"); return PNE_EOVERFLOW; }

@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 
 #include "pne_internal.h"
@@ -306,6 +307,8 @@ struct SearchCtl {
     int32_t cand_overflow;        // a candidate list outgrew kNodeU
     int32_t stop;                 // first level whose children did not fit (0: none)
     int64_t need;                 // arena size that level asked for
+    uint32_t bar_count, bar_gen;  // grid barrier of the cooperative level kernel
+    int32_t bar_timeout, pad;
 };
 
 struct Arena {
@@ -323,7 +326,10 @@ struct Arena {
 __global__ void arena_init_kernel(Arena a, int n_roots)
 {
     if (threadIdx.x <= kPrefixMax + 1) a.lv[threadIdx.x] = threadIdx.x == 0 ? 0 : n_roots;
-    if (threadIdx.x == 0) { a.ctl->cand_overflow = 0; a.ctl->stop = 0; a.ctl->need = 0; }
+    if (threadIdx.x == 0) {
+        a.ctl->cand_overflow = 0; a.ctl->stop = 0; a.ctl->need = 0;
+        a.ctl->bar_count = 0; a.ctl->bar_gen = 0; a.ctl->bar_timeout = 0; a.ctl->pad = 0;
+    }
 }
 
 // ---------------------------------------------------------------- roots
@@ -379,60 +385,95 @@ constexpr int kExpandWarps = 4;
 constexpr int kMaxNew = kNodeU / (kPrefixMax + 1);   // new candidates per step (site degree - 1)
 constexpr int kNodeWords = (int)(sizeof(Node) / 4);
 
-// every degree-one site of V has a bond among U[lo..hi) (endpoints UA/UB) or the
-// new candidates (endpoints NA/NB)
+// Node word offsets (the children are written word by word) and the staging
+// record of a growing lane: new-candidate count, new candidates, then the
+// child's vertex multiset in node order (vn, vdang, vv[], vd[]).
+constexpr int kOffNU = (int)(offsetof(Node, nU) / 4);
+constexpr int kOffT = (int)(offsetof(Node, t) / 4);
+constexpr int kOffVN = (int)(offsetof(Node, vn) / 4);
+constexpr int kStageWords = 1 + kMaxNew + 2 + 2 * kNodeV;
+static_assert(offsetof(Node, vdang) / 4 == kOffVN + 1 && offsetof(Node, vv) / 4 == kOffVN + 2 &&
+              offsetof(Node, vd) / 4 == kOffVN + 2 + kNodeV && sizeof(Node) / 4 == kOffVN + 2 + 2 * kNodeV,
+              "node layout");
+
+// Every degree-one vertex of V = V(S) + U[i] can still be repaired inside this
+// subtree.  A vertex of S (index < old_n) is, iff some candidate after i
+// touches it (last[j] > i); new candidates only touch the vertex b that U[i]
+// brought in, which is repairable iff it has new candidates or a later
+// candidate of the list touches it.
 template <int NV>
-__device__ bool repairable_split(const VSet<NV> &V, const int32_t *UA, const int32_t *UB, int lo, int hi,
-                                 const int32_t *NA, const int32_t *NB, int nn)
+__device__ bool repairable_after(const VSet<NV> &V, int old_n, int i, const int32_t *last, int b, int nn,
+                                 const int32_t *UA, const int32_t *UB, int nU)
 {
     if (V.dang == 0) return true;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        if (i >= V.n) break;
-        if (V.d[i] != 1) continue;
-        const int x = V.v[i];
-        bool found = false;
-        for (int q = lo; q < hi && !found; ++q) found = (UA[q] == x || UB[q] == x);
-        for (int q = 0; q < nn && !found; ++q) found = (NA[q] == x || NB[q] == x);
-        if (!found) return false;
+    for (int j = 0; j < NV; ++j) {
+        if (j >= V.n) break;
+        if (V.d[j] != 1) continue;
+        if (j < old_n) {
+            if (last[j] <= i) return false;
+        } else if (nn == 0) {
+            bool found = false;
+            for (int q = i + 1; q < nU && !found; ++q) found = (UA[q] == b || UB[q] == b);
+            if (!found) return false;
+        }
     }
     return true;
 }
 
-__global__ void __launch_bounds__(32 * kExpandWarps)
-expand_kernel(GeomView g, Arena A, int lo_level, int hi_level, int K, int mode, int pass, Emit out)
+// The block's chunk of the node range [r0, r1).  kChildren writes the
+// children from arena slot next + cbase_chunk on (cbase_chunk: the children of
+// the chunks before this one).
+__device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int64_t r1, int K, int mode, int pass,
+                             const Emit &out, int64_t next, int64_t cbase_chunk)
 {
     __shared__ Node sh_node[kExpandWarps];
     __shared__ int32_t sh_a[kExpandWarps][kNodeU], sh_b[kExpandWarps][kNodeU];
+    __shared__ int32_t sh_last[kExpandWarps][kNodeV];
+    __shared__ int32_t sh_stage[kExpandWarps][32 * kStageWords];
     __shared__ int64_t wsum[kExpandWarps];
-    if (pass == kChildren && A.ctl->stop != 0) return;              // uniform over the grid
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
+    const bool growing = (pass == kCount || pass == kChildren);
     Node &nd = sh_node[w];
-    int32_t *UA = sh_a[w], *UB = sh_b[w];
-    const int64_t r0 = A.lv[lo_level - 1], r1 = A.lv[hi_level];
+    int32_t *UA = sh_a[w], *UB = sh_b[w], *last = sh_last[w], *stage = sh_stage[w];
     const int64_t chunk = (r1 - r0 + gridDim.x - 1) / gridDim.x;
     const int64_t c0 = r0 + (int64_t)blockIdx.x * chunk;
     const int64_t c1 = c0 + chunk < r1 ? c0 + chunk : r1;
-    const int64_t next = A.lv[hi_level];                              // first child slot (kChildren)
-    const int64_t cbase_chunk = (pass == kChildren) ? A.chunk_tot[blockIdx.x] : 0;
     for (int64_t u = c0 + w; u < c1; u += kExpandWarps) {
+        // L2 loads: in the cooperative kernel these nodes were written by other
+        // blocks earlier in the same launch
         const int32_t *src = reinterpret_cast<const int32_t *>(A.nodes + u);
-        for (int q = lane; q < kNodeWords; q += 32) reinterpret_cast<int32_t *>(&nd)[q] = src[q];
+        for (int q = lane; q < kNodeWords; q += 32) reinterpret_cast<int32_t *>(&nd)[q] = __ldcg(src + q);
         __syncwarp();
-        const int nU = nd.nU, t = nd.t, anchor = nd.S[0];
+        const int nU = nd.nU, t = nd.t, anchor = nd.S[0], vn = nd.vn;
         for (int q = lane; q < nU; q += 32) {
             const int e = nd.U[q];
             UA[q] = g.bond_site[2 * e]; UB[q] = g.bond_site[2 * e + 1];
         }
         __syncwarp();
+        if (growing) {
+            // the last candidate touching each vertex of S (-1: none): a
+            // degree-one vertex of S + U[i] stays repairable iff it is > i
+            for (int j = 0; j < vn; ++j) {
+                const int x = nd.vv[j];
+                int lst = -1;
+                for (int i0 = 0; i0 < nU; i0 += 32) {
+                    const int q = i0 + lane;
+                    const unsigned m = __ballot_sync(0xffffffffu, q < nU && (UA[q] == x || UB[q] == x));
+                    if (m) lst = i0 + 31 - __clz(m);
+                }
+                if (lane == 0) last[j] = lst;
+            }
+            __syncwarp();
+        }
         int n_child = 0, n_emit = 0;
-        const int64_t cbase = (pass == kChildren) ? next + cbase_chunk + A.child_off[u] : 0;
+        const int64_t cbase = (pass == kChildren) ? next + cbase_chunk + __ldcg(A.child_off + u) : 0;
         const int64_t ebase = (pass == kEmit) ? A.base[(int64_t)(t + 1) * A.cap + u] : 0;
         for (int i0 = 0; i0 < nU; i0 += 32) {
             const int i = i0 + lane;
             bool emit = false, grow = false;
-            VSet<kPrefixMax + 2> V;
+            VSet<kNodeV> V;
             int32_t NU[kMaxNew], NA[kMaxNew], NB[kMaxNew];
             int nn = 0;
             if (i < nU) {
@@ -441,24 +482,52 @@ expand_kernel(GeomView g, Arena A, int lo_level, int hi_level, int K, int mode, 
                 const int b = !V.has(a0) ? a0 : (!V.has(a1) ? a1 : -1);
                 V.inc(a0); V.inc(a1);
                 emit = valid_set(mode, V.dang);
-                if ((pass == kCount || pass == kChildren) && may_grow(mode, t + 1, K, V.dang)) {
+                if (growing && may_grow(mode, t + 1, K, V.dang)) {
                     if (b >= 0) nn = append_new(g, b, e, anchor, V, NU, NA, NB, 0, kMaxNew, &A.ctl->cand_overflow);
-                    grow = mode == PNE_MODE_ALL || repairable_split(V, UA, UB, i + 1, nU, NA, NB, nn);
+                    grow = mode == PNE_MODE_ALL || repairable_after(V, vn, i, last, b, nn, UA, UB, nU);
                 }
             }
             const unsigned gm = __ballot_sync(0xffffffffu, grow), em = __ballot_sync(0xffffffffu, emit);
-            if (pass == kChildren && grow) {
-                Node *c = A.nodes + cbase + n_child + __popc(gm & lt);
-                for (int q = 0; q < t; ++q) c->S[q] = nd.S[q];
-                c->S[t] = nd.U[i];
-                c->t = t + 1;
-                int m = 0;
-                for (int q = i + 1; q < nU; ++q) c->U[m++] = nd.U[q];
-                for (int q = 0; q < nn; ++q) {
-                    if (m < kNodeU) c->U[m++] = NU[q]; else atomicExch(&A.ctl->cand_overflow, 1);
+            if (pass == kChildren && gm) {
+                // each growing lane stages what its child adds; then the warp
+                // writes the children one after another, 32 words per store
+                if (grow) {
+                    int32_t *st = stage + lane * kStageWords;
+                    st[0] = nn;
+                    for (int q = 0; q < nn; ++q) st[1 + q] = NU[q];
+                    st[1 + kMaxNew] = V.n;
+                    st[2 + kMaxNew] = V.dang;
+#pragma unroll
+                    for (int j = 0; j < kNodeV; ++j) { st[3 + kMaxNew + j] = V.v[j]; st[3 + kMaxNew + kNodeV + j] = V.d[j]; }
                 }
-                c->nU = m;
-                store_vset(c, V);
+                __syncwarp();
+                unsigned rem = gm;
+                for (int r = 0; rem; ++r) {
+                    const int o = __ffs(rem) - 1;
+                    rem &= rem - 1;
+                    const int io = i0 + o;
+                    const int32_t *so = stage + o * kStageWords;
+                    const int m0 = nU - io - 1, nno = so[0];
+                    int32_t *c = reinterpret_cast<int32_t *>(A.nodes + cbase + n_child + r);
+                    for (int q = lane; q < kNodeWords; q += 32) {
+                        int32_t val;
+                        if (q < kPrefixMax) {
+                            val = q < t ? nd.S[q] : (q == t ? nd.U[io] : 0);
+                        } else if (q < kPrefixMax + kNodeU) {
+                            const int idx = q - kPrefixMax;
+                            val = idx < m0 ? nd.U[io + 1 + idx] : (idx - m0 < nno ? so[1 + idx - m0] : 0);
+                        } else if (q == kOffNU) {
+                            val = m0 + nno < kNodeU ? m0 + nno : kNodeU;
+                        } else if (q == kOffT) {
+                            val = t + 1;
+                        } else {
+                            val = so[1 + kMaxNew + (q - kOffVN)];   // vn, vdang, vv[], vd[] in node order
+                        }
+                        c[q] = val;
+                    }
+                    if (lane == 0 && m0 + nno > kNodeU) atomicExch(&A.ctl->cand_overflow, 1);
+                }
+                __syncwarp();
             }
             if (pass == kEmit && emit) {
                 int32_t S[kPrefixMax + 1];
@@ -481,22 +550,86 @@ expand_kernel(GeomView g, Arena A, int lo_level, int hi_level, int K, int mode, 
         const int64_t tot = block_scan_range<32 * kExpandWarps>(A.child_cnt + c0, A.child_off + c0, len, wsum);
         if (threadIdx.x == 0) A.chunk_tot[blockIdx.x] = tot;
     }
+    __syncthreads();                                   // the shared node buffers are reused by the caller
 }
 
-// After the kCount pass of level d: scan the chunk totals in place and place
-// level d + 1, or stop the search if it does not fit.
-__global__ void __launch_bounds__(1024) level_close_kernel(Arena A, int d, int n_chunks)
+// kEmitCount / kEmit over levels lo..hi
+__global__ void __launch_bounds__(32 * kExpandWarps)
+expand_kernel(GeomView g, Arena A, int lo_level, int hi_level, int K, int mode, int pass, Emit out)
 {
-    __shared__ int64_t wsum[32];
-    const int64_t tot = block_scan_range<1024>(A.chunk_tot, A.chunk_tot, n_chunks, wsum);
+    expand_chunk(g, A, A.lv[lo_level - 1], A.lv[hi_level], K, mode, pass, out, 0, 0);
+}
+
+// Grid-wide barrier of a cooperative launch, bounded: after kSearchSpinLimit
+// polls it records a timeout and every block leaves the search.
+constexpr long long kSearchSpinLimit = 1LL << 26;
+
+__device__ bool search_barrier(SearchCtl *ctl, unsigned nblocks)
+{
+    __syncthreads();
     if (threadIdx.x == 0) {
-        const int64_t end = A.lv[d];
-        if (A.ctl->stop == 0 && end + tot <= A.cap) {
-            for (int e = d + 1; e <= kPrefixMax + 1; ++e) A.lv[e] = end + tot;
+        volatile unsigned *gen = &ctl->bar_gen;
+        const unsigned g0 = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
         } else {
-            if (A.ctl->stop == 0) { A.ctl->stop = d; A.ctl->need = end + tot; }
-            for (int e = d + 1; e <= kPrefixMax + 1; ++e) A.lv[e] = end;
+            long long spins = 0;
+            while (*gen == g0) {
+                if (++spins > kSearchSpinLimit) { atomicExch(&ctl->bar_timeout, 1); break; }
+                __nanosleep(32);
+            }
         }
+        __threadfence();
+    }
+    __syncthreads();
+    return *((volatile int32_t *)&ctl->bar_timeout) == 0;
+}
+
+// Prefix levels 1..D-1 in one cooperative launch: per level a counting phase
+// (children and emissions per node, chunk scans), a barrier, a writing phase
+// that places the next level (every block derives the same level size and stop
+// decision from the chunk totals), and a barrier.  Block 0 records the level
+// bounds and the stop for the kernels that follow.
+__global__ void __launch_bounds__(32 * kExpandWarps) bfs_levels_kernel(GeomView g, Arena A, int D, int K, int mode)
+{
+    __shared__ int64_t red[2][32 * kExpandWarps];
+    Emit none{nullptr, nullptr, nullptr, 0, 0};
+    int64_t lo = 0, hi = A.lv[1];                      // level 1: the anchors
+    for (int d = 1; d < D; ++d) {
+        expand_chunk(g, A, lo, hi, K, mode, kCount, none, 0, 0);
+        if (!search_barrier(A.ctl, gridDim.x)) return;
+        // children before this block's chunk, and in all chunks
+        int64_t before = 0, total = 0;
+        for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
+            const int64_t c = __ldcg(A.chunk_tot + q);
+            total += c;
+            if (q < (int)blockIdx.x) before += c;
+        }
+        red[0][threadIdx.x] = before; red[1][threadIdx.x] = total;
+        __syncthreads();
+        for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+            if ((int)threadIdx.x < h) {
+                red[0][threadIdx.x] += red[0][threadIdx.x + h];
+                red[1][threadIdx.x] += red[1][threadIdx.x + h];
+            }
+            __syncthreads();
+        }
+        before = red[0][0]; total = red[1][0];
+        __syncthreads();
+        const bool fits = hi + total <= A.cap;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            for (int e = d + 1; e <= kPrefixMax + 1; ++e) A.lv[e] = fits ? hi + total : hi;
+            if (!fits) { A.ctl->stop = d; A.ctl->need = hi + total; }
+        }
+        if (!fits) return;                             // the same decision in every block
+        expand_chunk(g, A, lo, hi, K, mode, kChildren, none, hi, before);
+        if (!search_barrier(A.ctl, gridDim.x)) return;
+        lo = hi;
+        hi += total;
     }
 }
 
@@ -779,7 +912,10 @@ pne_status scan_counts(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t 
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h, starts, (rows + 1) * 8, cudaMemcpyDeviceToHost, s));
     if (extra_bytes)
         PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h + rows + 1, extra_dev, extra_bytes, cudaMemcpyDeviceToHost, s));
-    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    {
+        HostScope hw__(ctx, "sync_counts");
+        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    }
     row_tot.assign(rows, 0);
     for (int r = 0; r < rows; ++r) row_tot[r] = h[r + 1] - h[r];
     if (extra_bytes) std::memcpy(extra_host, h + rows + 1, extra_bytes);
@@ -809,9 +945,11 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     const int final_kind = (K <= 1) ? 0 : (D == K - 1 ? 1 : 2);
     const bool small = (K <= 12 && umax_need <= 64);
     // chunks of the blocked passes: one wave of resident blocks
-    int per_sm = 0;
+    int per_sm = 0, per_sm_c = 0;
     PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel, 32 * kExpandWarps, 0));
+    PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, bfs_levels_kernel, 32 * kExpandWarps, 0));
     const int G = ctx->n_sm * std::max(1, per_sm);
+    const int Gc = ctx->n_sm * std::max(1, per_sm_c);   // co-resident blocks of the cooperative launch
     const int Gd = grid1(1 << 20, 128, ctx->n_sm);    // grid of the depth-first kernel
     const std::string hint_key = std::to_string(g.hash) + ":" + std::to_string(Mc) + ":" + std::to_string(K) + ":" +
                                  std::to_string(mode);
@@ -838,7 +976,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     for (;;) {
         // arena: nodes, then [lv | ctl | child_cnt | child_off | chunk_tot], then counts
         if ((st = dev_alloc(ctx, nodes, sizeof(Node) * (size_t)cap, s))) return st;
-        const size_t tab_bytes = sizeof(Readback) + (size_t)cap * 4 + (size_t)cap * 8 + (size_t)G * 8 + 64;
+        const size_t tab_bytes = sizeof(Readback) + (size_t)cap * 4 + (size_t)cap * 8 + (size_t)std::max(G, Gc) * 8 + 64;
         if ((st = dev_alloc(ctx, tables, tab_bytes, s))) return st;
         if ((st = dev_alloc(ctx, counts, (size_t)(K + 1) * cap * 4, s))) return st;
         char *tb = (char *)tables.ptr;
@@ -848,7 +986,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         A.ctl = (SearchCtl *)(tb + offsetof(Readback, ctl));
         A.child_off = (int64_t *)(tb + sizeof(Readback));
         A.chunk_tot = A.child_off + cap;
-        A.child_cnt = (int32_t *)(A.chunk_tot + G);
+        A.child_cnt = (int32_t *)(A.chunk_tot + std::max(G, Gc));
         A.counts = (int32_t *)counts.ptr;
         A.base = nullptr;
         PNE_CUDA_TRY(ctx, cudaMemsetAsync(counts.ptr, 0, (size_t)(K + 1) * cap * 4, s));
@@ -857,16 +995,12 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
             ProfScope ps__(ctx, s, "enum_roots");
             roots_kernel<<<grid1(Mc, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, mode, A, none, 0);
         }
-        for (int d = 1; d < D; ++d) {
-            {
-                ProfScope ps__(ctx, s, "enum_expand");
-                expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, d, K, mode, kCount, none);
-            }
-            level_close_kernel<<<1, 1024, 0, s>>>(A, d, G);
-            {
-                ProfScope ps__(ctx, s, "enum_expand");
-                expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, d, K, mode, kChildren, none);
-            }
+        if (D > 1) {
+            ProfScope ps__(ctx, s, "enum_expand");
+            int Dv = D, Kv = K, mv = mode;
+            void *args[] = {&gv, &A, &Dv, &Kv, &mv};
+            PNE_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void *)bfs_levels_kernel, dim3(Gc), dim3(32 * kExpandWarps),
+                                                          args, 0, s));
         }
         if (final_kind == 1) {
             ProfScope ps__(ctx, s, "enum_expand");
@@ -878,6 +1012,10 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         // one (size, node) table over the arena; the same round trip brings the
         // level bounds and the stop record
         if ((st = scan_counts(ctx, A.counts, K + 1, cap, base, per_size, s, A.lv, sizeof(Readback), &hb))) return st;
+        if (hb.ctl.bar_timeout) {
+            set_error(ctx, PNE_ETIMEOUT, "grid barrier timed out in the cluster search");
+            return PNE_ETIMEOUT;
+        }
         if (hb.ctl.cand_overflow) {
             set_error(ctx, PNE_EOVERFLOW, "candidate list overflow in the cluster search");
             return PNE_EOVERFLOW;
@@ -953,7 +1091,7 @@ pne_status enumerate_tuples(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s)
     DevBuf d_size_end;
     pne_status st = dev_alloc(ctx, d_size_end, (K + 2) * 8, s);
     if (st) return st;
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(d_size_end.ptr, size_end.data(), (K + 2) * 8, cudaMemcpyHostToDevice, s));
+    if ((st = upload(ctx, d_size_end.ptr, size_end.data(), (K + 2) * 8, s))) return st;
     // first round: every cluster that can start a pair (size <= K - s_min)
     int64_t n_in = (K - s_min >= s_min) ? size_end[K - s_min] : 0;
     DevBuf in_idx, in_ord;
@@ -977,12 +1115,26 @@ pne_status enumerate_tuples(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s)
         p.counts = nullptr; p.base = nullptr; p.out = nullptr; p.out_order = nullptr;
         DevBuf uoff;
         if ((st = dev_alloc(ctx, uoff, (n_in + 1) * 8, s))) return st;
-        {
-            ProfScope ps__(ctx, s, "enum_terms");
-            tuple_chunks_kernel<<<grid1(n_in, 256, ctx->n_sm), 256, 0, s>>>(p, (int64_t *)uoff.ptr);
-        }
         int64_t n_units = 0;
-        if ((st = device_exclusive_scan(ctx, (int64_t *)uoff.ptr, n_in, &n_units, s))) return st;
+        if (m == 1) {
+            // pairs: input tuple i is cluster i, whose size (hence the candidate
+            // range) the host knows from the size-grouped list
+            std::vector<int64_t> h_off(n_in + 1, 0);
+            for (int q = 1; q <= K; ++q)
+                for (int64_t i = rec.size_start[q]; i < std::min<int64_t>(rec.size_start[q + 1], n_in); ++i) {
+                    const int64_t lo = i + 1, hi = (q < K) ? size_end[K - q] : lo;
+                    h_off[i] = hi > lo ? (hi - lo + kTupleChunk - 1) / kTupleChunk : 0;
+                }
+            for (int64_t i = 0; i < n_in; ++i) { const int64_t c = h_off[i]; h_off[i] = n_units; n_units += c; }
+            h_off[n_in] = n_units;
+            if ((st = upload(ctx, uoff.ptr, h_off.data(), (n_in + 1) * 8, s))) return st;
+        } else {
+            {
+                ProfScope ps__(ctx, s, "enum_terms");
+                tuple_chunks_kernel<<<grid1(n_in, 256, ctx->n_sm), 256, 0, s>>>(p, (int64_t *)uoff.ptr);
+            }
+            if ((st = device_exclusive_scan(ctx, (int64_t *)uoff.ptr, n_in, &n_units, s))) return st;
+        }
         p.unit_off = (const int64_t *)uoff.ptr; p.n_units = n_units;
         const size_t tsmem = (size_t)kTupleWarps * (m * rec.vwidth + kMaxOrder + 1) * 4;
         EnumRecord::Level L;

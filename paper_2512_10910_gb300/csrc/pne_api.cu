@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -61,6 +62,70 @@ int64_t *pinned_i64(pne_ctx *ctx, size_t n)
     return buf ? buf : (n <= 64 ? fallback : nullptr);
 }
 
+namespace {
+struct HostStage {
+    char *buf = nullptr;
+    size_t cap = 0, used = 0;
+    std::vector<std::pair<cudaStream_t, cudaEvent_t>> marks;   // last copy queued per stream
+};
+HostStage &host_stage()
+{
+    thread_local HostStage h;
+    return h;
+}
+}  // namespace
+
+pne_status upload(pne_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) return PNE_OK;
+    HostStage &h = host_stage();
+    const size_t need = (bytes + 255) & ~size_t(255);
+    if (h.used + need > h.cap) {
+        // recycle the region once every copy out of it has completed
+        for (auto &m : h.marks) {
+            cudaEventSynchronize(m.second);
+            cudaEventDestroy(m.second);
+        }
+        h.marks.clear();
+        h.used = 0;
+        if (need > h.cap) {
+            if (h.buf) cudaFreeHost(h.buf);
+            h.cap = std::max(need, std::max<size_t>(2 * h.cap, size_t(1) << 20));
+            if (cudaMallocHost((void **)&h.buf, h.cap) != cudaSuccess) { h.buf = nullptr; h.cap = 0; }
+        }
+    }
+    if (!h.buf) {                                   // no pinned memory: a pageable copy
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+        return PNE_OK;
+    }
+    char *stage = h.buf + h.used;
+    std::memcpy(stage, src, bytes);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyHostToDevice, s));
+    h.used += need;
+    cudaEvent_t ev = nullptr;
+    for (auto &m : h.marks)
+        if (m.first == s) ev = m.second;
+    if (!ev) {
+        PNE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        h.marks.push_back({s, ev});
+    }
+    PNE_CUDA_TRY(ctx, cudaEventRecord(ev, s));
+    return PNE_OK;
+}
+
+void *pinned_slot(int slot, size_t bytes)
+{
+    thread_local void *buf[kPinnedSlots] = {};
+    thread_local size_t cap[kPinnedSlots] = {};
+    if (slot < 0 || slot >= kPinnedSlots) return nullptr;
+    if (bytes > cap[slot]) {
+        if (buf[slot]) cudaFreeHost(buf[slot]);
+        cap[slot] = std::max<size_t>(bytes, 4096);
+        if (cudaMallocHost(&buf[slot], cap[slot]) != cudaSuccess) { buf[slot] = nullptr; cap[slot] = 0; }
+    }
+    return buf[slot];
+}
+
 void dev_free(pne_ctx *ctx, DevBuf &b, cudaStream_t s)
 {
     if (!b.ptr) return;
@@ -93,6 +158,22 @@ ProfScope::~ProfScope()
     ctx->prof.pending.push_back({name, a, b});
 }
 
+HostScope::HostScope(pne_ctx *c, const char *n) : ctx(c), name(n)
+{
+    if (!ctx || !ctx->prof.on) return;
+    t0 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+HostScope::~HostScope()
+{
+    if (t0 < 0.0) return;
+    const double t1 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
+    auto &e = ctx->prof.acc[std::string("host:") + name];
+    e.first += 1;
+    e.second += t1 - t0;
+}
+
 EnumRecord::~EnumRecord()
 {
     if (!ctx) return;
@@ -104,6 +185,10 @@ EnumRecord::~EnumRecord()
     dev_free(ctx, perm, nullptr);
     dev_free(ctx, plans, nullptr);
     dev_free(ctx, plan_steps, nullptr);
+    dev_free(ctx, ops, nullptr);
+    dev_free(ctx, op_off, nullptr);
+    dev_free(ctx, step_off, nullptr);
+    dev_free(ctx, step_site, nullptr);
 }
 
 namespace {
@@ -118,6 +203,7 @@ uint64_t fnv(uint64_t h, const void *p, size_t n)
 // Derived tables of a geometry given bond_site, bond_dim, site_ptr, site_bonds.
 pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
 {
+    HostScope hs__(ctx, "geometry");
     const int N = g.n_sites, M = g.n_bonds;
     g.n_legs = g.site_ptr[N];
     g.bond_leg.assign(2 * M, -1);
@@ -222,10 +308,7 @@ pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
     g.d_blk_off = (int32_t *)(d + o_bo);
     g.d_color_ptr = (int32_t *)(d + o_cp);
     g.d_color_sites = (int32_t *)(d + o_cs);
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(g.storage.ptr, host.data(), bytes, cudaMemcpyHostToDevice, s));
-    // the host copy must stay alive until the copy ran
-    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    return PNE_OK;
+    return upload(ctx, g.storage.ptr, host.data(), bytes, s);
 }
 
 pne_status validate(pne_ctx *ctx, const pne_network *n)
@@ -321,6 +404,109 @@ void finalize_result(pne_result &r, int K, int mode, int dtype, const double *c,
     r.bp_residual = bp_residual;
 }
 
+// 64-bit hash of the raw geometry arrays (multiply-rotate over 32-bit words)
+uint64_t geometry_key(const pne_network *net)
+{
+    uint64_t h = 0x9E3779B97F4A7C15ull ^ ((uint64_t)(uint32_t)net->n_sites << 32 | (uint32_t)net->n_bonds);
+    auto mix = [&h](const int32_t *a, size_t n) {
+        for (size_t i = 0; i < n; ++i) {
+            h ^= (uint32_t)a[i];
+            h *= 0xBF58476D1CE4E5B9ull;
+            h ^= h >> 31;
+        }
+    };
+    mix(net->bond_site, 2 * (size_t)net->n_bonds);
+    mix(net->bond_dim, (size_t)net->n_bonds);
+    mix(net->site_ptr, (size_t)net->n_sites + 1);
+    mix(net->site_bonds, (size_t)net->site_ptr[net->n_sites]);
+    return h;
+}
+
+bool same_geometry(const GeomPair &g, const pne_network *net)
+{
+    const Geometry &f = g.full;
+    const int N = net->n_sites, M = net->n_bonds;
+    return f.n_sites == N && f.n_bonds == M && (int)f.site_bonds.size() == net->site_ptr[N] &&
+           std::equal(f.bond_site.begin(), f.bond_site.end(), net->bond_site) &&
+           std::equal(f.bond_dim.begin(), f.bond_dim.end(), net->bond_dim) &&
+           std::equal(f.site_ptr.begin(), f.site_ptr.end(), net->site_ptr) &&
+           std::equal(f.site_bonds.begin(), f.site_bonds.end(), net->site_bonds);
+}
+
+constexpr size_t kGeomCacheMax = 256;   // geometries kept per context
+
+// The full and closed geometry of a (validated) network: from the context's
+// cache when the same arrays were seen before, else built, uploaded on `s`
+// and cached.
+pne_status get_geometry(pne_ctx *ctx, const pne_network *net, cudaStream_t s, std::shared_ptr<GeomPair> &out)
+{
+    HostScope hs__(ctx, "geometry");
+    const uint64_t key = geometry_key(net);
+    {
+        std::lock_guard<std::mutex> lk(ctx->cache_mu);
+        auto it = ctx->geom_cache.find(key);
+        if (it != ctx->geom_cache.end())
+            for (auto &g : it->second)
+                if (same_geometry(*g, net)) {
+                    // the device copies may have been queued on another stream
+                    if (g->ready) PNE_CUDA_TRY(ctx, cudaStreamWaitEvent(s, g->ready, 0));
+                    out = g;
+                    return PNE_OK;
+                }
+    }
+    auto gp = std::make_shared<GeomPair>();
+    gp->ctx = ctx;
+    gp->key = key;
+    gp->free_stream = s;
+    const int N = net->n_sites, M = net->n_bonds;
+    Geometry &f = gp->full;
+    f.n_sites = N; f.n_bonds = M;
+    f.bond_site.assign(net->bond_site, net->bond_site + 2 * M);
+    f.bond_dim.assign(net->bond_dim, net->bond_dim + M);
+    f.site_ptr.assign(net->site_ptr, net->site_ptr + N + 1);
+    f.site_bonds.assign(net->site_bonds, net->site_bonds + net->site_ptr[N]);
+    // closed geometry: open bonds removed, remaining bonds renumbered in order
+    gp->closed_of_full.assign(M, -1);
+    Geometry &c = gp->closed;
+    c.n_sites = N;
+    int mc = 0;
+    for (int b = 0; b < M; ++b) {
+        if (f.bond_site[2 * b + 1] < 0) { gp->open_bonds.push_back(b); gp->open_dims.push_back(f.bond_dim[b]); continue; }
+        gp->closed_of_full[b] = mc++;
+        c.bond_site.push_back(f.bond_site[2 * b]); c.bond_site.push_back(f.bond_site[2 * b + 1]);
+        c.bond_dim.push_back(f.bond_dim[b]);
+    }
+    c.n_bonds = mc;
+    c.site_ptr.assign(N + 1, 0);
+    for (int v = 0; v < N; ++v) {
+        for (int i = f.site_ptr[v]; i < f.site_ptr[v + 1]; ++i) {
+            const int cb = gp->closed_of_full[f.site_bonds[i]];
+            if (cb >= 0) c.site_bonds.push_back(cb);
+        }
+        c.site_ptr[v + 1] = (int32_t)c.site_bonds.size();
+    }
+    pne_status st;
+    if ((st = finish_geometry(ctx, f, s)) || (st = finish_geometry(ctx, c, s))) return st;
+    PNE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&gp->ready, cudaEventDisableTiming));
+    PNE_CUDA_TRY(ctx, cudaEventRecord(gp->ready, s));
+    {
+        std::lock_guard<std::mutex> lk(ctx->cache_mu);
+        size_t n = 0;
+        for (auto &kv : ctx->geom_cache) n += kv.second.size();
+        if (n < kGeomCacheMax) ctx->geom_cache[key].push_back(gp);
+    }
+    out = gp;
+    return PNE_OK;
+}
+
+GeomPair::~GeomPair()
+{
+    if (ready) cudaEventDestroy(ready);
+    if (!ctx) return;
+    dev_free(ctx, full.storage, free_stream);
+    dev_free(ctx, closed.storage, free_stream);
+}
+
 }  // namespace pne
 
 using namespace pne;
@@ -363,6 +549,11 @@ void pne_ctx_destroy(pne_ctx *ctx)
     {
         std::lock_guard<std::mutex> lk(ctx->cache_mu);
         ctx->enum_cache.clear();
+        // the streams that last used a cached geometry may be gone by now
+        // (the server's prep streams): free on the default stream
+        for (auto &kv : ctx->geom_cache)
+            for (auto &g : kv.second) g->free_stream = nullptr;
+        ctx->geom_cache.clear();
     }
     cudaDeviceSynchronize();
     delete ctx;
@@ -384,6 +575,7 @@ pne_status pne_ctx_set_allocator(pne_ctx *ctx, pne_alloc_fn alloc, pne_free_fn f
 pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_partition_opts *opts,
                                void *stream, pne_partition **out)
 {
+    HostScope hs__(ctx, "partition");
     if (!ctx || !out) return PNE_EINVAL;
     *out = nullptr;
     pne_status st = validate(ctx, net);
@@ -398,39 +590,14 @@ pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_p
     p->ctx = ctx;
     p->last_stream = s;
     const int N = net->n_sites, M = net->n_bonds;
-    Geometry &f = p->full;
-    f.n_sites = N; f.n_bonds = M;
-    f.bond_site.assign(net->bond_site, net->bond_site + 2 * M);
-    f.bond_dim.assign(net->bond_dim, net->bond_dim + M);
-    f.site_ptr.assign(net->site_ptr, net->site_ptr + N + 1);
-    f.site_bonds.assign(net->site_bonds, net->site_bonds + net->site_ptr[N]);
-    // closed geometry: open bonds removed, remaining bonds renumbered in order
-    p->closed_of_full.assign(M, -1);
-    Geometry &c = p->closed;
-    c.n_sites = N;
-    int mc = 0;
-    for (int b = 0; b < M; ++b) {
-        if (f.bond_site[2 * b + 1] < 0) { p->open_bonds.push_back(b); p->open_dims.push_back(f.bond_dim[b]); continue; }
-        p->closed_of_full[b] = mc++;
-        c.bond_site.push_back(f.bond_site[2 * b]); c.bond_site.push_back(f.bond_site[2 * b + 1]);
-        c.bond_dim.push_back(f.bond_dim[b]);
-    }
-    c.n_bonds = mc;
-    c.site_ptr.assign(N + 1, 0);
-    for (int v = 0; v < N; ++v) {
-        for (int i = f.site_ptr[v]; i < f.site_ptr[v + 1]; ++i) {
-            const int cb = p->closed_of_full[f.site_bonds[i]];
-            if (cb >= 0) c.site_bonds.push_back(cb);
-        }
-        c.site_ptr[v + 1] = (int32_t)c.site_bonds.size();
-    }
+    if ((st = get_geometry(ctx, net, s, p->geo))) { delete p; return st; }
+    const Geometry &f = p->geo->full, &c = p->geo->closed;
     int64_t slices = 1;
-    for (int d : p->open_dims) slices *= d;
+    for (int d : p->geo->open_dims) slices *= d;
     if (slices > 4096) { delete p; set_error(ctx, PNE_EINVAL, "more than 4096 open-index assignments"); return PNE_EINVAL; }
     p->n_sets = net->n_batch;
     p->n_slices = (int)slices;
     p->n_members = p->n_sets * p->n_slices;
-    if ((st = finish_geometry(ctx, f, s)) || (st = finish_geometry(ctx, c, s))) { pne_partition_destroy(p); return st; }
     const int64_t fstride = f.tens_off[N], cstride = c.tens_off[N];
     const size_t B = p->n_sets, Bm = p->n_members;
     if ((st = dev_alloc(ctx, p->T, B * fstride * 8, s)) ||
@@ -453,17 +620,30 @@ pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_p
     }
     p->bp_iters.assign(B, 0);
     p->bp_residual.assign(B, 0.0);
-    int32_t flags[4] = {0, 0, 0, 0};
+    // convergence record: read back with the final synchronisation
+    char *rb = (char *)pinned_slot(0, B * 12 + 16);
+    std::vector<char> rb_fallback;
+    if (!rb) { rb_fallback.assign(B * 12 + 16, 0); rb = rb_fallback.data(); }
+    double *h_res = (double *)rb;
+    int32_t *flags = (int32_t *)(rb + B * 8);
+    int32_t *h_iters = flags + 4;
+    std::memset(rb, 0, B * 12 + 16);
     const int arith = opts ? opts->arithmetic : 0;
     if (arith != 0 && arith != 1) { pne_partition_destroy(p); set_error(ctx, PNE_EINVAL, "arithmetic must be 0 or 1"); return PNE_EINVAL; }
     p->arithmetic = arith;
-    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, p->bp_iters.data(), p->bp_residual.data(), flags, arith)) ||
+    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, h_iters, h_res, flags, arith)) ||
         (st = launch_gauge(ctx, p, s, nullptr))) {
         pne_partition_destroy(p);
         return st;
     }
-    cudaError_t e = cudaStreamSynchronize(s);
+    cudaError_t e;
+    {
+        HostScope hw__(ctx, "sync_partition");
+        e = cudaStreamSynchronize(s);
+    }
     if (e != cudaSuccess) { pne_partition_destroy(p); set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return PNE_ECUDA; }
+    std::memcpy(p->bp_iters.data(), h_iters, B * 4);
+    std::memcpy(p->bp_residual.data(), h_res, B * 8);
     if (flags[0] || flags[2]) { pne_partition_destroy(p); set_error(ctx, PNE_ETIMEOUT, "grid barrier timed out in BP"); return PNE_ETIMEOUT; }
     if (flags[1] || flags[3]) { pne_partition_destroy(p); set_error(ctx, PNE_EDEGENERATE, "zero message or zero message overlap"); return PNE_EDEGENERATE; }
     *out = p;
@@ -481,21 +661,23 @@ void pne_partition_destroy(pne_partition *p)
     pne_ctx *ctx = p->ctx;
     cudaStream_t s = p->last_stream;
     DevBuf *bufs[] = {&p->T, &p->msg, &p->gauge, &p->Mb, &p->site_info, &p->site_scale, &p->site_zero,
-                      &p->vac, &p->Mb32, &p->Mb16, &p->full.storage, &p->closed.storage};
+                      &p->vac, &p->Mb32, &p->Mb16};
     for (DevBuf *b : bufs) dev_free(ctx, *b, s);
+    if (p->geo) p->geo->free_stream = s;          // a geometry left without users is freed on this stream
     delete p;
 }
 
 pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pne_enum_opts *opts,
                                void *stream, pne_terms **out, uint64_t *n_clusters, uint64_t *n_terms)
 {
+    HostScope hs__(ctx, "enumerate");
     if (!ctx || !part || !opts || !out) return PNE_EINVAL;
     *out = nullptr;
     const int K = opts->max_order, mode = opts->mode;
     if (K < 0 || K > kMaxOrder) { set_error(ctx, PNE_EINVAL, "max_order must be in 0..32"); return PNE_EINVAL; }
     if (mode != PNE_MODE_LOOP && mode != PNE_MODE_ALL) { set_error(ctx, PNE_EINVAL, "unknown mode"); return PNE_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
-    const Geometry &g = part->closed;
+    const Geometry &g = part->geo->closed;
     std::string key = std::to_string(g.hash) + ":" + std::to_string(g.n_sites) + ":" + std::to_string(g.n_bonds) +
                       ":" + std::to_string(K) + ":" + std::to_string(mode);
     std::shared_ptr<EnumRecord> rec;
@@ -529,12 +711,19 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
                 rec->terms_by_order.assign(1, 1); rec->n_terms = 1;
                 rec->width = 1; rec->vwidth = 1;
             } else {
-                if ((st = enumerate_clusters(ctx, g, K, mode, *rec, s))) return st;
-                if ((st = enumerate_tuples(ctx, *rec, s))) return st;
-                if ((st = prepare_shapes(ctx, g, *rec, s))) return st;
+                // the shape hashes ride on the tuple stage's synchronisation
+                ShapePrep sp;
+                if ((st = enumerate_clusters(ctx, g, K, mode, *rec, s)) || (st = shapes_begin(ctx, g, *rec, sp, s)) ||
+                    (st = enumerate_tuples(ctx, *rec, s)) || (st = shapes_finish(ctx, g, *rec, sp, s))) {
+                    dev_free(ctx, sp.dh, s);
+                    return st;
+                }
             }
         }
         if (opts->use_cache) {
+            // a cached record may be used from other streams: finish it first
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) { set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return PNE_ECUDA; }
             std::lock_guard<std::mutex> lk(ctx->cache_mu);
             ctx->enum_cache[key] = rec;
         }
@@ -550,10 +739,13 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
             pne_terms_destroy(t); return st;
         }
     }
-    // the lists were written by kernels on `stream`; callers may use them from
-    // other streams (the server's launcher does), so finish them here
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { pne_terms_destroy(t); set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return PNE_ECUDA; }
+    // with the cache on, the handle's buffers are finished too (the server's
+    // launcher uses them from its own stream); otherwise the lists and buffers
+    // are ordered on `stream` like every other asynchronous call
+    if (opts->use_cache) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { pne_terms_destroy(t); set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return PNE_ECUDA; }
+    }
     *out = t;
     if (n_clusters) *n_clusters = rec->n_clusters;
     if (n_terms) *n_terms = rec->n_terms;
@@ -573,6 +765,7 @@ void pne_terms_destroy(pne_terms *t)
 
 pne_status pne_contract_terms(pne_ctx *ctx, pne_terms *t, pne_dtype dtype, void *stream)
 {
+    HostScope hs__(ctx, "contract");
     if (!ctx || !t) return PNE_EINVAL;
     if (dtype < PNE_F64 || dtype > PNE_BF16) { set_error(ctx, PNE_EINVAL, "unknown dtype"); return PNE_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
@@ -601,8 +794,8 @@ pne_status pne_terms_export(pne_ctx *ctx, const pne_terms *t, void *stream, int3
         PNE_CUDA_TRY(ctx, cudaMemcpyAsync(buf.data(), rec.cl_edges.ptr, buf.size() * 4, cudaMemcpyDeviceToHost, s));
         PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         std::vector<int32_t> full_of_closed;
-        for (size_t b = 0; b < t->part->closed_of_full.size(); ++b)
-            if (t->part->closed_of_full[b] >= 0) full_of_closed.push_back((int32_t)b);
+        for (size_t b = 0; b < t->part->geo->closed_of_full.size(); ++b)
+            if (t->part->geo->closed_of_full[b] >= 0) full_of_closed.push_back((int32_t)b);
         for (size_t i = 0; i < n; ++i)
             for (int j = 0; j < t->K; ++j) {
                 const int32_t e = (j < rec.width) ? buf[i * rec.width + j] : -1;
@@ -619,6 +812,7 @@ pne_status pne_terms_export(pne_ctx *ctx, const pne_terms *t, void *stream, int3
 
 pne_status pne_sum(pne_ctx *ctx, const pne_terms *t, void *stream, pne_result *out)
 {
+    HostScope hs__(ctx, "sum");
     if (!ctx || !t || !out) return PNE_EINVAL;
     if (!t->contracted) { set_error(ctx, PNE_EINVAL, "pne_contract_terms must run before pne_sum"); return PNE_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
@@ -626,12 +820,15 @@ pne_status pne_sum(pne_ctx *ctx, const pne_terms *t, void *stream, pne_result *o
     const int K = t->K, B = p->n_members;
     std::vector<double> c, a;
     int32_t status = 0;
+    // the vacuum record is read back with the sums (one synchronisation)
+    std::vector<double> vac((size_t)B * 3);
+    double *h_vac = (double *)pinned_slot(2, vac.size() * 8);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_vac ? (void *)h_vac : (void *)vac.data(), p->vac.ptr, vac.size() * 8,
+                                      cudaMemcpyDeviceToHost, s));
     pne_status st = launch_sums(ctx, t, s, c, a, &status);
     if (st) return st;
+    if (h_vac) std::memcpy(vac.data(), h_vac, vac.size() * 8);
     if (status) { set_error(ctx, PNE_EOVERFLOW, "a cluster exceeded the contraction buffer"); return PNE_EOVERFLOW; }
-    std::vector<double> vac((size_t)B * 3);
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(vac.data(), p->vac.ptr, vac.size() * 8, cudaMemcpyDeviceToHost, s));
-    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     for (int b = 0; b < B; ++b) {
         const int set = b / p->n_slices;
         finalize_result(out[b], K, t->mode, t->dtype, &c[(size_t)b * (K + 1)], &a[(size_t)b * (K + 1)], &vac[3 * (size_t)b],
@@ -650,15 +847,26 @@ pne_status pne_partition_update(pne_ctx *ctx, pne_partition *p, const double *da
     const int max_iter = (opts && opts->max_iter > 0) ? opts->max_iter : 10000;
     const double damping = opts ? opts->damping : 0.0;
     if (!(damping >= 0.0 && damping < 1.0)) { set_error(ctx, PNE_EINVAL, "damping must be in [0,1)"); return PNE_EINVAL; }
-    const size_t bytes = (size_t)p->n_sets * p->full.tens_off[p->full.n_sites] * 8;
+    const size_t bytes = (size_t)p->n_sets * p->geo->full.tens_off[p->geo->full.n_sites] * 8;
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(p->T.ptr, data, bytes, data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    int32_t flags[4] = {0, 0, 0, 0};
+    const size_t B = p->n_sets;
+    char *rb = (char *)pinned_slot(0, B * 12 + 16);
+    std::vector<char> rb_fallback;
+    if (!rb) { rb_fallback.assign(B * 12 + 16, 0); rb = rb_fallback.data(); }
+    double *h_res = (double *)rb;
+    int32_t *flags = (int32_t *)(rb + B * 8);
+    int32_t *h_iters = flags + 4;
+    std::memset(rb, 0, B * 12 + 16);
     pne_status st;
     const int arith = opts ? opts->arithmetic : p->arithmetic;
-    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, p->bp_iters.data(), p->bp_residual.data(), flags, arith)) ||
+    if (arith != 0 && arith != 1) { set_error(ctx, PNE_EINVAL, "arithmetic must be 0 or 1"); return PNE_EINVAL; }
+    p->arithmetic = arith;
+    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, h_iters, h_res, flags, arith)) ||
         (st = launch_gauge(ctx, p, s, nullptr)))
         return st;
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    std::memcpy(p->bp_iters.data(), h_iters, B * 4);
+    std::memcpy(p->bp_residual.data(), h_res, B * 8);
     p->mb32_dtype = -1;
     if (flags[0] || flags[2]) { set_error(ctx, PNE_ETIMEOUT, "grid barrier timed out in BP"); return PNE_ETIMEOUT; }
     if (flags[1] || flags[3]) { set_error(ctx, PNE_EDEGENERATE, "zero message or zero message overlap"); return PNE_EDEGENERATE; }

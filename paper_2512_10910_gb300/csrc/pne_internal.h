@@ -63,6 +63,18 @@ struct DevBuf {
 pne_status dev_alloc(pne_ctx *ctx, DevBuf &b, size_t bytes, cudaStream_t s);
 // small pinned host buffer for device-to-host reads of counts (per thread)
 int64_t *pinned_i64(pne_ctx *ctx, size_t n);
+// Host->device upload through a per-thread pinned staging region: the host data
+// is copied into pinned memory and the DMA is queued on `s`, so the caller may
+// release its buffer at once and no stream synchronisation is implied (a
+// pageable source would synchronise the stream).  The region is recycled only
+// after every copy queued out of it has completed.  Not for use inside stream
+// capture (a captured copy would read the region when replayed).
+pne_status upload(pne_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s);
+// Per-thread pinned readback area `slot` of at least `bytes` (nullptr if pinned
+// memory is unavailable); read after synchronising the stream of the copies.
+// Slots: 0 partition records, 1 sums, 2 vacuum records, 3 shape records.
+constexpr int kPinnedSlots = 4;
+void *pinned_slot(int slot, size_t bytes);
 void dev_free(pne_ctx *ctx, DevBuf &b, cudaStream_t s);
 
 // ------------------------------------------------------------------ geometry
@@ -89,6 +101,7 @@ struct Geometry {
 
 // ------------------------------------------------------------------ handles
 struct EnumRecord;  // cluster and term lists of one closed geometry
+struct GeomPair;    // full + closed geometry of one network (shared, cached)
 
 }  // namespace pne
 
@@ -116,18 +129,33 @@ struct pne_ctx {
     void *alloc_user = nullptr;
     std::map<std::string, std::shared_ptr<pne::EnumRecord>> enum_cache;
     std::map<std::string, int64_t> arena_hint;   // search-arena size that fitted, per (geometry, K, mode)
+    std::map<uint64_t, std::vector<std::shared_ptr<pne::GeomPair>>> geom_cache;   // by input-array hash
     std::mutex cache_mu;
     // scratch for small device-side status words
     int32_t *d_status = nullptr;
 };
 
+namespace pne {
+// The geometry of one network as given (full) and with its open bonds removed
+// (closed), host tables plus device copies; shared by every partition of the
+// same geometry through the context's cache.
+struct GeomPair {
+    pne_ctx *ctx = nullptr;
+    Geometry full;                       // as given (may have open bonds)
+    Geometry closed;                     // open bonds removed, bonds renumbered
+    std::vector<int32_t> closed_of_full; // full bond id -> closed id (-1 open)
+    std::vector<int32_t> open_bonds;     // full ids of open bonds, ascending
+    std::vector<int32_t> open_dims;
+    uint64_t key = 0;                    // hash of the input arrays
+    cudaStream_t free_stream = nullptr;  // stream of the last partition that used it
+    cudaEvent_t ready = nullptr;         // recorded after the device copies were queued
+    ~GeomPair();
+};
+}  // namespace pne
+
 struct pne_partition {
     pne_ctx *ctx = nullptr;
-    pne::Geometry full;              // as given (may have open bonds)
-    pne::Geometry closed;            // open bonds removed, bonds renumbered
-    std::vector<int32_t> closed_of_full;  // full bond id -> closed id (-1 open)
-    std::vector<int32_t> open_bonds;      // full ids of open bonds, ascending
-    std::vector<int32_t> open_dims;
+    std::shared_ptr<pne::GeomPair> geo;
     int n_sets = 1;                  // tensor sets (n_batch)
     int n_slices = 1;                // prod of open dims
     int n_members = 1;               // n_sets * n_slices
@@ -177,8 +205,17 @@ struct EnumRecord {
     DevBuf perm;                                // [n] int32 clusters ordered by shape
     DevBuf plans;                               // [n_shapes][plan ints]
     DevBuf plan_steps;                          // [n_shapes] int32
+    DevBuf ops;                                 // per shape: its plan's multiply-adds in order, (xi << 16) | mi
+    DevBuf op_off;                              // [n_shapes + 1] int64 offsets into ops
+    DevBuf step_off, step_site;                 // [n][step_stride] int32: block offset within a tensor
+    int step_stride = 0;                        //   set and the site of every plan step of every cluster
     std::vector<uint64_t> shape_fma;            // [n_shapes] multiply-adds of the plan
     std::vector<int64_t> shape_count;           // [n_shapes] clusters per shape
+    // perm lists the clusters by running-tensor class (largest intermediate
+    // tensor of the plan, rounded up to a power of two), then by shape:
+    // class q holds perm[class_start[q], class_start[q+1]) and needs class_xmax[q]
+    std::vector<int64_t> class_start;
+    std::vector<int> class_xmax;
     ~EnumRecord();
 };
 
@@ -210,6 +247,17 @@ struct ProfScope {
     ~ProfScope();
 };
 
+// Host wall time of a stretch of library code, accumulated under "host:<name>"
+// while profiling is on (the host side of a call: launches, allocations,
+// synchronisations and host loops).
+struct HostScope {
+    pne_ctx *ctx;
+    const char *name;
+    double t0 = -1.0;
+    HostScope(pne_ctx *c, const char *n);
+    ~HostScope();
+};
+
 // ------------------------------------------------------------------ kernels
 // BP, gauge, blocked layout (bp.cu)
 pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, double damping,
@@ -228,7 +276,14 @@ pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s,
                        std::vector<double> &c, std::vector<double> &abs_c, int32_t *h_status);
 pne_status launch_all_mode(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s);
 pne_status launch_plan_work(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, uint64_t *fma);
-pne_status prepare_shapes(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, cudaStream_t s);
+// contraction plans per cluster shape, in two halves around a synchronisation
+struct ShapePrep {
+    DevBuf dh;                    // per-cluster hashes on the device
+    void *h_pinned = nullptr;     // their readback
+    bool active = false;
+};
+pne_status shapes_begin(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s);
+pne_status shapes_finish(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s);
 pne_status launch_convert_only(pne_ctx *ctx, const pne_partition *p, int dtype, cudaStream_t s);
 
 // batched form (contract.cu)
