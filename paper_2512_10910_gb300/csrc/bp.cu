@@ -386,6 +386,47 @@ __device__ __forceinline__ bool ff_abs_gt(ff x, ff y)
     return x.h > y.h || (x.h == y.h && x.l > y.l);
 }
 
+// x * 2^-ex as a float-float pair (hi = x rounded to nearest-even in FP32, lo =
+// the remainder rounded), from the bits of x with integer operations only: no
+// FP64 instruction.  Requires |x| * 2^-ex <= 1 (ex at least the slice's
+// largest exponent).  Parts below FP32's normal range are flushed to zero:
+// entries 2^-126 below the slice maximum (hi) or 2^-74 below it (lo) carry
+// nothing the pair precision could keep anyway.
+__device__ __forceinline__ ff split_scaled(double x, int ex)
+{
+    const long long b = __double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    const int e2 = E - 1023 - ex;                       // exponent of the scaled value
+    if (E == 0 || e2 < -126) return {0.f, 0.f};
+    const unsigned long long m = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    unsigned long long q = m >> 29;                     // top 24 bits
+    const unsigned long long r = m & ((1ull << 29) - 1);
+    if (r > (1ull << 28) || (r == (1ull << 28) && (q & 1))) ++q;
+    const int rem = (int)((long long)m - (long long)(q << 29));   // |rem| <= 2^28
+    int eh = e2;
+    if (q == (1ull << 24)) { q >>= 1; ++eh; }
+    const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
+    const float hi = __int_as_float((int)(sign | ((unsigned)(eh + 127) << 23) | (unsigned)(q & 0x7FFFFF)));
+    float lo = 0.f;
+    if (rem != 0 && e2 - 52 >= -126) {
+        lo = __fmul_rn(__int2float_rn(rem), __int_as_float((e2 - 52 + 127) << 23));
+        if (sign) lo = -lo;
+    }
+    return {hi, lo};
+}
+
+// a normal FP32 value widened to FP64 from its bits (zero stays zero)
+__device__ __forceinline__ double widen(float f)
+{
+    const unsigned u = (unsigned)__float_as_int(f);
+    const unsigned e = (u >> 23) & 0xFF;
+    if (e == 0) return 0.0;
+    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                    ((unsigned long long)(e + 1023 - 127) << 52) |
+                                    ((unsigned long long)(u & 0x7FFFFF) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
 struct BPFFParams {
     int n_sets, n_sites, n_legs;
     const int32_t *site_ptr, *site_bonds, *bond_dim, *inc_slot;
@@ -893,12 +934,7 @@ __global__ void block_ff_kernel(BlockParams p)
             mxb = max(mxb, (int)((__double_as_longlong(T[src_of(e)]) >> 52) & 0x7FF));
         for (int off = 16; off > 0; off >>= 1) mxb = max(mxb, __shfl_xor_sync(0xffffffffu, mxb, off));
         const int ex = mxb > 0 ? min(mxb - 1022, 1022) : 0;        // slice values are below 2^ex
-        const double down = __longlong_as_double((long long)(1023 - ex) << 52);   // 2^-ex
-        for (int e = lane; e < n; e += 32) {
-            const double x = T[src_of(e)] * down;
-            const float hi = __double2float_rn(x);
-            bufA[e] = {hi, __double2float_rn(x - (double)hi)};
-        }
+        for (int e = lane; e < n; e += 32) bufA[e] = split_scaled(T[src_of(e)], ex);
         __syncwarp();
         ff *cur = bufA, *nxt = bufB;
         int post = n;
@@ -907,9 +943,7 @@ __global__ void block_ff_kernel(BlockParams p)
             post /= d;
             const double *G = p.gauge + (((int64_t)set * p.n_bonds_full + bonds[i]) * 2 + side[i]) * 64;
             for (int q = lane; q < d * 8; q += 32) {
-                const double g = G[q];
-                const float gh = __double2float_rn(g);
-                Gs[q] = {gh, __double2float_rn(g - (double)gh)};
+                Gs[q] = split_scaled(G[q], 0);
             }
             __syncwarp();
             const float inv_post = 1.0f / (float)post;
@@ -945,7 +979,7 @@ __global__ void block_ff_kernel(BlockParams p)
                 if (dgt > 0) { mask |= 1 << i; pos += (dgt - 1) * bm; bm *= cdims[i] - 1; }
             }
             const ff m = ff_mul(cur[e], f);
-            M[boff[mask] + pos] = (double)m.h + (double)m.l;
+            M[boff[mask] + pos] = widen(m.h) + widen(m.l);
         }
         if (lane == 0) {
             const double up = __longlong_as_double((long long)(1023 + ex) << 52);   // 2^ex

@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <unordered_map>
 
 #include "pne_internal.h"
@@ -756,35 +757,68 @@ __global__ void __launch_bounds__(256) contract_shaped_kernel(ContractParams P, 
     }
 }
 
+// Side streams of the context, created on first use (caller holds side_mu).
+pne_status side_streams(pne_ctx *ctx)
+{
+    if (ctx->side_ready) return PNE_OK;
+    for (auto &st : ctx->side) PNE_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (auto &ev : ctx->side_ev) PNE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    ctx->side_ready = true;
+    return PNE_OK;
+}
+
 template <typename T, typename L, int R>
 pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &rec, cudaStream_t s)
 {
     auto kern = contract_shaped_kernel<T, L, R>;
     // one launch per running-tensor class, each with buffers (and so an
-    // occupancy) sized for its own class
+    // occupancy) sized for its own class; the classes are independent, so
+    // when there are several they run concurrently on side streams forked
+    // from and joined back into `s`
     const size_t smem_cap = 200 * 1024;
-    bool attr_set = false;
-    for (size_t q = 0; q + 1 < rec.class_start.size(); ++q) {
+    std::vector<size_t> cls;
+    for (size_t q = 0; q + 1 < rec.class_start.size(); ++q)
+        if (rec.class_start[q + 1] > rec.class_start[q]) cls.push_back(q);
+    std::unique_lock<std::mutex> lk(ctx->side_mu, std::defer_lock);
+    const bool fork = cls.size() > 1;
+    if (fork) {
+        lk.lock();
+        pne_status st = side_streams(ctx);
+        if (st) return st;
+        PNE_CUDA_TRY(ctx, cudaEventRecord(ctx->side_ev[0], s));
+    }
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
+    // the largest running tensors (fewest, longest clusters) start first, on `s`
+    std::reverse(cls.begin(), cls.end());
+    for (size_t j = 0; j < cls.size(); ++j) {
+        const size_t q = cls[j];
         const int64_t i0 = rec.class_start[q], i1 = rec.class_start[q + 1];
-        if (i1 <= i0) continue;
         const int xmax = std::min(rec.class_xmax[q], std::max(rec.max_out, 1));
         const int per_warp = 2 * xmax * 32 * (int)sizeof(T);
         int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (smem_cap / 4) / per_warp));   // about four blocks per SM
         const size_t smem = (size_t)wpb * per_warp;
-        if (smem > 48 * 1024 && !attr_set) {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
-            attr_set = true;
-        }
         const int64_t items = ((i1 - i0 + 31) / 32) * cp.n_members;
         int64_t g = (items + wpb - 1) / wpb;
         const int64_t cap = (int64_t)ctx->n_sm * 32;
         if (g > cap) g = cap;
-        kern<<<(int)g, wpb * 32, smem, s>>>(cp, (const int32_t *)rec.perm.ptr, (const int32_t *)rec.shape_of.ptr,
-                                            (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr,
-                                            (const int32_t *)rec.ops.ptr, (const int64_t *)rec.op_off.ptr,
-                                            (const int32_t *)rec.step_off.ptr, (const int32_t *)rec.step_site.ptr,
-                                            rec.step_stride, xmax, i0, i1);
+        cudaStream_t ls = s;
+        if (fork && j > 0) {
+            ls = ctx->side[(j - 1) % pne_ctx::kSideStreams];
+            PNE_CUDA_TRY(ctx, cudaStreamWaitEvent(ls, ctx->side_ev[0], 0));
+        }
+        kern<<<(int)g, wpb * 32, smem, ls>>>(cp, (const int32_t *)rec.perm.ptr, (const int32_t *)rec.shape_of.ptr,
+                                             (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr,
+                                             (const int32_t *)rec.ops.ptr, (const int64_t *)rec.op_off.ptr,
+                                             (const int32_t *)rec.step_off.ptr, (const int32_t *)rec.step_site.ptr,
+                                             rec.step_stride, xmax, i0, i1);
         PNE_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    if (fork) {
+        const size_t used = std::min<size_t>(cls.size() - 1, pne_ctx::kSideStreams);
+        for (size_t k = 0; k < used; ++k) {
+            PNE_CUDA_TRY(ctx, cudaEventRecord(ctx->side_ev[1 + k], ctx->side[k]));
+            PNE_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->side_ev[1 + k], 0));
+        }
     }
     return PNE_OK;
 }

@@ -945,9 +945,15 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     const int final_kind = (K <= 1) ? 0 : (D == K - 1 ? 1 : 2);
     const bool small = (K <= 12 && umax_need <= 64);
     // chunks of the blocked passes: one wave of resident blocks
-    int per_sm = 0, per_sm_c = 0;
-    PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel, 32 * kExpandWarps, 0));
-    PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, bfs_levels_kernel, 32 * kExpandWarps, 0));
+    // resident blocks per SM of the two search kernels (queried once per context)
+    if (ctx->occ_expand < 0) {
+        int a = 0, b = 0;
+        PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, expand_kernel, 32 * kExpandWarps, 0));
+        PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bfs_levels_kernel, 32 * kExpandWarps, 0));
+        ctx->occ_bfs = b;
+        ctx->occ_expand = a;
+    }
+    const int per_sm = ctx->occ_expand, per_sm_c = ctx->occ_bfs;
     const int G = ctx->n_sm * std::max(1, per_sm);
     const int Gc = ctx->n_sm * std::max(1, per_sm_c);   // co-resident blocks of the cooperative launch
     const int Gd = grid1(1 << 20, 128, ctx->n_sm);    // grid of the depth-first kernel

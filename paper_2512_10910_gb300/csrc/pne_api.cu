@@ -556,6 +556,10 @@ void pne_ctx_destroy(pne_ctx *ctx)
         ctx->geom_cache.clear();
     }
     cudaDeviceSynchronize();
+    if (ctx->side_ready) {
+        for (auto st : ctx->side) cudaStreamDestroy(st);
+        for (auto ev : ctx->side_ev) cudaEventDestroy(ev);
+    }
     delete ctx;
 }
 
@@ -713,10 +717,22 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
             } else {
                 // the shape hashes ride on the tuple stage's synchronisation
                 ShapePrep sp;
-                if ((st = enumerate_clusters(ctx, g, K, mode, *rec, s)) || (st = shapes_begin(ctx, g, *rec, sp, s)) ||
-                    (st = enumerate_tuples(ctx, *rec, s)) || (st = shapes_finish(ctx, g, *rec, sp, s))) {
-                    dev_free(ctx, sp.dh, s);
-                    return st;
+                auto fail = [&](pne_status e) { dev_free(ctx, sp.dh, s); return e; };
+                {
+                    HostScope h1(ctx, "enum_clusters");
+                    if ((st = enumerate_clusters(ctx, g, K, mode, *rec, s))) return fail(st);
+                }
+                {
+                    HostScope h2(ctx, "enum_shapes_begin");
+                    if ((st = shapes_begin(ctx, g, *rec, sp, s))) return fail(st);
+                }
+                {
+                    HostScope h3(ctx, "enum_tuples");
+                    if ((st = enumerate_tuples(ctx, *rec, s))) return fail(st);
+                }
+                {
+                    HostScope h4(ctx, "enum_shapes_finish");
+                    if ((st = shapes_finish(ctx, g, *rec, sp, s))) return fail(st);
                 }
             }
         }

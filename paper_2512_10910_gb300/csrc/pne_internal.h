@@ -124,6 +124,7 @@ struct pne_ctx {
     int device = 0;
     int n_sm = 0;
     int64_t arena_max = 0;        // node-arena limit of the cluster search (0: the built-in limit)
+    int occ_expand = -1, occ_bfs = -1;   // resident blocks per SM of the search kernels (-1: not queried)
     pne_alloc_fn alloc = nullptr;
     pne_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
@@ -133,6 +134,13 @@ struct pne_ctx {
     std::mutex cache_mu;
     // scratch for small device-side status words
     int32_t *d_status = nullptr;
+    // side streams for independent launches of one call (fork/join through
+    // events, serialised per context by side_mu)
+    static constexpr int kSideStreams = 6;
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t side_ev[kSideStreams + 1] = {};
+    bool side_ready = false;
+    std::mutex side_mu;
 };
 
 namespace pne {
