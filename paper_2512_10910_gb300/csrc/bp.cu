@@ -21,6 +21,7 @@
 //   exactly one block per site.  Each site is divided by z_v (its all-zero
 //   entry) when z_v != 0, else by a power of two.
 #include <cuda_runtime.h>
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -529,7 +530,204 @@ __device__ void site_messages_ff(const ff *__restrict__ T, int k, const int *dim
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kBpWarps * 32) bp_ff_kernel(BPFFParams p)
+// ---- the same site update with the leg count K and a uniform bond dimension D
+// known at compile time (the lattice sites: every index decode is a constant
+// division, every loop bound a constant).  Same halves, same outputs.
+__host__ __device__ constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
+__host__ __device__ constexpr int lanes_for(int rows) { return rows >= 32 ? 1 : (rows > 16 ? 1 : (rows > 8 ? 2 : (rows > 4 ? 4 : (rows > 2 ? 8 : (rows > 1 ? 16 : 32))))); }
+
+// out for leg jj of a half with NL legs: sum over the other digits of X times
+// the messages on the other legs of the half (inh: the half's first message row)
+template <int NL, int D>
+__device__ __forceinline__ ff half_output(const ff *X, const ff *inh, int jj, int x)
+{
+    constexpr int REST = cpow(D, NL - 1);
+    ffacc acc;
+#pragma unroll 4
+    for (int r = 0; r < REST; ++r) {
+        // digits of the legs other than jj, last leg fastest; leg jj takes x
+        int rr = r, a = 0, mul = 1;
+        ff p = {1.f, 0.f};
+        bool first = true;
+#pragma unroll
+        for (int i = NL - 1; i >= 0; --i) {
+            int dgt;
+            if (i == jj) {
+                dgt = x;
+            } else {
+                dgt = rr % D;
+                rr /= D;
+                const ff m = inh[i * kMsgStride + dgt];
+                p = first ? m : ff_mul(p, m);
+                first = false;
+            }
+            a += dgt * mul;
+            mul *= D;
+        }
+        acc.add(first ? X[a] : ff_mul(X[a], p));
+    }
+    return acc.get();
+}
+
+template <int K, int D>
+__device__ void site_messages_ff_u(const ff *__restrict__ T, const ff *in, ff *u, ff *w, ff *x1, ff *x2, ff *out,
+                                   int lane)
+{
+    constexpr int H = K / 2, A = cpow(D, H), C = cpow(D, K - H);
+    for (int c = lane; c < C; c += 32) {
+        int r = c;
+        ff q = {1.f, 0.f};
+#pragma unroll
+        for (int i = K - 1; i >= H; --i) { q = ff_mul(q, in[i * kMsgStride + r % D]); r /= D; }
+        w[c] = q;
+    }
+    for (int a = lane; a < A; a += 32) {
+        int r = a;
+        ff q = {1.f, 0.f};
+#pragma unroll
+        for (int i = H - 1; i >= 0; --i) { q = ff_mul(q, in[i * kMsgStride + r % D]); r /= D; }
+        u[a] = q;
+    }
+    __syncwarp();
+    {   // x1 = T w: LPR lanes per row
+        constexpr int LPR = lanes_for(A), RPP = 32 / LPR;
+        const int sub = lane % LPR;
+#pragma unroll 1
+        for (int a0 = 0; a0 < A; a0 += RPP) {
+            const int a = a0 + lane / LPR;
+            ffacc acc;
+            if (a < A) {
+                const ff *row = T + (int64_t)a * C;
+#pragma unroll 4
+                for (int c = sub; c < C; c += LPR) acc.add(ff_mul(row[c], w[c]));
+            }
+            ff sm = acc.get();
+#pragma unroll
+            for (int off = LPR / 2; off > 0; off >>= 1) sm = ff_add(sm, ff_shfl_xor(sm, off));
+            if (a < A && sub == 0) x1[a] = sm;
+        }
+    }
+    {   // x2 = u^T T: LPC lanes per column
+        constexpr int LPC = lanes_for(C), CPP = 32 / LPC;
+        const int sub = lane / CPP;
+#pragma unroll 1
+        for (int c0 = 0; c0 < C; c0 += CPP) {
+            const int c = c0 + lane % CPP;
+            ffacc acc;
+            if (c < C) {
+#pragma unroll 4
+                for (int a = sub; a < A; a += LPC) acc.add(ff_mul(u[a], T[(int64_t)a * C + c]));
+            }
+            ff sm = acc.get();
+#pragma unroll
+            for (int off = 16; off >= CPP; off >>= 1) sm = ff_add(sm, ff_shfl_xor(sm, off));
+            if (c < C && sub == 0) x2[c] = sm;
+        }
+    }
+    __syncwarp();
+    for (int it = lane; it < K * D; it += 32) {
+        const int j = it / D, x = it % D;
+        out[j * kMsgStride + x] = (j < H) ? half_output<H, D>(x1, in, j, x)
+                                          : half_output<K - H, D>(x2, in + H * kMsgStride, j - H, x);
+    }
+    __syncwarp();
+}
+
+// the specialised update when the site's legs share one dimension of a
+// compiled (K, D) pair; false otherwise (the caller takes the general routine)
+__device__ __forceinline__ bool site_messages_ff_fast(const ff *T, int k, const int *dims, const ff *in, ff *u, ff *w,
+                                                      ff *x1, ff *x2, ff *out, int lane)
+{
+    const int D = dims[0];
+    for (int i = 1; i < k; ++i)
+        if (dims[i] != D) return false;
+    switch (k * 16 + D) {
+#define PNE_SITE_CASE(KK, DD) case KK * 16 + DD: site_messages_ff_u<KK, DD>(T, in, u, w, x1, x2, out, lane); return true;
+        PNE_SITE_CASE(2, 2) PNE_SITE_CASE(2, 3) PNE_SITE_CASE(2, 4) PNE_SITE_CASE(2, 5) PNE_SITE_CASE(2, 6)
+        PNE_SITE_CASE(3, 2) PNE_SITE_CASE(3, 3) PNE_SITE_CASE(3, 4) PNE_SITE_CASE(3, 5) PNE_SITE_CASE(3, 6)
+        PNE_SITE_CASE(4, 2) PNE_SITE_CASE(4, 3) PNE_SITE_CASE(4, 4) PNE_SITE_CASE(4, 5) PNE_SITE_CASE(4, 6)
+        PNE_SITE_CASE(5, 2) PNE_SITE_CASE(5, 3) PNE_SITE_CASE(5, 4)
+        PNE_SITE_CASE(6, 2) PNE_SITE_CASE(6, 3) PNE_SITE_CASE(6, 4)
+#undef PNE_SITE_CASE
+        default: return false;
+    }
+}
+
+__device__ __forceinline__ ff ldcg_ff(const ff *q)
+{
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(q));
+    return {v.x, v.y};
+}
+
+// One site's outgoing messages, normalised and written to mdst; returns the
+// largest entry change (the same in every lane).  Messages are read through L2
+// (__ldcg): other blocks wrote them earlier in the same launch.
+__device__ float ff_site_update(const BPFFParams &p, int set, int v, const ff *msrc, ff *mdst, ff *in, ff *out,
+                                ff *u, ff *w, ff *x1, ff *x2, int lane)
+{
+    const int l0 = p.site_ptr[v], k = p.site_ptr[v + 1] - l0;
+    int dims[kMaxDeg];
+    for (int i = 0; i < kMaxDeg; ++i) dims[i] = (i < k) ? p.bond_dim[p.site_bonds[l0 + i]] : 1;
+    for (int e = lane; e < k * kMsgStride; e += 32)
+        in[e] = ldcg_ff(&msrc[(int64_t)p.inc_slot[l0 + e / kMsgStride] * kMsgStride + e % kMsgStride]);
+    __syncwarp();
+    {
+        const ff *Tv = p.T + set * p.set_stride + p.tens_off[v];
+        if (!site_messages_ff_fast(Tv, k, dims, in, u, w, x1, x2, out, lane))
+            site_messages_ff(Tv, k, dims, in, u, w, x1, x2, out, lane);
+    }
+    float r = 0.f;
+    for (int j0 = 0; j0 < k; j0 += 4) {
+        const int j = j0 + (lane >> 3), a = lane & 7;
+        const bool live = (j < k) && (a < dims[j < k ? j : 0]);
+        const ff o = live ? out[j * kMsgStride + a] : ff{0.f, 0.f};
+        const ff old = live ? ldcg_ff(&msrc[(int64_t)(l0 + j) * kMsgStride + a]) : ff{0.f, 0.f};
+        ff n2 = ff_mul(o, o);
+        for (int off = 4; off > 0; off >>= 1) n2 = ff_add(n2, ff_shfl_xor(n2, off));
+        ff big = live ? o : ff{-1.f, 0.f};
+        bool has = live;
+        int arg = a;
+        for (int off = 4; off > 0; off >>= 1) {
+            const ff ob = ff_shfl_xor(big, off);
+            const int oa = __shfl_xor_sync(0xffffffffu, arg, off);
+            const bool oh = __shfl_xor_sync(0xffffffffu, has, off);
+            const bool take = oh && (!has || ff_abs_gt(ob, big) || (!ff_abs_gt(big, ob) && oa < arg));
+            if (take) { big = ob; arg = oa; has = true; }
+        }
+        const float oarg = __shfl_sync(0xffffffffu, o.h, (lane & ~7) | arg);
+        ff nrm = ff_sqrt(n2);
+        if (j < k && !(nrm.h > 0.f)) { atomicExch(p.flags + 1, 1); nrm = {1.f, 0.f}; }
+        ff nv = ff_div(oarg < 0.f ? ff{-o.h, -o.l} : o, nrm);
+        if (p.damping > 0.0) {
+            const float dm = (float)p.damping;
+            ff m = ff_add(ff_mul(nv, {1.f - dm, 0.f}), ff_mul(old, {dm, 0.f}));
+            ff m2 = live ? ff_mul(m, m) : ff{0.f, 0.f};
+            for (int off = 4; off > 0; off >>= 1) m2 = ff_add(m2, ff_shfl_xor(m2, off));
+            ff bg = live ? m : ff{-1.f, 0.f};
+            bool hs = live;
+            int ag = a;
+            for (int off = 4; off > 0; off >>= 1) {
+                const ff ob = ff_shfl_xor(bg, off);
+                const int oa = __shfl_xor_sync(0xffffffffu, ag, off);
+                const bool oh = __shfl_xor_sync(0xffffffffu, hs, off);
+                const bool take = oh && (!hs || ff_abs_gt(ob, bg) || (!ff_abs_gt(bg, ob) && oa < ag));
+                if (take) { bg = ob; ag = oa; hs = true; }
+            }
+            const float marg = __shfl_sync(0xffffffffu, m.h, (lane & ~7) | ag);
+            ff n3 = ff_sqrt(m2);
+            if (j < k && !(n3.h > 0.f)) { atomicExch(p.flags + 1, 1); n3 = {1.f, 0.f}; }
+            nv = ff_div(marg < 0.f ? ff{-m.h, -m.l} : m, n3);
+        }
+        if (live) {
+            mdst[(int64_t)(l0 + j) * kMsgStride + a] = nv;
+            r = fmaxf(r, fabsf(__fadd_rn(__fsub_rn(nv.h, old.h), __fsub_rn(nv.l, old.l))));
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
+    return r;
+}
+
+__global__ void __launch_bounds__(kBpWarps * 32, 4) bp_ff_kernel(BPFFParams p)
 {
     extern __shared__ ff ffsmem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -560,65 +758,11 @@ __global__ void __launch_bounds__(kBpWarps * 32) bp_ff_kernel(BPFFParams p)
         for (int64_t item = gwarp; item < items; item += nwarps) {
             const int set = (int)(item / nc), q = (int)(item % nc);
             const int v = colored ? p.color_sites[c0 + q] : q;
-            if (p.done_it[set] != 0) continue;
-            if (it > 1 && __uint_as_float(res_prev[set]) < p.tol) continue;
-            const int l0 = p.site_ptr[v], k = p.site_ptr[v + 1] - l0;
-            int dims[kMaxDeg];
-            for (int i = 0; i < kMaxDeg; ++i) dims[i] = (i < k) ? p.bond_dim[p.site_bonds[l0 + i]] : 1;
+            if (__ldcg(p.done_it + set) != 0) continue;
+            if (it > 1 && __uint_as_float(__ldcg(res_prev + set)) < p.tol) continue;
             const ff *msrc = p.msg + src * msg_buf + set * msg_set;
             ff *mdst = p.msg + dst * msg_buf + set * msg_set;
-            for (int e = lane; e < k * kMsgStride; e += 32)
-                in[e] = msrc[(int64_t)p.inc_slot[l0 + e / kMsgStride] * kMsgStride + e % kMsgStride];
-            __syncwarp();
-            site_messages_ff(p.T + set * p.set_stride + p.tens_off[v], k, dims, in, u, w, x1, x2, out, lane);
-            float r = 0.f;
-            for (int j0 = 0; j0 < k; j0 += 4) {
-                const int j = j0 + (lane >> 3), a = lane & 7;
-                const bool live = (j < k) && (a < dims[j < k ? j : 0]);
-                const ff o = live ? out[j * kMsgStride + a] : ff{0.f, 0.f};
-                const ff old = live ? msrc[(int64_t)(l0 + j) * kMsgStride + a] : ff{0.f, 0.f};
-                ff n2 = ff_mul(o, o);
-                for (int off = 4; off > 0; off >>= 1) n2 = ff_add(n2, ff_shfl_xor(n2, off));
-                ff big = live ? o : ff{-1.f, 0.f};
-                bool has = live;
-                int arg = a;
-                for (int off = 4; off > 0; off >>= 1) {
-                    const ff ob = ff_shfl_xor(big, off);
-                    const int oa = __shfl_xor_sync(0xffffffffu, arg, off);
-                    const bool oh = __shfl_xor_sync(0xffffffffu, has, off);
-                    const bool take = oh && (!has || ff_abs_gt(ob, big) || (!ff_abs_gt(big, ob) && oa < arg));
-                    if (take) { big = ob; arg = oa; has = true; }
-                }
-                const float oarg = __shfl_sync(0xffffffffu, o.h, (lane & ~7) | arg);
-                ff nrm = ff_sqrt(n2);
-                if (j < k && !(nrm.h > 0.f)) { atomicExch(p.flags + 1, 1); nrm = {1.f, 0.f}; }
-                ff nv = ff_div(oarg < 0.f ? ff{-o.h, -o.l} : o, nrm);
-                if (p.damping > 0.0) {
-                    const float dm = (float)p.damping;
-                    ff m = ff_add(ff_mul(nv, {1.f - dm, 0.f}), ff_mul(old, {dm, 0.f}));
-                    ff m2 = live ? ff_mul(m, m) : ff{0.f, 0.f};
-                    for (int off = 4; off > 0; off >>= 1) m2 = ff_add(m2, ff_shfl_xor(m2, off));
-                    ff bg = live ? m : ff{-1.f, 0.f};
-                    bool hs = live;
-                    int ag = a;
-                    for (int off = 4; off > 0; off >>= 1) {
-                        const ff ob = ff_shfl_xor(bg, off);
-                        const int oa = __shfl_xor_sync(0xffffffffu, ag, off);
-                        const bool oh = __shfl_xor_sync(0xffffffffu, hs, off);
-                        const bool take = oh && (!hs || ff_abs_gt(ob, bg) || (!ff_abs_gt(bg, ob) && oa < ag));
-                        if (take) { bg = ob; ag = oa; hs = true; }
-                    }
-                    const float marg = __shfl_sync(0xffffffffu, m.h, (lane & ~7) | ag);
-                    ff n3 = ff_sqrt(m2);
-                    if (j < k && !(n3.h > 0.f)) { atomicExch(p.flags + 1, 1); n3 = {1.f, 0.f}; }
-                    nv = ff_div(marg < 0.f ? ff{-m.h, -m.l} : m, n3);
-                }
-                if (live) {
-                    mdst[(int64_t)(l0 + j) * kMsgStride + a] = nv;
-                    r = fmaxf(r, fabsf(__fadd_rn(__fsub_rn(nv.h, old.h), __fsub_rn(nv.l, old.l))));
-                }
-            }
-            for (int off = 16; off > 0; off >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
+            const float r = ff_site_update(p, set, v, msrc, mdst, in, out, u, w, x1, x2, lane);
             if (lane == 0) atomicMax(res_cur + set, __float_as_uint(r));
             __syncwarp();
         }
@@ -632,9 +776,9 @@ __global__ void __launch_bounds__(kBpWarps * 32) bp_ff_kernel(BPFFParams p)
             const int s = s0 + lane;
             bool pending = false;
             if (s < p.n_sets) {
-                const bool was = p.done_it[s] != 0 || (it > 1 && __uint_as_float(res_prev[s]) < p.tol);
+                const bool was = __ldcg(p.done_it + s) != 0 || (it > 1 && __uint_as_float(__ldcg(res_prev + s)) < p.tol);
                 if (!was) {
-                    const float rs = __uint_as_float(res_cur[s]);
+                    const float rs = __uint_as_float(__ldcg(res_cur + s));
                     if (rs < p.tol) {
                         if (recorder) { p.done_it[s] = it; p.iters_out[s] = it; p.res_out[s] = (double)rs; p.final_buf[s] = dst; }
                     } else {
@@ -646,6 +790,59 @@ __global__ void __launch_bounds__(kBpWarps * 32) bp_ff_kernel(BPFFParams p)
             if (__any_sync(0xffffffffu, pending)) all_done = false;
         }
         if (all_done) return;
+    }
+}
+
+// Float-float BP with one thread-block cluster per tensor set: the cluster's
+// warps share the set's sites of one colour, and the hardware cluster barrier
+// separates the colour phases, so no grid-wide barrier is needed and every set
+// stops at its own convergence (the other sets do not wait for it).  Colour
+// order only (in place, buffer 0).  Every block of a cluster takes the same
+// path: the loop decision depends only on the set's residual, read after a
+// cluster barrier, and the loop is bounded by max_iter.
+__global__ void __launch_bounds__(kBpWarps * 32, 4) bp_ff_cluster_kernel(BPFFParams p)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ ff ffsmem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    ff *ws = ffsmem + wib * p.smem_per_warp;
+    ff *in = ws;
+    ff *out = in + kMaxDeg * kMsgStride;
+    ff *u = out + kMaxDeg * kMsgStride;
+    ff *w = u + p.tabA;
+    ff *x1 = w + p.tabC;
+    ff *x2 = x1 + p.tabA;
+    const int rank = (int)cluster.block_rank(), CL = (int)cluster.num_blocks();
+    const int set = blockIdx.x / CL;
+    const int cwarp = rank * kBpWarps + wib, cwarps = CL * kBpWarps;
+    const int64_t msg_set = (int64_t)p.n_legs * kMsgStride;
+    ff *msg = p.msg + set * msg_set;
+    for (int it = 1; it <= p.max_iter; ++it) {
+        // residual slots rotate over three sweeps: the slot cleared here was
+        // last read before the previous sweep's barriers
+        unsigned int *res_cur = p.res + (int64_t)(it % 3) * p.n_sets + set;
+        if (rank == 0 && threadIdx.x == 0) p.res[(int64_t)((it + 1) % 3) * p.n_sets + set] = 0u;
+        for (int ph = 0; ph < p.n_colors; ++ph) {
+            const int c0 = p.color_ptr[ph], nc = p.color_ptr[ph + 1] - c0;
+            for (int q = cwarp; q < nc; q += cwarps) {
+                const float r = ff_site_update(p, set, p.color_sites[c0 + q], msg, msg, in, out, u, w, x1, x2, lane);
+                if (lane == 0) atomicMax(res_cur, __float_as_uint(r));
+                __syncwarp();
+            }
+            cluster.sync();
+        }
+        const float rs = __uint_as_float(__ldcg(res_cur));
+        if (rs < p.tol || it == p.max_iter) {
+            if (rank == 0 && threadIdx.x == 0) {
+                const bool conv = rs < p.tol;
+                p.done_it[set] = conv ? it : 0;
+                p.iters_out[set] = conv ? it : 0;
+                p.res_out[set] = (double)rs;
+                p.final_buf[set] = 0;
+            }
+            return;
+        }
     }
 }
 
@@ -1124,6 +1321,39 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         fp.flags = flags; fp.res_out = res_out; fp.bar = bar;
         fp.smem_per_warp = per_warp; fp.tabA = tabA; fp.tabC = tabC;
         fp.n_colors = g.n_colors; fp.color_ptr = g.d_color_ptr; fp.color_sites = g.d_color_sites;
+        // one cluster per tensor set when the colour classes are small enough
+        // (at most four sites per warp and phase in a cluster of <= 16 blocks)
+        int max_color = 0;
+        for (int c = 0; c < g.n_colors; ++c) max_color = std::max(max_color, g.color_ptr[c + 1] - g.color_ptr[c]);
+        int CL = 1;
+        while (CL * kBpWarps < max_color && CL < 16) CL *= 2;
+        bool cluster_ok = g.n_colors > 0 && max_color <= CL * kBpWarps * 4;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute cattr[1];
+        if (cluster_ok) {
+            cudaFuncSetAttribute(bp_ff_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(bp_ff_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cfg.blockDim = dim3(kBpWarps * 32);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = s;
+            cattr[0].id = cudaLaunchAttributeClusterDimension;
+            cattr[0].val.clusterDim.y = 1;
+            cattr[0].val.clusterDim.z = 1;
+            cfg.attrs = cattr;
+            cfg.numAttrs = 1;
+            // the largest cluster the device schedules with this kernel's resources
+            for (;;) {
+                cattr[0].val.clusterDim.x = CL;
+                cfg.gridDim = dim3(CL);
+                int ncl = 0;
+                if (cudaOccupancyMaxActiveClusters(&ncl, (void *)bp_ff_cluster_kernel, &cfg) == cudaSuccess && ncl > 0) break;
+                cudaGetLastError();
+                if (CL == 1) { cluster_ok = false; break; }
+                CL /= 2;
+                if (max_color > CL * kBpWarps * 4) { cluster_ok = false; break; }
+            }
+        }
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(bp_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm_ff = 0;
@@ -1136,7 +1366,12 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         cudaError_t fe;
         {
             ProfScope ps(ctx, s, "bp_sweeps");
-            fe = cudaLaunchCooperativeKernel((void *)bp_ff_kernel, dim3(nb_ff), dim3(kBpWarps * 32), fargs, smem, s);
+            if (cluster_ok) {
+                cfg.gridDim = dim3((unsigned)(n_sets * CL));
+                fe = cudaLaunchKernelEx(&cfg, bp_ff_cluster_kernel, fp);
+            } else {
+                fe = cudaLaunchCooperativeKernel((void *)bp_ff_kernel, dim3(nb_ff), dim3(kBpWarps * 32), fargs, smem, s);
+            }
         }
         if (fe != cudaSuccess) { dev_free(ctx, ffbuf, s); dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, fe); }
         {
