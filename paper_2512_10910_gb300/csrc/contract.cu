@@ -583,15 +583,24 @@ __global__ void shape_verify_kernel(ContractParams P, const int32_t *shape_of, c
     }
 }
 
+// One plan per shape (built by lane 0 of a warp), plus the per-shape figures the
+// host needs: stats[sh] = {steps (-1: no plan), multiply-adds, largest running
+// tensor, 0}.
 __global__ void shape_plan_kernel(ContractParams P, const int32_t *rep, int n_shapes, int32_t *plans,
-                                  int32_t *steps)
+                                  int32_t *steps, int32_t *stats)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *plan = (int *)smem_raw + wib * (kMaxSteps * kStepInts + kMaxSteps + 4);
     int *sites = plan + kMaxSteps * kStepInts;
     for (int sh = blockIdx.x * kCtWarps + wib; sh < n_shapes; sh += gridDim.x * kCtWarps) {
-        if (lane == 0) steps[sh] = build_plan(P, rep[sh], plan, sites, kWarpTensorMax);
+        if (lane == 0) {
+            const int n = build_plan(P, rep[sh], plan, sites, kWarpTensorMax);
+            steps[sh] = n;
+            int fma = 0, mo = 1;
+            for (int t = 0; t < n; ++t) { fma += plan[t * kStepInts + 4] * plan[t * kStepInts + 5]; mo = max(mo, plan[t * kStepInts + 4]); }
+            stats[4 * sh] = n; stats[4 * sh + 1] = fma; stats[4 * sh + 2] = mo; stats[4 * sh + 3] = 0;
+        }
         __syncwarp();
         const int n = steps[sh];
         for (int i = lane; i < (n > 0 ? n : 0) * kStepInts; i += 32) plans[(int64_t)sh * kPlanInts + i] = plan[i];
@@ -905,35 +914,35 @@ pne_status shapes_finish(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, Shape
                                                                   (const int32_t *)drep.ptr, (int32_t *)dbad.ptr);
     PNE_CUDA_TRY(ctx, cudaGetLastError());
     int ns = (int)rep.size();
-    std::vector<int32_t> bad(n), steps, plans;
+    std::vector<int32_t> bad(n);
+    DevBuf dstats;
+    std::vector<int32_t> stats;
     auto make_plans = [&](bool with_bad) -> pne_status {
         dev_free(ctx, rec.plans, s);
         dev_free(ctx, rec.plan_steps, s);
+        dev_free(ctx, dstats, s);
         pne_status e;
         if ((e = dev_alloc(ctx, rec.plans, (size_t)ns * kPlanInts * 4, s)) ||
-            (e = dev_alloc(ctx, rec.plan_steps, (size_t)ns * 4, s)))
+            (e = dev_alloc(ctx, rec.plan_steps, (size_t)ns * 4, s)) || (e = dev_alloc(ctx, dstats, (size_t)ns * 16, s)))
             return e;
         const size_t smem = (size_t)kCtWarps * (kMaxSteps * kStepInts + kMaxSteps + 4) * 4;
         shape_plan_kernel<<<grid_for(ns, kCtWarps, ctx->n_sm, 16), kCtWarps * 32, smem, s>>>(
-            cp, (const int32_t *)drep.ptr, ns, (int32_t *)rec.plans.ptr, (int32_t *)rec.plan_steps.ptr);
+            cp, (const int32_t *)drep.ptr, ns, (int32_t *)rec.plans.ptr, (int32_t *)rec.plan_steps.ptr,
+            (int32_t *)dstats.ptr);
         PNE_CUDA_TRY(ctx, cudaGetLastError());
-        steps.assign(ns, 0);
-        plans.assign((size_t)ns * kPlanInts, 0);
-        const size_t nb = with_bad ? (size_t)n * 4 : 0, sb = (size_t)ns * 4, pb = plans.size() * 4;
-        char *hp = (char *)pinned_slot(3, nb + sb + pb);
+        stats.assign((size_t)ns * 4, 0);
+        const size_t nb = with_bad ? (size_t)n * 4 : 0, sb = stats.size() * 4;
+        char *hp = (char *)pinned_slot(3, nb + sb);
         if (hp) {
             if (nb) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(hp, dbad.ptr, nb, cudaMemcpyDeviceToHost, s));
-            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(hp + nb, rec.plan_steps.ptr, sb, cudaMemcpyDeviceToHost, s));
-            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(hp + nb + sb, rec.plans.ptr, pb, cudaMemcpyDeviceToHost, s));
+            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(hp + nb, dstats.ptr, sb, cudaMemcpyDeviceToHost, s));
             HostScope hw__(ctx, "sync_plans");
             PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
             if (nb) std::memcpy(bad.data(), hp, nb);
-            std::memcpy(steps.data(), hp + nb, sb);
-            std::memcpy(plans.data(), hp + nb + sb, pb);
+            std::memcpy(stats.data(), hp + nb, sb);
         } else {
             if (nb) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bad.data(), dbad.ptr, nb, cudaMemcpyDeviceToHost, s));
-            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(steps.data(), rec.plan_steps.ptr, sb, cudaMemcpyDeviceToHost, s));
-            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(plans.data(), rec.plans.ptr, pb, cudaMemcpyDeviceToHost, s));
+            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(stats.data(), dstats.ptr, sb, cudaMemcpyDeviceToHost, s));
             PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         }
         return PNE_OK;
@@ -958,13 +967,9 @@ pne_status shapes_finish(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, Shape
     bool ok = true;
     std::vector<int> shape_cls(ns, 0);
     for (int i = 0; i < ns; ++i) {
-        if (steps[i] < 0) { ok = false; break; }
-        int mo = 1;
-        for (int t = 0; t < steps[i]; ++t) {
-            const int32_t *stp = plans.data() + (size_t)i * kPlanInts + t * kStepInts;
-            rec.shape_fma[i] += (uint64_t)stp[4] * stp[5];
-            mo = std::max(mo, (int)stp[4]);
-        }
+        if (stats[4 * i] < 0) { ok = false; break; }
+        rec.shape_fma[i] = (uint64_t)stats[4 * i + 1];
+        const int mo = std::max(1, stats[4 * i + 2]);
         max_out = std::max(max_out, mo);
         while ((kClassMin << shape_cls[i]) < mo) ++shape_cls[i];
     }
@@ -1007,7 +1012,7 @@ pne_status shapes_finish(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, Shape
     // per-cluster step tables
     if (ok) {
         int max_steps = 1;
-        for (int i = 0; i < ns; ++i) max_steps = std::max(max_steps, steps[i]);
+        for (int i = 0; i < ns; ++i) max_steps = std::max(max_steps, stats[4 * i]);
         rec.step_stride = max_steps;
         dev_free(ctx, rec.step_off, s);
         dev_free(ctx, rec.step_site, s);
@@ -1025,7 +1030,7 @@ pne_status shapes_finish(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, Shape
     rec.n_shapes = ns;
     rec.max_out = max_out;
     rec.shaped = ok && max_out <= 256;
-    dev_free(ctx, dh, s); dev_free(ctx, drep, s); dev_free(ctx, dbad, s);
+    dev_free(ctx, dh, s); dev_free(ctx, drep, s); dev_free(ctx, dbad, s); dev_free(ctx, dstats, s);
     return PNE_OK;
 }
 
@@ -1330,12 +1335,16 @@ __device__ void lane_contract(const BatchGroup &G, int64_t i, int b, T *X0, T *X
 template <typename T, typename L, int R>
 __global__ void fused_batch_kernel(const BatchGroup *groups, const BatchItem *items, int64_t n_items,
                                    const SumDesc *descs, double *partials, unsigned long long *next,
-                                   unsigned int *done, const unsigned int *need, int xmax, int32_t *status)
+                                   unsigned int *done, const unsigned int *need, int xsm, int xglob, T *xscratch,
+                                   int32_t *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    T *X0 = (T *)smem_raw + (int64_t)wib * 2 * xmax * 32 + lane;
-    T *X1 = X0 + (int64_t)xmax * 32;
+    T *S0 = (T *)smem_raw + (int64_t)wib * 2 * xsm * 32 + lane;
+    T *S1 = S0 + (int64_t)xsm * 32;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    T *G0 = xscratch ? xscratch + gw * 2 * xglob * 32 + lane : nullptr;
+    T *G1 = xscratch ? G0 + (int64_t)xglob * 32 : nullptr;
     for (;;) {
         unsigned long long it = 0;
         if (lane == 0) it = atomicAdd(next, 1ull);
@@ -1345,7 +1354,8 @@ __global__ void fused_batch_kernel(const BatchGroup *groups, const BatchItem *it
         const BatchGroup &G = groups[wi.g];
         if (wi.kind == 0) {
             const int64_t i = wi.start + lane;
-            if (i < G.cp.n_clusters) lane_contract<T, L, R>(G, i, wi.member, X0, X1);
+            const bool big = wi.aux > xsm;             // running tensors beyond the shared slices
+            if (i < G.cp.n_clusters) lane_contract<T, L, R>(G, i, wi.member, big ? G0 : S0, big ? G1 : S1);
             __syncwarp();
             if (lane == 0) { __threadfence(); atomicAdd(done + wi.g, 1u); }
         } else {
@@ -1421,8 +1431,15 @@ __global__ void batch_finalize_kernel(const BatchGroup *groups, int G, const int
 // counters block: next item (u64) | done[G] (u32) | need[G] (u32) | status[4] (i32, 16-aligned)
 size_t status_offset(int G) { return ((size_t)8 + (size_t)8 * G + 15) & ~(size_t)15; }
 
+// Running tensors of the fused batch live in shared memory up to kBatchSmemX
+// entries per lane; items whose clusters need more use a per-warp slice of a
+// global scratch buffer (same interleaved layout), sized for the launch shape.
+constexpr int kBatchSmemX = 32;
+
 struct BatchPlan {
-    int dtype = 0, G = 0, xmax = 1;
+    int dtype = 0, G = 0, xmax = 1, xsm = 1;
+    DevBuf xscratch;                    // [warps][2][xmax][32] elements, when xmax > xsm
+    int64_t xscratch_warps = 0;
     int64_t n_items = 0, n_desc = 0, n_partials = 0, n_fin = 0, out_doubles = 0;
     std::vector<pne_terms *> terms;
     std::vector<int64_t> out_off;
@@ -1507,8 +1524,18 @@ pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms
         fin_start[g + 1] = fin_start[g] + (int64_t)p->n_members * (t->K + 1);
         // items: contraction chunks of 32 clusters, then (later) the sums
         const int64_t chunks = (cp.n_clusters + 31) / 32;
+        // running-tensor size an item needs: the class of its last cluster
+        // (the clusters are listed by ascending class)
+        std::vector<int32_t> chunk_x(chunks, 1);
+        if (G.shaped)
+            for (int64_t c = 0; c < chunks; ++c) {
+                const int64_t last = std::min<int64_t>(c * 32 + 31, cp.n_clusters - 1);
+                size_t q = 0;
+                while (q + 2 < rec.class_start.size() && rec.class_start[q + 1] <= last) ++q;
+                chunk_x[c] = std::min(rec.class_xmax[q], std::max(rec.max_out, 1));
+            }
         for (int b = 0; b < p->n_members; ++b)
-            for (int64_t c = 0; c < chunks; ++c) items.push_back({g, 0, b, 0, c * 32});
+            for (int64_t c = 0; c < chunks; ++c) items.push_back({g, 0, b, chunk_x[c], c * 32});
         need[g] = (unsigned int)(chunks * p->n_members);
         for (int b = 0; b < p->n_members; ++b)
             for (int d = 0; d < G.n_desc; ++d) sum_items.push_back({g, 1, b, d, 0});
@@ -1541,7 +1568,8 @@ pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(cb + 8 + (size_t)bp->G * 4, need.data(), (size_t)bp->G * 4, cudaMemcpyHostToDevice, s));
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const size_t elem = (dtype == PNE_F64) ? 8 : 4;
-    bp->smem_per_warp = 2 * (size_t)bp->xmax * 32 * elem;
+    bp->xsm = std::min(bp->xmax, kBatchSmemX);
+    bp->smem_per_warp = 2 * (size_t)bp->xsm * 32 * elem;
     *out = bp;
     return PNE_OK;
 }
@@ -1558,9 +1586,15 @@ pne_status launch_fused(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStrea
     unsigned int *done = (unsigned int *)(cb + 8);
     const unsigned int *need = (const unsigned int *)(cb + 8 + (size_t)bp->G * 4);
     int32_t *status = (int32_t *)(cb + status_offset(bp->G));
+    const bool glob = bp->xmax > bp->xsm;
+    if (glob && bp->xscratch_warps < (int64_t)wpb * bps * ctx->n_sm) {
+        set_error(ctx, PNE_EINVAL, "batch scratch not prepared for this launch shape");
+        return PNE_EINVAL;
+    }
     kern<<<bps * ctx->n_sm, wpb * 32, smem, s>>>((const BatchGroup *)bp->groups.ptr, (const BatchItem *)bp->items.ptr,
                                                  bp->n_items, (const SumDesc *)bp->descs.ptr, (double *)bp->partials.ptr,
-                                                 next, done, need, bp->xmax, status);
+                                                 next, done, need, bp->xsm, glob ? bp->xmax : 0,
+                                                 glob ? (T *)bp->xscratch.ptr : nullptr, status);
     PNE_CUDA_TRY(ctx, cudaGetLastError());
     return PNE_OK;
 }
@@ -1583,6 +1617,22 @@ int batch_max_blocks_per_sm(BatchPlan *bp, int wpb)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_batch_kernel<float, Load<float>, 0>, wpb * 32, smem);
     }
     return e == cudaSuccess ? n : 0;
+}
+
+// The global running-tensor scratch for a launch shape (grow only; call
+// before capturing a launch into a graph).
+pne_status batch_prepare(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStream_t s)
+{
+    if (bp->xmax <= bp->xsm) return PNE_OK;
+    const int64_t warps = (int64_t)wpb * bps * ctx->n_sm;
+    if (warps <= bp->xscratch_warps) return PNE_OK;
+    const size_t elem = (bp->dtype == PNE_F64) ? 8 : 4;
+    dev_free(ctx, bp->xscratch, s);
+    bp->xscratch_warps = 0;
+    pne_status st = dev_alloc(ctx, bp->xscratch, (size_t)warps * 2 * bp->xmax * 32 * elem, s);
+    if (st) return st;
+    bp->xscratch_warps = warps;
+    return PNE_OK;
 }
 
 pne_status batch_enqueue(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStream_t s)
@@ -1621,7 +1671,8 @@ pne_status batch_enqueue(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStre
 void batch_plan_destroy(pne_ctx *ctx, BatchPlan *bp)
 {
     if (!bp) return;
-    DevBuf *bufs[] = {&bp->groups, &bp->items, &bp->descs, &bp->partials, &bp->fin_start, &bp->counters, &bp->d_out};
+    DevBuf *bufs[] = {&bp->groups, &bp->items, &bp->descs, &bp->partials, &bp->fin_start, &bp->counters, &bp->d_out,
+                      &bp->xscratch};
     for (DevBuf *b : bufs) dev_free(ctx, *b, nullptr);
     if (bp->h_out) cudaFreeHost(bp->h_out);
     delete bp;

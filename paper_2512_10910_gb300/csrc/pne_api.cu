@@ -1044,6 +1044,9 @@ pne_status pne_batch_create(pne_ctx *ctx, int32_t n, pne_terms *const *terms, pn
                 for (int bi = 0; bi < 4; ++bi) {
                     if (bcand[bi] > maxb) continue;
                     double t_best = 1e300;
+                    if ((st = batch_prepare(ctx, b->plan, wcand[wi], bcand[bi], s))) {
+                        ctx->prof.on = prof; pne_batch_destroy(b); return st;
+                    }
                     for (int rep = 0; rep < 3; ++rep) {
                         cudaEventRecord(e0, s);
                         st = batch_enqueue(ctx, b->plan, wcand[wi], bcand[bi], s);
@@ -1062,6 +1065,7 @@ pne_status pne_batch_create(pne_ctx *ctx, int32_t n, pne_terms *const *terms, pn
             tune_cache_store(key, b->wpb, b->bps, best);
         }
     }
+    if ((st = batch_prepare(ctx, b->plan, b->wpb, b->bps, s))) { ctx->prof.on = prof; pne_batch_destroy(b); return st; }
     b->use_graph = !opts || opts->use_graph;
     if (b->use_graph) {
         cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
