@@ -129,6 +129,15 @@ def oracle_step(wl, net):
     return r.n_terms, time.perf_counter() - t0, r
 
 
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s (GB/s), else the fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (of fallback)"
+
+
 def algorithmic_bp_flops(g, iters):
     """FP64 flops of one BP sweep-set: per site and sweep, the two half
     contractions touch every tensor entry once with one multiply-add each
@@ -310,6 +319,17 @@ def main():
         roof.update(achieved=2.0 * fma * B / (avg_ms * 1e-3) / 1e12, peak=pk / 1e12,
                     peak_source="measured FMA-chain kernel (pne_measure_fma_peak)",
                     work=f"2 flops per plan multiply-add; {fma} multiply-adds per network")
+    elif fam in ("enum_expand", "enum_dfs"):
+        # the cluster search is integer work bound by latency; its algorithmic
+        # traffic is the cluster lists it writes (edges, sorted vertices, size)
+        n_cl = res[0]["n_clusters"]
+        per_cluster = 4 * K + 4 * (K + 1) + 4
+        per_search_ms = tot / prof_steps
+        peak_gbs, src = hbm_peak()
+        roof.update(bound="hbm", unit="GB/s", achieved=n_cl * per_cluster / (per_search_ms * 1e-3) / 1e9,
+                    peak=peak_gbs, peak_source=src,
+                    work=f"{n_cl} clusters x {per_cluster} B written per search "
+                         f"({launches // prof_steps} launches per search, timed together)")
     if roof["achieved"] is not None and roof["peak"]:
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["avg_launch_ms"] = avg_ms
