@@ -195,13 +195,22 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
 
     enum_cache = [0]      # the headline recomputes the enumeration every step
+    # the enumeration is geometry-only: it runs on a second stream while BP runs
+    # on the first (the partition is built without waiting for its convergence
+    # record, which pne_sum reads); the contraction waits for both
+    side = torch.cuda.Stream(dev)
+    side_h = side.cuda_stream
+    joined = torch.cuda.Event()
 
     def step(data, dtype):
         ns, keep = pne.network_struct(g, data=data, n_batch=B)
-        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0, BP_ARITH[args.bp]), ctypes_stream)
+        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0, BP_ARITH[args.bp], 1),
+                                          ctypes_stream)
         try:
-            terms, nc, nt = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, mode, enum_cache[0]), ctypes_stream)
+            terms, nc, nt = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, mode, enum_cache[0]), side_h)
             try:
+                joined.record(side)
+                stream.wait_event(joined)
                 pne.pne_contract_terms(ctx.h, terms, dtype, ctypes_stream)
                 res = pne.pne_sum(ctx.h, terms, ctypes_stream)
             finally:

@@ -104,6 +104,14 @@ typedef struct {
                             precision per operation, on the FP32 pipes); the
                             messages, projectors and blocked tensors handed on
                             are FP64 either way */
+    int32_t async_status; /* 0: pne_build_partition synchronises its stream and
+                            returns the convergence status; 1: it returns once
+                            the work is queued (no synchronisation), and the
+                            convergence record is read by the next call that
+                            synchronises for this partition (pne_sum returns
+                            PNE_ENOCONV / PNE_EDEGENERATE / PNE_ETIMEOUT then,
+                            after writing every result; non-converged sets show
+                            bp_iters == 0) */
 } pne_partition_opts;
 
 typedef struct {

@@ -1255,7 +1255,8 @@ int grid_for(int64_t n, int block, int n_sm)
 
 // ---------------------------------------------------------------- host launchers
 pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, double damping,
-                     cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags, int arithmetic)
+                     cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags, int arithmetic,
+                     cudaMemcpyKind rec_kind)
 {
     const Geometry &g = p->geo->full;
     const int n_sets = p->n_sets;
@@ -1419,9 +1420,9 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
     if (e != cudaSuccess) { dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, e); }
     }
     // copy out the convergence record
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_iters, iters, n_sets * 4, cudaMemcpyDeviceToHost, s));
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_res, res_out, n_sets * 8, cudaMemcpyDeviceToHost, s));
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_flags, flags, 8, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_iters, iters, n_sets * 4, rec_kind, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_res, res_out, n_sets * 8, rec_kind, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_flags, flags, 8, rec_kind, s));
     // the final-buffer index stays on the device for the gauge kernel
     if (p->gauge.ptr == nullptr) { dev_free(ctx, scratch, s); return PNE_EINVAL; }
     GaugeParams gp;
@@ -1434,7 +1435,7 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         gauge_kernel<<<grid_for((int64_t)n_sets * g.n_bonds, 128, ctx->n_sm), 128, 0, s>>>(gp);
     }
     PNE_CUDA_TRY(ctx, cudaGetLastError());
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_flags + 2, flags, 8, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_flags + 2, flags, 8, rec_kind, s));
     dev_free(ctx, ffbuf, s);
     dev_free(ctx, scratch, s);
     return PNE_OK;

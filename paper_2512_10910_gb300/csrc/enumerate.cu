@@ -16,12 +16,14 @@
 // sites only.
 //
 // Parallel schedule: the first levels of every anchor's tree are expanded
-// level by level (one warp per node, one lane per candidate); each node of the
-// last prefix level is then searched depth-first by one thread, unless the
-// prefix already reaches size K - 1 and one more warp-parallel step ends it.  Every unit first counts what it
-// emits per cluster size; an exclusive scan over (size, unit) gives each unit
-// its output slots, and a second pass writes.  The output is grouped by size
-// and deterministic.
+// level by level (one warp per node, one lane per candidate) into a node arena
+// whose level bounds stay on the device, so the levels need no host round
+// trip; each node of the last prefix level is then searched depth-first by one
+// thread, unless the prefix already reaches size K - 1 and one more
+// warp-parallel step ends it.  Every unit first counts what it emits per
+// cluster size; an exclusive scan over (size, unit) gives each unit its output
+// slots, and a second pass writes.  The output is grouped by size and
+// deterministic.
 //
 // Terms (Eq. A4): a term is a set of pairwise vertex-disjoint clusters with
 // total size <= K (the connected components of one P/Q string).  Tuples
@@ -307,8 +309,6 @@ struct SearchCtl {
     int32_t cand_overflow;        // a candidate list outgrew kNodeU
     int32_t stop;                 // first level whose children did not fit (0: none)
     int64_t need;                 // arena size that level asked for
-    uint32_t bar_count, bar_gen;  // grid barrier of the cooperative level kernel
-    int32_t bar_timeout, pad;
 };
 
 struct Arena {
@@ -328,7 +328,6 @@ __global__ void arena_init_kernel(Arena a, int n_roots)
     if (threadIdx.x <= kPrefixMax + 1) a.lv[threadIdx.x] = threadIdx.x == 0 ? 0 : n_roots;
     if (threadIdx.x == 0) {
         a.ctl->cand_overflow = 0; a.ctl->stop = 0; a.ctl->need = 0;
-        a.ctl->bar_count = 0; a.ctl->bar_gen = 0; a.ctl->bar_timeout = 0; a.ctl->pad = 0;
     }
 }
 
@@ -560,77 +559,41 @@ expand_kernel(GeomView g, Arena A, int lo_level, int hi_level, int K, int mode, 
     expand_chunk(g, A, A.lv[lo_level - 1], A.lv[hi_level], K, mode, pass, out, 0, 0);
 }
 
-// Grid-wide barrier of a cooperative launch, bounded: after kSearchSpinLimit
-// polls it records a timeout and every block leaves the search.
-constexpr long long kSearchSpinLimit = 1LL << 26;
-
-__device__ bool search_barrier(SearchCtl *ctl, unsigned nblocks)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *gen = &ctl->bar_gen;
-        const unsigned g0 = *gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&ctl->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*gen == g0) {
-                if (++spins > kSearchSpinLimit) { atomicExch(&ctl->bar_timeout, 1); break; }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return *((volatile int32_t *)&ctl->bar_timeout) == 0;
-}
-
-// Prefix levels 1..D-1 in one cooperative launch: per level a counting phase
-// (children and emissions per node, chunk scans), a barrier, a writing phase
-// that places the next level (every block derives the same level size and stop
-// decision from the chunk totals), and a barrier.  Block 0 records the level
-// bounds and the stop for the kernels that follow.
-__global__ void __launch_bounds__(32 * kExpandWarps) bfs_levels_kernel(GeomView g, Arena A, int D, int K, int mode)
+// One level step is two ordinary launches (no grid barrier, so the search can
+// share the GPU with other streams' work): expand_kernel(kCount) for level d,
+// then this kernel, which derives each block's child offset and the level's
+// size from the chunk totals, places level d + 1 (or records the stop, block 0)
+// and writes the children.  Every block reaches the same decision.
+__global__ void __launch_bounds__(32 * kExpandWarps) expand_children_kernel(GeomView g, Arena A, int d, int K, int mode)
 {
     __shared__ int64_t red[2][32 * kExpandWarps];
     Emit none{nullptr, nullptr, nullptr, 0, 0};
-    int64_t lo = 0, hi = A.lv[1];                      // level 1: the anchors
-    for (int d = 1; d < D; ++d) {
-        expand_chunk(g, A, lo, hi, K, mode, kCount, none, 0, 0);
-        if (!search_barrier(A.ctl, gridDim.x)) return;
-        // children before this block's chunk, and in all chunks
-        int64_t before = 0, total = 0;
-        for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
-            const int64_t c = __ldcg(A.chunk_tot + q);
-            total += c;
-            if (q < (int)blockIdx.x) before += c;
-        }
-        red[0][threadIdx.x] = before; red[1][threadIdx.x] = total;
-        __syncthreads();
-        for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-            if ((int)threadIdx.x < h) {
-                red[0][threadIdx.x] += red[0][threadIdx.x + h];
-                red[1][threadIdx.x] += red[1][threadIdx.x + h];
-            }
-            __syncthreads();
-        }
-        before = red[0][0]; total = red[1][0];
-        __syncthreads();
-        const bool fits = hi + total <= A.cap;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            for (int e = d + 1; e <= kPrefixMax + 1; ++e) A.lv[e] = fits ? hi + total : hi;
-            if (!fits) { A.ctl->stop = d; A.ctl->need = hi + total; }
-        }
-        if (!fits) return;                             // the same decision in every block
-        expand_chunk(g, A, lo, hi, K, mode, kChildren, none, hi, before);
-        if (!search_barrier(A.ctl, gridDim.x)) return;
-        lo = hi;
-        hi += total;
+    if (A.ctl->stop != 0) return;                      // an earlier level stopped the search
+    const int64_t lo = A.lv[d - 1], hi = A.lv[d];
+    int64_t before = 0, total = 0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
+        const int64_t c = A.chunk_tot[q];
+        total += c;
+        if (q < (int)blockIdx.x) before += c;
     }
+    red[0][threadIdx.x] = before; red[1][threadIdx.x] = total;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + h];
+            red[1][threadIdx.x] += red[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    before = red[0][0]; total = red[1][0];
+    __syncthreads();
+    const bool fits = hi + total <= A.cap;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int e = d + 1; e <= kPrefixMax + 1; ++e) A.lv[e] = fits ? hi + total : hi;
+        if (!fits) { A.ctl->stop = d; A.ctl->need = hi + total; }
+    }
+    if (!fits) return;
+    expand_chunk(g, A, lo, hi, K, mode, kChildren, none, hi, before);
 }
 
 // ---------------------------------------------------------------- depth-first tasks
@@ -945,17 +908,14 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     const int final_kind = (K <= 1) ? 0 : (D == K - 1 ? 1 : 2);
     const bool small = (K <= 12 && umax_need <= 64);
     // chunks of the blocked passes: one wave of resident blocks
-    // resident blocks per SM of the two search kernels (queried once per context)
+    // chunks of the blocked passes: one wave of resident blocks (the occupancy
+    // is queried once per context)
     if (ctx->occ_expand < 0) {
-        int a = 0, b = 0;
+        int a = 0;
         PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, expand_kernel, 32 * kExpandWarps, 0));
-        PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bfs_levels_kernel, 32 * kExpandWarps, 0));
-        ctx->occ_bfs = b;
         ctx->occ_expand = a;
     }
-    const int per_sm = ctx->occ_expand, per_sm_c = ctx->occ_bfs;
-    const int G = ctx->n_sm * std::max(1, per_sm);
-    const int Gc = ctx->n_sm * std::max(1, per_sm_c);   // co-resident blocks of the cooperative launch
+    const int G = ctx->n_sm * std::max(1, ctx->occ_expand);
     const int Gd = grid1(1 << 20, 128, ctx->n_sm);    // grid of the depth-first kernel
     const std::string hint_key = std::to_string(g.hash) + ":" + std::to_string(Mc) + ":" + std::to_string(K) + ":" +
                                  std::to_string(mode);
@@ -982,7 +942,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     for (;;) {
         // arena: nodes, then [lv | ctl | child_cnt | child_off | chunk_tot], then counts
         if ((st = dev_alloc(ctx, nodes, sizeof(Node) * (size_t)cap, s))) return st;
-        const size_t tab_bytes = sizeof(Readback) + (size_t)cap * 4 + (size_t)cap * 8 + (size_t)std::max(G, Gc) * 8 + 64;
+        const size_t tab_bytes = sizeof(Readback) + (size_t)cap * 4 + (size_t)cap * 8 + (size_t)G * 8 + 64;
         if ((st = dev_alloc(ctx, tables, tab_bytes, s))) return st;
         if ((st = dev_alloc(ctx, counts, (size_t)(K + 1) * cap * 4, s))) return st;
         char *tb = (char *)tables.ptr;
@@ -992,7 +952,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         A.ctl = (SearchCtl *)(tb + offsetof(Readback, ctl));
         A.child_off = (int64_t *)(tb + sizeof(Readback));
         A.chunk_tot = A.child_off + cap;
-        A.child_cnt = (int32_t *)(A.chunk_tot + std::max(G, Gc));
+        A.child_cnt = (int32_t *)(A.chunk_tot + G);
         A.counts = (int32_t *)counts.ptr;
         A.base = nullptr;
         PNE_CUDA_TRY(ctx, cudaMemsetAsync(counts.ptr, 0, (size_t)(K + 1) * cap * 4, s));
@@ -1001,12 +961,10 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
             ProfScope ps__(ctx, s, "enum_roots");
             roots_kernel<<<grid1(Mc, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, mode, A, none, 0);
         }
-        if (D > 1) {
+        for (int d = 1; d < D; ++d) {
             ProfScope ps__(ctx, s, "enum_expand");
-            int Dv = D, Kv = K, mv = mode;
-            void *args[] = {&gv, &A, &Dv, &Kv, &mv};
-            PNE_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void *)bfs_levels_kernel, dim3(Gc), dim3(32 * kExpandWarps),
-                                                          args, 0, s));
+            expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, d, K, mode, kCount, none);
+            expand_children_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, K, mode);
         }
         if (final_kind == 1) {
             ProfScope ps__(ctx, s, "enum_expand");
@@ -1018,10 +976,6 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         // one (size, node) table over the arena; the same round trip brings the
         // level bounds and the stop record
         if ((st = scan_counts(ctx, A.counts, K + 1, cap, base, per_size, s, A.lv, sizeof(Readback), &hb))) return st;
-        if (hb.ctl.bar_timeout) {
-            set_error(ctx, PNE_ETIMEOUT, "grid barrier timed out in the cluster search");
-            return PNE_ETIMEOUT;
-        }
         if (hb.ctl.cand_overflow) {
             set_error(ctx, PNE_EOVERFLOW, "candidate list overflow in the cluster search");
             return PNE_EOVERFLOW;

@@ -507,6 +507,35 @@ GeomPair::~GeomPair()
     dev_free(ctx, closed.storage, free_stream);
 }
 
+pne_status partition_record(pne_ctx *ctx, pne_partition *p, const char *rec)
+{
+    const size_t B = p->n_sets;
+    const int32_t *flags = (const int32_t *)(rec + B * 8);
+    std::memcpy(p->bp_residual.data(), rec, B * 8);
+    std::memcpy(p->bp_iters.data(), rec + B * 8 + 16, B * 4);
+    p->rec_pending = false;
+    if (flags[0] || flags[2]) { set_error(ctx, PNE_ETIMEOUT, "grid barrier timed out in BP"); return PNE_ETIMEOUT; }
+    if (flags[1] || flags[3]) { set_error(ctx, PNE_EDEGENERATE, "zero message or zero message overlap"); return PNE_EDEGENERATE; }
+    for (size_t b = 0; b < B; ++b)
+        if (p->bp_iters[b] == 0) {
+            set_error(ctx, PNE_ENOCONV, "BP did not converge for tensor set " + std::to_string(b));
+            return PNE_ENOCONV;
+        }
+    return PNE_OK;
+}
+
+pne_status partition_settle(pne_ctx *ctx, pne_partition *p)
+{
+    if (!p->rec_pending) return PNE_OK;
+    const size_t bytes = (size_t)p->n_sets * 12 + 16;
+    std::vector<char> rec(bytes);
+    char *h = (char *)pinned_slot(0, bytes);
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h ? h : rec.data(), p->rec_dev.ptr, bytes, cudaMemcpyDeviceToHost, p->last_stream));
+    PNE_CUDA_TRY(ctx, cudaStreamSynchronize(p->last_stream));
+    if (h) std::memcpy(rec.data(), h, bytes);
+    return partition_record(ctx, p, rec.data());
+}
+
 }  // namespace pne
 
 using namespace pne;
@@ -635,6 +664,21 @@ pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_p
     const int arith = opts ? opts->arithmetic : 0;
     if (arith != 0 && arith != 1) { pne_partition_destroy(p); set_error(ctx, PNE_EINVAL, "arithmetic must be 0 or 1"); return PNE_EINVAL; }
     p->arithmetic = arith;
+    if (opts && opts->async_status) {
+        // deferred record: kept on the device, read by the next synchronising call
+        if ((st = dev_alloc(ctx, p->rec_dev, B * 12 + 16, s))) { pne_partition_destroy(p); return st; }
+        char *rd = (char *)p->rec_dev.ptr;
+        if (cudaMemsetAsync(rd, 0, B * 12 + 16, s) != cudaSuccess ||
+            (st = launch_bp(ctx, p, tol, max_iter, damping, s, (int32_t *)(rd + B * 8 + 16), (double *)rd,
+                            (int32_t *)(rd + B * 8), arith, cudaMemcpyDeviceToDevice)) ||
+            (st = launch_gauge(ctx, p, s, nullptr))) {
+            pne_partition_destroy(p);
+            return st ? st : PNE_ECUDA;
+        }
+        p->rec_pending = true;
+        *out = p;
+        return PNE_OK;
+    }
     if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, h_iters, h_res, flags, arith)) ||
         (st = launch_gauge(ctx, p, s, nullptr))) {
         pne_partition_destroy(p);
@@ -665,7 +709,7 @@ void pne_partition_destroy(pne_partition *p)
     pne_ctx *ctx = p->ctx;
     cudaStream_t s = p->last_stream;
     DevBuf *bufs[] = {&p->T, &p->msg, &p->gauge, &p->Mb, &p->site_info, &p->site_scale, &p->site_zero,
-                      &p->vac, &p->Mb32, &p->Mb16};
+                      &p->vac, &p->Mb32, &p->Mb16, &p->rec_dev};
     for (DevBuf *b : bufs) dev_free(ctx, *b, s);
     if (p->geo) p->geo->free_stream = s;          // a geometry left without users is freed on this stream
     delete p;
@@ -682,6 +726,8 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
     if (mode != PNE_MODE_LOOP && mode != PNE_MODE_ALL) { set_error(ctx, PNE_EINVAL, "unknown mode"); return PNE_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     const Geometry &g = part->geo->closed;
+    // the geometry tables may have been queued on the partition's stream
+    if (part->geo->ready) PNE_CUDA_TRY(ctx, cudaStreamWaitEvent(s, part->geo->ready, 0));
     std::string key = std::to_string(g.hash) + ":" + std::to_string(g.n_sites) + ":" + std::to_string(g.n_bonds) +
                       ":" + std::to_string(K) + ":" + std::to_string(mode);
     std::shared_ptr<EnumRecord> rec;
@@ -836,27 +882,35 @@ pne_status pne_sum(pne_ctx *ctx, const pne_terms *t, void *stream, pne_result *o
     const int K = t->K, B = p->n_members;
     std::vector<double> c, a;
     int32_t status = 0;
-    // the vacuum record is read back with the sums (one synchronisation)
-    std::vector<double> vac((size_t)B * 3);
-    double *h_vac = (double *)pinned_slot(2, vac.size() * 8);
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_vac ? (void *)h_vac : (void *)vac.data(), p->vac.ptr, vac.size() * 8,
-                                      cudaMemcpyDeviceToHost, s));
+    // the vacuum record (and a deferred BP record) are read back with the sums:
+    // one synchronisation
+    const size_t vbytes = (size_t)B * 3 * 8;
+    const size_t rbytes = p->rec_pending ? (size_t)p->n_sets * 12 + 16 : 0;
+    std::vector<char> hb(vbytes + rbytes);
+    char *hp = (char *)pinned_slot(2, vbytes + rbytes);
+    char *dst = hp ? hp : hb.data();
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dst, p->vac.ptr, vbytes, cudaMemcpyDeviceToHost, s));
+    if (rbytes) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dst + vbytes, p->rec_dev.ptr, rbytes, cudaMemcpyDeviceToHost, s));
     pne_status st = launch_sums(ctx, t, s, c, a, &status);
     if (st) return st;
-    if (h_vac) std::memcpy(vac.data(), h_vac, vac.size() * 8);
+    if (hp) std::memcpy(hb.data(), hp, vbytes + rbytes);
+    const double *vac = (const double *)hb.data();
+    pne_status bp_st = PNE_OK;
+    if (rbytes) bp_st = partition_record(ctx, const_cast<pne_partition *>(p), hb.data() + vbytes);
     if (status) { set_error(ctx, PNE_EOVERFLOW, "a cluster exceeded the contraction buffer"); return PNE_EOVERFLOW; }
     for (int b = 0; b < B; ++b) {
         const int set = b / p->n_slices;
         finalize_result(out[b], K, t->mode, t->dtype, &c[(size_t)b * (K + 1)], &a[(size_t)b * (K + 1)], &vac[3 * (size_t)b],
                         t->rec->n_terms, t->rec->n_clusters, p->bp_iters[set], p->bp_residual[set]);
     }
-    return PNE_OK;
+    return bp_st;
 }
 
 pne_status pne_partition_update(pne_ctx *ctx, pne_partition *p, const double *data, int32_t data_on_device,
                                 const pne_partition_opts *opts, void *stream)
 {
     if (!ctx || !p || !data) return PNE_EINVAL;
+    partition_settle(ctx, p);                 // a deferred record of the previous build is superseded
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
     const double tol = (opts && opts->tol > 0) ? opts->tol : 1e-13;
@@ -1009,6 +1063,8 @@ pne_status pne_batch_create(pne_ctx *ctx, int32_t n, pne_terms *const *terms, pn
     for (pne_terms *t : b->terms) {
         if (!t) { delete b; return PNE_EINVAL; }
         b->n_results += t->part->n_members;
+        // the batch reports the BP record: read deferred ones now
+        partition_settle(ctx, const_cast<pne_partition *>(t->part));
     }
     pne_status st = batch_plan_create(ctx, b->terms, dtype, s, &b->plan);
     if (st) { delete b; return st; }

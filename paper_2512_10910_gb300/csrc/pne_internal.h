@@ -124,7 +124,7 @@ struct pne_ctx {
     int device = 0;
     int n_sm = 0;
     int64_t arena_max = 0;        // node-arena limit of the cluster search (0: the built-in limit)
-    int occ_expand = -1, occ_bfs = -1;   // resident blocks per SM of the search kernels (-1: not queried)
+    int occ_expand = -1;          // resident blocks per SM of the search kernel (-1: not queried)
     pne_alloc_fn alloc = nullptr;
     pne_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
@@ -182,6 +182,9 @@ struct pne_partition {
     std::vector<int32_t> bp_iters;   // per set
     std::vector<double> bp_residual; // per set
     cudaStream_t last_stream = nullptr;
+    // deferred convergence record (async_status): [res B doubles][flags 4][iters B]
+    pne::DevBuf rec_dev;
+    bool rec_pending = false;
 };
 
 namespace pne {
@@ -269,7 +272,13 @@ struct HostScope {
 // ------------------------------------------------------------------ kernels
 // BP, gauge, blocked layout (bp.cu)
 pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, double damping,
-                     cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags, int arithmetic = 0);
+                     cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags, int arithmetic = 0,
+                     cudaMemcpyKind rec_kind = cudaMemcpyDeviceToHost);
+// read a deferred convergence record (synchronises the partition's stream)
+pne_status partition_settle(pne_ctx *ctx, pne_partition *p);
+// parse a convergence record [res B doubles][flags 4][iters B] into the partition;
+// returns the BP status (ETIMEOUT, EDEGENERATE, ENOCONV or OK)
+pne_status partition_record(pne_ctx *ctx, pne_partition *p, const char *rec);
 pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t *h_flag);
 pne_status launch_convert(pne_ctx *ctx, pne_partition *p, int dtype, cudaStream_t s);
 

@@ -60,7 +60,7 @@ class Network(ctypes.Structure):
 
 class PartitionOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("damping", ctypes.c_double),
-                ("arithmetic", ctypes.c_int32)]
+                ("arithmetic", ctypes.c_int32), ("async_status", ctypes.c_int32)]
 
 
 class EnumOpts(ctypes.Structure):
@@ -383,10 +383,15 @@ def pne_measure_fma_peak(ctx, dtype, stream=None) -> float:
     return float(v.value)
 
 
-def pne_sum(ctx, terms, stream=None):
+def pne_sum(ctx, terms, stream=None, allow_noconv=False):
+    """Results of every tensor set and open-index assignment.  With a partition
+    built with async_status, a BP record that shows non-convergence makes this
+    raise unless allow_noconv (then the results carry bp_iters == 0)."""
     n = pne_terms_n_results(terms)
     out = (Result * n)()
-    _check(load_library().pne_sum(ctx, terms, stream, out), ctx)
+    st = load_library().pne_sum(ctx, terms, stream, out)
+    if not (st == PNE_ENOCONV and allow_noconv):
+        _check(st, ctx)
     return [r.as_dict() for r in out]
 
 

@@ -275,3 +275,49 @@ def test_search_arena_limit_gives_identical_lists(ctx, monkeypatch, shape, D, K,
         cl, _ = _canon(e1, None)
         assert cl == list(refo.clusters)
         _check_values(res, refo)
+
+
+# ---------------------------------------------------------------- deferred BP record, two streams
+def test_async_partition_and_enumeration_on_a_second_stream(ctx):
+    """The partition built without waiting for its BP record, the enumeration
+    run on another stream (it waits for the geometry only), the contraction
+    joined back: the same values bit for bit as the plain synchronous flow,
+    with the convergence record read by pne_sum."""
+    g = I.square_lattice(8, 8, 4)
+    nets = [I.random_tensors(g, s) for s in (11, 12)]
+    flat = np.concatenate([n.flat_data()[0] for n in nets])
+    data = torch.from_numpy(flat).cuda()
+    K = 8
+    ns, keep = pne.network_struct(g, data=data, n_batch=2)
+    part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0, 1, 0), None)
+    terms, _, _ = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, pne.PNE_MODE_LOOP, 0), None)
+    pne.pne_contract_terms(ctx.h, terms, pne.PNE_F64, None)
+    ref = pne.pne_sum(ctx.h, terms, None)
+    pne.pne_terms_destroy(terms); pne.pne_partition_destroy(part)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = torch.cuda.Event()
+    for _ in range(2):
+        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0, 1, 1), s1.cuda_stream)
+        terms, _, _ = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, pne.PNE_MODE_LOOP, 0), s2.cuda_stream)
+        ev.record(s2)
+        s1.wait_event(ev)
+        pne.pne_contract_terms(ctx.h, terms, pne.PNE_F64, s1.cuda_stream)
+        got = pne.pne_sum(ctx.h, terms, s1.cuda_stream)
+        pne.pne_terms_destroy(terms); pne.pne_partition_destroy(part)
+        for a, b in zip(got, ref):
+            assert a["log_abs"] == b["log_abs"] and a["sign"] == b["sign"]
+            assert np.array_equal(a["c"], b["c"])
+            assert a["bp_iters"] == b["bp_iters"] > 0
+    torch.cuda.synchronize()
+    del keep
+    # a deferred record that shows non-convergence: pne_sum reports it after
+    # writing the results
+    part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 2, 0.0, 1, 1), None)
+    terms, _, _ = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(4, pne.PNE_MODE_LOOP, 0), None)
+    pne.pne_contract_terms(ctx.h, terms, pne.PNE_F64, None)
+    with pytest.raises(pne.PneError) as ei:
+        pne.pne_sum(ctx.h, terms, None)
+    assert ei.value.status == pne.PNE_ENOCONV
+    res = pne.pne_sum(ctx.h, terms, None, allow_noconv=True)
+    assert all(r["bp_iters"] == 0 for r in res)
+    pne.pne_terms_destroy(terms); pne.pne_partition_destroy(part)
