@@ -206,6 +206,125 @@ __device__ int build_plan(const ContractParams &P, int64_t c, int *plan, int *si
     return nv;
 }
 
+// The same plan built by a whole warp: the greedy choice of each step is
+// evaluated by one lane per candidate site and settled by a warp minimum over
+// (new frontier, work, slot) — the serial order of preference — and lane 0
+// writes the step.  Working tables live in the warp's shared memory.
+struct PlanWork {
+    int legedge[kMaxSteps][kMaxDeg];
+    int mask[kMaxSteps];
+    int ends[32][2];
+    int qd[32];
+    int visited[kMaxSteps];
+    int F[kMaxFront];
+    int nF, fail;
+};
+static_assert(sizeof(PlanWork) <= 384 * sizeof(int), "plan work area");
+
+__device__ int build_plan_warp(const ContractParams &P, int64_t c, int *plan, int *sites_out, int maxT, PlanWork &W,
+                               int lane)
+{
+    const int32_t *E = P.cl_edges + c * P.width;
+    const int32_t *V = P.cl_verts + c * P.vwidth;
+    const int s = __popc(__ballot_sync(0xffffffffu, lane < P.width && E[lane] >= 0));
+    const int nv = __popc(__ballot_sync(0xffffffffu, lane < P.vwidth && V[lane] >= 0)) +
+                   ((P.vwidth > 32 && V[32] >= 0) ? 1 : 0);
+    if (nv > kMaxSteps) return -1;
+    for (int i = lane; i < kMaxSteps * kMaxDeg; i += 32) (&W.legedge[0][0])[i] = -1;
+    if (lane < kMaxSteps) { W.mask[lane] = 0; W.visited[lane] = 0; }
+    if (lane == 0) { W.fail = 0; W.nF = 0; }
+    __syncwarp();
+    if (lane < s) {
+        const int k = lane, e = E[k];
+        W.qd[k] = P.bond_dim[e] - 1;
+        for (int side = 0; side < 2; ++side) {
+            const int x = P.bond_site[2 * e + side];
+            int lo = 0, hi = nv - 1, slot = -1;
+            while (lo <= hi) { const int mid = (lo + hi) >> 1; if (V[mid] == x) { slot = mid; break; } if (V[mid] < x) lo = mid + 1; else hi = mid - 1; }
+            if (slot < 0) { W.fail = 1; continue; }
+            W.ends[k][side] = slot;
+            const int leg = P.bond_leg[2 * e + side];
+            W.legedge[slot][leg] = k;
+            atomicOr(&W.mask[slot], 1 << leg);
+        }
+    }
+    __syncwarp();
+    if (W.fail) return -1;
+    for (int t = 0; t < nv; ++t) {
+        unsigned key = 0xffffffffu;
+        if (lane < nv && !W.visited[lane]) {
+            int closing = 0, nnew = 0;
+            for (int l = 0; l < kMaxDeg; ++l) {
+                const int k = W.legedge[lane][l];
+                if (k < 0) continue;
+                const int other = W.ends[k][0] == lane ? W.ends[k][1] : W.ends[k][0];
+                if (W.visited[other]) ++closing; else ++nnew;
+            }
+            const int f = W.nF - closing + nnew, wk = W.nF + nnew;
+            key = ((unsigned)f << 20) | ((unsigned)wk << 8) | (unsigned)lane;
+        }
+        key = __reduce_min_sync(0xffffffffu, key);
+        const int v = (int)(key & 0xFF);
+        if (lane == 0) {
+            W.visited[v] = 1;
+            int *st = plan + t * kStepInts;
+            int *dimsF = st + 8, *sxF = dimsF + kMaxFront, *smF = sxF + kMaxFront;
+            int *dimsC = smF + kMaxFront, *sxC = dimsC + kMaxClose, *smC = sxC + kMaxClose;
+            int mstride[kMaxDeg];
+            {
+                int mul = 1;
+                for (int l = kMaxDeg - 1; l >= 0; --l)
+                    if (W.legedge[v][l] >= 0) { mstride[l] = mul; mul *= W.qd[W.legedge[v][l]]; }
+            }
+            int xstride[kMaxFront];
+            {
+                int mul = 1;
+                for (int i = W.nF - 1; i >= 0; --i) { xstride[i] = mul; mul *= W.qd[W.F[i]]; }
+            }
+            int F2[kMaxFront], n2 = 0, nC = 0;
+            for (int i = 0; i < W.nF && !W.fail; ++i) {
+                const int k = W.F[i];
+                int leg = -1;
+                for (int l = 0; l < kMaxDeg; ++l) if (W.legedge[v][l] == k) leg = l;
+                if (leg >= 0) {
+                    dimsC[nC] = W.qd[k]; sxC[nC] = xstride[i]; smC[nC] = mstride[leg]; ++nC;
+                } else if (n2 >= kMaxFront) {
+                    W.fail = 1;
+                } else {
+                    F2[n2] = k; dimsF[n2] = W.qd[k]; sxF[n2] = xstride[i]; smF[n2] = 0; ++n2;
+                }
+            }
+            for (int l = 0; l < kMaxDeg && !W.fail; ++l) {
+                const int k = W.legedge[v][l];
+                if (k < 0) continue;
+                const int other = W.ends[k][0] == v ? W.ends[k][1] : W.ends[k][0];
+                if (W.visited[other] && other != v) continue;   // already closed above
+                if (n2 >= kMaxFront) { W.fail = 1; break; }
+                F2[n2] = k; dimsF[n2] = W.qd[k]; sxF[n2] = 0; smF[n2] = mstride[l]; ++n2;
+            }
+            if (!W.fail) {
+                int outsz = 1, closz = 1;
+                for (int i = 0; i < n2; ++i) outsz *= dimsF[i];
+                for (int i = 0; i < nC; ++i) closz *= dimsC[i];
+                int *invF = smC + kMaxClose, *invC = invF + kMaxFront;
+                for (int i = 0; i < n2; ++i) invF[i] = __float_as_int(1.0f / (float)dimsF[i]);
+                for (int i = 0; i < nC; ++i) invC[i] = __float_as_int(1.0f / (float)dimsC[i]);
+                if (outsz > maxT) W.fail = 1;
+                st[0] = V[v];
+                st[1] = W.mask[v];
+                st[2] = n2; st[3] = nC; st[4] = outsz; st[5] = closz;
+                st[6] = v;
+                sites_out[t] = v;
+                for (int i = 0; i < n2; ++i) W.F[i] = F2[i];
+                W.nF = n2;
+            }
+        }
+        __syncwarp();
+        if (W.fail) return -1;
+    }
+    return nv;
+}
+
 template <typename T, typename L, int R>
 __global__ void __launch_bounds__(kCtWarps * 32) contract_general_kernel(ContractParams P)
 {
@@ -526,6 +645,9 @@ namespace {
 
 constexpr int kPlanInts = kMaxSteps * kStepInts;
 constexpr int kClassMin = 8;           // smallest running-tensor class of the shaped contraction
+// shared ints per warp of the plan kernel: plan, sites, spare, then a PlanWork
+// (declared below; its size is checked there)
+constexpr int kPlanWarpInts = kMaxSteps * kStepInts + kMaxSteps + 4 + 384;
 
 // Local structure of a cluster, independent of where it sits: site slots
 // (rank in the sorted vertex list), the leg of each bond end and each bond's
@@ -591,18 +713,18 @@ __global__ void shape_plan_kernel(ContractParams P, const int32_t *rep, int n_sh
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    int *plan = (int *)smem_raw + wib * (kMaxSteps * kStepInts + kMaxSteps + 4);
+    int *plan = (int *)smem_raw + wib * kPlanWarpInts;
     int *sites = plan + kMaxSteps * kStepInts;
+    PlanWork &W = *reinterpret_cast<PlanWork *>(sites + kMaxSteps + 4);
     for (int sh = blockIdx.x * kCtWarps + wib; sh < n_shapes; sh += gridDim.x * kCtWarps) {
+        const int n = build_plan_warp(P, rep[sh], plan, sites, kWarpTensorMax, W, lane);
         if (lane == 0) {
-            const int n = build_plan(P, rep[sh], plan, sites, kWarpTensorMax);
             steps[sh] = n;
             int fma = 0, mo = 1;
             for (int t = 0; t < n; ++t) { fma += plan[t * kStepInts + 4] * plan[t * kStepInts + 5]; mo = max(mo, plan[t * kStepInts + 4]); }
             stats[4 * sh] = n; stats[4 * sh + 1] = fma; stats[4 * sh + 2] = mo; stats[4 * sh + 3] = 0;
         }
         __syncwarp();
-        const int n = steps[sh];
         for (int i = lane; i < (n > 0 ? n : 0) * kStepInts; i += 32) plans[(int64_t)sh * kPlanInts + i] = plan[i];
         __syncwarp();
     }
@@ -925,7 +1047,7 @@ pne_status shapes_finish(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, Shape
         if ((e = dev_alloc(ctx, rec.plans, (size_t)ns * kPlanInts * 4, s)) ||
             (e = dev_alloc(ctx, rec.plan_steps, (size_t)ns * 4, s)) || (e = dev_alloc(ctx, dstats, (size_t)ns * 16, s)))
             return e;
-        const size_t smem = (size_t)kCtWarps * (kMaxSteps * kStepInts + kMaxSteps + 4) * 4;
+        const size_t smem = (size_t)kCtWarps * kPlanWarpInts * 4;
         shape_plan_kernel<<<grid_for(ns, kCtWarps, ctx->n_sm, 16), kCtWarps * 32, smem, s>>>(
             cp, (const int32_t *)drep.ptr, ns, (int32_t *)rec.plans.ptr, (int32_t *)rec.plan_steps.ptr,
             (int32_t *)dstats.ptr);
