@@ -319,6 +319,7 @@ struct Arena {
     int64_t *child_off;           // [cap] child offset within the node's chunk
     int64_t *chunk_tot;           // [grid] children per chunk, then their exclusive scan
     int32_t *counts;              // [K+1][cap] clusters emitted per (size, node)
+    uint64_t *gmask, *emask;      // [cap] per node: candidates that make a child / an emitted cluster
     const int64_t *base;          // [K+1][cap] first output slot per (size, node)
     SearchCtl *ctl;
 };
@@ -433,15 +434,19 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
     __shared__ int64_t wsum[kExpandWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const bool growing = (pass == kCount || pass == kChildren);
     Node &nd = sh_node[w];
     int32_t *UA = sh_a[w], *UB = sh_b[w], *last = sh_last[w], *stage = sh_stage[w];
     const int64_t chunk = (r1 - r0 + gridDim.x - 1) / gridDim.x;
     const int64_t c0 = r0 + (int64_t)blockIdx.x * chunk;
     const int64_t c1 = c0 + chunk < r1 ? c0 + chunk : r1;
     for (int64_t u = c0 + w; u < c1; u += kExpandWarps) {
-        // L2 loads: in the cooperative kernel these nodes were written by other
-        // blocks earlier in the same launch
+        // the writing passes replay the counting pass's decisions: nodes that
+        // make nothing are skipped, and only the lanes with a set bit work
+        uint64_t want = ~0ull;
+        if (pass == kChildren) want = __ldcg(reinterpret_cast<const unsigned long long *>(A.gmask + u));
+        else if (pass == kEmit) want = __ldcg(reinterpret_cast<const unsigned long long *>(A.emask + u));
+        if (want == 0) continue;
+        // L2 loads: these nodes were written by other blocks
         const int32_t *src = reinterpret_cast<const int32_t *>(A.nodes + u);
         for (int q = lane; q < kNodeWords; q += 32) reinterpret_cast<int32_t *>(&nd)[q] = __ldcg(src + q);
         __syncwarp();
@@ -451,7 +456,7 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
             UA[q] = g.bond_site[2 * e]; UB[q] = g.bond_site[2 * e + 1];
         }
         __syncwarp();
-        if (growing) {
+        if (pass == kCount) {
             // the last candidate touching each vertex of S (-1: none): a
             // degree-one vertex of S + U[i] stays repairable iff it is > i
             for (int j = 0; j < vn; ++j) {
@@ -469,24 +474,36 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
         int n_child = 0, n_emit = 0;
         const int64_t cbase = (pass == kChildren) ? next + cbase_chunk + __ldcg(A.child_off + u) : 0;
         const int64_t ebase = (pass == kEmit) ? A.base[(int64_t)(t + 1) * A.cap + u] : 0;
+        uint64_t gmask = 0, emask = 0;
         for (int i0 = 0; i0 < nU; i0 += 32) {
             const int i = i0 + lane;
             bool emit = false, grow = false;
             VSet<kNodeV> V;
             int32_t NU[kMaxNew], NA[kMaxNew], NB[kMaxNew];
             int nn = 0;
-            if (i < nU) {
+            const bool mine = i < nU && ((want >> i) & 1);
+            if (mine) {
                 load_vset(V, nd);
                 const int e = nd.U[i], a0 = UA[i], a1 = UB[i];
                 const int b = !V.has(a0) ? a0 : (!V.has(a1) ? a1 : -1);
                 V.inc(a0); V.inc(a1);
-                emit = valid_set(mode, V.dang);
-                if (growing && may_grow(mode, t + 1, K, V.dang)) {
+                if (pass == kChildren) {
+                    // decided by the counting pass; only the new candidates are rebuilt
+                    grow = true;
                     if (b >= 0) nn = append_new(g, b, e, anchor, V, NU, NA, NB, 0, kMaxNew, &A.ctl->cand_overflow);
-                    grow = mode == PNE_MODE_ALL || repairable_after(V, vn, i, last, b, nn, UA, UB, nU);
+                } else if (pass == kEmit) {
+                    emit = true;
+                } else {
+                    emit = valid_set(mode, V.dang);
+                    if (pass == kCount && may_grow(mode, t + 1, K, V.dang)) {
+                        if (b >= 0) nn = append_new(g, b, e, anchor, V, NU, NA, NB, 0, kMaxNew, &A.ctl->cand_overflow);
+                        grow = mode == PNE_MODE_ALL || repairable_after(V, vn, i, last, b, nn, UA, UB, nU);
+                    }
                 }
             }
             const unsigned gm = __ballot_sync(0xffffffffu, grow), em = __ballot_sync(0xffffffffu, emit);
+            gmask |= (uint64_t)gm << i0;
+            emask |= (uint64_t)em << i0;
             if (pass == kChildren && gm) {
                 // each growing lane stages what its child adds; then the warp
                 // writes the children one after another, 32 words per store
@@ -539,7 +556,8 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
         }
         if ((pass == kCount || pass == kEmitCount) && lane == 0) {
             A.counts[(int64_t)(t + 1) * A.cap + u] = n_emit;
-            if (pass == kCount) A.child_cnt[u] = n_child;
+            A.emask[u] = emask;
+            if (pass == kCount) { A.child_cnt[u] = n_child; A.gmask[u] = gmask; }
         }
         __syncwarp();
     }
@@ -940,9 +958,9 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     int dfs_level = 0;
     pne_status st;
     for (;;) {
-        // arena: nodes, then [lv | ctl | child_cnt | child_off | chunk_tot], then counts
+        // arena: nodes, then [lv, ctl | child_off | chunk_tot | gmask | emask | child_cnt], then counts
         if ((st = dev_alloc(ctx, nodes, sizeof(Node) * (size_t)cap, s))) return st;
-        const size_t tab_bytes = sizeof(Readback) + (size_t)cap * 4 + (size_t)cap * 8 + (size_t)G * 8 + 64;
+        const size_t tab_bytes = sizeof(Readback) + (size_t)cap * 4 + (size_t)cap * 24 + (size_t)G * 8 + 64;
         if ((st = dev_alloc(ctx, tables, tab_bytes, s))) return st;
         if ((st = dev_alloc(ctx, counts, (size_t)(K + 1) * cap * 4, s))) return st;
         char *tb = (char *)tables.ptr;
@@ -952,7 +970,9 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         A.ctl = (SearchCtl *)(tb + offsetof(Readback, ctl));
         A.child_off = (int64_t *)(tb + sizeof(Readback));
         A.chunk_tot = A.child_off + cap;
-        A.child_cnt = (int32_t *)(A.chunk_tot + G);
+        A.gmask = reinterpret_cast<uint64_t *>(A.chunk_tot + G);
+        A.emask = A.gmask + cap;
+        A.child_cnt = (int32_t *)(A.emask + cap);
         A.counts = (int32_t *)counts.ptr;
         A.base = nullptr;
         PNE_CUDA_TRY(ctx, cudaMemsetAsync(counts.ptr, 0, (size_t)(K + 1) * cap * 4, s));
