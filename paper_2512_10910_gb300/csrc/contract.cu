@@ -645,6 +645,7 @@ namespace {
 
 constexpr int kPlanInts = kMaxSteps * kStepInts;
 constexpr int kClassMin = 8;           // smallest running-tensor class of the shaped contraction
+constexpr int kWarpClassX = 32;        // classes from this running-tensor size on: one warp per cluster
 // shared ints per warp of the plan kernel: plan, sites, spare, then a PlanWork
 // (declared below; its size is checked there)
 constexpr int kPlanWarpInts = kMaxSteps * kStepInts + kMaxSteps + 4 + 384;
@@ -898,6 +899,91 @@ pne_status side_streams(pne_ctx *ctx)
     return PNE_OK;
 }
 
+// Clusters perm[i0, i1) of every tensor set, one warp per (cluster, set): the
+// running tensor sits in the warp's shared memory once (not once per lane) and
+// the lanes split each step's output entries; every output is the same chain
+// of multiply-adds in the same order as in shaped_cluster, and the rescaling
+// decision is the same, so the values agree bit for bit with the lane-per-
+// cluster form.  For the classes with large running tensors.
+template <typename T, typename L, int R>
+__global__ void __launch_bounds__(256) contract_warp_kernel(ContractParams P, const int32_t *perm, const int32_t *shape_of,
+                                                            const int32_t *plans, const int32_t *plan_steps,
+                                                            const int32_t *ops, const int64_t *op_off,
+                                                            const int32_t *step_off, const int32_t *step_site, int sstride,
+                                                            int xmax, int64_t i0, int64_t i1)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    T *X0 = (T *)smem_raw + (int64_t)wib * 2 * xmax;
+    T *X1 = X0 + xmax;
+    const int64_t nc = i1 - i0;
+    const int64_t items = nc * P.n_members;
+    for (int64_t it = (int64_t)blockIdx.x * wpb + wib; it < items; it += (int64_t)gridDim.x * wpb) {
+        const int b = (int)(it / nc);
+        const int64_t c = perm[i0 + it % nc];
+        const int sh = shape_of[c];
+        const int *plan = plans + (int64_t)sh * kPlanInts;
+        const int nsteps = plan_steps[sh];
+        const int32_t *op = ops + op_off[sh];
+        const int32_t *soff = step_off + c * sstride, *ssite = step_site + c * sstride;
+        T *X = X0, *Y = X1;
+        if (lane == 0) X[0] = (T)1;
+        __syncwarp();
+        int expo = 0, nz = 0;
+        double zs = 1.0;
+        for (int t = 0; t < nsteps; ++t) {
+            const int *st = plan + t * kStepInts;
+            const int outsz = st[4], closz = st[5];
+            const int64_t mbase = (int64_t)b * P.stride + __ldg(soff + t);
+            int mxb = 0;
+            for (int o = lane; o < outsz; o += 32) {
+                const int32_t *oo = op + (int64_t)o * closz;
+                T acc = (T)0;
+                int cc = 0;
+                for (; cc + 4 <= closz; cc += 4) {
+                    int32_t pk[4];
+                    T xv[4], mv[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) pk[k] = __ldg(oo + cc + k);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        xv[k] = rnd<R>(X[pk[k] >> 16]);
+                        mv[k] = (T)L::get(P.M, mbase + (pk[k] & 0xffff));
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc = fma(xv[k], mv[k], acc);
+                }
+                for (; cc < closz; ++cc) {
+                    const int32_t pk = __ldg(oo + cc);
+                    acc = fma(rnd<R>(X[pk >> 16]), (T)L::get(P.M, mbase + (pk & 0xffff)), acc);
+                }
+                Y[o] = acc;
+                mxb = max(mxb, Expo<T>::biased(acc));
+            }
+            op += (int64_t)outsz * closz;
+            mxb = __reduce_max_sync(0xffffffffu, mxb);
+            __syncwarp();
+            if (mxb > 0) {
+                const int e = mxb - (Expo<T>::kBias - 1);
+                if (e > Expo<T>::kWindow || e < -Expo<T>::kWindow) {
+                    const T sc = (e < Expo<T>::kBias) ? Expo<T>::inv_pow2(e) : (T)ldexp(1.0, -e);
+                    for (int o = lane; o < outsz; o += 32) Y[o] *= sc;
+                    expo += e;
+                    __syncwarp();
+                }
+            }
+            T *tmp = X; X = Y; Y = tmp;
+            const int site = __ldg(ssite + t);
+            if (P.zero[(int64_t)b * P.n_sites + site]) { ++nz; zs *= P.scale[(int64_t)b * P.n_sites + site]; }
+        }
+        if (lane == 0) {
+            P.w[(int64_t)b * P.n_clusters + c] = ldexp((double)X[0], expo) * zs;
+            P.nzc[(int64_t)b * P.n_clusters + c] = nz;
+        }
+        __syncwarp();
+    }
+}
+
 template <typename T, typename L, int R>
 pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &rec, cudaStream_t s)
 {
@@ -936,6 +1022,23 @@ pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &
         if (fork && j > 0) {
             ls = ctx->side[(j - 1) % pne_ctx::kSideStreams];
             PNE_CUDA_TRY(ctx, cudaStreamWaitEvent(ls, ctx->side_ev[0], 0));
+        }
+        if (xmax >= kWarpClassX) {
+            // large running tensors: one warp per cluster
+            auto wk = contract_warp_kernel<T, L, R>;
+            const int wpb2 = 8;
+            const size_t smem2 = (size_t)wpb2 * 2 * xmax * sizeof(T);
+            if (smem2 > 48 * 1024) cudaFuncSetAttribute(wk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+            const int64_t items2 = (i1 - i0) * cp.n_members;
+            int64_t g2 = (items2 + wpb2 - 1) / wpb2;
+            if (g2 > (int64_t)ctx->n_sm * 16) g2 = (int64_t)ctx->n_sm * 16;
+            wk<<<(int)g2, wpb2 * 32, smem2, ls>>>(cp, (const int32_t *)rec.perm.ptr, (const int32_t *)rec.shape_of.ptr,
+                                                 (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr,
+                                                 (const int32_t *)rec.ops.ptr, (const int64_t *)rec.op_off.ptr,
+                                                 (const int32_t *)rec.step_off.ptr, (const int32_t *)rec.step_site.ptr,
+                                                 rec.step_stride, xmax, i0, i1);
+            PNE_CUDA_TRY(ctx, cudaGetLastError());
+            continue;
         }
         kern<<<(int)g, wpb * 32, smem, ls>>>(cp, (const int32_t *)rec.perm.ptr, (const int32_t *)rec.shape_of.ptr,
                                              (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr,
