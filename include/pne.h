@@ -324,7 +324,9 @@ pne_status pne_bp_messages_noalloc(const pne_network *net, double tol, int32_t m
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around
  * every kernel the library launches (no effect on results).  enable != 0
- * turns it on and clears the record; 0 turns it off. */
+ * turns it on and clears the record; 0 turns it off.  enable == 2 also keeps
+ * a timeline (pne_ctx_trace_read): the call then synchronises the device
+ * once to fix the time origin. */
 pne_status pne_ctx_profile(pne_ctx *ctx, int enable);
 
 typedef struct {
@@ -336,6 +338,22 @@ typedef struct {
 /* Waits for the recorded events, then writes up to max entries (sorted by
  * total time, largest first); returns the number of kernel families. */
 int pne_ctx_profile_read(pne_ctx *ctx, pne_profile_entry *out, int max);
+
+typedef struct {
+    char name[32];        /* kernel family, or a host stretch of library code  */
+    int32_t kind;         /* 0: kernel (event-timed on its stream), 1: host    */
+    int32_t stream;       /* kernels: streams numbered by first appearance; -1 */
+    double t0_ms, t1_ms;  /* since the origin set by pne_ctx_profile(ctx, 2)   */
+} pne_trace_entry;
+
+/* The timeline recorded since pne_ctx_profile(ctx, 2): waits for the recorded
+ * events, writes up to max entries sorted by start time and returns how many
+ * there are (at most 2^18 of each kind are kept).  Kernel times come from
+ * events, host times from the steady clock; *host_origin_ms (may be NULL)
+ * receives the steady-clock reading, in ms, taken when the origin event
+ * completed, so that a caller's own monotonic timestamps can be placed on the
+ * same axis.  The two clocks agree to within the event-completion latency. */
+int pne_ctx_trace_read(pne_ctx *ctx, pne_trace_entry *out, int max, double *host_origin_ms);
 
 /* Multiply-adds of every cluster's contraction plan, summed over clusters (one
  * tensor set): the algorithmic work of pne_contract_terms per tensor set.

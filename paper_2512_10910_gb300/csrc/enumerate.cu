@@ -20,7 +20,12 @@
 // whose level bounds stay on the device, so the levels need no host round
 // trip; each node of the last prefix level is then searched depth-first by one
 // thread, unless the prefix already reaches size K - 1 and one more
-// warp-parallel step ends it.  Every unit first counts what it emits per
+// warp-parallel step ends it.  In LOOP mode the prefix stops at size K - 2:
+// the bond that completes a cluster of size K joins two vertices the set
+// already has, so a node of size K - 2 finds both remaining sizes in one
+// warp-parallel step (each lane's child, then the child's closing bonds among
+// the node's later candidates) and the far more numerous sets of size K - 1
+// that cannot be closed are never stored.  Every unit first counts what it emits per
 // cluster size; an exclusive scan over (size, unit) gives each unit its output
 // slots, and a second pass writes.  The output is grouped by size and
 // deterministic.
@@ -380,7 +385,10 @@ __global__ void roots_kernel(GeomView g, int n_closed, int mode, Arena A, Emit o
 //   kEmitCount: emissions only (the last level)
 //   kChildren:  write the children of level lo == hi, unless the search stopped
 //   kEmit:      write the emitted clusters of levels lo..hi
-enum ExpandPass { kCount = 0, kChildren = 1, kEmit = 2, kEmitCount = 3 };
+//   kPairCount: the closing level of LOOP mode (nodes of size K - 2): sizes
+//               K - 1 and K counted together, no nodes of size K - 1 made
+//               (see pair_node)
+enum ExpandPass { kCount = 0, kChildren = 1, kEmit = 2, kEmitCount = 3, kPairCount = 4 };
 constexpr int kExpandWarps = 4;
 constexpr int kMaxNew = kNodeU / (kPrefixMax + 1);   // new candidates per step (site degree - 1)
 constexpr int kNodeWords = (int)(sizeof(Node) / 4);
@@ -421,15 +429,103 @@ __device__ bool repairable_after(const VSet<NV> &V, int old_n, int i, const int3
     return true;
 }
 
+// A node of size K - 2 in LOOP mode, both remaining levels at once.  Its child
+// S + U[i] (size K - 1) is a cluster iff it has no degree-one vertex; a
+// cluster of size K below that child is S + U[i] + U[j] with a bond U[j] of
+// the child's candidate list that removes every degree-one vertex without
+// adding one: both ends of U[j] already belong to the child, so U[j] is not
+// one of the child's new candidates (those lead off the child's vertex set)
+// and is a later candidate U[j], j > i, of this node.  It closes the child
+// iff its ends include every degree-one vertex of the child (there are at
+// most two).  The sizes K - 1 and K come out in the order of the level-by-
+// level search: child by child, and per child in candidate order.
+//   counting (kPairCount): per node the size K - 1 and size K counts, the
+//     lanes with an emitted child (emask) and with a closing bond (gmask)
+//   writing (kEmit): both sizes, from the slots of the (size, node) scan
+// `out_v` holds, per candidate, its end outside the node's vertex set (-1:
+// both ends inside); `want` is the lane mask of the writing pass.
+__device__ void pair_node(const Arena &A, const Node &nd, int64_t u, const int32_t *UA, const int32_t *UB,
+                          const int32_t *out_v, int pass, uint64_t want, const Emit &out)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nU = nd.nU, t = nd.t;
+    int n_emit = 0, n_pair = 0;
+    uint64_t emask = 0, pmask = 0;
+    const int64_t ebase = (pass == kEmit) ? A.base[(int64_t)(t + 1) * A.cap + u] : 0;
+    const int64_t pbase = (pass == kEmit) ? A.base[(int64_t)(t + 2) * A.cap + u] : 0;
+    for (int i0 = 0; i0 < nU; i0 += 32) {
+        const int i = i0 + lane;
+        VSet<kNodeV> V;
+        bool emit = false;
+        int np = 0, d0 = -1, d1 = -1, b = -1;
+        const bool mine = i < nU && ((want >> i) & 1);
+        if (mine) {
+            load_vset(V, nd);
+            const int a0 = UA[i], a1 = UB[i];
+            b = !V.has(a0) ? a0 : (!V.has(a1) ? a1 : -1);
+            V.inc(a0); V.inc(a1);
+            emit = V.dang == 0;
+            if (V.dang <= 2) {
+#pragma unroll
+                for (int q = 0; q < kNodeV; ++q)
+                    if (q < V.n && V.d[q] == 1) { if (d0 < 0) d0 = V.v[q]; else d1 = V.v[q]; }
+                for (int j = i + 1; j < nU; ++j) {
+                    const int oj = out_v[j];
+                    if (oj != -1 && oj != b) continue;
+                    const int x = UA[j], y = UB[j];
+                    if ((d0 >= 0 && d0 != x && d0 != y) || (d1 >= 0 && d1 != x && d1 != y)) continue;
+                    ++np;
+                }
+            }
+        }
+        const unsigned em = __ballot_sync(0xffffffffu, emit), pm = __ballot_sync(0xffffffffu, np > 0);
+        emask |= (uint64_t)em << i0;
+        pmask |= (uint64_t)pm << i0;
+        int incl = np;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int z = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += z;
+        }
+        if (pass == kEmit && mine) {
+            int32_t S[kPrefixMax + 2];
+            for (int q = 0; q < t; ++q) S[q] = nd.S[q];
+            S[t] = nd.U[i];
+            if (emit) write_cluster(out, ebase + n_emit + __popc(em & lt), S, t + 1, V);
+            int64_t slot = pbase + n_pair + (incl - np);
+            if (np > 0)
+                for (int j = i + 1; j < nU; ++j) {
+                    const int oj = out_v[j];
+                    if (oj != -1 && oj != b) continue;
+                    const int x = UA[j], y = UB[j];
+                    if ((d0 >= 0 && d0 != x && d0 != y) || (d1 >= 0 && d1 != x && d1 != y)) continue;
+                    S[t + 1] = nd.U[j];
+                    write_cluster(out, slot++, S, t + 2, V);
+                }
+        }
+        n_emit += __popc(em);
+        n_pair += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (pass == kPairCount && lane == 0) {
+        A.counts[(int64_t)(t + 1) * A.cap + u] = n_emit;
+        A.counts[(int64_t)(t + 2) * A.cap + u] = n_pair;
+        A.emask[u] = emask;
+        A.gmask[u] = pmask;
+    }
+}
+
 // The block's chunk of the node range [r0, r1).  kChildren writes the
 // children from arena slot next + cbase_chunk on (cbase_chunk: the children of
 // the chunks before this one).
+// With `fuse`, nodes of size K - 2 (LOOP mode) are closing nodes (pair_node).
 __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int64_t r1, int K, int mode, int pass,
-                             const Emit &out, int64_t next, int64_t cbase_chunk)
+                             const Emit &out, int64_t next, int64_t cbase_chunk, int fuse)
 {
     __shared__ Node sh_node[kExpandWarps];
     __shared__ int32_t sh_a[kExpandWarps][kNodeU], sh_b[kExpandWarps][kNodeU];
     __shared__ int32_t sh_last[kExpandWarps][kNodeV];
+    __shared__ int32_t sh_out[kExpandWarps][kNodeU];
     __shared__ int32_t sh_stage[kExpandWarps][32 * kStageWords];
     __shared__ int64_t wsum[kExpandWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -445,6 +541,8 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
         uint64_t want = ~0ull;
         if (pass == kChildren) want = __ldcg(reinterpret_cast<const unsigned long long *>(A.gmask + u));
         else if (pass == kEmit) want = __ldcg(reinterpret_cast<const unsigned long long *>(A.emask + u));
+        if (pass == kEmit && fuse && __ldcg(&A.nodes[u].t) == K - 2)   // a closing node: lanes with a closing bond too
+            want |= __ldcg(reinterpret_cast<const unsigned long long *>(A.gmask + u));
         if (want == 0) continue;
         // L2 loads: these nodes were written by other blocks
         const int32_t *src = reinterpret_cast<const int32_t *>(A.nodes + u);
@@ -456,6 +554,20 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
             UA[q] = g.bond_site[2 * e]; UB[q] = g.bond_site[2 * e + 1];
         }
         __syncwarp();
+        if (fuse && t == K - 2) {
+            // a closing node: each candidate's end outside the vertex set of S
+            int32_t *ov = sh_out[w];
+            for (int q = lane; q < nU; q += 32) {
+                const int a = UA[q], b = UB[q];
+                bool ia = false, ib = false;
+                for (int k = 0; k < vn; ++k) { ia |= nd.vv[k] == a; ib |= nd.vv[k] == b; }
+                ov[q] = !ia ? a : (!ib ? b : -1);
+            }
+            __syncwarp();
+            pair_node(A, nd, u, UA, UB, ov, pass, want, out);
+            __syncwarp();
+            continue;
+        }
         if (pass == kCount) {
             // the last candidate touching each vertex of S (-1: none): a
             // degree-one vertex of S + U[i] stays repairable iff it is > i
@@ -570,11 +682,11 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
     __syncthreads();                                   // the shared node buffers are reused by the caller
 }
 
-// kEmitCount / kEmit over levels lo..hi
+// kCount / kEmitCount / kPairCount of level lo == hi, or kEmit over levels lo..hi
 __global__ void __launch_bounds__(32 * kExpandWarps)
-expand_kernel(GeomView g, Arena A, int lo_level, int hi_level, int K, int mode, int pass, Emit out)
+expand_kernel(GeomView g, Arena A, int lo_level, int hi_level, int K, int mode, int pass, Emit out, int fuse)
 {
-    expand_chunk(g, A, A.lv[lo_level - 1], A.lv[hi_level], K, mode, pass, out, 0, 0);
+    expand_chunk(g, A, A.lv[lo_level - 1], A.lv[hi_level], K, mode, pass, out, 0, 0, fuse);
 }
 
 // One level step is two ordinary launches (no grid barrier, so the search can
@@ -611,7 +723,7 @@ __global__ void __launch_bounds__(32 * kExpandWarps) expand_children_kernel(Geom
         if (!fits) { A.ctl->stop = d; A.ctl->need = hi + total; }
     }
     if (!fits) return;
-    expand_chunk(g, A, lo, hi, K, mode, kChildren, none, hi, before);
+    expand_chunk(g, A, lo, hi, K, mode, kChildren, none, hi, before, 0);
 }
 
 // ---------------------------------------------------------------- depth-first tasks
@@ -920,10 +1032,12 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     }
     if ((kPrefixMax + 1) * (maxdeg - 1) > kNodeU) { set_error(ctx, PNE_EINVAL, "site degree too large"); return PNE_EINVAL; }
     GeomView gv{g.d_bond_site, g.d_site_ptr, g.d_site_bonds};
-    // prefix levels 1..D are expanded breadth-first; the last one either only
-    // emits (D == K - 1) or is searched depth-first (K - 1 > kPrefixMax)
-    const int D = (K <= 1) ? 1 : std::min(kPrefixMax, K - 1);
-    const int final_kind = (K <= 1) ? 0 : (D == K - 1 ? 1 : 2);
+    // prefix levels 1..D are expanded breadth-first; the last one closes both
+    // remaining sizes (LOOP mode, D == K - 2), only emits (D == K - 1) or is
+    // searched depth-first (K - 1 > kPrefixMax)
+    const bool fuse = mode == PNE_MODE_LOOP && K >= 3 && K - 2 <= kPrefixMax;
+    const int D = fuse ? K - 2 : ((K <= 1) ? 1 : std::min(kPrefixMax, K - 1));
+    const int final_kind = fuse ? 3 : ((K <= 1) ? 0 : (D == K - 1 ? 1 : 2));
     const bool small = (K <= 12 && umax_need <= 64);
     // chunks of the blocked passes: one wave of resident blocks
     // chunks of the blocked passes: one wave of resident blocks (the occupancy
@@ -983,12 +1097,13 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         }
         for (int d = 1; d < D; ++d) {
             ProfScope ps__(ctx, s, "enum_expand");
-            expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, d, K, mode, kCount, none);
+            expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, d, K, mode, kCount, none, 0);
             expand_children_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, K, mode);
         }
-        if (final_kind == 1) {
+        if (final_kind == 1 || final_kind == 3) {
             ProfScope ps__(ctx, s, "enum_expand");
-            expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, D, D, K, mode, kEmitCount, none);
+            expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, D, D, K, mode, final_kind == 3 ? kPairCount : kEmitCount,
+                                                          none, final_kind == 3);
         } else if (final_kind == 2) {
             dfs(A, D, 0, none);
         }
@@ -1035,14 +1150,15 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     A.base = (const int64_t *)base.ptr;
     // write passes: the anchors (ALL mode), the breadth-first emissions of
     // levels 1..last_bfs, and the depth-first subtrees
-    const int last_bfs = dfs_level ? dfs_level - 1 : (final_kind == 1 ? D : 0);
+    const int last_bfs = dfs_level ? dfs_level - 1 : ((final_kind == 1 || final_kind == 3) ? D : 0);
     if (mode == PNE_MODE_ALL) {
         ProfScope ps__(ctx, s, "enum_roots");
         roots_kernel<<<grid1(Mc, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, mode, A, out, 1);
     }
     if (last_bfs >= 1) {
         ProfScope ps__(ctx, s, "enum_expand");
-        expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, 1, last_bfs, K, mode, kEmit, out);
+        expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, 1, last_bfs, K, mode, kEmit, out,
+                                                      final_kind == 3 && dfs_level == 0);
     }
     if (dfs_level) dfs(A, dfs_level, 1, out);
     PNE_CUDA_TRY(ctx, cudaGetLastError());

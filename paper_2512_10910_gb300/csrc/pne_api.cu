@@ -155,7 +155,7 @@ ProfScope::~ProfScope()
     if (!a) return;
     cudaEventRecord(b, s);
     std::lock_guard<std::mutex> lk(ctx->prof.mu);
-    ctx->prof.pending.push_back({name, a, b});
+    ctx->prof.pending.push_back({name, a, b, s});
 }
 
 HostScope::HostScope(pne_ctx *c, const char *n) : ctx(c), name(n)
@@ -172,6 +172,8 @@ HostScope::~HostScope()
     auto &e = ctx->prof.acc[std::string("host:") + name];
     e.first += 1;
     e.second += t1 - t0;
+    if (ctx->prof.trace && ctx->prof.host_trace.size() < kTraceMax)
+        ctx->prof.host_trace.push_back({name, t0 - ctx->prof.host_base, t1 - ctx->prof.host_base});
 }
 
 EnumRecord::~EnumRecord()
@@ -945,14 +947,59 @@ pne_status pne_partition_update(pne_ctx *ctx, pne_partition *p, const double *da
     return PNE_OK;
 }
 
+namespace {
+
+double host_ms_now()
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Waits for the pending event pairs and folds them into the sums (and, when
+// tracing, into the timeline).  Caller holds prof.mu.
+void prof_drain(pne_ctx *ctx)
+{
+    auto &P = ctx->prof;
+    for (auto &r : P.pending) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto &e = P.acc[r.name];
+        e.first += 1;
+        e.second += ms;
+        if (P.trace && P.base && P.gpu_trace.size() < kTraceMax) {
+            float t0 = 0.f;
+            cudaEventElapsedTime(&t0, P.base, r.a);
+            P.gpu_trace.push_back({r.name, r.s, (double)t0, (double)t0 + ms});
+        }
+        P.pool.push_back(r.a);
+        P.pool.push_back(r.b);
+    }
+    P.pending.clear();
+}
+
+}  // namespace
+
 pne_status pne_ctx_profile(pne_ctx *ctx, int enable)
 {
     if (!ctx) return PNE_EINVAL;
     std::lock_guard<std::mutex> lk(ctx->prof.mu);
-    for (auto &r : ctx->prof.pending) { cudaEventSynchronize(r.b); ctx->prof.pool.push_back(r.a); ctx->prof.pool.push_back(r.b); }
-    ctx->prof.pending.clear();
-    ctx->prof.acc.clear();
-    ctx->prof.on = enable != 0;
+    auto &P = ctx->prof;
+    for (auto &r : P.pending) { cudaEventSynchronize(r.b); P.pool.push_back(r.a); P.pool.push_back(r.b); }
+    P.pending.clear();
+    P.acc.clear();
+    P.gpu_trace.clear();
+    P.host_trace.clear();
+    P.on = enable != 0;
+    P.trace = enable == 2;
+    if (P.trace) {
+        // the origin: a device-wide idle point, then an event and the host
+        // clock read as soon as that event has completed
+        if (!P.base) PNE_CUDA_TRY(ctx, cudaEventCreate(&P.base));
+        PNE_CUDA_TRY(ctx, cudaDeviceSynchronize());
+        PNE_CUDA_TRY(ctx, cudaEventRecord(P.base, 0));
+        PNE_CUDA_TRY(ctx, cudaEventSynchronize(P.base));
+        P.host_base = host_ms_now();
+    }
     return PNE_OK;
 }
 
@@ -960,17 +1007,7 @@ int pne_ctx_profile_read(pne_ctx *ctx, pne_profile_entry *out, int max)
 {
     if (!ctx) return 0;
     std::lock_guard<std::mutex> lk(ctx->prof.mu);
-    for (auto &r : ctx->prof.pending) {
-        cudaEventSynchronize(r.b);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, r.a, r.b);
-        auto &e = ctx->prof.acc[r.name];
-        e.first += 1;
-        e.second += ms;
-        ctx->prof.pool.push_back(r.a);
-        ctx->prof.pool.push_back(r.b);
-    }
-    ctx->prof.pending.clear();
+    prof_drain(ctx);
     std::vector<std::pair<std::string, std::pair<int64_t, double>>> v(ctx->prof.acc.begin(), ctx->prof.acc.end());
     std::sort(v.begin(), v.end(), [](const auto &x, const auto &y) { return x.second.second > y.second.second; });
     const int n = (int)v.size();
@@ -980,6 +1017,47 @@ int pne_ctx_profile_read(pne_ctx *ctx, pne_profile_entry *out, int max)
         out[i].launches = v[i].second.first;
         out[i].total_ms = v[i].second.second;
     }
+    return n;
+}
+
+int pne_ctx_trace_read(pne_ctx *ctx, pne_trace_entry *out, int max, double *host_origin_ms)
+{
+    if (!ctx) return 0;
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
+    auto &P = ctx->prof;
+    prof_drain(ctx);
+    if (host_origin_ms) *host_origin_ms = P.host_base;
+    // streams numbered in order of first appearance
+    std::vector<cudaStream_t> ids;
+    auto sid = [&](cudaStream_t st) {
+        for (size_t i = 0; i < ids.size(); ++i)
+            if (ids[i] == st) return (int)i;
+        ids.push_back(st);
+        return (int)ids.size() - 1;
+    };
+    std::vector<pne_trace_entry> v;
+    v.reserve(P.gpu_trace.size() + P.host_trace.size());
+    for (auto &r : P.gpu_trace) {
+        pne_trace_entry e{};
+        std::strncpy(e.name, r.name, sizeof e.name - 1);
+        e.kind = 0;
+        e.stream = sid(r.s);
+        e.t0_ms = r.t0;
+        e.t1_ms = r.t1;
+        v.push_back(e);
+    }
+    for (auto &r : P.host_trace) {
+        pne_trace_entry e{};
+        std::strncpy(e.name, r.name, sizeof e.name - 1);
+        e.kind = 1;
+        e.stream = -1;
+        e.t0_ms = r.t0;
+        e.t1_ms = r.t1;
+        v.push_back(e);
+    }
+    std::stable_sort(v.begin(), v.end(), [](const pne_trace_entry &x, const pne_trace_entry &y) { return x.t0_ms < y.t0_ms; });
+    const int n = (int)v.size();
+    for (int i = 0; i < n && i < max && out; ++i) out[i] = v[i];
     return n;
 }
 

@@ -74,6 +74,7 @@ pne_status upload(pne_ctx *ctx, void *dst, const void *src, size_t bytes, cudaSt
 // memory is unavailable); read after synchronising the stream of the copies.
 // Slots: 0 partition records, 1 sums, 2 vacuum records, 3 shape records.
 constexpr int kPinnedSlots = 4;
+constexpr size_t kTraceMax = 1 << 18;   // timeline records kept per trace (later ones are dropped)
 void *pinned_slot(int slot, size_t bytes);
 void dev_free(pne_ctx *ctx, DevBuf &b, cudaStream_t s);
 
@@ -109,13 +110,24 @@ namespace pne {
 struct ProfRec {
     const char *name;
     cudaEvent_t a, b;
+    cudaStream_t s;
+};
+struct HostRec {
+    const char *name;
+    double t0, t1;        // ms since the trace base
 };
 struct Profiler {
     std::mutex mu;
     bool on = false;
+    bool trace = false;             // keep every record in order (a timeline), not only the sums
+    cudaEvent_t base = nullptr;     // GPU time origin of the timeline
+    double host_base = 0.0;         // steady-clock ms at the origin
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> pool;
     std::map<std::string, std::pair<int64_t, double>> acc;
+    std::vector<HostRec> host_trace;
+    struct GpuRec { const char *name; cudaStream_t s; double t0, t1; };
+    std::vector<GpuRec> gpu_trace;
 };
 }  // namespace pne
 

@@ -22,8 +22,8 @@ __all__ = [
     "pne_ctx_create", "pne_ctx_destroy", "pne_last_error", "pne_ctx_set_allocator",
     "pne_build_partition", "pne_partition_destroy", "pne_enumerate_terms", "pne_terms_destroy",
     "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_terms_export",
-    "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak", "pne_bp_messages_noalloc",
-    "pne_partition_update", "pne_batch_create", "pne_batch_run", "pne_batch_n_results", "pne_batch_config",
+    "pne_ctx_profile", "pne_ctx_profile_read", "pne_ctx_trace_read", "pne_terms_work", "pne_measure_fma_peak",
+    "pne_bp_messages_noalloc", "pne_partition_update", "pne_batch_create", "pne_batch_run", "pne_batch_n_results", "pne_batch_config",
     "pne_batch_destroy", "BatchOpts", "pne_server_create", "pne_server_submit", "pne_server_poll",
     "pne_server_drain", "pne_server_stats", "pne_server_destroy", "ServerOpts", "RequestInfo",
     "Network", "PartitionOpts", "EnumOpts", "Result", "Context", "run", "network_struct",
@@ -107,6 +107,11 @@ class ProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("kind", ctypes.c_int32), ("stream", ctypes.c_int32),
+                ("t0_ms", ctypes.c_double), ("t1_ms", ctypes.c_double)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -182,6 +187,8 @@ def load_library():
     lib.pne_ctx_profile.restype = ctypes.c_int
     lib.pne_ctx_profile_read.argtypes = [vp, ctypes.POINTER(ProfileEntry), ctypes.c_int]
     lib.pne_ctx_profile_read.restype = ctypes.c_int
+    lib.pne_ctx_trace_read.argtypes = [vp, ctypes.POINTER(TraceEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.pne_ctx_trace_read.restype = ctypes.c_int
     lib.pne_terms_work.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.pne_terms_work.restype = ctypes.c_int
     lib.pne_measure_fma_peak.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]
@@ -196,8 +203,7 @@ def exported_symbols() -> list:
     names = ["pne_ctx_create", "pne_ctx_destroy", "pne_last_error", "pne_ctx_set_allocator",
              "pne_build_partition", "pne_partition_destroy", "pne_enumerate_terms", "pne_terms_destroy",
              "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_terms_export",
-    "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak",
-             "pne_ctx_profile", "pne_ctx_profile_read", "pne_terms_work", "pne_measure_fma_peak",
+             "pne_ctx_profile", "pne_ctx_profile_read", "pne_ctx_trace_read", "pne_terms_work", "pne_measure_fma_peak",
              "pne_bp_messages_noalloc", "pne_partition_update", "pne_batch_create", "pne_batch_run",
              "pne_batch_n_results", "pne_batch_config", "pne_batch_destroy", "pne_server_create",
              "pne_server_submit", "pne_server_poll", "pne_server_drain", "pne_server_stats", "pne_server_destroy"]
@@ -359,8 +365,9 @@ def pne_server_destroy(srv):
     load_library().pne_server_destroy(srv)
 
 
-def pne_ctx_profile(ctx, enable=True):
-    _check(load_library().pne_ctx_profile(ctx, int(bool(enable))), ctx)
+def pne_ctx_profile(ctx, enable=True, trace=False):
+    """Turn the per-kernel event timing on or off; ``trace`` also keeps a timeline."""
+    _check(load_library().pne_ctx_profile(ctx, 2 if (enable and trace) else int(bool(enable))), ctx)
 
 
 def pne_ctx_profile_read(ctx) -> dict:
@@ -369,6 +376,20 @@ def pne_ctx_profile_read(ctx) -> dict:
     buf = (ProfileEntry * 64)()
     n = lib.pne_ctx_profile_read(ctx, buf, 64)
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n, 64))}
+
+
+def pne_ctx_trace_read(ctx):
+    """(entries, host_origin_ms): the timeline since ``pne_ctx_profile(ctx, trace=True)``
+    as dicts {name, kind ('gpu'|'host'), stream, t0_ms, t1_ms}, sorted by start."""
+    lib = load_library()
+    origin = ctypes.c_double()
+    n = lib.pne_ctx_trace_read(ctx, None, 0, ctypes.byref(origin))
+    buf = (TraceEntry * max(n, 1))()
+    n = min(n, lib.pne_ctx_trace_read(ctx, buf, max(n, 1), ctypes.byref(origin)))
+    out = [{"name": buf[i].name.decode(), "kind": "gpu" if buf[i].kind == 0 else "host",
+            "stream": int(buf[i].stream), "t0_ms": float(buf[i].t0_ms), "t1_ms": float(buf[i].t1_ms)}
+           for i in range(n)]
+    return out, float(origin.value)
 
 
 def pne_terms_work(ctx, terms, stream=None) -> int:

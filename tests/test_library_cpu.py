@@ -51,6 +51,8 @@ def test_struct_layouts():
     assert ctypes.sizeof(pne.Network) == 8 + 4 * 8 + 8 + 8 + 8
     assert ctypes.sizeof(pne.PartitionOpts) == 32
     assert ctypes.sizeof(pne.EnumOpts) == 12
+    # pne_trace_entry: name[32], kind, stream, t0_ms, t1_ms
+    assert ctypes.sizeof(pne.TraceEntry) == 32 + 4 + 4 + 8 + 8
 
 
 def test_tensor_offsets_match_per_site_leg_products():
