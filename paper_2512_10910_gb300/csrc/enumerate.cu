@@ -68,7 +68,13 @@ struct Node {
 struct GeomView {
     const int32_t *bond_site;     // closed geometry [Mc][2]
     const int32_t *site_ptr, *site_bonds;
+    const int2 *site_nbr;         // per leg: (bond, site at the other end)
 };
+
+__device__ __forceinline__ int2 bond_ends(const GeomView &g, int e)
+{
+    return __ldg(reinterpret_cast<const int2 *>(g.bond_site) + e);
+}
 
 struct Emit {
     int32_t *edges;               // [n][width]
@@ -178,16 +184,21 @@ __device__ void write_cluster(const Emit &o, int64_t slot, const int32_t *S, int
     o.size[slot] = s;
 }
 
-// Bonds at new vertex b (> anchor, other end not in V), appended to U.
+// Bonds at new vertex b (> anchor, other end not in V), appended to U.  The
+// site's (bond, other end) pairs are loaded together first, so the walk costs
+// two dependent loads, not two per bond.
 template <int NV>
 __device__ int append_new(const GeomView &g, int b, int e, int anchor, const VSet<NV> &V,
                           int32_t *U, int32_t *UA, int32_t *UB, int ne, int cap, int32_t *overflow)
 {
-    for (int p = g.site_ptr[b]; p < g.site_ptr[b + 1]; ++p) {
-        const int f = g.site_bonds[p];
-        if (f == e || f <= anchor) continue;
-        const int c = g.bond_site[2 * f] == b ? g.bond_site[2 * f + 1] : g.bond_site[2 * f];
-        if (V.has(c)) continue;
+    const int p0 = __ldg(g.site_ptr + b), p1 = __ldg(g.site_ptr + b + 1);
+    int2 nb[kMaxDeg];
+#pragma unroll
+    for (int k = 0; k < kMaxDeg; ++k) nb[k] = (p0 + k < p1) ? __ldg(g.site_nbr + p0 + k) : make_int2(-1, -1);
+#pragma unroll
+    for (int k = 0; k < kMaxDeg; ++k) {
+        const int f = nb[k].x, c = nb[k].y;
+        if (p0 + k >= p1 || f == e || f <= anchor || V.has(c)) continue;
         if (ne >= cap) { atomicExch(overflow, 1); return ne; }
         U[ne] = f; UA[ne] = b; UB[ne] = c;
         ++ne;
@@ -429,6 +440,70 @@ __device__ bool repairable_after(const VSet<NV> &V, int old_n, int i, const int3
     return true;
 }
 
+// Can the child S + U[i] (size K - 2, LOOP mode) still be closed with the two
+// bonds left?  Both must come from the child's candidate list (a bond of a
+// new candidate list leads to a vertex outside the set and leaves it with
+// degree one).  So every degree-one vertex v of the child needs, among those
+// candidates, a bond from v to a vertex of the child (cost 1) or two bonds
+// through one vertex w outside the child, one of them at v (cost 2).  Charging
+// each degree-one vertex to the bond ends that serve it (a bond has two ends,
+// a path through w four, serving at most two such vertices) shows that the
+// costs of a closable child sum to at most 4.
+// Node tables (shared by the warp): ov[q], the end of U[q] outside the node's
+// vertex set (-1: none); tw[q], the last other candidate with the same outside
+// end (-1: none); tmask[k], the candidates at the node's vertex k.  The child
+// adds bond U[i] and, when it brings in a vertex b (= ov[i]), the new
+// candidates (b, nb[k]), k < nn.  The candidates of the child are U[j], j > i,
+// and those new ones.
+template <int NV>
+__device__ bool closable2(const VSet<NV> &V, int i, int b, int nn, const int32_t *nb, const int32_t *ov,
+                          const int32_t *tw, const uint64_t *tmask, int nU)
+{
+    if (V.dang > 4) return false;
+    const uint64_t after = ~0ull << (i + 1);
+    auto in_nb = [&](int w) {
+        bool f = false;
+        for (int k = 0; k < nn; ++k) f |= nb[k] == w;
+        return f;
+    };
+    int sum = 0;
+    bool b_open = false;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        if (k >= V.n || V.d[k] != 1) continue;
+        const int v = V.v[k];
+        if (v == b) { b_open = true; continue; }
+        // v is vertex k of the node: its later candidates
+        uint64_t m = tmask[k] & after;
+        int cost = 3;
+        while (m) {
+            const int q = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            const int w = ov[q];
+            if (w < 0 || w == b) { cost = 1; break; }          // a bond to a vertex of the child
+            if (tw[q] > i || (b >= 0 && in_nb(w))) cost = 2;    // a second bond at w: later, or new from b
+        }
+        if (cost > 2) return false;
+        sum += cost;
+    }
+    if (b_open) {
+        if (tw[i] > i) {
+            sum += 1;            // a later candidate joins b to the node's vertex set
+        } else {
+            // a path b - c - y through one of b's new far ends c: a later
+            // candidate with outside end c, or a second new bond to c
+            if (sum + 2 > 4) return false;
+            bool ok = false;
+            for (int k = 0; k < nn && !ok; ++k)
+                for (int k2 = k + 1; k2 < nn; ++k2) ok |= nb[k] == nb[k2];
+            for (int q = i + 1; q < nU && !ok; ++q) ok = in_nb(ov[q]);
+            if (!ok) return false;
+            sum += 2;
+        }
+    }
+    return sum <= 4;
+}
+
 // A node of size K - 2 in LOOP mode, both remaining levels at once.  Its child
 // S + U[i] (size K - 1) is a cluster iff it has no degree-one vertex; a
 // cluster of size K below that child is S + U[i] + U[j] with a bond U[j] of
@@ -525,7 +600,8 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
     __shared__ Node sh_node[kExpandWarps];
     __shared__ int32_t sh_a[kExpandWarps][kNodeU], sh_b[kExpandWarps][kNodeU];
     __shared__ int32_t sh_last[kExpandWarps][kNodeV];
-    __shared__ int32_t sh_out[kExpandWarps][kNodeU];
+    __shared__ int32_t sh_out[kExpandWarps][kNodeU], sh_tw[kExpandWarps][kNodeU];
+    __shared__ uint64_t sh_tmask[kExpandWarps][kNodeV];
     __shared__ int32_t sh_stage[kExpandWarps][32 * kStageWords];
     __shared__ int64_t wsum[kExpandWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -550,8 +626,8 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
         __syncwarp();
         const int nU = nd.nU, t = nd.t, anchor = nd.S[0], vn = nd.vn;
         for (int q = lane; q < nU; q += 32) {
-            const int e = nd.U[q];
-            UA[q] = g.bond_site[2 * e]; UB[q] = g.bond_site[2 * e + 1];
+            const int2 ab = bond_ends(g, nd.U[q]);
+            UA[q] = ab.x; UB[q] = ab.y;
         }
         __syncwarp();
         if (fuse && t == K - 2) {
@@ -567,6 +643,30 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
             pair_node(A, nd, u, UA, UB, ov, pass, want, out);
             __syncwarp();
             continue;
+        }
+        if (pass == kCount && fuse && t + 1 == K - 2) {
+            // children are closing nodes: the tables of closable2
+            int32_t *ov = sh_out[w], *tw = sh_tw[w];
+            for (int q = lane; q < nU; q += 32) {
+                const int a = UA[q], b = UB[q];
+                bool ia = false, ib = false;
+                for (int k = 0; k < vn; ++k) { ia |= nd.vv[k] == a; ib |= nd.vv[k] == b; }
+                ov[q] = !ia ? a : (!ib ? b : -1);
+            }
+            __syncwarp();
+            for (int q = lane; q < nU; q += 32) {
+                const int o = ov[q];
+                int lw = -1;
+                if (o >= 0)
+                    for (int f = 0; f < nU; ++f) lw = (f != q && ov[f] == o) ? f : lw;
+                tw[q] = lw;
+            }
+            for (int k = 0; k < vn; ++k) {
+                const int x = nd.vv[k];
+                const unsigned m0 = __ballot_sync(0xffffffffu, lane < nU && (UA[lane] == x || UB[lane] == x));
+                const unsigned m1 = __ballot_sync(0xffffffffu, lane + 32 < nU && (UA[lane + 32] == x || UB[lane + 32] == x));
+                if (lane == 0) sh_tmask[w][k] = (uint64_t)m0 | ((uint64_t)m1 << 32);
+            }
         }
         if (pass == kCount) {
             // the last candidate touching each vertex of S (-1: none): a
@@ -610,6 +710,8 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
                     if (pass == kCount && may_grow(mode, t + 1, K, V.dang)) {
                         if (b >= 0) nn = append_new(g, b, e, anchor, V, NU, NA, NB, 0, kMaxNew, &A.ctl->cand_overflow);
                         grow = mode == PNE_MODE_ALL || repairable_after(V, vn, i, last, b, nn, UA, UB, nU);
+                        if (grow && fuse && t + 1 == K - 2)
+                            grow = closable2(V, i, b, nn, NB, sh_out[w], sh_tw[w], sh_tmask[w], nU);
                     }
                 }
             }
@@ -683,7 +785,7 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
 }
 
 // kCount / kEmitCount / kPairCount of level lo == hi, or kEmit over levels lo..hi
-__global__ void __launch_bounds__(32 * kExpandWarps)
+__global__ void __launch_bounds__(32 * kExpandWarps, 6)
 expand_kernel(GeomView g, Arena A, int lo_level, int hi_level, int K, int mode, int pass, Emit out, int fuse)
 {
     expand_chunk(g, A, A.lv[lo_level - 1], A.lv[hi_level], K, mode, pass, out, 0, 0, fuse);
@@ -744,7 +846,9 @@ __global__ void __launch_bounds__(128) dfs_kernel(GeomView g, Arena A, int level
         for (int i = 0; i < t0; ++i) S[i] = nd.S[i];
         int32_t U[UMAX], UA[UMAX], UB[UMAX];
         for (int i = 0; i < nd.nU; ++i) {
-            U[i] = nd.U[i]; UA[i] = g.bond_site[2 * U[i]]; UB[i] = g.bond_site[2 * U[i] + 1];
+            U[i] = nd.U[i];
+            const int2 ab = bond_ends(g, U[i]);
+            UA[i] = ab.x; UB[i] = ab.y;
         }
         int32_t pos[KMAX], end[KMAX];
         int32_t cnt[KMAX + 1];
@@ -760,12 +864,14 @@ __global__ void __launch_bounds__(128) dfs_kernel(GeomView g, Arena A, int level
                 if (lvl == 0) break;
                 --lvl;
                 const int e = S[--s];
-                V.dec(g.bond_site[2 * e + 1]); V.dec(g.bond_site[2 * e]);
+                const int2 ab = bond_ends(g, e);
+                V.dec(ab.y); V.dec(ab.x);
                 ++pos[lvl];
                 continue;
             }
             const int e = U[pos[lvl]];
-            const int a0 = g.bond_site[2 * e], a1 = g.bond_site[2 * e + 1];
+            const int2 ab = bond_ends(g, e);
+            const int a0 = ab.x, a1 = ab.y;
             const int b = !V.has(a0) ? a0 : (!V.has(a1) ? a1 : -1);
             V.inc(a0); V.inc(a1);
             S[s++] = e;
@@ -1031,7 +1137,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         return PNE_EINVAL;
     }
     if ((kPrefixMax + 1) * (maxdeg - 1) > kNodeU) { set_error(ctx, PNE_EINVAL, "site degree too large"); return PNE_EINVAL; }
-    GeomView gv{g.d_bond_site, g.d_site_ptr, g.d_site_bonds};
+    GeomView gv{g.d_bond_site, g.d_site_ptr, g.d_site_bonds, g.d_site_nbr};
     // prefix levels 1..D are expanded breadth-first; the last one closes both
     // remaining sizes (LOOP mode, D == K - 2), only emits (D == K - 1) or is
     // searched depth-first (K - 1 > kPrefixMax)
@@ -1097,7 +1203,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         }
         for (int d = 1; d < D; ++d) {
             ProfScope ps__(ctx, s, "enum_expand");
-            expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, d, K, mode, kCount, none, 0);
+            expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, d, K, mode, kCount, none, final_kind == 3);
             expand_children_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, K, mode);
         }
         if (final_kind == 1 || final_kind == 3) {

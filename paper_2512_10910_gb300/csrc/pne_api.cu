@@ -274,6 +274,13 @@ pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
         std::vector<int32_t> fill(g.color_ptr.begin(), g.color_ptr.end() - 1);
         for (int v = 0; v < N; ++v) g.color_sites[fill[col[v]]++] = v;
     }
+    g.site_nbr.assign(2 * g.site_bonds.size(), -1);
+    for (int v = 0; v < N; ++v)
+        for (int i = g.site_ptr[v]; i < g.site_ptr[v + 1]; ++i) {
+            const int b = g.site_bonds[i];
+            g.site_nbr[2 * i] = b;
+            g.site_nbr[2 * i + 1] = g.bond_site[2 * b] == v ? g.bond_site[2 * b + 1] : g.bond_site[2 * b];
+        }
     uint64_t h = 1469598103934665603ull;
     h = fnv(h, &N, sizeof N);
     h = fnv(h, g.bond_site.data(), g.bond_site.size() * 4);
@@ -282,7 +289,7 @@ pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
     // one device buffer for every table
     const size_t n_i32 = g.bond_site.size() + g.bond_dim.size() + g.site_ptr.size() + g.site_bonds.size() +
                          g.bond_leg.size() + g.inc_slot.size() + g.blk_off.size() + g.color_ptr.size() +
-                         g.color_sites.size();
+                         g.color_sites.size() + g.site_nbr.size();
     const size_t bytes = g.tens_off.size() * 8 + n_i32 * 4 + 64;
     pne_status st = dev_alloc(ctx, g.storage, bytes, s);
     if (st) return st;
@@ -290,6 +297,7 @@ pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
     size_t off = 0;
     auto put = [&](const void *src, size_t nb) { size_t o = off; std::memcpy(host.data() + off, src, nb); off += nb; return o; };
     const size_t o_tens = put(g.tens_off.data(), g.tens_off.size() * 8);
+    const size_t o_nbr = put(g.site_nbr.data(), g.site_nbr.size() * 4);      // 8-byte aligned pairs
     const size_t o_bs = put(g.bond_site.data(), g.bond_site.size() * 4);
     const size_t o_bd = put(g.bond_dim.data(), g.bond_dim.size() * 4);
     const size_t o_sp = put(g.site_ptr.data(), g.site_ptr.size() * 4);
@@ -301,6 +309,7 @@ pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
     const size_t o_cs = put(g.color_sites.data(), g.color_sites.size() * 4);
     char *d = (char *)g.storage.ptr;
     g.d_tens_off = (int64_t *)(d + o_tens);
+    g.d_site_nbr = (int2 *)(d + o_nbr);
     g.d_bond_site = (int32_t *)(d + o_bs);
     g.d_bond_dim = (int32_t *)(d + o_bd);
     g.d_site_ptr = (int32_t *)(d + o_sp);

@@ -89,6 +89,7 @@ struct Geometry {
     std::vector<int32_t> blk_off;       // [n_sites][64] excitation-block offsets
     std::vector<int32_t> color_ptr;     // [n_colors+1] proper colouring of the sites (closed bonds)
     std::vector<int32_t> color_sites;   // [n_sites] sites grouped by colour, ascending within a colour
+    std::vector<int32_t> site_nbr;      // [n_legs][2] per leg of site_bonds: (bond, site at its other end; -1 open)
     int n_colors = 0;
     int max_deg = 0, max_dim = 0;
     uint64_t hash = 0;
@@ -97,6 +98,7 @@ struct Geometry {
             *d_site_bonds = nullptr, *d_bond_leg = nullptr, *d_inc_slot = nullptr,
             *d_blk_off = nullptr, *d_color_ptr = nullptr, *d_color_sites = nullptr;
     int64_t *d_tens_off = nullptr;
+    int2 *d_site_nbr = nullptr;
     DevBuf storage;
 };
 
