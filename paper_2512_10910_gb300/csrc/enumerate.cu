@@ -519,9 +519,11 @@ __device__ bool closable2(const VSet<NV> &V, int i, int b, int nn, const int32_t
 //   writing (kEmit): both sizes, from the slots of the (size, node) scan
 // `out_v` holds, per candidate, its end outside the node's vertex set (-1:
 // both ends inside); `want` is the lane mask of the writing pass.
+template <int PASS>
 __device__ void pair_node(const Arena &A, const Node &nd, int64_t u, const int32_t *UA, const int32_t *UB,
-                          const int32_t *out_v, int pass, uint64_t want, const Emit &out)
+                          const int32_t *out_v, uint64_t want, const Emit &out)
 {
+    constexpr int pass = PASS;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int nU = nd.nU, t = nd.t;
@@ -593,10 +595,15 @@ __device__ void pair_node(const Arena &A, const Node &nd, int64_t u, const int32
 // The block's chunk of the node range [r0, r1).  kChildren writes the
 // children from arena slot next + cbase_chunk on (cbase_chunk: the children of
 // the chunks before this one).
-// With `fuse`, nodes of size K - 2 (LOOP mode) are closing nodes (pair_node).
-__device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int64_t r1, int K, int mode, int pass,
-                             const Emit &out, int64_t next, int64_t cbase_chunk, int fuse)
+// With FUSE, nodes of size K - 2 (LOOP mode) are closing nodes (pair_node).
+// One instance per pass keeps each kernel's code small enough for the
+// instruction cache.
+template <int PASS, bool FUSE>
+__device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int64_t r1, int K, int mode,
+                             const Emit &out, int64_t next, int64_t cbase_chunk)
 {
+    constexpr int pass = PASS;
+    constexpr bool fuse = FUSE;
     __shared__ Node sh_node[kExpandWarps];
     __shared__ int32_t sh_a[kExpandWarps][kNodeU], sh_b[kExpandWarps][kNodeU];
     __shared__ int32_t sh_last[kExpandWarps][kNodeV];
@@ -640,7 +647,7 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
                 ov[q] = !ia ? a : (!ib ? b : -1);
             }
             __syncwarp();
-            pair_node(A, nd, u, UA, UB, ov, pass, want, out);
+            pair_node<PASS>(A, nd, u, UA, UB, ov, want, out);
             __syncwarp();
             continue;
         }
@@ -785,10 +792,11 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
 }
 
 // kCount / kEmitCount / kPairCount of level lo == hi, or kEmit over levels lo..hi
+template <int PASS, bool FUSE>
 __global__ void __launch_bounds__(32 * kExpandWarps, 6)
-expand_kernel(GeomView g, Arena A, int lo_level, int hi_level, int K, int mode, int pass, Emit out, int fuse)
+expand_kernel(GeomView g, Arena A, int lo_level, int hi_level, int K, int mode, Emit out)
 {
-    expand_chunk(g, A, A.lv[lo_level - 1], A.lv[hi_level], K, mode, pass, out, 0, 0, fuse);
+    expand_chunk<PASS, FUSE>(g, A, A.lv[lo_level - 1], A.lv[hi_level], K, mode, out, 0, 0);
 }
 
 // One level step is two ordinary launches (no grid barrier, so the search can
@@ -825,7 +833,7 @@ __global__ void __launch_bounds__(32 * kExpandWarps) expand_children_kernel(Geom
         if (!fits) { A.ctl->stop = d; A.ctl->need = hi + total; }
     }
     if (!fits) return;
-    expand_chunk(g, A, lo, hi, K, mode, kChildren, none, hi, before, 0);
+    expand_chunk<kChildren, false>(g, A, lo, hi, K, mode, none, hi, before);
 }
 
 // ---------------------------------------------------------------- depth-first tasks
@@ -1123,6 +1131,28 @@ pne_status scan_counts(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t 
 
 }  // namespace
 
+namespace {
+
+void launch_expand(int pass, bool fuse, int G, cudaStream_t s, const GeomView &gv, const Arena &A, int lo, int hi,
+                   int K, int mode, const Emit &o)
+{
+    const int T = 32 * kExpandWarps;
+    switch (pass) {
+    case kCount:
+        if (fuse) expand_kernel<kCount, true><<<G, T, 0, s>>>(gv, A, lo, hi, K, mode, o);
+        else expand_kernel<kCount, false><<<G, T, 0, s>>>(gv, A, lo, hi, K, mode, o);
+        break;
+    case kEmitCount: expand_kernel<kEmitCount, false><<<G, T, 0, s>>>(gv, A, lo, hi, K, mode, o); break;
+    case kPairCount: expand_kernel<kPairCount, true><<<G, T, 0, s>>>(gv, A, lo, hi, K, mode, o); break;
+    default:
+        if (fuse) expand_kernel<kEmit, true><<<G, T, 0, s>>>(gv, A, lo, hi, K, mode, o);
+        else expand_kernel<kEmit, false><<<G, T, 0, s>>>(gv, A, lo, hi, K, mode, o);
+        break;
+    }
+}
+
+}  // namespace
+
 pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, EnumRecord &rec,
                               cudaStream_t s)
 {
@@ -1150,7 +1180,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     // is queried once per context)
     if (ctx->occ_expand < 0) {
         int a = 0;
-        PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, expand_kernel, 32 * kExpandWarps, 0));
+        PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, expand_kernel<kCount, true>, 32 * kExpandWarps, 0));
         ctx->occ_expand = a;
     }
     const int G = ctx->n_sm * std::max(1, ctx->occ_expand);
@@ -1203,13 +1233,12 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         }
         for (int d = 1; d < D; ++d) {
             ProfScope ps__(ctx, s, "enum_expand");
-            expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, d, K, mode, kCount, none, final_kind == 3);
+            launch_expand(kCount, final_kind == 3, G, s, gv, A, d, d, K, mode, none);
             expand_children_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, K, mode);
         }
         if (final_kind == 1 || final_kind == 3) {
             ProfScope ps__(ctx, s, "enum_expand");
-            expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, D, D, K, mode, final_kind == 3 ? kPairCount : kEmitCount,
-                                                          none, final_kind == 3);
+            launch_expand(final_kind == 3 ? kPairCount : kEmitCount, final_kind == 3, G, s, gv, A, D, D, K, mode, none);
         } else if (final_kind == 2) {
             dfs(A, D, 0, none);
         }
@@ -1263,8 +1292,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     }
     if (last_bfs >= 1) {
         ProfScope ps__(ctx, s, "enum_expand");
-        expand_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, 1, last_bfs, K, mode, kEmit, out,
-                                                      final_kind == 3 && dfs_level == 0);
+        launch_expand(kEmit, final_kind == 3 && dfs_level == 0, G, s, gv, A, 1, last_bfs, K, mode, out);
     }
     if (dfs_level) dfs(A, dfs_level, 1, out);
     PNE_CUDA_TRY(ctx, cudaGetLastError());
