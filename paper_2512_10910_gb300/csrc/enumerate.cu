@@ -37,6 +37,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstddef>
 #include <cstring>
 
@@ -406,36 +407,88 @@ constexpr int kNodeWords = (int)(sizeof(Node) / 4);
 
 // Node word offsets (the children are written word by word) and the staging
 // record of a growing lane: new-candidate count, new candidates, then the
-// child's vertex multiset in node order (vn, vdang, vv[], vd[]).
+// bond's end indices in the node's vertex list, the vertex it brings in and
+// the child's degree-one count.
 constexpr int kOffNU = (int)(offsetof(Node, nU) / 4);
 constexpr int kOffT = (int)(offsetof(Node, t) / 4);
 constexpr int kOffVN = (int)(offsetof(Node, vn) / 4);
-constexpr int kStageWords = 1 + kMaxNew + 2 + 2 * kNodeV;
+constexpr int kStageWords = 1 + kMaxNew + 4;
 static_assert(offsetof(Node, vdang) / 4 == kOffVN + 1 && offsetof(Node, vv) / 4 == kOffVN + 2 &&
               offsetof(Node, vd) / 4 == kOffVN + 2 + kNodeV && sizeof(Node) / 4 == kOffVN + 2 + 2 * kNodeV,
               "node layout");
+static_assert(kNodeV <= 32 && kNodeU <= 64, "vertex and candidate masks");
 
-// Every degree-one vertex of V = V(S) + U[i] can still be repaired inside this
-// subtree.  A vertex of S (index < old_n) is, iff some candidate after i
-// touches it (last[j] > i); new candidates only touch the vertex b that U[i]
-// brought in, which is repairable iff it has new candidates or a later
-// candidate of the list touches it.
-template <int NV>
-__device__ bool repairable_after(const VSet<NV> &V, int old_n, int i, const int32_t *last, int b, int nn,
-                                 const int32_t *UA, const int32_t *UB, int nU)
+// Per-node tables of one warp, in shared memory.  Every candidate U[q] touches
+// the node's vertex set; ia[q] and ib[q] are the indices of its two ends in
+// the node's vertex list (-1: not in it), so the child S + U[q] is described
+// relative to the node: the bond raises the degrees of ia and ib, and brings
+// in the vertex outside(q) when one end is missing.
+struct NodeTabs {
+    int32_t *UA, *UB;         // ends of U[q]
+    int32_t *ia, *ib;         // their indices in the node's vertex list, -1: outside
+    uint64_t *tmask;          // [vn] candidates at vertex k (counting pass)
+    int32_t *tw;              // last other candidate with the same outside end (-1: none)
+    __device__ __forceinline__ int outside(int q) const { return ia[q] < 0 ? UA[q] : (ib[q] < 0 ? UB[q] : -1); }
+};
+
+// The child S + U[i] relative to the node: its degree-one vertices are the
+// node's degree-one vertices the bond does not touch (mask over the vertex
+// list) plus the vertex b it brings in.
+struct Child {
+    int ia, ib, b;
+    uint32_t dmask;           // degree-one vertices of the node still at degree one
+    int dang;                 // the child's degree-one count
+};
+
+__device__ __forceinline__ Child make_child(const NodeTabs &T, int i, uint32_t node_dmask)
 {
-    if (V.dang == 0) return true;
+    Child c;
+    c.ia = T.ia[i]; c.ib = T.ib[i];
+    c.b = c.ia < 0 ? T.UA[i] : (c.ib < 0 ? T.UB[i] : -1);
+    c.dmask = node_dmask & ~((c.ia >= 0 ? 1u << c.ia : 0u) | (c.ib >= 0 ? 1u << c.ib : 0u));
+    c.dang = __popc(c.dmask) + (c.b >= 0 ? 1 : 0);
+    return c;
+}
+
+// Bonds at the new vertex b (> anchor, not e, other end outside the node's
+// vertex list vv[0, vn)): the child's new candidates, in the site's leg order.
+// The site's (bond, other end) pairs are loaded together, so the walk costs
+// two dependent loads.
+__device__ __forceinline__ int new_candidates(const GeomView &g, int b, int e, int anchor, const int32_t *vv, int vn,
+                                              int32_t *NU, int32_t *NB, int32_t *overflow)
+{
+    const int p0 = __ldg(g.site_ptr + b), p1 = __ldg(g.site_ptr + b + 1);
+    int2 nb[kMaxDeg];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        if (j >= V.n) break;
-        if (V.d[j] != 1) continue;
-        if (j < old_n) {
-            if (last[j] <= i) return false;
-        } else if (nn == 0) {
-            bool found = false;
-            for (int q = i + 1; q < nU && !found; ++q) found = (UA[q] == b || UB[q] == b);
-            if (!found) return false;
-        }
+    for (int k = 0; k < kMaxDeg; ++k) nb[k] = (p0 + k < p1) ? __ldg(g.site_nbr + p0 + k) : make_int2(-1, -1);
+    int ne = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxDeg; ++k) {
+        const int f = nb[k].x, c = nb[k].y;
+        if (p0 + k >= p1 || f == e || f <= anchor) continue;
+        bool in = false;
+        for (int j = 0; j < vn; ++j) in |= vv[j] == c;
+        if (in) continue;
+        if (ne >= kMaxNew) { atomicExch(overflow, 1); break; }
+        NU[ne] = f; NB[ne] = c;
+        ++ne;
+    }
+    return ne;
+}
+
+// Every degree-one vertex of the child can still be repaired inside its
+// subtree: a vertex of the node iff some candidate after i touches it; the
+// vertex b iff it has new candidates or a later candidate touches it.
+__device__ __forceinline__ bool repairable_child(const NodeTabs &T, const Child &c, int i, int nn, int nU)
+{
+    for (uint32_t m = c.dmask; m; m &= m - 1) {
+        const int k = __ffs(m) - 1;
+        if ((T.tmask[k] >> (i + 1)) == 0) return false;
+    }
+    if (c.b >= 0 && nn == 0) {
+        bool found = false;
+        for (int q = i + 1; q < nU && !found; ++q) found = T.outside(q) == c.b;
+        if (!found) return false;
     }
     return true;
 }
@@ -448,18 +501,11 @@ __device__ bool repairable_after(const VSet<NV> &V, int old_n, int i, const int3
 // through one vertex w outside the child, one of them at v (cost 2).  Charging
 // each degree-one vertex to the bond ends that serve it (a bond has two ends,
 // a path through w four, serving at most two such vertices) shows that the
-// costs of a closable child sum to at most 4.
-// Node tables (shared by the warp): ov[q], the end of U[q] outside the node's
-// vertex set (-1: none); tw[q], the last other candidate with the same outside
-// end (-1: none); tmask[k], the candidates at the node's vertex k.  The child
-// adds bond U[i] and, when it brings in a vertex b (= ov[i]), the new
-// candidates (b, nb[k]), k < nn.  The candidates of the child are U[j], j > i,
-// and those new ones.
-template <int NV>
-__device__ bool closable2(const VSet<NV> &V, int i, int b, int nn, const int32_t *nb, const int32_t *ov,
-                          const int32_t *tw, const uint64_t *tmask, int nU)
+// costs of a closable child sum to at most 4.  The candidates of the child
+// are U[j], j > i, and its new candidates (b, nb[k]), k < nn.
+__device__ bool closable2(const NodeTabs &T, const Child &c, int i, int nn, const int32_t *nb, int nU)
 {
-    if (V.dang > 4) return false;
+    if (c.dang > 4) return false;
     const uint64_t after = ~0ull << (i + 1);
     auto in_nb = [&](int w) {
         bool f = false;
@@ -467,41 +513,79 @@ __device__ bool closable2(const VSet<NV> &V, int i, int b, int nn, const int32_t
         return f;
     };
     int sum = 0;
-    bool b_open = false;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        if (k >= V.n || V.d[k] != 1) continue;
-        const int v = V.v[k];
-        if (v == b) { b_open = true; continue; }
-        // v is vertex k of the node: its later candidates
-        uint64_t m = tmask[k] & after;
+    for (uint32_t dm = c.dmask; dm; dm &= dm - 1) {
+        const int k = __ffs(dm) - 1;
+        uint64_t m = T.tmask[k] & after;
         int cost = 3;
         while (m) {
             const int q = __ffsll((long long)m) - 1;
             m &= m - 1;
-            const int w = ov[q];
-            if (w < 0 || w == b) { cost = 1; break; }          // a bond to a vertex of the child
-            if (tw[q] > i || (b >= 0 && in_nb(w))) cost = 2;    // a second bond at w: later, or new from b
+            const int w = T.outside(q);
+            if (w < 0 || w == c.b) { cost = 1; break; }            // a bond to a vertex of the child
+            if (T.tw[q] > i || (c.b >= 0 && in_nb(w))) cost = 2;   // a second bond at w: later, or new from b
         }
         if (cost > 2) return false;
         sum += cost;
     }
-    if (b_open) {
-        if (tw[i] > i) {
+    if (c.b >= 0) {
+        if (T.tw[i] > i) {
             sum += 1;            // a later candidate joins b to the node's vertex set
         } else {
-            // a path b - c - y through one of b's new far ends c: a later
-            // candidate with outside end c, or a second new bond to c
+            // a path b - x - y through one of b's new far ends x: a later
+            // candidate with outside end x, or a second new bond to x
             if (sum + 2 > 4) return false;
             bool ok = false;
             for (int k = 0; k < nn && !ok; ++k)
                 for (int k2 = k + 1; k2 < nn; ++k2) ok |= nb[k] == nb[k2];
-            for (int q = i + 1; q < nU && !ok; ++q) ok = in_nb(ov[q]);
+            for (int q = i + 1; q < nU && !ok; ++q) ok = in_nb(T.outside(q));
             if (!ok) return false;
             sum += 2;
         }
     }
     return sum <= 4;
+}
+
+// Sorts N values in registers (odd-even transposition; every index constant).
+template <int N>
+__device__ __forceinline__ void sort_regs(int32_t (&x)[N])
+{
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int j = r & 1; j + 1 < N; j += 2) {
+            const int lo = min(x[j], x[j + 1]), hi = max(x[j], x[j + 1]);
+            x[j] = lo; x[j + 1] = hi;
+        }
+}
+
+// Writes the cluster S + e1 (+ e2 when >= 0) of a node: bonds and vertices
+// (the node's list plus b when >= 0) sorted ascending, rows padded with -1.
+__device__ void write_child_cluster(const Emit &o, int64_t slot, const Node &nd, int e1, int e2, int b)
+{
+    constexpr int NS = kPrefixMax + 2, NVx = kNodeV + 1;
+    const int t = nd.t, vn = nd.vn;
+    int32_t sv[NS], vv[NVx];
+#pragma unroll
+    for (int q = 0; q < kPrefixMax; ++q) sv[q] = q < t ? nd.S[q] : INT_MAX;
+    sv[kPrefixMax] = e1;
+    sv[kPrefixMax + 1] = e2 >= 0 ? e2 : INT_MAX;
+#pragma unroll
+    for (int q = 0; q < kNodeV; ++q) vv[q] = q < vn ? nd.vv[q] : INT_MAX;
+    vv[kNodeV] = b >= 0 ? b : INT_MAX;
+    sort_regs(sv);
+    sort_regs(vv);
+    const int s = t + 1 + (e2 >= 0 ? 1 : 0), n = vn + (b >= 0 ? 1 : 0);
+    int32_t *er = o.edges + slot * o.width;
+#pragma unroll
+    for (int q = 0; q < NS; ++q)
+        if (q < o.width) er[q] = q < s ? sv[q] : -1;
+    for (int q = NS; q < o.width; ++q) er[q] = -1;
+    int32_t *vr = o.verts + slot * o.vwidth;
+#pragma unroll
+    for (int q = 0; q < NVx; ++q)
+        if (q < o.vwidth) vr[q] = q < n ? vv[q] : -1;
+    for (int q = NVx; q < o.vwidth; ++q) vr[q] = -1;
+    o.size[slot] = s;
 }
 
 // A node of size K - 2 in LOOP mode, both remaining levels at once.  Its child
@@ -517,11 +601,10 @@ __device__ bool closable2(const VSet<NV> &V, int i, int b, int nn, const int32_t
 //   counting (kPairCount): per node the size K - 1 and size K counts, the
 //     lanes with an emitted child (emask) and with a closing bond (gmask)
 //   writing (kEmit): both sizes, from the slots of the (size, node) scan
-// `out_v` holds, per candidate, its end outside the node's vertex set (-1:
-// both ends inside); `want` is the lane mask of the writing pass.
+// `want` is the lane mask of the writing pass.
 template <int PASS>
-__device__ void pair_node(const Arena &A, const Node &nd, int64_t u, const int32_t *UA, const int32_t *UB,
-                          const int32_t *out_v, uint64_t want, const Emit &out)
+__device__ void pair_node(const Arena &A, const Node &nd, int64_t u, const NodeTabs &T, uint32_t node_dmask,
+                          uint64_t want, const Emit &out)
 {
     constexpr int pass = PASS;
     const int lane = threadIdx.x & 31;
@@ -533,24 +616,23 @@ __device__ void pair_node(const Arena &A, const Node &nd, int64_t u, const int32
     const int64_t pbase = (pass == kEmit) ? A.base[(int64_t)(t + 2) * A.cap + u] : 0;
     for (int i0 = 0; i0 < nU; i0 += 32) {
         const int i = i0 + lane;
-        VSet<kNodeV> V;
         bool emit = false;
-        int np = 0, d0 = -1, d1 = -1, b = -1;
+        int np = 0, d0 = -1, d1 = -1;
+        Child c{-1, -1, -1, 0u, 0};
         const bool mine = i < nU && ((want >> i) & 1);
         if (mine) {
-            load_vset(V, nd);
-            const int a0 = UA[i], a1 = UB[i];
-            b = !V.has(a0) ? a0 : (!V.has(a1) ? a1 : -1);
-            V.inc(a0); V.inc(a1);
-            emit = V.dang == 0;
-            if (V.dang <= 2) {
-#pragma unroll
-                for (int q = 0; q < kNodeV; ++q)
-                    if (q < V.n && V.d[q] == 1) { if (d0 < 0) d0 = V.v[q]; else d1 = V.v[q]; }
+            c = make_child(T, i, node_dmask);
+            emit = c.dang == 0;
+            if (c.dang <= 2) {
+                for (uint32_t m = c.dmask; m; m &= m - 1) {
+                    const int v = nd.vv[__ffs(m) - 1];
+                    if (d0 < 0) d0 = v; else d1 = v;
+                }
+                if (c.b >= 0) { if (d0 < 0) d0 = c.b; else d1 = c.b; }
                 for (int j = i + 1; j < nU; ++j) {
-                    const int oj = out_v[j];
-                    if (oj != -1 && oj != b) continue;
-                    const int x = UA[j], y = UB[j];
+                    const int oj = T.outside(j);
+                    if (oj != -1 && oj != c.b) continue;
+                    const int x = T.UA[j], y = T.UB[j];
                     if ((d0 >= 0 && d0 != x && d0 != y) || (d1 >= 0 && d1 != x && d1 != y)) continue;
                     ++np;
                 }
@@ -566,19 +648,16 @@ __device__ void pair_node(const Arena &A, const Node &nd, int64_t u, const int32
             if (lane >= off) incl += z;
         }
         if (pass == kEmit && mine) {
-            int32_t S[kPrefixMax + 2];
-            for (int q = 0; q < t; ++q) S[q] = nd.S[q];
-            S[t] = nd.U[i];
-            if (emit) write_cluster(out, ebase + n_emit + __popc(em & lt), S, t + 1, V);
+            const int ei = nd.U[i];
+            if (emit) write_child_cluster(out, ebase + n_emit + __popc(em & lt), nd, ei, -1, c.b);
             int64_t slot = pbase + n_pair + (incl - np);
             if (np > 0)
                 for (int j = i + 1; j < nU; ++j) {
-                    const int oj = out_v[j];
-                    if (oj != -1 && oj != b) continue;
-                    const int x = UA[j], y = UB[j];
+                    const int oj = T.outside(j);
+                    if (oj != -1 && oj != c.b) continue;
+                    const int x = T.UA[j], y = T.UB[j];
                     if ((d0 >= 0 && d0 != x && d0 != y) || (d1 >= 0 && d1 != x && d1 != y)) continue;
-                    S[t + 1] = nd.U[j];
-                    write_cluster(out, slot++, S, t + 2, V);
+                    write_child_cluster(out, slot++, nd, ei, nd.U[j], c.b);
                 }
         }
         n_emit += __popc(em);
@@ -606,15 +685,16 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
     constexpr bool fuse = FUSE;
     __shared__ Node sh_node[kExpandWarps];
     __shared__ int32_t sh_a[kExpandWarps][kNodeU], sh_b[kExpandWarps][kNodeU];
-    __shared__ int32_t sh_last[kExpandWarps][kNodeV];
-    __shared__ int32_t sh_out[kExpandWarps][kNodeU], sh_tw[kExpandWarps][kNodeU];
+    __shared__ int32_t sh_ia[kExpandWarps][kNodeU], sh_ib[kExpandWarps][kNodeU];
     __shared__ uint64_t sh_tmask[kExpandWarps][kNodeV];
+    __shared__ int32_t sh_tw[kExpandWarps][kNodeU];
     __shared__ int32_t sh_stage[kExpandWarps][32 * kStageWords];
     __shared__ int64_t wsum[kExpandWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     Node &nd = sh_node[w];
-    int32_t *UA = sh_a[w], *UB = sh_b[w], *last = sh_last[w], *stage = sh_stage[w];
+    const NodeTabs T{sh_a[w], sh_b[w], sh_ia[w], sh_ib[w], sh_tmask[w], sh_tw[w]};
+    int32_t *stage = sh_stage[w];
     const int64_t chunk = (r1 - r0 + gridDim.x - 1) / gridDim.x;
     const int64_t c0 = r0 + (int64_t)blockIdx.x * chunk;
     const int64_t c1 = c0 + chunk < r1 ? c0 + chunk : r1;
@@ -634,59 +714,38 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
         const int nU = nd.nU, t = nd.t, anchor = nd.S[0], vn = nd.vn;
         for (int q = lane; q < nU; q += 32) {
             const int2 ab = bond_ends(g, nd.U[q]);
-            UA[q] = ab.x; UB[q] = ab.y;
+            int ia = -1, ib = -1;
+            for (int k = 0; k < vn; ++k) {
+                const int x = nd.vv[k];
+                ia = x == ab.x ? k : ia;
+                ib = x == ab.y ? k : ib;
+            }
+            T.UA[q] = ab.x; T.UB[q] = ab.y; T.ia[q] = ia; T.ib[q] = ib;
         }
+        const uint32_t dmask = __ballot_sync(0xffffffffu, lane < vn && nd.vd[lane] == 1);
         __syncwarp();
         if (fuse && t == K - 2) {
-            // a closing node: each candidate's end outside the vertex set of S
-            int32_t *ov = sh_out[w];
-            for (int q = lane; q < nU; q += 32) {
-                const int a = UA[q], b = UB[q];
-                bool ia = false, ib = false;
-                for (int k = 0; k < vn; ++k) { ia |= nd.vv[k] == a; ib |= nd.vv[k] == b; }
-                ov[q] = !ia ? a : (!ib ? b : -1);
-            }
-            __syncwarp();
-            pair_node<PASS>(A, nd, u, UA, UB, ov, want, out);
+            pair_node<PASS>(A, nd, u, T, dmask, want, out);
             __syncwarp();
             continue;
         }
-        if (pass == kCount && fuse && t + 1 == K - 2) {
-            // children are closing nodes: the tables of closable2
-            int32_t *ov = sh_out[w], *tw = sh_tw[w];
-            for (int q = lane; q < nU; q += 32) {
-                const int a = UA[q], b = UB[q];
-                bool ia = false, ib = false;
-                for (int k = 0; k < vn; ++k) { ia |= nd.vv[k] == a; ib |= nd.vv[k] == b; }
-                ov[q] = !ia ? a : (!ib ? b : -1);
-            }
-            __syncwarp();
-            for (int q = lane; q < nU; q += 32) {
-                const int o = ov[q];
-                int lw = -1;
-                if (o >= 0)
-                    for (int f = 0; f < nU; ++f) lw = (f != q && ov[f] == o) ? f : lw;
-                tw[q] = lw;
-            }
-            for (int k = 0; k < vn; ++k) {
-                const int x = nd.vv[k];
-                const unsigned m0 = __ballot_sync(0xffffffffu, lane < nU && (UA[lane] == x || UB[lane] == x));
-                const unsigned m1 = __ballot_sync(0xffffffffu, lane + 32 < nU && (UA[lane + 32] == x || UB[lane + 32] == x));
-                if (lane == 0) sh_tmask[w][k] = (uint64_t)m0 | ((uint64_t)m1 << 32);
-            }
-        }
+        const bool closing_children = pass == kCount && fuse && t + 1 == K - 2;
         if (pass == kCount) {
-            // the last candidate touching each vertex of S (-1: none): a
-            // degree-one vertex of S + U[i] stays repairable iff it is > i
-            for (int j = 0; j < vn; ++j) {
-                const int x = nd.vv[j];
-                int lst = -1;
-                for (int i0 = 0; i0 < nU; i0 += 32) {
-                    const int q = i0 + lane;
-                    const unsigned m = __ballot_sync(0xffffffffu, q < nU && (UA[q] == x || UB[q] == x));
-                    if (m) lst = i0 + 31 - __clz(m);
+            // the candidates at each vertex of the node
+            for (int k = 0; k < vn; ++k) {
+                const unsigned m0 = __ballot_sync(0xffffffffu, lane < nU && (T.ia[lane] == k || T.ib[lane] == k));
+                const unsigned m1 = __ballot_sync(0xffffffffu, lane + 32 < nU && (T.ia[lane + 32] == k || T.ib[lane + 32] == k));
+                if (lane == 0) T.tmask[k] = (uint64_t)m0 | ((uint64_t)m1 << 32);
+            }
+            if (closing_children) {
+                // children are closing nodes: the twin table of closable2
+                for (int q = lane; q < nU; q += 32) {
+                    const int o = T.outside(q);
+                    int lw = -1;
+                    if (o >= 0)
+                        for (int f = 0; f < nU; ++f) lw = (f != q && T.outside(f) == o) ? f : lw;
+                    T.tw[q] = lw;
                 }
-                if (lane == 0) last[j] = lst;
             }
             __syncwarp();
         }
@@ -697,28 +756,25 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
         for (int i0 = 0; i0 < nU; i0 += 32) {
             const int i = i0 + lane;
             bool emit = false, grow = false;
-            VSet<kNodeV> V;
-            int32_t NU[kMaxNew], NA[kMaxNew], NB[kMaxNew];
+            int32_t NU[kMaxNew], NB[kMaxNew];
             int nn = 0;
+            Child c{-1, -1, -1, 0u, 0};
             const bool mine = i < nU && ((want >> i) & 1);
             if (mine) {
-                load_vset(V, nd);
-                const int e = nd.U[i], a0 = UA[i], a1 = UB[i];
-                const int b = !V.has(a0) ? a0 : (!V.has(a1) ? a1 : -1);
-                V.inc(a0); V.inc(a1);
+                c = make_child(T, i, dmask);
+                const int e = nd.U[i];
                 if (pass == kChildren) {
                     // decided by the counting pass; only the new candidates are rebuilt
                     grow = true;
-                    if (b >= 0) nn = append_new(g, b, e, anchor, V, NU, NA, NB, 0, kMaxNew, &A.ctl->cand_overflow);
+                    if (c.b >= 0) nn = new_candidates(g, c.b, e, anchor, nd.vv, vn, NU, NB, &A.ctl->cand_overflow);
                 } else if (pass == kEmit) {
                     emit = true;
                 } else {
-                    emit = valid_set(mode, V.dang);
-                    if (pass == kCount && may_grow(mode, t + 1, K, V.dang)) {
-                        if (b >= 0) nn = append_new(g, b, e, anchor, V, NU, NA, NB, 0, kMaxNew, &A.ctl->cand_overflow);
-                        grow = mode == PNE_MODE_ALL || repairable_after(V, vn, i, last, b, nn, UA, UB, nU);
-                        if (grow && fuse && t + 1 == K - 2)
-                            grow = closable2(V, i, b, nn, NB, sh_out[w], sh_tw[w], sh_tmask[w], nU);
+                    emit = valid_set(mode, c.dang);
+                    if (pass == kCount && may_grow(mode, t + 1, K, c.dang)) {
+                        if (c.b >= 0) nn = new_candidates(g, c.b, e, anchor, nd.vv, vn, NU, NB, &A.ctl->cand_overflow);
+                        grow = mode == PNE_MODE_ALL || repairable_child(T, c, i, nn, nU);
+                        if (closing_children && grow) grow = closable2(T, c, i, nn, NB, nU);
                     }
                 }
             }
@@ -732,10 +788,10 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
                     int32_t *st = stage + lane * kStageWords;
                     st[0] = nn;
                     for (int q = 0; q < nn; ++q) st[1 + q] = NU[q];
-                    st[1 + kMaxNew] = V.n;
-                    st[2 + kMaxNew] = V.dang;
-#pragma unroll
-                    for (int j = 0; j < kNodeV; ++j) { st[3 + kMaxNew + j] = V.v[j]; st[3 + kMaxNew + kNodeV + j] = V.d[j]; }
+                    st[1 + kMaxNew] = c.ia;
+                    st[2 + kMaxNew] = c.ib;
+                    st[3 + kMaxNew] = c.b;
+                    st[4 + kMaxNew] = c.dang;
                 }
                 __syncwarp();
                 unsigned rem = gm;
@@ -745,7 +801,8 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
                     const int io = i0 + o;
                     const int32_t *so = stage + o * kStageWords;
                     const int m0 = nU - io - 1, nno = so[0];
-                    int32_t *c = reinterpret_cast<int32_t *>(A.nodes + cbase + n_child + r);
+                    const int cia = so[1 + kMaxNew], cib = so[2 + kMaxNew], cb = so[3 + kMaxNew];
+                    int32_t *cw = reinterpret_cast<int32_t *>(A.nodes + cbase + n_child + r);
                     for (int q = lane; q < kNodeWords; q += 32) {
                         int32_t val;
                         if (q < kPrefixMax) {
@@ -757,21 +814,26 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
                             val = m0 + nno < kNodeU ? m0 + nno : kNodeU;
                         } else if (q == kOffT) {
                             val = t + 1;
+                        } else if (q == kOffVN) {
+                            val = vn + (cb >= 0 ? 1 : 0);
+                        } else if (q == kOffVN + 1) {
+                            val = so[4 + kMaxNew];
+                        } else if (q < kOffVN + 2 + kNodeV) {
+                            const int j = q - (kOffVN + 2);                       // vertex list: the node's, then b
+                            val = j < vn ? nd.vv[j] : (j == vn && cb >= 0 ? cb : 0);
                         } else {
-                            val = so[1 + kMaxNew + (q - kOffVN)];   // vn, vdang, vv[], vd[] in node order
+                            const int j = q - (kOffVN + 2 + kNodeV);              // degrees
+                            val = j < vn ? nd.vd[j] + (j == cia ? 1 : 0) + (j == cib ? 1 : 0)
+                                         : (j == vn && cb >= 0 ? 1 : 0);
                         }
-                        c[q] = val;
+                        cw[q] = val;
                     }
                     if (lane == 0 && m0 + nno > kNodeU) atomicExch(&A.ctl->cand_overflow, 1);
                 }
                 __syncwarp();
             }
-            if (pass == kEmit && emit) {
-                int32_t S[kPrefixMax + 1];
-                for (int q = 0; q < t; ++q) S[q] = nd.S[q];
-                S[t] = nd.U[i];
-                write_cluster(out, ebase + n_emit + __popc(em & lt), S, t + 1, V);
-            }
+            if (pass == kEmit && emit)
+                write_child_cluster(out, ebase + n_emit + __popc(em & lt), nd, nd.U[i], -1, c.b);
             n_child += __popc(gm);
             n_emit += __popc(em);
         }
