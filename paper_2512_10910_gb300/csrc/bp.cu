@@ -847,6 +847,10 @@ __global__ void __launch_bounds__(kBpWarps * 32, 4) bp_ff_cluster_kernel(BPFFPar
 }
 
 // site tensors -> scaled float-float, one warp per (set, site)
+// FP64 tensors -> scaled float-float pairs, one warp per site: the largest
+// entry's exponent from the bits, then each entry split by integer operations
+// (split_scaled), so the conversion runs at memory speed rather than on the
+// FP64 pipe.
 __global__ void ff_tensor_kernel(const double *T, ff *out, const int64_t *tens_off, int n_sites, int n_sets, int64_t stride)
 {
     const int lane = threadIdx.x & 31;
@@ -857,16 +861,11 @@ __global__ void ff_tensor_kernel(const double *T, ff *out, const int64_t *tens_o
         const double *t = T + set * stride + tens_off[v];
         ff *o = out + set * stride + tens_off[v];
         const int64_t n = tens_off[v + 1] - tens_off[v];
-        double mx = 0.0;
-        for (int64_t e = lane; e < n; e += 32) mx = fmax(mx, fabs(t[e]));
-        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-        int ex = 0;
-        if (mx > 0.0) frexp(mx, &ex);
-        for (int64_t e = lane; e < n; e += 32) {
-            const double x = ldexp(t[e], -ex);
-            const float hi = __double2float_rn(x);
-            o[e] = {hi, __double2float_rn(x - (double)hi)};
-        }
+        int mxb = 0;                                     // largest biased exponent
+        for (int64_t e = lane; e < n; e += 32) mxb = max(mxb, (int)((__double_as_longlong(__ldg(t + e)) >> 52) & 0x7FF));
+        for (int off = 16; off > 0; off >>= 1) mxb = max(mxb, __shfl_xor_sync(0xffffffffu, mxb, off));
+        const int ex = mxb > 0 ? min(mxb - 1022, 1022) : 0;   // entries are below 2^ex
+        for (int64_t e = lane; e < n; e += 32) o[e] = split_scaled(__ldg(t + e), ex);
     }
 }
 
@@ -903,6 +902,13 @@ struct GaugeParams {
     int32_t *flags;              // [1] degenerate
 };
 
+// One thread per (tensor set, bond).  With n = m0 . m1 and the Householder
+// reflector H = I - 2 v v^T / (v . v) of v = m1 / |m1| + sign(m1[0]) e0, the
+// gauge pair is B = [m0^T / n ; rows 1.. of H] and A = B^-1, whose column 0
+// is m1 and column l >= 1 is H[l, :]^T - m1 (H[l, :] . m0) / n.  Every entry
+// has a closed form in n, v and v . m0, so the FP64 work per bond is O(d^2)
+// multiply-adds and three divisions.  Only the d x d corner of each 8 x 8
+// slot is written; readers take no more.
 __global__ void gauge_kernel(GaugeParams p)
 {
     int64_t total = (int64_t)p.n_sets * p.n_bonds;
@@ -913,40 +919,42 @@ __global__ void gauge_kernel(GaugeParams p)
         const int d = p.bond_dim[b];
         const int s0 = p.bond_site[2 * b], s1 = p.bond_site[2 * b + 1];
         if (s1 < 0) {                      // open index: not partitioned
-            for (int e = 0; e < 64; ++e) { G0[e] = (e / 8 == e % 8) ? 1.0 : 0.0; G1[e] = G0[e]; }
+            for (int a = 0; a < d; ++a)
+                for (int c = 0; c < d; ++c) { const double x = (a == c) ? 1.0 : 0.0; G0[a * 8 + c] = x; G1[a * 8 + c] = x; }
             continue;
         }
         const double *base = p.msg + ((int64_t)p.final_buf[set] * p.n_sets + set) * p.n_legs * kMsgStride;
-        const double *m0 = base + (int64_t)(p.site_ptr[s0] + p.bond_leg[2 * b]) * kMsgStride;
-        const double *m1 = base + (int64_t)(p.site_ptr[s1] + p.bond_leg[2 * b + 1]) * kMsgStride;
+        const double *m0p = base + (int64_t)(p.site_ptr[s0] + p.bond_leg[2 * b]) * kMsgStride;
+        const double *m1p = base + (int64_t)(p.site_ptr[s1] + p.bond_leg[2 * b + 1]) * kMsgStride;
+        double m0[kMaxDim], m1[kMaxDim];
+#pragma unroll
+        for (int a = 0; a < kMaxDim; ++a) { m0[a] = a < d ? m0p[a] : 0.0; m1[a] = a < d ? m1p[a] : 0.0; }
         double n = 0.0, nm1 = 0.0;
-        for (int a = 0; a < d; ++a) { n = fma(m0[a], m1[a], n); nm1 = fma(m1[a], m1[a], nm1); }
+#pragma unroll
+        for (int a = 0; a < kMaxDim; ++a) { n = fma(m0[a], m1[a], n); nm1 = fma(m1[a], m1[a], nm1); }
         if (!(fabs(n) >= 1e-300) || !(nm1 > 0.0)) { atomicExch(p.flags + 1, 1); n = 1.0; nm1 = 1.0; }
-        nm1 = sqrt(nm1);
-        // Householder vector: v = m1/|m1| + sign(m1[0]) e0
-        double v[kMaxDim], vv = 0.0;
-        for (int a = 0; a < d; ++a) v[a] = m1[a] / nm1;
+        const double inv_nm1 = 1.0 / sqrt(nm1), inv_n = 1.0 / n;
+        double v[kMaxDim];
+#pragma unroll
+        for (int a = 0; a < kMaxDim; ++a) v[a] = m1[a] * inv_nm1;
         v[0] += (v[0] < 0.0) ? -1.0 : 1.0;
-        for (int a = 0; a < d; ++a) vv = fma(v[a], v[a], vv);
-        // B = [m0^T / n ; H[1..d-1, :]],  H = I - 2 v v^T / (v^T v)
-        double B[kMaxDim][kMaxDim];
-        for (int c = 0; c < d; ++c) B[0][c] = m0[c] / n;
-        for (int r = 1; r < d; ++r)
-            for (int c = 0; c < d; ++c) B[r][c] = ((r == c) ? 1.0 : 0.0) - 2.0 * v[r] * v[c] / vv;
-        // A = B^{-1}: column 0 = m1; column l = R_l^T - m1 (R_l . m0) / n
-        double Ainv[kMaxDim][kMaxDim];
-        for (int a = 0; a < d; ++a) Ainv[a][0] = m1[a];
-        for (int l = 1; l < d; ++l) {
-            double rm = 0.0;
-            for (int c = 0; c < d; ++c) rm = fma(B[l][c], m0[c], rm);
-            for (int a = 0; a < d; ++a) Ainv[a][l] = B[l][a] - m1[a] * rm / n;
-        }
-        for (int e = 0; e < 64; ++e) { G0[e] = 0.0; G1[e] = 0.0; }
-        for (int a = 0; a < d; ++a)
-            for (int c = 0; c < d; ++c) {
-                G0[a * 8 + c] = Ainv[a][c];      // s0: T'[.., c, ..] = sum_a T[.., a, ..] A[a][c]
-                G1[a * 8 + c] = B[c][a];         // s1: T'[.., c, ..] = sum_a T[.., a, ..] B[c][a]
+        double vv = 0.0, vm0 = 0.0;
+#pragma unroll
+        for (int a = 0; a < kMaxDim; ++a) { vv = fma(v[a], v[a], vv); vm0 = fma(v[a], m0[a], vm0); }
+        const double k2 = 2.0 / vv;
+#pragma unroll
+        for (int c = 0; c < kMaxDim; ++c) {
+            if (c >= d) break;
+            // H[c, :] . m0 / n for the A column c (c >= 1)
+            const double rc = (m0[c] - k2 * v[c] * vm0) * inv_n;
+#pragma unroll
+            for (int a = 0; a < kMaxDim; ++a) {
+                if (a >= d) break;
+                const double h = ((a == c) ? 1.0 : 0.0) - k2 * v[c] * v[a];     // H[c][a]
+                G1[a * 8 + c] = (c == 0) ? m0[a] * inv_n : h;                   // B[c][a]
+                G0[a * 8 + c] = (c == 0) ? m1[a] : h - m1[a] * rc;              // A[a][c]
             }
+        }
     }
 }
 
@@ -1139,9 +1147,8 @@ __global__ void block_ff_kernel(BlockParams p)
             const int d = cdims[i];
             post /= d;
             const double *G = p.gauge + (((int64_t)set * p.n_bonds_full + bonds[i]) * 2 + side[i]) * 64;
-            for (int q = lane; q < d * 8; q += 32) {
-                Gs[q] = split_scaled(G[q], 0);
-            }
+            for (int q = lane; q < d * 8; q += 32)
+                if ((q & 7) < d) Gs[q] = split_scaled(G[q], 0);
             __syncwarp();
             const float inv_post = 1.0f / (float)post;
             for (int e = lane; e < n; e += 32) {
