@@ -343,6 +343,34 @@ def main():
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["avg_launch_ms"] = avg_ms
     roof["kernel_shares"] = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()}
+    # context beside the dominant kernel: the contraction and BP sweeps against
+    # their own arithmetic roofs (event-timed in the same profiled steps)
+    others = {}
+    if "contract" in prof and fam != "contract":
+        ns, keep = pne.network_struct(g, data=data_dev, n_batch=B)
+        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0, BP_ARITH[args.bp]), ctypes_stream)
+        terms, _, _ = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, mode, 0), ctypes_stream)
+        if mode == pne.PNE_MODE_LOOP:
+            fma = pne.pne_terms_work(ctx.h, terms, ctypes_stream)
+            c_ms = prof["contract"][1] / prof_steps
+            pk = peak_f64 if args.dtype == "f64" else peak_f32
+            ach = 2.0 * fma * B / (c_ms * 1e-3) / 1e12
+            others["contract"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": pk / 1e12,
+                                  "frac": ach / (pk / 1e12), "ms_per_step": c_ms,
+                                  "work": f"2 flops per plan multiply-add; {fma} multiply-adds per network",
+                                  "peak_source": "measured FMA-chain kernel (pne_measure_fma_peak)"}
+        pne.pne_terms_destroy(terms); pne.pne_partition_destroy(part)
+    if "bp_sweeps" in prof and fam != "bp_sweeps" and args.bp == "ff":
+        iters = [r["bp_iters"] for r in res[:B]]
+        b_ms = prof["bp_sweeps"][1] / prof_steps
+        ach = algorithmic_bp_flops(g, iters) / (b_ms * 1e-3) / 1e12
+        others["bp_sweeps"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": peak_f32 / 16 / 1e12,
+                               "frac": ach / (peak_f32 / 16 / 1e12), "ms_per_step": b_ms,
+                               "work": f"4 flops per tensor entry per site per sweep; {sum(iters)} sweeps over {B} sets",
+                               "peak_source": "measured FP32 FMA-chain kernel / 16 FP32 instructions per "
+                                              "float-float multiply-add"}
+    if others:
+        roof["others"] = others
 
     out = {
         "metric": "PNE terms contracted/sec",

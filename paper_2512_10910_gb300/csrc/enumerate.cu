@@ -695,10 +695,15 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
     Node &nd = sh_node[w];
     const NodeTabs T{sh_a[w], sh_b[w], sh_ia[w], sh_ib[w], sh_tmask[w], sh_tw[w]};
     int32_t *stage = sh_stage[w];
+    // the counting and children passes take contiguous chunks (the child
+    // offsets are scanned per chunk); the others stride over the whole range,
+    // so the costly nodes of the deepest level spread over every block
+    constexpr bool chunked = pass == kCount || pass == kChildren;
     const int64_t chunk = (r1 - r0 + gridDim.x - 1) / gridDim.x;
-    const int64_t c0 = r0 + (int64_t)blockIdx.x * chunk;
-    const int64_t c1 = c0 + chunk < r1 ? c0 + chunk : r1;
-    for (int64_t u = c0 + w; u < c1; u += kExpandWarps) {
+    const int64_t c0 = chunked ? r0 + (int64_t)blockIdx.x * chunk : r0 + (int64_t)blockIdx.x * kExpandWarps;
+    const int64_t c1 = chunked ? (c0 + chunk < r1 ? c0 + chunk : r1) : r1;
+    const int64_t ustep = chunked ? kExpandWarps : (int64_t)gridDim.x * kExpandWarps;
+    for (int64_t u = c0 + w; u < c1; u += ustep) {
         // the writing passes replay the counting pass's decisions: nodes that
         // make nothing are skipped, and only the lanes with a set bit work
         uint64_t want = ~0ull;
@@ -739,12 +744,21 @@ __device__ void expand_chunk(const GeomView &g, const Arena &A, int64_t r0, int6
             }
             if (closing_children) {
                 // children are closing nodes: the twin table of closable2
-                for (int q = lane; q < nU; q += 32) {
-                    const int o = T.outside(q);
+                // (lanes of one round with the same outside end found by a
+                // match; the other round, when there is one, walked)
+                for (int i0 = 0; i0 < nU; i0 += 32) {
+                    const int q = i0 + lane;
+                    const int o = q < nU ? T.outside(q) : -2 - lane;
+                    const unsigned m = __match_any_sync(0xffffffffu, o) & ~(1u << lane);
                     int lw = -1;
-                    if (o >= 0)
-                        for (int f = 0; f < nU; ++f) lw = (f != q && T.outside(f) == o) ? f : lw;
-                    T.tw[q] = lw;
+                    if (o >= 0) {
+                        if (m) lw = i0 + 31 - __clz(m);
+                        if (i0 == 0)
+                            for (int f = 32; f < nU; ++f) lw = T.outside(f) == o ? f : lw;
+                        else if (!m)
+                            for (int f = 0; f < 32; ++f) lw = T.outside(f) == o ? f : lw;
+                    }
+                    if (q < nU) T.tw[q] = lw;
                 }
             }
             __syncwarp();
