@@ -580,9 +580,11 @@ def run_serve(args, wl, rank, world, local_rank):
     wall = time.perf_counter() - start
     clk = clocks.stop()
     lat, terms, batch, first, last = [], 0, [], None, None
+    failed = {}
     for rid in ids:
         st, res, info = pne.pne_server_poll(srv, rid)
         if st != pne.PNE_OK:
+            failed[int(st)] = failed.get(int(st), 0) + 1
             continue
         lat.append(info["t_done"] - info["t_arrival"])
         terms += res["n_terms"]
@@ -593,11 +595,15 @@ def run_serve(args, wl, rank, world, local_rank):
     pne.pne_server_destroy(srv)
     ctx.close()
     lat = np.array(lat)
+    if not len(lat):
+        print(json.dumps({"error": "no request completed", "failed_by_status": failed}), file=sys.stderr)
+        return 1
     span = last - first
     out = {"metric": "PNE terms contracted/sec", "value": terms / span, "unit": "terms/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * span, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": wl["desc"], "requests": len(ids), "completed": int(len(lat)),
+                      "failed_by_status": failed,
                       "offered_rate_req_s": wl["rate"], "trace_s": float(t_arr[-1]),
                       "served_req_s": len(lat) / span, "geometries_warmed": len(seen),
                       "device_budget_bytes": int(opts.device_budget_bytes), "peak_admitted_bytes": peak,
