@@ -847,16 +847,28 @@ __global__ void __launch_bounds__(kBpWarps * 32, 4) bp_ff_cluster_kernel(BPFFPar
 }
 
 // site tensors -> scaled float-float, one warp per (set, site)
-// FP64 tensors -> scaled float-float pairs, one warp per site: the largest
-// entry's exponent from the bits, then each entry split by integer operations
-// (split_scaled), so the conversion runs at memory speed rather than on the
-// FP64 pipe.
-__global__ void ff_tensor_kernel(const double *T, ff *out, const int64_t *tens_off, int n_sites, int n_sets, int64_t stride)
+// Set-up of the float-float sweeps in one launch, grid-stride: scratch words
+// cleared; first messages 1/sqrt(d) as pairs; and, one warp per site, the FP64
+// tensors as scaled float-float pairs -- the largest entry's exponent from the
+// bits, then each entry split by integer operations (split_scaled), so the
+// conversion runs at memory speed rather than on the FP64 pipe.
+__global__ void ff_prepare_kernel(const double *T, ff *out, const int64_t *tens_off, int n_sites, int n_sets,
+                                  int64_t stride, ff *msg, const int32_t *site_bonds, const int32_t *bond_dim,
+                                  int n_legs, uint32_t *scratch, int64_t scratch_words)
 {
     const int lane = threadIdx.x & 31;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < scratch_words; i += nth) scratch[i] = 0u;
+    const int64_t total = (int64_t)n_sets * n_legs;
+    for (int64_t i = tid; i < total; i += nth) {
+        const int d = bond_dim[site_bonds[i % n_legs]];
+        const double v = 1.0 / sqrt((double)d);
+        const float hi = __double2float_rn(v);
+        const float lo = __double2float_rn(v - (double)hi);
+        for (int a = 0; a < kMsgStride; ++a) msg[i * kMsgStride + a] = (a < d) ? ff{hi, lo} : ff{0.f, 0.f};
+    }
     const int64_t items = (int64_t)n_sets * n_sites;
-    for (int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < items;
-         item += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    for (int64_t item = tid >> 5; item < items; item += nth >> 5) {
         const int set = (int)(item / n_sites), v = (int)(item % n_sites);
         const double *t = T + set * stride + tens_off[v];
         ff *o = out + set * stride + tens_off[v];
@@ -866,18 +878,6 @@ __global__ void ff_tensor_kernel(const double *T, ff *out, const int64_t *tens_o
         for (int off = 16; off > 0; off >>= 1) mxb = max(mxb, __shfl_xor_sync(0xffffffffu, mxb, off));
         const int ex = mxb > 0 ? min(mxb - 1022, 1022) : 0;   // entries are below 2^ex
         for (int64_t e = lane; e < n; e += 32) o[e] = split_scaled(__ldg(t + e), ex);
-    }
-}
-
-__global__ void ff_init_kernel(ff *msg, const int32_t *site_bonds, const int32_t *bond_dim, int n_legs, int n_sets)
-{
-    const int64_t total = (int64_t)n_sets * n_legs;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int d = bond_dim[site_bonds[i % n_legs]];
-        const double v = 1.0 / sqrt((double)d);
-        const float hi = __double2float_rn(v);
-        const float lo = __double2float_rn(v - (double)hi);
-        for (int a = 0; a < kMsgStride; ++a) msg[i * kMsgStride + a] = (a < d) ? ff{hi, lo} : ff{0.f, 0.f};
     }
 }
 
@@ -1261,10 +1261,26 @@ int grid_for(int64_t n, int block, int n_sm)
 }  // namespace
 
 // ---------------------------------------------------------------- host launchers
-pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, double damping,
-                     cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags, int arithmetic,
-                     cudaMemcpyKind rec_kind)
+namespace {
+
+// Raises a kernel's dynamic shared-memory limit once per context and size
+// (slot: one per kernel).
+template <typename F>
+void grant_smem(pne_ctx *ctx, int slot, F func, size_t bytes)
 {
+    if (bytes <= 48 * 1024) return;
+    std::lock_guard<std::mutex> lk(ctx->launch_mu);
+    if (bytes <= ctx->bp_smem_set[slot]) return;
+    cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    ctx->bp_smem_set[slot] = bytes;
+}
+
+}  // namespace
+
+pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, double damping,
+                     cudaStream_t s, void *rec, int arithmetic, cudaMemcpyKind rec_kind)
+{
+    HostScope hs__(ctx, "part_bp");
     const Geometry &g = p->geo->full;
     const int n_sets = p->n_sets;
     // table sizes: halves of the largest site
@@ -1285,40 +1301,43 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         set_error(ctx, PNE_EINVAL, "site tensor too large for the BP kernel");
         return PNE_EINVAL;
     }
-    // scratch: res[4][n_sets] u64, res_out [n_sets] f64, done/iters/final [n_sets] i32,
-    // flags[4] i32, barrier[2] u32
+    // scratch: res[4][n_sets] u64, then the convergence record as it is read
+    // back -- res_out [n_sets] f64, flags[4] i32, iters [n_sets] i32 -- then
+    // done/final [n_sets] i32, barrier[2] u32; in float-float arithmetic the
+    // pair tensors and pair messages follow (one allocation)
+    const size_t rec_bytes = (size_t)n_sets * 12 + 16;
+    const size_t bytes = ((4 * n_sets * 8 + rec_bytes + 2 * n_sets * 4 + 8) + 255) & ~size_t(255);
+    const int64_t stride = g.tens_off[g.n_sites];
+    const size_t tbytes = arithmetic == 1 ? (size_t)n_sets * stride * sizeof(ff) : 0;
+    const size_t mbytes = arithmetic == 1 ? (size_t)2 * n_sets * g.n_legs * kMsgStride * sizeof(ff) : 0;
     DevBuf scratch;
-    const size_t bytes = 4 * n_sets * 8 + n_sets * 8 + 3 * n_sets * 4 + 16 + 8 + 64;
-    pne_status st = dev_alloc(ctx, scratch, bytes, s);
+    pne_status st = dev_alloc(ctx, scratch, bytes + tbytes + mbytes, s);
     if (st) return st;
     char *base = (char *)scratch.ptr;
     unsigned long long *res = (unsigned long long *)base;
-    double *res_out = (double *)(base + 4 * n_sets * 8);
-    int32_t *done = (int32_t *)(base + 5 * n_sets * 8);
-    int32_t *iters = done + n_sets;
-    int32_t *finalb = iters + n_sets;
-    int32_t *flags = finalb + n_sets;
-    unsigned int *bar = (unsigned int *)(flags + 4);
-    cudaError_t e = cudaMemsetAsync(scratch.ptr, 0, bytes, s);
-    if (e != cudaSuccess) { dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, e); }
+    char *rec_dev = base + 4 * n_sets * 8;
+    double *res_out = (double *)rec_dev;
+    int32_t *flags = (int32_t *)(rec_dev + n_sets * 8);
+    int32_t *iters = flags + 4;
+    int32_t *done = iters + n_sets;
+    int32_t *finalb = done + n_sets;
+    unsigned int *bar = (unsigned int *)(finalb + n_sets);
+    cudaError_t e;
 
     double *msg = (double *)p->msg.ptr;
-    DevBuf ffbuf;
     if (arithmetic == 1) {
-        // float-float sweeps: pair tensors and pair messages in scratch, the
-        // final messages exported to the FP64 buffer for the gauge
-        const int64_t stride = g.tens_off[g.n_sites];
-        const size_t tbytes = (size_t)n_sets * stride * sizeof(ff);
-        const size_t mbytes = (size_t)2 * n_sets * g.n_legs * kMsgStride * sizeof(ff);
-        if ((st = dev_alloc(ctx, ffbuf, tbytes + mbytes, s))) { dev_free(ctx, scratch, s); return st; }
-        ff *Tff = (ff *)ffbuf.ptr;
-        ff *mff = (ff *)((char *)ffbuf.ptr + tbytes);
+        // float-float sweeps: pair tensors and pair messages after the
+        // scratch words, the final messages exported to the FP64 buffer for
+        // the gauge; one launch converts the tensors, sets the first messages
+        // and clears the scratch words
+        ff *Tff = (ff *)(base + bytes);
+        ff *mff = (ff *)(base + bytes + tbytes);
         {
             ProfScope ps(ctx, s, "bp_init");
-            ff_tensor_kernel<<<grid_for((int64_t)n_sets * g.n_sites * 32, 256, ctx->n_sm), 256, 0, s>>>(
-                (const double *)p->T.ptr, Tff, g.d_tens_off, g.n_sites, n_sets, stride);
-            ff_init_kernel<<<grid_for((int64_t)n_sets * g.n_legs, 256, ctx->n_sm), 256, 0, s>>>(
-                mff, g.d_site_bonds, g.d_bond_dim, g.n_legs, n_sets);
+            const int64_t warps = (int64_t)n_sets * g.n_sites;
+            ff_prepare_kernel<<<grid_for(warps * 32, 256, ctx->n_sm), 256, 0, s>>>(
+                (const double *)p->T.ptr, Tff, g.d_tens_off, g.n_sites, n_sets, stride, mff, g.d_site_bonds,
+                g.d_bond_dim, g.n_legs, (uint32_t *)base, (int64_t)(bytes / 4));
         }
         BPFFParams fp;
         fp.n_sets = n_sets; fp.n_sites = g.n_sites; fp.n_legs = g.n_legs;
@@ -1339,9 +1358,7 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute cattr[1];
         if (cluster_ok) {
-            cudaFuncSetAttribute(bp_ff_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            if (smem > 48 * 1024)
-                cudaFuncSetAttribute(bp_ff_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            grant_smem(ctx, 0, bp_ff_cluster_kernel, smem);
             cfg.blockDim = dim3(kBpWarps * 32);
             cfg.dynamicSmemBytes = smem;
             cfg.stream = s;
@@ -1350,26 +1367,60 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
             cattr[0].val.clusterDim.z = 1;
             cfg.attrs = cattr;
             cfg.numAttrs = 1;
-            // the largest cluster the device schedules with this kernel's resources
-            for (;;) {
+            // the largest cluster the device schedules with this kernel's
+            // resources (queried once per context, shared memory and size)
+            const std::pair<size_t, int> key{smem, CL};
+            int chosen = -1;
+            {
+                std::lock_guard<std::mutex> lk(ctx->launch_mu);
+                auto it = ctx->bp_cluster.find(key);
+                if (it != ctx->bp_cluster.end()) chosen = it->second;
+            }
+            if (chosen < 0) {
+                cudaFuncSetAttribute(bp_ff_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+                chosen = 0;
+                for (int cl = CL;;) {
+                    cattr[0].val.clusterDim.x = cl;
+                    cfg.gridDim = dim3(cl);
+                    int ncl = 0;
+                    if (cudaOccupancyMaxActiveClusters(&ncl, (void *)bp_ff_cluster_kernel, &cfg) == cudaSuccess && ncl > 0) {
+                        chosen = cl;
+                        break;
+                    }
+                    cudaGetLastError();
+                    if (cl == 1) break;
+                    cl /= 2;
+                    if (max_color > cl * kBpWarps * 4) break;
+                }
+                std::lock_guard<std::mutex> lk(ctx->launch_mu);
+                ctx->bp_cluster[key] = chosen;
+            }
+            if (chosen > 0) {
+                CL = chosen;
                 cattr[0].val.clusterDim.x = CL;
-                cfg.gridDim = dim3(CL);
-                int ncl = 0;
-                if (cudaOccupancyMaxActiveClusters(&ncl, (void *)bp_ff_cluster_kernel, &cfg) == cudaSuccess && ncl > 0) break;
-                cudaGetLastError();
-                if (CL == 1) { cluster_ok = false; break; }
-                CL /= 2;
-                if (max_color > CL * kBpWarps * 4) { cluster_ok = false; break; }
+            } else {
+                cluster_ok = false;
             }
         }
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(bp_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int per_sm_ff = 0;
-        PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_ff, bp_ff_kernel, kBpWarps * 32, smem));
-        if (per_sm_ff < 1) { dev_free(ctx, ffbuf, s); dev_free(ctx, scratch, s); set_error(ctx, PNE_EINVAL, "BP kernel does not fit"); return PNE_EINVAL; }
-        const int64_t items_ff = (int64_t)n_sets * g.n_sites;
-        const int64_t want_ff = (items_ff + kBpWarps - 1) / kBpWarps, cap_ff = (int64_t)per_sm_ff * ctx->n_sm;
-        const int nb_ff = (int)std::max<int64_t>(1, want_ff < cap_ff ? want_ff : cap_ff);
+        int nb_ff = 1;
+        if (!cluster_ok) {
+            grant_smem(ctx, 1, bp_ff_kernel, smem);
+            int per_sm_ff = 0;
+            {
+                std::lock_guard<std::mutex> lk(ctx->launch_mu);
+                auto it = ctx->bp_grid_occ.find(smem);
+                if (it != ctx->bp_grid_occ.end()) per_sm_ff = it->second;
+            }
+            if (per_sm_ff == 0) {
+                PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_ff, bp_ff_kernel, kBpWarps * 32, smem));
+                std::lock_guard<std::mutex> lk(ctx->launch_mu);
+                ctx->bp_grid_occ[smem] = per_sm_ff;
+            }
+            if (per_sm_ff < 1) { dev_free(ctx, scratch, s); set_error(ctx, PNE_EINVAL, "BP kernel does not fit"); return PNE_EINVAL; }
+            const int64_t items_ff = (int64_t)n_sets * g.n_sites;
+            const int64_t want_ff = (items_ff + kBpWarps - 1) / kBpWarps, cap_ff = (int64_t)per_sm_ff * ctx->n_sm;
+            nb_ff = (int)std::max<int64_t>(1, want_ff < cap_ff ? want_ff : cap_ff);
+        }
         void *fargs[] = {&fp};
         cudaError_t fe;
         {
@@ -1381,7 +1432,7 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
                 fe = cudaLaunchCooperativeKernel((void *)bp_ff_kernel, dim3(nb_ff), dim3(kBpWarps * 32), fargs, smem, s);
             }
         }
-        if (fe != cudaSuccess) { dev_free(ctx, ffbuf, s); dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, fe); }
+        if (fe != cudaSuccess) { dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, fe); }
         {
             ProfScope ps(ctx, s, "bp_export");
             ff_export_kernel<<<grid_for((int64_t)n_sets * g.n_legs * kMsgStride, 256, ctx->n_sm), 256, 0, s>>>(
@@ -1390,6 +1441,8 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         PNE_CUDA_TRY(ctx, cudaGetLastError());
     }
     if (arithmetic != 1) {
+    e = cudaMemsetAsync(scratch.ptr, 0, bytes, s);
+    if (e != cudaSuccess) { dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, e); }
     {
         ProfScope ps(ctx, s, "bp_init");
         bp_init_kernel<<<grid_for((int64_t)n_sets * g.n_legs, 256, ctx->n_sm), 256, 0, s>>>(
@@ -1407,8 +1460,7 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
     prm.smem_per_warp = per_warp; prm.tabA = tabA; prm.tabC = tabC;
     prm.n_colors = g.n_colors; prm.color_ptr = g.d_color_ptr; prm.color_sites = g.d_color_sites;
 
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(bp_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    grant_smem(ctx, 2, bp_persistent_kernel, smem);
     int per_sm = 0;
     PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bp_persistent_kernel,
                                                                      kBpWarps * 32, smem));
@@ -1426,10 +1478,6 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
     }
     if (e != cudaSuccess) { dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, e); }
     }
-    // copy out the convergence record
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_iters, iters, n_sets * 4, rec_kind, s));
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_res, res_out, n_sets * 8, rec_kind, s));
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_flags, flags, 8, rec_kind, s));
     // the final-buffer index stays on the device for the gauge kernel
     if (p->gauge.ptr == nullptr) { dev_free(ctx, scratch, s); return PNE_EINVAL; }
     GaugeParams gp;
@@ -1442,42 +1490,26 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         gauge_kernel<<<grid_for((int64_t)n_sets * g.n_bonds, 128, ctx->n_sm), 128, 0, s>>>(gp);
     }
     PNE_CUDA_TRY(ctx, cudaGetLastError());
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_flags + 2, flags, 8, rec_kind, s));
-    dev_free(ctx, ffbuf, s);
+    // the convergence record (residuals, flags of BP and the gauge, sweeps) in one copy
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(rec, rec_dev, rec_bytes, rec_kind, s));
     dev_free(ctx, scratch, s);
     return PNE_OK;
 }
 
 pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t *h_flag)
 {
+    HostScope hs__(ctx, "part_gauge");
     (void)h_flag;
     const Geometry &f = p->geo->full, &c = p->geo->closed;
-    int nmax = 1;
-    for (int v = 0; v < f.n_sites; ++v) {
-        int n = 1;
-        for (int i = f.site_ptr[v]; i < f.site_ptr[v + 1]; ++i) n *= f.bond_dim[f.site_bonds[i]];
-        nmax = nmax > n ? nmax : n;
-    }
+    const int nmax = p->geo->gauge_nmax;
     if (nmax > 4096) { set_error(ctx, PNE_EINVAL, "site tensor larger than 4096 entries"); return PNE_EINVAL; }
     const int half = nmax < 32 ? 32 : nmax;
     int wpb = (int)((48 * 1024) / (2 * half * sizeof(double)));
     if (wpb > 8) wpb = 8;
     if (wpb < 1) wpb = 1;
     const size_t smem = (size_t)wpb * 2 * half * sizeof(double);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    // device table of open positions and dims
-    std::vector<int32_t> open_pos(f.n_bonds, -1);
-    for (size_t q = 0; q < p->geo->open_bonds.size(); ++q) open_pos[p->geo->open_bonds[q]] = (int32_t)q;
-    DevBuf tab;
-    const size_t tb = (f.n_bonds + p->geo->open_dims.size() + 1) * 4;
-    pne_status st = dev_alloc(ctx, tab, tb, s);
-    if (st) return st;
-    int32_t *d_open_pos = (int32_t *)tab.ptr, *d_open_dims = d_open_pos + f.n_bonds;
-    std::vector<int32_t> h(open_pos);
-    h.insert(h.end(), p->geo->open_dims.begin(), p->geo->open_dims.end());
-    h.push_back(0);
-    if ((st = upload(ctx, tab.ptr, h.data(), tb, s))) return st;
+    // geometry table of open positions and dims (built with the geometry)
+    const int32_t *d_open_pos = (const int32_t *)p->geo->gauge_tab.ptr, *d_open_dims = d_open_pos + f.n_bonds;
     BlockParams bp;
     bp.n_sets = p->n_sets; bp.n_slices = p->n_slices; bp.n_sites = f.n_sites;
     bp.n_bonds_full = f.n_bonds; bp.n_open = (int)p->geo->open_bonds.size();
@@ -1497,9 +1529,10 @@ pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t 
         ProfScope ps(ctx, s, "gauge_block");
         if (p->arithmetic == 1) {
             const size_t smem_ff = smem + (size_t)wpb * 64 * sizeof(ff);   // plus one gauge matrix per warp
-            if (smem_ff > 48 * 1024) cudaFuncSetAttribute(block_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ff);
+            grant_smem(ctx, 3, block_ff_kernel, smem_ff);
             block_ff_kernel<<<(int)g, wpb * 32, smem_ff, s>>>(bp);
         } else {
+            grant_smem(ctx, 4, block_kernel, smem);
             block_kernel<<<(int)g, wpb * 32, smem, s>>>(bp);
         }
     }
@@ -1510,7 +1543,6 @@ pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t 
                                                                     p->n_members, (double *)p->vac.ptr);
     }
     PNE_CUDA_TRY(ctx, cudaGetLastError());
-    dev_free(ctx, tab, s);
     return PNE_OK;
 }
 
@@ -1734,8 +1766,12 @@ extern "C" pne_status pne_bp_messages_noalloc(const pne_network *net, double tol
     prm.final_buf = finalb; prm.flags = flags; prm.bar = bar;
     prm.smem_per_warp = per_warp; prm.tabA = tabA; prm.tabC = tabC;
     prm.n_colors = 0; prm.color_ptr = nullptr; prm.color_sites = nullptr;   // Jacobi sweeps, two buffers
-    if (smem > 48 * 1024)
-        PNE_CUDA_TRY(nullptr, cudaFuncSetAttribute(bp_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) {
+        // only ever raised: a context may have granted this kernel more already
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, bp_persistent_kernel) != cudaSuccess || fa.maxDynamicSharedSizeBytes < (int)smem)
+            PNE_CUDA_TRY(nullptr, cudaFuncSetAttribute(bp_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
     int per_sm = 0;
     PNE_CUDA_TRY(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bp_persistent_kernel, kBpWarps * 32, smem));
     if (per_sm < 1) { set_error(nullptr, PNE_EINVAL, "BP kernel does not fit"); return PNE_EINVAL; }

@@ -164,7 +164,9 @@ HostScope::HostScope(pne_ctx *c, const char *n) : ctx(c), name(n)
     t0 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-HostScope::~HostScope()
+HostScope::~HostScope() { stop(); }
+
+void HostScope::stop()
 {
     if (t0 < 0.0) return;
     const double t1 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -174,6 +176,7 @@ HostScope::~HostScope()
     e.second += t1 - t0;
     if (ctx->prof.trace && ctx->prof.host_trace.size() < kTraceMax)
         ctx->prof.host_trace.push_back({name, t0 - ctx->prof.host_base, t1 - ctx->prof.host_base});
+    t0 = -1.0;
 }
 
 EnumRecord::~EnumRecord()
@@ -498,6 +501,21 @@ pne_status get_geometry(pne_ctx *ctx, const pne_network *net, cudaStream_t s, st
     }
     pne_status st;
     if ((st = finish_geometry(ctx, f, s)) || (st = finish_geometry(ctx, c, s))) return st;
+    {
+        // gauge-transform table: open position per full bond, then the open dims
+        for (int v = 0; v < N; ++v) {
+            int n = 1;
+            for (int i = f.site_ptr[v]; i < f.site_ptr[v + 1]; ++i) n *= f.bond_dim[f.site_bonds[i]];
+            gp->gauge_nmax = std::max(gp->gauge_nmax, n);
+        }
+        std::vector<int32_t> h(M, -1);
+        for (size_t q = 0; q < gp->open_bonds.size(); ++q) h[gp->open_bonds[q]] = (int32_t)q;
+        h.insert(h.end(), gp->open_dims.begin(), gp->open_dims.end());
+        h.push_back(0);
+        if ((st = dev_alloc(ctx, gp->gauge_tab, h.size() * 4, s)) ||
+            (st = upload(ctx, gp->gauge_tab.ptr, h.data(), h.size() * 4, s)))
+            return st;
+    }
     PNE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&gp->ready, cudaEventDisableTiming));
     PNE_CUDA_TRY(ctx, cudaEventRecord(gp->ready, s));
     {
@@ -516,6 +534,7 @@ GeomPair::~GeomPair()
     if (!ctx) return;
     dev_free(ctx, full.storage, free_stream);
     dev_free(ctx, closed.storage, free_stream);
+    dev_free(ctx, gauge_tab, free_stream);
 }
 
 pne_status partition_record(pne_ctx *ctx, pne_partition *p, const char *rec)
@@ -622,8 +641,11 @@ pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_p
     HostScope hs__(ctx, "partition");
     if (!ctx || !out) return PNE_EINVAL;
     *out = nullptr;
-    pne_status st = validate(ctx, net);
-    if (st) return st;
+    pne_status st;
+    {
+        HostScope hv__(ctx, "part_validate");
+        if ((st = validate(ctx, net))) return st;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     double tol = (opts && opts->tol > 0) ? opts->tol : 1e-13;
     int max_iter = (opts && opts->max_iter > 0) ? opts->max_iter : 10000;
@@ -644,16 +666,23 @@ pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_p
     p->n_members = p->n_sets * p->n_slices;
     const int64_t fstride = f.tens_off[N], cstride = c.tens_off[N];
     const size_t B = p->n_sets, Bm = p->n_members;
-    if ((st = dev_alloc(ctx, p->T, B * fstride * 8, s)) ||
-        (st = dev_alloc(ctx, p->msg, 2 * B * f.n_legs * kMsgStride * 8, s)) ||
-        (st = dev_alloc(ctx, p->gauge, B * std::max(M, 1) * 2 * 64 * 8, s)) ||
-        (st = dev_alloc(ctx, p->Mb, Bm * cstride * 8, s)) ||
-        (st = dev_alloc(ctx, p->site_info, Bm * N * 8, s)) ||
-        (st = dev_alloc(ctx, p->site_scale, Bm * N * 8, s)) ||
-        (st = dev_alloc(ctx, p->site_zero, Bm * N, s)) ||
-        (st = dev_alloc(ctx, p->vac, Bm * 3 * 8, s))) {
-        pne_partition_destroy(p);
-        return st;
+    HostScope ha__(ctx, "part_alloc");
+    {
+        // one allocation, carved into the partition's buffers (256-byte aligned)
+        DevBuf *parts[] = {&p->T, &p->msg, &p->gauge, &p->Mb, &p->site_info, &p->site_scale, &p->vac,
+                           &p->rec_dev, &p->site_zero};
+        const size_t sizes[] = {B * fstride * 8, 2 * B * f.n_legs * kMsgStride * 8, B * std::max(M, 1) * 2 * 64 * 8,
+                                Bm * cstride * 8, Bm * N * 8, Bm * N * 8, Bm * 3 * 8,
+                                (opts && opts->async_status) ? B * 12 + 16 : 0, Bm * N};
+        size_t total = 0;
+        for (size_t i = 0; i < sizeof sizes / sizeof sizes[0]; ++i) total += (sizes[i] + 255) & ~size_t(255);
+        if ((st = dev_alloc(ctx, p->storage, total, s))) { pne_partition_destroy(p); return st; }
+        char *at = (char *)p->storage.ptr;
+        for (size_t i = 0; i < sizeof sizes / sizeof sizes[0]; ++i) {
+            parts[i]->ptr = sizes[i] ? at : nullptr;
+            parts[i]->bytes = sizes[i];
+            at += (sizes[i] + 255) & ~size_t(255);
+        }
     }
     // input tensors: a host or device source, in one copy
     {
@@ -662,6 +691,7 @@ pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_p
                                         net->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) { pne_partition_destroy(p); set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return PNE_ECUDA; }
     }
+    ha__.stop();
     p->bp_iters.assign(B, 0);
     p->bp_residual.assign(B, 0.0);
     // convergence record: read back with the final synchronisation
@@ -677,11 +707,8 @@ pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_p
     p->arithmetic = arith;
     if (opts && opts->async_status) {
         // deferred record: kept on the device, read by the next synchronising call
-        if ((st = dev_alloc(ctx, p->rec_dev, B * 12 + 16, s))) { pne_partition_destroy(p); return st; }
         char *rd = (char *)p->rec_dev.ptr;
-        if (cudaMemsetAsync(rd, 0, B * 12 + 16, s) != cudaSuccess ||
-            (st = launch_bp(ctx, p, tol, max_iter, damping, s, (int32_t *)(rd + B * 8 + 16), (double *)rd,
-                            (int32_t *)(rd + B * 8), arith, cudaMemcpyDeviceToDevice)) ||
+        if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, rd, arith, cudaMemcpyDeviceToDevice)) ||
             (st = launch_gauge(ctx, p, s, nullptr))) {
             pne_partition_destroy(p);
             return st ? st : PNE_ECUDA;
@@ -690,7 +717,7 @@ pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_p
         *out = p;
         return PNE_OK;
     }
-    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, h_iters, h_res, flags, arith)) ||
+    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, rb, arith)) ||
         (st = launch_gauge(ctx, p, s, nullptr))) {
         pne_partition_destroy(p);
         return st;
@@ -719,8 +746,9 @@ void pne_partition_destroy(pne_partition *p)
     if (!p) return;
     pne_ctx *ctx = p->ctx;
     cudaStream_t s = p->last_stream;
-    DevBuf *bufs[] = {&p->T, &p->msg, &p->gauge, &p->Mb, &p->site_info, &p->site_scale, &p->site_zero,
-                      &p->vac, &p->Mb32, &p->Mb16, &p->rec_dev};
+    // the partition's buffers are views of one allocation; the converted
+    // copies are allocated on demand
+    DevBuf *bufs[] = {&p->storage, &p->Mb32, &p->Mb16};
     for (DevBuf *b : bufs) dev_free(ctx, *b, s);
     if (p->geo) p->geo->free_stream = s;          // a geometry left without users is freed on this stream
     delete p;
@@ -942,7 +970,7 @@ pne_status pne_partition_update(pne_ctx *ctx, pne_partition *p, const double *da
     const int arith = opts ? opts->arithmetic : p->arithmetic;
     if (arith != 0 && arith != 1) { set_error(ctx, PNE_EINVAL, "arithmetic must be 0 or 1"); return PNE_EINVAL; }
     p->arithmetic = arith;
-    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, h_iters, h_res, flags, arith)) ||
+    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, rb, arith)) ||
         (st = launch_gauge(ctx, p, s, nullptr)))
         return st;
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));

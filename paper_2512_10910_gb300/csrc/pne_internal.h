@@ -145,6 +145,12 @@ struct pne_ctx {
     std::map<std::string, std::shared_ptr<pne::EnumRecord>> enum_cache;
     std::map<std::string, int64_t> arena_hint;   // search-arena size that fitted, per (geometry, K, mode)
     std::map<uint64_t, std::vector<std::shared_ptr<pne::GeomPair>>> geom_cache;   // by input-array hash
+    // BP launch decisions per dynamic shared-memory size: the cluster size the
+    // device schedules (0: none) and the blocks per SM of the grid form
+    std::map<std::pair<size_t, int>, int> bp_cluster;
+    std::map<size_t, int> bp_grid_occ;
+    size_t bp_smem_set[6] = {0, 0, 0, 0, 0, 0};   // largest dynamic shared memory granted per BP/gauge kernel
+    std::mutex launch_mu;
     std::mutex cache_mu;
     // scratch for small device-side status words
     int32_t *d_status = nullptr;
@@ -171,6 +177,10 @@ struct GeomPair {
     uint64_t key = 0;                    // hash of the input arrays
     cudaStream_t free_stream = nullptr;  // stream of the last partition that used it
     cudaEvent_t ready = nullptr;         // recorded after the device copies were queued
+    // gauge-transform table (open position per full bond, then the open dims)
+    // and the largest site tensor, fixed by the geometry
+    DevBuf gauge_tab;
+    int gauge_nmax = 1;
     ~GeomPair();
 };
 }  // namespace pne
@@ -181,6 +191,7 @@ struct pne_partition {
     int n_sets = 1;                  // tensor sets (n_batch)
     int n_slices = 1;                // prod of open dims
     int n_members = 1;               // n_sets * n_slices
+    pne::DevBuf storage;             // one allocation holding the buffers below (views, not owners)
     pne::DevBuf T;                   // [n_sets][full.tens_off[N]] raw FP64
     pne::DevBuf msg;                 // [2][n_sets][full.n_legs][8]
     pne::DevBuf gauge;               // [n_sets][full.n_bonds][2][64] leg matrices
@@ -281,12 +292,17 @@ struct HostScope {
     double t0 = -1.0;
     HostScope(pne_ctx *c, const char *n);
     ~HostScope();
+    void stop();          // end the stretch early (the destructor then records nothing)
 };
 
 // ------------------------------------------------------------------ kernels
 // BP, gauge, blocked layout (bp.cu)
+// `rec` receives the convergence record, [n_sets] residuals (f64), 4 flags
+// (i32: grid-barrier timeout, zero message or overlap, 0, 0), [n_sets] sweeps
+// (i32); host memory (read after the stream synchronises) or, with
+// cudaMemcpyDeviceToDevice, device memory.
 pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, double damping,
-                     cudaStream_t s, int32_t *h_iters, double *h_res, int32_t *h_flags, int arithmetic = 0,
+                     cudaStream_t s, void *rec, int arithmetic = 0,
                      cudaMemcpyKind rec_kind = cudaMemcpyDeviceToHost);
 // read a deferred convergence record (synchronises the partition's stream)
 pne_status partition_settle(pne_ctx *ctx, pne_partition *p);

@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import math
+import collections.abc
 import os
 
 import numpy as np
@@ -413,7 +414,34 @@ def pne_sum(ctx, terms, stream=None, allow_noconv=False):
     st = load_library().pne_sum(ctx, terms, stream, out)
     if not (st == PNE_ENOCONV and allow_noconv):
         _check(st, ctx)
-    return [r.as_dict() for r in out]
+    return Results(out)
+
+
+class Results(collections.abc.Sequence):
+    """The results of a pne_sum call as a sequence of dicts (``Result.as_dict``).
+    The values are already in host memory; each dict is built on first access."""
+
+    def __init__(self, arr):
+        self._arr = arr
+        self._dicts = {}
+
+    def __len__(self):
+        return len(self._arr)
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self[j] for j in range(*i.indices(len(self)))]
+        if i < 0:
+            i += len(self)
+        if not 0 <= i < len(self):
+            raise IndexError(i)
+        d = self._dicts.get(i)
+        if d is None:
+            d = self._dicts[i] = self._arr[i].as_dict()
+        return d
+
+    def __repr__(self):
+        return repr(list(self))
 
 
 # ------------------------------------------------------------------ marshalling helpers

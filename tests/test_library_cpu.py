@@ -71,3 +71,22 @@ def test_tensor_offsets_match_per_site_leg_products():
         want = [int(np.prod(g.leg_dims(v))) for v in range(g.n_sites)]
         assert list(sizes) == want
         assert off[0] == 0 and list(np.diff(off)) == want
+
+
+def test_results_sequence_converts_on_access():
+    arr = (pne.Result * 3)()
+    for i in range(3):
+        arr[i].log_abs = float(i)
+        arr[i].n_orders = 2
+        arr[i].c[0], arr[i].c[1] = 1.0, 0.5 * i
+    res = pne.Results(arr)
+    assert len(res) == 3
+    assert res[-1]["log_abs"] == 2.0 and res[0]["log_abs"] == 0.0
+    assert [r["log_abs"] for r in res] == [0.0, 1.0, 2.0]
+    assert [r["log_abs"] for r in res[1:]] == [1.0, 2.0]
+    assert list(res[2]["c"]) == [1.0, 1.0]
+    assert res[1] is res[1]                       # built once
+    (a, b, c) = res
+    assert c["log_abs"] == 2.0
+    with pytest.raises(IndexError):
+        res[3]
