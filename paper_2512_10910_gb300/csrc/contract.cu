@@ -1068,11 +1068,16 @@ pne_status dispatch_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRec
 // Shape preparation, first half: hash every cluster's local structure and
 // queue the hashes' readback (no synchronisation; the caller's next
 // synchronisation of `s` brings them).
+bool shapes_needed(const Geometry &g, const EnumRecord &rec)
+{
+    return rec.n_clusters > 0 && !all_dims_two(g);
+}
+
 pne_status shapes_begin(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s)
 {
     rec.shaped = false;
     sp.active = false;
-    if (rec.n_clusters == 0 || all_dims_two(g)) return PNE_OK;
+    if (!shapes_needed(g, rec)) return PNE_OK;
     const int64_t n = (int64_t)rec.n_clusters;
     ContractParams cp;
     cp.n_clusters = n; cp.n_members = 1; cp.n_sites = g.n_sites;
@@ -1093,99 +1098,153 @@ pne_status shapes_begin(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapeP
     return PNE_OK;
 }
 
-// Second half: shape ids, exact-key verification, one plan per shape, and the
-// clusters grouped by shape.
-pne_status shapes_finish(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s)
+namespace {
+
+ContractParams shape_params(const Geometry &g, const EnumRecord &rec)
 {
-    if (!sp.active) return PNE_OK;
-    sp.active = false;
-    const int64_t n = (int64_t)rec.n_clusters;
     ContractParams cp;
-    cp.n_clusters = n; cp.n_members = 1; cp.n_sites = g.n_sites;
+    cp.n_clusters = (int64_t)rec.n_clusters; cp.n_members = 1; cp.n_sites = g.n_sites;
     cp.width = rec.width; cp.vwidth = rec.vwidth;
     cp.cl_edges = (const int32_t *)rec.cl_edges.ptr; cp.cl_verts = (const int32_t *)rec.cl_verts.ptr;
     cp.cl_size = (const int32_t *)rec.cl_size.ptr;
     cp.bond_site = g.d_bond_site; cp.bond_dim = g.d_bond_dim; cp.bond_leg = g.d_bond_leg;
-    DevBuf &dh = sp.dh;
+    return cp;
+}
+
+// One plan per representative, its statistics [steps, multiply-adds, largest
+// output, 0] (and, with_bad, the verification flags) read back into pinned
+// memory -- queued, or read at once when no pinned memory is available.
+pne_status plans_launch(pne_ctx *ctx, const ContractParams &cp, EnumRecord &rec, ShapePrep &sp, bool with_bad,
+                        cudaStream_t s)
+{
+    const int64_t n = cp.n_clusters;
+    const int ns = sp.ns;
+    dev_free(ctx, rec.plans, s);
+    dev_free(ctx, rec.plan_steps, s);
+    dev_free(ctx, sp.dstats, s);
+    pne_status e;
+    if ((e = dev_alloc(ctx, rec.plans, (size_t)ns * kPlanInts * 4, s)) ||
+        (e = dev_alloc(ctx, rec.plan_steps, (size_t)ns * 4, s)) || (e = dev_alloc(ctx, sp.dstats, (size_t)ns * 16, s)))
+        return e;
+    const size_t smem = (size_t)kCtWarps * kPlanWarpInts * 4;
+    shape_plan_kernel<<<grid_for(ns, kCtWarps, ctx->n_sm, 16), kCtWarps * 32, smem, s>>>(
+        cp, (const int32_t *)sp.drep.ptr, ns, (int32_t *)rec.plans.ptr, (int32_t *)rec.plan_steps.ptr,
+        (int32_t *)sp.dstats.ptr);
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    sp.stats.assign((size_t)ns * 4, 0);
+    sp.nb = with_bad ? (size_t)n * 4 : 0;
+    const size_t sb = sp.stats.size() * 4;
+    sp.hp = (char *)pinned_slot(3, sp.nb + sb);
+    if (sp.hp) {
+        if (sp.nb) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(sp.hp, sp.dbad.ptr, sp.nb, cudaMemcpyDeviceToHost, s));
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(sp.hp + sp.nb, sp.dstats.ptr, sb, cudaMemcpyDeviceToHost, s));
+    } else {
+        if (sp.nb) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(sp.bad.data(), sp.dbad.ptr, sp.nb, cudaMemcpyDeviceToHost, s));
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(sp.stats.data(), sp.dstats.ptr, sb, cudaMemcpyDeviceToHost, s));
+        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    }
+    return PNE_OK;
+}
+
+pne_status plans_read(pne_ctx *ctx, ShapePrep &sp, cudaStream_t s)
+{
+    if (!sp.hp) return PNE_OK;
+    {
+        HostScope hw__(ctx, "sync_plans");
+        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    }
+    if (sp.nb) std::memcpy(sp.bad.data(), sp.hp, sp.nb);
+    std::memcpy(sp.stats.data(), sp.hp + sp.nb, sp.stats.size() * 4);
+    sp.hp = nullptr;
+    return PNE_OK;
+}
+
+}  // namespace
+
+void shapes_release(pne_ctx *ctx, ShapePrep &sp, cudaStream_t s)
+{
+    dev_free(ctx, sp.dh, s);
+    dev_free(ctx, sp.dshape, s);
+    dev_free(ctx, sp.drep, s);
+    dev_free(ctx, sp.dbad, s);
+    dev_free(ctx, sp.dstats, s);
+    sp.active = sp.planned = false;
+}
+
+// Second stage: shape ids in order of first appearance (deterministic), an
+// exact-key check of every cluster against its representative, one plan per
+// representative; the flags and plan statistics are read back by
+// shapes_complete.
+pne_status shapes_plan(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s)
+{
+    if (!sp.active) return PNE_OK;
+    sp.active = false;
+    const int64_t n = (int64_t)rec.n_clusters;
+    const ContractParams cp = shape_params(g, rec);
     pne_status st;
     std::vector<unsigned long long> h(n);
     if (sp.h_pinned) {
         HostScope hw__(ctx, "sync_shapes");
-        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));        // returns at once when the caller already did
+        PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         std::memcpy(h.data(), sp.h_pinned, n * 8);
     } else {
-        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), dh.ptr, n * 8, cudaMemcpyDeviceToHost, s));
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), sp.dh.ptr, n * 8, cudaMemcpyDeviceToHost, s));
         PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     }
-    // shape ids in order of first appearance (deterministic)
+    dev_free(ctx, sp.dh, s);
     std::unordered_map<unsigned long long, int32_t> id;
     id.reserve(1024);
-    std::vector<int32_t> shape(n), rep;
+    sp.shape.assign(n, 0);
+    sp.rep.clear();
     for (int64_t c = 0; c < n; ++c) {
         auto it = id.find(h[c]);
-        if (it == id.end()) { it = id.emplace(h[c], (int32_t)rep.size()).first; rep.push_back((int32_t)c); }
-        shape[c] = it->second;
+        if (it == id.end()) { it = id.emplace(h[c], (int32_t)sp.rep.size()).first; sp.rep.push_back((int32_t)c); }
+        sp.shape[c] = it->second;
     }
     // exact key check against the representative (a mismatch gets its own
     // shape) and the plans of the representatives, read back together
-    DevBuf dshape, drep, dbad;
-    if ((st = dev_alloc(ctx, dshape, n * 4, s)) || (st = dev_alloc(ctx, drep, rep.size() * 4, s)) ||
-        (st = dev_alloc(ctx, dbad, n * 4, s)))
+    if ((st = dev_alloc(ctx, sp.dshape, n * 4, s)) || (st = dev_alloc(ctx, sp.drep, sp.rep.size() * 4, s)) ||
+        (st = dev_alloc(ctx, sp.dbad, n * 4, s)))
         return st;
-    if ((st = upload(ctx, dshape.ptr, shape.data(), n * 4, s)) ||
-        (st = upload(ctx, drep.ptr, rep.data(), rep.size() * 4, s)))
+    if ((st = upload(ctx, sp.dshape.ptr, sp.shape.data(), n * 4, s)) ||
+        (st = upload(ctx, sp.drep.ptr, sp.rep.data(), sp.rep.size() * 4, s)))
         return st;
-    shape_verify_kernel<<<grid_for(n, 128, ctx->n_sm), 128, 0, s>>>(cp, (const int32_t *)dshape.ptr,
-                                                                  (const int32_t *)drep.ptr, (int32_t *)dbad.ptr);
+    shape_verify_kernel<<<grid_for(n, 128, ctx->n_sm), 128, 0, s>>>(cp, (const int32_t *)sp.dshape.ptr,
+                                                                  (const int32_t *)sp.drep.ptr, (int32_t *)sp.dbad.ptr);
     PNE_CUDA_TRY(ctx, cudaGetLastError());
-    int ns = (int)rep.size();
-    std::vector<int32_t> bad(n);
-    DevBuf dstats;
-    std::vector<int32_t> stats;
-    auto make_plans = [&](bool with_bad) -> pne_status {
-        dev_free(ctx, rec.plans, s);
-        dev_free(ctx, rec.plan_steps, s);
-        dev_free(ctx, dstats, s);
-        pne_status e;
-        if ((e = dev_alloc(ctx, rec.plans, (size_t)ns * kPlanInts * 4, s)) ||
-            (e = dev_alloc(ctx, rec.plan_steps, (size_t)ns * 4, s)) || (e = dev_alloc(ctx, dstats, (size_t)ns * 16, s)))
-            return e;
-        const size_t smem = (size_t)kCtWarps * kPlanWarpInts * 4;
-        shape_plan_kernel<<<grid_for(ns, kCtWarps, ctx->n_sm, 16), kCtWarps * 32, smem, s>>>(
-            cp, (const int32_t *)drep.ptr, ns, (int32_t *)rec.plans.ptr, (int32_t *)rec.plan_steps.ptr,
-            (int32_t *)dstats.ptr);
-        PNE_CUDA_TRY(ctx, cudaGetLastError());
-        stats.assign((size_t)ns * 4, 0);
-        const size_t nb = with_bad ? (size_t)n * 4 : 0, sb = stats.size() * 4;
-        char *hp = (char *)pinned_slot(3, nb + sb);
-        if (hp) {
-            if (nb) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(hp, dbad.ptr, nb, cudaMemcpyDeviceToHost, s));
-            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(hp + nb, dstats.ptr, sb, cudaMemcpyDeviceToHost, s));
-            HostScope hw__(ctx, "sync_plans");
-            PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-            if (nb) std::memcpy(bad.data(), hp, nb);
-            std::memcpy(stats.data(), hp + nb, sb);
-        } else {
-            if (nb) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bad.data(), dbad.ptr, nb, cudaMemcpyDeviceToHost, s));
-            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(stats.data(), dstats.ptr, sb, cudaMemcpyDeviceToHost, s));
-            PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-        }
-        return PNE_OK;
-    };
-    if ((st = make_plans(true))) return st;
+    sp.ns = (int)sp.rep.size();
+    sp.bad.assign(n, 0);
+    if ((st = plans_launch(ctx, cp, rec, sp, true, s))) return st;
+    sp.planned = true;
+    return PNE_OK;
+}
+
+// Third stage: the plan statistics, then the multiply-add lists of every
+// shape, the clusters ordered by running-tensor class and shape, and the
+// per-cluster step tables.
+pne_status shapes_complete(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s)
+{
+    if (!sp.planned) return PNE_OK;
+    sp.planned = false;
+    const int64_t n = (int64_t)rec.n_clusters;
+    const ContractParams cp = shape_params(g, rec);
+    pne_status st;
+    if ((st = plans_read(ctx, sp, s))) return st;
+    std::vector<int32_t> &shape = sp.shape, &rep = sp.rep, &stats = sp.stats;
     bool any_bad = false;
     for (int64_t c = 0; c < n; ++c)
-        if (bad[c]) { shape[c] = (int32_t)rep.size(); rep.push_back((int32_t)c); any_bad = true; }
+        if (sp.bad[c]) { shape[c] = (int32_t)rep.size(); rep.push_back((int32_t)c); any_bad = true; }
     if (any_bad) {
         // hash collisions (rare): the split-off clusters become representatives
-        ns = (int)rep.size();
-        dev_free(ctx, drep, s);
-        if ((st = dev_alloc(ctx, drep, ns * 4, s))) return st;
-        if ((st = upload(ctx, drep.ptr, rep.data(), ns * 4, s)) ||
-            (st = upload(ctx, dshape.ptr, shape.data(), n * 4, s)))
+        sp.ns = (int)rep.size();
+        dev_free(ctx, sp.drep, s);
+        if ((st = dev_alloc(ctx, sp.drep, sp.ns * 4, s))) return st;
+        if ((st = upload(ctx, sp.drep.ptr, rep.data(), sp.ns * 4, s)) ||
+            (st = upload(ctx, sp.dshape.ptr, shape.data(), n * 4, s)))
             return st;
-        if ((st = make_plans(false))) return st;
+        if ((st = plans_launch(ctx, cp, rec, sp, false, s)) || (st = plans_read(ctx, sp, s))) return st;
     }
+    const int ns = sp.ns;
     rec.shape_fma.assign(ns, 0);
     rec.shape_count.assign(ns, 0);
     int max_out = 1;
@@ -1247,16 +1306,23 @@ pne_status shapes_finish(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, Shape
         ContractParams cq = cp;
         cq.tens_off = g.d_tens_off; cq.blk_off = g.d_blk_off;
         cluster_steps_kernel<<<grid_for(n, 128, ctx->n_sm), 128, 0, s>>>(
-            cq, (const int32_t *)dshape.ptr, (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr,
+            cq, (const int32_t *)sp.dshape.ptr, (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr,
             max_steps, (int32_t *)rec.step_off.ptr, (int32_t *)rec.step_site.ptr);
         PNE_CUDA_TRY(ctx, cudaGetLastError());
     }
-    rec.shape_of = dshape;
+    rec.shape_of = sp.dshape;
+    sp.dshape = DevBuf{};                 // the record owns it now
     rec.n_shapes = ns;
     rec.max_out = max_out;
     rec.shaped = ok && max_out <= 256;
-    dev_free(ctx, dh, s); dev_free(ctx, drep, s); dev_free(ctx, dbad, s); dev_free(ctx, dstats, s);
+    shapes_release(ctx, sp, s);
     return PNE_OK;
+}
+
+pne_status shapes_finish(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s)
+{
+    pne_status st = shapes_plan(ctx, g, rec, sp, s);
+    return st ? st : shapes_complete(ctx, g, rec, sp, s);
 }
 
 namespace {

@@ -1173,12 +1173,12 @@ pne_status scan_i32_to(pne_ctx *ctx, const int32_t *src, int64_t *dst, int64_t n
     return scan_to<int32_t>(ctx, src, dst, n, d_total, s);
 }
 
-// counts [rows][cols] int32 -> base (exclusive scan, row-major) int64; per-row totals.
-// The row starts are gathered on the device and read back in one copy, together
-// with `extra_bytes` from `extra_dev` (a multiple of 8) into `extra_host`.
-pne_status scan_counts(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t cols, DevBuf &base,
-                       std::vector<int64_t> &row_tot, cudaStream_t s, const void *extra_dev = nullptr,
-                       size_t extra_bytes = 0, void *extra_host = nullptr)
+// counts [rows][cols] int32 -> base (exclusive scan, row-major) int64.  The
+// row starts are gathered on the device and their copy to pinned memory is
+// queued, together with `extra_bytes` from `extra_dev` (a multiple of 8);
+// *h_out receives the pinned words (rows + 1 starts, then the extra bytes).
+pne_status scan_counts_queue(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t cols, DevBuf &base,
+                             cudaStream_t s, int64_t **h_out, const void *extra_dev = nullptr, size_t extra_bytes = 0)
 {
     const int64_t n = (int64_t)rows * cols;
     pne_status st = dev_alloc(ctx, base, (size_t)(std::max<int64_t>(n, 1) + rows + 3) * 8, s);
@@ -1195,6 +1195,19 @@ pne_status scan_counts(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t 
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h, starts, (rows + 1) * 8, cudaMemcpyDeviceToHost, s));
     if (extra_bytes)
         PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h + rows + 1, extra_dev, extra_bytes, cudaMemcpyDeviceToHost, s));
+    *h_out = h;
+    return PNE_OK;
+}
+
+// ... and the same with the wait: per-row totals into row_tot, the extra
+// bytes into extra_host.
+pne_status scan_counts(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t cols, DevBuf &base,
+                       std::vector<int64_t> &row_tot, cudaStream_t s, const void *extra_dev = nullptr,
+                       size_t extra_bytes = 0, void *extra_host = nullptr)
+{
+    int64_t *h = nullptr;
+    pne_status st = scan_counts_queue(ctx, d_counts, rows, cols, base, s, &h, extra_dev, extra_bytes);
+    if (st) return st;
     {
         HostScope hw__(ctx, "sync_counts");
         PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
@@ -1204,10 +1217,6 @@ pne_status scan_counts(pne_ctx *ctx, const int32_t *d_counts, int rows, int64_t 
     if (extra_bytes) std::memcpy(extra_host, h + rows + 1, extra_bytes);
     return PNE_OK;
 }
-
-}  // namespace
-
-namespace {
 
 void launch_expand(int pass, bool fuse, int G, cudaStream_t s, const GeomView &gv, const Arena &A, int lo, int hi,
                    int K, int mode, const Emit &o)
@@ -1379,115 +1388,173 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     return PNE_OK;
 }
 
-pne_status enumerate_tuples(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s)
+namespace {
+
+// Counting half of one tuple round (input tuples of length tp.m): the unit
+// offsets, the counting pass and the queued readback of the (order, unit)
+// row starts.
+pne_status tuple_round_count(pne_ctx *ctx, EnumRecord &rec, TuplePrep &tp, cudaStream_t s)
+{
+    const int K = rec.K, m = tp.m;
+    TupleParams p;
+    p.verts = (const int32_t *)rec.cl_verts.ptr; p.size = (const int32_t *)rec.cl_size.ptr;
+    p.vwidth = rec.vwidth; p.K = K; p.m = m;
+    p.in = (const int32_t *)tp.in_idx.ptr; p.in_order = (const int32_t *)tp.in_ord.ptr; p.n_in = tp.n_in;
+    p.size_end = (const int64_t *)tp.d_size_end.ptr;
+    p.counts = nullptr; p.base = nullptr; p.out = nullptr; p.out_order = nullptr;
+    pne_status st;
+    if ((st = dev_alloc(ctx, tp.uoff, (tp.n_in + 1) * 8, s))) return st;
+    int64_t n_units = 0;
+    if (m == 1) {
+        // pairs: input tuple i is cluster i, whose size (hence the candidate
+        // range) the host knows from the size-grouped list
+        std::vector<int64_t> h_off(tp.n_in + 1, 0);
+        for (int q = 1; q <= K; ++q)
+            for (int64_t i = rec.size_start[q]; i < std::min<int64_t>(rec.size_start[q + 1], tp.n_in); ++i) {
+                const int64_t lo = i + 1, hi = (q < K) ? tp.size_end[K - q] : lo;
+                h_off[i] = hi > lo ? (hi - lo + kTupleChunk - 1) / kTupleChunk : 0;
+            }
+        for (int64_t i = 0; i < tp.n_in; ++i) { const int64_t c = h_off[i]; h_off[i] = n_units; n_units += c; }
+        h_off[tp.n_in] = n_units;
+        if ((st = upload(ctx, tp.uoff.ptr, h_off.data(), (tp.n_in + 1) * 8, s))) return st;
+    } else {
+        {
+            ProfScope ps__(ctx, s, "enum_terms");
+            tuple_chunks_kernel<<<grid1(tp.n_in, 256, ctx->n_sm), 256, 0, s>>>(p, (int64_t *)tp.uoff.ptr);
+        }
+        if ((st = device_exclusive_scan(ctx, (int64_t *)tp.uoff.ptr, tp.n_in, &n_units, s))) return st;
+    }
+    tp.n_units = n_units;
+    p.unit_off = (const int64_t *)tp.uoff.ptr; p.n_units = n_units;
+    tp.tsmem = (size_t)kTupleWarps * (m * rec.vwidth + kMaxOrder + 1) * 4;
+    tp.h = nullptr;
+    if (n_units > 0) {
+        if ((st = dev_alloc(ctx, tp.counts, (size_t)(K + 1) * n_units * 4, s))) return st;
+        p.counts = (int32_t *)tp.counts.ptr;
+        {
+            ProfScope ps__(ctx, s, "enum_terms");
+            tuple_kernel<<<grid1(n_units, kTupleWarps, ctx->n_sm), 32 * kTupleWarps, tp.tsmem, s>>>(p, 0);
+        }
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+        if ((st = scan_counts_queue(ctx, (const int32_t *)tp.counts.ptr, K + 1, n_units, tp.base, s, &tp.h))) return st;
+    }
+    return PNE_OK;
+}
+
+// Writing half: waits for the row starts, writes the round's tuples (a new
+// level of terms) and makes them the next round's input.
+pne_status tuple_round_write(pne_ctx *ctx, EnumRecord &rec, TuplePrep &tp, cudaStream_t s)
+{
+    const int K = rec.K, m = tp.m;
+    std::vector<int64_t> per_order(K + 1, 0);
+    if (tp.h) {
+        {
+            HostScope hw__(ctx, "sync_counts");
+            PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        }
+        for (int r = 0; r <= K; ++r) per_order[r] = tp.h[r + 1] - tp.h[r];
+        tp.h = nullptr;
+    }
+    EnumRecord::Level L;
+    L.m = m + 1;
+    L.order_start.assign(K + 2, 0);
+    int64_t n_out = 0;
+    for (int q = 0; q <= K; ++q) { L.order_start[q] = n_out; n_out += per_order[q]; }
+    L.order_start[K + 1] = n_out;
+    L.n = (uint64_t)n_out;
+    DevBuf out_ord;
+    pne_status st;
+    if (n_out > 0) {
+        if ((st = dev_alloc(ctx, L.idx, (size_t)n_out * (m + 1) * 4, s))) return st;
+        if ((st = dev_alloc(ctx, out_ord, (size_t)n_out * 4, s))) return st;
+        TupleParams p;
+        p.verts = (const int32_t *)rec.cl_verts.ptr; p.size = (const int32_t *)rec.cl_size.ptr;
+        p.vwidth = rec.vwidth; p.K = K; p.m = m;
+        p.in = (const int32_t *)tp.in_idx.ptr; p.in_order = (const int32_t *)tp.in_ord.ptr; p.n_in = tp.n_in;
+        p.size_end = (const int64_t *)tp.d_size_end.ptr;
+        p.unit_off = (const int64_t *)tp.uoff.ptr; p.n_units = tp.n_units;
+        p.counts = (int32_t *)tp.counts.ptr;
+        p.base = (const int64_t *)tp.base.ptr;
+        p.out = (int32_t *)L.idx.ptr; p.out_order = (int32_t *)out_ord.ptr;
+        {
+            ProfScope ps__(ctx, s, "enum_terms");
+            tuple_kernel<<<grid1(tp.n_units, kTupleWarps, ctx->n_sm), 32 * kTupleWarps, tp.tsmem, s>>>(p, 1);
+        }
+        PNE_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    for (int q = 0; q <= K; ++q) rec.terms_by_order[q] += per_order[q];
+    rec.n_terms += (uint64_t)n_out;
+    dev_free(ctx, tp.uoff, s); dev_free(ctx, tp.counts, s); dev_free(ctx, tp.base, s);
+    if (tp.in_owned) dev_free(ctx, tp.in_idx, s);
+    dev_free(ctx, tp.in_ord, s);
+    if (n_out > 0) rec.levels.push_back(L);
+    tp.in_idx = L.idx; tp.in_owned = false;     // the level keeps ownership
+    tp.in_ord = out_ord;
+    tp.n_in = n_out;
+    tp.m = m + 1;
+    return PNE_OK;
+}
+
+}  // namespace
+
+pne_status tuples_begin(pne_ctx *ctx, EnumRecord &rec, TuplePrep &tp, cudaStream_t s)
 {
     const int K = rec.K;
+    tp = TuplePrep();
     rec.levels.clear();
     rec.terms_by_order.assign(K + 1, 0);
     rec.terms_by_order[0] = 1;
     for (int q = 1; q <= K; ++q) rec.terms_by_order[q] += rec.size_start[q + 1] - rec.size_start[q];
-    int s_min = 0;
-    for (int q = 1; q <= K; ++q) if (rec.size_start[q + 1] > rec.size_start[q]) { s_min = q; break; }
+    for (int q = 1; q <= K; ++q) if (rec.size_start[q + 1] > rec.size_start[q]) { tp.s_min = q; break; }
     rec.n_terms = 1 + rec.n_clusters;
-    if (s_min == 0 || rec.n_clusters == 0) return PNE_OK;
+    if (tp.s_min == 0 || rec.n_clusters == 0) return PNE_OK;
     // size_end[q] = first cluster index with size > q
-    std::vector<int64_t> size_end(K + 2, 0);
-    for (int q = 0; q <= K; ++q) size_end[q] = rec.size_start[q + 1];
-    size_end[K + 1] = rec.size_start[K + 1];
-    DevBuf d_size_end;
-    pne_status st = dev_alloc(ctx, d_size_end, (K + 2) * 8, s);
-    if (st) return st;
-    if ((st = upload(ctx, d_size_end.ptr, size_end.data(), (K + 2) * 8, s))) return st;
+    tp.size_end.assign(K + 2, 0);
+    for (int q = 0; q <= K; ++q) tp.size_end[q] = rec.size_start[q + 1];
+    tp.size_end[K + 1] = rec.size_start[K + 1];
+    pne_status st;
+    if ((st = dev_alloc(ctx, tp.d_size_end, (K + 2) * 8, s))) return st;
+    if ((st = upload(ctx, tp.d_size_end.ptr, tp.size_end.data(), (K + 2) * 8, s))) return st;
     // first round: every cluster that can start a pair (size <= K - s_min)
-    int64_t n_in = (K - s_min >= s_min) ? size_end[K - s_min] : 0;
-    DevBuf in_idx, in_ord;
-    bool in_owned = true;
-    int m = 1;
-    if (n_in > 0) {
-        if ((st = dev_alloc(ctx, in_idx, n_in * 4, s))) return st;
-        if ((st = dev_alloc(ctx, in_ord, n_in * 4, s))) return st;
+    tp.n_in = (K - tp.s_min >= tp.s_min) ? tp.size_end[K - tp.s_min] : 0;
+    tp.m = 1;
+    if (tp.n_in > 0) {
+        if ((st = dev_alloc(ctx, tp.in_idx, tp.n_in * 4, s))) return st;
+        if ((st = dev_alloc(ctx, tp.in_ord, tp.n_in * 4, s))) return st;
         {
             ProfScope ps__(ctx, s, "enum_terms");
-            iota_order_kernel<<<grid1(n_in, 256, ctx->n_sm), 256, 0, s>>>((int32_t *)in_idx.ptr, (int32_t *)in_ord.ptr,
-                                                                       (const int32_t *)rec.cl_size.ptr, n_in);
+            iota_order_kernel<<<grid1(tp.n_in, 256, ctx->n_sm), 256, 0, s>>>((int32_t *)tp.in_idx.ptr,
+                                                                          (int32_t *)tp.in_ord.ptr,
+                                                                          (const int32_t *)rec.cl_size.ptr, tp.n_in);
+        }
+        if (2 * tp.s_min <= K) {
+            if ((st = tuple_round_count(ctx, rec, tp, s))) return st;
+            tp.active = true;
         }
     }
-    while (n_in > 0 && (m + 1) * s_min <= K) {
-        TupleParams p;
-        p.verts = (const int32_t *)rec.cl_verts.ptr; p.size = (const int32_t *)rec.cl_size.ptr;
-        p.vwidth = rec.vwidth; p.K = K; p.m = m;
-        p.in = (const int32_t *)in_idx.ptr; p.in_order = (const int32_t *)in_ord.ptr; p.n_in = n_in;
-        p.size_end = (const int64_t *)d_size_end.ptr;
-        p.counts = nullptr; p.base = nullptr; p.out = nullptr; p.out_order = nullptr;
-        DevBuf uoff;
-        if ((st = dev_alloc(ctx, uoff, (n_in + 1) * 8, s))) return st;
-        int64_t n_units = 0;
-        if (m == 1) {
-            // pairs: input tuple i is cluster i, whose size (hence the candidate
-            // range) the host knows from the size-grouped list
-            std::vector<int64_t> h_off(n_in + 1, 0);
-            for (int q = 1; q <= K; ++q)
-                for (int64_t i = rec.size_start[q]; i < std::min<int64_t>(rec.size_start[q + 1], n_in); ++i) {
-                    const int64_t lo = i + 1, hi = (q < K) ? size_end[K - q] : lo;
-                    h_off[i] = hi > lo ? (hi - lo + kTupleChunk - 1) / kTupleChunk : 0;
-                }
-            for (int64_t i = 0; i < n_in; ++i) { const int64_t c = h_off[i]; h_off[i] = n_units; n_units += c; }
-            h_off[n_in] = n_units;
-            if ((st = upload(ctx, uoff.ptr, h_off.data(), (n_in + 1) * 8, s))) return st;
-        } else {
-            {
-                ProfScope ps__(ctx, s, "enum_terms");
-                tuple_chunks_kernel<<<grid1(n_in, 256, ctx->n_sm), 256, 0, s>>>(p, (int64_t *)uoff.ptr);
-            }
-            if ((st = device_exclusive_scan(ctx, (int64_t *)uoff.ptr, n_in, &n_units, s))) return st;
-        }
-        p.unit_off = (const int64_t *)uoff.ptr; p.n_units = n_units;
-        const size_t tsmem = (size_t)kTupleWarps * (m * rec.vwidth + kMaxOrder + 1) * 4;
-        EnumRecord::Level L;
-        L.m = m + 1;
-        L.order_start.assign(K + 2, 0);
-        DevBuf counts, base, out_ord;
-        std::vector<int64_t> per_order(K + 1, 0);
-        if (n_units > 0) {
-            if ((st = dev_alloc(ctx, counts, (size_t)(K + 1) * n_units * 4, s))) return st;
-            p.counts = (int32_t *)counts.ptr;
-            {
-                ProfScope ps__(ctx, s, "enum_terms");
-                tuple_kernel<<<grid1(n_units, kTupleWarps, ctx->n_sm), 32 * kTupleWarps, tsmem, s>>>(p, 0);
-            }
-            PNE_CUDA_TRY(ctx, cudaGetLastError());
-            if ((st = scan_counts(ctx, (const int32_t *)counts.ptr, K + 1, n_units, base, per_order, s))) return st;
-        }
-        int64_t n_out = 0;
-        for (int q = 0; q <= K; ++q) { L.order_start[q] = n_out; n_out += per_order[q]; }
-        L.order_start[K + 1] = n_out;
-        L.n = (uint64_t)n_out;
-        if (n_out > 0) {
-            if ((st = dev_alloc(ctx, L.idx, (size_t)n_out * (m + 1) * 4, s))) return st;
-            if ((st = dev_alloc(ctx, out_ord, (size_t)n_out * 4, s))) return st;
-            p.base = (const int64_t *)base.ptr;
-            p.out = (int32_t *)L.idx.ptr; p.out_order = (int32_t *)out_ord.ptr;
-            {
-                ProfScope ps__(ctx, s, "enum_terms");
-                tuple_kernel<<<grid1(n_units, kTupleWarps, ctx->n_sm), 32 * kTupleWarps, tsmem, s>>>(p, 1);
-            }
-            PNE_CUDA_TRY(ctx, cudaGetLastError());
-        }
-        for (int q = 0; q <= K; ++q) rec.terms_by_order[q] += per_order[q];
-        rec.n_terms += (uint64_t)n_out;
-        dev_free(ctx, uoff, s); dev_free(ctx, counts, s); dev_free(ctx, base, s);
-        if (in_owned) dev_free(ctx, in_idx, s);
-        dev_free(ctx, in_ord, s);
-        if (n_out > 0) rec.levels.push_back(L);
-        in_idx = L.idx; in_owned = false;     // the level keeps ownership
-        in_ord = out_ord;
-        n_in = n_out;
-        m += 1;
-    }
-    if (in_owned) dev_free(ctx, in_idx, s);
-    dev_free(ctx, in_ord, s);
-    dev_free(ctx, d_size_end, s);
     return PNE_OK;
+}
+
+pne_status tuples_finish(pne_ctx *ctx, EnumRecord &rec, TuplePrep &tp, cudaStream_t s)
+{
+    const int K = rec.K;
+    pne_status st;
+    while (tp.active) {
+        if ((st = tuple_round_write(ctx, rec, tp, s))) return st;
+        tp.active = tp.n_in > 0 && (tp.m + 1) * tp.s_min <= K;
+        if (tp.active && (st = tuple_round_count(ctx, rec, tp, s))) return st;
+    }
+    if (tp.in_owned) dev_free(ctx, tp.in_idx, s);
+    dev_free(ctx, tp.in_ord, s);
+    dev_free(ctx, tp.d_size_end, s);
+    return PNE_OK;
+}
+
+pne_status enumerate_tuples(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s)
+{
+    TuplePrep tp;
+    pne_status st = tuples_begin(ctx, rec, tp, s);
+    return st ? st : tuples_finish(ctx, rec, tp, s);
 }
 
 }  // namespace pne

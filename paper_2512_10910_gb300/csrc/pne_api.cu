@@ -619,6 +619,11 @@ void pne_ctx_destroy(pne_ctx *ctx)
         for (auto st : ctx->side) cudaStreamDestroy(st);
         for (auto ev : ctx->side_ev) cudaEventDestroy(ev);
     }
+    for (auto &l : ctx->stream_pool) {
+        cudaStreamDestroy(l.s);
+        cudaEventDestroy(l.fork);
+        cudaEventDestroy(l.join);
+    }
     delete ctx;
 }
 
@@ -800,24 +805,65 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
                 rec->terms_by_order.assign(1, 1); rec->n_terms = 1;
                 rec->width = 1; rec->vwidth = 1;
             } else {
-                // the shape hashes ride on the tuple stage's synchronisation
-                ShapePrep sp;
-                auto fail = [&](pne_status e) { dev_free(ctx, sp.dh, s); return e; };
                 {
                     HostScope h1(ctx, "enum_clusters");
-                    if ((st = enumerate_clusters(ctx, g, K, mode, *rec, s))) return fail(st);
+                    if ((st = enumerate_clusters(ctx, g, K, mode, *rec, s))) return st;
+                }
+                // the shape stage (contraction plans) and the term stage run on
+                // two streams, their host waits interleaved: each waits for its
+                // own readback while the other's work runs
+                ShapePrep sp;
+                TuplePrep tp;
+                pne_ctx::Lent ls;
+                const bool shapes = shapes_needed(g, *rec);
+                cudaStream_t sb = s;
+                if (shapes) {
+                    std::lock_guard<std::mutex> lk(ctx->pool_mu);
+                    if (!ctx->stream_pool.empty()) {
+                        ls = ctx->stream_pool.back();
+                        ctx->stream_pool.pop_back();
+                    }
+                }
+                auto fail = [&](pne_status e) {
+                    shapes_release(ctx, sp, sb);
+                    if (ls.s) { std::lock_guard<std::mutex> lk(ctx->pool_mu); ctx->stream_pool.push_back(ls); }
+                    return e;
+                };
+                if (shapes) {
+                    if (!ls.s) {
+                        PNE_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ls.s, cudaStreamNonBlocking));
+                        PNE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ls.fork, cudaEventDisableTiming));
+                        PNE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ls.join, cudaEventDisableTiming));
+                    }
+                    sb = ls.s;
+                    if (cudaEventRecord(ls.fork, s) != cudaSuccess || cudaStreamWaitEvent(sb, ls.fork, 0) != cudaSuccess)
+                        return fail(PNE_ECUDA);
                 }
                 {
                     HostScope h2(ctx, "enum_shapes_begin");
-                    if ((st = shapes_begin(ctx, g, *rec, sp, s))) return fail(st);
+                    if ((st = shapes_begin(ctx, g, *rec, sp, sb))) return fail(st);
                 }
                 {
-                    HostScope h3(ctx, "enum_tuples");
-                    if ((st = enumerate_tuples(ctx, *rec, s))) return fail(st);
+                    HostScope h3(ctx, "enum_tuples_begin");
+                    if ((st = tuples_begin(ctx, *rec, tp, s))) return fail(st);
                 }
                 {
-                    HostScope h4(ctx, "enum_shapes_finish");
-                    if ((st = shapes_finish(ctx, g, *rec, sp, s))) return fail(st);
+                    HostScope h4(ctx, "enum_shapes_plan");
+                    if ((st = shapes_plan(ctx, g, *rec, sp, sb))) return fail(st);
+                }
+                {
+                    HostScope h5(ctx, "enum_tuples_finish");
+                    if ((st = tuples_finish(ctx, *rec, tp, s))) return fail(st);
+                }
+                {
+                    HostScope h6(ctx, "enum_shapes_complete");
+                    if ((st = shapes_complete(ctx, g, *rec, sp, sb))) return fail(st);
+                }
+                if (ls.s) {
+                    if (cudaEventRecord(ls.join, sb) != cudaSuccess || cudaStreamWaitEvent(s, ls.join, 0) != cudaSuccess)
+                        return fail(PNE_ECUDA);
+                    std::lock_guard<std::mutex> lk(ctx->pool_mu);
+                    ctx->stream_pool.push_back(ls);
                 }
             }
         }

@@ -161,6 +161,11 @@ struct pne_ctx {
     cudaEvent_t side_ev[kSideStreams + 1] = {};
     bool side_ready = false;
     std::mutex side_mu;
+    // streams lent to one call at a time (the shape stage of an enumeration),
+    // each with a fork and a join event
+    struct Lent { cudaStream_t s = nullptr; cudaEvent_t fork = nullptr, join = nullptr; };
+    std::vector<Lent> stream_pool;
+    std::mutex pool_mu;
 };
 
 namespace pne {
@@ -316,6 +321,20 @@ pne_status launch_convert(pne_ctx *ctx, pne_partition *p, int dtype, cudaStream_
 pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode,
                               EnumRecord &rec, cudaStream_t s);
 pne_status enumerate_tuples(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s);
+// The same in two halves: the first round's counting with its readback queued
+// (begin), then the wait, its writing pass and any further rounds (finish).
+struct TuplePrep {
+    bool active = false;          // a round's counting is queued
+    int m = 1, s_min = 0;         // length of the round's input tuples; smallest cluster size
+    int64_t n_in = 0, n_units = 0;
+    std::vector<int64_t> size_end;
+    DevBuf d_size_end, in_idx, in_ord, uoff, counts, base;
+    bool in_owned = true;
+    int64_t *h = nullptr;         // pinned readback of the (order, unit) row starts
+    size_t tsmem = 0;
+};
+pne_status tuples_begin(pne_ctx *ctx, EnumRecord &rec, TuplePrep &tp, cudaStream_t s);
+pne_status tuples_finish(pne_ctx *ctx, EnumRecord &rec, TuplePrep &tp, cudaStream_t s);
 
 // contraction and sums (contract.cu)
 pne_status launch_contract(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s);
@@ -328,8 +347,24 @@ struct ShapePrep {
     DevBuf dh;                    // per-cluster hashes on the device
     void *h_pinned = nullptr;     // their readback
     bool active = false;
+    // after shapes_plan: shape ids and representatives, the verification and
+    // plan launches, and their queued readback
+    bool planned = false;
+    std::vector<int32_t> shape, rep, bad, stats;
+    DevBuf dshape, drep, dbad, dstats;
+    char *hp = nullptr;
+    size_t nb = 0;
+    int ns = 0;
 };
+void shapes_release(pne_ctx *ctx, ShapePrep &sp, cudaStream_t s);
+bool shapes_needed(const Geometry &g, const EnumRecord &rec);
+// Shape preparation in three stages on one stream, each queueing work and
+// readbacks without waiting except for the readback of the stage before:
+// hashes (begin), shape ids + plans (plan), multiply-add lists and cluster
+// order (complete).  shapes_finish = plan + complete.
 pne_status shapes_begin(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s);
+pne_status shapes_plan(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s);
+pne_status shapes_complete(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s);
 pne_status shapes_finish(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePrep &sp, cudaStream_t s);
 pne_status launch_convert_only(pne_ctx *ctx, const pne_partition *p, int dtype, cudaStream_t s);
 
