@@ -645,7 +645,7 @@ namespace {
 
 constexpr int kPlanInts = kMaxSteps * kStepInts;
 constexpr int kClassMin = 8;           // smallest running-tensor class of the shaped contraction
-constexpr int kWarpClassX = 32;        // classes from this running-tensor size on: one warp per cluster
+constexpr int kGroupClassX = 8;        // classes from this running-tensor size on: a group of lanes per cluster
 // shared ints per warp of the plan kernel: plan, sites, spare, then a PlanWork
 // (declared below; its size is checked there)
 constexpr int kPlanWarpInts = kMaxSteps * kStepInts + kMaxSteps + 4 + 384;
@@ -899,26 +899,33 @@ pne_status side_streams(pne_ctx *ctx)
     return PNE_OK;
 }
 
-// Clusters perm[i0, i1) of every tensor set, one warp per (cluster, set): the
-// running tensor sits in the warp's shared memory once (not once per lane) and
-// the lanes split each step's output entries; every output is the same chain
-// of multiply-adds in the same order as in shaped_cluster, and the rescaling
-// decision is the same, so the values agree bit for bit with the lane-per-
-// cluster form.  For the classes with large running tensors.
-template <typename T, typename L, int R>
-__global__ void __launch_bounds__(256) contract_warp_kernel(ContractParams P, const int32_t *perm, const int32_t *shape_of,
-                                                            const int32_t *plans, const int32_t *plan_steps,
-                                                            const int32_t *ops, const int64_t *op_off,
-                                                            const int32_t *step_off, const int32_t *step_site, int sstride,
-                                                            int xmax, int64_t i0, int64_t i1)
+// Clusters perm[i0, i1) of every tensor set, G lanes per (cluster, set): the
+// running tensor sits once per group in shared memory and the group's lanes
+// split each step's outputs (lane j of the group takes outputs j, j + G, ...).
+// Every output is the same chain of multiply-adds in the same order as in
+// shaped_cluster, and the rescaling decision is the same, so the values agree
+// bit for bit with the lane-per-cluster form.  Neighbouring outputs read
+// neighbouring block entries, so a warp's gathers touch 32 / G clusters
+// instead of 32; groups sync and reduce over their own lane mask, so groups
+// of different shapes in one warp never wait for each other.
+template <typename T, typename L, int R, int G>
+__global__ void __launch_bounds__(256) contract_group_kernel(ContractParams P, const int32_t *perm,
+                                                             const int32_t *shape_of, const int32_t *plans,
+                                                             const int32_t *plan_steps, const int32_t *ops,
+                                                             const int64_t *op_off, const int32_t *step_off,
+                                                             const int32_t *step_site, int sstride, int xmax,
+                                                             int64_t i0, int64_t i1)
 {
+    static_assert(G == 4 || G == 8 || G == 16 || G == 32, "group size");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    T *X0 = (T *)smem_raw + (int64_t)wib * 2 * xmax;
+    const int lane = threadIdx.x & 31, sub = lane % G;
+    const int gib = threadIdx.x / G, gpb = blockDim.x / G;            // group in block, groups per block
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - sub));
+    T *X0 = (T *)smem_raw + (int64_t)gib * 2 * xmax;
     T *X1 = X0 + xmax;
     const int64_t nc = i1 - i0;
     const int64_t items = nc * P.n_members;
-    for (int64_t it = (int64_t)blockIdx.x * wpb + wib; it < items; it += (int64_t)gridDim.x * wpb) {
+    for (int64_t it = (int64_t)blockIdx.x * gpb + gib; it < items; it += (int64_t)gridDim.x * gpb) {
         const int b = (int)(it / nc);
         const int64_t c = perm[i0 + it % nc];
         const int sh = shape_of[c];
@@ -927,8 +934,8 @@ __global__ void __launch_bounds__(256) contract_warp_kernel(ContractParams P, co
         const int32_t *op = ops + op_off[sh];
         const int32_t *soff = step_off + c * sstride, *ssite = step_site + c * sstride;
         T *X = X0, *Y = X1;
-        if (lane == 0) X[0] = (T)1;
-        __syncwarp();
+        if (sub == 0) X[0] = (T)1;
+        __syncwarp(gmask);
         int expo = 0, nz = 0;
         double zs = 1.0;
         for (int t = 0; t < nsteps; ++t) {
@@ -936,7 +943,7 @@ __global__ void __launch_bounds__(256) contract_warp_kernel(ContractParams P, co
             const int outsz = st[4], closz = st[5];
             const int64_t mbase = (int64_t)b * P.stride + __ldg(soff + t);
             int mxb = 0;
-            for (int o = lane; o < outsz; o += 32) {
+            for (int o = sub; o < outsz; o += G) {
                 const int32_t *oo = op + (int64_t)o * closz;
                 T acc = (T)0;
                 int cc = 0;
@@ -961,26 +968,27 @@ __global__ void __launch_bounds__(256) contract_warp_kernel(ContractParams P, co
                 mxb = max(mxb, Expo<T>::biased(acc));
             }
             op += (int64_t)outsz * closz;
-            mxb = __reduce_max_sync(0xffffffffu, mxb);
-            __syncwarp();
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) mxb = max(mxb, __shfl_xor_sync(gmask, mxb, off));
+            __syncwarp(gmask);
             if (mxb > 0) {
                 const int e = mxb - (Expo<T>::kBias - 1);
                 if (e > Expo<T>::kWindow || e < -Expo<T>::kWindow) {
                     const T sc = (e < Expo<T>::kBias) ? Expo<T>::inv_pow2(e) : (T)ldexp(1.0, -e);
-                    for (int o = lane; o < outsz; o += 32) Y[o] *= sc;
+                    for (int o = sub; o < outsz; o += G) Y[o] *= sc;
                     expo += e;
-                    __syncwarp();
+                    __syncwarp(gmask);
                 }
             }
             T *tmp = X; X = Y; Y = tmp;
             const int site = __ldg(ssite + t);
             if (P.zero[(int64_t)b * P.n_sites + site]) { ++nz; zs *= P.scale[(int64_t)b * P.n_sites + site]; }
         }
-        if (lane == 0) {
+        if (sub == 0) {
             P.w[(int64_t)b * P.n_clusters + c] = ldexp((double)X[0], expo) * zs;
             P.nzc[(int64_t)b * P.n_clusters + c] = nz;
         }
-        __syncwarp();
+        __syncwarp(gmask);
     }
 }
 
@@ -1023,20 +1031,26 @@ pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &
             ls = ctx->side[(j - 1) % pne_ctx::kSideStreams];
             PNE_CUDA_TRY(ctx, cudaStreamWaitEvent(ls, ctx->side_ev[0], 0));
         }
-        if (xmax >= kWarpClassX) {
-            // large running tensors: one warp per cluster
-            auto wk = contract_warp_kernel<T, L, R>;
-            const int wpb2 = 8;
-            const size_t smem2 = (size_t)wpb2 * 2 * xmax * sizeof(T);
-            if (smem2 > 48 * 1024) cudaFuncSetAttribute(wk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        if (xmax >= kGroupClassX) {
+            // a group of lanes per cluster: 32 for large running tensors, else
+            // about one lane per two outputs of the largest step
+            const int G = xmax >= 32 ? 32 : (xmax >= 16 ? 8 : 4);
+            const int gpb = 256 / G;
+            const size_t smem2 = (size_t)gpb * 2 * xmax * sizeof(T);
             const int64_t items2 = (i1 - i0) * cp.n_members;
-            int64_t g2 = (items2 + wpb2 - 1) / wpb2;
+            int64_t g2 = (items2 + gpb - 1) / gpb;
             if (g2 > (int64_t)ctx->n_sm * 16) g2 = (int64_t)ctx->n_sm * 16;
-            wk<<<(int)g2, wpb2 * 32, smem2, ls>>>(cp, (const int32_t *)rec.perm.ptr, (const int32_t *)rec.shape_of.ptr,
-                                                 (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr,
-                                                 (const int32_t *)rec.ops.ptr, (const int64_t *)rec.op_off.ptr,
-                                                 (const int32_t *)rec.step_off.ptr, (const int32_t *)rec.step_site.ptr,
-                                                 rec.step_stride, xmax, i0, i1);
+            auto launch = [&](auto kernel) {
+                if (smem2 > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+                kernel<<<(int)g2, 256, smem2, ls>>>(cp, (const int32_t *)rec.perm.ptr, (const int32_t *)rec.shape_of.ptr,
+                                                    (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr,
+                                                    (const int32_t *)rec.ops.ptr, (const int64_t *)rec.op_off.ptr,
+                                                    (const int32_t *)rec.step_off.ptr, (const int32_t *)rec.step_site.ptr,
+                                                    rec.step_stride, xmax, i0, i1);
+            };
+            if (G == 32) launch(contract_group_kernel<T, L, R, 32>);
+            else if (G == 8) launch(contract_group_kernel<T, L, R, 8>);
+            else launch(contract_group_kernel<T, L, R, 4>);
             PNE_CUDA_TRY(ctx, cudaGetLastError());
             continue;
         }
