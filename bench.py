@@ -598,18 +598,20 @@ def run_serve(args, wl, rank, world, local_rank):
         first = info["t_arrival"] if first is None else min(first, info["t_arrival"])
         last = info["t_done"] if last is None else max(last, info["t_done"])
     peak, _ = pne.pne_server_stats(srv)
+    first_error = pne.pne_server_first_error(srv)
     pne.pne_server_destroy(srv)
     ctx.close()
     lat = np.array(lat)
     if not len(lat):
-        print(json.dumps({"error": "no request completed", "failed_by_status": failed}), file=sys.stderr)
+        print(json.dumps({"error": "no request completed", "failed_by_status": failed, "first_error": first_error}),
+              file=sys.stderr)
         return 1
     span = last - first
     out = {"metric": "PNE terms contracted/sec", "value": terms / span, "unit": "terms/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * span, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": wl["desc"], "requests": len(ids), "completed": int(len(lat)),
-                      "failed_by_status": failed,
+                      "failed_by_status": failed, "first_error": first_error,
                       "offered_rate_req_s": wl["rate"], "trace_s": float(t_arr[-1]),
                       "served_req_s": len(lat) / span, "geometries_warmed": len(seen),
                       "device_budget_bytes": int(opts.device_budget_bytes), "peak_admitted_bytes": peak,

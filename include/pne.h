@@ -285,6 +285,10 @@ pne_status pne_server_poll(pne_server *s, uint64_t id, pne_result *out, pne_requ
 pne_status pne_server_drain(pne_server *s);
 /* Largest admitted estimate seen at once, and the server clock (seconds). */
 pne_status pne_server_stats(pne_server *s, uint64_t *peak_inflight_bytes, double *now);
+/* The error text of the first request that failed ("" while none has): the
+ * message of the failing library call, as pne_last_error gives it in the
+ * server thread that made it.  Valid until the server is destroyed. */
+const char *pne_server_first_error(pne_server *s);
 void pne_server_destroy(pne_server *s);
 
 /* ---- belief propagation without device allocation ------------------------ */

@@ -21,6 +21,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -68,6 +69,7 @@ struct pne_server {
     std::vector<cudaStream_t> streams;
     cudaStream_t launch_stream = nullptr;
     std::chrono::steady_clock::time_point t0;
+    std::string first_error;      // message of the first failed request
 
     double now() const
     {
@@ -114,6 +116,11 @@ bool fits(pne_server *s, const Request &r)
 
 void finish_locked(pne_server *s, Request *r, pne_status st)
 {
+    if (st != PNE_OK && s->first_error.empty()) {
+        // the failing call ran in this thread: its message is this thread's
+        s->first_error = std::string("request ") + std::to_string(r->id) + ": " + pne_last_error(s->ctx);
+        if (s->first_error.empty()) s->first_error = "status " + std::to_string((int)st);
+    }
     r->status = st;
     r->done = true;
     r->info.t_done = s->now();
@@ -303,6 +310,13 @@ pne_status pne_server_stats(pne_server *s, uint64_t *peak_inflight_bytes, double
     if (peak_inflight_bytes) *peak_inflight_bytes = s->peak_bytes;
     if (now) *now = s->now();
     return PNE_OK;
+}
+
+const char *pne_server_first_error(pne_server *s)
+{
+    if (!s) return "";
+    std::lock_guard<std::mutex> lk(s->mu);
+    return s->first_error.c_str();
 }
 
 void pne_server_destroy(pne_server *s)

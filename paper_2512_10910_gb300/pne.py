@@ -26,7 +26,7 @@ __all__ = [
     "pne_ctx_profile", "pne_ctx_profile_read", "pne_ctx_trace_read", "pne_terms_work", "pne_measure_fma_peak",
     "pne_bp_messages_noalloc", "pne_partition_update", "pne_batch_create", "pne_batch_run", "pne_batch_n_results", "pne_batch_config",
     "pne_batch_destroy", "BatchOpts", "pne_server_create", "pne_server_submit", "pne_server_poll",
-    "pne_server_drain", "pne_server_stats", "pne_server_destroy", "ServerOpts", "RequestInfo",
+    "pne_server_drain", "pne_server_stats", "pne_server_first_error", "pne_server_destroy", "ServerOpts", "RequestInfo",
     "Network", "PartitionOpts", "EnumOpts", "Result", "Context", "run", "network_struct",
 ]
 
@@ -182,6 +182,8 @@ def load_library():
     lib.pne_server_drain.restype = ctypes.c_int
     lib.pne_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]
     lib.pne_server_stats.restype = ctypes.c_int
+    lib.pne_server_first_error.argtypes = [vp]
+    lib.pne_server_first_error.restype = ctypes.c_char_p
     lib.pne_server_destroy.argtypes = [vp]
     lib.pne_server_destroy.restype = None
     lib.pne_ctx_profile.argtypes = [vp, ctypes.c_int]
@@ -207,7 +209,8 @@ def exported_symbols() -> list:
              "pne_ctx_profile", "pne_ctx_profile_read", "pne_ctx_trace_read", "pne_terms_work", "pne_measure_fma_peak",
              "pne_bp_messages_noalloc", "pne_partition_update", "pne_batch_create", "pne_batch_run",
              "pne_batch_n_results", "pne_batch_config", "pne_batch_destroy", "pne_server_create",
-             "pne_server_submit", "pne_server_poll", "pne_server_drain", "pne_server_stats", "pne_server_destroy"]
+             "pne_server_submit", "pne_server_poll", "pne_server_drain", "pne_server_stats", "pne_server_first_error",
+             "pne_server_destroy"]
     return [n for n in names if hasattr(lib, n)]
 
 
@@ -360,6 +363,11 @@ def pne_server_stats(srv):
     b, t = ctypes.c_uint64(), ctypes.c_double()
     _check(load_library().pne_server_stats(srv, ctypes.byref(b), ctypes.byref(t)))
     return int(b.value), float(t.value)
+
+
+def pne_server_first_error(srv) -> str:
+    """Error text of the first failed request ('' while none has)."""
+    return (load_library().pne_server_first_error(srv) or b"").decode()
 
 
 def pne_server_destroy(srv):
