@@ -1033,12 +1033,23 @@ __global__ void block_kernel(BlockParams p)
             const int d = cdims[ci++];
             post /= d;
             const double *G = p.gauge + (((int64_t)set * p.n_bonds_full + bonds[i]) * 2 + side[i]) * 64;
-            for (int e = lane; e < n; e += 32) {
-                const int lo = e % post, c = (e / post) % d, hi = e / (post * d);
-                const double *src = cur + (int64_t)hi * d * post + lo;
-                double s = 0.0;
-                for (int a = 0; a < d; ++a) s = fma(src[(int64_t)a * post], G[a * 8 + c], s);
-                nxt[e] = s;
+            // one lane per fiber (hi, lo): its d inputs read once, its d outputs
+            const int fibers = n / d;
+            for (int f = lane; f < fibers; f += 32) {
+                const int lo = f % post, hi = f / post;
+                const int64_t base = (int64_t)hi * d * post + lo;
+                double x[kMaxDim];
+#pragma unroll
+                for (int a = 0; a < kMaxDim; ++a) x[a] = a < d ? cur[base + (int64_t)a * post] : 0.0;
+#pragma unroll
+                for (int c = 0; c < kMaxDim; ++c) {
+                    if (c >= d) break;
+                    double s = 0.0;
+#pragma unroll
+                    for (int a = 0; a < kMaxDim; ++a)
+                        if (a < d) s = fma(x[a], G[a * 8 + c], s);
+                    nxt[base + (int64_t)c * post] = s;
+                }
             }
             __syncwarp();
             double *t = cur; cur = nxt; nxt = t;
@@ -1128,7 +1139,9 @@ __global__ void block_ff_kernel(BlockParams p)
         int n = 1;
         for (int i = 0; i < kc; ++i) n *= cdims[i];
         const double *T = p.T + set * p.f_stride + p.f_tens_off[v] + fixed_off;
+        const bool ident = kc == k;          // no open legs: the slice is the tensor itself
         auto src_of = [&](int e) {
+            if (ident) return e;
             int r = e, src = 0;
             for (int i = kc - 1; i >= 0; --i) { int dgt; r = fdivmod(r, cdims[i], cinv[i], dgt); src += dgt * cstr[i]; }
             return src;
@@ -1150,15 +1163,26 @@ __global__ void block_ff_kernel(BlockParams p)
             for (int q = lane; q < d * 8; q += 32)
                 if ((q & 7) < d) Gs[q] = split_scaled(G[q], 0);
             __syncwarp();
+            // one lane per fiber (hi, lo) of this leg: its d inputs are read
+            // once and give its d outputs, each summed over a in order
             const float inv_post = 1.0f / (float)post;
-            for (int e = lane; e < n; e += 32) {
-                int lo, c;
-                const int rest = fdivmod(e, post, inv_post, lo);
-                const int hi = fdivmod(rest, d, cinv[i], c);
-                const ff *src = cur + (int64_t)hi * d * post + lo;
-                ffacc acc;
-                for (int a = 0; a < d; ++a) acc.add(ff_mul(src[(int64_t)a * post], Gs[a * 8 + c]));
-                nxt[e] = acc.get();
+            const int fibers = n / d;
+            for (int f = lane; f < fibers; f += 32) {
+                int lo;
+                const int hi = fdivmod(f, post, inv_post, lo);
+                const int64_t base = (int64_t)hi * d * post + lo;
+                ff x[kMaxDim];
+#pragma unroll
+                for (int a = 0; a < kMaxDim; ++a) x[a] = a < d ? cur[base + (int64_t)a * post] : ff{0.f, 0.f};
+#pragma unroll
+                for (int c = 0; c < kMaxDim; ++c) {
+                    if (c >= d) break;
+                    ffacc acc;
+#pragma unroll
+                    for (int a = 0; a < kMaxDim; ++a)
+                        if (a < d) acc.add(ff_mul(x[a], Gs[a * 8 + c]));
+                    nxt[base + (int64_t)c * post] = acc.get();
+                }
             }
             __syncwarp();
             ff *t = cur; cur = nxt; nxt = t;
