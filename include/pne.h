@@ -209,6 +209,13 @@ pne_status pne_terms_export(pne_ctx *ctx, const pne_terms *t, void *stream, int3
  * or device pointer when data_on_device != 0.  Synchronises `stream`. */
 pne_status pne_partition_update(pne_ctx *ctx, pne_partition *p, const double *data, int32_t data_on_device,
                                 const pne_partition_opts *opts, void *stream);
+/* With opts->async_status != 0 the update returns without synchronising: the
+ * convergence record stays on the device and is read by the next pne_sum,
+ * pne_batch_run, pne_batch_create or pne_partition_update that involves the
+ * partition (pne_batch_run reads the records of all its partitions together
+ * and returns the first non-OK record status after writing the results).
+ * Work on another stream that uses the partition must wait for `stream`
+ * (an event), as with any stream-ordered call. */
 
 /* ---- batched form: one persistent launch over many networks -------------- */
 

@@ -566,6 +566,42 @@ pne_status partition_settle(pne_ctx *ctx, pne_partition *p)
     return partition_record(ctx, p, rec.data());
 }
 
+// Reads the deferred records of several partitions: every copy queued on its
+// partition's stream, then one wait per distinct stream.  Returns the first
+// non-OK record status (all records are read either way).
+pne_status partition_settle_many(pne_ctx *ctx, const std::vector<pne_partition *> &ps)
+{
+    std::vector<pne_partition *> pend;
+    size_t total = 0;
+    for (pne_partition *p : ps)
+        if (p->rec_pending && std::find(pend.begin(), pend.end(), p) == pend.end()) {
+            pend.push_back(p);
+            total += ((size_t)p->n_sets * 12 + 16 + 15) & ~size_t(15);
+        }
+    if (pend.empty()) return PNE_OK;
+    std::vector<char> fallback;
+    char *h = (char *)pinned_slot(0, total);
+    if (!h) { fallback.assign(total, 0); h = fallback.data(); }
+    std::vector<cudaStream_t> streams;
+    size_t off = 0;
+    for (pne_partition *p : pend) {
+        const size_t bytes = (size_t)p->n_sets * 12 + 16;
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h + off, p->rec_dev.ptr, bytes, cudaMemcpyDeviceToHost, p->last_stream));
+        if (std::find(streams.begin(), streams.end(), p->last_stream) == streams.end()) streams.push_back(p->last_stream);
+        off += (bytes + 15) & ~size_t(15);
+    }
+    for (cudaStream_t st : streams) PNE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    pne_status first = PNE_OK;
+    off = 0;
+    for (pne_partition *p : pend) {
+        const size_t bytes = (size_t)p->n_sets * 12 + 16;
+        const pne_status st = partition_record(ctx, p, h + off);
+        if (st != PNE_OK && first == PNE_OK) first = st;
+        off += (bytes + 15) & ~size_t(15);
+    }
+    return first;
+}
+
 }  // namespace pne
 
 using namespace pne;
@@ -753,7 +789,7 @@ void pne_partition_destroy(pne_partition *p)
     cudaStream_t s = p->last_stream;
     // the partition's buffers are views of one allocation; the converted
     // copies are allocated on demand
-    DevBuf *bufs[] = {&p->storage, &p->Mb32, &p->Mb16};
+    DevBuf *bufs[] = {&p->storage, &p->Mb32, &p->Mb16, &p->rec_own};
     for (DevBuf *b : bufs) dev_free(ctx, *b, s);
     if (p->geo) p->geo->free_stream = s;          // a geometry left without users is freed on this stream
     delete p;
@@ -1016,6 +1052,20 @@ pne_status pne_partition_update(pne_ctx *ctx, pne_partition *p, const double *da
     const int arith = opts ? opts->arithmetic : p->arithmetic;
     if (arith != 0 && arith != 1) { set_error(ctx, PNE_EINVAL, "arithmetic must be 0 or 1"); return PNE_EINVAL; }
     p->arithmetic = arith;
+    if (opts && opts->async_status) {
+        // deferred record, read by the next call that synchronises
+        if (!p->rec_dev.ptr) {
+            if ((st = dev_alloc(ctx, p->rec_own, B * 12 + 16, s))) return st;
+            p->rec_dev.ptr = p->rec_own.ptr;
+            p->rec_dev.bytes = p->rec_own.bytes;
+        }
+        if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, p->rec_dev.ptr, arith, cudaMemcpyDeviceToDevice)) ||
+            (st = launch_gauge(ctx, p, s, nullptr)))
+            return st;
+        p->mb32_dtype = -1;
+        p->rec_pending = true;
+        return PNE_OK;
+    }
     if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, rb, arith)) ||
         (st = launch_gauge(ctx, p, s, nullptr)))
         return st;
@@ -1312,6 +1362,10 @@ pne_status pne_batch_run(pne_ctx *ctx, pne_batch *b, void *stream, pne_result *o
     }
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (batch_status_host(b->plan)) { set_error(ctx, PNE_ETIMEOUT, "a batched sum waited too long"); return PNE_ETIMEOUT; }
+    // convergence records deferred by asynchronous partition updates
+    std::vector<pne_partition *> parts;
+    for (const pne_terms *t : b->terms) parts.push_back(const_cast<pne_partition *>(t->part));
+    const pne_status rec_st = partition_settle_many(ctx, parts);
     const double *h = batch_host_out(b->plan);
     const std::vector<int64_t> &off = batch_out_offsets(b->plan);
     int64_t r = 0;
@@ -1328,7 +1382,7 @@ pne_status pne_batch_run(pne_ctx *ctx, pne_batch *b, void *stream, pne_result *o
                             p->bp_iters[set], p->bp_residual[set]);
         }
     }
-    return PNE_OK;
+    return rec_st;
 }
 
 int64_t pne_batch_n_results(const pne_batch *b) { return b ? b->n_results : 0; }

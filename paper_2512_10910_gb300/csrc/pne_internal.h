@@ -213,7 +213,8 @@ struct pne_partition {
     std::vector<double> bp_residual; // per set
     cudaStream_t last_stream = nullptr;
     // deferred convergence record (async_status): [res B doubles][flags 4][iters B]
-    pne::DevBuf rec_dev;
+    pne::DevBuf rec_dev;             // deferred convergence record (a view of storage or of rec_own)
+    pne::DevBuf rec_own;             // its own buffer when an update defers a record the build did not
     bool rec_pending = false;
 };
 

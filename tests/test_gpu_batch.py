@@ -127,3 +127,33 @@ def test_batch_after_partition_update(ctx):
             assert abs(r["log_abs"] - fresh["log_abs"]) <= 1e-12
     finally:
         _free(parts, terms)
+
+
+def test_batch_after_asynchronous_updates_on_two_streams(ctx):
+    # partition updates that defer their convergence record, issued on two
+    # streams and joined into the batch's stream, give the same results, bit
+    # for bit, as synchronous updates
+    groups = [(I.square_lattice(6, 6, 3), [I.random_tensors(I.square_lattice(6, 6, 3), s) for s in (1, 2)]),
+              (I.square_lattice(5, 7, 2), [I.ising_tensors(I.square_lattice(5, 7, 2), b) for b in (0.3, 0.4)])]
+    parts, terms, keep = _make(ctx, groups)
+    new = [torch.from_numpy(np.concatenate([I.random_tensors(groups[0][0], s).flat_data()[0] for s in (5, 6)])).cuda(),
+           torch.from_numpy(np.concatenate([I.ising_tensors(groups[1][0], b).flat_data()[0] for b in (0.35, 0.45)])).cuda()]
+    try:
+        b = pne.pne_batch_create(ctx.h, terms, pne.PNE_F64)
+        for p, d in zip(parts, new):
+            pne.pne_partition_update(ctx.h, p, d)
+        ref = [(r["log_abs"], tuple(r["c"]), r["bp_iters"]) for r in pne.pne_batch_run(ctx.h, b)]
+        main = torch.cuda.current_stream()
+        side = [torch.cuda.Stream(), torch.cuda.Stream()]
+        for _ in range(2):
+            for p, d, st in zip(parts, new, side):
+                st.wait_stream(main)
+                pne.pne_partition_update(ctx.h, p, d, pne.PartitionOpts(1e-13, 10000, 0.0, 0, 1), st.cuda_stream)
+            for st in side:
+                main.wait_stream(st)
+            got = [(r["log_abs"], tuple(r["c"]), r["bp_iters"]) for r in pne.pne_batch_run(ctx.h, b)]
+            assert got == ref
+            assert all(it > 0 for _, _, it in got)
+        pne.pne_batch_destroy(b)
+    finally:
+        _free(parts, terms)
