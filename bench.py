@@ -198,7 +198,9 @@ def main():
     # the enumeration is geometry-only: it runs on a second stream while BP runs
     # on the first (the partition is built without waiting for its convergence
     # record, which pne_sum reads); the contraction waits for both
-    side = torch.cuda.Stream(dev)
+    # the enumeration is the longer chain: its stream gets the higher priority,
+    # so its small level launches are scheduled ahead of BP's blocks
+    side = torch.cuda.Stream(dev, priority=-1)
     side_h = side.cuda_stream
     joined = torch.cuda.Event()
 

@@ -899,15 +899,85 @@ pne_status side_streams(pne_ctx *ctx)
     return PNE_OK;
 }
 
-// Clusters perm[i0, i1) of every tensor set, G lanes per (cluster, set): the
-// running tensor sits once per group in shared memory and the group's lanes
-// split each step's outputs (lane j of the group takes outputs j, j + G, ...).
-// Every output is the same chain of multiply-adds in the same order as in
-// shaped_cluster, and the rescaling decision is the same, so the values agree
-// bit for bit with the lane-per-cluster form.  Neighbouring outputs read
-// neighbouring block entries, so a warp's gathers touch 32 / G clusters
-// instead of 32; groups sync and reduce over their own lane mask, so groups
-// of different shapes in one warp never wait for each other.
+// One cluster c of tensor set b contracted by a group of G lanes (lane `sub`
+// of the group, mask `gmask`): the running tensor X/Y sits once in shared
+// memory and the group's lanes split each step's outputs (lane j takes
+// outputs j, j + G, ...).  Every output is the same chain of multiply-adds in
+// the same order as in shaped_cluster, and the rescaling decision is the same,
+// so the values agree bit for bit with the lane-per-cluster form.
+template <typename T, typename L, int R, int G>
+__device__ __forceinline__ void group_cluster(const ContractParams &P, const int *plan, int nsteps, const int32_t *op,
+                                              const int32_t *soff, const int32_t *ssite, int64_t c, int b, T *X, T *Y,
+                                              int sub, unsigned gmask)
+{
+    if (sub == 0) X[0] = (T)1;
+    __syncwarp(gmask);
+    int expo = 0, nz = 0;
+    double zs = 1.0;
+    for (int t = 0; t < nsteps; ++t) {
+        const int *st = plan + t * kStepInts;
+        const int outsz = st[4], closz = st[5];
+        const int64_t mbase = (int64_t)b * P.stride + __ldg(soff + t);
+        int mxb = 0;
+        for (int o = sub; o < outsz; o += G) {
+            const int32_t *oo = op + (int64_t)o * closz;
+            T acc = (T)0;
+            int cc = 0;
+            for (; cc + 4 <= closz; cc += 4) {
+                int32_t pk[4];
+                T xv[4], mv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) pk[k] = __ldg(oo + cc + k);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    xv[k] = rnd<R>(X[pk[k] >> 16]);
+                    mv[k] = (T)L::get(P.M, mbase + (pk[k] & 0xffff));
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc = fma(xv[k], mv[k], acc);
+            }
+            for (; cc < closz; ++cc) {
+                const int32_t pk = __ldg(oo + cc);
+                acc = fma(rnd<R>(X[pk >> 16]), (T)L::get(P.M, mbase + (pk & 0xffff)), acc);
+            }
+            Y[o] = acc;
+            mxb = max(mxb, Expo<T>::biased(acc));
+        }
+        op += (int64_t)outsz * closz;
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) mxb = max(mxb, __shfl_xor_sync(gmask, mxb, off));
+        __syncwarp(gmask);
+        if (mxb > 0) {
+            const int e = mxb - (Expo<T>::kBias - 1);
+            if (e > Expo<T>::kWindow || e < -Expo<T>::kWindow) {
+                const T sc = (e < Expo<T>::kBias) ? Expo<T>::inv_pow2(e) : (T)ldexp(1.0, -e);
+                for (int o = sub; o < outsz; o += G) Y[o] *= sc;
+                expo += e;
+                __syncwarp(gmask);
+            }
+        }
+        T *tmp = X; X = Y; Y = tmp;
+        const int site = __ldg(ssite + t);
+        if (P.zero[(int64_t)b * P.n_sites + site]) { ++nz; zs *= P.scale[(int64_t)b * P.n_sites + site]; }
+    }
+    if (sub == 0) {
+        P.w[(int64_t)b * P.n_clusters + c] = ldexp((double)X[0], expo) * zs;
+        P.nzc[(int64_t)b * P.n_clusters + c] = nz;
+    }
+    __syncwarp(gmask);
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask(int lane)
+{
+    return (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - lane % G));
+}
+
+// Clusters perm[i0, i1) of every tensor set, a group of G lanes per (cluster,
+// set) (group_cluster).  Neighbouring outputs read neighbouring block entries,
+// so a warp's gathers touch 32 / G clusters instead of 32; groups sync and
+// reduce over their own lane mask, so groups of different shapes in one warp
+// never wait for each other.
 template <typename T, typename L, int R, int G>
 __global__ void __launch_bounds__(256) contract_group_kernel(ContractParams P, const int32_t *perm,
                                                              const int32_t *shape_of, const int32_t *plans,
@@ -920,7 +990,7 @@ __global__ void __launch_bounds__(256) contract_group_kernel(ContractParams P, c
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, sub = lane % G;
     const int gib = threadIdx.x / G, gpb = blockDim.x / G;            // group in block, groups per block
-    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - sub));
+    const unsigned gmask = group_mask<G>(lane);
     T *X0 = (T *)smem_raw + (int64_t)gib * 2 * xmax;
     T *X1 = X0 + xmax;
     const int64_t nc = i1 - i0;
@@ -929,66 +999,8 @@ __global__ void __launch_bounds__(256) contract_group_kernel(ContractParams P, c
         const int b = (int)(it / nc);
         const int64_t c = perm[i0 + it % nc];
         const int sh = shape_of[c];
-        const int *plan = plans + (int64_t)sh * kPlanInts;
-        const int nsteps = plan_steps[sh];
-        const int32_t *op = ops + op_off[sh];
-        const int32_t *soff = step_off + c * sstride, *ssite = step_site + c * sstride;
-        T *X = X0, *Y = X1;
-        if (sub == 0) X[0] = (T)1;
-        __syncwarp(gmask);
-        int expo = 0, nz = 0;
-        double zs = 1.0;
-        for (int t = 0; t < nsteps; ++t) {
-            const int *st = plan + t * kStepInts;
-            const int outsz = st[4], closz = st[5];
-            const int64_t mbase = (int64_t)b * P.stride + __ldg(soff + t);
-            int mxb = 0;
-            for (int o = sub; o < outsz; o += G) {
-                const int32_t *oo = op + (int64_t)o * closz;
-                T acc = (T)0;
-                int cc = 0;
-                for (; cc + 4 <= closz; cc += 4) {
-                    int32_t pk[4];
-                    T xv[4], mv[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) pk[k] = __ldg(oo + cc + k);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        xv[k] = rnd<R>(X[pk[k] >> 16]);
-                        mv[k] = (T)L::get(P.M, mbase + (pk[k] & 0xffff));
-                    }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) acc = fma(xv[k], mv[k], acc);
-                }
-                for (; cc < closz; ++cc) {
-                    const int32_t pk = __ldg(oo + cc);
-                    acc = fma(rnd<R>(X[pk >> 16]), (T)L::get(P.M, mbase + (pk & 0xffff)), acc);
-                }
-                Y[o] = acc;
-                mxb = max(mxb, Expo<T>::biased(acc));
-            }
-            op += (int64_t)outsz * closz;
-#pragma unroll
-            for (int off = G / 2; off > 0; off >>= 1) mxb = max(mxb, __shfl_xor_sync(gmask, mxb, off));
-            __syncwarp(gmask);
-            if (mxb > 0) {
-                const int e = mxb - (Expo<T>::kBias - 1);
-                if (e > Expo<T>::kWindow || e < -Expo<T>::kWindow) {
-                    const T sc = (e < Expo<T>::kBias) ? Expo<T>::inv_pow2(e) : (T)ldexp(1.0, -e);
-                    for (int o = sub; o < outsz; o += G) Y[o] *= sc;
-                    expo += e;
-                    __syncwarp(gmask);
-                }
-            }
-            T *tmp = X; X = Y; Y = tmp;
-            const int site = __ldg(ssite + t);
-            if (P.zero[(int64_t)b * P.n_sites + site]) { ++nz; zs *= P.scale[(int64_t)b * P.n_sites + site]; }
-        }
-        if (sub == 0) {
-            P.w[(int64_t)b * P.n_clusters + c] = ldexp((double)X[0], expo) * zs;
-            P.nzc[(int64_t)b * P.n_clusters + c] = nz;
-        }
-        __syncwarp(gmask);
+        group_cluster<T, L, R, G>(P, plans + (int64_t)sh * kPlanInts, plan_steps[sh], ops + op_off[sh],
+                                  step_off + c * sstride, step_site + c * sstride, c, b, X0, X1, sub, gmask);
     }
 }
 
@@ -1633,6 +1645,30 @@ __device__ void lane_contract(const BatchGroup &G, int64_t i, int b, T *X0, T *X
                             G.step_off + c * G.step_stride, G.step_site + c * G.step_stride, c, b, X0, X1);
 }
 
+// The 32 clusters of a contraction item by groups of G lanes: 32 / G groups,
+// group j taking clusters j, j + 32 / G, ... of the item; each group's
+// running tensors sit in its slice of the warp's shared region W (2 * aux
+// entries per group, within the 2 * 32 * xsm of the lane form).
+template <typename T, typename L, int R, int G>
+__device__ __forceinline__ void batch_groups(const BatchGroup &Gr, const BatchItem &wi, T *W, int lane)
+{
+    constexpr int NG = 32 / G;
+    const int gi = lane / G, sub = lane % G;
+    const unsigned gmask = group_mask<G>(lane);
+    T *X = W + (int64_t)gi * 2 * wi.aux;
+    T *Y = X + wi.aux;
+    const ContractParams &P = Gr.cp;
+    for (int k = 0; k < G; ++k) {
+        const int64_t i = wi.start + gi + (int64_t)k * NG;
+        if (i >= P.n_clusters) break;
+        const int64_t c = Gr.perm[i];
+        const int sh = Gr.shape_of[c];
+        group_cluster<T, L, R, G>(P, Gr.plans + (int64_t)sh * kPlanInts, Gr.plan_steps[sh], Gr.ops + Gr.op_off[sh],
+                                  Gr.step_off + c * Gr.step_stride, Gr.step_site + c * Gr.step_stride, c, wi.member,
+                                  X, Y, sub, gmask);
+    }
+}
+
 // One persistent launch: warps take items from one queue in order.  A sum item
 // of handle g waits until every contraction item of g has been counted done;
 // those items were taken earlier by running warps, so the wait ends.  It is
@@ -1645,8 +1681,8 @@ __global__ void fused_batch_kernel(const BatchGroup *groups, const BatchItem *it
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    T *S0 = (T *)smem_raw + (int64_t)wib * 2 * xsm * 32 + lane;
-    T *S1 = S0 + (int64_t)xsm * 32;
+    const int wstride = max(8 * xsm, 16 * min(xsm, 8));          // shared entries per warp
+
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     T *G0 = xscratch ? xscratch + gw * 2 * xglob * 32 + lane : nullptr;
     T *G1 = xscratch ? G0 + (int64_t)xglob * 32 : nullptr;
@@ -1658,9 +1694,18 @@ __global__ void fused_batch_kernel(const BatchGroup *groups, const BatchItem *it
         const BatchItem wi = items[it];
         const BatchGroup &G = groups[wi.g];
         if (wi.kind == 0) {
-            const int64_t i = wi.start + lane;
             const bool big = wi.aux > xsm;             // running tensors beyond the shared slices
-            if (i < G.cp.n_clusters) lane_contract<T, L, R>(G, i, wi.member, big ? G0 : S0, big ? G1 : S1);
+            if (G.shaped && !big) {
+                // groups of lanes per cluster in the warp's shared slices
+                T *W = (T *)smem_raw + (int64_t)wib * wstride;
+                if (wi.aux <= 8) batch_groups<T, L, R, 4>(G, wi, W, lane);
+                else batch_groups<T, L, R, 8>(G, wi, W, lane);
+            } else {
+                // bond dimension 2 (no running tensor) or a running tensor in
+                // the warp's global scratch
+                const int64_t i = wi.start + lane;
+                if (i < G.cp.n_clusters) lane_contract<T, L, R>(G, i, wi.member, G0, G1);
+            }
             __syncwarp();
             if (lane == 0) { __threadfence(); atomicAdd(done + wi.g, 1u); }
         } else {
@@ -1737,8 +1782,9 @@ __global__ void batch_finalize_kernel(const BatchGroup *groups, int G, const int
 size_t status_offset(int G) { return ((size_t)8 + (size_t)8 * G + 15) & ~(size_t)15; }
 
 // Running tensors of the fused batch live in shared memory up to kBatchSmemX
-// entries per lane; items whose clusters need more use a per-warp slice of a
-// global scratch buffer (same interleaved layout), sized for the launch shape.
+// entries, one pair per group of lanes (a warp's groups share one cluster
+// item); items whose clusters need more use a per-warp slice of a global
+// scratch buffer (one interleaved pair per lane), sized for the launch shape.
 constexpr int kBatchSmemX = 32;
 
 struct BatchPlan {
@@ -1874,7 +1920,9 @@ pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const size_t elem = (dtype == PNE_F64) ? 8 : 4;
     bp->xsm = std::min(bp->xmax, kBatchSmemX);
-    bp->smem_per_warp = 2 * (size_t)bp->xsm * 32 * elem;
+    // per warp: the running tensors of its lane groups (4 groups of 2 * aux
+    // entries for items up to 32 entries, 8 groups of 2 * 8 for items up to 8)
+    bp->smem_per_warp = (size_t)std::max(8 * bp->xsm, 16 * std::min(bp->xsm, 8)) * elem;
     *out = bp;
     return PNE_OK;
 }
