@@ -282,7 +282,9 @@ typedef struct {
 
 pne_status pne_server_create(pne_ctx *ctx, const pne_server_opts *opts, pne_server **out);
 /* Copies the network (host tensors; n_batch must be 1, no open indices) and
- * queues it; returns at once with the request id. */
+ * queues it; returns at once with the request id.  A served request's
+ * partition is built with float-float BP sweeps (pne_partition_opts
+ * arithmetic 1, tol 1e-13). */
 pne_status pne_server_submit(pne_server *s, const pne_network *net, int32_t max_order, uint64_t *id);
 /* PNE_OK and the result when the request is done (its record is then
  * released), PNE_EBUSY while it is queued or running, PNE_EINVAL for an

@@ -158,7 +158,9 @@ void prep_loop(pne_server *s, int w)
         net.site_ptr = r->site_ptr.data(); net.site_bonds = r->site_bonds.data();
         net.data = r->data.data(); net.data_off = r->data_off.data();
         net.data_on_device = 0; net.n_batch = 1;
-        pne_partition_opts po{1e-13, 10000, 0.0};
+        // float-float sweeps: one thread-block cluster per network, so the
+        // partitions of several requests run side by side on the FP32 pipes
+        pne_partition_opts po{1e-13, 10000, 0.0, 1, 0};
         pne_status rc = pne_build_partition(s->ctx, &net, &po, st, &r->part);
         if (rc == PNE_OK) {
             pne_enum_opts eo{r->K, PNE_MODE_LOOP, 1};

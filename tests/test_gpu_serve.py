@@ -66,7 +66,7 @@ def test_alone_equals_in_mix_and_single_path(ctx, dtype):
     finally:
         pne.pne_server_destroy(srv)
     for (net, K), a in zip(reqs, alone):
-        (single,) = ctx.expand(net, K, pne.PNE_MODE_LOOP, dtype)
+        (single,) = ctx.expand(net, K, pne.PNE_MODE_LOOP, dtype, arithmetic=1)   # the server's BP arithmetic
         tol = 1e-12 if dtype == pne.PNE_F64 else 1e-6
         assert abs(single["log_abs"] - a["log_abs"]) <= tol
         assert single["n_terms"] == a["n_terms"]
