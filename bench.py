@@ -573,7 +573,7 @@ def run_serve(args, wl, rank, world, local_rank):
     build_s = time.time() - t0
     dtype = pne.DTYPES[args.dtype]
     ctx = pne.Context(local_rank)
-    opts = pne.ServerOpts(64 << 30, 512, 6, 512, dtype, 0, 0)
+    opts = pne.ServerOpts(64 << 30, 512, 12, 512, dtype, 0, 0)
     srv = pne.pne_server_create(ctx.h, opts)
     # warm the geometry cache: one request per distinct (geometry, K)
     seen, warm = set(), []
