@@ -645,7 +645,6 @@ namespace {
 
 constexpr int kPlanInts = kMaxSteps * kStepInts;
 constexpr int kClassMin = 8;           // smallest running-tensor class of the shaped contraction
-constexpr int kGroupClassX = 8;        // classes from this running-tensor size on: a group of lanes per cluster
 // shared ints per warp of the plan kernel: plan, sites, spare, then a PlanWork
 // (declared below; its size is checked there)
 constexpr int kPlanWarpInts = kMaxSteps * kStepInts + kMaxSteps + 4 + 384;
@@ -861,34 +860,6 @@ __device__ __forceinline__ void shaped_cluster(const ContractParams &P, const in
     P.nzc[(int64_t)b * P.n_clusters + c] = nz;
 }
 
-// One cluster per lane; the 32 lanes of a warp take consecutive clusters in
-// shape order and run the same plan on their own sites.
-// Clusters perm[i0, i1) (one running-tensor class) of every tensor set.
-template <typename T, typename L, int R>
-__global__ void __launch_bounds__(256) contract_shaped_kernel(ContractParams P, const int32_t *perm,
-                                                              const int32_t *shape_of, const int32_t *plans,
-                                                              const int32_t *plan_steps, const int32_t *ops,
-                                                              const int64_t *op_off, const int32_t *step_off,
-                                                              const int32_t *step_site, int sstride, int xmax,
-                                                              int64_t i0, int64_t i1)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    T *X0 = (T *)smem_raw + (int64_t)wib * 2 * xmax * 32 + lane;
-    T *X1 = X0 + (int64_t)xmax * 32;
-    const int64_t groups = (i1 - i0 + 31) / 32;
-    const int64_t items = groups * P.n_members;
-    for (int64_t it = (int64_t)blockIdx.x * wpb + wib; it < items; it += (int64_t)gridDim.x * wpb) {
-        const int b = (int)(it / groups);
-        const int64_t i = i0 + (it % groups) * 32 + lane;
-        if (i >= i1) continue;
-        const int64_t c = perm[i];
-        const int sh = shape_of[c];
-        shaped_cluster<T, L, R>(P, plans + (int64_t)sh * kPlanInts, plan_steps[sh], ops + op_off[sh],
-                                step_off + c * sstride, step_site + c * sstride, c, b, X0, X1);
-    }
-}
-
 // Side streams of the context, created on first use (caller holds side_mu).
 pne_status side_streams(pne_ctx *ctx)
 {
@@ -1007,12 +978,10 @@ __global__ void __launch_bounds__(256) contract_group_kernel(ContractParams P, c
 template <typename T, typename L, int R>
 pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &rec, cudaStream_t s)
 {
-    auto kern = contract_shaped_kernel<T, L, R>;
     // one launch per running-tensor class, each with buffers (and so an
     // occupancy) sized for its own class; the classes are independent, so
     // when there are several they run concurrently on side streams forked
     // from and joined back into `s`
-    const size_t smem_cap = 200 * 1024;
     std::vector<size_t> cls;
     for (size_t q = 0; q + 1 < rec.class_start.size(); ++q)
         if (rec.class_start[q + 1] > rec.class_start[q]) cls.push_back(q);
@@ -1024,26 +993,18 @@ pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &
         if (st) return st;
         PNE_CUDA_TRY(ctx, cudaEventRecord(ctx->side_ev[0], s));
     }
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
     // the largest running tensors (fewest, longest clusters) start first, on `s`
     std::reverse(cls.begin(), cls.end());
     for (size_t j = 0; j < cls.size(); ++j) {
         const size_t q = cls[j];
         const int64_t i0 = rec.class_start[q], i1 = rec.class_start[q + 1];
         const int xmax = std::min(rec.class_xmax[q], std::max(rec.max_out, 1));
-        const int per_warp = 2 * xmax * 32 * (int)sizeof(T);
-        int wpb = (int)std::min<size_t>(8, std::max<size_t>(1, (smem_cap / 4) / per_warp));   // about four blocks per SM
-        const size_t smem = (size_t)wpb * per_warp;
-        const int64_t items = ((i1 - i0 + 31) / 32) * cp.n_members;
-        int64_t g = (items + wpb - 1) / wpb;
-        const int64_t cap = (int64_t)ctx->n_sm * 32;
-        if (g > cap) g = cap;
         cudaStream_t ls = s;
         if (fork && j > 0) {
             ls = ctx->side[(j - 1) % pne_ctx::kSideStreams];
             PNE_CUDA_TRY(ctx, cudaStreamWaitEvent(ls, ctx->side_ev[0], 0));
         }
-        if (xmax >= kGroupClassX) {
+        {
             // a group of lanes per cluster: 32 for large running tensors, else
             // about one lane per two outputs of the largest step
             const int G = xmax >= 32 ? 32 : (xmax >= 16 ? 8 : 4);
@@ -1064,14 +1025,7 @@ pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &
             else if (G == 8) launch(contract_group_kernel<T, L, R, 8>);
             else launch(contract_group_kernel<T, L, R, 4>);
             PNE_CUDA_TRY(ctx, cudaGetLastError());
-            continue;
         }
-        kern<<<(int)g, wpb * 32, smem, ls>>>(cp, (const int32_t *)rec.perm.ptr, (const int32_t *)rec.shape_of.ptr,
-                                             (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr,
-                                             (const int32_t *)rec.ops.ptr, (const int64_t *)rec.op_off.ptr,
-                                             (const int32_t *)rec.step_off.ptr, (const int32_t *)rec.step_site.ptr,
-                                             rec.step_stride, xmax, i0, i1);
-        PNE_CUDA_TRY(ctx, cudaGetLastError());
     }
     if (fork) {
         const size_t used = std::min<size_t>(cls.size() - 1, pne_ctx::kSideStreams);

@@ -196,6 +196,40 @@ def test_multi_edges_and_irregular_graph(ctx):
         _check_values(res, ref)
 
 
+def _random_multigraph(seed):
+    # a connected random multigraph (parallel bonds allowed), site degree <= 6
+    rng = np.random.default_rng(1000 + seed)
+    n = 7 + seed % 4
+    m = n + 5 + seed
+    deg = np.zeros(n, dtype=int)
+    edges = [(v, v + 1) for v in range(n - 1)]            # a path keeps it connected
+    for a, b in edges:
+        deg[a] += 1; deg[b] += 1
+    while len(edges) < m:
+        a, b = (int(x) for x in rng.integers(0, n, size=2))
+        if a == b or deg[a] >= 6 or deg[b] >= 6:
+            continue
+        edges.append((min(a, b), max(a, b)))
+        deg[a] += 1; deg[b] += 1
+    dims = [int(d) for d in rng.integers(2, 4, size=m)]
+    return I.grid_graph(n, edges, dims)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_multigraph_clusters_and_values(ctx, seed):
+    # the search's closing level (sizes K - 1 and K from the size K - 2 sets)
+    # and its two-bond closing test, on irregular graphs with parallel bonds:
+    # cluster lists bit-exact, values within the FP64 tolerance
+    net = I.random_tensors(_random_multigraph(seed), seed)
+    for K in (3, 4, 6, 8):
+        ref = X.pne(net, K, E.LOOP)
+        (res,), (edges, w) = ctx.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64, export=True)
+        cl, wc = _canon(edges, w)
+        assert cl == list(ref.clusters), (seed, K)
+        np.testing.assert_allclose(wc[0], ref.w, rtol=1e-9, atol=1e-13)
+        _check_values(res, ref)
+
+
 def test_invalid_input_is_rejected(ctx):
     net = I.random_tensors(I.square_lattice(3, 3, 2), 1)
     bad = I.Network(net.n_sites, net.bond_site, np.full(net.n_bonds, 9, dtype=np.int32), net.site_ptr,
