@@ -1162,24 +1162,32 @@ pne_status shapes_plan(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePr
     const int64_t n = (int64_t)rec.n_clusters;
     const ContractParams cp = shape_params(g, rec);
     pne_status st;
-    std::vector<unsigned long long> h(n);
+    std::vector<unsigned long long> hv;
+    const unsigned long long *h = (const unsigned long long *)sp.h_pinned;
     if (sp.h_pinned) {
         HostScope hw__(ctx, "sync_shapes");
         PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-        std::memcpy(h.data(), sp.h_pinned, n * 8);
     } else {
-        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), sp.dh.ptr, n * 8, cudaMemcpyDeviceToHost, s));
+        hv.resize(n);
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(hv.data(), sp.dh.ptr, n * 8, cudaMemcpyDeviceToHost, s));
         PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        h = hv.data();
     }
     dev_free(ctx, sp.dh, s);
-    std::unordered_map<unsigned long long, int32_t> id;
-    id.reserve(1024);
+    // shape ids by first appearance: an open-addressing table of the hashes
+    // (linear probing, at most half full)
+    size_t cap = 64;
+    while (cap < 2 * (size_t)n) cap *= 2;
+    std::vector<unsigned long long> keys(cap);
+    std::vector<int32_t> vals(cap, -1);
     sp.shape.assign(n, 0);
     sp.rep.clear();
     for (int64_t c = 0; c < n; ++c) {
-        auto it = id.find(h[c]);
-        if (it == id.end()) { it = id.emplace(h[c], (int32_t)sp.rep.size()).first; sp.rep.push_back((int32_t)c); }
-        sp.shape[c] = it->second;
+        const unsigned long long k = h[c];
+        size_t at = (size_t)((k ^ (k >> 29)) * 0x9E3779B97F4A7C15ull) & (cap - 1);
+        while (vals[at] >= 0 && keys[at] != k) at = (at + 1) & (cap - 1);
+        if (vals[at] < 0) { keys[at] = k; vals[at] = (int32_t)sp.rep.size(); sp.rep.push_back((int32_t)c); }
+        sp.shape[c] = vals[at];
     }
     // exact key check against the representative (a mismatch gets its own
     // shape) and the plans of the representatives, read back together
