@@ -86,3 +86,29 @@ def test_admission_respects_the_budget(ctx):
         assert all(r["n_terms"] > 0 for r, _ in out)
     finally:
         pne.pne_server_destroy(srv)
+
+
+def test_failed_request_reports_its_status_and_error_text(ctx):
+    # a network whose tensors are all zero has zero BP messages: the partition
+    # reports PNE_EDEGENERATE (a flag the kernels set, no fault); the server
+    # finishes that request with the status, keeps serving the others, and
+    # records the failing call's message
+    good = I.aklt_tensors(I.square_lattice(5, 5, 4))
+    bad = I.aklt_tensors(I.square_lattice(5, 5, 4))
+    flat = np.zeros_like(bad.flat_data()[0])
+    ns_bad, keep_bad = pne.network_struct(bad, data=flat)
+    ns_good, keep_good = pne.network_struct(good)
+    srv = pne.pne_server_create(ctx.h, pne.ServerOpts(0, 0, 2, 0, pne.PNE_F64, 0, 0))
+    try:
+        assert pne.pne_server_first_error(srv) == ""
+        rid_bad = pne.pne_server_submit(srv, ns_bad, 4)
+        rid_good = pne.pne_server_submit(srv, ns_good, 4)
+        pne.pne_server_drain(srv)
+        st, res, info = pne.pne_server_poll(srv, rid_bad)
+        assert st == pne.PNE_EDEGENERATE and res is None
+        res, info = _wait(srv, rid_good)
+        assert res["n_terms"] > 0
+        msg = pne.pne_server_first_error(srv)
+        assert msg.startswith("request %d:" % rid_bad) and "zero message" in msg
+    finally:
+        pne.pne_server_destroy(srv)
