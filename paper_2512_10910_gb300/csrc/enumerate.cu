@@ -25,10 +25,11 @@
 // already has, so a node of size K - 2 finds both remaining sizes in one
 // warp-parallel step (each lane's child, then the child's closing bonds among
 // the node's later candidates) and the far more numerous sets of size K - 1
-// that cannot be closed are never stored.  Every unit first counts what it emits per
-// cluster size; an exclusive scan over (size, unit) gives each unit its output
-// slots, and a second pass writes.  The output is grouped by size and
-// deterministic.
+// that cannot be closed are never stored; a child of size K - 2 is kept only
+// if two more candidate bonds can still close it (closable2).  Every unit
+// first counts what it emits per cluster size; an exclusive scan over (size,
+// unit) gives each unit its output slots, and a second pass writes.  The
+// output is grouped by size and deterministic.
 //
 // Terms (Eq. A4): a term is a set of pairwise vertex-disjoint clusters with
 // total size <= K (the connected components of one P/Q string).  Tuples
