@@ -692,10 +692,10 @@ __global__ void shape_hash_kernel(ContractParams P, unsigned long long *hash)
 }
 
 // 1 where a cluster's key differs from its shape representative's (a hash collision)
-__global__ void shape_verify_kernel(ContractParams P, const int32_t *shape_of, const int32_t *rep, int32_t *bad)
+__device__ void verify_range(const ContractParams &P, const int32_t *shape_of, const int32_t *rep, int32_t *bad,
+                             int64_t first, int64_t stride)
 {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < P.n_clusters;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t c = first; c < P.n_clusters; c += stride) {
         int32_t a[2 + 5 * 32], b[2 + 5 * 32];
         const int na = cluster_key(P, c, a, 2 + 5 * 32);
         const int nb = cluster_key(P, rep[shape_of[c]], b, 2 + 5 * 32);
@@ -708,15 +708,15 @@ __global__ void shape_verify_kernel(ContractParams P, const int32_t *shape_of, c
 // One plan per shape (built by lane 0 of a warp), plus the per-shape figures the
 // host needs: stats[sh] = {steps (-1: no plan), multiply-adds, largest running
 // tensor, 0}.
-__global__ void shape_plan_kernel(ContractParams P, const int32_t *rep, int n_shapes, int32_t *plans,
-                                  int32_t *steps, int32_t *stats)
+__device__ void plan_range(const ContractParams &P, const int32_t *rep, int n_shapes, int32_t *plans, int32_t *steps,
+                           int32_t *stats, int bid, int nblk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *plan = (int *)smem_raw + wib * kPlanWarpInts;
     int *sites = plan + kMaxSteps * kStepInts;
     PlanWork &W = *reinterpret_cast<PlanWork *>(sites + kMaxSteps + 4);
-    for (int sh = blockIdx.x * kCtWarps + wib; sh < n_shapes; sh += gridDim.x * kCtWarps) {
+    for (int sh = bid * kCtWarps + wib; sh < n_shapes; sh += nblk * kCtWarps) {
         const int n = build_plan_warp(P, rep[sh], plan, sites, kWarpTensorMax, W, lane);
         if (lane == 0) {
             steps[sh] = n;
@@ -727,6 +727,26 @@ __global__ void shape_plan_kernel(ContractParams P, const int32_t *rep, int n_sh
         __syncwarp();
         for (int i = lane; i < (n > 0 ? n : 0) * kStepInts; i += 32) plans[(int64_t)sh * kPlanInts + i] = plan[i];
         __syncwarp();
+    }
+}
+
+__global__ void shape_plan_kernel(ContractParams P, const int32_t *rep, int n_shapes, int32_t *plans,
+                                  int32_t *steps, int32_t *stats)
+{
+    plan_range(P, rep, n_shapes, plans, steps, stats, blockIdx.x, gridDim.x);
+}
+
+// The exact-key check of every cluster against its representative and the
+// representatives' plans in one launch: blocks [0, plan_blocks) build plans,
+// the others check keys (one thread per cluster), so the two run side by side.
+__global__ void shape_verify_plan_kernel(ContractParams P, const int32_t *shape_of, const int32_t *rep, int32_t *bad,
+                                         int n_shapes, int32_t *plans, int32_t *steps, int32_t *stats, int plan_blocks)
+{
+    if ((int)blockIdx.x < plan_blocks) {
+        plan_range(P, rep, n_shapes, plans, steps, stats, blockIdx.x, plan_blocks);
+    } else {
+        const int64_t vb = (int64_t)blockIdx.x - plan_blocks, nvb = (int64_t)gridDim.x - plan_blocks;
+        verify_range(P, shape_of, rep, bad, vb * blockDim.x + threadIdx.x, nvb * blockDim.x);
     }
 }
 
@@ -1107,9 +1127,18 @@ pne_status plans_launch(pne_ctx *ctx, const ContractParams &cp, EnumRecord &rec,
         (e = dev_alloc(ctx, rec.plan_steps, (size_t)ns * 4, s)) || (e = dev_alloc(ctx, sp.dstats, (size_t)ns * 16, s)))
         return e;
     const size_t smem = (size_t)kCtWarps * kPlanWarpInts * 4;
-    shape_plan_kernel<<<grid_for(ns, kCtWarps, ctx->n_sm, 16), kCtWarps * 32, smem, s>>>(
-        cp, (const int32_t *)sp.drep.ptr, ns, (int32_t *)rec.plans.ptr, (int32_t *)rec.plan_steps.ptr,
-        (int32_t *)sp.dstats.ptr);
+    const int pblocks = grid_for(ns, kCtWarps, ctx->n_sm, 16);
+    if (with_bad) {
+        // with the verification of every cluster in the same launch
+        const int vblocks = grid_for(n, kCtWarps * 32, ctx->n_sm);
+        shape_verify_plan_kernel<<<pblocks + vblocks, kCtWarps * 32, smem, s>>>(
+            cp, (const int32_t *)sp.dshape.ptr, (const int32_t *)sp.drep.ptr, (int32_t *)sp.dbad.ptr, ns,
+            (int32_t *)rec.plans.ptr, (int32_t *)rec.plan_steps.ptr, (int32_t *)sp.dstats.ptr, pblocks);
+    } else {
+        shape_plan_kernel<<<pblocks, kCtWarps * 32, smem, s>>>(
+            cp, (const int32_t *)sp.drep.ptr, ns, (int32_t *)rec.plans.ptr, (int32_t *)rec.plan_steps.ptr,
+            (int32_t *)sp.dstats.ptr);
+    }
     PNE_CUDA_TRY(ctx, cudaGetLastError());
     sp.stats.assign((size_t)ns * 4, 0);
     sp.nb = with_bad ? (size_t)n * 4 : 0;
@@ -1197,9 +1226,6 @@ pne_status shapes_plan(pne_ctx *ctx, const Geometry &g, EnumRecord &rec, ShapePr
     if ((st = upload(ctx, sp.dshape.ptr, sp.shape.data(), n * 4, s)) ||
         (st = upload(ctx, sp.drep.ptr, sp.rep.data(), sp.rep.size() * 4, s)))
         return st;
-    shape_verify_kernel<<<grid_for(n, 128, ctx->n_sm), 128, 0, s>>>(cp, (const int32_t *)sp.dshape.ptr,
-                                                                  (const int32_t *)sp.drep.ptr, (int32_t *)sp.dbad.ptr);
-    PNE_CUDA_TRY(ctx, cudaGetLastError());
     sp.ns = (int)sp.rep.size();
     sp.bad.assign(n, 0);
     if ((st = plans_launch(ctx, cp, rec, sp, true, s))) return st;
