@@ -867,7 +867,12 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
                 };
                 if (shapes) {
                     if (!ls.s) {
-                        PNE_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ls.s, cudaStreamNonBlocking));
+                        // the shape stage sits on the enumeration's critical path: the
+                        // device's highest stream priority, so its small launches are
+                        // scheduled ahead of other streams' waiting blocks
+                        int least = 0, greatest = 0;
+                        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+                        PNE_CUDA_TRY(ctx, cudaStreamCreateWithPriority(&ls.s, cudaStreamNonBlocking, greatest));
                         PNE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ls.fork, cudaEventDisableTiming));
                         PNE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ls.join, cudaEventDisableTiming));
                     }
