@@ -355,3 +355,34 @@ def test_async_partition_and_enumeration_on_a_second_stream(ctx):
     res = pne.pne_sum(ctx.h, terms, None, allow_noconv=True)
     assert all(r["bp_iters"] == 0 for r in res)
     pne.pne_terms_destroy(terms); pne.pne_partition_destroy(part)
+
+
+def test_full_size_cluster_and_term_counts_match_the_oracle_golden_file(ctx):
+    # lattices too large for the oracle inside a test run (the 16x16 bench
+    # geometry and the 8x8x8 one among them): counts written by the oracle
+    # (tests/golden/make_golden.py), bit-exact on the GPU, clusters by size too
+    import json
+    import os
+    from collections import Counter
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cluster_counts.json")))["cases"]
+    geoms = {"square16x16": I.square_lattice(16, 16, 2), "square24x24": I.square_lattice(24, 24, 2),
+             "cubic6x6x6": I.cubic_lattice(6, 6, 6, 2), "cubic8x8x8": I.cubic_lattice(8, 8, 8, 2),
+             "cubic4x4x4_K10": I.cubic_lattice(4, 4, 4, 2)}
+    assert set(geoms) == set(golden)
+    for name, g in geoms.items():
+        ref = golden[name]
+        net = I.ising_tensors(g, 0.3)
+        ns, keep = pne.network_struct(net)
+        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0))
+        try:
+            terms, nc, nt = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(ref["K"], pne.PNE_MODE_LOOP, 0))
+            try:
+                assert (nc, nt) == (ref["n_clusters"], ref["n_terms"]), name
+                edges, _ = pne.pne_terms_export(ctx.h, terms, nc, ref["K"], with_values=False)
+                by_size = Counter(int((row >= 0).sum()) for row in edges)
+                assert {str(k): v for k, v in sorted(by_size.items())} == ref["clusters_by_size"], name
+            finally:
+                pne.pne_terms_destroy(terms)
+        finally:
+            pne.pne_partition_destroy(part)
+        del keep
