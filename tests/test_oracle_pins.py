@@ -357,3 +357,21 @@ def test_neumaier_and_power_series_log():
     l = X.power_series_log(c, 5)
     for k in range(1, 6):
         assert l[k] == pytest.approx((-1) ** (k + 1) * (a ** k + b ** k) / k, rel=1e-14)
+
+
+def test_golden_count_file_is_the_oracle_output():
+    # the stored full-size counts come from the oracle alone: recompute the
+    # cheapest entry (the 16x16 bench geometry, K = 8) and compare every field
+    import json
+    import os
+    from collections import Counter
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cluster_counts.json")))
+    ref = golden["cases"]["square16x16"]
+    g = I.square_lattice(16, 16, 2)
+    cl = E.clusters_grow(g, 8, E.LOOP)
+    terms = E.enumerate_terms(g, cl, 8)
+    assert (len(cl), len(terms)) == (ref["n_clusters"], ref["n_terms"]) == (2827, 27216)
+    by_size = Counter(len(c) for c in cl)
+    by_order = Counter(sum(len(cl[i]) for i in t) for t in terms)
+    assert {str(k): v for k, v in sorted(by_size.items())} == ref["clusters_by_size"]
+    assert {str(k): v for k, v in sorted(by_order.items())} == ref["terms_by_order"]
