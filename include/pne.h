@@ -157,8 +157,9 @@ pne_status pne_ctx_set_allocator(pne_ctx *ctx, pne_alloc_fn alloc, pne_free_fn f
  * messages to unit overlap, gauge every closed bond so that P = e0 e0^T and
  * Q = diag(0,1,..,1), and keep the gauged site tensors, z_v and the vacuum
  * value on the device.  Synchronises `stream` once at the end to read the
- * convergence record.  Returns PNE_ENOCONV (handle still returned, usable)
- * when some tensor set did not converge, PNE_EDEGENERATE on a zero overlap. */
+ * convergence record (unless opts->async_status: see pne_partition_opts).
+ * Returns PNE_ENOCONV (handle still returned, usable) when some tensor set
+ * did not converge, PNE_EDEGENERATE on a zero overlap. */
 pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net,
                                const pne_partition_opts *opts, void *stream,
                                pne_partition **out);
@@ -168,11 +169,14 @@ void pne_partition_destroy(pne_partition *p);
  * mode) and the terms (vertex-disjoint cluster tuples with total size <= K,
  * Eq. A4).  Geometry only: the lists are shared by every tensor set and
  * cached in the context when use_cache != 0.  Synchronises `stream` while it
- * searches (the counts size the buffers).  With use_cache != 0 the returned
- * lists and buffers are complete on return and may be used from any stream;
- * with use_cache == 0 their last writes are still queued on `stream`, so use
- * them on `stream` or after it (an event or a synchronisation).  n_clusters /
- * n_terms may be NULL. */
+ * searches (the counts size the buffers).  The contraction plans of the
+ * clusters are prepared on a second stream lent from the context (created at
+ * the device's highest stream priority) and joined back into `stream` before
+ * the call returns.  With use_cache != 0 the returned lists and buffers are
+ * complete on return and may be used from any stream; with use_cache == 0
+ * their last writes are still queued on `stream`, so use them on `stream` or
+ * after it (an event or a synchronisation).  n_clusters / n_terms may be
+ * NULL. */
 pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part,
                                const pne_enum_opts *opts, void *stream,
                                pne_terms **out, uint64_t *n_clusters, uint64_t *n_terms);
