@@ -1261,7 +1261,6 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     const int D = fuse ? K - 2 : ((K <= 1) ? 1 : std::min(kPrefixMax, K - 1));
     const int final_kind = fuse ? 3 : ((K <= 1) ? 0 : (D == K - 1 ? 1 : 2));
     const bool small = (K <= 12 && umax_need <= 64);
-    // chunks of the blocked passes: one wave of resident blocks
     // chunks of the blocked passes: one wave of resident blocks (the occupancy
     // is queried once per context)
     if (ctx->occ_expand < 0) {
@@ -1269,7 +1268,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         PNE_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, expand_kernel<kCount, true>, 32 * kExpandWarps, 0));
         ctx->occ_expand = a;
     }
-    const int G = ctx->n_sm * std::max(1, ctx->occ_expand);
+    const int G = ctx->n_sm * std::max(1, ctx->occ_expand.load());
     const int Gd = grid1(1 << 20, 128, ctx->n_sm);    // grid of the depth-first kernel
     const std::string hint_key = std::to_string(g.hash) + ":" + std::to_string(Mc) + ":" + std::to_string(K) + ":" +
                                  std::to_string(mode);

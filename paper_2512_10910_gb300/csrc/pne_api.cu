@@ -1235,7 +1235,11 @@ struct pne_batch {
 
 namespace {
 
+// Launch shapes found by the autotuner, by batch signature (process-wide;
+// g_tune_mu guards the map, its file and the one-time load).
 std::map<std::string, std::pair<std::pair<int, int>, double>> g_tune_cache;
+std::mutex g_tune_mu;
+bool g_tune_loaded = false;
 
 void tune_cache_load()
 {
@@ -1297,8 +1301,8 @@ pne_status pne_batch_create(pne_ctx *ctx, int32_t n, pne_terms *const *terms, pn
         }
         b->wpb = w0; b->bps = b0;
     } else {
-        static bool loaded = false;
-        if (!loaded) { tune_cache_load(); loaded = true; }
+        std::unique_lock<std::mutex> tlk(g_tune_mu);
+        if (!g_tune_loaded) { tune_cache_load(); g_tune_loaded = true; }
         uint64_t ncl = 0, nmem = 0;
         for (pne_terms *t : b->terms) { ncl += t->rec->n_clusters; nmem += t->part->n_members; }
         const std::string key = "d" + std::to_string(dtype) + "_g" + std::to_string(n) + "_c" + std::to_string(ncl) +

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 #include <memory>
+#include <atomic>
 #include <map>
 #include <mutex>
 
@@ -120,7 +121,7 @@ struct HostRec {
 };
 struct Profiler {
     std::mutex mu;
-    bool on = false;
+    std::atomic<bool> on{false};    // read without the lock by every launch site
     bool trace = false;             // keep every record in order (a timeline), not only the sums
     cudaEvent_t base = nullptr;     // GPU time origin of the timeline
     double host_base = 0.0;         // steady-clock ms at the origin
@@ -138,7 +139,7 @@ struct pne_ctx {
     int device = 0;
     int n_sm = 0;
     int64_t arena_max = 0;        // node-arena limit of the cluster search (0: the built-in limit)
-    int occ_expand = -1;          // resident blocks per SM of the search kernel (-1: not queried)
+    std::atomic<int> occ_expand{-1};   // resident blocks per SM of the search kernel (-1: not queried)
     pne_alloc_fn alloc = nullptr;
     pne_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
