@@ -90,3 +90,23 @@ def test_results_sequence_converts_on_access():
     assert c["log_abs"] == 2.0
     with pytest.raises(IndexError):
         res[3]
+
+
+def test_open_tensor_assembles_set_major_row_major_slices():
+    import math
+    import numpy as np
+    dims, n_sets = (2, 3), 2
+    arr = (pne.Result * (n_sets * 6))()
+    want = np.zeros((n_sets,) + dims)
+    for r in range(n_sets * 6):
+        b, a = divmod(r, 6)
+        i, j = divmod(a, 3)
+        v = (-1.0) ** r * (1.0 + r)
+        want[b, i, j] = v
+        arr[r].sign = 1 if v > 0 else -1
+        arr[r].log_abs = math.log(abs(v))
+        arr[r].n_orders = 1
+    arr[5].sign = 0                      # a zero result (Z_ref = 0 on that slice)
+    want[0, 1, 2] = 0.0
+    got = pne.open_tensor(pne.Results(arr), dims, n_sets)
+    np.testing.assert_allclose(got, want, rtol=1e-15)
