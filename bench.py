@@ -588,8 +588,19 @@ def run_serve(args, wl, rank, world, local_rank):
             seen.add(key)
             warm.append(pne.pne_server_submit(srv, ns, r[3]))
     pne.pne_server_drain(srv)
+    warm_failed = {}
     for rid in warm:
-        pne.pne_server_poll(srv, rid)
+        st, _, _ = pne.pne_server_poll(srv, rid)
+        if st != pne.PNE_OK:
+            warm_failed[int(st)] = warm_failed.get(int(st), 0) + 1
+    if warm_failed:
+        # a failed warm-up request is reported, and the trace is not run on a
+        # context that may have lost its device
+        print(json.dumps({"error": "warm-up requests failed", "failed_by_status": warm_failed,
+                          "first_error": pne.pne_server_first_error(srv)}), file=sys.stderr)
+        pne.pne_server_destroy(srv)
+        ctx.close()
+        return 1
     clocks = ClockSampler(local_rank)
     clocks.start()
     ids = []

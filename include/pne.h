@@ -17,10 +17,21 @@
  *   - Inputs are borrowed for the duration of the call and copied.
  *   - Handles (pne_ctx, pne_partition, pne_terms) are owned by the caller once
  *     returned and released with the matching *_destroy call; device memory
- *     they hold is freed there (stream-ordered on the stream last used).
+ *     they hold is released there, stream-ordered behind the work already
+ *     queued for the handle (on every stream that used it), so a handle may be
+ *     destroyed while that work is still running.  Destroy batches before the
+ *     terms handles they hold, and terms handles before the partition they
+ *     were enumerated from.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls are asynchronous on it unless stated otherwise.
- *   - One context serves one device and one host thread at a time.
+ *   - One context serves one device.  It may be used by several host threads
+ *     at once, provided each handle (partition, terms, batch) is used by one
+ *     thread at a time: the context's shared state -- the geometry and
+ *     enumeration caches, launch decisions, stream and event pools, the
+ *     profiler -- is guarded, and objects shared between handles (a cached
+ *     geometry or enumeration) are released only after every stream that used
+ *     them.  pne_ctx_set_allocator and pne_ctx_destroy must not overlap any
+ *     other call on the context.
  *   - Floating point: partitions (messages, gauge, site values) are FP64;
  *     cluster contractions run in the pne_dtype given; term products and the
  *     per-order sums are FP64.
@@ -133,7 +144,13 @@ typedef struct {
     int32_t n_zero_sites;    /* sites with z_v == 0                            */
     double log_series;       /* ln|Z_ref| + sum_{k=1..K} [x^k] ln(sum_j c_j x^j);
                                 NaN when undefined (not part of the paper)    */
-    double err_bound;        /* rounding bound of the dtype on Z_K, relative  */
+    double err_bound;        /* a-priori rounding bound on Z_K, relative:
+                                (gamma(2(K+1)) u_dtype sum_{k}|c_k|' +
+                                gamma(K + 2 + log2 n_terms) 2^-53 sum_k|c_k|)
+                                / |sum_k c_k|, where ' leaves out the exact
+                                empty term, gamma(n) = n u / (1 - n u) and
+                                u_dtype = 2^-53, 2^-24, 2^-11, 2^-8 for F64,
+                                F32, TF32, BF16                               */
     uint64_t n_terms, n_clusters;
     int32_t bp_iters;        /* sweeps BP took for this tensor set            */
     double bp_residual;      /* last sweep's largest message change           */

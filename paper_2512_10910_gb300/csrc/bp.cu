@@ -1287,16 +1287,12 @@ int grid_for(int64_t n, int block, int n_sm)
 // ---------------------------------------------------------------- host launchers
 namespace {
 
-// Raises a kernel's dynamic shared-memory limit once per context and size
-// (slot: one per kernel).
+// Raises a kernel's dynamic shared-memory limit (process-wide, only upwards).
 template <typename F>
 void grant_smem(pne_ctx *ctx, int slot, F func, size_t bytes)
 {
-    if (bytes <= 48 * 1024) return;
-    std::lock_guard<std::mutex> lk(ctx->launch_mu);
-    if (bytes <= ctx->bp_smem_set[slot]) return;
-    cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    ctx->bp_smem_set[slot] = bytes;
+    (void)ctx; (void)slot;
+    grant_dynamic_smem((const void *)func, bytes);
 }
 
 }  // namespace
@@ -1362,6 +1358,13 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
             ff_prepare_kernel<<<grid_for(warps * 32, 256, ctx->n_sm), 256, 0, s>>>(
                 (const double *)p->T.ptr, Tff, g.d_tens_off, g.n_sites, n_sets, stride, mff, g.d_site_bonds,
                 g.d_bond_dim, g.n_legs, (uint32_t *)base, (int64_t)(bytes / 4));
+        }
+        // the sweeps read what this launch writes (pair tensors, first
+        // messages, cleared scratch words): it must have been queued
+        if (cudaGetLastError() != cudaSuccess) {
+            dev_free(ctx, scratch, s);
+            set_error(ctx, PNE_ECUDA, "ff_prepare_kernel launch failed");
+            return PNE_ECUDA;
         }
         BPFFParams fp;
         fp.n_sets = n_sets; fp.n_sites = g.n_sites; fp.n_legs = g.n_legs;
@@ -1471,6 +1474,11 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         ProfScope ps(ctx, s, "bp_init");
         bp_init_kernel<<<grid_for((int64_t)n_sets * g.n_legs, 256, ctx->n_sm), 256, 0, s>>>(
             msg, g.d_site_ptr, g.d_site_bonds, g.d_bond_dim, g.n_sites, g.n_legs, n_sets);
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+        dev_free(ctx, scratch, s);
+        set_error(ctx, PNE_ECUDA, "bp_init_kernel launch failed");
+        return PNE_ECUDA;
     }
 
     BPParams prm;
@@ -1794,7 +1802,7 @@ extern "C" pne_status pne_bp_messages_noalloc(const pne_network *net, double tol
         // only ever raised: a context may have granted this kernel more already
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, bp_persistent_kernel) != cudaSuccess || fa.maxDynamicSharedSizeBytes < (int)smem)
-            PNE_CUDA_TRY(nullptr, cudaFuncSetAttribute(bp_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            PNE_CUDA_TRY(nullptr, grant_dynamic_smem((const void *)bp_persistent_kernel, smem));
     }
     int per_sm = 0;
     PNE_CUDA_TRY(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bp_persistent_kernel, kBpWarps * 32, smem));

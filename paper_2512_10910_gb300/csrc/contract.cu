@@ -632,7 +632,7 @@ template <typename KERN>
 pne_status run_general(pne_ctx *ctx, KERN kern, const ContractParams &cp, size_t elem, cudaStream_t s)
 {
     const size_t smem = (size_t)kCtWarps * ((kMaxSteps * kStepInts + kMaxSteps + 4) * 4 + 2 * kWarpTensorMax * elem);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    grant_dynamic_smem((const void *)kern, smem);
     const int g = grid_for(cp.n_clusters, kCtWarps, ctx->n_sm, 16);
     kern<<<g, kCtWarps * 32, smem, s>>>(cp);
     PNE_CUDA_TRY(ctx, cudaGetLastError());
@@ -1034,7 +1034,7 @@ pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &
             int64_t g2 = (items2 + gpb - 1) / gpb;
             if (g2 > (int64_t)ctx->n_sm * 16) g2 = (int64_t)ctx->n_sm * 16;
             auto launch = [&](auto kernel) {
-                if (smem2 > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+                grant_dynamic_smem((const void *)kernel, smem2);
                 kernel<<<(int)g2, 256, smem2, ls>>>(cp, (const int32_t *)rec.perm.ptr, (const int32_t *)rec.shape_of.ptr,
                                                     (const int32_t *)rec.plans.ptr, (const int32_t *)rec.plan_steps.ptr,
                                                     (const int32_t *)rec.ops.ptr, (const int64_t *)rec.op_off.ptr,
@@ -1784,16 +1784,18 @@ struct BatchPlan {
     std::vector<int64_t> out_off;
     DevBuf groups, items, descs, partials, fin_start, counters, d_out;
     double *h_out = nullptr;
+    size_t h_out_bytes = 0;
     size_t smem_per_warp = 0;
 };
 
 double *batch_host_out(BatchPlan *bp) { return bp->h_out; }
 const std::vector<int64_t> &batch_out_offsets(BatchPlan *bp) { return bp->out_off; }
 
+// The status words arrive with the results (read after the run's stream is
+// synchronised): they sit right after the result doubles.
 int32_t batch_status_host(BatchPlan *bp)
 {
-    int32_t st[2] = {0, 0};
-    cudaMemcpy(st, (char *)bp->counters.ptr + status_offset(bp->G), 8, cudaMemcpyDeviceToHost);
+    const int32_t *st = (const int32_t *)(bp->h_out + std::max<int64_t>(bp->out_doubles, 1));
     return st[0] | st[1];
 }
 
@@ -1894,10 +1896,17 @@ pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms
         (st = dev_alloc(ctx, bp->fin_start, fin_start.size() * 8, s)) ||
         (st = dev_alloc(ctx, bp->counters, cnt_bytes, s)) ||
         (st = dev_alloc(ctx, bp->d_out, std::max<int64_t>(out_off, 1) * 8, s))) {
-        batch_plan_destroy(ctx, bp);
+        batch_plan_destroy(ctx, bp, s);
         return st;
     }
-    PNE_CUDA_TRY(ctx, cudaMallocHost((void **)&bp->h_out, std::max<int64_t>(out_off, 1) * 8));
+    // results and the two status words, in pinned memory from the context's
+    // pool (a cudaFreeHost per batch would synchronise the whole device)
+    bp->h_out = (double *)take_pinned(ctx, (size_t)(std::max<int64_t>(out_off, 1) + 1) * 8, &bp->h_out_bytes);
+    if (!bp->h_out) {
+        batch_plan_destroy(ctx, bp, s);
+        set_error(ctx, PNE_ENOMEM, "no pinned host memory for the batch results");
+        return PNE_ENOMEM;
+    }
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->groups.ptr, groups.data(), groups.size() * sizeof(BatchGroup), cudaMemcpyHostToDevice, s));
     if (!items.empty()) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->items.ptr, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s));
     if (!descs.empty()) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->descs.ptr, descs.data(), descs.size() * sizeof(SumDesc), cudaMemcpyHostToDevice, s));
@@ -1921,7 +1930,7 @@ pne_status launch_fused(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStrea
 {
     auto kern = fused_batch_kernel<T, L, R>;
     const size_t smem = bp->smem_per_warp * wpb;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    grant_dynamic_smem((const void *)kern, smem);
     char *cb = (char *)bp->counters.ptr;
     unsigned long long *next = (unsigned long long *)cb;
     unsigned int *done = (unsigned int *)(cb + 8);
@@ -1948,13 +1957,13 @@ int batch_max_blocks_per_sm(BatchPlan *bp, int wpb)
     if (smem > 200 * 1024) return 0;
     cudaError_t e;
     if (bp->dtype == PNE_F64) {
-        cudaFuncSetAttribute(fused_batch_kernel<double, Load<double>, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        grant_dynamic_smem((const void *)fused_batch_kernel<double, Load<double>, 0>, 200 * 1024);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_batch_kernel<double, Load<double>, 0>, wpb * 32, smem);
     } else if (bp->dtype == PNE_BF16) {
-        cudaFuncSetAttribute(fused_batch_kernel<float, LoadBF16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        grant_dynamic_smem((const void *)fused_batch_kernel<float, LoadBF16, 2>, 200 * 1024);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_batch_kernel<float, LoadBF16, 2>, wpb * 32, smem);
     } else {
-        cudaFuncSetAttribute(fused_batch_kernel<float, Load<float>, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        grant_dynamic_smem((const void *)fused_batch_kernel<float, Load<float>, 0>, 200 * 1024);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_batch_kernel<float, Load<float>, 0>, wpb * 32, smem);
     }
     return e == cudaSuccess ? n : 0;
@@ -2006,16 +2015,22 @@ pne_status batch_enqueue(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStre
     }
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->h_out, bp->d_out.ptr, std::max<int64_t>(bp->out_doubles, 1) * 8,
                                       cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->h_out + std::max<int64_t>(bp->out_doubles, 1),
+                                      (char *)bp->counters.ptr + status_offset(bp->G), 8, cudaMemcpyDeviceToHost, s));
     return PNE_OK;
 }
 
-void batch_plan_destroy(pne_ctx *ctx, BatchPlan *bp)
+void batch_plan_destroy(pne_ctx *ctx, BatchPlan *bp, cudaStream_t s)
 {
     if (!bp) return;
     DevBuf *bufs[] = {&bp->groups, &bp->items, &bp->descs, &bp->partials, &bp->fin_start, &bp->counters, &bp->d_out,
                       &bp->xscratch};
-    for (DevBuf *b : bufs) dev_free(ctx, *b, nullptr);
-    if (bp->h_out) cudaFreeHost(bp->h_out);
+    for (DevBuf *b : bufs) dev_free(ctx, *b, s);
+    if (bp->h_out) {
+        // the last copy into the pinned result buffer may still be queued
+        cudaStreamSynchronize(s);
+        give_pinned(ctx, bp->h_out, bp->h_out_bytes);
+    }
     delete bp;
 }
 

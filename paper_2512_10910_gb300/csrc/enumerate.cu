@@ -1130,7 +1130,11 @@ pne_status scan_to(pne_ctx *ctx, const T *src, int64_t *dst, int64_t n, int64_t 
         ProfScope ps__(ctx, s, "scan");
         scan_tiles_kernel<T><<<(unsigned)nb, 1024, 0, s>>>(src, dst, n, ts);
     }
-    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    if (cudaGetLastError() != cudaSuccess) {
+        dev_free(ctx, sums, s);
+        set_error(ctx, PNE_ECUDA, "scan_tiles_kernel launch failed");
+        return PNE_ECUDA;
+    }
     if ((st = scan_to<int64_t>(ctx, ts, ts, nb, d_total, s))) { dev_free(ctx, sums, s); return st; }
     {
         ProfScope ps__(ctx, s, "scan");
@@ -1190,7 +1194,7 @@ pne_status scan_counts_queue(pne_ctx *ctx, const int32_t *d_counts, int rows, in
     // exclusive scan; its total lands in tot
     if ((st = scan_i32_to(ctx, d_counts, b, n, tot, s))) return st;
     row_starts_kernel<<<(rows + 1 + 127) / 128, 128, 0, s>>>(b, rows, cols, n, starts, tot);
-    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    PNE_LAUNCH_CHECK(ctx);
     const size_t words = (size_t)(rows + 1) + extra_bytes / 8;
     int64_t *h = pinned_i64(ctx, words);
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h, starts, (rows + 1) * 8, cudaMemcpyDeviceToHost, s));
@@ -1288,6 +1292,12 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     };
     struct Readback { int64_t lv[kPrefixMax + 2]; SearchCtl ctl; } hb;
     DevBuf nodes, tables, counts, base;
+    // the arena's buffers are released on every exit, behind the kernels
+    // already queued on `s`
+    struct Release {
+        pne_ctx *ctx; cudaStream_t s; DevBuf *b[4];
+        ~Release() { for (DevBuf *x : b) dev_free(ctx, *x, s); }
+    } release_arena{ctx, s, {&nodes, &tables, &counts, &base}};
     Arena A{};
     std::vector<int64_t> per_size;
     int dfs_level = 0;
@@ -1312,14 +1322,18 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         A.base = nullptr;
         PNE_CUDA_TRY(ctx, cudaMemsetAsync(counts.ptr, 0, (size_t)(K + 1) * cap * 4, s));
         arena_init_kernel<<<1, 32, 0, s>>>(A, Mc);
+        PNE_LAUNCH_CHECK(ctx);
         {
             ProfScope ps__(ctx, s, "enum_roots");
             roots_kernel<<<grid1(Mc, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, mode, A, none, 0);
         }
+        PNE_LAUNCH_CHECK(ctx);
         for (int d = 1; d < D; ++d) {
             ProfScope ps__(ctx, s, "enum_expand");
             launch_expand(kCount, final_kind == 3, G, s, gv, A, d, d, K, mode, none);
+            PNE_LAUNCH_CHECK(ctx);
             expand_children_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, K, mode);
+            PNE_LAUNCH_CHECK(ctx);
         }
         if (final_kind == 1 || final_kind == 3) {
             ProfScope ps__(ctx, s, "enum_expand");
@@ -1327,7 +1341,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         } else if (final_kind == 2) {
             dfs(A, D, 0, none);
         }
-        PNE_CUDA_TRY(ctx, cudaGetLastError());
+        PNE_LAUNCH_CHECK(ctx);
         // one (size, node) table over the arena; the same round trip brings the
         // level bounds and the stop record
         if ((st = scan_counts(ctx, A.counts, K + 1, cap, base, per_size, s, A.lv, sizeof(Readback), &hb))) return st;
@@ -1345,7 +1359,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         // the largest arena holds levels 1..stop: search below level `stop` depth-first
         dfs_level = hb.ctl.stop;
         dfs(A, dfs_level, 0, none);
-        PNE_CUDA_TRY(ctx, cudaGetLastError());
+        PNE_LAUNCH_CHECK(ctx);
         dev_free(ctx, base, s);
         if ((st = scan_counts(ctx, A.counts, K + 1, cap, base, per_size, s))) return st;
         break;
@@ -1375,16 +1389,14 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
         ProfScope ps__(ctx, s, "enum_roots");
         roots_kernel<<<grid1(Mc, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, mode, A, out, 1);
     }
+    PNE_LAUNCH_CHECK(ctx);
     if (last_bfs >= 1) {
         ProfScope ps__(ctx, s, "enum_expand");
         launch_expand(kEmit, final_kind == 3 && dfs_level == 0, G, s, gv, A, 1, last_bfs, K, mode, out);
     }
+    PNE_LAUNCH_CHECK(ctx);
     if (dfs_level) dfs(A, dfs_level, 1, out);
-    PNE_CUDA_TRY(ctx, cudaGetLastError());
-    dev_free(ctx, nodes, s);
-    dev_free(ctx, tables, s);
-    dev_free(ctx, counts, s);
-    dev_free(ctx, base, s);
+    PNE_LAUNCH_CHECK(ctx);
     return PNE_OK;
 }
 
@@ -1422,6 +1434,7 @@ pne_status tuple_round_count(pne_ctx *ctx, EnumRecord &rec, TuplePrep &tp, cudaS
             ProfScope ps__(ctx, s, "enum_terms");
             tuple_chunks_kernel<<<grid1(tp.n_in, 256, ctx->n_sm), 256, 0, s>>>(p, (int64_t *)tp.uoff.ptr);
         }
+        PNE_LAUNCH_CHECK(ctx);
         if ((st = device_exclusive_scan(ctx, (int64_t *)tp.uoff.ptr, tp.n_in, &n_units, s))) return st;
     }
     tp.n_units = n_units;
@@ -1527,6 +1540,7 @@ pne_status tuples_begin(pne_ctx *ctx, EnumRecord &rec, TuplePrep &tp, cudaStream
                                                                           (int32_t *)tp.in_ord.ptr,
                                                                           (const int32_t *)rec.cl_size.ptr, tp.n_in);
         }
+        PNE_LAUNCH_CHECK(ctx);
         if (2 * tp.s_min <= K) {
             if ((st = tuple_round_count(ctx, rec, tp, s))) return st;
             tp.active = true;
@@ -1548,6 +1562,14 @@ pne_status tuples_finish(pne_ctx *ctx, EnumRecord &rec, TuplePrep &tp, cudaStrea
     dev_free(ctx, tp.in_ord, s);
     dev_free(ctx, tp.d_size_end, s);
     return PNE_OK;
+}
+
+void tuples_abort(pne_ctx *ctx, TuplePrep &tp, cudaStream_t s)
+{
+    DevBuf *bufs[] = {&tp.d_size_end, &tp.in_ord, &tp.uoff, &tp.counts, &tp.base};
+    for (DevBuf *b : bufs) dev_free(ctx, *b, s);
+    if (tp.in_owned) dev_free(ctx, tp.in_idx, s);
+    tp.active = false;
 }
 
 pne_status enumerate_tuples(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s)

@@ -126,6 +126,36 @@ void *pinned_slot(int slot, size_t bytes)
     return buf[slot];
 }
 
+void *take_pinned(pne_ctx *ctx, size_t bytes, size_t *got)
+{
+    {
+        std::lock_guard<std::mutex> lk(ctx->pinned_mu);
+        size_t best = ctx->pinned_pool.size();
+        for (size_t i = 0; i < ctx->pinned_pool.size(); ++i)
+            if (ctx->pinned_pool[i].second >= bytes &&
+                (best == ctx->pinned_pool.size() || ctx->pinned_pool[i].second < ctx->pinned_pool[best].second))
+                best = i;
+        if (best < ctx->pinned_pool.size()) {
+            void *p = ctx->pinned_pool[best].first;
+            *got = ctx->pinned_pool[best].second;
+            ctx->pinned_pool.erase(ctx->pinned_pool.begin() + best);
+            return p;
+        }
+    }
+    const size_t cap = std::max<size_t>(bytes, 64 * 1024);
+    void *p = nullptr;
+    if (cudaMallocHost(&p, cap) != cudaSuccess) return nullptr;
+    *got = cap;
+    return p;
+}
+
+void give_pinned(pne_ctx *ctx, void *p, size_t bytes)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(ctx->pinned_mu);
+    ctx->pinned_pool.push_back({p, bytes});
+}
+
 void dev_free(pne_ctx *ctx, DevBuf &b, cudaStream_t s)
 {
     if (!b.ptr) return;
@@ -133,6 +163,72 @@ void dev_free(pne_ctx *ctx, DevBuf &b, cudaStream_t s)
     else cudaFreeAsync(b.ptr, s);
     b.ptr = nullptr;
     b.bytes = 0;
+}
+
+cudaError_t grant_dynamic_smem(const void *func, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::map<const void *, size_t> granted;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &g = granted[func];
+    if (bytes <= g) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) g = bytes;
+    return e;
+}
+
+cudaEvent_t take_event(pne_ctx *ctx)
+{
+    {
+        std::lock_guard<std::mutex> lk(ctx->event_mu);
+        if (!ctx->event_pool.empty()) {
+            cudaEvent_t ev = ctx->event_pool.back();
+            ctx->event_pool.pop_back();
+            return ev;
+        }
+    }
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    return ev;
+}
+
+void give_event(pne_ctx *ctx, cudaEvent_t ev)
+{
+    if (!ev) return;
+    std::lock_guard<std::mutex> lk(ctx->event_mu);
+    ctx->event_pool.push_back(ev);
+}
+
+void UseFence::note(pne_ctx *ctx, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &u : uses)
+        if (u.first == s) { cudaEventRecord(u.second, s); return; }
+    cudaEvent_t ev = take_event(ctx);
+    if (!ev) {
+        // no event: wait here for the stream's queued work instead
+        cudaStreamSynchronize(s);
+        return;
+    }
+    cudaEventRecord(ev, s);
+    uses.push_back({s, ev});
+}
+
+bool UseFence::join(cudaStream_t target)
+{
+    std::lock_guard<std::mutex> lk(mu);
+    bool ok = true;
+    for (auto &u : uses)
+        if (cudaStreamWaitEvent(target, u.second, 0) != cudaSuccess) ok = false;
+    return ok;
+}
+
+void UseFence::release(pne_ctx *ctx)
+{
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &u : uses) give_event(ctx, u.second);
+    uses.clear();
 }
 
 ProfScope::ProfScope(pne_ctx *c, cudaStream_t st, const char *n) : ctx(c), s(st), name(n)
@@ -182,18 +278,24 @@ void HostScope::stop()
 EnumRecord::~EnumRecord()
 {
     if (!ctx) return;
-    dev_free(ctx, cl_edges, nullptr);
-    dev_free(ctx, cl_verts, nullptr);
-    dev_free(ctx, cl_size, nullptr);
-    for (auto &L : levels) dev_free(ctx, L.idx, nullptr);
-    dev_free(ctx, shape_of, nullptr);
-    dev_free(ctx, perm, nullptr);
-    dev_free(ctx, plans, nullptr);
-    dev_free(ctx, plan_steps, nullptr);
-    dev_free(ctx, ops, nullptr);
-    dev_free(ctx, op_off, nullptr);
-    dev_free(ctx, step_off, nullptr);
-    dev_free(ctx, step_site, nullptr);
+    // released after every stream that used the record (the search and shape
+    // streams, the contractions and sums of every terms handle) reaches the
+    // point where it stopped using it
+    cudaStream_t rs = ctx->release_stream;
+    if (!uses.join(rs)) { cudaDeviceSynchronize(); rs = nullptr; }
+    uses.release(ctx);
+    dev_free(ctx, cl_edges, rs);
+    dev_free(ctx, cl_verts, rs);
+    dev_free(ctx, cl_size, rs);
+    for (auto &L : levels) dev_free(ctx, L.idx, rs);
+    dev_free(ctx, shape_of, rs);
+    dev_free(ctx, perm, rs);
+    dev_free(ctx, plans, rs);
+    dev_free(ctx, plan_steps, rs);
+    dev_free(ctx, ops, rs);
+    dev_free(ctx, op_off, rs);
+    dev_free(ctx, step_off, rs);
+    dev_free(ctx, step_site, rs);
 }
 
 namespace {
@@ -411,7 +513,16 @@ void finalize_result(pne_result &r, int K, int mode, int dtype, const double *c,
     } else {
         r.log_series = std::numeric_limits<double>::quiet_NaN();
     }
-    r.err_bound = (sum != 0.0) ? gamma_n(nops, u) * asum / std::fabs(sum) : std::numeric_limits<double>::infinity();
+    // Only cluster values carry the working dtype's rounding: the empty term
+    // (exactly 1 in FP64 when no site has z_v == 0) does not, so it is left
+    // out of the absolute sum the dtype's bound multiplies.  The FP64 products
+    // and sums add at most (K + 2 + log2 of the term count) roundings of 2^-53
+    // on every term.
+    const double exact = (nzero == 0) ? 1.0 : 0.0;
+    const double cl_abs = std::max(0.0, asum - exact);
+    const int n64 = K + 2 + (int)std::ceil(std::log2((double)std::max<uint64_t>(n_terms, 2)));
+    r.err_bound = (sum != 0.0) ? (gamma_n(nops, u) * cl_abs + gamma_n(n64, 0x1p-53) * asum) / std::fabs(sum)
+                               : std::numeric_limits<double>::infinity();
     r.n_terms = n_terms;
     r.n_clusters = n_clusters;
     r.bp_iters = bp_iters;
@@ -452,6 +563,8 @@ constexpr size_t kGeomCacheMax = 256;   // geometries kept per context
 // The full and closed geometry of a (validated) network: from the context's
 // cache when the same arrays were seen before, else built, uploaded on `s`
 // and cached.
+pne_status build_geometry(pne_ctx *ctx, const pne_network *net, GeomPair &gpr, cudaStream_t s);
+
 pne_status get_geometry(pne_ctx *ctx, const pne_network *net, cudaStream_t s, std::shared_ptr<GeomPair> &out)
 {
     HostScope hs__(ctx, "geometry");
@@ -471,7 +584,27 @@ pne_status get_geometry(pne_ctx *ctx, const pne_network *net, cudaStream_t s, st
     auto gp = std::make_shared<GeomPair>();
     gp->ctx = ctx;
     gp->key = key;
-    gp->free_stream = s;
+    pne_status st = build_geometry(ctx, net, *gp, s);
+    // the uploads (and, on failure, whatever was queued) are on `s`: the
+    // geometry's memory is released only after them
+    gp->uses.note(ctx, s);
+    if (st) return st;
+    PNE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&gp->ready, cudaEventDisableTiming));
+    PNE_CUDA_TRY(ctx, cudaEventRecord(gp->ready, s));
+    {
+        std::lock_guard<std::mutex> lk(ctx->cache_mu);
+        size_t n = 0;
+        for (auto &kv : ctx->geom_cache) n += kv.second.size();
+        if (n < kGeomCacheMax) ctx->geom_cache[key].push_back(gp);
+    }
+    out = gp;
+    return PNE_OK;
+}
+
+// Host tables and device copies (queued on `s`) of a validated network.
+pne_status build_geometry(pne_ctx *ctx, const pne_network *net, GeomPair &gpr, cudaStream_t s)
+{
+    GeomPair *gp = &gpr;
     const int N = net->n_sites, M = net->n_bonds;
     Geometry &f = gp->full;
     f.n_sites = N; f.n_bonds = M;
@@ -516,15 +649,6 @@ pne_status get_geometry(pne_ctx *ctx, const pne_network *net, cudaStream_t s, st
             (st = upload(ctx, gp->gauge_tab.ptr, h.data(), h.size() * 4, s)))
             return st;
     }
-    PNE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&gp->ready, cudaEventDisableTiming));
-    PNE_CUDA_TRY(ctx, cudaEventRecord(gp->ready, s));
-    {
-        std::lock_guard<std::mutex> lk(ctx->cache_mu);
-        size_t n = 0;
-        for (auto &kv : ctx->geom_cache) n += kv.second.size();
-        if (n < kGeomCacheMax) ctx->geom_cache[key].push_back(gp);
-    }
-    out = gp;
     return PNE_OK;
 }
 
@@ -532,9 +656,13 @@ GeomPair::~GeomPair()
 {
     if (ready) cudaEventDestroy(ready);
     if (!ctx) return;
-    dev_free(ctx, full.storage, free_stream);
-    dev_free(ctx, closed.storage, free_stream);
-    dev_free(ctx, gauge_tab, free_stream);
+    // after every partition that used it (their streams may be gone by now)
+    cudaStream_t rs = ctx->release_stream;
+    if (!uses.join(rs)) { cudaDeviceSynchronize(); rs = nullptr; }
+    uses.release(ctx);
+    dev_free(ctx, full.storage, rs);
+    dev_free(ctx, closed.storage, rs);
+    dev_free(ctx, gauge_tab, rs);
 }
 
 pne_status partition_record(pne_ctx *ctx, pne_partition *p, const char *rec)
@@ -623,6 +751,8 @@ pne_status pne_ctx_create(int device, pne_ctx **out)
     if (e != cudaSuccess) { g_last_error = cudaGetErrorString(e); return PNE_ECUDA; }
     pne_ctx *c = new pne_ctx();
     c->device = device;
+    e = cudaStreamCreateWithFlags(&c->release_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { g_last_error = cudaGetErrorString(e); delete c; return PNE_ECUDA; }
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
     // PNE_SEARCH_ARENA_MAX (nodes) lowers the node-arena limit of the cluster
     // search, so that the depth-first completion below the deepest level that
@@ -642,15 +772,16 @@ void pne_ctx_destroy(pne_ctx *ctx)
 {
     if (!ctx) return;
     {
+        // cached records and geometries are released on the release stream
+        // after the streams that used them (which may be gone by now)
         std::lock_guard<std::mutex> lk(ctx->cache_mu);
         ctx->enum_cache.clear();
-        // the streams that last used a cached geometry may be gone by now
-        // (the server's prep streams): free on the default stream
-        for (auto &kv : ctx->geom_cache)
-            for (auto &g : kv.second) g->free_stream = nullptr;
         ctx->geom_cache.clear();
     }
     cudaDeviceSynchronize();
+    if (ctx->release_stream) cudaStreamDestroy(ctx->release_stream);
+    for (auto ev : ctx->event_pool) cudaEventDestroy(ev);
+    for (auto &pb : ctx->pinned_pool) cudaFreeHost(pb.first);
     if (ctx->side_ready) {
         for (auto st : ctx->side) cudaStreamDestroy(st);
         for (auto ev : ctx->side_ev) cudaEventDestroy(ev);
@@ -786,12 +917,17 @@ void pne_partition_destroy(pne_partition *p)
 {
     if (!p) return;
     pne_ctx *ctx = p->ctx;
-    cudaStream_t s = p->last_stream;
+    // released after the partition's own stream and the streams of the terms
+    // handles that read it (destroyed before it) reach their last use
+    cudaStream_t s = ctx->release_stream;
+    p->uses.note(ctx, p->last_stream);
+    if (!p->uses.join(s)) { cudaDeviceSynchronize(); s = nullptr; }
+    p->uses.release(ctx);
     // the partition's buffers are views of one allocation; the converted
     // copies are allocated on demand
     DevBuf *bufs[] = {&p->storage, &p->Mb32, &p->Mb16, &p->rec_own};
     for (DevBuf *b : bufs) dev_free(ctx, *b, s);
-    if (p->geo) p->geo->free_stream = s;          // a geometry left without users is freed on this stream
+    if (p->geo) p->geo->uses.note(ctx, s);        // the geometry outlives every use of the partition
     delete p;
 }
 
@@ -820,6 +956,13 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
     if (!rec) {
         rec = std::make_shared<EnumRecord>();
         rec->ctx = ctx;
+        // every exit, failures included, leaves the record's memory fenced
+        // behind the work this call queued for it (on `s` and on the shape
+        // stage's stream), so that it is never released under a running kernel
+        struct Fence {
+            pne_ctx *ctx; EnumRecord *r; cudaStream_t s; cudaStream_t sb = nullptr;
+            ~Fence() { r->uses.note(ctx, s); if (sb && sb != s) r->uses.note(ctx, sb); }
+        } fence{ctx, rec.get(), s};
         if (mode == PNE_MODE_ALL) {
             if (g.n_bonds > kMaxAllBonds || g.n_sites > 64) {
                 set_error(ctx, PNE_EINVAL, "ALL mode needs <= 30 closed bonds and <= 64 sites"); return PNE_EINVAL;
@@ -861,7 +1004,11 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
                     }
                 }
                 auto fail = [&](pne_status e) {
+                    // buffers of the unfinished stages are released behind the
+                    // kernels already queued on their streams
                     shapes_release(ctx, sp, sb);
+                    tuples_abort(ctx, tp, s);
+                    fence.sb = sb;
                     if (ls.s) { std::lock_guard<std::mutex> lk(ctx->pool_mu); ctx->stream_pool.push_back(ls); }
                     return e;
                 };
@@ -877,6 +1024,7 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
                         PNE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ls.join, cudaEventDisableTiming));
                     }
                     sb = ls.s;
+                    fence.sb = sb;
                     if (cudaEventRecord(ls.fork, s) != cudaSuccess || cudaStreamWaitEvent(sb, ls.fork, 0) != cudaSuccess)
                         return fail(PNE_ECUDA);
                 }
@@ -918,6 +1066,7 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
     }
     pne_terms *t = new pne_terms();
     t->ctx = ctx; t->part = part; t->rec = rec; t->K = K; t->mode = mode;
+    t->last_stream = s;
     const size_t Bm = part->n_members;
     const size_t ncl = std::max<uint64_t>(rec->n_clusters, 1);
     if ((st = dev_alloc(ctx, t->status, 16, s))) { delete t; return st; }
@@ -943,7 +1092,10 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
 void pne_terms_destroy(pne_terms *t)
 {
     if (!t) return;
-    cudaStream_t s = t->part ? t->part->last_stream : nullptr;
+    cudaStream_t s = t->last_stream;
+    if (t->rec) t->rec->uses.note(t->ctx, s);    // the record outlives this stream's queued work
+    // so does the partition (terms handles are destroyed before it)
+    if (t->part) const_cast<pne_partition *>(t->part)->uses.note(t->ctx, s);
     dev_free(t->ctx, t->w, s);
     dev_free(t->ctx, t->nzc, s);
     dev_free(t->ctx, t->sums, s);
@@ -957,6 +1109,7 @@ pne_status pne_contract_terms(pne_ctx *ctx, pne_terms *t, pne_dtype dtype, void 
     if (!ctx || !t) return PNE_EINVAL;
     if (dtype < PNE_F64 || dtype > PNE_BF16) { set_error(ctx, PNE_EINVAL, "unknown dtype"); return PNE_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
+    t->last_stream = s;
     pne_status st = (t->mode == PNE_MODE_ALL) ? launch_all_mode(ctx, t, dtype, s) : launch_contract(ctx, t, dtype, s);
     if (st) return st;
     t->dtype = dtype;
@@ -974,6 +1127,7 @@ pne_status pne_terms_export(pne_ctx *ctx, const pne_terms *t, void *stream, int3
     if (!ctx || !t) return PNE_EINVAL;
     if (t->mode != PNE_MODE_LOOP) { set_error(ctx, PNE_EINVAL, "export needs LOOP mode"); return PNE_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
+    const_cast<pne_terms *>(t)->last_stream = s;
     const EnumRecord &rec = *t->rec;
     const size_t n = rec.n_clusters;
     if (n == 0) return PNE_OK;
@@ -1004,6 +1158,7 @@ pne_status pne_sum(pne_ctx *ctx, const pne_terms *t, void *stream, pne_result *o
     if (!ctx || !t || !out) return PNE_EINVAL;
     if (!t->contracted) { set_error(ctx, PNE_EINVAL, "pne_contract_terms must run before pne_sum"); return PNE_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
+    const_cast<pne_terms *>(t)->last_stream = s;
     const pne_partition *p = t->part;
     const int K = t->K, B = p->n_members;
     std::vector<double> c, a;
@@ -1231,6 +1386,7 @@ struct pne_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t n_results = 0;
+    cudaStream_t last = nullptr;          // stream of the last call that queued work for the batch
 };
 
 namespace {
@@ -1279,9 +1435,11 @@ pne_status pne_batch_create(pne_ctx *ctx, int32_t n, pne_terms *const *terms, pn
     pne_batch *b = new pne_batch();
     b->ctx = ctx;
     b->dtype = dtype;
+    b->last = s;
     b->terms.assign(terms, terms + n);
     for (pne_terms *t : b->terms) {
         if (!t) { delete b; return PNE_EINVAL; }
+        t->last_stream = s;                       // conversions and tuning runs use the handles on `s`
         b->n_results += t->part->n_members;
         // the batch reports the BP record: read deferred ones now
         partition_settle(ctx, const_cast<pne_partition *>(t->part));
@@ -1362,6 +1520,8 @@ pne_status pne_batch_run(pne_ctx *ctx, pne_batch *b, void *stream, pne_result *o
 {
     if (!ctx || !b || !out) return PNE_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
+    b->last = s;
+    for (pne_terms *t : b->terms) t->last_stream = s;     // the handles' buffers are used on `s`
     if (b->use_graph) {
         ProfScope ps(ctx, s, "batch_graph");
         PNE_CUDA_TRY(ctx, cudaGraphLaunch(b->exec, s));
@@ -1411,7 +1571,7 @@ void pne_batch_destroy(pne_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
-    if (b->plan) batch_plan_destroy(b->ctx, b->plan);
+    if (b->plan) batch_plan_destroy(b->ctx, b->plan, b->last);
     delete b;
 }
 

@@ -54,6 +54,17 @@ void set_error(pne_ctx *ctx, pne_status st, const std::string &msg);
         }                                                                         \
     } while (0)
 
+// After a launch whose output later launches read: a launch that was refused
+// (configuration, resources) queues nothing, so the launches behind it would
+// read memory nobody wrote.  Checked at once, before anything depends on it.
+#define PNE_LAUNCH_CHECK(ctx) PNE_CUDA_TRY(ctx, cudaGetLastError())
+
+// Dynamic shared memory above 48 KB for a kernel.  The limit is an attribute
+// of the function, shared by every context and thread of the process, so it is
+// only ever raised (under one process-wide lock): a smaller request never
+// lowers it under a launch of another thread that needs more.
+cudaError_t grant_dynamic_smem(const void *func, size_t bytes);
+
 // ------------------------------------------------------------------ memory
 // Device buffer owned through the context's allocator.
 struct DevBuf {
@@ -77,7 +88,31 @@ pne_status upload(pne_ctx *ctx, void *dst, const void *src, size_t bytes, cudaSt
 constexpr int kPinnedSlots = 4;
 constexpr size_t kTraceMax = 1 << 18;   // timeline records kept per trace (later ones are dropped)
 void *pinned_slot(int slot, size_t bytes);
+// Pinned host buffers owned by one object at a time (batch results), from a
+// per-context pool: *got receives the buffer's size; nullptr if none can be had.
+void *take_pinned(pne_ctx *ctx, size_t bytes, size_t *got);
+void give_pinned(pne_ctx *ctx, void *p, size_t bytes);
 void dev_free(pne_ctx *ctx, DevBuf &b, cudaStream_t s);
+
+// ------------------------------------------------------------------ shared objects
+// The streams on which a device object shared by several handles (a geometry,
+// an enumeration record) was used: each user, when it is destroyed, records an
+// event on the stream it last used.  The object's memory is released on the
+// context's release stream after it has waited for every such event, so it is
+// never handed to a new allocation while a kernel queued by any user can still
+// read it, whichever thread or stream drops the last reference.
+// Events come from (and return to) the owning context's pool.
+struct UseFence {
+    std::mutex mu;
+    std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;
+    void note(pne_ctx *ctx, cudaStream_t s);
+    // makes `target` wait for every noted use; false when a CUDA call failed
+    bool join(cudaStream_t target);
+    // returns the events to the context's pool (the object's destructor)
+    void release(pne_ctx *ctx);
+};
+cudaEvent_t take_event(pne_ctx *ctx);
+void give_event(pne_ctx *ctx, cudaEvent_t ev);
 
 // ------------------------------------------------------------------ geometry
 // Host + device copy of one network geometry (closed or with open bonds).
@@ -150,11 +185,15 @@ struct pne_ctx {
     // device schedules (0: none) and the blocks per SM of the grid form
     std::map<std::pair<size_t, int>, int> bp_cluster;
     std::map<size_t, int> bp_grid_occ;
-    size_t bp_smem_set[6] = {0, 0, 0, 0, 0, 0};   // largest dynamic shared memory granted per BP/gauge kernel
     std::mutex launch_mu;
     std::mutex cache_mu;
-    // scratch for small device-side status words
-    int32_t *d_status = nullptr;
+    // stream on which shared objects (geometries, enumeration records, batch
+    // plans) are released, after waiting for every stream that used them
+    cudaStream_t release_stream = nullptr;
+    std::vector<cudaEvent_t> event_pool;          // timing-free events for use fences
+    std::mutex event_mu;
+    std::vector<std::pair<void *, size_t>> pinned_pool;   // free pinned host buffers (take_pinned)
+    std::mutex pinned_mu;
     // side streams for independent launches of one call (fork/join through
     // events, serialised per context by side_mu)
     static constexpr int kSideStreams = 6;
@@ -181,7 +220,7 @@ struct GeomPair {
     std::vector<int32_t> open_bonds;     // full ids of open bonds, ascending
     std::vector<int32_t> open_dims;
     uint64_t key = 0;                    // hash of the input arrays
-    cudaStream_t free_stream = nullptr;  // stream of the last partition that used it
+    UseFence uses;                       // streams of the partitions that used it
     cudaEvent_t ready = nullptr;         // recorded after the device copies were queued
     // gauge-transform table (open position per full bond, then the open dims)
     // and the largest site tensor, fixed by the geometry
@@ -217,6 +256,7 @@ struct pne_partition {
     pne::DevBuf rec_dev;             // deferred convergence record (a view of storage or of rec_own)
     pne::DevBuf rec_own;             // its own buffer when an update defers a record the build did not
     bool rec_pending = false;
+    pne::UseFence uses;              // streams of the terms handles that read it
 };
 
 namespace pne {
@@ -259,6 +299,7 @@ struct EnumRecord {
     // class q holds perm[class_start[q], class_start[q+1]) and needs class_xmax[q]
     std::vector<int64_t> class_start;
     std::vector<int> class_xmax;
+    UseFence uses;                              // streams of the terms handles that used it
     ~EnumRecord();
 };
 
@@ -275,6 +316,7 @@ struct pne_terms {
     pne::DevBuf sums;                    // ALL mode / reduction partials
     pne::DevBuf status;                  // int32 error flags
     bool contracted = false;
+    cudaStream_t last_stream = nullptr;  // stream of the last call that used the handle
 };
 
 namespace pne {
@@ -337,6 +379,8 @@ struct TuplePrep {
 };
 pne_status tuples_begin(pne_ctx *ctx, EnumRecord &rec, TuplePrep &tp, cudaStream_t s);
 pne_status tuples_finish(pne_ctx *ctx, EnumRecord &rec, TuplePrep &tp, cudaStream_t s);
+// Releases the buffers of an unfinished TuplePrep (stream-ordered on `s`).
+void tuples_abort(pne_ctx *ctx, TuplePrep &tp, cudaStream_t s);
 
 // contraction and sums (contract.cu)
 pne_status launch_contract(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s);
@@ -377,7 +421,8 @@ pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms
 pne_status batch_prepare(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStream_t s);
 pne_status batch_enqueue(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStream_t s);
 int batch_max_blocks_per_sm(BatchPlan *bp, int wpb);
-void batch_plan_destroy(pne_ctx *ctx, BatchPlan *bp);
+// releases the plan's buffers behind the work queued on `s` (its last stream)
+void batch_plan_destroy(pne_ctx *ctx, BatchPlan *bp, cudaStream_t s);
 double *batch_host_out(BatchPlan *bp);
 const std::vector<int64_t> &batch_out_offsets(BatchPlan *bp);
 int32_t batch_status_host(BatchPlan *bp);

@@ -1,5 +1,11 @@
 // Served form: continuous batching of expansion requests (host runtime).
 //
+// One context is shared by every server thread: the context's caches, pools
+// and launch decisions are guarded, each request's handles are used by one
+// thread at a time (its prep thread, then the launcher), and device memory
+// shared between requests (cached geometries and enumerations) is released
+// only after every stream that used it.
+//
 // Requests arrive as single networks of any size, bond dimension and order.
 // They are admitted in arrival order while the estimated device bytes and the
 // number of admitted, unfinished requests stay within the server's budget.
@@ -210,6 +216,10 @@ void launch_loop(pne_server *s)
         std::vector<pne_result> res(batch.size());
         if (rc == PNE_OK) rc = pne_batch_run(s->ctx, b, s->launch_stream, res.data());
         if (b) pne_batch_destroy(b);
+        // a failed create or run may leave work queued for these requests:
+        // let it finish before their buffers go (their release is fenced
+        // behind the launch stream anyway; this keeps a failure contained)
+        if (rc != PNE_OK) cudaStreamSynchronize(s->launch_stream);
         for (Request *r : batch) release(r);
         std::unique_lock<std::mutex> lk(s->mu);
         for (size_t i = 0; i < batch.size(); ++i) {

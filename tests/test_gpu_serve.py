@@ -1,6 +1,15 @@
-"""Served form: continuous batching with memory admission.  Each request's
-result is the same alone and inside a mix of concurrent requests, and equals
-the single-request path."""
+"""Served form: continuous batching with memory admission.
+
+Each served result is checked against the FP64 CPU oracle (counts exact;
+FP64 contractions within 1e-10 relative on Z_K and per order within 1e-10 of
+sum_k |c_k|; FP32 / TF32 / BF16 contractions within the library's stated
+a-priori bound err_bound, whose own size is capped per dtype), is the same
+alone and inside a mix of concurrent requests (bit for bit), and equals the
+single-request path through the four calls.  A burst of requests that share
+geometries at several orders -- enumerated cold, concurrently, on several
+prep streams -- is served and checked against the oracle too.
+"""
+import math
 import time
 
 import numpy as np
@@ -12,6 +21,11 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2512_10910_gb300 import pne  # noqa: E402
+from oracle import enumerate as E  # noqa: E402
+from oracle import expansion as X  # noqa: E402
+
+# largest stated bound accepted per dtype (the bound itself must be small)
+BOUND_CAP = {pne.PNE_F32: 1e-5, pne.PNE_TF32: 2e-2, pne.PNE_BF16: 1e-1}
 
 
 @pytest.fixture(scope="module")
@@ -25,13 +39,42 @@ def ctx():
     c.close()
 
 
-def _requests():
-    reqs = []
-    for L, K in ((6, 6), (8, 8), (5, 4), (9, 8)):
-        reqs.append((I.aklt_tensors(I.square_lattice(L, L, 4)), K))
-    for L, D, K, sd in ((3, 2, 8, 1), (4, 3, 6, 2), (3, 4, 8, 3), (5, 2, 4, 4)):
-        reqs.append((I.random_tensors(I.cubic_lattice(L, L, L, D), sd, "n1,0.3"), K))
-    return reqs
+def _networks():
+    nets = []
+    for L in (6, 8, 5, 9):
+        nets.append(I.aklt_tensors(I.square_lattice(L, L, 4)))
+    for L, D, sd in ((3, 2, 1), (4, 3, 2), (3, 4, 3), (5, 2, 4)):
+        nets.append(I.random_tensors(I.cubic_lattice(L, L, L, D), sd, "n1,0.3"))
+    return nets
+
+
+def _requests(nets):
+    return list(zip(nets, (6, 8, 4, 8, 8, 6, 8, 4)))
+
+
+@pytest.fixture(scope="module")
+def oracle():
+    """FP64 oracle result per (network index, K), computed once."""
+    cache = {}
+
+    def get(i, net, K):
+        if (i, K) not in cache:
+            cache[(i, K)] = X.pne(net, K, E.LOOP)
+        return cache[(i, K)]
+    return get
+
+
+def _check_vs_oracle(res, ref, dtype):
+    assert res["n_clusters"] == ref.n_clusters and res["n_terms"] == ref.n_terms
+    assert res["sign"] == ref.sign
+    rel = abs(math.expm1(res["log_abs"] - ref.log_abs))
+    if dtype == pne.PNE_F64:
+        assert rel <= 1e-10, rel
+        scale = float(np.sum(np.abs(ref.c)))
+        np.testing.assert_allclose(res["c"], ref.c, rtol=0, atol=1e-10 * scale)
+    else:
+        assert res["err_bound"] <= BOUND_CAP[dtype], res["err_bound"]
+        assert rel <= res["err_bound"], (rel, res["err_bound"])
 
 
 def _wait(srv, rid, timeout=120.0):
@@ -39,15 +82,16 @@ def _wait(srv, rid, timeout=120.0):
     while True:
         st, res, info = pne.pne_server_poll(srv, rid)
         if st != pne.PNE_EBUSY:
-            assert st == pne.PNE_OK, st
+            assert st == pne.PNE_OK, (st, pne.pne_server_first_error(srv))
             return res, info
         assert time.time() - t0 < timeout
         time.sleep(0.001)
 
 
-@pytest.mark.parametrize("dtype", [pne.PNE_F64, pne.PNE_F32])
-def test_alone_equals_in_mix_and_single_path(ctx, dtype):
-    reqs = _requests()
+@pytest.mark.parametrize("dtype", [pne.PNE_F64, pne.PNE_F32, pne.PNE_TF32, pne.PNE_BF16])
+def test_served_results_match_oracle_alone_and_in_mix(ctx, oracle, dtype):
+    nets = _networks()
+    reqs = _requests(nets)
     structs = [pne.network_struct(net) for net, _ in reqs]
     srv = pne.pne_server_create(ctx.h, pne.ServerOpts(0, 0, 3, 0, dtype, 0, 0))
     try:
@@ -65,15 +109,39 @@ def test_alone_equals_in_mix_and_single_path(ctx, dtype):
             assert info["t_arrival"] <= info["t_admit"] <= info["t_ready"] <= info["t_done"]
     finally:
         pne.pne_server_destroy(srv)
-    for (net, K), a in zip(reqs, alone):
+    for i, ((net, K), a) in enumerate(zip(reqs, alone)):
+        _check_vs_oracle(a, oracle(i, net, K), dtype)
         (single,) = ctx.expand(net, K, pne.PNE_MODE_LOOP, dtype, arithmetic=1)   # the server's BP arithmetic
         tol = 1e-12 if dtype == pne.PNE_F64 else 1e-6
         assert abs(single["log_abs"] - a["log_abs"]) <= tol
         assert single["n_terms"] == a["n_terms"]
 
 
+def test_cold_burst_of_shared_geometries_matches_oracle(ctx, oracle):
+    # every network at three orders, submitted at once on a fresh context: the
+    # same geometries are partitioned and enumerated concurrently (cold caches)
+    # on six prep streams while earlier requests run in fused launches
+    nets = _networks()
+    c2 = pne.Context(0)
+    try:
+        srv = pne.pne_server_create(c2.h, pne.ServerOpts(0, 0, 6, 0, pne.PNE_F64, 0, 0))
+        try:
+            jobs = [(i, net, K) for K in (4, 6, 8) for i, net in enumerate(nets)]
+            structs = [pne.network_struct(net) for _, net, _ in jobs]
+            ids = [pne.pne_server_submit(srv, ns, K) for (_, _, K), (ns, _) in zip(jobs, structs)]
+            pne.pne_server_drain(srv)
+            assert pne.pne_server_first_error(srv) == ""
+            for (i, net, K), rid in zip(jobs, ids):
+                res, _ = _wait(srv, rid)
+                _check_vs_oracle(res, oracle(i, net, K), pne.PNE_F64)
+        finally:
+            pne.pne_server_destroy(srv)
+    finally:
+        c2.close()
+
+
 def test_admission_respects_the_budget(ctx):
-    reqs = _requests() * 2
+    reqs = _requests(_networks()) * 2
     structs = [pne.network_struct(net) for net, _ in reqs]
     budget = 4 << 20
     srv = pne.pne_server_create(ctx.h, pne.ServerOpts(budget, 0, 4, 0, pne.PNE_F32, 0, 0))
