@@ -199,13 +199,18 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part,
                                pne_terms **out, uint64_t *n_clusters, uint64_t *n_terms);
 void pne_terms_destroy(pne_terms *t);
 
-/* Contract every cluster of every tensor set in `dtype`: w(C) = Z'_C /
+/* Contract every cluster of every tensor set in `dtype` (Sec. II.C: with P
+ * bonds cut and capped, a term factorises into the capped sites and one
+ * local contraction per connected excited cluster; Sec. III.A: that
+ * contraction is the cluster's only cost): w(C) = Z'_C /
  * prod_{v in C, z_v != 0} z_v with a per-cluster power-of-two exponent carried
  * through the contraction.  Asynchronous. */
 pne_status pne_contract_terms(pne_ctx *ctx, pne_terms *t, pne_dtype dtype, void *stream);
 
-/* Form every term's value (product of its clusters' w) and sum by order in
- * FP64 with a fixed reduction tree; write one pne_result per tensor set and
+/* Form every term's value (product of its clusters' w; a term of the
+ * expansion Eq. A4 is a vertex-disjoint set of clusters) and sum by order in
+ * FP64 with a fixed reduction tree, keeping the orders |E| <= K (the
+ * truncation of Sec. II.B); write one pne_result per tensor set and
  * open-index assignment into out[] (pne_terms_n_results entries, set-major,
  * assignments row-major over the open bonds in ascending id).  Synchronises
  * `stream`. */
@@ -213,6 +218,27 @@ pne_status pne_sum(pne_ctx *ctx, const pne_terms *t, void *stream, pne_result *o
 
 /* Number of pne_result entries pne_sum writes (= n_batch * prod of open dims). */
 int64_t pne_terms_n_results(const pne_terms *t);
+
+/* Open-index output (Sec. III.D: open indices are left unpartitioned, and the
+ * result is the network's tensor over them; Eq. B2 measures its error).  The
+ * entry at one assignment o of the open indices is Z_K of the closed slice
+ * with the open indices fixed to o (the slices share the partition's
+ * projectors and the enumeration).  Runs pne_sum's work on `stream`
+ * (synchronises it) and writes, for every tensor set b,
+ *   tensor[b][o] = out[b * n_open + o] * exp(log_scale[b]),
+ * o row-major over the open bonds in ascending bond id, n_open = the product
+ * of their dimensions (pne_terms_n_results(t) / n_batch), and log_scale[b] =
+ * max_o ln|Z_K(b, o)| so that |out| <= 1 and no entry overflows (log_scale is
+ * -inf and out zero when every slice of the set is zero).
+ *   out        host [n_batch * n_open] doubles, caller-owned
+ *   log_scale  host [n_batch] doubles, caller-owned
+ * A network without open indices gives one entry per set (its Z_K). */
+pne_status pne_open_tensor(pne_ctx *ctx, const pne_terms *t, void *stream, double *out, double *log_scale);
+
+/* The assembly step of pne_open_tensor alone, from results pne_sum wrote
+ * (res[n_sets * n_open], set-major): host arithmetic only, no device. */
+pne_status pne_open_tensor_assemble(const pne_result *res, int64_t n_sets, int64_t n_open, double *out,
+                                    double *log_scale);
 
 /* Copy the cluster list and the contracted cluster values to host memory, for
  * inspection and element-by-element checks.  LOOP mode only.
@@ -323,18 +349,20 @@ void pne_server_destroy(pne_server *s);
 
 /* ---- belief propagation without device allocation ------------------------ */
 
-/* The paper has no counterpart to this call; it exists for callers that cannot
- * allocate device memory while they run -- code inside a CUDA stream capture,
- * a host framework that owns a fixed device arena, or a real-time loop where
- * cudaMalloc's implicit synchronisation is not allowed.  It runs the same BP
- * sweeps as pne_build_partition and returns the fixed-point messages, but
- * calls no cudaMalloc, cudaFree or allocating library routine: its working
+/* The paper has no counterpart to this call.  It is for callers that must not
+ * allocate device memory while they run: a host framework that has reserved
+ * the device's memory for its own allocator and lends the library only fixed
+ * buffers, or a latency-critical loop in which cudaMalloc / cudaFree (and the
+ * device-wide synchronisation they can imply) are not allowed.  It runs the
+ * same BP sweeps as pne_build_partition and returns the fixed-point messages,
+ * but calls no cudaMalloc, cudaFree or allocating library routine: its working
  * memory (geometry tables, the second message buffer, convergence words) is a
  * file-scope device array of PNE_NOALLOC_SCRATCH_BYTES that every GPU which
  * loads the library holds until the process exits.
  *
  *   net        network as for pne_build_partition; net->data must be a device
- *              pointer (data_on_device != 0), n_batch tensor sets.
+ *              pointer (data_on_device != 0), n_batch tensor sets.  The
+ *              geometry arrays are host arrays, copied with cudaMemcpyAsync.
  *   tol, max_iter  as in pne_partition_opts (defaults when <= 0).
  *   msg_out    device buffer [n_batch][site_ptr[n_sites]][8] doubles: for every
  *              leg slot (sites in order, each site's legs in ascending bond
@@ -343,13 +371,14 @@ void pne_server_destroy(pne_server *s);
  *   iters_out, residual_out  host arrays [n_batch] (may be NULL): sweeps taken
  *              (0 = not converged) and the last sweep's largest change.
  * Returns PNE_EINVAL when the tables and buffers need more than
- * PNE_NOALLOC_SCRATCH_BYTES (or on malformed input), PNE_ENOCONV,
- * PNE_EDEGENERATE, PNE_ETIMEOUT or PNE_ECUDA as pne_build_partition does.
- * Synchronises `stream`.  The first call on a device looks up the array's
- * device address (per device, with that device current); make that first
- * call before any stream capture.  All calls share the one array and it keeps
- * the last call's contents: calls that overlap on the GPU (other streams,
- * other host threads) race and corrupt each other. */
+ * PNE_NOALLOC_SCRATCH_BYTES, checked on the host before any GPU work (or on
+ * malformed input), PNE_ENOCONV, PNE_EDEGENERATE, PNE_ETIMEOUT or PNE_ECUDA as
+ * pne_build_partition does.  Synchronises `stream` before it returns.  The
+ * first call on a device looks up the array's device address (per device,
+ * with that device current).  All calls share the one array and it keeps the
+ * last call's contents (each call clears the words that must start at zero):
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * corrupt each other. */
 #define PNE_NOALLOC_SCRATCH_BYTES (8u << 20)
 pne_status pne_bp_messages_noalloc(const pne_network *net, double tol, int32_t max_iter, double *msg_out,
                                    int32_t *iters_out, double *residual_out, void *stream);

@@ -27,6 +27,8 @@
 
 #include <algorithm>
 
+#include <atomic>
+
 #include "pne_internal.h"
 
 namespace pne {
@@ -1626,7 +1628,9 @@ namespace pne {
 namespace {
 
 constexpr int kNoAllocMaxDevices = 64;
-void *g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+// device address of the array, per device (host threads may race to fill an
+// entry; each writes the same address)
+std::atomic<void *> g_noalloc_addr[kNoAllocMaxDevices] = {};
 
 // bond_leg, incoming-message slots and tensor offsets from the raw geometry,
 // one thread (tables are small; the call allocates nothing to go faster)
@@ -1664,6 +1668,13 @@ __global__ void noalloc_copy_kernel(const double *msg, const int32_t *final_buf,
         const int set = (int)(i / per_set);
         out[i] = msg[((int64_t)final_buf[set] * n_sets) * per_set + i];
     }
+}
+
+// flag[0] = 1 when some tensor set did not converge (sweeps recorded as 0)
+__global__ void noalloc_conv_kernel(const int32_t *iters, int n_sets, int32_t *flag)
+{
+    for (int i = threadIdx.x; i < n_sets; i += blockDim.x)
+        if (iters[i] == 0) atomicExch(flag, 1);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1762,12 +1773,12 @@ extern "C" pne_status pne_bp_messages_noalloc(const pne_network *net, double tol
     int dev = 0;
     PNE_CUDA_TRY(nullptr, cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoAllocMaxDevices) { set_error(nullptr, PNE_EINVAL, "device ordinal out of range"); return PNE_EINVAL; }
-    if (!g_noalloc_addr[dev]) {
+    if (!g_noalloc_addr[dev].load()) {
         void *ptr = nullptr;
         PNE_CUDA_TRY(nullptr, cudaGetSymbolAddress(&ptr, g_bp_noalloc_scratch));
-        g_noalloc_addr[dev] = ptr;
+        g_noalloc_addr[dev].store(ptr);
     }
-    char *base = (char *)g_noalloc_addr[dev];
+    char *base = (char *)g_noalloc_addr[dev].load();
     int32_t *bs = (int32_t *)(base + o_bs), *bd = (int32_t *)(base + o_bd), *sp = (int32_t *)(base + o_sp);
     int32_t *sb = (int32_t *)(base + o_sb), *bl = (int32_t *)(base + o_bl), *is = (int32_t *)(base + o_is);
     int64_t *to = (int64_t *)(base + o_to);
@@ -1817,20 +1828,17 @@ extern "C" pne_status pne_bp_messages_noalloc(const pne_network *net, double tol
     const int64_t per_set = (int64_t)L * kMsgStride;
     noalloc_copy_kernel<<<grid_for((int64_t)B * per_set, 256, n_sm), 256, 0, s>>>(msg, finalb, B, per_set, msg_out);
     PNE_CUDA_TRY(nullptr, cudaGetLastError());
-    int32_t hflags[2] = {0, 0};
-    PNE_CUDA_TRY(nullptr, cudaMemcpyAsync(hflags, flags, 8, cudaMemcpyDeviceToHost, s));
+    // the convergence verdict of every set folded into one word on the device,
+    // read back with the barrier and degeneracy flags in one copy on `s`
+    noalloc_conv_kernel<<<1, 256, 0, s>>>(iters, B, flags + 2);
+    PNE_CUDA_TRY(nullptr, cudaGetLastError());
+    int32_t hflags[3] = {0, 0, 0};
+    PNE_CUDA_TRY(nullptr, cudaMemcpyAsync(hflags, flags, 12, cudaMemcpyDeviceToHost, s));
     if (iters_out) PNE_CUDA_TRY(nullptr, cudaMemcpyAsync(iters_out, iters, (size_t)B * 4, cudaMemcpyDeviceToHost, s));
     if (residual_out) PNE_CUDA_TRY(nullptr, cudaMemcpyAsync(residual_out, res_out, (size_t)B * 8, cudaMemcpyDeviceToHost, s));
     PNE_CUDA_TRY(nullptr, cudaStreamSynchronize(s));
     if (hflags[0]) { set_error(nullptr, PNE_ETIMEOUT, "grid barrier timed out in BP"); return PNE_ETIMEOUT; }
     if (hflags[1]) { set_error(nullptr, PNE_EDEGENERATE, "zero BP message"); return PNE_EDEGENERATE; }
-    // convergence record through a fixed host buffer (no allocation)
-    int32_t chunk[256];
-    for (int b0 = 0; b0 < B; b0 += 256) {
-        const int nb = (B - b0 < 256) ? B - b0 : 256;
-        PNE_CUDA_TRY(nullptr, cudaMemcpy(chunk, iters + b0, (size_t)nb * 4, cudaMemcpyDeviceToHost));
-        for (int i = 0; i < nb; ++i)
-            if (chunk[i] == 0) { set_error(nullptr, PNE_ENOCONV, "BP did not converge"); return PNE_ENOCONV; }
-    }
+    if (hflags[2]) { set_error(nullptr, PNE_ENOCONV, "BP did not converge"); return PNE_ENOCONV; }
     return PNE_OK;
 }

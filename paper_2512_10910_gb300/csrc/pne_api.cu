@@ -1122,6 +1122,35 @@ int64_t pne_terms_n_results(const pne_terms *t)
     return t && t->part ? (int64_t)t->part->n_members : 0;
 }
 
+pne_status pne_open_tensor_assemble(const pne_result *res, int64_t n_sets, int64_t n_open, double *out,
+                                    double *log_scale)
+{
+    if (!res || !out || !log_scale || n_sets < 1 || n_open < 1) return PNE_EINVAL;
+    for (int64_t b = 0; b < n_sets; ++b) {
+        const pne_result *r = res + b * n_open;
+        double m = -std::numeric_limits<double>::infinity();
+        for (int64_t o = 0; o < n_open; ++o)
+            if (r[o].sign != 0 && std::isfinite(r[o].log_abs)) m = std::max(m, r[o].log_abs);
+        log_scale[b] = m;
+        for (int64_t o = 0; o < n_open; ++o) {
+            const bool zero = r[o].sign == 0 || !std::isfinite(r[o].log_abs) || !std::isfinite(m);
+            out[b * n_open + o] = zero ? 0.0 : r[o].sign * std::exp(r[o].log_abs - m);
+        }
+    }
+    return PNE_OK;
+}
+
+pne_status pne_open_tensor(pne_ctx *ctx, const pne_terms *t, void *stream, double *out, double *log_scale)
+{
+    if (!ctx || !t || !out || !log_scale) return PNE_EINVAL;
+    const pne_partition *p = t->part;
+    std::vector<pne_result> res((size_t)p->n_members);
+    const pne_status st = pne_sum(ctx, t, stream, res.data());
+    if (st != PNE_OK && st != PNE_ENOCONV) return st;
+    const pne_status sa = pne_open_tensor_assemble(res.data(), p->n_sets, p->n_slices, out, log_scale);
+    return sa != PNE_OK ? sa : st;
+}
+
 pne_status pne_terms_export(pne_ctx *ctx, const pne_terms *t, void *stream, int32_t *edges, double *w)
 {
     if (!ctx || !t) return PNE_EINVAL;

@@ -11,7 +11,6 @@ and ``run`` wrap one full pass for convenience.
 from __future__ import annotations
 
 import ctypes
-import math
 import collections.abc
 import os
 
@@ -153,6 +152,11 @@ def load_library():
     lib.pne_sum.restype = ctypes.c_int
     lib.pne_terms_n_results.argtypes = [vp]
     lib.pne_terms_n_results.restype = ctypes.c_int64
+    lib.pne_open_tensor.argtypes = [vp, vp, vp, ctypes.c_void_p, ctypes.c_void_p]
+    lib.pne_open_tensor.restype = ctypes.c_int
+    lib.pne_open_tensor_assemble.argtypes = [ctypes.POINTER(Result), ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                             ctypes.c_void_p]
+    lib.pne_open_tensor_assemble.restype = ctypes.c_int
     lib.pne_terms_export.argtypes = [vp, vp, vp, ctypes.c_void_p, ctypes.c_void_p]
     lib.pne_terms_export.restype = ctypes.c_int
     lib.pne_bp_messages_noalloc.argtypes = [ctypes.POINTER(Network), ctypes.c_double, ctypes.c_int32, ctypes.c_void_p,
@@ -205,7 +209,8 @@ def exported_symbols() -> list:
     lib = load_library()
     names = ["pne_ctx_create", "pne_ctx_destroy", "pne_last_error", "pne_ctx_set_allocator",
              "pne_build_partition", "pne_partition_destroy", "pne_enumerate_terms", "pne_terms_destroy",
-             "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_terms_export",
+             "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_open_tensor", "pne_open_tensor_assemble",
+             "pne_terms_export",
              "pne_ctx_profile", "pne_ctx_profile_read", "pne_ctx_trace_read", "pne_terms_work", "pne_measure_fma_peak",
              "pne_bp_messages_noalloc", "pne_partition_update", "pne_batch_create", "pne_batch_run",
              "pne_batch_n_results", "pne_batch_config", "pne_batch_destroy", "pne_server_create",
@@ -425,6 +430,29 @@ def pne_sum(ctx, terms, stream=None, allow_noconv=False):
     return Results(out)
 
 
+def pne_open_tensor(ctx, terms, n_sets, open_dims, stream=None, allow_noconv=False):
+    """The open-index tensors of every tensor set through the C call: returns
+    (mantissa [n_sets, *open_dims], log_scale [n_sets]); the tensor of set b is
+    mantissa[b] * exp(log_scale[b])."""
+    n = pne_terms_n_results(terms)
+    out = np.zeros(n, dtype=np.float64)
+    ls = np.zeros(n_sets, dtype=np.float64)
+    st = load_library().pne_open_tensor(ctx, terms, stream, out.ctypes.data, ls.ctypes.data)
+    if not (st == PNE_ENOCONV and allow_noconv):
+        _check(st, ctx)
+    return out.reshape((n_sets,) + tuple(open_dims)), ls
+
+
+def pne_open_tensor_assemble(results, n_sets, open_dims):
+    """The assembly step alone (host only) from pne_sum's results."""
+    arr = results._arr if isinstance(results, Results) else results
+    n_open = int(np.prod(open_dims)) if len(open_dims) else 1
+    out = np.zeros(n_sets * n_open, dtype=np.float64)
+    ls = np.zeros(n_sets, dtype=np.float64)
+    _check(load_library().pne_open_tensor_assemble(arr, int(n_sets), n_open, out.ctypes.data, ls.ctypes.data))
+    return out.reshape((n_sets,) + tuple(open_dims)), ls
+
+
 class Results(collections.abc.Sequence):
     """The results of a pne_sum call as a sequence of dicts (``Result.as_dict``).
     The values are already in host memory; each dict is built on first access."""
@@ -557,6 +585,30 @@ class Context:
         return res
 
 
+def _context_open_tensor(self, net, K, mode=PNE_MODE_LOOP, dtype=PNE_F64, data=None, n_batch=1, stream=None,
+                         arithmetic=0):
+    """One pass (partition -> enumerate -> contract) and the open-index tensor
+    through pne_open_tensor: (mantissa [n_batch, *open_dims], log_scale)."""
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    open_dims = [int(net.bond_dim[b]) for b in range(net.n_bonds) if int(net.bond_site[b][1]) < 0]
+    ns, keep = network_struct(net, data=data, n_batch=n_batch)
+    part, _ = pne_build_partition(self.h, ns, PartitionOpts(1e-13, 10000, 0.0, arithmetic), stream)
+    try:
+        terms, _, _ = pne_enumerate_terms(self.h, part, EnumOpts(K, mode, 1), stream)
+        try:
+            pne_contract_terms(self.h, terms, dtype, stream)
+            return pne_open_tensor(self.h, terms, n_batch, open_dims, stream)
+        finally:
+            pne_terms_destroy(terms)
+    finally:
+        pne_partition_destroy(part)
+        del keep
+
+
+Context.open_tensor = _context_open_tensor
+
+
 def run(net, K, mode=PNE_MODE_LOOP, dtype=PNE_F64, device=0, **kw):
     ctx = Context(device)
     try:
@@ -566,8 +618,11 @@ def run(net, K, mode=PNE_MODE_LOOP, dtype=PNE_F64, device=0, **kw):
 
 
 def open_tensor(results, open_dims, n_sets=1):
-    """Assemble the open-index tensors from pne_sum's results (set-major,
-    assignments row-major over the open bonds in ascending id)."""
-    vals = np.array([r["sign"] * math.exp(r["log_abs"]) if r["sign"] != 0 and np.isfinite(r["log_abs"]) else 0.0
-                     for r in results])
-    return vals.reshape((n_sets,) + tuple(open_dims))
+    """The open-index tensors (n_sets, *open_dims) from pne_sum's results,
+    assembled by the library (pne_open_tensor_assemble) and scaled back to
+    plain values; entries beyond the FP64 range become +-inf (use
+    pne_open_tensor_assemble for the mantissa and its log scale)."""
+    mant, ls = pne_open_tensor_assemble(results, n_sets, open_dims)
+    with np.errstate(over="ignore", invalid="ignore"):
+        scale = np.exp(np.where(np.isfinite(ls), ls, 0.0))
+    return mant * scale.reshape((n_sets,) + (1,) * len(open_dims))

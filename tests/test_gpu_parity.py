@@ -193,8 +193,9 @@ def test_reduced_precision_ising_cubic(ctx, dtype):
 def test_open_output_all_mode_exact(ctx):
     go = I.with_open_legs(I.square_lattice(3, 2, 2), [(0, 2), (2, 2), (4, 2)])
     net = I.random_tensors(go, 12)
-    res = ctx.expand(net, 7, pne.PNE_MODE_ALL, pne.PNE_F64)      # 7 closed bonds: full order
-    T = pne.open_tensor(res, [2, 2, 2])[0]
+    mant, ls = ctx.open_tensor(net, 7, pne.PNE_MODE_ALL, pne.PNE_F64)   # 7 closed bonds: full order
+    T = mant[0] * math.exp(ls[0])                                       # through pne_open_tensor
+    assert np.max(np.abs(mant)) == pytest.approx(1.0)
     assert Ex.eps2(Ex.contract_einsum(net), T) < 1e-12
 
 
@@ -202,9 +203,16 @@ def test_open_output_loop_parity(ctx):
     go = I.with_open_legs(I.square_lattice(4, 3, 3), [(0, 2), (5, 3), (11, 2)])
     net = I.random_tensors(go, 5)
     ref, entries, _ = X.pne_open(net, 8, E.LOOP)
-    res = ctx.expand(net, 8, pne.PNE_MODE_LOOP, pne.PNE_F64)
-    T = pne.open_tensor(res, [2, 3, 2])[0]
+    mant, ls = ctx.open_tensor(net, 8, pne.PNE_MODE_LOOP, pne.PNE_F64)
+    T = mant[0] * math.exp(ls[0])                                       # through pne_open_tensor
     np.testing.assert_allclose(T, ref, rtol=1e-10)
+    # two tensor sets at once: set-major output, one scale per set
+    net2 = I.random_tensors(go, 6)
+    data = np.concatenate([net.flat_data()[0], net2.flat_data()[0]])
+    mant2, ls2 = ctx.open_tensor(net, 8, pne.PNE_MODE_LOOP, pne.PNE_F64, data=data, n_batch=2)
+    ref2, _, _ = X.pne_open(net2, 8, E.LOOP)
+    np.testing.assert_allclose(mant2[0] * math.exp(ls2[0]), ref, rtol=1e-10)
+    np.testing.assert_allclose(mant2[1] * math.exp(ls2[1]), ref2, rtol=1e-10)
 
 
 # ---------------------------------------------------------------- edge cases

@@ -110,3 +110,42 @@ def test_open_tensor_assembles_set_major_row_major_slices():
     want[0, 1, 2] = 0.0
     got = pne.open_tensor(pne.Results(arr), dims, n_sets)
     np.testing.assert_allclose(got, want, rtol=1e-15)
+
+
+def test_noalloc_bp_rejects_an_oversized_network_on_the_host():
+    # the scratch-size check runs on the host before any CUDA call: a network
+    # whose messages alone exceed PNE_NOALLOC_SCRATCH_BYTES (8 MiB) comes back
+    # with PNE_EINVAL; the device pointers are never dereferenced, so stand-ins
+    # serve (no GPU is touched)
+    import numpy as np
+    from paper_2512_10910_gb300 import inputs as I
+    g = I.square_lattice(4, 4, 2)
+    B = 4096
+    ns, keep = pne.network_struct(g, data=np.zeros(1), n_batch=B)
+    ns.data = 0x1000
+    ns.data_on_device = 1
+    with pytest.raises(pne.PneError) as e:
+        pne.pne_bp_messages_noalloc(ns, 0x2000, 1e-13, 10000)
+    assert e.value.status == pne.PNE_EINVAL and "PNE_NOALLOC_SCRATCH_BYTES" in str(e.value)
+    del keep
+
+
+def test_open_tensor_assembly_keeps_huge_values_as_mantissa_and_scale():
+    # slices whose |Z_K| is far beyond the FP64 range (ln|Z| ~ 800): the
+    # library's assembly returns mantissas in [-1, 1] and the log scale
+    import math
+    import numpy as np
+    n_sets, n_open = 2, 4
+    arr = (pne.Result * (n_sets * n_open))()
+    logs = [800.0, 801.5, 799.0, 802.25, -3.0, -2.0, float("-inf"), -1.0]
+    signs = [1, -1, 1, 1, -1, 1, 1, 1]
+    for r in range(n_sets * n_open):
+        arr[r].sign = signs[r]
+        arr[r].log_abs = logs[r]
+        arr[r].n_orders = 1
+    mant, ls = pne.pne_open_tensor_assemble(pne.Results(arr), n_sets, [n_open])
+    assert ls[0] == 802.25 and ls[1] == -1.0
+    np.testing.assert_allclose(mant[0], [math.exp(-2.25), -math.exp(-0.75), math.exp(-3.25), 1.0], rtol=1e-15)
+    np.testing.assert_allclose(mant[1], [-math.exp(-2.0), math.exp(-1.0), 0.0, 1.0], rtol=1e-15)
+    full = pne.open_tensor(pne.Results(arr), [n_open], n_sets)     # plain values: +-inf beyond range
+    assert np.isinf(full[0]).all() and np.isfinite(full[1]).all()
