@@ -8,7 +8,14 @@ enumeration, cluster contractions, FP64 term sums) over a batch of 32
 networks.  Metric: PNE terms contracted per second (whole job, all ranks).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pne|reference]
-                  [--dtype f64|f32|tf32|bf16] [--workload random16|ising4|ising3d]
+                  [--dtype f64|f32|tf32|bf16] [--bp ff|fp64]
+                  [--workload random16|ising4|ising3d|batched|serve] [--no-extras]
+
+At one GPU the default run also measures, in the same process and under
+"workloads" of the same JSON line: the step with FP64 BP; the 3D Ising 8x8x8
+networks at orders 8 and 10 in FP64/TF32/BF16 against the closed form; the
+batched form (4096 networks, one fused launch); and the served form against
+the plain FP64 single-request path on the same request trace.
 
 Under torchrun each rank works on its own 32 networks (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
@@ -148,6 +155,118 @@ def algorithmic_bp_flops(g, iters):
     return per_sweep * float(sum(iters))
 
 
+def oracle_all_cores(wl, nets, budget_s=10.0):
+    """The oracle as it stands, one network per process on every host core
+    (spawned workers, before any GPU work of theirs), whole networks of the
+    step until about budget_s of wall time; returns (terms, seconds, cores,
+    networks)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    done_terms, used = 0, 0
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        i = 0
+        while i < len(nets):
+            batch = nets[i:i + cores]
+            for nt, _, _ in ex.map(_oracle_worker, [(wl, n) for n in batch]):
+                done_terms += nt
+            used += len(batch)
+            i += len(batch)
+            if time.perf_counter() - t0 > budget_s:
+                break
+    return done_terms, time.perf_counter() - t0, cores, used
+
+
+def _oracle_worker(arg):
+    wl, net = arg
+    nt, secs, _ = oracle_step(wl, net)
+    return nt, secs, None
+
+
+class StepBench:
+    """One pass of the hot path over a batch of networks of one geometry:
+    partition (BP, gauge) on the main stream, enumeration (geometry only,
+    recomputed every step unless enum_cache) on a second stream while BP runs,
+    contraction after both, FP64 sums; L2 flushed between timed steps."""
+
+    def __init__(self, ctx, pne, torch, dev, g, nets, K, mode, bp_arith, world=1, dist=None):
+        self.ctx, self.pne, self.torch, self.dev = ctx, pne, torch, dev
+        self.g, self.nets, self.K, self.mode = g, nets, K, mode
+        self.B = len(nets)
+        self.world, self.dist = world, dist
+        self.flat = np.concatenate([n.flat_data()[0] for n in nets])
+        self.data_dev = torch.from_numpy(self.flat).to(dev)
+        self.data_host = torch.from_numpy(self.flat).pin_memory()
+        self.stream = torch.cuda.current_stream(dev)
+        self.sh = self.stream.cuda_stream
+        # the enumeration is the longer chain: its stream gets the higher
+        # priority, so its small level launches are scheduled ahead of BP's blocks
+        self.side = torch.cuda.Stream(dev, priority=-1)
+        self.side_h = self.side.cuda_stream
+        self.joined = torch.cuda.Event()
+        self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+        self.enum_cache = 0
+        self.structs = {}
+        self.set_bp(bp_arith)
+
+    def set_bp(self, bp_arith):
+        self.popts = self.pne.PartitionOpts(1e-13, 10000, 0.0, bp_arith, 1)
+
+    def step(self, data, dtype):
+        pne = self.pne
+        # the network description is marshalled once per input buffer, as a
+        # caller stepping one geometry would; the library reads and checks it
+        # on every call
+        if id(data) not in self.structs:
+            self.structs[id(data)] = pne.network_struct(self.g, data=data, n_batch=self.B)
+        ns, keep = self.structs[id(data)]
+        part, _ = pne.pne_build_partition(self.ctx.h, ns, self.popts, self.sh)
+        try:
+            terms, nc, nt = pne.pne_enumerate_terms(self.ctx.h, part, pne.EnumOpts(self.K, self.mode, self.enum_cache),
+                                                    self.side_h)
+            try:
+                self.joined.record(self.side)
+                self.stream.wait_event(self.joined)
+                pne.pne_contract_terms(self.ctx.h, terms, dtype, self.sh)
+                res = pne.pne_sum(self.ctx.h, terms, self.sh)
+            finally:
+                pne.pne_terms_destroy(terms)
+        finally:
+            pne.pne_partition_destroy(part)
+        return res
+
+    def timed(self, data, dtype, steps, warmup, profile=False):
+        torch, pne = self.torch, self.pne
+        for _ in range(warmup):
+            self.step(data, dtype)
+        if self.world > 1:
+            self.dist.barrier()
+        torch.cuda.synchronize(self.dev)
+        if profile:
+            pne.pne_ctx_profile(self.ctx.h, True)
+        total = 0.0
+        res = None
+        for _ in range(steps):
+            self.flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            res = self.step(data, dtype)
+            b.record(self.stream)
+            b.synchronize()
+            total += a.elapsed_time(b)
+        torch.cuda.synchronize(self.dev)
+        prof = pne.pne_ctx_profile_read(self.ctx.h) if profile else None
+        if profile:
+            pne.pne_ctx_profile(self.ctx.h, False)
+        if self.world > 1:
+            t = torch.tensor([total], device=self.dev, dtype=torch.float64)
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total, res, prof
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -158,6 +277,9 @@ def main():
     ap.add_argument("--workload", default="random16", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads measured beside the default line")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the served trace")
     ap.add_argument("--bp", default="ff", choices=["fp64", "ff"],
                     help="BP sweep arithmetic: FP64, or float-float pairs on the FP32 pipes")
     args = ap.parse_args()
@@ -170,10 +292,19 @@ def main():
     if args.impl == "reference":
         return run_reference(args, wl, rank, world)
     if wl["kind"] == "batched":
-        return run_batched(args, wl, rank, world, local_rank)
+        out = run_batched(args, wl, rank, world, local_rank)
+        if rank == 0 and out:
+            print(json.dumps(out))
+        return 0
     if wl["kind"] == "serve":
-        return run_serve(args, wl, rank, world, local_rank)
+        out = run_serve_workload(args, wl, rank, world, local_rank)
+        if rank == 0 and out:
+            print(json.dumps(out))
+        return 0 if out else 1
+    return run_step_bench(args, wl, rank, world, local_rank)
 
+
+def run_step_bench(args, wl, rank, world, local_rank):
     import torch
     import torch.distributed as dist
     from paper_2512_10910_gb300 import pne
@@ -182,90 +313,22 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)
-    stream = torch.cuda.current_stream(dev)
-    sh = ctypes_stream = stream.cuda_stream
-
     g, nets = make_networks(wl, rank)
-    B = len(nets)
-    flat = np.concatenate([n.flat_data()[0] for n in nets])
-    data_dev = torch.from_numpy(flat).to(dev)
-    data_host = torch.from_numpy(flat).pin_memory()
     ctx = pne.Context(local_rank)
     K, mode = wl["K"], wl["mode"]
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
-
-    enum_cache = [0]      # the headline recomputes the enumeration every step
-    # the enumeration is geometry-only: it runs on a second stream while BP runs
-    # on the first (the partition is built without waiting for its convergence
-    # record, which pne_sum reads); the contraction waits for both
-    # the enumeration is the longer chain: its stream gets the higher priority,
-    # so its small level launches are scheduled ahead of BP's blocks
-    side = torch.cuda.Stream(dev, priority=-1)
-    side_h = side.cuda_stream
-    joined = torch.cuda.Event()
-
-    # the network description (geometry arrays, tensor pointer) is marshalled
-    # once per input buffer, as a caller stepping one geometry would; the
-    # library still reads and checks it on every call
-    structs = {}
-    popts = pne.PartitionOpts(1e-13, 10000, 0.0, BP_ARITH[args.bp], 1)
-
-    def step(data, dtype):
-        if id(data) not in structs:
-            structs[id(data)] = pne.network_struct(g, data=data, n_batch=B)
-        ns, keep = structs[id(data)]
-        part, _ = pne.pne_build_partition(ctx.h, ns, popts, ctypes_stream)
-        try:
-            terms, nc, nt = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, mode, enum_cache[0]), side_h)
-            try:
-                joined.record(side)
-                stream.wait_event(joined)
-                pne.pne_contract_terms(ctx.h, terms, dtype, ctypes_stream)
-                res = pne.pne_sum(ctx.h, terms, ctypes_stream)
-            finally:
-                pne.pne_terms_destroy(terms)
-        finally:
-            pne.pne_partition_destroy(part)
-        return res
-
-    def timed(data, dtype, steps, warmup, profile=False):
-        for _ in range(warmup):
-            step(data, dtype)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        if profile:
-            pne.pne_ctx_profile(ctx.h, True)
-        total = 0.0
-        res = None
-        for _ in range(steps):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            res = step(data, dtype)
-            b.record(stream)
-            b.synchronize()
-            total += a.elapsed_time(b)
-        torch.cuda.synchronize(dev)
-        prof = pne.pne_ctx_profile_read(ctx.h) if profile else None
-        if profile:
-            pne.pne_ctx_profile(ctx.h, False)
-        if world > 1:
-            t = torch.tensor([total], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
-        return total, res, prof
+    sb = StepBench(ctx, pne, torch, dev, g, nets, K, mode, BP_ARITH[args.bp], world, dist)
+    B = sb.B
+    ctypes_stream = sb.sh
 
     dtype = pne.DTYPES[args.dtype]
     clocks = ClockSampler(local_rank)
     clocks.start()
-    total_ms, res, _ = timed(data_dev, dtype, args.steps, args.warmup)
+    total_ms, res, _ = sb.timed(sb.data_dev, dtype, args.steps, args.warmup)
     clk = clocks.stop()
     # per-kernel event timings come from a separate pass, so that the timed
     # steps carry no profiling events
     prof_steps = max(5, args.steps // 4)
-    _, _, prof_all = timed(data_dev, dtype, prof_steps, 1, profile=True)
+    _, _, prof_all = sb.timed(sb.data_dev, dtype, prof_steps, 1, profile=True)
     prof = {k: v for k, v in prof_all.items() if not k.startswith("host:")}
     host_ms = {k[5:]: round(v[1] / prof_steps, 4) for k, v in prof_all.items() if k.startswith("host:")}
     n_terms = res[0]["n_terms"]
@@ -274,71 +337,155 @@ def main():
     value = terms_per_step * world / (ms_per_step * 1e-3)
 
     # end to end: host (pinned) input copied inside the call, results read back
-    e2e_ms, _, _ = timed(data_host, dtype, max(5, args.steps // 5), 2)
-    e2e_ms /= max(5, args.steps // 5)
+    n_e2e = max(5, args.steps // 5)
+    e2e_ms, _, _ = sb.timed(sb.data_host, dtype, n_e2e, 2)
+    e2e_ms /= n_e2e
     geom_bytes = 2 * ((g.n_sites + 1) * 8 + (3 * g.n_bonds + g.n_sites + 1 + len(g.site_bonds) + 2 * g.n_bonds
                                               + len(g.site_bonds) + 64 * g.n_sites) * 4)
-    h2d = int(flat.nbytes + geom_bytes)
+    h2d = int(sb.flat.nbytes + geom_bytes)
     d2h = int(B * (K + 1) * 2 * 8 + B * 3 * 8 + B * 12 + 64)
 
-    # variants in the other precisions (fewer steps)
+    n_var = max(5, args.steps // 5)
     variants = {}
     if not args.no_variants:
         for dn in ("f64", "f32", "tf32", "bf16"):
             if dn == args.dtype:
                 continue
-            tv, rv, _ = timed(data_dev, pne.DTYPES[dn], max(5, args.steps // 5), 2)
-            msv = tv / max(5, args.steps // 5)
+            tv, rv, _ = sb.timed(sb.data_dev, pne.DTYPES[dn], n_var, 2)
+            msv = tv / n_var
             variants[dn] = {"value": terms_per_step * world / (msv * 1e-3), "ms_per_step": msv,
                             "log_abs_first": rv[0]["log_abs"], "err_bound_first": rv[0]["err_bound"]}
+        # the step with the other BP arithmetic (the partition in FP64 sweeps,
+        # or in float-float), everything else the same
+        other = "fp64" if args.bp == "ff" else "ff"
+        sb.set_bp(BP_ARITH[other])
+        tv, rv, _ = sb.timed(sb.data_dev, dtype, n_var, 2)
+        sb.set_bp(BP_ARITH[args.bp])
+        msv = tv / n_var
+        variants[args.dtype + "_bp_" + other] = {"value": terms_per_step * world / (msv * 1e-3), "ms_per_step": msv,
+                                                 "max_abs_dlnZ_vs_headline": max(abs(a["log_abs"] - b["log_abs"])
+                                                                                 for a, b in zip(rv, res))}
         # context only: the same step with the enumeration taken from the
         # context's cache (geometry-only work done once, as a user stepping many
         # tensor sets of one geometry would); not the headline
-        enum_cache[0] = 1
-        tv, rv, _ = timed(data_dev, dtype, max(5, args.steps // 5), 2)
-        enum_cache[0] = 0
-        msv = tv / max(5, args.steps // 5)
+        sb.enum_cache = 1
+        tv, rv, _ = sb.timed(sb.data_dev, dtype, n_var, 2)
+        sb.enum_cache = 0
+        msv = tv / n_var
         variants[args.dtype + "_enumeration_cached"] = {"value": terms_per_step * world / (msv * 1e-3),
                                                         "ms_per_step": msv}
 
-    # roofline of the dominant kernel (largest event-timed share of the step)
+    roof = step_roofline(args, pne, ctx, ctypes_stream, g, sb, res, prof, prof_steps, B, K, mode)
+    gpu_launches = int(round(sum(v[0] for v in prof.values()) / prof_steps)) * args.steps
+
+    out = {
+        "metric": "PNE terms contracted/sec",
+        "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": wl["desc"], "networks_per_step_per_gpu": B, "terms_per_network": n_terms,
+                   "clusters_per_network": res[0]["n_clusters"], "K": K,
+                   "bp_arithmetic": {"ff": "float-float pairs of FP32 (~2^-48 per operation), FP64 storage",
+                                     "fp64": "FP64"}[args.bp],
+                   "contraction_dtype": args.dtype, "term_sums": "FP64",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "enumeration": "recomputed every step (cache off)",
+                   "parallelism": f"independent networks per GPU x{world}"},
+        "e2e": {"value": terms_per_step * world / (e2e_ms * 1e-3), "unit": "terms/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": gpu_launches,
+        "host_ms_per_step": host_ms,
+        "roofline": roof,
+        "clocks": clk,
+        "variants": variants,
+        "peaks_measured": roof.pop("_peaks"),
+    }
+
+    # CPU baseline: the oracle on a bounded sample (rank 0, single GPU only)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nt, secs, r = oracle_step(wl, nets[0])
+        used = 1
+        while secs < 10.0 and used < B:
+            nt_i, secs_i, _ = oracle_step(wl, nets[used])
+            nt += nt_i; secs += secs_i; used += 1
+        t_all, s_all, cores, n_all = oracle_all_cores(wl, nets, 10.0)
+        out["cpu_baseline"] = {"value": t_all / s_all, "unit": "terms/s", "cores": cores, "kind": "oracle",
+                               "sample": f"networks 0..{n_all - 1} of the {B} per step, full oracle pipeline, one "
+                                         f"network per process on {cores} host cores ({t_all} terms in "
+                                         f"{s_all:.1f} s wall)",
+                               "single_thread": {"value": nt / secs, "cores": 1,
+                                                 "sample": f"networks 0..{used - 1}, {nt} terms in {secs:.1f} s"}}
+        # time to 1e-6: wall time of one pass through the four calls (first
+        # call to pne_sum's return) for each dtype on network 0, and its error
+        ttt = {}
+        for dn in ("bf16", "tf32", "f32", "f64"):
+            t0 = time.perf_counter()
+            (rr,) = ctx.expand(nets[0], K, mode, pne.DTYPES[dn], arithmetic=BP_ARITH[args.bp])
+            wall = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            (rr,) = ctx.expand(nets[0], K, mode, pne.DTYPES[dn], arithmetic=BP_ARITH[args.bp])
+            wall = min(wall, time.perf_counter() - t0)
+            err = abs(math.expm1(rr["log_abs"] - r.log_abs))
+            ttt[dn] = {"rel_err_vs_oracle": err, "wall_ms_build_to_sum": 1e3 * wall,
+                       "err_bound": rr["err_bound"], "reached_1e-6": bool(err <= 1e-6)}
+        ok = [d for d in ("bf16", "tf32", "f32", "f64") if ttt[d]["reached_1e-6"]]
+        out["time_to_1e-6"] = {"cheapest_dtype": ok[0] if ok else None,
+                               "wall_ms": ttt[ok[0]]["wall_ms_build_to_sum"] if ok else None,
+                               "network": "network 0 of the step (one network, enumeration cached)",
+                               "by_dtype": ttt}
+
+    if rank == 0 and world == 1 and not args.no_extras and wl["kind"] == "random2d":
+        extras = {}
+        for name, fn in (("cfg3_ising3d_8x8x8", run_cfg3), ("cfg4_batched", run_batched_extra),
+                         ("cfg5_served", run_served_comparison)):
+            t0 = time.perf_counter()
+            try:
+                extras[name] = fn(args, ctx, pne, torch, dev, local_rank)
+            except Exception as e:          # a failed extra is reported, the headline stands
+                extras[name] = {"error": f"{type(e).__name__}: {e}"}
+            extras[name]["bench_seconds"] = round(time.perf_counter() - t0, 1)
+        out["workloads"] = extras
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def step_roofline(args, pne, ctx, ctypes_stream, g, sb, res, prof, prof_steps, B, K, mode):
+    """Roofline entry of the dominant kernel (largest event-timed share of the
+    step), with the contraction and BP sweeps against their own roofs beside it."""
     fam, (launches, tot) = max(prof.items(), key=lambda kv: kv[1][1])
     avg_ms = tot / max(launches, 1)
-    # the launch sequence of a step is fixed for a given network: launches per
-    # profiled step times the timed steps
-    gpu_launches = int(round(sum(v[0] for v in prof.values()) / prof_steps)) * args.steps
     peak_f64 = pne.pne_measure_fma_peak(ctx.h, pne.PNE_F64, ctypes_stream)
     peak_f32 = pne.pne_measure_fma_peak(ctx.h, pne.PNE_F32, ctypes_stream)
     roof = {"kernel": fam, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s",
             "frac": None, "traffic": None}
+    iters = [r["bp_iters"] for r in res[:B]]
+    ns, keep = pne.network_struct(g, data=sb.data_dev, n_batch=B)
+    part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0, BP_ARITH[args.bp]),
+                                      ctypes_stream)
+    terms, _, _ = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, mode, 0), ctypes_stream)
+    fma = pne.pne_terms_work(ctx.h, terms, ctypes_stream) if mode == pne.PNE_MODE_LOOP else 0
+    pne.pne_terms_destroy(terms)
+    pne.pne_partition_destroy(part)
+    pk_c = peak_f64 if args.dtype == "f64" else peak_f32
+    bp_peak = (peak_f32 / 16) if args.bp == "ff" else peak_f64
+    bp_src = ("measured FP32 FMA-chain kernel (pne_measure_fma_peak) / 16 FP32 instructions per float-float "
+              "multiply-add" if args.bp == "ff" else "measured FP64 FMA-chain kernel (pne_measure_fma_peak)")
+    bp_work = f"4 flops per tensor entry per site per sweep; {sum(iters)} sweeps over {B} sets"
+    c_work = f"2 flops per plan multiply-add; {fma} multiply-adds per network"
     if fam == "bp_sweeps":
-        iters = [r["bp_iters"] for r in res[:B]]
-        flops = algorithmic_bp_flops(g, iters)
-        if args.bp == "ff":
-            # float-float sweeps: a multiply-add costs 16 FP32 instructions (8 for the
-            # error-free product, 8 for the compensated accumulation), so the ALU
-            # roof for this work is the FP32 FMA-chain rate / 16
-            roof.update(achieved=flops / (avg_ms * 1e-3) / 1e12, peak=peak_f32 / 16 / 1e12,
-                        peak_source="measured FP32 FMA-chain kernel (pne_measure_fma_peak) / 16 FP32 "
-                                    "instructions per float-float multiply-add",
-                        work=f"4 flops per tensor entry per site per sweep; {sum(iters)} sweeps over {B} sets")
-        else:
-            roof.update(achieved=flops / (avg_ms * 1e-3) / 1e12, peak=peak_f64 / 1e12,
-                        peak_source="measured FP64 FMA-chain kernel (pne_measure_fma_peak)",
-                        work=f"4 flops per tensor entry per site per sweep; {sum(iters)} sweeps over {B} sets")
+        roof.update(achieved=algorithmic_bp_flops(g, iters) / (avg_ms * 1e-3) / 1e12, peak=bp_peak / 1e12,
+                    peak_source=bp_src, work=bp_work)
     elif fam == "contract":
-        ns, keep = pne.network_struct(g, data=data_dev, n_batch=B)
-        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0, BP_ARITH[args.bp]), ctypes_stream)
-        terms, _, _ = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, mode, 0), ctypes_stream)
-        fma = pne.pne_terms_work(ctx.h, terms, ctypes_stream)
-        pne.pne_terms_destroy(terms); pne.pne_partition_destroy(part)
-        pk = peak_f64 if args.dtype == "f64" else peak_f32
-        roof.update(achieved=2.0 * fma * B / (avg_ms * 1e-3) / 1e12, peak=pk / 1e12,
-                    peak_source="measured FMA-chain kernel (pne_measure_fma_peak)",
-                    work=f"2 flops per plan multiply-add; {fma} multiply-adds per network")
+        roof.update(achieved=2.0 * fma * B / (avg_ms * 1e-3) / 1e12, peak=pk_c / 1e12,
+                    peak_source="measured FMA-chain kernel (pne_measure_fma_peak)", work=c_work)
     elif fam in ("enum_expand", "enum_dfs"):
-        # the cluster search is integer work bound by latency; its algorithmic
-        # traffic is the cluster lists it writes (edges, sorted vertices, size)
+        # the cluster search is integer work bound by issue and latency; its
+        # algorithmic traffic is the cluster lists it writes (edges, sorted
+        # vertices, size) -- an HBM fraction far below 1 by nature
         n_cl = res[0]["n_clusters"]
         per_cluster = 4 * K + 4 * (K + 1) + 4
         per_search_ms = tot / prof_steps
@@ -351,84 +498,72 @@ def main():
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["avg_launch_ms"] = avg_ms
     roof["kernel_shares"] = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()}
-    # context beside the dominant kernel: the contraction and BP sweeps against
-    # their own arithmetic roofs (event-timed in the same profiled steps)
     others = {}
-    if "contract" in prof and fam != "contract":
-        ns, keep = pne.network_struct(g, data=data_dev, n_batch=B)
-        part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0, BP_ARITH[args.bp]), ctypes_stream)
-        terms, _, _ = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(K, mode, 0), ctypes_stream)
-        if mode == pne.PNE_MODE_LOOP:
-            fma = pne.pne_terms_work(ctx.h, terms, ctypes_stream)
-            c_ms = prof["contract"][1] / prof_steps
-            pk = peak_f64 if args.dtype == "f64" else peak_f32
-            ach = 2.0 * fma * B / (c_ms * 1e-3) / 1e12
-            others["contract"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": pk / 1e12,
-                                  "frac": ach / (pk / 1e12), "ms_per_step": c_ms,
-                                  "work": f"2 flops per plan multiply-add; {fma} multiply-adds per network",
-                                  "peak_source": "measured FMA-chain kernel (pne_measure_fma_peak)"}
-        pne.pne_terms_destroy(terms); pne.pne_partition_destroy(part)
-    if "bp_sweeps" in prof and fam != "bp_sweeps" and args.bp == "ff":
-        iters = [r["bp_iters"] for r in res[:B]]
+    if "contract" in prof and fam != "contract" and fma:
+        c_ms = prof["contract"][1] / prof_steps
+        ach = 2.0 * fma * B / (c_ms * 1e-3) / 1e12
+        others["contract"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": pk_c / 1e12,
+                              "frac": ach / (pk_c / 1e12), "ms_per_step": c_ms, "work": c_work,
+                              "peak_source": "measured FMA-chain kernel (pne_measure_fma_peak)"}
+    if "bp_sweeps" in prof and fam != "bp_sweeps":
         b_ms = prof["bp_sweeps"][1] / prof_steps
         ach = algorithmic_bp_flops(g, iters) / (b_ms * 1e-3) / 1e12
-        others["bp_sweeps"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": peak_f32 / 16 / 1e12,
-                               "frac": ach / (peak_f32 / 16 / 1e12), "ms_per_step": b_ms,
-                               "work": f"4 flops per tensor entry per site per sweep; {sum(iters)} sweeps over {B} sets",
-                               "peak_source": "measured FP32 FMA-chain kernel / 16 FP32 instructions per "
-                                              "float-float multiply-add"}
+        others["bp_sweeps"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": bp_peak / 1e12,
+                               "frac": ach / (bp_peak / 1e12), "ms_per_step": b_ms, "work": bp_work,
+                               "peak_source": bp_src}
     if others:
         roof["others"] = others
-
-    out = {
-        "metric": "PNE terms contracted/sec",
-        "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": args.dtype, "data": "synthetic",
-        "config": {"workload": wl["desc"], "networks_per_step_per_gpu": B, "terms_per_network": n_terms,
-                   "clusters_per_network": res[0]["n_clusters"], "K": K,
-                   "l2": "flushed between timed steps (256 MB write)",
-                   "enumeration": "recomputed every step (cache off)",
-                   "parallelism": f"independent networks per GPU x{world}"},
-        "e2e": {"value": terms_per_step * world / (e2e_ms * 1e-3), "unit": "terms/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "gpu_launches": gpu_launches,
-        "host_ms_per_step": host_ms,
-        "roofline": roof,
-        "clocks": clk,
-        "variants": variants,
-        "peaks_measured": {"fp64_tflops": peak_f64 / 1e12, "fp32_tflops": peak_f32 / 1e12},
-    }
-
-    # CPU baseline: the oracle on a bounded sample (rank 0, single GPU only)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # whole networks of the step, in order, until about 10 s of CPU work
-        nt, secs, r = oracle_step(wl, nets[0])
-        used = 1
-        while secs < 10.0 and used < B:
-            nt_i, secs_i, _ = oracle_step(wl, nets[used])
-            nt += nt_i; secs += secs_i; used += 1
-        out["cpu_baseline"] = {"value": nt / secs, "unit": "terms/s", "cores": 1, "kind": "oracle",
-                               "sample": f"networks 0..{used - 1} of the {B} per step, full oracle pipeline "
-                                         f"({nt} terms in {secs:.1f} s, single thread)"}
-        # time to 1e-6: cheapest dtype whose result is within 1e-6 of the oracle
-        ttt = {}
-        for dn in ("bf16", "tf32", "f32", "f64"):
-            (rr,) = ctx.expand(nets[0], K, mode, pne.DTYPES[dn])
-            err = abs(math.expm1(rr["log_abs"] - r.log_abs))
-            ms = ms_per_step if dn == args.dtype else variants.get(dn, {}).get("ms_per_step")
-            ttt[dn] = {"rel_err_vs_oracle": err, "ms_per_step": ms, "reached_1e-6": bool(err <= 1e-6)}
-        ok = [d for d in ("bf16", "tf32", "f32", "f64") if ttt[d]["reached_1e-6"]]
-        out["time_to_1e-6"] = {"cheapest_dtype": ok[0] if ok else None,
-                               "ms_per_step": ttt[ok[0]]["ms_per_step"] if ok else None, "by_dtype": ttt}
-    if rank == 0:
-        print(json.dumps(out))
-    ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
+    roof["_peaks"] = {"fp64_tflops": peak_f64 / 1e12, "fp32_tflops": peak_f32 / 1e12,
+                      "how": "FMA-chain kernel (pne_measure_fma_peak), 2 flops per FMA"}
+    del keep
+    return roof
 
 
-def run_batched(args, wl, rank, world, local_rank):
+# ---------------------------------------------------------------- cfg3
+def ising3d_closed_form(g, beta, K, even_by_order):
+    """ln Z_K of the Ising network in the paramagnetic gauge: Z_BP = 2^N
+    cosh^M(beta) times sum_{k<=K} n_k tanh^k(beta), n_k the even subgraphs of k
+    bonds (the oracle's counts)."""
+    t = math.tanh(beta)
+    s = sum(n * t ** int(k) for k, n in even_by_order.items() if int(k) <= K)
+    return g.n_sites * math.log(2.0) + g.n_bonds * math.log(math.cosh(beta)) + math.log(s)
+
+
+def run_cfg3(args, ctx, pne, torch, dev, local_rank):
+    """3D Ising 8x8x8, beta in {0.20, 0.2217, 0.25}, orders 8 and 10, cluster
+    contractions in FP64, TF32 and BF16 (FP32 accumulation, per-cluster log
+    scale), FP64 term sums; each result against the closed form with the
+    oracle's even-subgraph counts (tests/golden/cluster_counts.json)."""
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", "cluster_counts.json")))["cases"]
+    even = golden["cubic8x8x8_K10"]["even_terms_by_order"]
+    g = I.cubic_lattice(8, 8, 8, 2)
+    betas = (0.20, 0.2217, 0.25)
+    nets = [I.ising_tensors(g, b) for b in betas]
+    out = {"workload": "3D Ising 8x8x8 open, D=2, beta in {0.20, 0.2217, 0.25} (3 networks per step), LOOP",
+           "reference": "closed form: N ln2 + M ln cosh(beta) + ln sum_k n_k tanh^k(beta), n_k = even subgraphs "
+                        "of k bonds counted by the oracle"}
+    sb = StepBench(ctx, pne, torch, dev, g, nets, 8, pne.PNE_MODE_LOOP, BP_ARITH[args.bp])
+    for K in (8, 10):
+        sb.K = K
+        rows = {}
+        for dn in ("f64", "tf32", "bf16"):
+            tot, res, _ = sb.timed(sb.data_dev, pne.DTYPES[dn], 5, 2)
+            ms = tot / 5
+            errs = [abs(math.expm1(r["log_abs"] - ising3d_closed_form(g, b, K, even))) for r, b in zip(res, betas)]
+            rows[dn] = {"value": res[0]["n_terms"] * len(nets) / (ms * 1e-3), "ms_per_step": ms,
+                        "max_rel_err_vs_closed_form": max(errs), "max_err_bound": max(r["err_bound"] for r in res)}
+        out[f"K{K}"] = {"terms_per_network": res[0]["n_terms"], "clusters_per_network": res[0]["n_clusters"],
+                        "by_dtype": rows, "enumeration": "recomputed every step (cache off)"}
+    return out
+
+
+# ---------------------------------------------------------------- cfg4
+def run_batched_extra(args, ctx, pne, torch, dev, local_rank):
+    wl = WORKLOADS["batched"]
+    return run_batched(args, wl, 0, 1, local_rank, steps=min(args.steps, 20), warmup=3)
+
+
+def run_batched(args, wl, rank, world, local_rank, steps=None, warmup=None):
     """cfg4: networks grouped by geometry; one partition and one enumeration
     per group (enumeration is geometry-only and built once), one batch over all
     groups.  A step re-runs every partition on its tensors (BP, gauge) and
@@ -437,8 +572,11 @@ def run_batched(args, wl, rank, world, local_rank):
     import torch
     import torch.distributed as dist
     from paper_2512_10910_gb300 import pne
+    steps = steps or args.steps
+    warmup = args.warmup if warmup is None else warmup
     torch.cuda.set_device(local_rank)
-    if world > 1:
+    own_pg = world > 1 and not dist.is_initialized()
+    if own_pg:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
@@ -479,7 +617,7 @@ def run_batched(args, wl, rank, world, local_rank):
             stream.wait_stream(st)
         return pne.pne_batch_run(ctx.h, batch, sh)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(local_rank)
@@ -487,7 +625,7 @@ def run_batched(args, wl, rank, world, local_rank):
     pne.pne_ctx_profile(ctx.h, True)
     total = 0.0
     res = None
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True); e = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -501,12 +639,11 @@ def run_batched(args, wl, rank, world, local_rank):
         tt = torch.tensor([total], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total = float(tt.item())
-    ms = total / args.steps
+    ms = total / steps
     n_terms = sum(r["n_terms"] for r in res)
     n_clusters = sum(r["n_clusters"] for r in res)
-    fam, (launches, tot) = max(prof.items(), key=lambda kv: kv[1][1])
     out = {"metric": "PNE terms contracted/sec", "value": n_terms * world / (ms * 1e-3), "unit": "terms/s",
-           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "n_gpus": world, "steps": steps, "warmup": warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": wl["desc"], "networks": len(work), "geometry_groups": len(groups),
                       "terms_per_step": n_terms, "clusters_per_step": n_clusters,
@@ -515,21 +652,20 @@ def run_batched(args, wl, rank, world, local_rank):
                       "l2": "flushed between timed steps (256 MB write)"},
            "gpu_launches": int(sum(v[0] for v in prof.values())),
            "kernel_shares": {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in prof.items()},
-           "kernel_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in prof.items()},
+           "kernel_ms_per_step": {k: round(v[1] / steps, 3) for k, v in prof.items()},
            "clocks": clk}
-    if rank == 0:
-        print(json.dumps(out))
     pne.pne_batch_destroy(batch)
     for t in terms:
         pne.pne_terms_destroy(t)
     for p in parts:
         pne.pne_partition_destroy(p)
     ctx.close()
-    if world > 1:
+    if own_pg:
         dist.destroy_process_group()
-    del fam, launches, tot
+    return out
 
 
+# ---------------------------------------------------------------- cfg5
 def serve_trace(n, rate, seed):
     """Arrival times and request descriptors of the served workload."""
     u = I.splitmix64_uniform(seed, 6 * n).reshape(n, 6)
@@ -546,77 +682,76 @@ def serve_trace(n, rate, seed):
     return t, reqs
 
 
-def run_serve(args, wl, rank, world, local_rank):
-    """cfg5: requests replayed in real time against the library's server.
-    Geometries (and their enumerations) are warmed once before the trace."""
-    import torch
-    from paper_2512_10910_gb300 import pne
-    torch.cuda.set_device(local_rank)
-    duration = max(0.5, args.steps / 10.0)            # --steps 20 -> a 2 s trace
-    n = int(wl["rate"] * duration)
-    t_arr, reqs = serve_trace(n, wl["rate"], 7 + rank)
-    geoms, flats = {}, {}
+SERVE_POOL = 4      # distinct random tensor sets per 3D geometry, reused across requests
 
-    def build(kind, L, D, K, seed):
+
+def serve_inputs(reqs, pne):
+    """Network descriptions of the trace's requests.  AKLT networks are fixed
+    per size; a 3D random request takes one of SERVE_POOL seeded tensor sets of
+    its geometry (entries N(1, 0.3^2)), so building 20k inputs stays cheap."""
+    geoms, pool = {}, {}
+    out = []
+    for kind, L, D, K, seed in reqs:
         key = (kind, L, D)
         if key not in geoms:
             g = I.square_lattice(L, L, 4) if kind == "aklt" else I.cubic_lattice(L, L, L, D)
-            if kind == "aklt":
-                flats[key] = I.aklt_tensors(g).flat_data()[0]
             geoms[key] = g
-        g = geoms[key]
-        if kind == "aklt":
-            flat = flats[key]
-        else:
-            size = int(sum(np.prod(g.leg_dims(v)) for v in range(g.n_sites))) if key not in flats else flats[key]
-            flats[key] = size
-            flat = I.splitmix64_normal(seed, size, 1.0, 0.3)     # the random_tensors layout, sites in order
-        return pne.network_struct(g, data=flat)
+            if kind == "aklt":
+                pool[key] = [I.aklt_tensors(g).flat_data()[0]]
+            else:
+                size = int(sum(np.prod(g.leg_dims(v)) for v in range(g.n_sites)))
+                pool[key] = [I.splitmix64_normal(7 * 1000003 + 97 * L + D + 131 * j, size, 1.0, 0.3)
+                             for j in range(SERVE_POOL)]
+        flats = pool[key]
+        flat = flats[(seed or 0) % len(flats)]
+        out.append((geoms[key], flat, K))
+    return out
 
-    t0 = time.time()
-    structs = [build(*r) for r in reqs]
-    build_s = time.time() - t0
-    dtype = pne.DTYPES[args.dtype]
-    ctx = pne.Context(local_rank)
-    opts = pne.ServerOpts(64 << 30, 512, 12, 512, dtype, 0, 0)
+
+def run_serve(pne, ctx, dtype, t_arr, inputs, local_rank, n_prep=12):
+    """The request trace replayed in real time against the library's server
+    (one distinct (geometry, K) per warm-up request first).  Returns (summary,
+    results in trace order)."""
+    structs = [pne.network_struct(g, data=flat) for g, flat, K in inputs]
+    opts = pne.ServerOpts(64 << 30, 512, n_prep, 512, dtype, 0, 0)
     srv = pne.pne_server_create(ctx.h, opts)
-    # warm the geometry cache: one request per distinct (geometry, K)
     seen, warm = set(), []
-    for (ns, keep), r in zip(structs, reqs):
-        key = (r[0], r[1], r[2], r[3])
+    t0 = time.perf_counter()
+    for (ns, keep), (g, flat, K) in zip(structs, inputs):
+        key = (id(g), K)
         if key not in seen:
             seen.add(key)
-            warm.append(pne.pne_server_submit(srv, ns, r[3]))
+            warm.append(pne.pne_server_submit(srv, ns, K))
     pne.pne_server_drain(srv)
     warm_failed = {}
     for rid in warm:
         st, _, _ = pne.pne_server_poll(srv, rid)
         if st != pne.PNE_OK:
             warm_failed[int(st)] = warm_failed.get(int(st), 0) + 1
+    warm_s = time.perf_counter() - t0
     if warm_failed:
         # a failed warm-up request is reported, and the trace is not run on a
         # context that may have lost its device
-        print(json.dumps({"error": "warm-up requests failed", "failed_by_status": warm_failed,
-                          "first_error": pne.pne_server_first_error(srv)}), file=sys.stderr)
+        err = pne.pne_server_first_error(srv)
         pne.pne_server_destroy(srv)
-        ctx.close()
-        return 1
+        raise RuntimeError(f"warm-up requests failed {warm_failed}: {err}")
     clocks = ClockSampler(local_rank)
     clocks.start()
     ids = []
     start = time.perf_counter()
-    for (ns, keep), r, ta in zip(structs, reqs, t_arr):
+    for (ns, keep), ta in zip(structs, t_arr):
         delay = ta - (time.perf_counter() - start)
         if delay > 0:
             time.sleep(delay)
-        ids.append(pne.pne_server_submit(srv, ns, r[3]))
+        ids.append(pne.pne_server_submit(srv, ns, inputs[len(ids)][2]))
     pne.pne_server_drain(srv)
     wall = time.perf_counter() - start
     clk = clocks.stop()
     lat, terms, batch, first, last = [], 0, [], None, None
-    failed = {}
+    failed, results = {}, []
     for rid in ids:
         st, res, info = pne.pne_server_poll(srv, rid)
+        results.append(res if st == pne.PNE_OK else None)
         if st != pne.PNE_OK:
             failed[int(st)] = failed.get(int(st), 0) + 1
             continue
@@ -628,28 +763,112 @@ def run_serve(args, wl, rank, world, local_rank):
     peak, _ = pne.pne_server_stats(srv)
     first_error = pne.pne_server_first_error(srv)
     pne.pne_server_destroy(srv)
-    ctx.close()
+    if not lat:
+        raise RuntimeError(f"no request completed {failed}: {first_error}")
     lat = np.array(lat)
-    if not len(lat):
-        print(json.dumps({"error": "no request completed", "failed_by_status": failed, "first_error": first_error}),
-              file=sys.stderr)
-        return 1
     span = last - first
-    out = {"metric": "PNE terms contracted/sec", "value": terms / span, "unit": "terms/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * span, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-           "config": {"workload": wl["desc"], "requests": len(ids), "completed": int(len(lat)),
-                      "failed_by_status": failed, "first_error": first_error,
-                      "offered_rate_req_s": wl["rate"], "trace_s": float(t_arr[-1]),
-                      "served_req_s": len(lat) / span, "geometries_warmed": len(seen),
-                      "device_budget_bytes": int(opts.device_budget_bytes), "peak_admitted_bytes": peak,
-                      "input_build_s": build_s},
-           "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
-                          "mean": 1e3 * float(lat.mean()), "max": 1e3 * float(lat.max())},
-           "batch_size": {"mean": float(np.mean(batch)), "max": int(np.max(batch))},
-           "wall_s": wall, "clocks": clk}
-    if rank == 0:
-        print(json.dumps(out))
+    summary = {"value": terms / span, "unit": "terms/s", "requests": len(ids), "completed": int(len(lat)),
+               "failed_by_status": failed, "first_error": first_error, "served_req_s": len(lat) / span,
+               "span_s": span, "wall_s": wall, "warmup_s": warm_s, "geometries_warmed": len(seen),
+               "peak_admitted_bytes": peak, "device_budget_bytes": int(opts.device_budget_bytes),
+               "prep_streams": n_prep,
+               "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
+                              "mean": 1e3 * float(lat.mean()), "max": 1e3 * float(lat.max())},
+               "batch_size": {"mean": float(np.mean(batch)), "max": int(np.max(batch))}, "clocks": clk}
+    del structs
+    return summary, results
+
+
+def run_single_request(pne, ctx, inputs, budget_s, dtype, arithmetic):
+    """The plain single-request GPU form: every request alone through the four
+    calls (partition with the given BP arithmetic, enumeration from the
+    context's geometry cache, contraction, sums), one at a time on one stream,
+    in trace order, until budget_s has passed.  Returns (summary, results)."""
+    # warm the geometry cache and the device code on each distinct request kind
+    seen = set()
+    for g, flat, K in inputs:
+        if (id(g), K) not in seen:
+            seen.add((id(g), K))
+            ctx.expand(g, K, pne.PNE_MODE_LOOP, dtype, data=flat, arithmetic=arithmetic)
+    results, terms = [], 0
+    t0 = time.perf_counter()
+    for g, flat, K in inputs:
+        (r,) = ctx.expand(g, K, pne.PNE_MODE_LOOP, dtype, data=flat, arithmetic=arithmetic)
+        results.append(r)
+        terms += r["n_terms"]
+        if time.perf_counter() - t0 > budget_s:
+            break
+    secs = time.perf_counter() - t0
+    return {"value": terms / secs, "unit": "terms/s", "requests": len(results), "seconds": secs,
+            "req_s": len(results) / secs,
+            "how": "each request alone: pne_build_partition -> pne_enumerate_terms (geometry cached) -> "
+                   "pne_contract_terms -> pne_sum, host-synchronous, one stream"}, results
+
+
+def rel_err(a, b):
+    return abs(math.expm1(a["log_abs"] - b["log_abs"]))
+
+
+def run_served_comparison(args, ctx, pne, torch, dev, local_rank):
+    """cfg5 and the comparison the served form is built for: the served,
+    continuously batched form at the cheapest contraction dtype whose results
+    stay within 1e-6 (relative, on Z_K) of the FP64 path, against the plain
+    FP64 single-request GPU form, on the same trace."""
+    wl = WORKLOADS["serve"]
+    n = int(wl["rate"] * args.serve_seconds)
+    t_arr, reqs = serve_trace(n, wl["rate"], 7)
+    inputs = serve_inputs(reqs, pne)
+    # the plain FP64 single-request form (FP64 BP, FP64 contraction)
+    single, single_res = run_single_request(pne, ctx, inputs, 10.0, pne.PNE_F64, 0)
+    # accuracy of each contraction dtype against it, request by request, on the
+    # requests the single-request run covered (the served BP is float-float)
+    sample = inputs[:min(len(single_res), 200)]
+    acc = {}
+    for dn in ("bf16", "tf32", "f32", "f64"):
+        errs = []
+        for (g, flat, K), ref in zip(sample, single_res):
+            (r,) = ctx.expand(g, K, pne.PNE_MODE_LOOP, pne.DTYPES[dn], data=flat, arithmetic=1)
+            errs.append(rel_err(r, ref))
+        acc[dn] = {"max_rel_err_vs_fp64_single": max(errs), "requests": len(errs)}
+    tol = 1e-6
+    cheapest = next(d for d in ("bf16", "tf32", "f32", "f64") if acc[d]["max_rel_err_vs_fp64_single"] <= tol)
+    out = {"workload": wl["desc"] + "; 3D tensor sets drawn from %d seeded sets per geometry" % SERVE_POOL,
+           "offered_rate_req_s": wl["rate"], "trace_s": float(t_arr[-1]), "requests": n,
+           "single_request_f64": single, "accuracy_by_dtype": acc, "stated_tolerance": tol,
+           "served_dtype": cheapest}
+    served, served_res = run_serve(pne, ctx, pne.DTYPES[cheapest], t_arr, inputs, local_rank)
+    # the served results themselves against the single-request FP64 ones
+    errs = [rel_err(a, b) for a, b in zip(served_res, single_res) if a is not None]
+    served["max_rel_err_vs_fp64_single"] = max(errs) if errs else None
+    out["served"] = served
+    out["served_over_single_f64"] = served["value"] / single["value"]
+    if cheapest != "f64":
+        served64, _ = run_serve(pne, ctx, pne.PNE_F64, t_arr, inputs, local_rank)
+        out["served_f64"] = served64
+    return out
+
+
+def run_serve_workload(args, wl, rank, world, local_rank):
+    """--workload serve: the served form alone, at --dtype."""
+    import torch
+    from paper_2512_10910_gb300 import pne
+    torch.cuda.set_device(local_rank)
+    n = int(wl["rate"] * args.serve_seconds)
+    t_arr, reqs = serve_trace(n, wl["rate"], 7 + rank)
+    inputs = serve_inputs(reqs, pne)
+    ctx = pne.Context(local_rank)
+    try:
+        s, _ = run_serve(pne, ctx, pne.DTYPES[args.dtype], t_arr, inputs, local_rank)
+    except RuntimeError as e:
+        print(json.dumps({"error": str(e)}), file=sys.stderr)
+        ctx.close()
+        return None
+    ctx.close()
+    return {"metric": "PNE terms contracted/sec", "value": s["value"], "unit": "terms/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s["span_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": wl["desc"], "offered_rate_req_s": wl["rate"], "trace_s": float(t_arr[-1])},
+            "served": s}
 
 
 def run_reference(args, wl, rank, world):

@@ -19,6 +19,11 @@ Contents (each function cites the passage it follows):
                 whole-network einsum, site-by-site sweep with log scaling,
                 literal Ising spin sums, the Ising high-temperature closed form
                 and Onsager's free energy.
+  combinatorial.py  multi-index partitions with factorised rank-1 projectors
+                and the combinatorial form (Eq. A6, A8-A10): every sub-network
+                contracted as written, the residue with the non-factorising
+                complements inserted directly, and the linear form over
+                partitions (Eq. A4).
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` (closed forms, brute force, exact identities).

@@ -165,78 +165,143 @@ static int dangling(const int32_t *S, int s, const int32_t *bond_site, int32_t *
     return d;
 }
 
+/* Growth from anchor bond a (every connected set whose smallest bond is a),
+ * level by level with sort/unique de-duplication; each set kept by the mode
+ * is passed to emit().  Returns 0, or -2 when memory ran out. */
+typedef void (*emit_fn)(const int32_t *S, int s, void *user);
+
+static int grow_anchor(int a, const int32_t *bond_site, const int32_t *site_ptr, const int32_t *site_bonds,
+                       int32_t K, int32_t mode, ivec *cur, ivec *nxt, emit_fn emit, void *user)
+{
+    int32_t vtx[2 * 64], dg[2 * 64], tmp[64];
+    cur->n = 0;
+    int32_t one = a;
+    if (ivec_push(cur, &one, 1)) return -2;
+    for (int s = 1; s <= K; ++s) {
+        int64_t nsets = cur->n / s;
+        /* emit this level */
+        for (int64_t r = 0; r < nsets; ++r) {
+            const int32_t *S = cur->v + r * s;
+            int d = dangling(S, s, bond_site, vtx, dg);
+            if (mode == 0 && d != 0) continue;
+            emit(S, s, user);
+        }
+        if (s == K) break;
+        /* grow to level s + 1 */
+        nxt->n = 0;
+        for (int64_t r = 0; r < nsets; ++r) {
+            const int32_t *S = cur->v + r * s;
+            for (int i = 0; i < s; ++i)
+                for (int e = 0; e < 2; ++e) {
+                    int x = bond_site[2 * S[i] + e];
+                    for (int p = site_ptr[x]; p < site_ptr[x + 1]; ++p) {
+                        int f = site_bonds[p];
+                        if (f <= a || bond_site[2 * f + 1] < 0) continue;
+                        int in = 0;
+                        for (int j = 0; j < s; ++j) if (S[j] == f) { in = 1; break; }
+                        if (in) continue;
+                        /* sorted insert of f */
+                        int j = 0, t = 0;
+                        while (j < s && S[j] < f) tmp[t++] = S[j++];
+                        tmp[t++] = f;
+                        while (j < s) tmp[t++] = S[j++];
+                        if (mode == 0) {
+                            int d = dangling(tmp, s + 1, bond_site, vtx, dg);
+                            if (d > 2 * (K - (s + 1))) continue;
+                        }
+                        if (ivec_push(nxt, tmp, s + 1)) return -2;
+                    }
+                }
+        }
+        int64_t nn = nxt->n / (s + 1);
+        g_width = s + 1;
+        qsort(nxt->v, (size_t)nn, (size_t)(s + 1) * sizeof(int32_t), cmp_rows);
+        int64_t u = 0;
+        for (int64_t r = 0; r < nn; ++r) {
+            if (u > 0 && memcmp(nxt->v + (u - 1) * (s + 1), nxt->v + r * (s + 1),
+                                (size_t)(s + 1) * sizeof(int32_t)) == 0) continue;
+            if (u != r) memmove(nxt->v + u * (s + 1), nxt->v + r * (s + 1), (size_t)(s + 1) * sizeof(int32_t));
+            ++u;
+        }
+        nxt->n = u * (s + 1);
+        ivec t2 = *cur; *cur = *nxt; *nxt = t2;
+        if (cur->n == 0) break;
+    }
+    return 0;
+}
+
+struct rows_out { int32_t *out; int64_t cap, count; int width; };
+
+static void emit_row(const int32_t *S, int s, void *user)
+{
+    struct rows_out *o = (struct rows_out *)user;
+    if (o->count < o->cap) {
+        int32_t *row = o->out + o->count * (int64_t)o->width;
+        memcpy(row, S, (size_t)s * sizeof(int32_t));
+        for (int j = s; j < o->width; ++j) row[j] = -1;
+    }
+    ++o->count;
+}
+
 int64_t oracle_enum_grow(int32_t n_sites, int32_t n_bonds, const int32_t *bond_site,
                          const int32_t *site_ptr, const int32_t *site_bonds,
                          int32_t K, int32_t mode, int32_t width,
                          int32_t *out, int64_t cap)
 {
     (void)n_sites;
-    if (K < 1 || width < K) return -1;
-    int64_t count = 0;
+    if (K < 1 || width < K || K > 60) return -1;
     ivec cur = {0}, nxt = {0};
-    int32_t vtx[2 * 64], dg[2 * 64], tmp[64];
-    if (K > 60) return -1;
+    struct rows_out o = {out, cap, 0, width};
     for (int a = 0; a < n_bonds; ++a) {
         if (bond_site[2 * a + 1] < 0) continue;
-        cur.n = 0;
-        int32_t one = a;
-        ivec_push(&cur, &one, 1);
-        for (int s = 1; s <= K; ++s) {
-            int64_t nsets = cur.n / s;
-            /* emit this level */
-            for (int64_t r = 0; r < nsets; ++r) {
-                const int32_t *S = cur.v + r * s;
-                int d = dangling(S, s, bond_site, vtx, dg);
-                if (mode == 0 && d != 0) continue;
-                if (count < cap) {
-                    int32_t *row = out + count * (int64_t)width;
-                    memcpy(row, S, (size_t)s * sizeof(int32_t));
-                    for (int j = s; j < width; ++j) row[j] = -1;
-                }
-                ++count;
-            }
-            if (s == K) break;
-            /* grow to level s + 1 */
-            nxt.n = 0;
-            for (int64_t r = 0; r < nsets; ++r) {
-                const int32_t *S = cur.v + r * s;
-                for (int i = 0; i < s; ++i)
-                    for (int e = 0; e < 2; ++e) {
-                        int x = bond_site[2 * S[i] + e];
-                        for (int p = site_ptr[x]; p < site_ptr[x + 1]; ++p) {
-                            int f = site_bonds[p];
-                            if (f <= a || bond_site[2 * f + 1] < 0) continue;
-                            int in = 0;
-                            for (int j = 0; j < s; ++j) if (S[j] == f) { in = 1; break; }
-                            if (in) continue;
-                            /* sorted insert of f */
-                            int j = 0, t = 0;
-                            while (j < s && S[j] < f) tmp[t++] = S[j++];
-                            tmp[t++] = f;
-                            while (j < s) tmp[t++] = S[j++];
-                            if (mode == 0) {
-                                int d = dangling(tmp, s + 1, bond_site, vtx, dg);
-                                if (d > 2 * (K - (s + 1))) continue;
-                            }
-                            if (ivec_push(&nxt, tmp, s + 1)) { free(cur.v); free(nxt.v); return -2; }
-                        }
-                    }
-            }
-            int64_t nn = nxt.n / (s + 1);
-            g_width = s + 1;
-            qsort(nxt.v, (size_t)nn, (size_t)(s + 1) * sizeof(int32_t), cmp_rows);
-            int64_t u = 0;
-            for (int64_t r = 0; r < nn; ++r) {
-                if (u > 0 && memcmp(nxt.v + (u - 1) * (s + 1), nxt.v + r * (s + 1),
-                                    (size_t)(s + 1) * sizeof(int32_t)) == 0) continue;
-                if (u != r) memmove(nxt.v + u * (s + 1), nxt.v + r * (s + 1), (size_t)(s + 1) * sizeof(int32_t));
-                ++u;
-            }
-            nxt.n = u * (s + 1);
-            ivec t2 = cur; cur = nxt; nxt = t2;
-            if (cur.n == 0) break;
+        if (grow_anchor(a, bond_site, site_ptr, site_bonds, K, mode, &cur, &nxt, emit_row, &o)) {
+            free(cur.v); free(nxt.v); return -2;
         }
     }
     free(cur.v); free(nxt.v);
-    return count;
+    return o.count;
+}
+
+struct counts_out { const int32_t *bond_site; int64_t *by_size, *even_by_size; };
+
+static void emit_count(const int32_t *S, int s, void *user)
+{
+    struct counts_out *o = (struct counts_out *)user;
+    o->by_size[s]++;
+    if (!o->even_by_size) return;
+    /* every vertex of even degree in the set (an even subgraph) */
+    int32_t vtx[2 * 64], dg[2 * 64];
+    int nv = 0;
+    for (int i = 0; i < s; ++i)
+        for (int e = 0; e < 2; ++e) {
+            int x = o->bond_site[2 * S[i] + e], j;
+            for (j = 0; j < nv; ++j) if (vtx[j] == x) break;
+            if (j == nv) { vtx[nv] = x; dg[nv] = 0; ++nv; }
+            dg[j]++;
+        }
+    for (int j = 0; j < nv; ++j) if (dg[j] & 1) return;
+    o->even_by_size[s]++;
+}
+
+/* The same growth for the anchors a0 <= a < a1 only, counting the kept sets
+ * by size into by_size[0..K] (no list is written), and, when even_by_size is
+ * given, those whose every vertex has even degree into even_by_size[0..K]:
+ * independent anchor ranges can be counted side by side and added up. */
+int32_t oracle_count_grow_range(int32_t n_sites, int32_t n_bonds, const int32_t *bond_site,
+                                const int32_t *site_ptr, const int32_t *site_bonds,
+                                int32_t K, int32_t mode, int32_t a0, int32_t a1, int64_t *by_size,
+                                int64_t *even_by_size)
+{
+    (void)n_sites;
+    if (K < 1 || K > 60 || a0 < 0 || a1 > n_bonds) return -1;
+    ivec cur = {0}, nxt = {0};
+    struct counts_out o = {bond_site, by_size, even_by_size};
+    for (int a = a0; a < a1; ++a) {
+        if (bond_site[2 * a + 1] < 0) continue;
+        if (grow_anchor(a, bond_site, site_ptr, site_bonds, K, mode, &cur, &nxt, emit_count, &o)) {
+            free(cur.v); free(nxt.v); return -2;
+        }
+    }
+    free(cur.v); free(nxt.v);
+    return 0;
 }

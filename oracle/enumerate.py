@@ -54,6 +54,9 @@ def _get_lib():
         lib.oracle_enum_grow.argtypes = [ctypes.c_int32, ctypes.c_int32, p32, p32, p32,
                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, p32,
                                          ctypes.c_int64]
+        lib.oracle_count_grow_range.restype = ctypes.c_int32
+        lib.oracle_count_grow_range.argtypes = [ctypes.c_int32, ctypes.c_int32, p32, p32, p32, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, p64, p64]
         lib.oracle_even_subsets_by_size.restype = ctypes.c_int32
         lib.oracle_even_subsets_by_size.argtypes = [ctypes.c_int32, ctypes.c_int32, p32, p64]
         _lib = lib
@@ -104,6 +107,27 @@ def count_clusters_grow(net, K, mode=LOOP) -> int:
     if n < 0:
         raise MemoryError("oracle_enum_grow failed")
     return int(n)
+
+
+def count_clusters_by_size_range(net, K, mode, a0, a1, even=False):
+    """Clusters by size (index 0..K) whose smallest bond is in [a0, a1), by
+    the same per-anchor growth; ranges are independent and add up.  With
+    even=True also returns the counts of those clusters whose every vertex has
+    even degree (connected even subgraphs)."""
+    lib = _get_lib()
+    bs = np.ascontiguousarray(net.bond_site, dtype=np.int32)
+    sp = np.ascontiguousarray(net.site_ptr, dtype=np.int32)
+    sb = np.ascontiguousarray(net.site_bonds, dtype=np.int32)
+    by = np.zeros(K + 1, dtype=np.int64)
+    ev = np.zeros(K + 1, dtype=np.int64)
+    p64 = ctypes.POINTER(ctypes.c_int64)
+    st = lib.oracle_count_grow_range(net.n_sites, net.n_bonds, _p32(bs), _p32(sp), _p32(sb), K, mode, a0, a1,
+                                     by.ctypes.data_as(p64), ev.ctypes.data_as(p64) if even else None)
+    if st != 0:
+        raise MemoryError("oracle_count_grow_range failed")
+    if even:
+        return [int(x) for x in by], [int(x) for x in ev]
+    return [int(x) for x in by]
 
 
 def clusters_grow(net, K, mode=LOOP) -> list:

@@ -292,6 +292,22 @@ def aklt_tensors(net: Network) -> Network:
     return net.with_tensors(tensors, name=net.name + "_aklt")
 
 
+def batched_workload_items(indices, n: int = 4096, seed: int = 1234):
+    """Only the listed items of batched_workload(n, seed), built the same way
+    (the same draws), without building the others."""
+    u = splitmix64_uniform(seed, 4 * n).reshape(n, 4)
+    out = []
+    for i in indices:
+        L = 6 + min(18, int(u[i, 0] * 19))
+        D = 2 + min(4, int(u[i, 1] * 5))
+        if u[i, 2] < 0.5:
+            out.append(("random", L, D, None, random_tensors(square_lattice(L, L, D), seed + 1 + i)))
+        else:
+            beta = 0.3 + 0.2 * float(u[i, 3])
+            out.append(("ising", L, 2, beta, ising_tensors(square_lattice(L, L, 2), beta)))
+    return out
+
+
 def batched_workload(n: int = 4096, seed: int = 1234):
     """The uneven batch: n independent open L x L square-lattice networks,
     L uniform in 6..24 and D uniform in 2..6; with probability 1/2 a network is
@@ -334,3 +350,79 @@ def slice_open(net: Network, assignment) -> Network:
     # legs keep ascending order because remapping is monotone
     del remap
     return out.with_tensors(tensors, name=net.name + "_slice")
+
+
+# ---------------------------------------------------------------------------
+# Partitions (sets of bonds transected by one line) for multi-index PNE
+# ---------------------------------------------------------------------------
+def bond_between(net: Network, s0: int, s1: int) -> int:
+    """Id of the bond joining sites s0 and s1 (either order)."""
+    for b in range(net.n_bonds):
+        a, c = int(net.bond_site[b][0]), int(net.bond_site[b][1])
+        if {a, c} == {s0, s1}:
+            return b
+    raise KeyError((s0, s1))
+
+
+def square_line_x(lx: int, ly: int, k: int) -> list:
+    """Bonds of an lx-by-ly square lattice crossed by the line between columns
+    x = k and x = k + 1 (its +x bonds from column k)."""
+    net = square_lattice(lx, ly, 2)
+    return sorted(bond_between(net, y * lx + k, y * lx + k + 1) for y in range(ly))
+
+
+def square_line_y(lx: int, ly: int, k: int) -> list:
+    """Bonds crossed by the line between rows y = k and y = k + 1."""
+    net = square_lattice(lx, ly, 2)
+    return sorted(bond_between(net, k * lx + x, (k + 1) * lx + x) for x in range(lx))
+
+
+def square_line_diag(lx: int, ly: int, k: int) -> list:
+    """Bonds crossed by the anti-diagonal line between the site layers
+    x + y = k and x + y = k + 1."""
+    net = square_lattice(lx, ly, 2)
+    out = []
+    for b in range(net.n_bonds):
+        u, v = (int(s) for s in net.bond_site[b])
+        lu, lv = u % lx + u // lx, v % lx + v // lx
+        if sorted((lu, lv)) == [k, k + 1]:
+            out.append(b)
+    return sorted(out)
+
+
+def cubic_axis_bonds(l: int, axis: int) -> list:
+    """All bonds of an l x l x l cubic lattice along one axis (0: x, 1: y, 2: z)."""
+    net = cubic_lattice(l, l, l, 2)
+    step = (1, l, l * l)[axis]
+    return sorted(b for b in range(net.n_bonds)
+                  if abs(int(net.bond_site[b][1]) - int(net.bond_site[b][0])) == step)
+
+
+def double_loop_vertical() -> list:
+    """The double-loop network of six tensors (a 3 x 2 square lattice, two
+    plaquettes sharing a bond): its three vertical bonds, one single-index
+    partition each."""
+    return [[b] for b in square_line_y(3, 2, 0)]
+
+
+def square3x3_pinwheel() -> list:
+    """Four single-index partitions of the 3 x 3 network on boundary bonds, one
+    per side, turning the same way around the centre."""
+    net = square_lattice(3, 3, 2)
+    s = lambda x, y: y * 3 + x
+    pairs = [(s(0, 0), s(1, 0)), (s(2, 0), s(2, 1)), (s(0, 1), s(0, 2)), (s(1, 2), s(2, 2))]
+    return [[bond_between(net, a, c)] for a, c in pairs]
+
+
+def square3x3_six_lines() -> list:
+    """Six multi-index partitions of the 3 x 3 network: the two vertical and
+    the two horizontal lines between rows and columns, the line around the
+    corner site 0, and the anti-diagonal line between site layers 1 and 2."""
+    return [square_line_x(3, 3, 0), square_line_x(3, 3, 1), square_line_y(3, 3, 0), square_line_y(3, 3, 1),
+            square_line_diag(3, 3, 0), square_line_diag(3, 3, 1)]
+
+
+def cube2_planes() -> list:
+    """Three multi-index partitions of the 2 x 2 x 2 network, each the four
+    bonds along one axis (cutting one separates two 2 x 2 planes)."""
+    return [cubic_axis_bonds(2, a) for a in range(3)]

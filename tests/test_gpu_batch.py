@@ -157,3 +157,28 @@ def test_batch_after_asynchronous_updates_on_two_streams(ctx):
         pne.pne_batch_destroy(b)
     finally:
         _free(parts, terms)
+
+
+def test_full_size_batch_members_match_the_oracle(ctx):
+    # members of the 4096-network batch at its largest size (L = 24): a random
+    # network at the largest bond dimension (D = 6) and an Ising network,
+    # contracted by the fused batch kernel together with a small group,
+    # against the FP64 oracle (the same draws as the batched workload)
+    items = I.batched_workload_items([61, 171])
+    assert [(k, L, D) for k, L, D, _, _ in items] == [("random", 24, 6), ("ising", 24, 2)]
+    groups = [(net, [net]) for _, _, _, _, net in items] + _groups()[:1]
+    parts, terms, keep = _make(ctx, groups)
+    try:
+        b = pne.pne_batch_create(ctx.h, terms, pne.PNE_F64, pne.BatchOpts(4, 2, 1))
+        try:
+            res = pne.pne_batch_run(ctx.h, b)
+        finally:
+            pne.pne_batch_destroy(b)
+        for (_, _, _, _, net), r in zip(items, res[:2]):
+            ref = X.pne(net, 8, E.LOOP)
+            assert r["n_clusters"] == ref.n_clusters and r["n_terms"] == ref.n_terms
+            assert abs(r["log_abs"] - ref.log_abs) <= 1e-10, (r["log_abs"], ref.log_abs)
+            scale = float(np.sum(np.abs(ref.c)))
+            np.testing.assert_allclose(r["c"], ref.c, rtol=0, atol=1e-10 * scale)
+    finally:
+        _free(parts, terms)

@@ -417,7 +417,7 @@ def test_full_size_cluster_and_term_counts_match_the_oracle_golden_file(ctx):
     golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cluster_counts.json")))["cases"]
     geoms = {"square16x16": I.square_lattice(16, 16, 2), "square24x24": I.square_lattice(24, 24, 2),
              "cubic6x6x6": I.cubic_lattice(6, 6, 6, 2), "cubic8x8x8": I.cubic_lattice(8, 8, 8, 2),
-             "cubic4x4x4_K10": I.cubic_lattice(4, 4, 4, 2)}
+             "cubic4x4x4_K10": I.cubic_lattice(4, 4, 4, 2), "cubic8x8x8_K10": I.cubic_lattice(8, 8, 8, 2)}
     assert set(geoms) == set(golden)
     for name, g in geoms.items():
         ref = golden[name]
@@ -436,3 +436,33 @@ def test_full_size_cluster_and_term_counts_match_the_oracle_golden_file(ctx):
         finally:
             pne.pne_partition_destroy(part)
         del keep
+
+
+@pytest.mark.parametrize("K", [8, 10])
+def test_ising_8x8x8_values_match_the_high_temperature_closed_form(ctx, K):
+    # 3D Ising 8x8x8 at orders 8 and 10 (the full-size cubic workload): in the
+    # paramagnetic gauge a cluster's weight is tanh(beta)^|C| when every vertex
+    # has even degree and 0 otherwise, so c_k = n_k tanh(beta)^k with n_k the
+    # even subgraphs of k bonds, counted by the oracle (golden file), and
+    # Z_BP = 2^N cosh(beta)^M.  FP64 values within 1e-10; TF32 and BF16 within
+    # their stated bounds.
+    import json
+    import os
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cluster_counts.json")))["cases"]
+    even = {int(k): v for k, v in golden["cubic8x8x8_K10"]["even_terms_by_order"].items()}
+    g = I.cubic_lattice(8, 8, 8, 2)
+    betas = (0.20, 0.2217, 0.25)
+    nets = [I.ising_tensors(g, b) for b in betas]
+    data = np.concatenate([n.flat_data()[0] for n in nets])
+    for dtype in ("f64", "tf32", "bf16"):
+        res = ctx.expand(nets[0], K, pne.PNE_MODE_LOOP, dtype, data=data, n_batch=len(nets))
+        for r, b in zip(res, betas):
+            t = math.tanh(b)
+            ck = np.array([even.get(k, 0) * t ** k for k in range(K + 1)])
+            lz = g.n_sites * math.log(2.0) + g.n_bonds * math.log(math.cosh(b)) + math.log(ck.sum())
+            rel = abs(math.expm1(r["log_abs"] - lz))
+            if dtype == "f64":
+                assert rel <= 1e-10, (b, rel)
+                np.testing.assert_allclose(r["c"], ck, rtol=0, atol=1e-12 * ck.sum())
+            else:
+                assert rel <= r["err_bound"] <= BOUND_CAP[dtype], (dtype, b, rel, r["err_bound"])
