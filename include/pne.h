@@ -66,8 +66,10 @@ typedef enum {
 typedef enum { PNE_F64 = 0, PNE_F32 = 1, PNE_TF32 = 2, PNE_BF16 = 3 } pne_dtype;
 /* LOOP: clusters with a site of cluster-degree one ("dangling excitation",
  *       Sec. III.A) are dropped -- they vanish at a BP fixed point.
- * ALL:  every bond subset is a term (networks with <= 30 closed bonds). */
-typedef enum { PNE_MODE_LOOP = 0, PNE_MODE_ALL = 1 } pne_mode;
+ * ALL:  every bond subset is a term (networks with <= 30 closed bonds).
+ * COMB: the combinatorial form over multi-index partitions (handles made by
+ *       pne_enumerate_combinatorial only). */
+typedef enum { PNE_MODE_LOOP = 0, PNE_MODE_ALL = 1, PNE_MODE_COMB = 2 } pne_mode;
 
 /* Library limits (checked; violations return PNE_EINVAL). */
 #define PNE_MAX_DEG 6        /* legs per site                                */
@@ -199,6 +201,30 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part,
                                pne_terms **out, uint64_t *n_clusters, uint64_t *n_terms);
 void pne_terms_destroy(pne_terms *t);
 
+/* The combinatorial form of the expansion over multi-index partitions
+ * (Sec. II.A Eq. A6; Sec. II.C Eq. A8-A10).  Partition p transects the bonds
+ * partition_bonds[partition_ptr[p] .. partition_ptr[p+1]) (ids of the network
+ * as given; closed bonds only; two partitions may share a bond), and its
+ * projector is the product of the rank-1 BP projectors of those bonds (Eq.
+ * A10, from `part`).  The terms are the 2^M - 1 sub-networks Z(P^x), x a
+ * non-empty set of partitions: every bond of an active partition cut and
+ * capped by the messages, every other bond kept at its full dimension.  A
+ * sub-network factorises into the connected components of its kept bonds
+ * (sites with no kept bond contribute their capped value z_v); the handle
+ * lists the distinct components as its clusters, pne_contract_terms contracts
+ * each exactly, and pne_sum forms every sub-network as the product of its
+ * components and sums them by |x|:
+ *   c_k = sum_{|x| = k} Z(P^x) / Z_ref  (k = 1..M, c_0 = 0),
+ *   Z   = Z_ref sum_{k=1..M} (-1)^{k+1} c_k,
+ * the residue Z(Q_1, ..., Q_M) neglected (log_series is NaN).  Limits: M <=
+ * 20; every component of at most 32 bonds and 32 sites; bond dimensions <= 7
+ * (PNE_EINVAL otherwise).  A component whose contraction needs a running
+ * tensor above the kernels' limit makes pne_sum return PNE_EOVERFLOW.
+ * Synchronises `stream`.  n_components / n_terms may be NULL. */
+pne_status pne_enumerate_combinatorial(pne_ctx *ctx, const pne_partition *part, int32_t n_partitions,
+                                       const int32_t *partition_ptr, const int32_t *partition_bonds, void *stream,
+                                       pne_terms **out, uint64_t *n_components, uint64_t *n_terms);
+
 /* Contract every cluster of every tensor set in `dtype` (Sec. II.C: with P
  * bonds cut and capped, a term factorises into the capped sites and one
  * local contraction per connected excited cluster; Sec. III.A: that
@@ -241,12 +267,14 @@ pne_status pne_open_tensor_assemble(const pne_result *res, int64_t n_sets, int64
                                     double *log_scale);
 
 /* Copy the cluster list and the contracted cluster values to host memory, for
- * inspection and element-by-element checks.  LOOP mode only.
+ * inspection and element-by-element checks.  LOOP and COMB modes.
  *   edges  [n_clusters][max_order] int32: each cluster's bond ids (ids of the
  *          network as given), ascending, padded with -1; may be NULL.
  *   w      [pne_terms_n_results][n_clusters] double: w(C) per tensor set and
  *          open-index assignment (needs pne_contract_terms first); may be NULL.
- * Clusters are listed grouped by size.  Synchronises `stream`. */
+ * Clusters are listed grouped by size.  For a combinatorial handle (COMB
+ * mode) the clusters are its components and each row of `edges` holds
+ * PNE_MAX_ORDER entries instead of max_order.  Synchronises `stream`. */
 pne_status pne_terms_export(pne_ctx *ctx, const pne_terms *t, void *stream, int32_t *edges, double *w);
 
 /* Re-run the partition of an existing handle on new tensors of the same

@@ -1580,6 +1580,16 @@ pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t 
     return PNE_OK;
 }
 
+pne_status convert_buffer(pne_ctx *ctx, const double *src, int64_t n, int dtype, void *dst, cudaStream_t s)
+{
+    if (dtype == PNE_BF16)
+        convert_kernel<<<grid_for(n, 256, ctx->n_sm), 256, 0, s>>>(src, n, dtype, nullptr, (__nv_bfloat16 *)dst);
+    else
+        convert_kernel<<<grid_for(n, 256, ctx->n_sm), 256, 0, s>>>(src, n, dtype, (float *)dst, nullptr);
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    return PNE_OK;
+}
+
 // conversion only, into buffers that already exist (safe inside stream capture)
 pne_status launch_convert_only(pne_ctx *ctx, const pne_partition *p, int dtype, cudaStream_t s)
 {

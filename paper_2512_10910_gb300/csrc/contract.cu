@@ -447,8 +447,8 @@ struct SumParams {
     const double *w;
     const int32_t *nzc;
     const double *vac;        // [members][3]
-    const int32_t *lvl_idx[8];
-    int lvl_m[8];
+    const int32_t *lvl_idx[16];
+    int lvl_m[16];
     double *partial;          // [members][n_desc][2]
 };
 
@@ -1389,11 +1389,104 @@ pne_status launch_plan_work(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, ui
     return PNE_OK;
 }
 
+namespace {
+
+// Full-range blocks of the virtual geometry (bond dimensions d + 1) from the
+// gauged blocked tensors: the block of leg set S holds T'_v / z_v with every
+// leg outside S at 0 and every leg in S over its full range 0..d-1 (row-major,
+// last leg fastest); each entry is the gauged entry of the same indices, which
+// the blocked layout keeps in the block of its nonzero legs.  One warp per
+// (member, site); index arithmetic only.
+__global__ void comb_fill_kernel(const double *Mb, const int64_t *tens_off, const int32_t *blk_off, int64_t stride,
+                                 const int64_t *vtens_off, const int32_t *vblk_off, int64_t vstride,
+                                 const int32_t *site_ptr, const int32_t *site_bonds, const int32_t *bond_dim,
+                                 int n_sites, int n_members, double *Mf)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t items = (int64_t)n_members * n_sites;
+    for (int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < items;
+         item += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t member = item / n_sites;
+        const int v = (int)(item % n_sites);
+        const int l0 = site_ptr[v], k = site_ptr[v + 1] - l0;
+        int d[kMaxDeg];
+        for (int i = 0; i < k; ++i) d[i] = bond_dim[site_bonds[l0 + i]];
+        const double *src = Mb + member * stride + tens_off[v];
+        const int32_t *boff = blk_off + (int64_t)v * kBlkStride;
+        const int32_t *vboff = vblk_off + (int64_t)v * kBlkStride;
+        double *dst = Mf + member * vstride + vtens_off[v];
+        for (int S = 0; S < (1 << k); ++S) {
+            int n = 1;
+            for (int i = 0; i < k; ++i) if (S >> i & 1) n *= d[i];
+            for (int e = lane; e < n; e += 32) {
+                int r = e, mask = 0, pos = 0, mul = 1;
+                for (int i = k - 1; i >= 0; --i) {
+                    if (!(S >> i & 1)) continue;
+                    const int dgt = r % d[i];
+                    r /= d[i];
+                    if (dgt > 0) { mask |= 1 << i; pos += (dgt - 1) * mul; mul *= d[i] - 1; }
+                }
+                dst[vboff[S] + e] = src[boff[mask] + pos];
+            }
+        }
+    }
+}
+
+}  // namespace
+
 pne_status launch_contract(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s)
 {
     const pne_partition *p = t->part;
     EnumRecord &rec = *t->rec;
     if (rec.n_clusters == 0) return PNE_OK;
+    if (rec.comb) {
+        // the combinatorial form: components contracted over the full range of
+        // their bonds through the virtual geometry's blocks
+        const Geometry &c = p->geo->closed, &vg = rec.vgeo;
+        const int64_t vstride = vg.tens_off[vg.n_sites];
+        const int64_t nf = (int64_t)p->n_members * vstride;
+        pne_status st;
+        if (!t->Mf.ptr && (st = dev_alloc(ctx, t->Mf, nf * 8, s))) return st;
+        {
+            ProfScope ps__(ctx, s, "comb_fill");
+            const int64_t warps = (int64_t)p->n_members * c.n_sites;
+            comb_fill_kernel<<<grid_for(warps * 32, 256, ctx->n_sm), 256, 0, s>>>(
+                (const double *)p->Mb.ptr, c.d_tens_off, c.d_blk_off, c.tens_off[c.n_sites], vg.d_tens_off, vg.d_blk_off,
+                vstride, c.d_site_ptr, c.d_site_bonds, c.d_bond_dim, c.n_sites, p->n_members, (double *)t->Mf.ptr);
+        }
+        PNE_LAUNCH_CHECK(ctx);
+        const void *M = t->Mf.ptr;
+        if (dtype == PNE_BF16) {
+            if (!t->Mf16.ptr && (st = dev_alloc(ctx, t->Mf16, nf * 2, s))) return st;
+            if ((st = convert_buffer(ctx, (const double *)t->Mf.ptr, nf, dtype, t->Mf16.ptr, s))) return st;
+            M = t->Mf16.ptr;
+        } else if (dtype != PNE_F64) {
+            if (!t->Mf32.ptr && (st = dev_alloc(ctx, t->Mf32, nf * 4, s))) return st;
+            if ((st = convert_buffer(ctx, (const double *)t->Mf.ptr, nf, dtype, t->Mf32.ptr, s))) return st;
+            M = t->Mf32.ptr;
+        }
+        ContractParams cp;
+        cp.n_clusters = (int64_t)rec.n_clusters; cp.n_members = p->n_members; cp.n_sites = c.n_sites;
+        cp.width = rec.width; cp.vwidth = rec.vwidth;
+        cp.cl_edges = (const int32_t *)rec.cl_edges.ptr; cp.cl_verts = (const int32_t *)rec.cl_verts.ptr;
+        cp.cl_size = (const int32_t *)rec.cl_size.ptr;
+        cp.bond_site = vg.d_bond_site; cp.bond_dim = vg.d_bond_dim; cp.bond_leg = vg.d_bond_leg;
+        cp.blk_off = vg.d_blk_off; cp.tens_off = vg.d_tens_off; cp.stride = vstride;
+        cp.scale = (const double *)p->site_scale.ptr; cp.zero = (const int8_t *)p->site_zero.ptr;
+        cp.w = (double *)t->w.ptr; cp.nzc = (int32_t *)t->nzc.ptr; cp.status = (int32_t *)t->status.ptr;
+        cp.M = M;
+        ProfScope ps__(ctx, s, "contract");
+        if (rec.shaped) {
+            if (dtype == PNE_F64) return dispatch_shaped<double, Load<double>, 0>(ctx, cp, rec, s);
+            if (dtype == PNE_BF16) return dispatch_shaped<float, LoadBF16, 2>(ctx, cp, rec, s);
+            if (dtype == PNE_TF32) return dispatch_shaped<float, Load<float>, 1>(ctx, cp, rec, s);
+            return dispatch_shaped<float, Load<float>, 0>(ctx, cp, rec, s);
+        }
+        if (dtype == PNE_F64) return run_general(ctx, contract_general_kernel<double, Load<double>, 0>, cp, 8, s);
+        if (dtype == PNE_BF16) return run_general(ctx, contract_general_kernel<float, LoadBF16, 2>, cp, 4, s);
+        if (dtype == PNE_TF32) return run_general(ctx, contract_general_kernel<float, Load<float>, 1>, cp, 4, s);
+        return run_general(ctx, contract_general_kernel<float, Load<float>, 0>, cp, 4, s);
+    }
     pne_status st = launch_convert(ctx, const_cast<pne_partition *>(p), dtype, s);
     if (st) return st;
     ContractParams cp;
@@ -1453,7 +1546,7 @@ pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, std::ve
     for (int k = 1; k <= K; ++k)
         for (int64_t b0 = rec.size_start[k]; b0 < rec.size_start[k + 1]; b0 += kSumChunk)
             desc.push_back({0, k, b0, std::min<int64_t>(b0 + kSumChunk, rec.size_start[k + 1])});
-    if (rec.levels.size() > 8) { set_error(ctx, PNE_EOVERFLOW, "too many tuple levels"); return PNE_EOVERFLOW; }
+    if (rec.levels.size() > 16) { set_error(ctx, PNE_EOVERFLOW, "too many tuple levels"); return PNE_EOVERFLOW; }
     for (size_t l = 0; l < rec.levels.size(); ++l)
         for (int k = 0; k <= K; ++k)
             for (int64_t b0 = rec.levels[l].order_start[k]; b0 < rec.levels[l].order_start[k + 1]; b0 += kSumChunk)
@@ -1471,7 +1564,7 @@ pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, std::ve
         sp.n_clusters = (int64_t)rec.n_clusters;
         sp.w = (const double *)t->w.ptr; sp.nzc = (const int32_t *)t->nzc.ptr;
         sp.vac = (const double *)p->vac.ptr;
-        for (int l = 0; l < 8; ++l) { sp.lvl_idx[l] = nullptr; sp.lvl_m[l] = 0; }
+        for (int l = 0; l < 16; ++l) { sp.lvl_idx[l] = nullptr; sp.lvl_m[l] = 0; }
         for (size_t l = 0; l < rec.levels.size(); ++l) {
             sp.lvl_idx[l] = (const int32_t *)rec.levels[l].idx.ptr;
             sp.lvl_m[l] = rec.levels[l].m;

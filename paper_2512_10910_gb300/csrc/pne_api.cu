@@ -12,7 +12,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <limits>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -296,6 +298,7 @@ EnumRecord::~EnumRecord()
     dev_free(ctx, op_off, rs);
     dev_free(ctx, step_off, rs);
     dev_free(ctx, step_site, rs);
+    dev_free(ctx, vgeo.storage, rs);
 }
 
 namespace {
@@ -306,6 +309,8 @@ uint64_t fnv(uint64_t h, const void *p, size_t n)
     for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
     return h;
 }
+
+}  // namespace
 
 // Derived tables of a geometry given bond_site, bond_dim, site_ptr, site_bonds.
 pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
@@ -427,6 +432,8 @@ pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
     return upload(ctx, g.storage.ptr, host.data(), bytes, s);
 }
 
+namespace {
+
 pne_status validate(pne_ctx *ctx, const pne_network *n)
 {
     auto bad = [&](const std::string &m) { set_error(ctx, PNE_EINVAL, m); return PNE_EINVAL; };
@@ -522,6 +529,46 @@ void finalize_result(pne_result &r, int K, int mode, int dtype, const double *c,
     const double cl_abs = std::max(0.0, asum - exact);
     const int n64 = K + 2 + (int)std::ceil(std::log2((double)std::max<uint64_t>(n_terms, 2)));
     r.err_bound = (sum != 0.0) ? (gamma_n(nops, u) * cl_abs + gamma_n(n64, 0x1p-53) * asum) / std::fabs(sum)
+                               : std::numeric_limits<double>::infinity();
+    r.n_terms = n_terms;
+    r.n_clusters = n_clusters;
+    r.bp_iters = bp_iters;
+    r.bp_residual = bp_residual;
+}
+
+// The combinatorial form's result (Eq. A6 without the residue): the sub-network
+// sums c_k (k = |x|) enter with the sign (-1)^{k+1}.  Every sub-network is an
+// exact contraction of at most all N sites, so a product path rounds at most
+// 2 N times in the working dtype.
+void finalize_comb_result(pne_result &r, int M, int dtype, const double *c, const double *abs_c, const double *vac,
+                          uint64_t n_terms, uint64_t n_clusters, int n_sites, int bp_iters, double bp_residual)
+{
+    static const double unit[4] = {0x1p-53, 0x1p-24, 0x1p-11, 0x1p-8};
+    const double u = unit[dtype < 0 ? 0 : dtype];
+    std::memset(&r, 0, sizeof r);
+    const double lz = vac[0], sz = vac[1];
+    r.n_orders = M + 1;
+    double sum = 0.0, comp = 0.0, asum = 0.0;            // Neumaier over |x|
+    for (int k = 0; k <= M; ++k) {
+        r.c[k] = c[k];
+        r.abs_c[k] = abs_c[k];
+        const double x = (k % 2 == 1) ? c[k] : -c[k], tt = sum + x;
+        if (k == 0) continue;
+        comp += (std::fabs(sum) >= std::fabs(x)) ? (sum - tt) + x : (x - tt) + sum;
+        sum = tt;
+        asum += abs_c[k];
+    }
+    sum += comp;
+    r.log_abs_zref = lz;
+    r.sign_zref = sz < 0 ? -1 : 1;
+    r.n_zero_sites = (int)vac[2];
+    r.sign = (sum < 0 ? -1 : 1) * r.sign_zref;
+    r.log_abs = (sum != 0.0) ? lz + std::log(std::fabs(sum)) : -std::numeric_limits<double>::infinity();
+    r.value = (sum == 0.0) ? 0.0 : (r.log_abs > 709.7 ? r.sign * std::numeric_limits<double>::infinity()
+                                                       : r.sign * std::exp(r.log_abs));
+    r.log_series = std::numeric_limits<double>::quiet_NaN();
+    const int n64 = M + 2 + (int)std::ceil(std::log2((double)std::max<uint64_t>(n_terms, 2)));
+    r.err_bound = (sum != 0.0) ? (gamma_n(2 * n_sites, u) + gamma_n(n64, 0x1p-53)) * asum / std::fabs(sum)
                                : std::numeric_limits<double>::infinity();
     r.n_terms = n_terms;
     r.n_clusters = n_clusters;
@@ -1089,6 +1136,186 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
     return PNE_OK;
 }
 
+pne_status pne_enumerate_combinatorial(pne_ctx *ctx, const pne_partition *part, int32_t n_partitions,
+                                       const int32_t *partition_ptr, const int32_t *partition_bonds, void *stream,
+                                       pne_terms **out, uint64_t *n_components, uint64_t *n_terms)
+{
+    HostScope hs__(ctx, "enumerate_comb");
+    if (!ctx || !part || !out || !partition_ptr || !partition_bonds) return PNE_EINVAL;
+    *out = nullptr;
+    auto bad = [&](const std::string &m) { set_error(ctx, PNE_EINVAL, m); return PNE_EINVAL; };
+    const int M = n_partitions;
+    if (M < 1 || M > 20) return bad("the combinatorial form takes 1..20 partitions");
+    cudaStream_t s = (cudaStream_t)stream;
+    const GeomPair &gp = *part->geo;
+    const Geometry &g = gp.closed;
+    const int N = g.n_sites, B = g.n_bonds;
+    for (int b = 0; b < B; ++b)
+        if (g.bond_dim[b] > kMaxDim - 1) return bad("the combinatorial form needs bond dimensions <= 7");
+    // each partition as closed bond ids
+    if (partition_ptr[0] != 0) return bad("partition_ptr[0] must be 0");
+    std::vector<std::vector<int>> parts(M);
+    for (int p = 0; p < M; ++p) {
+        if (partition_ptr[p + 1] <= partition_ptr[p]) return bad("every partition needs at least one bond");
+        for (int i = partition_ptr[p]; i < partition_ptr[p + 1]; ++i) {
+            const int fb = partition_bonds[i];
+            if (fb < 0 || fb >= gp.full.n_bonds) return bad("partition bond out of range");
+            const int cb = gp.closed_of_full[fb];
+            if (cb < 0) return bad("partitions transect closed bonds only");
+            parts[p].push_back(cb);
+        }
+    }
+    if (part->geo->ready) PNE_CUDA_TRY(ctx, cudaStreamWaitEvent(s, part->geo->ready, 0));
+    auto rec = std::make_shared<EnumRecord>();
+    rec->ctx = ctx;
+    rec->comb = true;
+    rec->K = M;
+    rec->mode = PNE_MODE_COMB;
+    rec->n_closed = B;
+    rec->empty_by_order.assign(M + 1, 0);
+    struct Fence {
+        pne_ctx *ctx; EnumRecord *r; cudaStream_t s;
+        ~Fence() { r->uses.note(ctx, s); }
+    } fence{ctx, rec.get(), s};
+    // every sub-network: union-find over the sites along its kept bonds; the
+    // distinct components become the record's clusters
+    std::map<std::vector<int32_t>, int32_t> comp_id;
+    std::vector<std::vector<int32_t>> comps;
+    std::vector<std::vector<std::pair<int, std::vector<int32_t>>>> by_m;   // [m] -> (order, component ids)
+    std::vector<int> parent(N), cut(B);
+    std::function<int(int)> find = [&](int x) { while (parent[x] != x) { parent[x] = parent[parent[x]]; x = parent[x]; } return x; };
+    for (uint32_t x = 1; x < (1u << M); ++x) {
+        std::fill(cut.begin(), cut.end(), 0);
+        int order = 0;
+        for (int p = 0; p < M; ++p)
+            if (x >> p & 1) { ++order; for (int b : parts[p]) cut[b] = 1; }
+        for (int v = 0; v < N; ++v) parent[v] = v;
+        for (int b = 0; b < B; ++b)
+            if (!cut[b]) {
+                const int a = find(g.bond_site[2 * b]), c = find(g.bond_site[2 * b + 1]);
+                if (a != c) parent[a] = c;
+            }
+        std::map<int, std::vector<int32_t>> groups;          // root -> kept bonds (ascending)
+        for (int b = 0; b < B; ++b)
+            if (!cut[b]) groups[find(g.bond_site[2 * b])].push_back(b);
+        if (groups.empty()) { rec->empty_by_order[order] += 1; continue; }
+        std::vector<int32_t> ids;
+        for (auto &kv : groups) {
+            if (kv.second.size() > (size_t)kMaxOrder) return bad("a component of a sub-network has more than 32 bonds");
+            auto it = comp_id.find(kv.second);
+            int32_t id;
+            if (it == comp_id.end()) {
+                id = (int32_t)comps.size();
+                comp_id.emplace(kv.second, id);
+                comps.push_back(kv.second);
+            } else {
+                id = it->second;
+            }
+            ids.push_back(id);
+        }
+        std::sort(ids.begin(), ids.end());
+        const size_t m = ids.size();
+        if (by_m.size() < m + 1) by_m.resize(m + 1);
+        by_m[m].push_back({order, ids});
+    }
+    const int64_t nc = (int64_t)comps.size();
+    int width = 1, vwidth = 1;
+    std::vector<std::vector<int32_t>> verts(nc);
+    for (int64_t c = 0; c < nc; ++c) {
+        std::vector<int32_t> vs;
+        for (int b : comps[c]) { vs.push_back(g.bond_site[2 * b]); vs.push_back(g.bond_site[2 * b + 1]); }
+        std::sort(vs.begin(), vs.end());
+        vs.erase(std::unique(vs.begin(), vs.end()), vs.end());
+        if (vs.size() > 32) return bad("a component of a sub-network has more than 32 sites");
+        verts[c] = vs;
+        width = std::max(width, (int)comps[c].size());
+        vwidth = std::max(vwidth, (int)vs.size());
+    }
+    rec->width = width;
+    rec->vwidth = vwidth;
+    rec->n_clusters = (uint64_t)nc;
+    rec->size_start.assign(M + 2, 0);                     // no single-cluster terms: every term is a level entry
+    if (by_m.size() > 17) {
+        set_error(ctx, PNE_EOVERFLOW, "a sub-network has more than 16 components");
+        return PNE_EOVERFLOW;
+    }
+    pne_status st;
+    {
+        const size_t nn = std::max<int64_t>(nc, 1);
+        std::vector<int32_t> he(nn * width, -1), hv(nn * vwidth, -1), hs(nn, 0);
+        for (int64_t c = 0; c < nc; ++c) {
+            for (size_t j = 0; j < comps[c].size(); ++j) he[c * width + j] = comps[c][j];
+            for (size_t j = 0; j < verts[c].size(); ++j) hv[c * vwidth + j] = verts[c][j];
+            hs[c] = (int32_t)comps[c].size();
+        }
+        if ((st = dev_alloc(ctx, rec->cl_edges, he.size() * 4, s)) || (st = dev_alloc(ctx, rec->cl_verts, hv.size() * 4, s)) ||
+            (st = dev_alloc(ctx, rec->cl_size, hs.size() * 4, s)) ||
+            (st = upload(ctx, rec->cl_edges.ptr, he.data(), he.size() * 4, s)) ||
+            (st = upload(ctx, rec->cl_verts.ptr, hv.data(), hv.size() * 4, s)) ||
+            (st = upload(ctx, rec->cl_size.ptr, hs.data(), hs.size() * 4, s)))
+            return st;
+    }
+    // the terms, one level per number of components, ordered by |x|
+    rec->terms_by_order.assign(M + 1, 0);
+    rec->n_terms = 0;
+    for (int k = 1; k <= M; ++k) rec->terms_by_order[k] += rec->empty_by_order[k];
+    for (size_t m = 1; m < by_m.size(); ++m) {
+        auto &lst = by_m[m];
+        if (lst.empty()) continue;
+        std::stable_sort(lst.begin(), lst.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
+        EnumRecord::Level L;
+        L.m = (int)m;
+        L.n = lst.size();
+        L.order_start.assign(M + 2, 0);
+        std::vector<int32_t> idx(lst.size() * m);
+        for (size_t i = 0; i < lst.size(); ++i) {
+            for (size_t j = 0; j < m; ++j) idx[i * m + j] = lst[i].second[j];
+            rec->terms_by_order[lst[i].first] += 1;
+        }
+        for (int k = 0; k <= M + 1; ++k) {
+            int64_t n = 0;
+            for (auto &e : lst) n += (e.first < k);
+            L.order_start[k] = n;
+        }
+        if ((st = dev_alloc(ctx, L.idx, idx.size() * 4, s)) || (st = upload(ctx, L.idx.ptr, idx.data(), idx.size() * 4, s)))
+            return st;
+        rec->levels.push_back(L);
+    }
+    for (int k = 0; k <= M; ++k) rec->n_terms += rec->terms_by_order[k];
+    // the virtual geometry (bond dimensions d + 1) and the contraction plans
+    Geometry &vg = rec->vgeo;
+    vg.n_sites = N; vg.n_bonds = B;
+    vg.bond_site = g.bond_site; vg.site_ptr = g.site_ptr; vg.site_bonds = g.site_bonds;
+    vg.bond_dim = g.bond_dim;
+    for (auto &d : vg.bond_dim) d += 1;
+    if ((st = finish_geometry(ctx, vg, s))) return st;
+    if (nc > 0) {
+        ShapePrep sp;
+        if ((st = shapes_begin(ctx, vg, *rec, sp, s)) || (st = shapes_plan(ctx, vg, *rec, sp, s)) ||
+            (st = shapes_complete(ctx, vg, *rec, sp, s))) {
+            shapes_release(ctx, sp, s);
+            return st;
+        }
+    }
+    pne_terms *t = new pne_terms();
+    t->ctx = ctx; t->part = part; t->rec = rec; t->K = M; t->mode = PNE_MODE_COMB;
+    t->last_stream = s;
+    const size_t Bm = part->n_members;
+    const size_t ncl = std::max<int64_t>(nc, 1);
+    if ((st = dev_alloc(ctx, t->status, 16, s)) || (st = dev_alloc(ctx, t->w, Bm * ncl * 8, s)) ||
+        (st = dev_alloc(ctx, t->nzc, Bm * ncl * 4, s))) {
+        pne_terms_destroy(t);
+        return st;
+    }
+    cudaMemsetAsync(t->status.ptr, 0, 16, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { pne_terms_destroy(t); set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return PNE_ECUDA; }
+    *out = t;
+    if (n_components) *n_components = (uint64_t)nc;
+    if (n_terms) *n_terms = rec->n_terms;
+    return PNE_OK;
+}
+
 void pne_terms_destroy(pne_terms *t)
 {
     if (!t) return;
@@ -1096,6 +1323,9 @@ void pne_terms_destroy(pne_terms *t)
     if (t->rec) t->rec->uses.note(t->ctx, s);    // the record outlives this stream's queued work
     // so does the partition (terms handles are destroyed before it)
     if (t->part) const_cast<pne_partition *>(t->part)->uses.note(t->ctx, s);
+    dev_free(t->ctx, t->Mf, s);
+    dev_free(t->ctx, t->Mf32, s);
+    dev_free(t->ctx, t->Mf16, s);
     dev_free(t->ctx, t->w, s);
     dev_free(t->ctx, t->nzc, s);
     dev_free(t->ctx, t->sums, s);
@@ -1154,7 +1384,11 @@ pne_status pne_open_tensor(pne_ctx *ctx, const pne_terms *t, void *stream, doubl
 pne_status pne_terms_export(pne_ctx *ctx, const pne_terms *t, void *stream, int32_t *edges, double *w)
 {
     if (!ctx || !t) return PNE_EINVAL;
-    if (t->mode != PNE_MODE_LOOP) { set_error(ctx, PNE_EINVAL, "export needs LOOP mode"); return PNE_EINVAL; }
+    if (t->mode != PNE_MODE_LOOP && t->mode != PNE_MODE_COMB) {
+        set_error(ctx, PNE_EINVAL, "export needs LOOP or COMB mode");
+        return PNE_EINVAL;
+    }
+    const int row = (t->mode == PNE_MODE_COMB) ? kMaxOrder : t->K;    // entries per exported cluster row
     cudaStream_t s = (cudaStream_t)stream;
     const_cast<pne_terms *>(t)->last_stream = s;
     const EnumRecord &rec = *t->rec;
@@ -1168,9 +1402,9 @@ pne_status pne_terms_export(pne_ctx *ctx, const pne_terms *t, void *stream, int3
         for (size_t b = 0; b < t->part->geo->closed_of_full.size(); ++b)
             if (t->part->geo->closed_of_full[b] >= 0) full_of_closed.push_back((int32_t)b);
         for (size_t i = 0; i < n; ++i)
-            for (int j = 0; j < t->K; ++j) {
+            for (int j = 0; j < row; ++j) {
                 const int32_t e = (j < rec.width) ? buf[i * rec.width + j] : -1;
-                edges[i * t->K + j] = (e >= 0) ? full_of_closed[e] : -1;
+                edges[i * row + j] = (e >= 0) ? full_of_closed[e] : -1;
             }
     }
     if (w) {
@@ -1210,6 +1444,16 @@ pne_status pne_sum(pne_ctx *ctx, const pne_terms *t, void *stream, pne_result *o
     if (status) { set_error(ctx, PNE_EOVERFLOW, "a cluster exceeded the contraction buffer"); return PNE_EOVERFLOW; }
     for (int b = 0; b < B; ++b) {
         const int set = b / p->n_slices;
+        if (t->rec->comb) {
+            // sub-networks with no kept bond are the capped sites alone: 1
+            // relative to Z_ref, unless a capped site is zero
+            double *cb = &c[(size_t)b * (K + 1)], *ab = &a[(size_t)b * (K + 1)];
+            if ((int)vac[3 * (size_t)b + 2] == 0)
+                for (int k = 0; k <= K; ++k) { cb[k] += (double)t->rec->empty_by_order[k]; ab[k] += (double)t->rec->empty_by_order[k]; }
+            finalize_comb_result(out[b], K, t->dtype, cb, ab, &vac[3 * (size_t)b], t->rec->n_terms, t->rec->n_clusters,
+                                 p->geo->closed.n_sites, p->bp_iters[set], p->bp_residual[set]);
+            continue;
+        }
         finalize_result(out[b], K, t->mode, t->dtype, &c[(size_t)b * (K + 1)], &a[(size_t)b * (K + 1)], &vac[3 * (size_t)b],
                         t->rec->n_terms, t->rec->n_clusters, p->bp_iters[set], p->bp_residual[set]);
     }
@@ -1386,7 +1630,10 @@ int pne_ctx_trace_read(pne_ctx *ctx, pne_trace_entry *out, int max, double *host
 pne_status pne_terms_work(pne_ctx *ctx, const pne_terms *t, void *stream, uint64_t *fma_per_set)
 {
     if (!ctx || !t || !fma_per_set) return PNE_EINVAL;
-    if (t->mode != PNE_MODE_LOOP) { set_error(ctx, PNE_EINVAL, "work count needs LOOP mode"); return PNE_EINVAL; }
+    if (t->mode != PNE_MODE_LOOP && t->mode != PNE_MODE_COMB) {
+        set_error(ctx, PNE_EINVAL, "work count needs LOOP or COMB mode");
+        return PNE_EINVAL;
+    }
     if (t->rec->shaped) {
         uint64_t f = 0;
         for (int i = 0; i < t->rec->n_shapes; ++i) f += t->rec->shape_fma[i] * (uint64_t)t->rec->shape_count[i];

@@ -300,6 +300,15 @@ struct EnumRecord {
     std::vector<int64_t> class_start;
     std::vector<int> class_xmax;
     UseFence uses;                              // streams of the terms handles that used it
+    // combinatorial form (COMB mode): the clusters are the distinct connected
+    // components of the kept bonds of the sub-networks; each term is one
+    // sub-network (order = number of active partitions).  Contractions run on
+    // a virtual copy of the closed geometry whose bond dimensions are d + 1, so
+    // that the excited range 1..d of the blocked layout is the full range of a
+    // kept bond (blocks gathered from the gauged tensors).
+    bool comb = false;
+    Geometry vgeo;
+    std::vector<uint64_t> empty_by_order;       // [K+1] sub-networks with no kept bond
     ~EnumRecord();
 };
 
@@ -317,6 +326,7 @@ struct pne_terms {
     pne::DevBuf status;                  // int32 error flags
     bool contracted = false;
     cudaStream_t last_stream = nullptr;  // stream of the last call that used the handle
+    pne::DevBuf Mf, Mf32, Mf16;          // COMB: full-range blocks of the virtual geometry
 };
 
 namespace pne {
@@ -360,6 +370,8 @@ pne_status partition_settle(pne_ctx *ctx, pne_partition *p);
 pne_status partition_record(pne_ctx *ctx, pne_partition *p, const char *rec);
 pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t *h_flag);
 pne_status launch_convert(pne_ctx *ctx, pne_partition *p, int dtype, cudaStream_t s);
+// FP64 -> FP32 (TF32 rounding for PNE_TF32) or BF16 copy of n entries
+pne_status convert_buffer(pne_ctx *ctx, const double *src, int64_t n, int dtype, void *dst, cudaStream_t s);
 
 // enumeration (enumerate.cu)
 pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode,
@@ -388,6 +400,8 @@ pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s,
                        std::vector<double> &c, std::vector<double> &abs_c, int32_t *h_status);
 pne_status launch_all_mode(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s);
 pne_status launch_plan_work(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, uint64_t *fma);
+// device tables of a geometry built from its bond_site/bond_dim/site_ptr/site_bonds (pne_api.cu)
+pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s);
 // contraction plans per cluster shape, in two halves around a synchronisation
 struct ShapePrep {
     DevBuf dh;                    // per-cluster hashes on the device

@@ -31,7 +31,8 @@ __all__ = [
 
 PNE_OK, PNE_EINVAL, PNE_ENOMEM, PNE_ECUDA, PNE_ENOCONV, PNE_EDEGENERATE, PNE_ETIMEOUT, PNE_EOVERFLOW, PNE_EBUSY = range(9)
 PNE_F64, PNE_F32, PNE_TF32, PNE_BF16 = range(4)
-PNE_MODE_LOOP, PNE_MODE_ALL = 0, 1
+PNE_MODE_LOOP, PNE_MODE_ALL, PNE_MODE_COMB = 0, 1, 2
+PNE_MAX_ORDER = 32
 MAX_ORDER = 32
 DTYPES = {"f64": PNE_F64, "f32": PNE_F32, "tf32": PNE_TF32, "bf16": PNE_BF16}
 
@@ -152,6 +153,10 @@ def load_library():
     lib.pne_sum.restype = ctypes.c_int
     lib.pne_terms_n_results.argtypes = [vp]
     lib.pne_terms_n_results.restype = ctypes.c_int64
+    lib.pne_enumerate_combinatorial.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, vp,
+                                                ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint64),
+                                                ctypes.POINTER(ctypes.c_uint64)]
+    lib.pne_enumerate_combinatorial.restype = ctypes.c_int
     lib.pne_open_tensor.argtypes = [vp, vp, vp, ctypes.c_void_p, ctypes.c_void_p]
     lib.pne_open_tensor.restype = ctypes.c_int
     lib.pne_open_tensor_assemble.argtypes = [ctypes.POINTER(Result), ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
@@ -209,7 +214,7 @@ def exported_symbols() -> list:
     lib = load_library()
     names = ["pne_ctx_create", "pne_ctx_destroy", "pne_last_error", "pne_ctx_set_allocator",
              "pne_build_partition", "pne_partition_destroy", "pne_enumerate_terms", "pne_terms_destroy",
-             "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_open_tensor", "pne_open_tensor_assemble",
+             "pne_enumerate_combinatorial", "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_open_tensor", "pne_open_tensor_assemble",
              "pne_terms_export",
              "pne_ctx_profile", "pne_ctx_profile_read", "pne_ctx_trace_read", "pne_terms_work", "pne_measure_fma_peak",
              "pne_bp_messages_noalloc", "pne_partition_update", "pne_batch_create", "pne_batch_run",
@@ -263,6 +268,20 @@ def pne_enumerate_terms(ctx, part, opts: EnumOpts, stream=None):
     _check(load_library().pne_enumerate_terms(ctx, part, ctypes.byref(opts), stream, ctypes.byref(h),
                                               ctypes.byref(nc), ctypes.byref(nt)), ctx)
     return h, nc.value, nt.value
+
+
+def pne_enumerate_combinatorial(ctx, part, partitions, stream=None):
+    """Combinatorial-form handle over multi-index partitions (each a list of
+    bond ids of the network).  Returns (terms, n_components, n_terms)."""
+    ptr = np.zeros(len(partitions) + 1, dtype=np.int32)
+    for i, S in enumerate(partitions):
+        ptr[i + 1] = ptr[i] + len(S)
+    bonds = np.ascontiguousarray(np.concatenate([np.asarray(S, dtype=np.int32) for S in partitions]), dtype=np.int32)
+    h = ctypes.c_void_p()
+    nc, nt = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load_library().pne_enumerate_combinatorial(ctx, part, len(partitions), ptr.ctypes.data, bonds.ctypes.data,
+                                                      stream, ctypes.byref(h), ctypes.byref(nc), ctypes.byref(nt)), ctx)
+    return h, int(nc.value), int(nt.value)
 
 
 def pne_terms_destroy(t):
@@ -607,6 +626,33 @@ def _context_open_tensor(self, net, K, mode=PNE_MODE_LOOP, dtype=PNE_F64, data=N
 
 
 Context.open_tensor = _context_open_tensor
+
+
+def _context_combinatorial(self, net, partitions, dtype=PNE_F64, data=None, n_batch=1, stream=None, arithmetic=0,
+                           export=False):
+    """One pass of the combinatorial form (partition -> sub-network components
+    -> contraction -> signed sums).  Returns the result dicts (one per tensor
+    set); with export=True also (component edges, component values)."""
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    ns, keep = network_struct(net, data=data, n_batch=n_batch)
+    part, _ = pne_build_partition(self.h, ns, PartitionOpts(1e-13, 10000, 0.0, arithmetic), stream)
+    try:
+        terms, nc, nt = pne_enumerate_combinatorial(self.h, part, partitions, stream)
+        try:
+            pne_contract_terms(self.h, terms, dtype, stream)
+            res = pne_sum(self.h, terms, stream)
+            if export:
+                res = (res, pne_terms_export(self.h, terms, nc, PNE_MAX_ORDER, True, stream))
+            return res
+        finally:
+            pne_terms_destroy(terms)
+    finally:
+        pne_partition_destroy(part)
+        del keep
+
+
+Context.combinatorial = _context_combinatorial
 
 
 def run(net, K, mode=PNE_MODE_LOOP, dtype=PNE_F64, device=0, **kw):
