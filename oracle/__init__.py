@@ -24,6 +24,8 @@ Contents (each function cites the passage it follows):
                 contracted as written, the residue with the non-factorising
                 complements inserted directly, and the linear form over
                 partitions (Eq. A4).
+  weights.py    weight passing (App. C) and expansions with rank-r projectors
+                onto the largest weights (Sec. V), linear and combinatorial.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` (closed forms, brute force, exact identities).

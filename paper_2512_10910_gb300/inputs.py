@@ -426,3 +426,37 @@ def cube2_planes() -> list:
     """Three multi-index partitions of the 2 x 2 x 2 network, each the four
     bonds along one axis (cutting one separates two 2 x 2 planes)."""
     return [cubic_axis_bonds(2, a) for a in range(3)]
+
+
+def ising_blocked(lx: int, ly: int, block: int, beta: float, J: float = 1.0) -> Network:
+    """The 2D Ising network of a (lx*block) x (ly*block) open lattice,
+    coarse-grained into an lx x ly network: each site is a block x block patch
+    of spins contracted over its internal bonds, and the block fine bonds
+    crossing between two patches are grouped into one index of dimension
+    2^block (row-major over the fine bonds in ascending fine id).  The
+    network contracts to the same partition function."""
+    fine = ising_tensors(square_lattice(lx * block, ly * block, 2), beta, J)
+    FX = lx * block
+    coarse = square_lattice(lx, ly, 2 ** block)
+    cell = lambda s: ((s % FX) // block, (s // FX) // block)
+    # fine bonds crossing each coarse bond
+    groups = {b: [] for b in range(coarse.n_bonds)}
+    for fb in range(fine.n_bonds):
+        u, v = (int(x) for x in fine.bond_site[fb])
+        cu, cv = cell(u), cell(v)
+        if cu != cv:
+            cb = bond_between(coarse, cu[1] * lx + cu[0], cv[1] * lx + cv[0])
+            groups[cb].append(fb)
+    tensors = []
+    for Y in range(ly):
+        for X in range(lx):
+            c = Y * lx + X
+            sites = [s for s in range(fine.n_sites) if cell(s) == (X, Y)]
+            lab = {}
+            ops = []
+            for s in sites:
+                ops += [fine.tensors[s], [lab.setdefault(int(b), len(lab)) for b in fine.legs(s)]]
+            out = [lab[fb] for cb in coarse.legs(c) for fb in sorted(groups[int(cb)])]
+            t = np.einsum(*ops, out, optimize="greedy")
+            tensors.append(np.ascontiguousarray(t.reshape(coarse.leg_dims(c))))
+    return coarse.with_tensors(tensors, name=f"ising{lx * block}x{ly * block}_blocked{block}_b{beta:g}")
