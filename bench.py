@@ -482,7 +482,7 @@ def step_roofline(args, pne, ctx, ctypes_stream, g, sb, res, prof, prof_steps, B
     elif fam == "contract":
         roof.update(achieved=2.0 * fma * B / (avg_ms * 1e-3) / 1e12, peak=pk_c / 1e12,
                     peak_source="measured FMA-chain kernel (pne_measure_fma_peak)", work=c_work)
-    elif fam in ("enum_expand", "enum_dfs"):
+    elif fam.startswith("enum_"):
         # the cluster search is integer work bound by issue and latency; its
         # algorithmic traffic is the cluster lists it writes (edges, sorted
         # vertices, size) -- an HBM fraction far below 1 by nature
@@ -493,7 +493,7 @@ def step_roofline(args, pne, ctx, ctypes_stream, g, sb, res, prof, prof_steps, B
         roof.update(bound="hbm", unit="GB/s", achieved=n_cl * per_cluster / (per_search_ms * 1e-3) / 1e9,
                     peak=peak_gbs, peak_source=src,
                     work=f"{n_cl} clusters x {per_cluster} B written per search "
-                         f"({launches // prof_steps} launches per search, timed together)")
+                         f"({launches // prof_steps} launches of {fam} per search)")
     if roof["achieved"] is not None and roof["peak"]:
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["avg_launch_ms"] = avg_ms

@@ -375,6 +375,57 @@ pne_status pne_server_stats(pne_server *s, uint64_t *peak_inflight_bytes, double
 const char *pne_server_first_error(pne_server *s);
 void pne_server_destroy(pne_server *s);
 
+/* ---- rank-r projectors by weight passing ---------------------------------- */
+
+/* Weight passing (App. C): a diagonal matrix of positive weights S_i on every
+ * bond, found by repeated local updates that are pure changes of gauge (Eq.
+ * weight1-3): for bond i between tensors A and B, the weights of all other
+ * legs are absorbed into A and B, the SVDs of both (between index i and the
+ * rest) and of S_A V_A^T S_i U_B S_B are taken, A and B are re-gauged and S_i
+ * becomes S_C^alpha.  Sweeps visit the bonds in id order until the largest
+ * weight change is below tol.  The weights are rescaled to a largest entry of
+ * 1 after each update and the factor kept in a log scale.  The handle keeps,
+ * on the device, the weighted network -- sqrt(S_i) absorbed into both ends of
+ * every bond, so that it contracts to the input's value times exp(-log_scale)
+ * -- in which the rank-r projector onto the r largest weights of a bond is the
+ * restriction of its index to the first r values (the weights are sorted).
+ *   net    closed network (no open indices), host or device tensors, n_batch
+ *          tensor sets; every bond dimension at most 16 and at most the
+ *          product of the other dimensions of either of its tensors.
+ *   alpha  in (0, 1] (the paper's benchmarks use 0.8); tol > 0; max_sweeps > 0.
+ * FP64 throughout.  Synchronises `stream`.  Returns PNE_ENOCONV (handle
+ * still returned) when some set did not reach tol, PNE_EDEGENERATE when a
+ * tensor is rank-deficient across a bond (a zero singular value). */
+typedef struct pne_weights pne_weights;
+pne_status pne_weight_passing(pne_ctx *ctx, const pne_network *net, double alpha, double tol, int32_t max_sweeps,
+                              void *stream, pne_weights **out);
+/* weights [n_batch][n_bonds][16] (zero-padded, descending per bond), sweeps
+ * [n_batch], log_scale [n_batch]; host arrays, each may be NULL.  Synchronises. */
+pne_status pne_weights_read(pne_ctx *ctx, const pne_weights *w, void *stream, double *weights, int32_t *sweeps,
+                            double *log_scale);
+void pne_weights_destroy(pne_weights *w);
+
+/* The expansion with rank-r projectors (Sec. V.A) built on the weights: every
+ * partition's projector keeps the `rank` largest weights of each of its bonds
+ * (first `rank` index values of the weighted network), Q = I - P.
+ *   form 0  linear form over single-index partitions (Eq. A4): terms
+ *           Z(Q_1, ..., Q_k, P_{k+1}, I, ...), k = 0 .. M-1, each partition
+ *           exactly one bond;
+ *   form 1  combinatorial form over multi-index partitions (Eq. A6): the
+ *           2^M - 1 sub-networks Z(P^x) with alternating signs.
+ * Every term is the weighted network with each bond's index restricted to
+ * the P range [0, rank), the Q range [rank, d) or left whole, contracted
+ * exactly in FP64 (a dense contraction site by site); the residue is
+ * neglected.  One pne_result per tensor set in out[n_batch]: value, sign,
+ * log_abs (the scale included), c[k] = sum of the order-k terms times
+ * exp(-log_scale) (k = |x| for form 1, k = position in Eq. A4 for form 0),
+ * n_terms.  Partition bonds as in pne_enumerate_combinatorial.  Limits: M <=
+ * 20, 1 <= rank < every partitioned bond's dimension, an intermediate tensor
+ * of at most 2^20 entries (PNE_EINVAL otherwise).  Synchronises `stream`. */
+pne_status pne_rank_r_expand(pne_ctx *ctx, const pne_weights *w, int32_t rank, int32_t form, int32_t n_partitions,
+                             const int32_t *partition_ptr, const int32_t *partition_bonds, void *stream,
+                             pne_result *out);
+
 /* ---- belief propagation without device allocation ------------------------ */
 
 /* The paper has no counterpart to this call.  It is for callers that must not

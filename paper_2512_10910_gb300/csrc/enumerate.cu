@@ -1328,15 +1328,21 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
             roots_kernel<<<grid1(Mc, 128, ctx->n_sm), 128, 0, s>>>(gv, Mc, mode, A, none, 0);
         }
         PNE_LAUNCH_CHECK(ctx);
+        // each pass is its own kernel and is timed under its own name
         for (int d = 1; d < D; ++d) {
-            ProfScope ps__(ctx, s, "enum_expand");
-            launch_expand(kCount, final_kind == 3, G, s, gv, A, d, d, K, mode, none);
+            {
+                ProfScope ps__(ctx, s, "enum_count");
+                launch_expand(kCount, final_kind == 3, G, s, gv, A, d, d, K, mode, none);
+            }
             PNE_LAUNCH_CHECK(ctx);
-            expand_children_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, K, mode);
+            {
+                ProfScope ps__(ctx, s, "enum_children");
+                expand_children_kernel<<<G, 32 * kExpandWarps, 0, s>>>(gv, A, d, K, mode);
+            }
             PNE_LAUNCH_CHECK(ctx);
         }
         if (final_kind == 1 || final_kind == 3) {
-            ProfScope ps__(ctx, s, "enum_expand");
+            ProfScope ps__(ctx, s, "enum_close_count");
             launch_expand(final_kind == 3 ? kPairCount : kEmitCount, final_kind == 3, G, s, gv, A, D, D, K, mode, none);
         } else if (final_kind == 2) {
             dfs(A, D, 0, none);
@@ -1391,7 +1397,7 @@ pne_status enumerate_clusters(pne_ctx *ctx, const Geometry &g, int K, int mode, 
     }
     PNE_LAUNCH_CHECK(ctx);
     if (last_bfs >= 1) {
-        ProfScope ps__(ctx, s, "enum_expand");
+        ProfScope ps__(ctx, s, "enum_emit");
         launch_expand(kEmit, final_kind == 3 && dfs_level == 0, G, s, gv, A, 1, last_bfs, K, mode, out);
     }
     PNE_LAUNCH_CHECK(ctx);

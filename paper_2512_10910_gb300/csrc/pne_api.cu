@@ -434,7 +434,7 @@ pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
 
 namespace {
 
-pne_status validate(pne_ctx *ctx, const pne_network *n)
+pne_status validate(pne_ctx *ctx, const pne_network *n, int max_dim = kMaxDim, int64_t max_size = 4096)
 {
     auto bad = [&](const std::string &m) { set_error(ctx, PNE_EINVAL, m); return PNE_EINVAL; };
     if (!n || n->n_sites < 1 || n->n_bonds < 0) return bad("empty or malformed network");
@@ -446,7 +446,8 @@ pne_status validate(pne_ctx *ctx, const pne_network *n)
     for (int b = 0; b < M; ++b) {
         const int s0 = n->bond_site[2 * b], s1 = n->bond_site[2 * b + 1];
         if (s0 < 0 || s0 >= N || s1 >= N || s1 < -1 || s0 == s1) return bad("bond " + std::to_string(b) + " has invalid sites");
-        if (n->bond_dim[b] < 2 || n->bond_dim[b] > kMaxDim) return bad("bond dimension must be in 2..8");
+        if (n->bond_dim[b] < 2 || n->bond_dim[b] > max_dim)
+            return bad("bond dimension must be in 2.." + std::to_string(max_dim));
     }
     if (n->site_ptr[0] != 0) return bad("site_ptr[0] must be 0");
     for (int v = 0; v < N; ++v) {
@@ -462,7 +463,7 @@ pne_status validate(pne_ctx *ctx, const pne_network *n)
             size *= n->bond_dim[b];
         }
         if (n->data_off[v + 1] - n->data_off[v] != size) return bad("data_off inconsistent with leg dimensions");
-        if (size > 4096) return bad("site tensor larger than 4096 entries");
+        if (size > max_size) return bad("site tensor larger than " + std::to_string(max_size) + " entries");
     }
     if (n->data_off[0] != 0) return bad("data_off[0] must be 0");
     for (int b = 0; b < M; ++b) {
@@ -710,6 +711,16 @@ GeomPair::~GeomPair()
     dev_free(ctx, full.storage, rs);
     dev_free(ctx, closed.storage, rs);
     dev_free(ctx, gauge_tab, rs);
+}
+
+// A validated network's geometry through the context's cache (for the other
+// translation units' entry points).
+pne_status geometry_for(pne_ctx *ctx, const pne_network *net, cudaStream_t s, std::shared_ptr<GeomPair> &out,
+                        int max_dim, int64_t max_size)
+{
+    pne_status st = validate(ctx, net, max_dim, max_size);
+    if (st) return st;
+    return get_geometry(ctx, net, s, out);
 }
 
 pne_status partition_record(pne_ctx *ctx, pne_partition *p, const char *rec)

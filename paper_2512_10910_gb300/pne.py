@@ -157,6 +157,16 @@ def load_library():
                                                 ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint64),
                                                 ctypes.POINTER(ctypes.c_uint64)]
     lib.pne_enumerate_combinatorial.restype = ctypes.c_int
+    lib.pne_weight_passing.argtypes = [vp, ctypes.POINTER(Network), ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                       vp, ctypes.POINTER(vp)]
+    lib.pne_weight_passing.restype = ctypes.c_int
+    lib.pne_weights_read.argtypes = [vp, vp, vp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.pne_weights_read.restype = ctypes.c_int
+    lib.pne_weights_destroy.argtypes = [vp]
+    lib.pne_weights_destroy.restype = None
+    lib.pne_rank_r_expand.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_void_p, vp, ctypes.POINTER(Result)]
+    lib.pne_rank_r_expand.restype = ctypes.c_int
     lib.pne_open_tensor.argtypes = [vp, vp, vp, ctypes.c_void_p, ctypes.c_void_p]
     lib.pne_open_tensor.restype = ctypes.c_int
     lib.pne_open_tensor_assemble.argtypes = [ctypes.POINTER(Result), ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
@@ -220,7 +230,8 @@ def exported_symbols() -> list:
              "pne_bp_messages_noalloc", "pne_partition_update", "pne_batch_create", "pne_batch_run",
              "pne_batch_n_results", "pne_batch_config", "pne_batch_destroy", "pne_server_create",
              "pne_server_submit", "pne_server_poll", "pne_server_drain", "pne_server_stats", "pne_server_first_error",
-             "pne_server_destroy"]
+             "pne_server_destroy", "pne_weight_passing", "pne_weights_read", "pne_weights_destroy",
+             "pne_rank_r_expand"]
     return [n for n in names if hasattr(lib, n)]
 
 
@@ -282,6 +293,42 @@ def pne_enumerate_combinatorial(ctx, part, partitions, stream=None):
     _check(load_library().pne_enumerate_combinatorial(ctx, part, len(partitions), ptr.ctypes.data, bonds.ctypes.data,
                                                       stream, ctypes.byref(h), ctypes.byref(nc), ctypes.byref(nt)), ctx)
     return h, int(nc.value), int(nt.value)
+
+
+def pne_weight_passing(ctx, net: Network, alpha=0.8, tol=1e-12, max_sweeps=5000, stream=None, allow_noconv=False):
+    """Weight passing (App. C) on the device; returns the handle."""
+    h = ctypes.c_void_p()
+    st = load_library().pne_weight_passing(ctx, ctypes.byref(net), float(alpha), float(tol), int(max_sweeps), stream,
+                                           ctypes.byref(h))
+    if not (st == PNE_ENOCONV and allow_noconv):
+        _check(st, ctx)
+    return h
+
+
+def pne_weights_read(ctx, w, n_sets, n_bonds, stream=None):
+    """(weights [n_sets, n_bonds, 16], sweeps [n_sets], log_scale [n_sets])."""
+    wts = np.zeros((n_sets, max(n_bonds, 1), 16))
+    sw = np.zeros(n_sets, dtype=np.int32)
+    ls = np.zeros(n_sets)
+    _check(load_library().pne_weights_read(ctx, w, stream, wts.ctypes.data, sw.ctypes.data, ls.ctypes.data), ctx)
+    return wts[:, :n_bonds], sw, ls
+
+
+def pne_weights_destroy(w):
+    load_library().pne_weights_destroy(w)
+
+
+def pne_rank_r_expand(ctx, w, rank, form, partitions, n_sets, stream=None):
+    """The rank-r expansion (form 0 linear, 1 combinatorial) on the weights:
+    one result dict per tensor set."""
+    ptr = np.zeros(len(partitions) + 1, dtype=np.int32)
+    for i, S in enumerate(partitions):
+        ptr[i + 1] = ptr[i] + len(S)
+    bonds = np.ascontiguousarray(np.concatenate([np.asarray(S, dtype=np.int32) for S in partitions]), dtype=np.int32)
+    out = (Result * n_sets)()
+    _check(load_library().pne_rank_r_expand(ctx, w, int(rank), int(form), len(partitions), ptr.ctypes.data,
+                                            bonds.ctypes.data, stream, out), ctx)
+    return [r.as_dict() for r in out]
 
 
 def pne_terms_destroy(t):
@@ -653,6 +700,24 @@ def _context_combinatorial(self, net, partitions, dtype=PNE_F64, data=None, n_ba
 
 
 Context.combinatorial = _context_combinatorial
+
+
+def _context_rank_r(self, net, partitions, rank, form, alpha=0.8, tol=1e-12, max_sweeps=5000, data=None, n_batch=1,
+                    stream=None):
+    """Weight passing then the rank-r expansion (form 0 linear over single-index
+    partitions, 1 combinatorial): (results, weights, sweeps, log_scale)."""
+    ns, keep = network_struct(net, data=data, n_batch=n_batch)
+    w = pne_weight_passing(self.h, ns, alpha, tol, max_sweeps, stream)
+    try:
+        res = pne_rank_r_expand(self.h, w, rank, form, partitions, n_batch, stream)
+        wts, sw, ls = pne_weights_read(self.h, w, n_batch, int(net.n_bonds), stream)
+        return res, wts, sw, ls
+    finally:
+        pne_weights_destroy(w)
+        del keep
+
+
+Context.rank_r = _context_rank_r
 
 
 def run(net, K, mode=PNE_MODE_LOOP, dtype=PNE_F64, device=0, **kw):
