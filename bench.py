@@ -184,6 +184,15 @@ def _oracle_worker(arg):
     return nt, secs, None
 
 
+def max_over_ranks(total_ms, dist, device):
+    """The step time every rank reports: the largest over the ranks (one
+    all-reduce of one number, after the timed region)."""
+    import torch
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class StepBench:
     """One pass of the hot path over a batch of networks of one geometry:
     partition (BP, gauge) on the main stream, enumeration (geometry only,
@@ -261,9 +270,7 @@ class StepBench:
         if profile:
             pne.pne_ctx_profile(self.ctx.h, False)
         if self.world > 1:
-            t = torch.tensor([total], device=self.dev, dtype=torch.float64)
-            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
-            total = float(t.item())
+            total = max_over_ranks(total, self.dist, self.dev)
         return total, res, prof
 
 
@@ -437,7 +444,8 @@ def run_step_bench(args, wl, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_extras and wl["kind"] == "random2d":
         extras = {}
         for name, fn in (("cfg3_ising3d_8x8x8", run_cfg3), ("cfg4_batched", run_batched_extra),
-                         ("cfg5_served", run_served_comparison)):
+                         ("cfg5_served", run_served_comparison), ("combinatorial_3x3", run_combinatorial_extra),
+                         ("rank_r_ising_sec5b", run_rank_r_extra)):
             t0 = time.perf_counter()
             try:
                 extras[name] = fn(args, ctx, pne, torch, dev, local_rank)
@@ -557,6 +565,76 @@ def run_cfg3(args, ctx, pne, torch, dev, local_rank):
     return out
 
 
+# ---------------------------------------------------------------- multi-index and rank-r forms
+def _exact_einsum(net):
+    """The whole small network in one numpy einsum (the value the expansion
+    approximates; reported beside the throughput)."""
+    ops = []
+    for v in range(net.n_sites):
+        ops += [np.asarray(net.tensors[v]), [int(b) for b in net.legs(v)]]
+    return float(np.einsum(*ops, [], optimize="greedy"))
+
+
+def _timed_calls(torch, dev, fn, steps, warmup):
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        out = fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / steps, out
+
+
+def run_combinatorial_extra(args, ctx, pne, torch, dev, local_rank):
+    """The combinatorial form over six multi-index partitions of a 3 x 3
+    network (random tensors, D = 4), 1024 tensor sets per step: partition,
+    sub-network components, exact component contractions, signed sums."""
+    g = I.square_lattice(3, 3, 4)
+    B = 1024
+    nets = [I.random_tensors(g, 5000 + i) for i in range(B)]
+    data = torch.from_numpy(np.concatenate([n.flat_data()[0] for n in nets])).to(dev)
+    parts = I.square3x3_six_lines()
+
+    def step():
+        return ctx.combinatorial(g, parts, pne.PNE_F64, data=data, n_batch=B, arithmetic=1)
+    ms, res = _timed_calls(torch, dev, step, 5, 2)
+    errs = [abs(math.expm1(res[i]["log_abs"] - math.log(_exact_einsum(nets[i])))) for i in range(8)]
+    return {"workload": "3x3 random U[0,1)+0.1, D=4, six multi-index partitions (2^6 - 1 = 63 sub-networks), "
+                        "1024 tensor sets per step", "ms_per_step": ms,
+            "sub_networks_per_s": res[0]["n_terms"] * B / (ms * 1e-3),
+            "components_per_network": res[0]["n_clusters"],
+            "max_rel_err_vs_exact_first8": max(errs),
+            "note": "error of the O(chi^4) expansion itself (residue neglected), not of the arithmetic"}
+
+
+def run_rank_r_extra(args, ctx, pne, torch, dev, local_rank):
+    """Weight passing and the rank-2 expansions of the coarse-grained 12 x 12
+    Ising network (3 x 3, bond dimension 16) at 32 temperatures from 0.5 T_c to
+    1.1 T_c, all in one step, against the exact contraction."""
+    bc = math.log(1 + math.sqrt(2)) / 2
+    fracs = np.linspace(0.5, 1.1, 32)
+    nets = [I.ising_blocked(3, 3, 4, bc / f) for f in fracs]
+    g = nets[0]
+    data = torch.from_numpy(np.concatenate([n.flat_data()[0] for n in nets])).to(dev)
+    exact = [math.log(_exact_einsum(n)) for n in nets]
+    out = {"workload": "12x12 Ising coarse-grained to 3x3 (bond dimension 16), 32 temperatures 0.5..1.1 T_c per "
+                       "step: weight passing (alpha 0.8) + rank-2 expansion"}
+    for form, parts, name in ((0, I.square3x3_pinwheel(), "linear_4_single_index"),
+                              (1, I.square3x3_six_lines(), "combinatorial_6_multi_index")):
+        def step():
+            return ctx.rank_r(g, parts, 2, form, alpha=0.8, tol=1e-10, data=data, n_batch=len(nets))
+        ms, (res, wts, sw, ls) = _timed_calls(torch, dev, step, 3, 1)
+        errs = [abs(math.expm1(r["log_abs"] - e)) for r, e in zip(res, exact)]
+        out[name] = {"ms_per_step": ms, "terms_per_s": res[0]["n_terms"] * len(nets) / (ms * 1e-3),
+                     "max_rel_err_vs_exact": max(errs), "max_sweeps": int(np.max(sw))}
+    return out
+
+
 # ---------------------------------------------------------------- cfg4
 def run_batched_extra(args, ctx, pne, torch, dev, local_rank):
     wl = WORKLOADS["batched"]
@@ -636,9 +714,7 @@ def run_batched(args, wl, rank, world, local_rank, steps=None, warmup=None):
     pne.pne_ctx_profile(ctx.h, False)
     clk = clocks.stop()
     if world > 1:
-        tt = torch.tensor([total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = float(tt.item())
+        total = max_over_ranks(total, dist, dev)
     ms = total / steps
     n_terms = sum(r["n_terms"] for r in res)
     n_clusters = sum(r["n_clusters"] for r in res)
