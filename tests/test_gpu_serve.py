@@ -101,12 +101,21 @@ def test_served_results_match_oracle_alone_and_in_mix(ctx, oracle, dtype):
             res, info = _wait(srv, rid)
             assert info["batch_size"] == 1
             alone.append(res)
-        ids = [pne.pne_server_submit(srv, ns, K) for (net, K), (ns, _) in zip(reqs, structs)]
-        mix = [_wait(srv, rid) for rid in ids]
-        assert max(info["batch_size"] for _, info in mix) > 1        # they did share launches
-        for a, (m, info) in zip(alone, mix):
-            assert a["log_abs"] == m["log_abs"] and np.array_equal(a["c"], m["c"])
-            assert info["t_arrival"] <= info["t_admit"] <= info["t_ready"] <= info["t_done"]
+        # whether warm requests submitted back to back share a launch depends on
+        # how fast each is prepared; submit the mix (every request three times)
+        # until one launch held several, checking every result of every round
+        shared = 0
+        for _ in range(8):
+            ids = [pne.pne_server_submit(srv, ns, K) for _ in range(3) for (net, K), (ns, _) in zip(reqs, structs)]
+            mix = [_wait(srv, rid) for rid in ids]
+            for j, (m, info) in enumerate(mix):
+                a = alone[j % len(reqs)]
+                assert a["log_abs"] == m["log_abs"] and np.array_equal(a["c"], m["c"])
+                assert info["t_arrival"] <= info["t_admit"] <= info["t_ready"] <= info["t_done"]
+            shared = max(shared, max(info["batch_size"] for _, info in mix))
+            if shared > 1:
+                break
+        assert shared > 1                                            # they did share launches
     finally:
         pne.pne_server_destroy(srv)
     for i, ((net, K), a) in enumerate(zip(reqs, alone)):
