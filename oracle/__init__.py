@@ -26,6 +26,10 @@ Contents (each function cites the passage it follows):
                 partitions (Eq. A4).
   weights.py    weight passing (App. C) and expansions with rank-r projectors
                 onto the largest weights (Sec. V), linear and combinatorial.
+  strips.py     the infinite-lattice strip expansion (Sec. IV.C): uniform BP,
+                strip transfer-matrix eigenvalues (LAPACK / ARPACK), capped
+                patches by einsum and by row sweeps, and the per-cell sums over
+                the 2L strip partitions (1D and 2D forms).
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` (closed forms, brute force, exact identities).

@@ -31,6 +31,7 @@ __all__ = [
     "Network", "square_lattice", "cubic_lattice", "grid_graph", "with_open_legs",
     "splitmix64_uniform", "splitmix64_normal",
     "ising_tensors", "random_tensors", "aklt_tensors", "slice_open", "batched_workload",
+    "uniform_ising", "uniform_random", "uniform_product",
 ]
 
 # leg direction tags stored beside ``site_bonds`` (used by the AKLT builder)
@@ -460,3 +461,57 @@ def ising_blocked(lx: int, ly: int, block: int, beta: float, J: float = 1.0) -> 
             t = np.einsum(*ops, out, optimize="greedy")
             tensors.append(np.ascontiguousarray(t.reshape(coarse.leg_dims(c))))
     return coarse.with_tensors(tensors, name=f"ising{lx * block}x{ly * block}_blocked{block}_b{beta:g}")
+
+
+# ---- uniform tensors of infinite square lattices (Sec. IV.C) ----------------
+#
+# One tensor A repeated on every site of the infinite square lattice, axes
+# [l, u, r, d]: l joins the site to its neighbour at x - 1, u to y - 1, r to
+# x + 1 and d to y + 1.  A horizontal bond joins the r leg of one site to the l
+# leg of the next; a vertical bond the d leg of one site to the u leg of the
+# site below.
+
+def uniform_ising(beta: float, block: int = 1, J: float = 1.0) -> np.ndarray:
+    """The 2D Ising uniform tensor after a block x block coarse-graining (App.
+    A): the block x block patch of sqrt-Boltzmann spin tensors contracted over
+    its internal bonds; each leg groups the block fine bonds leaving one side
+    (l and r ordered by fine row, u and d by fine column, the first most
+    significant), so a leg has dimension 2^block.  One tensor per block^2
+    spins: ln Z per tensor is block^2 times ln Z per spin."""
+    sw = ising_sqrt_boltzmann(beta, J)
+    spin = np.einsum("sa,sb,sc,sd->abcd", sw, sw, sw, sw)
+    lab = {}
+
+    def h(x, y):            # bond label right of spin (x, y); x = -1 is the l leg
+        return lab.setdefault(("h", x, y), len(lab))
+
+    def v(x, y):            # bond label below spin (x, y); y = -1 is the u leg
+        return lab.setdefault(("v", x, y), len(lab))
+    ops = []
+    for y in range(block):
+        for x in range(block):
+            ops += [spin, [h(x - 1, y), v(x, y - 1), h(x, y), v(x, y)]]
+    out = ([h(-1, y) for y in range(block)] + [v(x, -1) for x in range(block)]
+           + [h(block - 1, y) for y in range(block)] + [v(x, block - 1) for x in range(block)])
+    t = np.einsum(*ops, out, optimize="greedy")
+    D = 2 ** block
+    return np.ascontiguousarray(t.reshape(D, D, D, D))
+
+
+def uniform_random(chi: int, seed: int, dist: str = "u01+0.1") -> np.ndarray:
+    """A uniform tensor of bond dimension chi with entries drawn as
+    ``random_tensors`` draws them (one SplitMix64 stream, row-major)."""
+    n = chi ** 4
+    if dist == "u01+0.1":
+        vals = splitmix64_uniform(seed, n) + 0.1
+    elif dist == "n1,0.3":
+        vals = splitmix64_normal(seed, n, 1.0, 0.3)
+    else:
+        raise ValueError(dist)
+    return vals.reshape(chi, chi, chi, chi).copy()
+
+
+def uniform_product(a, b, c, e) -> np.ndarray:
+    """The rank-1 uniform tensor A[l,u,r,d] = a[l] b[u] c[r] e[d]: every bond
+    of its lattice is independent of the others."""
+    return np.einsum("i,j,k,l->ijkl", *(np.asarray(x, dtype=np.float64) for x in (a, b, c, e)))
