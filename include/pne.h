@@ -426,6 +426,78 @@ pne_status pne_rank_r_expand(pne_ctx *ctx, const pne_weights *w, int32_t rank, i
                              const int32_t *partition_ptr, const int32_t *partition_bonds, void *stream,
                              pne_result *out);
 
+/* ---- infinite lattices: the strip expansion ------------------------------ */
+
+/* Free energy density of an infinite, translation-invariant square-lattice
+ * network of one tensor A (Sec. IV.C).  A partition is the set of bonds cut
+ * by every L-th vertical line at one offset (L of them), or by every L-th
+ * horizontal line (L more); its projector is the rank-1 BP projector on
+ * every cut bond (Eq. A7, A8), which splits the lattice into strips whose
+ * cut legs are capped by the BP messages (scaled to unit overlap on every
+ * bond).  The expansion is the combinatorial form (Eq. A6) over the 2L
+ * partitions of one L x L cell, written per cell: every non-empty subset x
+ * contributes (-1)^{|x|+1} times its pieces over the cell --
+ *   vertical offsets V only:   prod over the gaps w of V of lambda_w^L,
+ *   horizontal offsets H only: prod over the gaps h of H of gamma_h^L,
+ *   both:                      prod over w, h of Z_wh,
+ * (gaps taken cyclically, summing to L) -- and f = -ln(sum) / L^2 per site
+ * (two_d = 0: vertical strips only, L partitions, f = -ln(sum) / L).
+ * lambda_k (gamma_k) is the leading eigenvalue of the row transfer matrix
+ * of a vertical (horizontal) strip k sites wide, Z_wh the value of a capped
+ * patch of w columns and h rows.  For L = 2 the sum is the paper's
+ * 2 lambda_2 - lambda_1^2 (1D) and R1 - R2 + R3 - R4 (2D); the width-3 sum is
+ * taken with the alternating signs of Eq. A6.
+ *
+ *   chi        bond dimension, 2 .. PNE_STRIP_MAX_CHI.
+ *   n_tensors  1 .. 65535 tensors evaluated independently (e.g. a temperature sweep).
+ *   A          [n_tensors][chi^4] doubles, each row-major over the legs
+ *              [l, u, r, d] (towards x - 1, y - 1, x + 1, y + 1); host memory
+ *              (A_on_device = 0) or device memory.
+ *   opts       L in 1 .. PNE_STRIP_MAX_L with chi^(L+1) <= 2^28; tolerances
+ *              and iteration limits (0 selects the default given beside each).
+ *   out        [n_tensors] host results.
+ * Method: uniform BP to bp_tol (parallel updates, FP64); each lambda_k by
+ * power iteration from the product of the incoming messages, the row
+ * transfer matrix applied site by site (FP64 multiply-adds) and the estimate
+ * the Rayleigh quotient, until lambda changes by less than eig_tol
+ * (relative) in three successive iterations (and at least L iterations, whose first L
+ * iterates, closed with the outgoing messages, give Z_k1 .. Z_kL); the 2^(2L)
+ * - 1 terms are summed as sign * expm1(ln term - L^2 ln z_BP) in double-double
+ * arithmetic (the signs sum to one).  Needs 2 (chi^L + chi^(L+1)) doubles of
+ * device memory per tensor in flight (tensors are processed in groups that fit
+ * a 24 GB working set).  Returns PNE_ENOCONV (results filled with the last
+ * estimates) when BP or a power iteration did not converge, PNE_EDEGENERATE
+ * when a message overlap vanishes or an eigenvalue estimate or the sum is not
+ * positive, PNE_EINVAL on bad arguments (nothing launched).  Synchronises
+ * `stream`. */
+#define PNE_STRIP_MAX_L 12
+#define PNE_STRIP_MAX_CHI 8
+typedef struct {
+    int32_t L;               /* strip width                                   */
+    int32_t two_d;           /* 1: vertical and horizontal strips; 0: vertical */
+    double bp_tol;           /* largest message change (0: 1e-14)             */
+    double eig_tol;          /* relative change of lambda (0: 1e-14)          */
+    int32_t bp_max_iter;     /* (0: 100000)                                   */
+    int32_t eig_max_iter;    /* power iterations per eigenvalue (0: 20000)    */
+} pne_strip_opts;
+
+typedef struct {
+    double f;                /* free energy per site of A's lattice           */
+    double f_bp;             /* -ln z_BP                                      */
+    double log_lambda[PNE_STRIP_MAX_L + 1];  /* [k] = ln lambda_k, k = 1..L   */
+    double log_gamma[PNE_STRIP_MAX_L + 1];   /* [k] = ln gamma_k (2D only)    */
+    double log_z[(PNE_STRIP_MAX_L + 1) * (PNE_STRIP_MAX_L + 1)];  /* [w*(MAX_L+1)+h] = ln|Z_wh| */
+    int32_t sign_z[(PNE_STRIP_MAX_L + 1) * (PNE_STRIP_MAX_L + 1)]; /* sign of Z_wh */
+    double messages[4 * PNE_STRIP_MAX_CHI];  /* mR, mL, mD, mU (chi each, unit overlaps) */
+    double eig_change;       /* largest last relative change of lambda over k */
+    int32_t bp_sweeps;       /* BP iterations                                 */
+    int32_t eig_iters;       /* largest power-iteration count over k          */
+    pne_status status;       /* this tensor's status                          */
+} pne_strip_result;
+
+pne_status pne_strip_expansion(pne_ctx *ctx, int32_t chi, int32_t n_tensors, const double *A, int32_t A_on_device,
+                               const pne_strip_opts *opts, void *stream, pne_strip_result *out);
+
 /* ---- belief propagation without device allocation ------------------------ */
 
 /* The paper has no counterpart to this call.  It is for callers that must not

@@ -27,6 +27,7 @@ __all__ = [
     "pne_batch_destroy", "BatchOpts", "pne_server_create", "pne_server_submit", "pne_server_poll",
     "pne_server_drain", "pne_server_stats", "pne_server_first_error", "pne_server_destroy", "ServerOpts", "RequestInfo",
     "Network", "PartitionOpts", "EnumOpts", "Result", "Context", "run", "network_struct",
+    "pne_strip_expansion", "StripOpts", "StripResult", "PNE_STRIP_MAX_L", "PNE_STRIP_MAX_CHI",
 ]
 
 PNE_OK, PNE_EINVAL, PNE_ENOMEM, PNE_ECUDA, PNE_ENOCONV, PNE_EDEGENERATE, PNE_ETIMEOUT, PNE_EOVERFLOW, PNE_EBUSY = range(9)
@@ -104,6 +105,37 @@ class RequestInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+PNE_STRIP_MAX_L, PNE_STRIP_MAX_CHI = 12, 8
+
+
+class StripOpts(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("two_d", ctypes.c_int32), ("bp_tol", ctypes.c_double),
+                ("eig_tol", ctypes.c_double), ("bp_max_iter", ctypes.c_int32), ("eig_max_iter", ctypes.c_int32)]
+
+
+_SM1 = PNE_STRIP_MAX_L + 1
+
+
+class StripResult(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_double), ("f_bp", ctypes.c_double),
+                ("log_lambda", ctypes.c_double * _SM1), ("log_gamma", ctypes.c_double * _SM1),
+                ("log_z", ctypes.c_double * (_SM1 * _SM1)), ("sign_z", ctypes.c_int32 * (_SM1 * _SM1)),
+                ("messages", ctypes.c_double * (4 * PNE_STRIP_MAX_CHI)), ("eig_change", ctypes.c_double),
+                ("bp_sweeps", ctypes.c_int32), ("eig_iters", ctypes.c_int32), ("status", ctypes.c_int)]
+
+    def as_dict(self, L, chi):
+        lz = np.ctypeslib.as_array(self.log_z).reshape(_SM1, _SM1)
+        sz = np.ctypeslib.as_array(self.sign_z).reshape(_SM1, _SM1)
+        msg = np.ctypeslib.as_array(self.messages).reshape(4, PNE_STRIP_MAX_CHI)[:, :chi]
+        return {"f": self.f, "f_bp": self.f_bp,
+                "log_lam": [None] + list(self.log_lambda[1:L + 1]),
+                "log_gam": [None] + list(self.log_gamma[1:L + 1]),
+                "log_z": [None] + [[None] + list(lz[w, 1:L + 1]) for w in range(1, L + 1)],
+                "sign_z": [None] + [[None] + [int(x) for x in sz[w, 1:L + 1]] for w in range(1, L + 1)],
+                "msgs": tuple(np.array(m) for m in msg), "eig_change": self.eig_change,
+                "bp_sweeps": self.bp_sweeps, "eig_iters": self.eig_iters, "status": self.status}
+
+
 class ProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -167,6 +199,9 @@ def load_library():
     lib.pne_rank_r_expand.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.c_void_p, vp, ctypes.POINTER(Result)]
     lib.pne_rank_r_expand.restype = ctypes.c_int
+    lib.pne_strip_expansion.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.POINTER(StripOpts), vp, ctypes.POINTER(StripResult)]
+    lib.pne_strip_expansion.restype = ctypes.c_int
     lib.pne_open_tensor.argtypes = [vp, vp, vp, ctypes.c_void_p, ctypes.c_void_p]
     lib.pne_open_tensor.restype = ctypes.c_int
     lib.pne_open_tensor_assemble.argtypes = [ctypes.POINTER(Result), ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
@@ -231,7 +266,7 @@ def exported_symbols() -> list:
              "pne_batch_n_results", "pne_batch_config", "pne_batch_destroy", "pne_server_create",
              "pne_server_submit", "pne_server_poll", "pne_server_drain", "pne_server_stats", "pne_server_first_error",
              "pne_server_destroy", "pne_weight_passing", "pne_weights_read", "pne_weights_destroy",
-             "pne_rank_r_expand"]
+             "pne_rank_r_expand", "pne_strip_expansion"]
     return [n for n in names if hasattr(lib, n)]
 
 
@@ -329,6 +364,33 @@ def pne_rank_r_expand(ctx, w, rank, form, partitions, n_sets, stream=None):
     _check(load_library().pne_rank_r_expand(ctx, w, int(rank), int(form), len(partitions), ptr.ctypes.data,
                                             bonds.ctypes.data, stream, out), ctx)
     return [r.as_dict() for r in out]
+
+
+def pne_strip_expansion(ctx, A, L, two_d=True, bp_tol=0.0, eig_tol=0.0, bp_max_iter=0, eig_max_iter=0,
+                        stream=None, allow_noconv=False):
+    """The infinite-lattice strip expansion (Sec. IV.C) of uniform tensors:
+    ``A`` a [n, chi, chi, chi, chi] (or one [chi]*4) host array or a CUDA
+    tensor; one result dict per tensor (log lists indexed from 1)."""
+    dev = hasattr(A, "data_ptr")
+    if dev:
+        if A.dim() == 4:
+            A = A.unsqueeze(0)
+        A = A.contiguous()
+        n, chi = int(A.shape[0]), int(A.shape[1])
+        ptr = A.data_ptr()
+    else:
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        if A.ndim == 4:
+            A = A[None]
+        n, chi = A.shape[0], A.shape[1]
+        ptr = A.ctypes.data
+    opts = StripOpts(int(L), 1 if two_d else 0, float(bp_tol), float(eig_tol), int(bp_max_iter), int(eig_max_iter))
+    out = (StripResult * n)()
+    st = load_library().pne_strip_expansion(ctx, int(chi), int(n), ptr, 1 if dev else 0, ctypes.byref(opts), stream,
+                                            out)
+    if not (st == PNE_ENOCONV and allow_noconv):
+        _check(st, ctx)
+    return [r.as_dict(int(L), int(chi)) for r in out]
 
 
 def pne_terms_destroy(t):

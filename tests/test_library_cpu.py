@@ -149,3 +149,26 @@ def test_open_tensor_assembly_keeps_huge_values_as_mantissa_and_scale():
     np.testing.assert_allclose(mant[1], [-math.exp(-2.0), math.exp(-1.0), 0.0, 1.0], rtol=1e-15)
     full = pne.open_tensor(pne.Results(arr), [n_open], n_sets)     # plain values: +-inf beyond range
     assert np.isinf(full[0]).all() and np.isfinite(full[1]).all()
+
+
+def test_strip_struct_layouts_match_the_header(tmp_path):
+    # the C compiler's sizes and offsets of the strip-expansion structs
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "lay.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pne.h"\nint main(void){\n'
+                   'printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pne_strip_opts), sizeof(pne_strip_result),\n'
+                   ' offsetof(pne_strip_result, log_z), offsetof(pne_strip_result, sign_z),\n'
+                   ' offsetof(pne_strip_result, messages), offsetof(pne_strip_result, eig_change),\n'
+                   ' offsetof(pne_strip_result, status), offsetof(pne_strip_opts, eig_max_iter));\nreturn 0;}\n')
+    exe = tmp_path / "lay"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    R, O = pne.StripResult, pne.StripOpts
+    want = [ctypes.sizeof(O), ctypes.sizeof(R), R.log_z.offset, R.sign_z.offset, R.messages.offset,
+            R.eig_change.offset, R.status.offset, O.eig_max_iter.offset]
+    assert got == want
