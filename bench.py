@@ -286,6 +286,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads measured beside the default line")
+    ap.add_argument("--extras", default="",
+                    help="comma-separated names of the extra workloads to run (default: all)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the served trace")
     ap.add_argument("--bp", default="ff", choices=["fp64", "ff"],
                     help="BP sweep arithmetic: FP64, or float-float pairs on the FP32 pipes")
@@ -445,7 +447,9 @@ def run_step_bench(args, wl, rank, world, local_rank):
         extras = {}
         for name, fn in (("cfg3_ising3d_8x8x8", run_cfg3), ("cfg4_batched", run_batched_extra),
                          ("cfg5_served", run_served_comparison), ("combinatorial_3x3", run_combinatorial_extra),
-                         ("rank_r_ising_sec5b", run_rank_r_extra)):
+                         ("rank_r_ising_sec5b", run_rank_r_extra), ("strips_infinite_ising", run_strip_extra)):
+            if args.extras and name not in args.extras.split(","):
+                continue
             t0 = time.perf_counter()
             try:
                 extras[name] = fn(args, ctx, pne, torch, dev, local_rank)
@@ -632,6 +636,71 @@ def run_rank_r_extra(args, ctx, pne, torch, dev, local_rank):
         errs = [abs(math.expm1(r["log_abs"] - e)) for r, e in zip(res, exact)]
         out[name] = {"ms_per_step": ms, "terms_per_s": res[0]["n_terms"] * len(nets) / (ms * 1e-3),
                      "max_rel_err_vs_exact": max(errs), "max_sweeps": int(np.max(sw))}
+    return out
+
+
+def _onsager_minus_beta_f(beta):
+    """Onsager's free energy per spin of the square-lattice Ising model (J = 1),
+    in its one-dimensional integral form: ln(2 cosh 2b) + (1/pi) int_0^{pi/2}
+    ln[(1 + sqrt(1 - k^2 sin^2 t)) / 2] dt with k = 2 sinh 2b / cosh^2 2b."""
+    from scipy.integrate import quad
+    k = 2 * math.sinh(2 * beta) / math.cosh(2 * beta) ** 2
+    v, _ = quad(lambda t: math.log((1 + math.sqrt(max(0.0, 1 - k * k * math.sin(t) ** 2))) / 2), 0, math.pi / 2,
+                epsabs=1e-15, epsrel=1e-15, limit=400)
+    return math.log(2 * math.cosh(2 * beta)) + v / math.pi
+
+
+def _strip_row_flops(chi, k):
+    """Multiply-adds of one row transfer application of width k (capped first
+    site chi -> chi^2, k - 2 middle sites chi^2 -> chi^2, last site chi^2 ->
+    chi; one chi x chi matrix for k = 1), times 2."""
+    if k == 1:
+        return 2 * chi * chi
+    return 2 * chi ** (k + 2) * (2 + (k - 2) * chi)
+
+
+def run_strip_extra(args, ctx, pne, torch, dev, local_rank):
+    """The infinite-lattice strip expansion (Sec. IV.C) of the 2D Ising model
+    after a 2 x 2 blocking (chi = 4): eight temperatures at strip width L = 10
+    in one call, float-float and FP64 row products, and one L = 12 call (24
+    spins wide) at one temperature; free energies against Onsager's."""
+    betas = [0.30, 0.36, 0.40, 0.42, 0.44, 0.46, 0.50, 0.60]
+    A = np.stack([I.uniform_ising(b, 2) for b in betas])
+    exact = [-4.0 * _onsager_minus_beta_f(b) for b in betas]
+    peak64 = pne.pne_measure_fma_peak(ctx.h, pne.PNE_F64, None)
+    peak32 = pne.pne_measure_fma_peak(ctx.h, pne.PNE_F32, None)
+    out = {"workload": "infinite 2D Ising, 2x2 blocked (chi = 4), 2D strip expansion; 8 temperatures "
+                       "beta in {0.30..0.60} per call at L = 10 (20 spins wide), one call at L = 12 (24 spins)",
+           "reference": "Onsager's free energy (one-dimensional integral form), 4 spins per blocked site"}
+    for L, sel, tag in ((10, list(range(len(betas))), "L10_8_temperatures"), (12, [4], "L12_beta0.44")):
+        for arith, aname in ((1, "ff"), (0, "fp64")):
+            if L == 12 and arith == 0:
+                continue
+            pne.pne_ctx_profile(ctx.h, True)
+            t0 = time.perf_counter()
+            res = pne.pne_strip_expansion(ctx.h, A[sel], L, arithmetic=arith, allow_noconv=True)
+            wall = time.perf_counter() - t0
+            prof = {k: v for k, v in pne.pne_ctx_profile_read(ctx.h).items() if not k.startswith("host:")}
+            pne.pne_ctx_profile(ctx.h, False)
+            flops = sum(r["iters"][o][k] * _strip_row_flops(4, k) for r in res for o in (0, 1) for k in range(1, L + 1))
+            row_ms = prof.get("strip_row", (0, 0.0))[1]
+            peak = peak64 if arith == 0 else peak32 / 12.0
+            rec = {"wall_s": wall, "kernel_ms": {k: round(v[1], 3) for k, v in prof.items()},
+                   "max_rel_err_vs_onsager": max(abs(r["f"] - exact[i]) / abs(exact[i]) for i, r in zip(sel, res)),
+                   "rel_err_by_beta": {f"{betas[i]:.2f}": abs(r["f"] - exact[i]) / abs(exact[i])
+                                       for i, r in zip(sel, res)},
+                   "bp_rel_err_by_beta": {f"{betas[i]:.2f}": abs(r["f_bp"] - exact[i]) / abs(exact[i])
+                                          for i, r in zip(sel, res)},
+                   "max_power_iterations": max(r["eig_iters"] for r in res),
+                   "status": sorted({int(r["status"]) for r in res}),
+                   "row_products": {"bound": "alu", "unit": "TFLOP/s", "achieved": flops / (row_ms * 1e-3) / 1e12,
+                                    "peak": peak / 1e12, "frac": flops / (row_ms * 1e-3) / peak if row_ms else None,
+                                    "work": "2 flops per multiply-add of the site-by-site row products, summed over "
+                                            "every power iteration of every width and orientation",
+                                    "peak_source": ("measured FP64 FMA-chain kernel" if arith == 0 else
+                                                    "measured FP32 FMA-chain kernel / 12 FP32 instructions per "
+                                                    "float-float multiply-add")}}
+            out[f"{tag}_{aname}"] = rec
     return out
 
 

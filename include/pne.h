@@ -479,6 +479,10 @@ typedef struct {
     double eig_tol;          /* relative change of lambda (0: 1e-14)          */
     int32_t bp_max_iter;     /* (0: 100000)                                   */
     int32_t eig_max_iter;    /* power iterations per eigenvalue (0: 20000)    */
+    int32_t arithmetic;      /* row transfer products: 0 FP64 multiply-adds,
+                                1 float-float (compensated FP32 dot products,
+                                ~2^-48 relative per site; FP64 storage of the
+                                iterates, FP64 reductions and sums)           */
 } pne_strip_opts;
 
 typedef struct {
@@ -493,6 +497,8 @@ typedef struct {
     int32_t bp_sweeps;       /* BP iterations                                 */
     int32_t eig_iters;       /* largest power-iteration count over k          */
     pne_status status;       /* this tensor's status                          */
+    int32_t iters[2 * (PNE_STRIP_MAX_L + 1)];  /* [o*(MAX_L+1)+k]: power iterations of
+                                                  width k, o = 0 vertical, 1 horizontal */
 } pne_strip_result;
 
 pne_status pne_strip_expansion(pne_ctx *ctx, int32_t chi, int32_t n_tensors, const double *A, int32_t A_on_device,

@@ -238,32 +238,102 @@ struct ApplyParams {
 };
 
 // out[p][o][s] = sum_i mat[o][i] * in[p][i][s] (* scale): one site of the row.
-template <int NIN, int NOUT>
+// IN / OUT formats: 0 FP64, 1 float-float pair (hi, lo) in the same 8 bytes.
+// With FF the multiply-adds run on the FP32 pipes as compensated dot products
+// (each product split exactly by one FMA, the running sum by Knuth's two-sum,
+// the error terms and the low-part cross products gathered in one FP32
+// compensation): about 2^-48 relative to sum |a x| per output, where the FP64
+// pipe of this part retires 1/60 of the FP32 rate.
+struct ffp { float h, l; };
+
+__device__ __forceinline__ ffp split_double(double x)
+{
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+
+template <int NIN, int NOUT, int IN_FF, int OUT_FF>
 __global__ void __launch_bounds__(kThreads) strip_apply_kernel(ApplyParams p)
 {
     const int b = blockIdx.y;
     if (p.st[b].done) return;
-    __shared__ double M[NOUT * NIN];
+    constexpr bool FF = IN_FF || OUT_FF;
+    __shared__ double M[FF ? 1 : NOUT * NIN];
+    __shared__ float Mh[FF ? NOUT * NIN : 1], Ml[FF ? NOUT * NIN : 1];
     const double *mat = p.ops + b * p.ops_stride + p.mat_off;
-    for (int i = threadIdx.x; i < NOUT * NIN; i += blockDim.x) M[i] = mat[i];
+    for (int i = threadIdx.x; i < NOUT * NIN; i += blockDim.x) {
+        if (FF) {
+            const ffp a = split_double(mat[i]);
+            Mh[i] = a.h;
+            Ml[i] = a.l;
+        } else {
+            M[i] = mat[i];
+        }
+    }
     __syncthreads();
     const double sc = p.use_scale ? p.st[b].scale : 1.0;
-    const double *in = p.in + b * p.in_stride;
-    double *out = p.out + b * p.out_stride;
     const int64_t units = p.P * p.S;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < units; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t pp = q / p.S, s = q - pp * p.S;
-        const double *src = in + pp * NIN * p.S + s;
-        double x[NIN];
+        const int64_t src0 = (pp * NIN) * p.S + s, dst0 = (pp * NOUT) * p.S + s;
+        if (!FF) {
+            const double *in = p.in + b * p.in_stride + src0;
+            double *out = p.out + b * p.out_stride + dst0;
+            double x[NIN];
 #pragma unroll
-        for (int i = 0; i < NIN; ++i) x[i] = __ldg(src + i * p.S) * sc;
-        double *dst = out + pp * NOUT * p.S + s;
+            for (int i = 0; i < NIN; ++i) x[i] = __ldg(in + i * p.S) * sc;
 #pragma unroll 4
-        for (int o = 0; o < NOUT; ++o) {
-            double acc = 0.0;
+            for (int o = 0; o < NOUT; ++o) {
+                double acc = 0.0;
 #pragma unroll
-            for (int i = 0; i < NIN; ++i) acc = fma(M[o * NIN + i], x[i], acc);
-            dst[o * p.S] = acc;
+                for (int i = 0; i < NIN; ++i) acc = fma(M[o * NIN + i], x[i], acc);
+                out[o * p.S] = acc;
+            }
+        } else {
+            float xh[NIN], xl[NIN];
+            if (IN_FF) {
+                const float2 *in = reinterpret_cast<const float2 *>(p.in + b * p.in_stride) + src0;
+#pragma unroll
+                for (int i = 0; i < NIN; ++i) {
+                    const float2 v = __ldg(in + i * p.S);
+                    xh[i] = v.x;
+                    xl[i] = v.y;
+                }
+            } else {
+                const double *in = p.in + b * p.in_stride + src0;
+#pragma unroll
+                for (int i = 0; i < NIN; ++i) {
+                    const ffp v = split_double(__ldg(in + i * p.S) * sc);
+                    xh[i] = v.h;
+                    xl[i] = v.l;
+                }
+            }
+#pragma unroll 2
+            for (int o = 0; o < NOUT; ++o) {
+                float sh = 0.f, c = 0.f;
+#pragma unroll
+                for (int i = 0; i < NIN; ++i) {
+                    const float ah = Mh[o * NIN + i], al = Ml[o * NIN + i];
+                    const float pr = __fmul_rn(ah, xh[i]);
+                    const float e = __fmaf_rn(ah, xh[i], -pr);
+                    const float t = __fadd_rn(sh, pr);
+                    const float bb = __fsub_rn(t, sh);
+                    const float q2 = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(pr, bb));
+                    sh = t;
+                    c = __fadd_rn(c, __fadd_rn(q2, e));
+                    c = __fmaf_rn(ah, xl[i], c);
+                    c = __fmaf_rn(al, xh[i], c);
+                }
+                const float hi = __fadd_rn(sh, c);
+                const float lo = __fsub_rn(c, __fsub_rn(hi, sh));
+                if (OUT_FF) {
+                    float2 *out = reinterpret_cast<float2 *>(p.out + b * p.out_stride) + dst0;
+                    out[o * p.S] = make_float2(hi, lo);
+                } else {
+                    double *out = p.out + b * p.out_stride + dst0;
+                    out[o * p.S] = (double)hi + (double)lo;
+                }
+            }
         }
     }
 }
@@ -326,7 +396,10 @@ __device__ __forceinline__ void block_sum3(double &a, double &b, double &c, doub
     }
 }
 
-// per block: sum w^2, sum v w, sum w * capBot^{(x)k}
+// per block: sum w^2, sum v w, sum w * capBot^{(x)k}.  The cap product of an
+// index is looked up per group of g base-chi digits (chi^g <= 256 entries, a
+// shorter table for the last r = k mod g digits): a few FP64 multiplies per
+// entry instead of k.
 __global__ void __launch_bounds__(kThreads) strip_reduce_kernel(const double *V, const double *W, int64_t stride,
                                                                 const double *ops, int64_t ops_stride,
                                                                 int64_t bot_off, int chi, int k, int64_t N,
@@ -336,7 +409,35 @@ __global__ void __launch_bounds__(kThreads) strip_reduce_kernel(const double *V,
     if (st[b].done) return;
     __shared__ double sh[3 * (kThreads / 32)];
     __shared__ double bot[kMaxChi];
+    __shared__ double tabF[256], tabP[256];
+    int g = 1, cg = chi;
+    while (cg * chi <= 256) {
+        cg *= chi;
+        ++g;
+    }
+    const int ng = k / g, r = k - ng * g;
+    int cr = 1;
+    for (int i = 0; i < r; ++i) cr *= chi;
     if (threadIdx.x < chi) bot[threadIdx.x] = ops[b * ops_stride + bot_off + threadIdx.x];
+    __syncthreads();
+    for (int j = threadIdx.x; j < cg; j += blockDim.x) {
+        double x = 1.0;
+        int t = j;
+        for (int i = 0; i < g; ++i) {
+            x *= bot[t % chi];
+            t /= chi;
+        }
+        tabF[j] = x;
+        if (j < cr) {
+            double y = 1.0;
+            t = j;
+            for (int i = 0; i < r; ++i) {
+                y *= bot[t % chi];
+                t /= chi;
+            }
+            tabP[j] = y;
+        }
+    }
     __syncthreads();
     const double *v = V + b * stride, *w = W + b * stride;
     double ww = 0.0, vw = 0.0, wc = 0.0;
@@ -344,11 +445,12 @@ __global__ void __launch_bounds__(kThreads) strip_reduce_kernel(const double *V,
         const double x = w[q];
         ww = fma(x, x, ww);
         vw = fma(v[q], x, vw);
-        int64_t r = q;
-        double c = 1.0;
-        for (int i = 0; i < k; ++i) {
-            c *= bot[r % chi];
-            r /= chi;
+        int64_t t = q;
+        double c = r ? tabP[t % cr] : 1.0;
+        if (r) t /= cr;
+        for (int i = 0; i < ng; ++i) {
+            c *= tabF[t % cg];
+            t /= cg;
         }
         wc = fma(x, c, wc);
     }
@@ -591,38 +693,40 @@ __global__ void strip_sum_finish_kernel(const double *part, int nblk, const doub
     status[b] = 0;
 }
 
-template <int NIN, int NOUT>
+template <int NIN, int NOUT, int IN_FF, int OUT_FF>
 cudaError_t launch_apply(const ApplyParams &p, int n, cudaStream_t s)
 {
     const int64_t units = p.P * p.S;
     int64_t blocks = (units + kThreads - 1) / kThreads;
     blocks = std::min<int64_t>(std::max<int64_t>(blocks, 1), 152 * 16);
-    strip_apply_kernel<NIN, NOUT><<<dim3((unsigned)blocks, (unsigned)n), kThreads, 0, s>>>(p);
+    strip_apply_kernel<NIN, NOUT, IN_FF, OUT_FF><<<dim3((unsigned)blocks, (unsigned)n), kThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 
+// shape 0 one-site strip, 1 first site, 2 middle site, 3 last site; ff: the
+// running tensor between the first and the last site is float-float
 template <int CHI>
-cudaError_t apply_shape(int shape, const ApplyParams &p, int n, cudaStream_t s)
+cudaError_t apply_shape(int shape, int ff, const ApplyParams &p, int n, cudaStream_t s)
 {
     constexpr int C2 = CHI * CHI;
     switch (shape) {
-    case 0: return launch_apply<CHI, CHI>(p, n, s);      // one-site strip
-    case 1: return launch_apply<CHI, C2>(p, n, s);       // first site
-    case 2: return launch_apply<C2, C2>(p, n, s);        // middle site
-    default: return launch_apply<C2, CHI>(p, n, s);      // last site
+    case 0: return launch_apply<CHI, CHI, 0, 0>(p, n, s);
+    case 1: return ff ? launch_apply<CHI, C2, 0, 1>(p, n, s) : launch_apply<CHI, C2, 0, 0>(p, n, s);
+    case 2: return ff ? launch_apply<C2, C2, 1, 1>(p, n, s) : launch_apply<C2, C2, 0, 0>(p, n, s);
+    default: return ff ? launch_apply<C2, CHI, 1, 0>(p, n, s) : launch_apply<C2, CHI, 0, 0>(p, n, s);
     }
 }
 
-cudaError_t apply_site(int chi, int shape, const ApplyParams &p, int n, cudaStream_t s)
+cudaError_t apply_site(int chi, int shape, int ff, const ApplyParams &p, int n, cudaStream_t s)
 {
     switch (chi) {
-    case 2: return apply_shape<2>(shape, p, n, s);
-    case 3: return apply_shape<3>(shape, p, n, s);
-    case 4: return apply_shape<4>(shape, p, n, s);
-    case 5: return apply_shape<5>(shape, p, n, s);
-    case 6: return apply_shape<6>(shape, p, n, s);
-    case 7: return apply_shape<7>(shape, p, n, s);
-    default: return apply_shape<8>(shape, p, n, s);
+    case 2: return apply_shape<2>(shape, ff, p, n, s);
+    case 3: return apply_shape<3>(shape, ff, p, n, s);
+    case 4: return apply_shape<4>(shape, ff, p, n, s);
+    case 5: return apply_shape<5>(shape, ff, p, n, s);
+    case 6: return apply_shape<6>(shape, ff, p, n, s);
+    case 7: return apply_shape<7>(shape, ff, p, n, s);
+    default: return apply_shape<8>(shape, ff, p, n, s);
     }
 }
 
@@ -652,6 +756,8 @@ pne_status pne_strip_expansion(pne_ctx *ctx, int32_t chi, int32_t n_tensors, con
     const double eig_tol = opts->eig_tol > 0 ? opts->eig_tol : 1e-14;
     const int bp_max = opts->bp_max_iter > 0 ? opts->bp_max_iter : 100000;
     const int eig_max = std::max(L, opts->eig_max_iter > 0 ? opts->eig_max_iter : 20000);
+    if (opts->arithmetic != 0 && opts->arithmetic != 1) return bad("arithmetic must be 0 (FP64) or 1 (float-float)");
+    const int ff = opts->arithmetic;
     cudaStream_t s = (cudaStream_t)stream;
     const int n = n_tensors;
     const OpsLayout lay(chi);
@@ -760,7 +866,7 @@ pne_status pne_strip_expansion(pne_ctx *ctx, int32_t chi, int32_t n_tensors, con
                             ap.mat_off = orient + lay.T1;
                             ap.use_scale = 1;
                             ap.P = 1; ap.S = 1;
-                            if ((e = apply_site(chi, 0, ap, gn, s)) != cudaSuccess) return cuda_fail(e, "strip_apply");
+                            if ((e = apply_site(chi, 0, 0, ap, gn, s)) != cudaSuccess) return cuda_fail(e, "strip_apply");
                         } else {
                             // site j maps [chi^j][pair][chi^(k-1-j)]; V -> X -> Y -> X ... -> W
                             const double *cur = V;
@@ -777,7 +883,7 @@ pne_status pne_strip_expansion(pne_ctx *ctx, int32_t chi, int32_t n_tensors, con
                                 ap.S = cpow[k - 1 - j];
                                 const int shape = j == 0 ? 1 : (last ? 3 : 2);
                                 ap.mat_off = orient + (j == 0 ? lay.F : (last ? lay.G : lay.M));
-                                if ((e = apply_site(chi, shape, ap, gn, s)) != cudaSuccess)
+                                if ((e = apply_site(chi, shape, ff, ap, gn, s)) != cudaSuccess)
                                     return cuda_fail(e, "strip_apply");
                                 cur = nxt;
                                 cur_stride = ap.out_stride;
@@ -851,6 +957,7 @@ pne_status pne_strip_expansion(pne_ctx *ctx, int32_t chi, int32_t n_tensors, con
                 (o == 0 ? r.log_lambda : r.log_gamma)[k] = kr.log_lam;
                 r.eig_change = std::max(r.eig_change, kr.change);
                 r.eig_iters = std::max(r.eig_iters, kr.iters);
+                r.iters[o * (kMaxL + 1) + k] = kr.iters;
                 if (kr.status == 2) sb = PNE_EDEGENERATE;
                 else if (kr.status == 1 && sb == PNE_OK) sb = PNE_ENOCONV;
                 if (o == 0)

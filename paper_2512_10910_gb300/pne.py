@@ -110,7 +110,8 @@ PNE_STRIP_MAX_L, PNE_STRIP_MAX_CHI = 12, 8
 
 class StripOpts(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("two_d", ctypes.c_int32), ("bp_tol", ctypes.c_double),
-                ("eig_tol", ctypes.c_double), ("bp_max_iter", ctypes.c_int32), ("eig_max_iter", ctypes.c_int32)]
+                ("eig_tol", ctypes.c_double), ("bp_max_iter", ctypes.c_int32), ("eig_max_iter", ctypes.c_int32),
+                ("arithmetic", ctypes.c_int32)]
 
 
 _SM1 = PNE_STRIP_MAX_L + 1
@@ -121,7 +122,8 @@ class StripResult(ctypes.Structure):
                 ("log_lambda", ctypes.c_double * _SM1), ("log_gamma", ctypes.c_double * _SM1),
                 ("log_z", ctypes.c_double * (_SM1 * _SM1)), ("sign_z", ctypes.c_int32 * (_SM1 * _SM1)),
                 ("messages", ctypes.c_double * (4 * PNE_STRIP_MAX_CHI)), ("eig_change", ctypes.c_double),
-                ("bp_sweeps", ctypes.c_int32), ("eig_iters", ctypes.c_int32), ("status", ctypes.c_int)]
+                ("bp_sweeps", ctypes.c_int32), ("eig_iters", ctypes.c_int32), ("status", ctypes.c_int),
+                ("iters", ctypes.c_int32 * (2 * _SM1))]
 
     def as_dict(self, L, chi):
         lz = np.ctypeslib.as_array(self.log_z).reshape(_SM1, _SM1)
@@ -133,7 +135,8 @@ class StripResult(ctypes.Structure):
                 "log_z": [None] + [[None] + list(lz[w, 1:L + 1]) for w in range(1, L + 1)],
                 "sign_z": [None] + [[None] + [int(x) for x in sz[w, 1:L + 1]] for w in range(1, L + 1)],
                 "msgs": tuple(np.array(m) for m in msg), "eig_change": self.eig_change,
-                "bp_sweeps": self.bp_sweeps, "eig_iters": self.eig_iters, "status": self.status}
+                "bp_sweeps": self.bp_sweeps, "eig_iters": self.eig_iters, "status": self.status,
+                "iters": [list(self.iters[0:L + 1]), list(self.iters[_SM1:_SM1 + L + 1])]}
 
 
 class ProfileEntry(ctypes.Structure):
@@ -367,7 +370,7 @@ def pne_rank_r_expand(ctx, w, rank, form, partitions, n_sets, stream=None):
 
 
 def pne_strip_expansion(ctx, A, L, two_d=True, bp_tol=0.0, eig_tol=0.0, bp_max_iter=0, eig_max_iter=0,
-                        stream=None, allow_noconv=False):
+                        arithmetic=0, stream=None, allow_noconv=False):
     """The infinite-lattice strip expansion (Sec. IV.C) of uniform tensors:
     ``A`` a [n, chi, chi, chi, chi] (or one [chi]*4) host array or a CUDA
     tensor; one result dict per tensor (log lists indexed from 1)."""
@@ -384,7 +387,8 @@ def pne_strip_expansion(ctx, A, L, two_d=True, bp_tol=0.0, eig_tol=0.0, bp_max_i
             A = A[None]
         n, chi = A.shape[0], A.shape[1]
         ptr = A.ctypes.data
-    opts = StripOpts(int(L), 1 if two_d else 0, float(bp_tol), float(eig_tol), int(bp_max_iter), int(eig_max_iter))
+    opts = StripOpts(int(L), 1 if two_d else 0, float(bp_tol), float(eig_tol), int(bp_max_iter), int(eig_max_iter),
+                     int(arithmetic))
     out = (StripResult * n)()
     st = load_library().pne_strip_expansion(ctx, int(chi), int(n), ptr, 1 if dev else 0, ctypes.byref(opts), stream,
                                             out)

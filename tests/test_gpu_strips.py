@@ -56,23 +56,40 @@ def _check(res, ref, L, two_d=True):
     assert abs(res["f"] - ref["f"]) <= 1e-10 * abs(ref["f"]), (res["f"], ref["f"])
 
 
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp64", "ff"])
 @pytest.mark.parametrize("L", [1, 2, 4])
-def test_strip_expansion_matches_oracle_2d(ctx, L):
+def test_strip_expansion_matches_oracle_2d(ctx, L, arith):
     # every tensor of one chi in one call (data-parallel over the tensors)
     groups = {}
     for name, A in _tensors():
         groups.setdefault(A.shape[0], []).append((name, A))
     for chi, items in groups.items():
-        res = pne.pne_strip_expansion(ctx.h, np.stack([A for _, A in items]), L)
+        res = pne.pne_strip_expansion(ctx.h, np.stack([A for _, A in items]), L, arithmetic=arith)
         for (name, A), r in zip(items, res):
             assert r["status"] == pne.PNE_OK, name
             _check(r, S.strip_expansion(A, L), L)
 
 
-def test_strip_expansion_matches_oracle_width5(ctx):
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp64", "ff"])
+def test_strip_expansion_matches_oracle_width5(ctx, arith):
     A = I.uniform_ising(0.42, 2)
-    (r,) = pne.pne_strip_expansion(ctx.h, A, 5)
+    (r,) = pne.pne_strip_expansion(ctx.h, A, 5, arithmetic=arith)
     _check(r, S.strip_expansion(A, 5), 5)
+
+
+def test_float_float_rows_agree_with_fp64_at_width8(ctx):
+    # the two arithmetics of the row products, beyond the oracle's widths
+    A = np.stack([I.uniform_ising(b, 2) for b in (0.35, 0.44)] + [I.uniform_random(4, 3)])
+    r64 = pne.pne_strip_expansion(ctx.h, A, 8, arithmetic=0)
+    rff = pne.pne_strip_expansion(ctx.h, A, 8, arithmetic=1)
+    for a, b in zip(r64, rff):
+        for k in range(1, 9):
+            assert abs(a["log_lam"][k] - b["log_lam"][k]) < 1e-11
+            assert abs(a["log_gam"][k] - b["log_gam"][k]) < 1e-11
+            for h in range(1, 9):
+                assert abs(a["log_z"][k][h] - b["log_z"][k][h]) < 1e-11
+        assert abs(a["f"] - b["f"]) <= 1e-11 * abs(a["f"])
+        assert all(x >= 8 for x in a["iters"][0][1:]) and all(x >= 8 for x in b["iters"][1][1:])
 
 
 def test_one_dimensional_form_matches_oracle(ctx):
@@ -105,7 +122,7 @@ def test_wide_strips_approach_onsager(ctx):
     # oracle's, and the error against Onsager keeps falling with L
     betas = (0.30, 0.42, 0.60)
     A = np.stack([I.uniform_ising(b, 2) for b in betas])
-    res10 = pne.pne_strip_expansion(ctx.h, A, 10)
+    res10 = pne.pne_strip_expansion(ctx.h, A, 10, arithmetic=1)
     for beta, r in zip(betas, res10):
         exact = -4.0 * X.onsager_minus_beta_f(beta)
         ref = S.strip_expansion(I.uniform_ising(beta, 2), 4)

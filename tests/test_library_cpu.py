@@ -164,11 +164,11 @@ def test_strip_struct_layouts_match_the_header(tmp_path):
                    'printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pne_strip_opts), sizeof(pne_strip_result),\n'
                    ' offsetof(pne_strip_result, log_z), offsetof(pne_strip_result, sign_z),\n'
                    ' offsetof(pne_strip_result, messages), offsetof(pne_strip_result, eig_change),\n'
-                   ' offsetof(pne_strip_result, status), offsetof(pne_strip_opts, eig_max_iter));\nreturn 0;}\n')
+                   ' offsetof(pne_strip_result, iters), offsetof(pne_strip_opts, arithmetic));\nreturn 0;}\n')
     exe = tmp_path / "lay"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     R, O = pne.StripResult, pne.StripOpts
     want = [ctypes.sizeof(O), ctypes.sizeof(R), R.log_z.offset, R.sign_z.offset, R.messages.offset,
-            R.eig_change.offset, R.status.offset, O.eig_max_iter.offset]
+            R.eig_change.offset, R.iters.offset, O.arithmetic.offset]
     assert got == want
