@@ -504,6 +504,50 @@ typedef struct {
 pne_status pne_strip_expansion(pne_ctx *ctx, int32_t chi, int32_t n_tensors, const double *A, int32_t A_on_device,
                                const pne_strip_opts *opts, void *stream, pne_strip_result *out);
 
+/* ---- dense contractions of blocked large-chi networks (tensor cores) ----- */
+
+/* Batched dense product C[b] = A[b] B[b]^T on the device: A [M][K] (row stride
+ * lda), B [N][K] (row stride ldb), C [M][N] (row stride ldc), set b at
+ * offsets b * stride*.  All device pointers.
+ *   PNE_TF32 / PNE_BF16: A, B, C FP32; the inputs rounded to TF32 (nearest,
+ *     ties away) or BF16 (nearest-even) and multiplied on the 5th-generation
+ *     tensor cores (tcgen05.mma, M = 128 tiles, N <= 256 per tile) with FP32
+ *     accumulation in tensor memory: |error| <= (2 u_in + K 2^-24) sum_k |a b|
+ *     to first order, u_in = 2^-11 (TF32) or 2^-8 (BF16).
+ *   PNE_F64: A, B, C FP64, FP64 multiply-adds on the CUDA cores.
+ * This is the primitive of pne_grid_contract.  Returns PNE_EINVAL on bad
+ * sizes (batch 1..65535, M, N, K >= 1, lda, ldb >= K, ldc >= N) or PNE_F32,
+ * PNE_ETIMEOUT if a tensor-core stage wait gave up (bounded at about 2 s).
+ * Synchronises `stream`. */
+pne_status pne_dense_gemm(pne_ctx *ctx, pne_dtype dtype, int32_t batch, int32_t M, int32_t N, int32_t K,
+                          const void *A, int64_t lda, int64_t strideA, const void *B, int64_t ldb, int64_t strideB,
+                          void *C, int64_t ldc, int64_t strideC, void *stream);
+
+/* Exact contraction (Eq. A1) of a closed 2D grid network: the lattices the
+ * paper coarse-grains into bond dimension chi = 16 or 64 (App. A) and
+ * contracts exactly as the reference of its benchmarks and as the terms of
+ * its expansions (Sec. III, Sec. IV.A).  Sites are an lx x ly grid, site id =
+ * y * lx + x, and every bond joins grid neighbours (each neighbour pair by
+ * exactly one bond, any dimension 1..4096); n_batch tensor sets, FP64 data on
+ * the host or the device as for pne_build_partition.  The grid is contracted
+ * row by row; absorbing a site is one dense product of the running tensor
+ * (rows: its legs other than the site's up and left legs) with the site's
+ * [down, right] x [up, left] matrix, scaled to a largest entry in [1, 2) by a
+ * power of two each step (kept exactly in a log scale).
+ *   dtype  PNE_F64 (FP64 products on the CUDA cores), PNE_TF32 or PNE_BF16
+ *          (products on the tensor cores, FP32 running tensor and
+ *          accumulation); PNE_F32 is rejected.
+ *   out    [n_batch]: sign, log_abs, value of Z; err_bound = the first-order
+ *          bound sum over sites of (2 u_in + K_site u_acc) on |error| / Z_abs,
+ *          Z_abs the contraction of |T| (= |Z| for non-negative networks);
+ *          n_terms = 1, c[0] = 1.
+ * The running tensor holds at most prod of the open vertical bonds of a row
+ * times two horizontal ones; PNE_EINVAL when the batch's running tensors would
+ * exceed 64 GB, or on a network that is not such a grid.  Synchronises
+ * `stream`. */
+pne_status pne_grid_contract(pne_ctx *ctx, const pne_network *net, int32_t lx, int32_t ly, pne_dtype dtype,
+                             void *stream, pne_result *out);
+
 /* ---- belief propagation without device allocation ------------------------ */
 
 /* The paper has no counterpart to this call.  It is for callers that must not

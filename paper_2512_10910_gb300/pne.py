@@ -28,6 +28,7 @@ __all__ = [
     "pne_server_drain", "pne_server_stats", "pne_server_first_error", "pne_server_destroy", "ServerOpts", "RequestInfo",
     "Network", "PartitionOpts", "EnumOpts", "Result", "Context", "run", "network_struct",
     "pne_strip_expansion", "StripOpts", "StripResult", "PNE_STRIP_MAX_L", "PNE_STRIP_MAX_CHI",
+    "pne_dense_gemm", "pne_grid_contract",
 ]
 
 PNE_OK, PNE_EINVAL, PNE_ENOMEM, PNE_ECUDA, PNE_ENOCONV, PNE_EDEGENERATE, PNE_ETIMEOUT, PNE_EOVERFLOW, PNE_EBUSY = range(9)
@@ -205,6 +206,13 @@ def load_library():
     lib.pne_strip_expansion.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
                                         ctypes.POINTER(StripOpts), vp, ctypes.POINTER(StripResult)]
     lib.pne_strip_expansion.restype = ctypes.c_int
+    lib.pne_dense_gemm.argtypes = [vp, ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, vp]
+    lib.pne_dense_gemm.restype = ctypes.c_int
+    lib.pne_grid_contract.argtypes = [vp, ctypes.POINTER(Network), ctypes.c_int32, ctypes.c_int32, ctypes.c_int, vp,
+                                      ctypes.POINTER(Result)]
+    lib.pne_grid_contract.restype = ctypes.c_int
     lib.pne_open_tensor.argtypes = [vp, vp, vp, ctypes.c_void_p, ctypes.c_void_p]
     lib.pne_open_tensor.restype = ctypes.c_int
     lib.pne_open_tensor_assemble.argtypes = [ctypes.POINTER(Result), ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
@@ -269,7 +277,7 @@ def exported_symbols() -> list:
              "pne_batch_n_results", "pne_batch_config", "pne_batch_destroy", "pne_server_create",
              "pne_server_submit", "pne_server_poll", "pne_server_drain", "pne_server_stats", "pne_server_first_error",
              "pne_server_destroy", "pne_weight_passing", "pne_weights_read", "pne_weights_destroy",
-             "pne_rank_r_expand", "pne_strip_expansion"]
+             "pne_rank_r_expand", "pne_strip_expansion", "pne_dense_gemm", "pne_grid_contract"]
     return [n for n in names if hasattr(lib, n)]
 
 
@@ -395,6 +403,27 @@ def pne_strip_expansion(ctx, A, L, two_d=True, bp_tol=0.0, eig_tol=0.0, bp_max_i
     if not (st == PNE_ENOCONV and allow_noconv):
         _check(st, ctx)
     return [r.as_dict(int(L), int(chi)) for r in out]
+
+
+def pne_dense_gemm(ctx, dtype, A, B, C, stream=None):
+    """C[b] = A[b] B[b]^T for CUDA tensors A [batch, M, K], B [batch, N, K],
+    C [batch, M, N] (FP32 for TF32/BF16, FP64 for F64; contiguous rows)."""
+    batch, M, K = (int(x) for x in A.shape)
+    N = int(B.shape[1])
+    _check(load_library().pne_dense_gemm(ctx, int(dtype), batch, M, N, K, A.data_ptr(), A.stride(1), A.stride(0),
+                                         B.data_ptr(), B.stride(1), B.stride(0), C.data_ptr(), C.stride(1),
+                                         C.stride(0), stream), ctx)
+
+
+def pne_grid_contract(ctx, net, lx, ly, dtype, data=None, n_batch=None, stream=None):
+    """Exact contraction of a closed lx x ly grid network (site id = y * lx +
+    x); one result dict per tensor set."""
+    ns, keep = network_struct(net, data=data, n_batch=n_batch or 1)
+    nb = int(ns.n_batch)
+    out = (Result * nb)()
+    _check(load_library().pne_grid_contract(ctx, ctypes.byref(ns), int(lx), int(ly), int(dtype), stream, out), ctx)
+    del keep
+    return [r.as_dict() for r in out]
 
 
 def pne_terms_destroy(t):
