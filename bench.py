@@ -447,7 +447,8 @@ def run_step_bench(args, wl, rank, world, local_rank):
         extras = {}
         for name, fn in (("cfg3_ising3d_8x8x8", run_cfg3), ("cfg4_batched", run_batched_extra),
                          ("cfg5_served", run_served_comparison), ("combinatorial_3x3", run_combinatorial_extra),
-                         ("rank_r_ising_sec5b", run_rank_r_extra), ("strips_infinite_ising", run_strip_extra)):
+                         ("rank_r_ising_sec5b", run_rank_r_extra), ("strips_infinite_ising", run_strip_extra),
+                         ("dense_blocked_chi16", run_dense_extra)):
             if args.extras and name not in args.extras.split(","):
                 continue
             t0 = time.perf_counter()
@@ -701,6 +702,91 @@ def run_strip_extra(args, ctx, pne, torch, dev, local_rank):
                                                     "measured FP32 FMA-chain kernel / 12 FP32 instructions per "
                                                     "float-float multiply-add")}}
             out[f"{tag}_{aname}"] = rec
+    return out
+
+
+def _grid_flops(lx, ly, chi):
+    """2 x the multiply-adds of the row-by-row contraction of an lx x ly grid
+    of uniform bond dimension chi (the site GEMMs, boundary legs of size 1)."""
+    state, total = 1, 0
+    for y in range(ly):
+        for x in range(lx):
+            ku, kh = (chi if y > 0 else 1), (chi if x > 0 else 1)
+            nd, nh = (chi if y + 1 < ly else 1), (chi if x + 1 < lx else 1)
+            r = state // (ku * kh)
+            total += 2 * r * ku * kh * nd * nh
+            state = r * nd * nh
+    return total
+
+
+def run_dense_extra(args, ctx, pne, torch, dev, local_rank):
+    """Dense contractions of blocked large-chi networks: the tcgen05 GEMM alone
+    (4 x 32768 x 256 x 256) and the exact contraction of 32 random 5 x 4
+    networks of bond dimension 16 (the paper's blocked random benchmark
+    networks), TF32 and BF16 on the tensor cores against FP64 on the CUDA cores."""
+    peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    bf16_peak = float(peaks["bf16_tflops"])
+    peak = {pne.PNE_BF16: bf16_peak, pne.PNE_TF32: bf16_peak * 1.1 / 2.25, pne.PNE_F64: None}
+    f64_peak = pne.pne_measure_fma_peak(ctx.h, pne.PNE_F64, None) / 1e12
+    names = {pne.PNE_TF32: "tf32", pne.PNE_BF16: "bf16", pne.PNE_F64: "f64"}
+    out = {"workload": "tcgen05 GEMM 4 x (32768 x 256 x 256); exact contraction of 32 random 5x4 networks, "
+                       "bond dimension 16 (U[0,1)+0.1), 20 site GEMMs each",
+           "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured); TF32 = that x 1.1/2.25 (nominal ratio); "
+                          "FP64 = measured FMA-chain kernel"}
+    batch, M, N, K = 4, 32768, 256, 256
+    g = torch.Generator(device="cpu").manual_seed(5)
+    A64 = torch.rand(batch, M, K, generator=g, dtype=torch.float64).to(dev)
+    B64 = torch.rand(batch, N, K, generator=g, dtype=torch.float64).to(dev)
+    ref = None
+    gemm = {}
+    for dt in (pne.PNE_F64, pne.PNE_TF32, pne.PNE_BF16):
+        A = A64 if dt == pne.PNE_F64 else A64.float()
+        B = B64 if dt == pne.PNE_F64 else B64.float()
+        C = torch.empty(batch, M, N, dtype=A.dtype, device=dev)
+        pne.pne_dense_gemm(ctx.h, dt, A, B, C)
+        pne.pne_ctx_profile(ctx.h, True)
+        reps = 3 if dt == pne.PNE_F64 else 20
+        for _ in range(reps):
+            pne.pne_dense_gemm(ctx.h, dt, A, B, C)
+        prof = pne.pne_ctx_profile_read(ctx.h)
+        pne.pne_ctx_profile(ctx.h, False)
+        key = "dense_gemm_f64" if dt == pne.PNE_F64 else "dense_gemm_tc"
+        ms = prof[key][1] / prof[key][0]
+        tf = 2.0 * batch * M * N * K / (ms * 1e-3) / 1e12
+        if dt == pne.PNE_F64:
+            ref = C.double()
+            err = 0.0
+        else:
+            err = float(((C.double() - ref).abs() / ref.abs()).max())
+        pk = peak[dt] if peak[dt] else f64_peak
+        gemm[names[dt]] = {"ms": ms, "tflops": tf, "peak_tflops": pk, "frac": tf / pk, "max_rel_err_vs_f64": err}
+    out["gemm"] = gemm
+    lx, ly, chi, nn = 5, 4, 16, 32
+    gg = I.square_lattice(lx, ly, chi)
+    flat = np.concatenate([I.random_tensors(gg, 7000 + i).flat_data()[0] for i in range(nn)])
+    data = torch.from_numpy(flat).to(dev)
+    flops = _grid_flops(lx, ly, chi) * nn
+    grid = {}
+    ref = None
+    for dt in (pne.PNE_F64, pne.PNE_TF32, pne.PNE_BF16):
+        pne.pne_grid_contract(ctx.h, gg, lx, ly, dt, data=data, n_batch=nn)
+        pne.pne_ctx_profile(ctx.h, True)
+        t0 = time.perf_counter()
+        res = pne.pne_grid_contract(ctx.h, gg, lx, ly, dt, data=data, n_batch=nn)
+        wall = time.perf_counter() - t0
+        prof = {k: v for k, v in pne.pne_ctx_profile_read(ctx.h).items() if not k.startswith("host:")}
+        pne.pne_ctx_profile(ctx.h, False)
+        key = "grid_gemm_f64" if dt == pne.PNE_F64 else "grid_gemm_tc"
+        gms = prof[key][1]
+        if dt == pne.PNE_F64:
+            ref = [r["log_abs"] for r in res]
+        err = max(abs(math.expm1(r["log_abs"] - e)) for r, e in zip(res, ref))
+        pk = peak[dt] if peak[dt] else f64_peak
+        grid[names[dt]] = {"wall_s": wall, "networks_per_s": nn / wall, "gemm_ms": gms,
+                           "kernel_ms": {k: round(v[1], 3) for k, v in prof.items()},
+                           "gemm_tflops": flops / (gms * 1e-3) / 1e12, "frac": flops / (gms * 1e-3) / 1e12 / pk,
+                           "max_rel_err_vs_f64": err, "stated_err_bound": res[0]["err_bound"]}
+    out["grid_5x4_chi16"] = grid
     return out
 
 
