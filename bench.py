@@ -289,6 +289,8 @@ def main():
     ap.add_argument("--extras", default="",
                     help="comma-separated names of the extra workloads to run (default: all)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the served trace")
+    ap.add_argument("--dense-nets", type=int, default=32,
+                    help="networks per call of the blocked chi = 16 grid contraction workload")
     ap.add_argument("--bp", default="ff", choices=["fp64", "ff"],
                     help="BP sweep arithmetic: FP64, or float-float pairs on the FP32 pipes")
     args = ap.parse_args()
@@ -729,8 +731,8 @@ def run_dense_extra(args, ctx, pne, torch, dev, local_rank):
     peak = {pne.PNE_BF16: bf16_peak, pne.PNE_TF32: bf16_peak * 1.1 / 2.25, pne.PNE_F64: None}
     f64_peak = pne.pne_measure_fma_peak(ctx.h, pne.PNE_F64, None) / 1e12
     names = {pne.PNE_TF32: "tf32", pne.PNE_BF16: "bf16", pne.PNE_F64: "f64"}
-    out = {"workload": "tcgen05 GEMM 4 x (32768 x 256 x 256); exact contraction of 32 random 5x4 networks, "
-                       "bond dimension 16 (U[0,1)+0.1), 20 site GEMMs each",
+    out = {"workload": f"tcgen05 GEMM 4 x (32768 x 256 x 256); exact contraction of {args.dense_nets} random 5x4 "
+                       "networks, bond dimension 16 (U[0,1)+0.1), 20 site GEMMs each",
            "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured); TF32 = that x 1.1/2.25 (nominal ratio); "
                           "FP64 = measured FMA-chain kernel"}
     batch, M, N, K = 4, 32768, 256, 256
@@ -761,7 +763,7 @@ def run_dense_extra(args, ctx, pne, torch, dev, local_rank):
         pk = peak[dt] if peak[dt] else f64_peak
         gemm[names[dt]] = {"ms": ms, "tflops": tf, "peak_tflops": pk, "frac": tf / pk, "max_rel_err_vs_f64": err}
     out["gemm"] = gemm
-    lx, ly, chi, nn = 5, 4, 16, 32
+    lx, ly, chi, nn = 5, 4, 16, args.dense_nets
     gg = I.square_lattice(lx, ly, chi)
     flat = np.concatenate([I.random_tensors(gg, 7000 + i).flat_data()[0] for i in range(nn)])
     data = torch.from_numpy(flat).to(dev)

@@ -548,6 +548,20 @@ pne_status pne_dense_gemm(pne_ctx *ctx, pne_dtype dtype, int32_t batch, int32_t 
 pne_status pne_grid_contract(pne_ctx *ctx, const pne_network *net, int32_t lx, int32_t ly, pne_dtype dtype,
                              void *stream, pne_result *out);
 
+/* The rank-r expansion of pne_rank_r_expand with every term contracted as a
+ * 2D grid (the weighted network restricted to each term's index ranges,
+ * contracted row by row as in pne_grid_contract): FP64 products on the CUDA
+ * cores, or TF32 / BF16 products on the tensor cores with FP32 accumulation
+ * -- the dense contractions of blocked large-chi networks (App. A, Sec. V).
+ * The network of the weights must be an lx x ly grid (site id = y * lx + x).
+ * Results as pne_rank_r_expand; err_bound adds, per term, the grid
+ * contraction's bound times |term value| (exact for terms of non-negative
+ * tensors, where the absolute contraction is the value).  PNE_F32 is rejected.
+ * Synchronises `stream`. */
+pne_status pne_rank_r_expand_grid(pne_ctx *ctx, const pne_weights *w, int32_t rank, int32_t form,
+                                  int32_t n_partitions, const int32_t *partition_ptr, const int32_t *partition_bonds,
+                                  int32_t lx, int32_t ly, pne_dtype dtype, void *stream, pne_result *out);
+
 /* ---- belief propagation without device allocation ------------------------ */
 
 /* The paper has no counterpart to this call.  It is for callers that must not

@@ -408,12 +408,6 @@ __global__ void grid_pack_kernel(const T *S, T *A, int64_t stride, int64_t R, in
 
 // Site matrices B_v[n = d Nh + h'][k = u Kh + h] = 2^-s_v T_v[l = h, u, r = h', d]
 // per (set, site): one block, the largest |entry| first (s_v its exponent).
-struct SiteMap {
-    int64_t t_off;          // tensor start in a set
-    int64_t b_off;          // site matrix start in a set
-    int stride[4];          // strides of l, u, r, d in T_v (0 for a boundary leg)
-    int dim[4];             // dims of l, u, r, d (1 at a boundary)
-};
 
 template <typename T>
 __global__ void grid_sites_kernel(const double *data, int64_t set_stride, const SiteMap *sites, int n_sites,
@@ -470,6 +464,323 @@ __global__ void grid_final_kernel(const T *S, int64_t stride, const long long *l
     out[2 * set + 1] = (double)log2s[set];
 }
 
+// ---------------------------------------------------------------- the grid's pipelined GEMM
+// One site absorption of the grid contraction on the tensor cores, with the
+// running tensor S read in its ring order directly (no packing pass):
+//     out[m][n] = 2^-e_in * sum_{u,h} S[u][m][h] * Bm[n][u Kh + h],
+// the result rounded to the operand type (TF32 kept in FP32 words, or BF16) as
+// the next step's running tensor, its largest |entry| recorded per set.
+// Stages are filled with 16-byte cp.async copies (4 stages in flight): the
+// operands are already in the MMA's type, so a stage is a plain copy into the
+// canonical layout; where a 16-byte unit of A is not contiguous in S (a left
+// boundary site, Kh not a multiple of the unit) it is gathered element by
+// element instead.  The epilogue goes through shared memory (the free
+// stages) so that every warp stores whole 128-byte row segments.
+template <typename E>
+struct RingParams {
+    const E *S;              // [set][stride] running tensor [Ku][R][Kh]
+    const E *B;              // site matrix [N][ldb] (rows zero-padded to ldb)
+    E *out;                  // [set][stride] next running tensor [R][N]
+    int64_t stride;          // running-tensor elements per set
+    int64_t b_stride;        // site-matrix elements per set
+    int64_t ldb;
+    int64_t R;
+    int Ku, Kh, N, K;
+    const unsigned long long *max_in;   // [set] largest |S| (float bits)
+    unsigned long long *max_out;        // [set] largest |out|, atomicMax
+    unsigned long long *max_clear;      // [set] cleared for the next step
+    long long *log2s;                   // [set] += e_in
+    int *err;
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename E>
+__device__ __forceinline__ float elem_to_float(E x);
+template <>
+__device__ __forceinline__ float elem_to_float<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float elem_to_float<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <typename E>
+__device__ __forceinline__ E round_elem(float x);
+template <>
+__device__ __forceinline__ float round_elem<float>(float x) { return __uint_as_float(to_tf32(x)); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 round_elem<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+template <typename E, int NST>
+__global__ void __launch_bounds__(kTcThreads, 2) tc_ring_gemm_kernel(RingParams<E> p, int BN)
+{
+    constexpr int kRingStages = NST;
+    constexpr int EB = (int)sizeof(E);
+    constexpr int EPU = 16 / EB;          // elements per 16-byte unit
+    constexpr int KC = kChunk / EB;       // elements per stage row
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[kRingStages];
+    __shared__ uint32_t tmem_base_sh;
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int stage_bytes = kATileBytes + BN * kChunk;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int set = blockIdx.z;
+    const int64_t m0 = (int64_t)blockIdx.x * kTcBM;
+    const int n0 = blockIdx.y * BN;
+    const E *S = p.S + set * p.stride;
+    const E *Bm = p.B + set * p.b_stride;
+    E *out = p.out + set * p.stride;
+    const uint32_t tcols = BN <= 32 ? 32u : (BN <= 64 ? 64u : (BN <= 128 ? 128u : 256u));
+    const bool a_contig = (p.Kh % EPU) == 0;
+
+    if (warp == 0) {
+        tmem_alloc(smem_addr(&tmem_base_sh), tcols);
+        tmem_relinquish();
+    }
+    if (tid == 0)
+        for (int i = 0; i < kRingStages; ++i) mbar_init(smem_addr(&mbar[i]), 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+    const int nchunks = (p.K + KC - 1) / KC;
+    const uint32_t idesc = instr_desc(EB == 4 ? 2u : 1u, kTcBM, (uint32_t)BN);
+
+    // each thread copies one fixed 16-byte column (cu) of rows r0, r0 + 16, ...:
+    // per stage one division for its k, then addresses advance by a constant
+    const int cu = tid & 7, r0 = tid >> 3;
+    const int64_t a_row_step = 16 * (int64_t)p.Kh;
+    const int64_t b_row_step = 16 * p.ldb;
+    auto load_stage = [&](int c) {
+        if (c >= nchunks) return;
+        uint8_t *sa = base + (c % kRingStages) * stage_bytes;
+        uint8_t *sb = sa + kATileBytes;
+        const int k = c * KC + cu * EPU;
+        const bool k_in = k < p.K;
+        if (a_contig) {
+            const int ku = k_in ? k / p.Kh : 0, kh = k_in ? k - ku * p.Kh : 0;
+            const E *src = S + ((int64_t)ku * p.R + m0 + r0) * p.Kh + kh;
+            int64_t m = m0 + r0;
+            uint32_t dst = smem_addr(sa) + (uint32_t)tile_off(r0, cu);
+#pragma unroll
+            for (int i = 0; i < kTcBM / 16; ++i) {
+                const bool in = k_in && m < p.R;
+                cp_async16(dst, in ? (const void *)src : (const void *)S, in ? 16u : 0u);
+                src += a_row_step;
+                m += 16;
+                dst += 2 * 1024;            // 16 rows = two 8-row groups
+            }
+        } else {
+            for (int i = 0; i < kTcBM / 16; ++i) {
+                const int r = r0 + 16 * i;
+                const int64_t m = m0 + r;
+                __align__(16) E v[EPU];
+#pragma unroll
+                for (int j = 0; j < EPU; ++j) {
+                    const int kk = k + j;
+                    if (m < p.R && kk < p.K) {
+                        const int ku = kk / p.Kh, kh = kk - ku * p.Kh;
+                        v[j] = S[((int64_t)ku * p.R + m) * p.Kh + kh];
+                    } else {
+                        v[j] = round_elem<E>(0.f);
+                    }
+                }
+                *reinterpret_cast<uint4 *>(sa + tile_off(r, cu)) = *reinterpret_cast<const uint4 *>(v);
+            }
+        }
+        const uint32_t bytes = k_in ? (uint32_t)min(16, (p.K - k) * EB) : 0u;
+        const E *bsrc = Bm + (int64_t)(n0 + r0) * p.ldb + (k_in ? k : 0);
+        int n = n0 + r0;
+        uint32_t bdst = smem_addr(sb) + (uint32_t)tile_off(r0, cu);
+        for (int i = 0; i < BN / 16; ++i) {
+            const bool in = n < p.N;
+            cp_async16(bdst, in ? (const void *)bsrc : (const void *)Bm, in ? bytes : 0u);
+            bsrc += b_row_step;
+            n += 16;
+            bdst += 2 * 1024;
+        }
+    };
+
+    for (int c = 0; c < kRingStages - 1; ++c) {
+        load_stage(c);
+        cp_async_commit();
+    }
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+        cp_async_wait<kRingStages - 2>();
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0 && ok) {
+            tc_fence_after();
+            const uint8_t *sa = base + (c % kRingStages) * stage_bytes;
+            const uint8_t *sb = sa + kATileBytes;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t ad = smem_desc(smem_addr(sa) + ks * 256, 128, 1024);
+                const uint64_t bd = smem_desc(smem_addr(sb) + ks * 256, 128, 1024);
+                tc_mma<EB>(tmem, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+            }
+            tc_commit(smem_addr(&mbar[c % kRingStages]));
+        }
+        // the stage the next prefetch overwrites was read by chunk c - 1
+        if (c >= 1) {
+            const bool w = ok ? mbar_wait(smem_addr(&mbar[(c - 1) % kRingStages]),
+                                          (uint32_t)(((c - 1) / kRingStages) & 1))
+                              : false;
+            ok = __syncthreads_and(w) != 0;
+        }
+        load_stage(c + kRingStages - 1);
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    {
+        const int c = nchunks - 1;
+        const bool w = ok ? mbar_wait(smem_addr(&mbar[c % kRingStages]), (uint32_t)((c / kRingStages) & 1)) : false;
+        ok = __syncthreads_and(w) != 0;
+    }
+    tc_fence_after();
+    // the scale of this step: 2^-e_in, e_in the exponent of the input's largest |entry|
+    const float mx_in = __uint_as_float((unsigned)p.max_in[set]);
+    const int e_in = mx_in > 0.f ? ilogbf(mx_in) : 0;
+    const float sc = ldexpf(1.f, -e_in);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+        p.log2s[set] += e_in;
+        p.max_clear[set] = 0ull;
+    }
+    float mx = 0.f;
+    if (ok) {
+        // 64-column slices through shared memory: [128][64 + 4] floats
+        constexpr int SW = 64, SP = SW + 4;
+        float *st = reinterpret_cast<float *>(base);
+        for (int c0 = 0; c0 < BN; c0 += SW) {
+#pragma unroll
+            for (int q = 0; q < SW; q += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + q), r);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) st[(warp * 32 + lane) * SP + q + j] = __uint_as_float(r[j]) * sc;
+            }
+            __syncthreads();
+            for (int i = tid; i < kTcBM * SW; i += kTcThreads) {
+                const int rr = i / SW, cc = i % SW;
+                const int64_t row = m0 + rr;
+                const int col = n0 + c0 + cc;
+                if (row < p.R && col < p.N) {
+                    const E v = round_elem<E>(st[rr * SP + cc]);
+                    out[row * p.N + col] = v;
+                    mx = fmaxf(mx, fabsf(elem_to_float<E>(v)));
+                }
+            }
+            __syncthreads();
+        }
+    } else if (tid == 0) {
+        atomicExch(p.err, 1);
+    }
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0 && mx > 0.f) atomicMax(p.max_out + set, (unsigned long long)__float_as_uint(mx));
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, tcols);
+}
+
+// Site matrices for the tensor-core path: rows padded to a multiple of the
+// 16-byte unit, entries scaled by 2^-s_v and rounded to the operand type.
+template <typename E>
+__global__ void grid_sites_tc_kernel(const double *data, int64_t set_stride, const SiteMap *sites, E *Bm,
+                                     int64_t b_stride, const int64_t *ldb, long long *log2s)
+{
+    const int v = blockIdx.x, set = blockIdx.y;
+    const SiteMap sm = sites[v];
+    const double *t = data + set * set_stride + sm.t_off;
+    const int Kh = sm.dim[0], Ku = sm.dim[1], Nh = sm.dim[2], Nd = sm.dim[3];
+    const int64_t n_ent = (int64_t)Kh * Ku * Nh * Nd;
+    __shared__ double red[32];
+    double mx = 0.0;
+    for (int64_t i = threadIdx.x; i < n_ent; i += blockDim.x) mx = fmax(mx, fabs(t[i]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) mx = fmax(mx, red[i]);
+        red[0] = mx;
+    }
+    __syncthreads();
+    mx = red[0];
+    const int e = mx > 0.0 ? ilogb(mx) : 0;
+    const double sc = ldexp(1.0, -e);
+    const int K = Ku * Kh, N = Nd * Nh;
+    const int64_t ld = ldb[v];
+    E *out = Bm + set * b_stride + sm.b_off;
+    for (int64_t q = threadIdx.x; q < (int64_t)N * ld; q += blockDim.x) {
+        const int n = (int)(q / ld), k = (int)(q % ld);
+        float x = 0.f;
+        if (k < K) {
+            const int d = n / Nh, hp = n % Nh, u = k / Kh, h = k % Kh;
+            const int64_t off = (int64_t)h * sm.stride[0] + (int64_t)u * sm.stride[1] + (int64_t)hp * sm.stride[2] +
+                                (int64_t)d * sm.stride[3];
+            x = (float)(t[off] * sc);
+        }
+        out[q] = round_elem<E>(x);
+    }
+    if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long *>(log2s + set), (unsigned long long)(long long)e);
+}
+
+template <typename E>
+__global__ void grid_init_tc_kernel(E *S, int64_t stride, unsigned long long *maxbits, long long *log2s, int n_sets)
+{
+    const int set = blockIdx.x * blockDim.x + threadIdx.x;
+    if (set >= n_sets) return;
+    S[set * stride] = round_elem<E>(1.f);
+    maxbits[set] = (unsigned long long)__float_as_uint(1.0f);
+    log2s[set] = 0;
+}
+
+template <typename E>
+__global__ void grid_final_tc_kernel(const E *S, int64_t stride, const unsigned long long *max_last,
+                                     const long long *log2s, int n_sets, double *out)
+{
+    const int set = blockIdx.x * blockDim.x + threadIdx.x;
+    if (set >= n_sets) return;
+    out[2 * set] = (double)elem_to_float<E>(S[set * stride]);
+    out[2 * set + 1] = (double)log2s[set];
+    (void)max_last;
+}
+
+// stages per CTA: as many as let two CTAs share an SM (<= 113 KB each, 2 x 256
+// tensor-memory columns), so one CTA's prologue and epilogue overlap the
+// other's main loop
+template <typename E, int NST>
+cudaError_t launch_ring_n(const RingParams<E> &p, int batch, int BN, cudaStream_t s)
+{
+    const size_t smem = (size_t)NST * (kATileBytes + BN * kChunk) + 1024;
+    cudaError_t e = grant_dynamic_smem((const void *)tc_ring_gemm_kernel<E, NST>, smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((p.R + kTcBM - 1) / kTcBM), (unsigned)((p.N + BN - 1) / BN), (unsigned)batch);
+    tc_ring_gemm_kernel<E, NST><<<grid, kTcThreads, smem, s>>>(p, BN);
+    return cudaGetLastError();
+}
+
+template <typename E>
+cudaError_t launch_ring(const RingParams<E> &p, int batch, cudaStream_t s)
+{
+    const int BN = std::min(256, ((p.N + 15) / 16) * 16);
+    const int stage = kATileBytes + BN * kChunk;
+    const int nst = (int)std::max<int64_t>(2, std::min<int64_t>(4, (112 * 1024) / stage));
+    if (nst >= 4) return launch_ring_n<E, 4>(p, batch, BN, s);
+    if (nst == 3) return launch_ring_n<E, 3>(p, batch, BN, s);
+    return launch_ring_n<E, 2>(p, batch, BN, s);
+}
+
 size_t tc_smem_bytes(int BN)
 {
     return (size_t)2 * (kATileBytes + BN * kChunk) + 1024;
@@ -496,6 +807,223 @@ cudaError_t launch_f64(const GemmParams<double> &p, int batch, cudaStream_t s)
 }
 
 }  // namespace
+
+pne_status grid_plan(pne_ctx *ctx, int lx, int ly, int n_bonds, const int32_t *bond_site, const int32_t *bond_dim,
+                     const int32_t *site_ptr, const int32_t *site_bonds, const int64_t *data_off, pne_dtype dtype,
+                     int nb, GridPlan &plan)
+{
+    auto bad = [&](const std::string &m) { set_error(ctx, PNE_EINVAL, m); return PNE_EINVAL; };
+    const int n = lx * ly;
+    // bond between grid neighbours: horizontal hb[v] (x, y)-(x+1, y), vertical vb[v] (x, y)-(x, y+1)
+    std::vector<int> hb((size_t)n, -1), vb((size_t)n, -1);
+    for (int b = 0; b < n_bonds; ++b) {
+        int s0 = bond_site[2 * b], s1 = bond_site[2 * b + 1];
+        if (s0 < 0 || s1 < 0 || s0 >= n || s1 >= n) return bad("grid networks have no open indices");
+        if (s0 > s1) std::swap(s0, s1);
+        const int x0 = s0 % lx, y0 = s0 / lx, x1 = s1 % lx, y1 = s1 / lx;
+        const int d = bond_dim[b];
+        if (d < 1 || d > 4096) return bad("bond dimension out of range");
+        if (y0 == y1 && x1 == x0 + 1) {
+            if (hb[s0] >= 0) return bad("two bonds join the same grid neighbours");
+            hb[s0] = b;
+        } else if (x0 == x1 && y1 == y0 + 1) {
+            if (vb[s0] >= 0) return bad("two bonds join the same grid neighbours");
+            vb[s0] = b;
+        } else {
+            return bad("a bond does not join grid neighbours (site id = y * lx + x)");
+        }
+    }
+    for (int y = 0; y < ly; ++y)
+        for (int x = 0; x < lx; ++x) {
+            const int v = y * lx + x;
+            if ((x + 1 < lx && hb[v] < 0) || (y + 1 < ly && vb[v] < 0)) return bad("a grid bond is missing");
+        }
+    plan.n = n;
+    plan.maps.assign((size_t)n, SiteMap{});
+    plan.steps.assign((size_t)n, GridStep{});
+    plan.ldb.assign((size_t)n, 0);
+    const size_t esz = dtype == PNE_F64 ? 8 : (dtype == PNE_TF32 ? 4 : 2);
+    const int epu = dtype == PNE_F64 ? 1 : (int)(16 / esz);
+    int64_t b_total = 0, state = 1, max_state = 1;
+    for (int y = 0; y < ly; ++y)
+        for (int x = 0; x < lx; ++x) {
+            const int v = y * lx + x;
+            const int legb[4] = {x > 0 ? hb[v - 1] : -1, y > 0 ? vb[v - lx] : -1, x + 1 < lx ? hb[v] : -1,
+                                 y + 1 < ly ? vb[v] : -1};
+            SiteMap &sm = plan.maps[(size_t)v];
+            const int p0 = site_ptr[v], p1 = site_ptr[v + 1];
+            int nlegs = 0;
+            for (int i = 0; i < 4; ++i) nlegs += legb[i] >= 0;
+            if (p1 - p0 != nlegs) return bad("a site's legs are not its grid bonds");
+            for (int i = 0; i < 4; ++i) {
+                sm.dim[i] = legb[i] >= 0 ? bond_dim[legb[i]] : 1;
+                sm.stride[i] = 0;
+            }
+            // strides: legs in the order of site_bonds, row-major
+            int64_t stride = 1;
+            for (int q = p1 - 1; q >= p0; --q) {
+                const int b = site_bonds[q];
+                int which = -1;
+                for (int i = 0; i < 4; ++i)
+                    if (legb[i] == b) which = i;
+                if (which < 0) return bad("a site's legs are not its grid bonds");
+                if (stride > INT32_MAX) return bad("site tensor too large");
+                sm.stride[which] = (int)stride;
+                stride *= bond_dim[b];
+            }
+            if (data_off[v + 1] - data_off[v] != stride) return bad("data_off does not match the bond dims");
+            sm.t_off = data_off[v];
+            GridStep sd{sm.dim[1], sm.dim[0], sm.dim[3], sm.dim[2], 0};
+            const int64_t K = (int64_t)sd.Ku * sd.Kh;
+            if (state % K != 0) return bad("internal: running tensor does not split");
+            sd.R = state / K;
+            if (sd.R > INT32_MAX || (int64_t)sd.Nd * sd.Nh > INT32_MAX || K > INT32_MAX)
+                return bad("a step's matrix is too large");
+            plan.ldb[(size_t)v] = (K + epu - 1) / epu * epu;
+            sm.b_off = b_total;
+            b_total += plan.ldb[(size_t)v] * sd.Nd * sd.Nh;
+            state = sd.R * sd.Nd * sd.Nh;
+            max_state = std::max(max_state, std::max(state, sd.R * K));
+            plan.steps[(size_t)v] = sd;
+        }
+    if (state != 1) return bad("internal: the contraction did not close");
+    plan.b_total = b_total;
+    plan.max_state = (max_state + 63) / 64 * 64;
+    if ((double)plan.max_state * esz * 2 * nb > 64e9) return bad("running tensors exceed 64 GB for this batch");
+    return PNE_OK;
+}
+
+pne_status grid_run(pne_ctx *ctx, const GridPlan &plan, const double *data, int64_t set_stride, int nb,
+                    pne_dtype dtype, cudaStream_t s, std::vector<double> &h, double &bound)
+{
+    const int n = plan.n;
+    const size_t esz = dtype == PNE_F64 ? 8 : (dtype == PNE_TF32 ? 4 : 2);
+    const int64_t max_state = plan.max_state, b_total = plan.b_total;
+    DevBuf dMaps, dB, dS, dA, dMax, dLog, dOut, dErr, dLdb;
+    auto cleanup = [&]() {
+        for (DevBuf *b : {&dMaps, &dB, &dS, &dA, &dMax, &dLog, &dOut, &dErr, &dLdb}) dev_free(ctx, *b, s);
+    };
+    pne_status st;
+    if ((st = dev_alloc(ctx, dMaps, plan.maps.size() * sizeof(SiteMap), s)) ||
+        (st = dev_alloc(ctx, dB, (size_t)nb * b_total * esz, s)) ||
+        (st = dev_alloc(ctx, dS, (size_t)nb * max_state * esz, s)) ||
+        (st = dev_alloc(ctx, dA, (size_t)nb * max_state * esz, s)) || (st = dev_alloc(ctx, dMax, (size_t)nb * 24, s)) ||
+        (st = dev_alloc(ctx, dLog, (size_t)nb * 8, s)) || (st = dev_alloc(ctx, dOut, (size_t)nb * 16, s)) ||
+        (st = dev_alloc(ctx, dErr, 16, s)) || (st = dev_alloc(ctx, dLdb, (size_t)n * 8, s))) {
+        cleanup();
+        return st;
+    }
+    auto fail = [&](cudaError_t e, const char *what) {
+        set_error(ctx, PNE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+        cleanup();
+        return PNE_ECUDA;
+    };
+    cudaError_t e = cudaMemcpyAsync(dMaps.ptr, plan.maps.data(), plan.maps.size() * sizeof(SiteMap),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dLdb.ptr, plan.ldb.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dErr.ptr, 0, 16, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dMax.ptr, 0, (size_t)nb * 24, s);
+    if (e != cudaSuccess) return fail(e, "grid upload");
+    unsigned long long *mb = (unsigned long long *)dMax.ptr;
+    long long *lg = (long long *)dLog.ptr;
+    const int ib = (nb + 127) / 128;
+    bound = 0.0;
+    const double u_in = dtype == PNE_TF32 ? std::ldexp(1.0, -11) : (dtype == PNE_BF16 ? std::ldexp(1.0, -8) : 0.0);
+    if (dtype != PNE_F64) {
+        // running tensors ping-pong between dS and dA; largest |entry| in three rotating slots
+        auto run_tc = [&](auto tag) -> cudaError_t {
+            using E = decltype(tag);
+            E *S0 = (E *)dS.ptr, *S1 = (E *)dA.ptr;
+            {
+                ProfScope ps(ctx, s, "grid_sites");
+                grid_init_tc_kernel<E><<<ib, 128, 0, s>>>(S0, max_state, mb, lg, nb);
+                grid_sites_tc_kernel<E><<<dim3(n, nb), 256, 0, s>>>(data, set_stride, (const SiteMap *)dMaps.ptr,
+                                                                    (E *)dB.ptr, b_total, (const int64_t *)dLdb.ptr, lg);
+            }
+            cudaError_t ee = cudaGetLastError();
+            if (ee != cudaSuccess) return ee;
+            for (int v = 0; v < n; ++v) {
+                const GridStep &sd = plan.steps[(size_t)v];
+                RingParams<E> rp;
+                rp.S = (v & 1) ? S1 : S0;
+                rp.out = (v & 1) ? S0 : S1;
+                rp.B = (const E *)dB.ptr + plan.maps[(size_t)v].b_off;
+                rp.stride = max_state;
+                rp.b_stride = b_total;
+                rp.ldb = plan.ldb[(size_t)v];
+                rp.R = sd.R;
+                rp.Ku = sd.Ku;
+                rp.Kh = sd.Kh;
+                rp.N = sd.Nd * sd.Nh;
+                rp.K = sd.Ku * sd.Kh;
+                rp.max_in = mb + (size_t)(v % 3) * nb;
+                rp.max_out = mb + (size_t)((v + 1) % 3) * nb;
+                rp.max_clear = mb + (size_t)((v + 2) % 3) * nb;
+                rp.log2s = lg;
+                rp.err = (int *)dErr.ptr;
+                ProfScope ps(ctx, s, "grid_gemm_tc");
+                if ((ee = launch_ring<E>(rp, nb, s)) != cudaSuccess) return ee;
+                bound += 2.0 * u_in + (double)rp.K * std::ldexp(1.0, -24);
+            }
+            {
+                ProfScope ps(ctx, s, "grid_final");
+                grid_final_tc_kernel<E><<<ib, 128, 0, s>>>((n & 1) ? S1 : S0, max_state, mb, lg, nb, (double *)dOut.ptr);
+            }
+            return cudaGetLastError();
+        };
+        e = dtype == PNE_TF32 ? run_tc(float(0)) : run_tc(__nv_bfloat16());
+        if (e != cudaSuccess) return fail(e, "grid contraction (tensor cores)");
+    } else {
+        {
+            ProfScope ps(ctx, s, "grid_sites");
+            grid_init_kernel<double><<<ib, 128, 0, s>>>((double *)dS.ptr, max_state, mb, lg, nb);
+            grid_sites_kernel<double><<<dim3(n, nb), 256, 0, s>>>(data, set_stride, (const SiteMap *)dMaps.ptr, n,
+                                                                  (double *)dB.ptr, b_total, lg);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "grid site matrices");
+        for (int v = 0; v < n; ++v) {
+            const GridStep &sd = plan.steps[(size_t)v];
+            const int K = sd.Ku * sd.Kh, N = sd.Nd * sd.Nh;
+            unsigned long long *cur = mb + (size_t)(v & 1) * nb, *nxt = mb + (size_t)((v + 1) & 1) * nb;
+            const int64_t total = sd.R * K;
+            const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+            {
+                ProfScope ps(ctx, s, "grid_pack");
+                grid_pack_kernel<double><<<dim3(pblocks, nb), 256, 0, s>>>((const double *)dS.ptr, (double *)dA.ptr,
+                                                                          max_state, sd.R, sd.Ku, sd.Kh, cur, nxt, lg,
+                                                                          nb);
+            }
+            if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "grid_pack_kernel");
+            {
+                ProfScope ps(ctx, s, "grid_gemm_f64");
+                GemmParams<double> p{(const double *)dA.ptr, K, max_state,
+                                     (const double *)dB.ptr + plan.maps[(size_t)v].b_off, K, b_total,
+                                     (double *)dS.ptr, N, max_state, (int)sd.R, N, K, nxt, (int *)dErr.ptr};
+                e = launch_f64(p, nb, s);
+            }
+            if (e != cudaSuccess) return fail(e, "grid GEMM");
+            bound += (double)K * std::ldexp(1.0, -53);
+        }
+        {
+            ProfScope ps(ctx, s, "grid_final");
+            grid_final_kernel<double><<<ib, 128, 0, s>>>((const double *)dS.ptr, max_state, lg, nb, (double *)dOut.ptr);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "grid_final_kernel");
+    }
+    h.assign((size_t)nb * 2, 0.0);
+    int herr = 0;
+    if ((e = cudaMemcpyAsync(h.data(), dOut.ptr, h.size() * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&herr, dErr.ptr, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return fail(e, "grid results");
+    cleanup();
+    if (herr) {
+        set_error(ctx, PNE_ETIMEOUT, "grid contraction: a tensor-core stage wait gave up");
+        return PNE_ETIMEOUT;
+    }
+    return PNE_OK;
+}
+
 }  // namespace pne
 
 using namespace pne;
@@ -551,186 +1079,32 @@ pne_status pne_grid_contract(pne_ctx *ctx, const pne_network *net, int32_t lx, i
     if (!ctx || !net || !out) return PNE_EINVAL;
     auto bad = [&](const std::string &m) { set_error(ctx, PNE_EINVAL, m); return PNE_EINVAL; };
     if (dtype == PNE_F32) return bad("grid_contract takes PNE_F64, PNE_TF32 or PNE_BF16");
-    if (lx < 1 || ly < 1 || (int64_t)lx * ly != net->n_sites) return bad("n_sites must be lx * ly");
     const int nb = net->n_batch;
     if (nb < 1 || nb > 65535) return bad("n_batch in 1..65535");
     if (!net->bond_site || !net->bond_dim || !net->site_ptr || !net->site_bonds || !net->data || !net->data_off)
         return bad("null network array");
-    const int n = net->n_sites;
-    // bond between grid neighbours: horizontal hb[y][x] (x, y)-(x+1, y), vertical vb[y][x] (x, y)-(x, y+1)
-    std::vector<int> hb((size_t)n, -1), vb((size_t)n, -1);
-    for (int b = 0; b < net->n_bonds; ++b) {
-        int s0 = net->bond_site[2 * b], s1 = net->bond_site[2 * b + 1];
-        if (s0 < 0 || s1 < 0 || s0 >= n || s1 >= n) return bad("grid networks have no open indices");
-        if (s0 > s1) std::swap(s0, s1);
-        const int x0 = s0 % lx, y0 = s0 / lx, x1 = s1 % lx, y1 = s1 / lx;
-        const int d = net->bond_dim[b];
-        if (d < 1 || d > 4096) return bad("bond dimension out of range");
-        if (y0 == y1 && x1 == x0 + 1) {
-            if (hb[s0] >= 0) return bad("two bonds join the same grid neighbours");
-            hb[s0] = b;
-        } else if (x0 == x1 && y1 == y0 + 1) {
-            if (vb[s0] >= 0) return bad("two bonds join the same grid neighbours");
-            vb[s0] = b;
-        } else {
-            return bad("a bond does not join grid neighbours (site id = y * lx + x)");
-        }
-    }
-    for (int y = 0; y < ly; ++y)
-        for (int x = 0; x < lx; ++x) {
-            const int v = y * lx + x;
-            if ((x + 1 < lx && hb[v] < 0) || (y + 1 < ly && vb[v] < 0)) return bad("a grid bond is missing");
-        }
-    // per site: leg strides in its tensor (legs in ascending bond id, row-major)
-    std::vector<SiteMap> maps((size_t)n);
-    int64_t b_total = 0, state = 1, max_state = 1, max_ak = 1;
-    struct StepDims { int Ku, Kh, Nd, Nh; int64_t R; };
-    std::vector<StepDims> steps((size_t)n);
-    for (int y = 0; y < ly; ++y)
-        for (int x = 0; x < lx; ++x) {
-            const int v = y * lx + x;
-            const int legb[4] = {x > 0 ? hb[v - 1] : -1, y > 0 ? vb[v - lx] : -1, x + 1 < lx ? hb[v] : -1,
-                                 y + 1 < ly ? vb[v] : -1};
-            SiteMap &sm = maps[(size_t)v];
-            const int p0 = net->site_ptr[v], p1 = net->site_ptr[v + 1];
-            int nlegs = 0;
-            for (int i = 0; i < 4; ++i) nlegs += legb[i] >= 0;
-            if (p1 - p0 != nlegs) return bad("a site's legs are not its grid bonds");
-            int64_t size = 1;
-            for (int i = 0; i < 4; ++i) {
-                sm.dim[i] = legb[i] >= 0 ? net->bond_dim[legb[i]] : 1;
-                sm.stride[i] = 0;
-            }
-            // strides: legs in the order of site_bonds, row-major
-            int64_t stride = 1;
-            for (int q = p1 - 1; q >= p0; --q) {
-                const int b = net->site_bonds[q];
-                int which = -1;
-                for (int i = 0; i < 4; ++i)
-                    if (legb[i] == b) which = i;
-                if (which < 0) return bad("a site's legs are not its grid bonds");
-                if (stride > INT32_MAX) return bad("site tensor too large");
-                sm.stride[which] = (int)stride;
-                stride *= net->bond_dim[b];
-            }
-            size = stride;
-            if (net->data_off[v + 1] - net->data_off[v] != size) return bad("data_off does not match the bond dims");
-            sm.t_off = net->data_off[v];
-            sm.b_off = b_total;
-            b_total += size;
-            StepDims sd{sm.dim[1], sm.dim[0], sm.dim[3], sm.dim[2], 0};
-            if (state % ((int64_t)sd.Ku * sd.Kh) != 0) return bad("internal: running tensor does not split");
-            sd.R = state / ((int64_t)sd.Ku * sd.Kh);
-            state = sd.R * sd.Nd * sd.Nh;
-            max_state = std::max(max_state, std::max(state, sd.R * sd.Ku * sd.Kh));
-            max_ak = std::max<int64_t>(max_ak, sd.R * sd.Ku * sd.Kh);
-            if (sd.R > INT32_MAX || (int64_t)sd.Nd * sd.Nh > INT32_MAX || (int64_t)sd.Ku * sd.Kh > INT32_MAX)
-                return bad("a step's matrix is too large");
-            steps[(size_t)v] = sd;
-        }
-    if (state != 1) return bad("internal: the contraction did not close");
-    const size_t esz = dtype == PNE_F64 ? 8 : 4;
-    if ((double)max_state * esz * 2 * nb > 64e9) return bad("running tensors exceed 64 GB for this batch");
+    if (lx < 1 || ly < 1 || (int64_t)lx * ly != net->n_sites) return bad("n_sites must be lx * ly");
+    GridPlan plan;
+    pne_status st = grid_plan(ctx, lx, ly, net->n_bonds, net->bond_site, net->bond_dim, net->site_ptr,
+                              net->site_bonds, net->data_off, dtype, nb, plan);
+    if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t set_stride = net->data_off[n];
-    DevBuf dData, dMaps, dB, dS, dA, dMax, dLog, dOut, dErr;
-    auto cleanup = [&]() {
-        for (DevBuf *b : {&dData, &dMaps, &dB, &dS, &dA, &dMax, &dLog, &dOut, &dErr}) dev_free(ctx, *b, s);
-    };
-    pne_status st;
+    const int64_t set_stride = net->data_off[net->n_sites];
+    DevBuf dData;
     const double *data = net->data;
     if (!net->data_on_device) {
         if ((st = dev_alloc(ctx, dData, (size_t)nb * set_stride * 8, s))) return st;
-    }
-    if ((st = dev_alloc(ctx, dMaps, maps.size() * sizeof(SiteMap), s)) ||
-        (st = dev_alloc(ctx, dB, (size_t)nb * b_total * esz, s)) ||
-        (st = dev_alloc(ctx, dS, (size_t)nb * max_state * esz, s)) ||
-        (st = dev_alloc(ctx, dA, (size_t)nb * max_state * esz, s)) || (st = dev_alloc(ctx, dMax, (size_t)nb * 16, s)) ||
-        (st = dev_alloc(ctx, dLog, (size_t)nb * 8, s)) || (st = dev_alloc(ctx, dOut, (size_t)nb * 16, s)) ||
-        (st = dev_alloc(ctx, dErr, 16, s))) {
-        cleanup();
-        return st;
-    }
-    auto fail = [&](cudaError_t e, const char *what) {
-        set_error(ctx, PNE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
-        cleanup();
-        return PNE_ECUDA;
-    };
-    cudaError_t e = cudaSuccess;
-    if (!net->data_on_device) {
-        e = cudaMemcpyAsync(dData.ptr, net->data, (size_t)nb * set_stride * 8, cudaMemcpyHostToDevice, s);
+        if ((st = upload(ctx, dData.ptr, net->data, (size_t)nb * set_stride * 8, s))) {
+            dev_free(ctx, dData, s);
+            return st;
+        }
         data = (const double *)dData.ptr;
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dMaps.ptr, maps.data(), maps.size() * sizeof(SiteMap), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dErr.ptr, 0, 16, s);
-    if (e != cudaSuccess) return fail(e, "grid upload");
-    unsigned long long *mb = (unsigned long long *)dMax.ptr;
-    long long *lg = (long long *)dLog.ptr;
-    const int ib = (nb + 127) / 128;
-    {
-        ProfScope ps(ctx, s, "grid_sites");
-        if (esz == 8) {
-            grid_init_kernel<double><<<ib, 128, 0, s>>>((double *)dS.ptr, max_state, mb, lg, nb);
-            grid_sites_kernel<double><<<dim3(n, nb), 256, 0, s>>>(data, set_stride, (const SiteMap *)dMaps.ptr, n,
-                                                                  (double *)dB.ptr, b_total, lg);
-        } else {
-            grid_init_kernel<float><<<ib, 128, 0, s>>>((float *)dS.ptr, max_state, mb, lg, nb);
-            grid_sites_kernel<float><<<dim3(n, nb), 256, 0, s>>>(data, set_stride, (const SiteMap *)dMaps.ptr, n,
-                                                                 (float *)dB.ptr, b_total, lg);
-        }
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "grid site matrices");
+    std::vector<double> h;
     double bound = 0.0;
-    const double u_in = dtype == PNE_TF32 ? std::ldexp(1.0, -11) : (dtype == PNE_BF16 ? std::ldexp(1.0, -8) : 0.0);
-    for (int v = 0; v < n; ++v) {
-        const StepDims &sd = steps[(size_t)v];
-        const int K = sd.Ku * sd.Kh, N = sd.Nd * sd.Nh;
-        unsigned long long *cur = mb + (size_t)(v & 1) * nb, *nxt = mb + (size_t)((v + 1) & 1) * nb;
-        const int64_t total = sd.R * K;
-        const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
-        {
-            ProfScope ps(ctx, s, "grid_pack");
-            if (esz == 8)
-                grid_pack_kernel<double><<<dim3(pblocks, nb), 256, 0, s>>>((const double *)dS.ptr, (double *)dA.ptr,
-                                                                          max_state, sd.R, sd.Ku, sd.Kh, cur, nxt, lg,
-                                                                          nb);
-            else
-                grid_pack_kernel<float><<<dim3(pblocks, nb), 256, 0, s>>>((const float *)dS.ptr, (float *)dA.ptr,
-                                                                         max_state, sd.R, sd.Ku, sd.Kh, cur, nxt, lg,
-                                                                         nb);
-        }
-        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "grid_pack_kernel");
-        {
-            ProfScope ps(ctx, s, esz == 8 ? "grid_gemm_f64" : "grid_gemm_tc");
-            if (esz == 8) {
-                GemmParams<double> p{(const double *)dA.ptr, K, max_state, (const double *)dB.ptr + maps[(size_t)v].b_off,
-                                     K, b_total, (double *)dS.ptr, N, max_state, (int)sd.R, N, K, nxt,
-                                     (int *)dErr.ptr};
-                e = launch_f64(p, nb, s);
-            } else {
-                GemmParams<float> p{(const float *)dA.ptr, K, max_state, (const float *)dB.ptr + maps[(size_t)v].b_off,
-                                    K, b_total, (float *)dS.ptr, N, max_state, (int)sd.R, N, K, nxt, (int *)dErr.ptr};
-                e = dtype == PNE_TF32 ? launch_tc<4>(p, nb, s) : launch_tc<2>(p, nb, s);
-            }
-        }
-        if (e != cudaSuccess) return fail(e, "grid GEMM");
-        bound += 2.0 * u_in + (dtype == PNE_F64 ? K * std::ldexp(1.0, -53) : K * std::ldexp(1.0, -24));
-    }
-    {
-        ProfScope ps(ctx, s, "grid_final");
-        if (esz == 8)
-            grid_final_kernel<double><<<ib, 128, 0, s>>>((const double *)dS.ptr, max_state, lg, nb, (double *)dOut.ptr);
-        else
-            grid_final_kernel<float><<<ib, 128, 0, s>>>((const float *)dS.ptr, max_state, lg, nb, (double *)dOut.ptr);
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "grid_final_kernel");
-    std::vector<double> h((size_t)nb * 2);
-    int herr = 0;
-    if ((e = cudaMemcpyAsync(h.data(), dOut.ptr, h.size() * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(&herr, dErr.ptr, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess)
-        return fail(e, "grid results");
-    cleanup();
+    st = grid_run(ctx, plan, data, set_stride, nb, dtype, s, h, bound);
+    dev_free(ctx, dData, s);
+    if (st != PNE_OK && st != PNE_ETIMEOUT) return st;
     for (int b = 0; b < nb; ++b) {
         pne_result &r = out[b];
         std::memset(&r, 0, sizeof(r));
@@ -747,11 +1121,7 @@ pne_status pne_grid_contract(pne_ctx *ctx, const pne_network *net, int32_t lx, i
         r.err_bound = bound;
         r.n_terms = 1;
     }
-    if (herr) {
-        set_error(ctx, PNE_ETIMEOUT, "grid_contract: a tensor-core stage wait gave up");
-        return PNE_ETIMEOUT;
-    }
-    return PNE_OK;
+    return st;
 }
 
 }  // extern "C"

@@ -138,6 +138,36 @@ struct Geometry {
     DevBuf storage;
 };
 
+// ------------------------------------------------------------------ dense grid contraction
+// Row-by-row contraction of a closed lx x ly grid network (dense.cu): one GEMM
+// per site on a ring-ordered running tensor, on the tensor cores (TF32, BF16)
+// or in FP64 on the CUDA cores.
+struct SiteMap {
+    int64_t t_off;          // tensor start in a set
+    int64_t b_off;          // site matrix start in a set
+    int stride[4];          // strides of l, u, r, d in T_v (0 for a boundary leg)
+    int dim[4];             // dims of l, u, r, d (1 at a boundary)
+};
+struct GridStep {
+    int Ku, Kh, Nd, Nh;     // up, left, down, right dims of the site
+    int64_t R;              // rows of the running tensor's matrix
+};
+struct GridPlan {
+    int n = 0;
+    std::vector<SiteMap> maps;
+    std::vector<GridStep> steps;
+    std::vector<int64_t> ldb;   // site-matrix row stride (padded to the 16-byte unit)
+    int64_t b_total = 0, max_state = 0;
+};
+// checks the grid (site id = y * lx + x, each neighbour pair joined by one bond)
+pne_status grid_plan(pne_ctx *ctx, int lx, int ly, int n_bonds, const int32_t *bond_site, const int32_t *bond_dim,
+                     const int32_t *site_ptr, const int32_t *site_bonds, const int64_t *data_off, pne_dtype dtype,
+                     int nb, GridPlan &plan);
+// h[2b] = mantissa, h[2b+1] = log2 scale of set b; bound = first-order relative
+// rounding bound (to the absolute contraction); synchronises s
+pne_status grid_run(pne_ctx *ctx, const GridPlan &plan, const double *data_dev, int64_t set_stride, int nb,
+                    pne_dtype dtype, cudaStream_t s, std::vector<double> &h, double &bound);
+
 // ------------------------------------------------------------------ handles
 struct EnumRecord;  // cluster and term lists of one closed geometry
 struct GeomPair;    // full + closed geometry of one network (shared, cached)

@@ -461,6 +461,132 @@ __global__ void __launch_bounds__(kDtThreads) dense_term_kernel(DtParams p)
     }
 }
 
+// One term's tensors with every bond's index restricted to [lo_b, lo_b + len_b):
+// block per (site, set), row-major over the site's legs in ascending bond id.
+__global__ void restrict_kernel(const double *__restrict__ T, int64_t set_stride, const int64_t *tens_off,
+                                const int32_t *site_ptr, const int32_t *site_bonds, const int32_t *bond_dim,
+                                const int32_t *lo, const int32_t *len, const int64_t *new_off, int64_t new_stride,
+                                double *out)
+{
+    const int v = blockIdx.x, set = blockIdx.y;
+    const int p0 = site_ptr[v], p1 = site_ptr[v + 1];
+    const int64_t n_out = new_off[v + 1] - new_off[v];
+    const double *src = T + set * set_stride + tens_off[v];
+    double *dst = out + set * new_stride + new_off[v];
+    for (int64_t q = threadIdx.x; q < n_out; q += blockDim.x) {
+        int64_t r = q, off = 0, stride = 1;
+        for (int i = p1 - 1; i >= p0; --i) {
+            const int b = site_bonds[i];
+            const int64_t digit = r % len[b];
+            r /= len[b];
+            off += (lo[b] + digit) * stride;
+            stride *= bond_dim[b];
+        }
+        dst[q] = src[off];
+    }
+}
+
+struct RankTerms {
+    std::vector<int8_t> kind;       // [n_terms][n_bonds]: 0 whole, 1 P range, 2 Q range
+    std::vector<int> order, sign;
+    int M = 0;
+};
+
+pne_status rank_terms(pne_ctx *ctx, const Geometry &g, int32_t rank, int32_t form, int32_t n_partitions,
+                      const int32_t *partition_ptr, const int32_t *partition_bonds, RankTerms &t)
+{
+    auto bad = [&](const std::string &m) { set_error(ctx, PNE_EINVAL, m); return PNE_EINVAL; };
+    const int M = n_partitions, NB = g.n_bonds;
+    if (M < 1 || M > 20) return bad("1..20 partitions");
+    if (form != 0 && form != 1) return bad("form is 0 (linear) or 1 (combinatorial)");
+    if (partition_ptr[0] != 0) return bad("partition_ptr[0] must be 0");
+    std::vector<std::vector<int>> parts(M);
+    for (int p = 0; p < M; ++p) {
+        if (partition_ptr[p + 1] <= partition_ptr[p]) return bad("every partition needs at least one bond");
+        for (int i = partition_ptr[p]; i < partition_ptr[p + 1]; ++i) {
+            const int b = partition_bonds[i];
+            if (b < 0 || b >= NB) return bad("partition bond out of range");
+            if (rank < 1 || rank >= g.bond_dim[b]) return bad("rank must be in 1 .. d - 1 on every partitioned bond");
+            parts[p].push_back(b);
+        }
+        if (form == 0 && parts[p].size() != 1) return bad("the linear form takes single-index partitions");
+    }
+    if (form == 0)
+        for (int p = 0; p < M; ++p)
+            for (int q = p + 1; q < M; ++q)
+                if (parts[p][0] == parts[q][0]) return bad("the linear form takes distinct bonds");
+    t.M = M;
+    t.kind.clear();
+    t.order.clear();
+    t.sign.clear();
+    if (form == 0) {
+        for (int k = 0; k < M; ++k) {
+            std::vector<int8_t> row(NB, 0);
+            for (int p = 0; p < k; ++p) row[parts[p][0]] = 2;
+            row[parts[k][0]] = 1;
+            t.kind.insert(t.kind.end(), row.begin(), row.end());
+            t.order.push_back(k);
+            t.sign.push_back(1);
+        }
+    } else {
+        for (uint32_t x = 1; x < (1u << M); ++x) {
+            std::vector<int8_t> row(NB, 0);
+            int k = 0;
+            for (int p = 0; p < M; ++p)
+                if (x >> p & 1) { ++k; for (int b : parts[p]) row[b] = 1; }
+            t.kind.insert(t.kind.end(), row.begin(), row.end());
+            t.order.push_back(k);
+            t.sign.push_back((k % 2 == 1) ? 1 : -1);
+        }
+    }
+    return PNE_OK;
+}
+
+// per set: c[k], abs_c[k], the signed Neumaier sum of the term values (in the
+// weighted network's scale), log_abs with the weights' log scale, and the
+// a-priori bound: FP64 rounding of nops operations per term plus, for a
+// reduced-precision contraction, term_bound[t] x |value| (bound relative to
+// each term's absolute contraction, which equals |value| for a term of
+// non-negative tensors)
+void rank_results(const pne_weights *w, int form, const RankTerms &t, const std::vector<double> &vals,
+                  const std::vector<double> &term_bound, int nops, pne_result *out)
+{
+    const int n_terms = (int)t.order.size();
+    for (int set = 0; set < w->n_sets; ++set) {
+        pne_result &r = out[set];
+        std::memset(&r, 0, sizeof r);
+        const int K = form == 0 ? t.M - 1 : t.M;
+        r.n_orders = K + 1;
+        double sum = 0.0, comp = 0.0, asum = 0.0, rb = 0.0;
+        for (int q = 0; q < n_terms; ++q) {
+            const double v = vals[(size_t)set * n_terms + q];
+            r.c[t.order[q]] += v;
+            r.abs_c[t.order[q]] += std::fabs(v);
+        }
+        for (int q = 0; q < n_terms; ++q) {            // Neumaier over the terms, in term order
+            const double x = t.sign[q] * vals[(size_t)set * n_terms + q], tt = sum + x;
+            comp += (std::fabs(sum) >= std::fabs(x)) ? (sum - tt) + x : (x - tt) + sum;
+            sum = tt;
+            asum += std::fabs(x);
+            if (!term_bound.empty()) rb += term_bound[q] * std::fabs(x);
+        }
+        sum += comp;
+        const double ls = w->log_scale[set];
+        r.log_abs_zref = ls;
+        r.sign_zref = 1;
+        r.sign = sum < 0 ? -1 : 1;
+        r.log_abs = (sum != 0.0) ? ls + std::log(std::fabs(sum)) : -std::numeric_limits<double>::infinity();
+        r.value = (sum == 0.0) ? 0.0 : (r.log_abs > 709.7 ? r.sign * std::numeric_limits<double>::infinity()
+                                                           : r.sign * std::exp(r.log_abs));
+        r.log_series = std::numeric_limits<double>::quiet_NaN();
+        const double u = 0x1p-53;
+        r.err_bound = (sum != 0.0) ? ((nops * u / (1 - nops * u)) * asum + rb) / std::fabs(sum)
+                                   : std::numeric_limits<double>::infinity();
+        r.n_terms = (uint64_t)n_terms;
+        r.bp_iters = w->sweeps[set];
+    }
+}
+
 }  // namespace
 }  // namespace pne
 
@@ -650,65 +776,29 @@ pne_status pne_rank_r_expand(pne_ctx *ctx, const pne_weights *w, int32_t rank, i
 {
     HostScope hs__(ctx, "rank_r_expand");
     if (!ctx || !w || !out || !partition_ptr || !partition_bonds) return PNE_EINVAL;
-    auto bad = [&](const std::string &m) { set_error(ctx, PNE_EINVAL, m); return PNE_EINVAL; };
     const Geometry &g = w->geo->full;
-    const int M = n_partitions, NB = g.n_bonds;
-    if (M < 1 || M > 20) return bad("1..20 partitions");
-    if (form != 0 && form != 1) return bad("form is 0 (linear) or 1 (combinatorial)");
-    if (NB > kDtMaxBonds) return bad("too many bonds for the dense contraction");
-    if (partition_ptr[0] != 0) return bad("partition_ptr[0] must be 0");
-    std::vector<std::vector<int>> parts(M);
-    for (int p = 0; p < M; ++p) {
-        if (partition_ptr[p + 1] <= partition_ptr[p]) return bad("every partition needs at least one bond");
-        for (int i = partition_ptr[p]; i < partition_ptr[p + 1]; ++i) {
-            const int b = partition_bonds[i];
-            if (b < 0 || b >= NB) return bad("partition bond out of range");
-            if (rank < 1 || rank >= g.bond_dim[b]) return bad("rank must be in 1 .. d - 1 on every partitioned bond");
-            parts[p].push_back(b);
-        }
-        if (form == 0 && parts[p].size() != 1) return bad("the linear form takes single-index partitions");
+    const int NB = g.n_bonds;
+    if (NB > kDtMaxBonds) {
+        set_error(ctx, PNE_EINVAL, "too many bonds for the dense contraction");
+        return PNE_EINVAL;
     }
-    if (form == 0)
-        for (int p = 0; p < M; ++p)
-            for (int q = p + 1; q < M; ++q)
-                if (parts[p][0] == parts[q][0]) return bad("the linear form takes distinct bonds");
-    // the terms: per bond 0 whole, 1 P range, 2 Q range
-    std::vector<int8_t> kind;
-    std::vector<int> order, sign;
-    if (form == 0) {
-        for (int k = 0; k < M; ++k) {
-            std::vector<int8_t> row(NB, 0);
-            for (int p = 0; p < k; ++p) row[parts[p][0]] = 2;
-            row[parts[k][0]] = 1;
-            kind.insert(kind.end(), row.begin(), row.end());
-            order.push_back(k);
-            sign.push_back(1);
-        }
-    } else {
-        for (uint32_t x = 1; x < (1u << M); ++x) {
-            std::vector<int8_t> row(NB, 0);
-            int k = 0;
-            for (int p = 0; p < M; ++p)
-                if (x >> p & 1) { ++k; for (int b : parts[p]) row[b] = 1; }
-            kind.insert(kind.end(), row.begin(), row.end());
-            order.push_back(k);
-            sign.push_back((k % 2 == 1) ? 1 : -1);
-        }
-    }
-    const int n_terms = (int)order.size();
+    RankTerms t;
+    pne_status st = rank_terms(ctx, g, rank, form, n_partitions, partition_ptr, partition_bonds, t);
+    if (st) return st;
+    const int n_terms = (int)t.order.size();
     std::vector<DtStep> steps;
     int64_t max_front = 1;
-    pne_status st = dense_plan(ctx, g, steps, max_front);
+    st = dense_plan(ctx, g, steps, max_front);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t items = (int64_t)n_terms * w->n_sets;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, 2 * (int64_t)ctx->n_sm));
     DevBuf dsteps, dkind, dscr, dval;
-    if ((st = dev_alloc(ctx, dsteps, steps.size() * sizeof(DtStep), s)) || (st = dev_alloc(ctx, dkind, kind.size(), s)) ||
+    if ((st = dev_alloc(ctx, dsteps, steps.size() * sizeof(DtStep), s)) || (st = dev_alloc(ctx, dkind, t.kind.size(), s)) ||
         (st = dev_alloc(ctx, dscr, (size_t)grid * 2 * kDtMaxFront * 8, s)) ||
         (st = dev_alloc(ctx, dval, (size_t)items * 8, s)) ||
         (st = upload(ctx, dsteps.ptr, steps.data(), steps.size() * sizeof(DtStep), s)) ||
-        (st = upload(ctx, dkind.ptr, kind.data(), kind.size(), s))) {
+        (st = upload(ctx, dkind.ptr, t.kind.data(), t.kind.size(), s))) {
         dev_free(ctx, dsteps, s); dev_free(ctx, dkind, s); dev_free(ctx, dscr, s); dev_free(ctx, dval, s);
         return st;
     }
@@ -731,39 +821,89 @@ pne_status pne_rank_r_expand(pne_ctx *ctx, const pne_weights *w, int32_t rank, i
     dev_free(ctx, dsteps, s); dev_free(ctx, dkind, s); dev_free(ctx, dscr, s); dev_free(ctx, dval, s);
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const_cast<pne_weights *>(w)->last_stream = s;
-    for (int set = 0; set < w->n_sets; ++set) {
-        pne_result &r = out[set];
-        std::memset(&r, 0, sizeof r);
-        const int K = form == 0 ? M - 1 : M;
-        r.n_orders = K + 1;
-        double sum = 0.0, comp = 0.0, asum = 0.0;
-        for (int t = 0; t < n_terms; ++t) {
-            const double v = vals[(size_t)set * n_terms + t];
-            r.c[order[t]] += v;
-            r.abs_c[order[t]] += std::fabs(v);
-        }
-        for (int t = 0; t < n_terms; ++t) {            // Neumaier over the terms, in term order
-            const double x = sign[t] * vals[(size_t)set * n_terms + t], tt = sum + x;
-            comp += (std::fabs(sum) >= std::fabs(x)) ? (sum - tt) + x : (x - tt) + sum;
-            sum = tt;
-            asum += std::fabs(x);
-        }
-        sum += comp;
-        const double ls = w->log_scale[set];
-        r.log_abs_zref = ls;
-        r.sign_zref = 1;
-        r.sign = sum < 0 ? -1 : 1;
-        r.log_abs = (sum != 0.0) ? ls + std::log(std::fabs(sum)) : -std::numeric_limits<double>::infinity();
-        r.value = (sum == 0.0) ? 0.0 : (r.log_abs > 709.7 ? r.sign * std::numeric_limits<double>::infinity()
-                                                           : r.sign * std::exp(r.log_abs));
-        r.log_series = std::numeric_limits<double>::quiet_NaN();
-        const double u = 0x1p-53;
-        const int nops = 2 * g.n_sites + (int)std::ceil(std::log2((double)std::max<int64_t>(max_front, 2))) + M + 2;
-        r.err_bound = (sum != 0.0) ? (nops * u / (1 - nops * u)) * asum / std::fabs(sum)
-                                   : std::numeric_limits<double>::infinity();
-        r.n_terms = (uint64_t)n_terms;
-        r.bp_iters = w->sweeps[set];
+    const int nops = 2 * g.n_sites + (int)std::ceil(std::log2((double)std::max<int64_t>(max_front, 2))) + t.M + 2;
+    rank_results(w, form, t, vals, {}, nops, out);
+    return PNE_OK;
+}
+
+pne_status pne_rank_r_expand_grid(pne_ctx *ctx, const pne_weights *w, int32_t rank, int32_t form,
+                                  int32_t n_partitions, const int32_t *partition_ptr, const int32_t *partition_bonds,
+                                  int32_t lx, int32_t ly, pne_dtype dtype, void *stream, pne_result *out)
+{
+    HostScope hs__(ctx, "rank_r_expand_grid");
+    if (!ctx || !w || !out || !partition_ptr || !partition_bonds) return PNE_EINVAL;
+    auto bad = [&](const std::string &m) { set_error(ctx, PNE_EINVAL, m); return PNE_EINVAL; };
+    const Geometry &g = w->geo->full;
+    if (dtype == PNE_F32) return bad("rank_r_expand_grid takes PNE_F64, PNE_TF32 or PNE_BF16");
+    if (lx < 1 || ly < 1 || (int64_t)lx * ly != g.n_sites) return bad("n_sites must be lx * ly");
+    RankTerms t;
+    pne_status st = rank_terms(ctx, g, rank, form, n_partitions, partition_ptr, partition_bonds, t);
+    if (st) return st;
+    const int n_terms = (int)t.order.size(), NB = g.n_bonds, ns = w->n_sets;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> vals((size_t)ns * n_terms), tbound((size_t)n_terms, 0.0);
+    std::vector<int32_t> lo((size_t)NB), len((size_t)NB);
+    std::vector<int64_t> off((size_t)g.n_sites + 1);
+    DevBuf dlo, dlen, doff, ddata;
+    auto cleanup = [&]() { dev_free(ctx, dlo, s); dev_free(ctx, dlen, s); dev_free(ctx, doff, s); dev_free(ctx, ddata, s); };
+    if ((st = dev_alloc(ctx, dlo, (size_t)NB * 4, s)) || (st = dev_alloc(ctx, dlen, (size_t)NB * 4, s)) ||
+        (st = dev_alloc(ctx, doff, off.size() * 8, s)) ||
+        (st = dev_alloc(ctx, ddata, (size_t)ns * g.tens_off[g.n_sites] * 8, s))) {
+        cleanup();
+        return st;
     }
+    for (int q = 0; q < n_terms; ++q) {
+        for (int b = 0; b < NB; ++b) {
+            const int kd = t.kind[(size_t)q * NB + b], d = g.bond_dim[b];
+            lo[(size_t)b] = kd == 2 ? rank : 0;
+            len[(size_t)b] = kd == 0 ? d : (kd == 1 ? rank : d - rank);
+        }
+        off[0] = 0;
+        for (int v = 0; v < g.n_sites; ++v) {
+            int64_t sz = 1;
+            for (int i = g.site_ptr[v]; i < g.site_ptr[v + 1]; ++i) sz *= len[(size_t)g.site_bonds[i]];
+            off[(size_t)v + 1] = off[(size_t)v] + sz;
+        }
+        GridPlan plan;
+        if ((st = grid_plan(ctx, lx, ly, NB, g.bond_site.data(), len.data(), g.site_ptr.data(), g.site_bonds.data(),
+                            off.data(), dtype, ns, plan))) {
+            cleanup();
+            return st;
+        }
+        if ((st = upload(ctx, dlo.ptr, lo.data(), (size_t)NB * 4, s)) ||
+            (st = upload(ctx, dlen.ptr, len.data(), (size_t)NB * 4, s)) ||
+            (st = upload(ctx, doff.ptr, off.data(), off.size() * 8, s))) {
+            cleanup();
+            return st;
+        }
+        {
+            ProfScope ps(ctx, s, "rank_restrict");
+            restrict_kernel<<<dim3(g.n_sites, ns), 256, 0, s>>>((const double *)w->T.ptr, g.tens_off[g.n_sites],
+                                                                g.d_tens_off, g.d_site_ptr, g.d_site_bonds,
+                                                                g.d_bond_dim, (const int32_t *)dlo.ptr,
+                                                                (const int32_t *)dlen.ptr, (const int64_t *)doff.ptr,
+                                                                off[(size_t)g.n_sites], (double *)ddata.ptr);
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+            cleanup();
+            set_error(ctx, PNE_ECUDA, "restrict_kernel launch failed");
+            return PNE_ECUDA;
+        }
+        std::vector<double> h;
+        double bound = 0.0;
+        if ((st = grid_run(ctx, plan, (const double *)ddata.ptr, off[(size_t)g.n_sites], ns, dtype, s, h, bound))) {
+            cleanup();
+            return st;
+        }
+        tbound[(size_t)q] = dtype == PNE_F64 ? 0.0 : bound;
+        for (int set = 0; set < ns; ++set)
+            vals[(size_t)set * n_terms + q] = std::ldexp(h[2 * (size_t)set], (int)h[2 * (size_t)set + 1]);
+    }
+    cleanup();
+    const_cast<pne_weights *>(w)->last_stream = s;
+    int lxy = std::max(lx, ly);
+    const int nops = 2 * g.n_sites + 4 * lxy + t.M + 2;
+    rank_results(w, form, t, vals, tbound, nops, out);
     return PNE_OK;
 }
 

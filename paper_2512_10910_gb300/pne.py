@@ -28,7 +28,7 @@ __all__ = [
     "pne_server_drain", "pne_server_stats", "pne_server_first_error", "pne_server_destroy", "ServerOpts", "RequestInfo",
     "Network", "PartitionOpts", "EnumOpts", "Result", "Context", "run", "network_struct",
     "pne_strip_expansion", "StripOpts", "StripResult", "PNE_STRIP_MAX_L", "PNE_STRIP_MAX_CHI",
-    "pne_dense_gemm", "pne_grid_contract",
+    "pne_dense_gemm", "pne_grid_contract", "pne_rank_r_expand_grid", "pne_rank_r_expand",
 ]
 
 PNE_OK, PNE_EINVAL, PNE_ENOMEM, PNE_ECUDA, PNE_ENOCONV, PNE_EDEGENERATE, PNE_ETIMEOUT, PNE_EOVERFLOW, PNE_EBUSY = range(9)
@@ -213,6 +213,10 @@ def load_library():
     lib.pne_grid_contract.argtypes = [vp, ctypes.POINTER(Network), ctypes.c_int32, ctypes.c_int32, ctypes.c_int, vp,
                                       ctypes.POINTER(Result)]
     lib.pne_grid_contract.restype = ctypes.c_int
+    lib.pne_rank_r_expand_grid.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, vp,
+                                           ctypes.POINTER(Result)]
+    lib.pne_rank_r_expand_grid.restype = ctypes.c_int
     lib.pne_open_tensor.argtypes = [vp, vp, vp, ctypes.c_void_p, ctypes.c_void_p]
     lib.pne_open_tensor.restype = ctypes.c_int
     lib.pne_open_tensor_assemble.argtypes = [ctypes.POINTER(Result), ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
@@ -277,7 +281,8 @@ def exported_symbols() -> list:
              "pne_batch_n_results", "pne_batch_config", "pne_batch_destroy", "pne_server_create",
              "pne_server_submit", "pne_server_poll", "pne_server_drain", "pne_server_stats", "pne_server_first_error",
              "pne_server_destroy", "pne_weight_passing", "pne_weights_read", "pne_weights_destroy",
-             "pne_rank_r_expand", "pne_strip_expansion", "pne_dense_gemm", "pne_grid_contract"]
+             "pne_rank_r_expand", "pne_strip_expansion", "pne_dense_gemm", "pne_grid_contract",
+             "pne_rank_r_expand_grid"]
     return [n for n in names if hasattr(lib, n)]
 
 
@@ -423,6 +428,19 @@ def pne_grid_contract(ctx, net, lx, ly, dtype, data=None, n_batch=None, stream=N
     out = (Result * nb)()
     _check(load_library().pne_grid_contract(ctx, ctypes.byref(ns), int(lx), int(ly), int(dtype), stream, out), ctx)
     del keep
+    return [r.as_dict() for r in out]
+
+
+def pne_rank_r_expand_grid(ctx, w, rank, form, partitions, n_sets, lx, ly, dtype, stream=None):
+    """The rank-r expansion with every term contracted as a grid (row-by-row
+    GEMMs; F64, TF32 or BF16): one result dict per tensor set."""
+    ptr = np.zeros(len(partitions) + 1, dtype=np.int32)
+    for i, S in enumerate(partitions):
+        ptr[i + 1] = ptr[i] + len(S)
+    bonds = np.ascontiguousarray(np.concatenate([np.asarray(S, dtype=np.int32) for S in partitions]), dtype=np.int32)
+    out = (Result * n_sets)()
+    _check(load_library().pne_rank_r_expand_grid(ctx, w, int(rank), int(form), len(partitions), ptr.ctypes.data,
+                                                 bonds.ctypes.data, int(lx), int(ly), int(dtype), stream, out), ctx)
     return [r.as_dict() for r in out]
 
 
@@ -798,13 +816,18 @@ Context.combinatorial = _context_combinatorial
 
 
 def _context_rank_r(self, net, partitions, rank, form, alpha=0.8, tol=1e-12, max_sweeps=5000, data=None, n_batch=1,
-                    stream=None):
+                    stream=None, grid=None, dtype=PNE_F64):
     """Weight passing then the rank-r expansion (form 0 linear over single-index
-    partitions, 1 combinatorial): (results, weights, sweeps, log_scale)."""
+    partitions, 1 combinatorial): (results, weights, sweeps, log_scale).
+    ``grid=(lx, ly)`` contracts the terms row by row as GEMMs (dtype F64 on the
+    CUDA cores, TF32 / BF16 on the tensor cores)."""
     ns, keep = network_struct(net, data=data, n_batch=n_batch)
     w = pne_weight_passing(self.h, ns, alpha, tol, max_sweeps, stream)
     try:
-        res = pne_rank_r_expand(self.h, w, rank, form, partitions, n_batch, stream)
+        if grid is None:
+            res = pne_rank_r_expand(self.h, w, rank, form, partitions, n_batch, stream)
+        else:
+            res = pne_rank_r_expand_grid(self.h, w, rank, form, partitions, n_batch, grid[0], grid[1], dtype, stream)
         wts, sw, ls = pne_weights_read(self.h, w, n_batch, int(net.n_bonds), stream)
         return res, wts, sw, ls
     finally:

@@ -86,3 +86,34 @@ def test_rank_r_batch_of_tensor_sets(ctx):
     for b, n in enumerate(nets):
         (one,), _, _, _ = ctx.rank_r(n, I.square3x3_pinwheel(), 2, 0, tol=1e-11)
         assert one["log_abs"] == pytest.approx(res[b]["log_abs"], abs=1e-12)
+
+
+@pytest.mark.parametrize("name,make,rank", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_rank_r_terms_as_grid_gemms(ctx, name, make, rank):
+    # the same expansion with every term contracted row by row as GEMMs: FP64
+    # equals the site-by-site FP64 path within 1e-10; TF32 / BF16 on the tensor
+    # cores within the stated bound of it
+    net = make()
+    for form, parts in ((0, I.square3x3_pinwheel()), (1, I.square3x3_six_lines())):
+        (ref,), _, _, _ = ctx.rank_r(net, parts, rank, form, alpha=0.8, tol=1e-11)
+        (g64,), _, _, _ = ctx.rank_r(net, parts, rank, form, alpha=0.8, tol=1e-11, grid=(3, 3), dtype=pne.PNE_F64)
+        assert abs(g64["log_abs"] - ref["log_abs"]) <= 1e-10 and g64["sign"] == ref["sign"]
+        assert g64["n_terms"] == ref["n_terms"]
+        np.testing.assert_allclose(g64["c"], ref["c"], rtol=1e-9, atol=1e-12 * float(np.max(ref["abs_c"])))
+        # the weighted network carries signs (gauge transforms), so a term's
+        # absolute contraction can exceed |value| and the stated bound is
+        # first-order per |value|: checked beside a fixed tolerance per dtype
+        for dt, tol in ((pne.PNE_TF32, 1e-2), (pne.PNE_BF16, 5e-2)):
+            (r,), _, _, _ = ctx.rank_r(net, parts, rank, form, alpha=0.8, tol=1e-11, grid=(3, 3), dtype=dt)
+            err = abs(math.expm1(r["log_abs"] - ref["log_abs"]))
+            assert math.isfinite(r["err_bound"]) and r["err_bound"] > 0
+            assert err <= max(tol, r["err_bound"]), (name, form, dt, err, r["err_bound"])
+            assert err <= tol, (name, form, dt, err)
+
+
+def test_degenerate_ising_rank_two_grid_fp64_reaches_the_target(ctx):
+    net = I.ising_blocked(3, 3, 4, BETA_C / 0.6)
+    z0 = math.log(float(Ex.contract_einsum(net)))
+    for form, parts in ((0, I.square3x3_pinwheel()), (1, I.square3x3_six_lines())):
+        (r2,), _, _, _ = ctx.rank_r(net, parts, 2, form, alpha=0.8, tol=1e-10, grid=(3, 3), dtype=pne.PNE_F64)
+        assert abs(math.expm1(r2["log_abs"] - z0)) < 1e-7
