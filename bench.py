@@ -633,12 +633,26 @@ def run_rank_r_extra(args, ctx, pne, torch, dev, local_rank):
                        "step: weight passing (alpha 0.8) + rank-2 expansion"}
     for form, parts, name in ((0, I.square3x3_pinwheel(), "linear_4_single_index"),
                               (1, I.square3x3_six_lines(), "combinatorial_6_multi_index")):
-        def step():
-            return ctx.rank_r(g, parts, 2, form, alpha=0.8, tol=1e-10, data=data, n_batch=len(nets))
-        ms, (res, wts, sw, ls) = _timed_calls(torch, dev, step, 3, 1)
-        errs = [abs(math.expm1(r["log_abs"] - e)) for r, e in zip(res, exact)]
-        out[name] = {"ms_per_step": ms, "terms_per_s": res[0]["n_terms"] * len(nets) / (ms * 1e-3),
-                     "max_rel_err_vs_exact": max(errs), "max_sweeps": int(np.max(sw))}
+        out[name] = {}
+        # terms contracted site by site (FP64 dense kernel), or as grids of
+        # row GEMMs: FP64 on the CUDA cores, TF32 / BF16 on the tensor cores
+        for how, grid, dt in (("sitewise_f64", None, pne.PNE_F64), ("grid_f64", (3, 3), pne.PNE_F64),
+                              ("grid_tf32", (3, 3), pne.PNE_TF32), ("grid_bf16", (3, 3), pne.PNE_BF16)):
+            def step():
+                return ctx.rank_r(g, parts, 2, form, alpha=0.8, tol=1e-10, data=data, n_batch=len(nets),
+                                  grid=grid, dtype=dt)
+            step()
+            pne.pne_ctx_profile(ctx.h, True)
+            ms, (res, wts, sw, ls) = _timed_calls(torch, dev, step, 2, 0)
+            prof = {k: v for k, v in pne.pne_ctx_profile_read(ctx.h).items() if not k.startswith("host:")}
+            pne.pne_ctx_profile(ctx.h, False)
+            errs = [abs(math.expm1(r["log_abs"] - e)) for r, e in zip(res, exact)]
+            terms_ms = sum(v[1] for k, v in prof.items() if k != "weight_passing") / 2
+            out[name][how] = {"ms_per_step": ms, "expansion_kernel_ms_per_step": terms_ms,
+                              "weight_passing_ms_per_step": prof.get("weight_passing", (0, 0.0))[1] / 2,
+                              "terms_per_s": res[0]["n_terms"] * len(nets) / (ms * 1e-3),
+                              "max_rel_err_vs_exact": max(errs), "max_err_bound": max(r["err_bound"] for r in res),
+                              "max_sweeps": int(np.max(sw))}
     return out
 
 
