@@ -667,6 +667,156 @@ def run_rank_r_extra(args, ctx, pne, torch, dev, local_rank):
     return out
 
 
+def _onsager_minus_beta_f(beta):
+    """Onsager's free energy per spin of the square-lattice Ising model (J = 1),
+    in its one-dimensional integral form: ln(2 cosh 2b) + (1/pi) int_0^{pi/2}
+    ln[(1 + sqrt(1 - k^2 sin^2 t)) / 2] dt with k = 2 sinh 2b / cosh^2 2b."""
+    from scipy.integrate import quad
+    k = 2 * math.sinh(2 * beta) / math.cosh(2 * beta) ** 2
+    v, _ = quad(lambda t: math.log((1 + math.sqrt(max(0.0, 1 - k * k * math.sin(t) ** 2))) / 2), 0, math.pi / 2,
+                epsabs=1e-15, epsrel=1e-15, limit=400)
+    return math.log(2 * math.cosh(2 * beta)) + v / math.pi
+
+
+def _strip_row_flops(chi, k):
+    """Multiply-adds of one row transfer application of width k (capped first
+    site chi -> chi^2, k - 2 middle sites chi^2 -> chi^2, last site chi^2 ->
+    chi; one chi x chi matrix for k = 1), times 2."""
+    if k == 1:
+        return 2 * chi * chi
+    return 2 * chi ** (k + 2) * (2 + (k - 2) * chi)
+
+
+def run_strip_extra(args, ctx, pne, torch, dev, local_rank):
+    """The infinite-lattice strip expansion (Sec. IV.C) of the 2D Ising model
+    after a 2 x 2 blocking (chi = 4): eight temperatures at strip width L = 10
+    in one call, float-float and FP64 row products, and one L = 12 call (24
+    spins wide) at one temperature; free energies against Onsager's."""
+    betas = [0.30, 0.36, 0.40, 0.42, 0.44, 0.46, 0.50, 0.60]
+    A = np.stack([I.uniform_ising(b, 2) for b in betas])
+    exact = [-4.0 * _onsager_minus_beta_f(b) for b in betas]
+    peak64 = pne.pne_measure_fma_peak(ctx.h, pne.PNE_F64, None)
+    peak32 = pne.pne_measure_fma_peak(ctx.h, pne.PNE_F32, None)
+    out = {"workload": "infinite 2D Ising, 2x2 blocked (chi = 4), 2D strip expansion; 8 temperatures "
+                       "beta in {0.30..0.60} per call at L = 10 (20 spins wide), one call at L = 12 (24 spins)",
+           "reference": "Onsager's free energy (one-dimensional integral form), 4 spins per blocked site"}
+    for L, sel, tag in ((10, list(range(len(betas))), "L10_8_temperatures"), (12, [4], "L12_beta0.44")):
+        for arith, aname in ((1, "ff"), (0, "fp64")):
+            if L == 12 and arith == 0:
+                continue
+            pne.pne_ctx_profile(ctx.h, True)
+            t0 = time.perf_counter()
+            res = pne.pne_strip_expansion(ctx.h, A[sel], L, arithmetic=arith, allow_noconv=True)
+            wall = time.perf_counter() - t0
+            prof = {k: v for k, v in pne.pne_ctx_profile_read(ctx.h).items() if not k.startswith("host:")}
+            pne.pne_ctx_profile(ctx.h, False)
+            flops = sum(r["iters"][o][k] * _strip_row_flops(4, k) for r in res for o in (0, 1) for k in range(1, L + 1))
+            row_ms = prof.get("strip_row", (0, 0.0))[1]
+            peak = peak64 if arith == 0 else peak32 / 12.0
+            rec = {"wall_s": wall, "kernel_ms": {k: round(v[1], 3) for k, v in prof.items()},
+                   "max_rel_err_vs_onsager": max(abs(r["f"] - exact[i]) / abs(exact[i]) for i, r in zip(sel, res)),
+                   "rel_err_by_beta": {f"{betas[i]:.2f}": abs(r["f"] - exact[i]) / abs(exact[i])
+                                       for i, r in zip(sel, res)},
+                   "bp_rel_err_by_beta": {f"{betas[i]:.2f}": abs(r["f_bp"] - exact[i]) / abs(exact[i])
+                                          for i, r in zip(sel, res)},
+                   "max_power_iterations": max(r["eig_iters"] for r in res),
+                   "status": sorted({int(r["status"]) for r in res}),
+                   "row_products": {"bound": "alu", "unit": "TFLOP/s", "achieved": flops / (row_ms * 1e-3) / 1e12,
+                                    "peak": peak / 1e12, "frac": flops / (row_ms * 1e-3) / peak if row_ms else None,
+                                    "work": "2 flops per multiply-add of the site-by-site row products, summed over "
+                                            "every power iteration of every width and orientation",
+                                    "peak_source": ("measured FP64 FMA-chain kernel" if arith == 0 else
+                                                    "measured FP32 FMA-chain kernel / 12 FP32 instructions per "
+                                                    "float-float multiply-add")}}
+            out[f"{tag}_{aname}"] = rec
+    return out
+
+
+def _grid_flops(lx, ly, chi):
+    """2 x the multiply-adds of the row-by-row contraction of an lx x ly grid
+    of uniform bond dimension chi (the site GEMMs, boundary legs of size 1)."""
+    state, total = 1, 0
+    for y in range(ly):
+        for x in range(lx):
+            ku, kh = (chi if y > 0 else 1), (chi if x > 0 else 1)
+            nd, nh = (chi if y + 1 < ly else 1), (chi if x + 1 < lx else 1)
+            r = state // (ku * kh)
+            total += 2 * r * ku * kh * nd * nh
+            state = r * nd * nh
+    return total
+
+
+def run_dense_extra(args, ctx, pne, torch, dev, local_rank):
+    """Dense contractions of blocked large-chi networks: the tcgen05 GEMM alone
+    (4 x 32768 x 256 x 256) and the exact contraction of 32 random 5 x 4
+    networks of bond dimension 16 (the paper's blocked random benchmark
+    networks), TF32 and BF16 on the tensor cores against FP64 on the CUDA cores."""
+    peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    bf16_peak = float(peaks["bf16_tflops"])
+    peak = {pne.PNE_BF16: bf16_peak, pne.PNE_TF32: bf16_peak * 1.1 / 2.25, pne.PNE_F64: None}
+    f64_peak = pne.pne_measure_fma_peak(ctx.h, pne.PNE_F64, None) / 1e12
+    names = {pne.PNE_TF32: "tf32", pne.PNE_BF16: "bf16", pne.PNE_F64: "f64"}
+    out = {"workload": f"tcgen05 GEMM 4 x (32768 x 256 x 256); exact contraction of {args.dense_nets} random 5x4 "
+                       "networks, bond dimension 16 (U[0,1)+0.1), 20 site GEMMs each",
+           "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured); TF32 = that x 1.1/2.25 (nominal ratio); "
+                          "FP64 = measured FMA-chain kernel"}
+    batch, M, N, K = 4, 32768, 256, 256
+    g = torch.Generator(device="cpu").manual_seed(5)
+    A64 = torch.rand(batch, M, K, generator=g, dtype=torch.float64).to(dev)
+    B64 = torch.rand(batch, N, K, generator=g, dtype=torch.float64).to(dev)
+    ref = None
+    gemm = {}
+    for dt in (pne.PNE_F64, pne.PNE_TF32, pne.PNE_BF16):
+        A = A64 if dt == pne.PNE_F64 else A64.float()
+        B = B64 if dt == pne.PNE_F64 else B64.float()
+        C = torch.empty(batch, M, N, dtype=A.dtype, device=dev)
+        pne.pne_dense_gemm(ctx.h, dt, A, B, C)
+        pne.pne_ctx_profile(ctx.h, True)
+        reps = 3 if dt == pne.PNE_F64 else 20
+        for _ in range(reps):
+            pne.pne_dense_gemm(ctx.h, dt, A, B, C)
+        prof = pne.pne_ctx_profile_read(ctx.h)
+        pne.pne_ctx_profile(ctx.h, False)
+        key = "dense_gemm_f64" if dt == pne.PNE_F64 else "dense_gemm_tc"
+        ms = prof[key][1] / prof[key][0]
+        tf = 2.0 * batch * M * N * K / (ms * 1e-3) / 1e12
+        if dt == pne.PNE_F64:
+            ref = C.double()
+            err = 0.0
+        else:
+            err = float(((C.double() - ref).abs() / ref.abs()).max())
+        pk = peak[dt] if peak[dt] else f64_peak
+        gemm[names[dt]] = {"ms": ms, "tflops": tf, "peak_tflops": pk, "frac": tf / pk, "max_rel_err_vs_f64": err}
+    out["gemm"] = gemm
+    lx, ly, chi, nn = 5, 4, 16, args.dense_nets
+    gg = I.square_lattice(lx, ly, chi)
+    flat = np.concatenate([I.random_tensors(gg, 7000 + i).flat_data()[0] for i in range(nn)])
+    data = torch.from_numpy(flat).to(dev)
+    flops = _grid_flops(lx, ly, chi) * nn
+    grid = {}
+    ref = None
+    for dt in (pne.PNE_F64, pne.PNE_TF32, pne.PNE_BF16):
+        pne.pne_grid_contract(ctx.h, gg, lx, ly, dt, data=data, n_batch=nn)
+        pne.pne_ctx_profile(ctx.h, True)
+        t0 = time.perf_counter()
+        res = pne.pne_grid_contract(ctx.h, gg, lx, ly, dt, data=data, n_batch=nn)
+        wall = time.perf_counter() - t0
+        prof = {k: v for k, v in pne.pne_ctx_profile_read(ctx.h).items() if not k.startswith("host:")}
+        pne.pne_ctx_profile(ctx.h, False)
+        key = "grid_gemm_f64" if dt == pne.PNE_F64 else "grid_gemm_tc"
+        gms = prof[key][1]
+        if dt == pne.PNE_F64:
+            ref = [r["log_abs"] for r in res]
+        err = max(abs(math.expm1(r["log_abs"] - e)) for r, e in zip(res, ref))
+        pk = peak[dt] if peak[dt] else f64_peak
+        grid[names[dt]] = {"wall_s": wall, "networks_per_s": nn / wall, "gemm_ms": gms,
+                           "kernel_ms": {k: round(v[1], 3) for k, v in prof.items()},
+                           "gemm_tflops": flops / (gms * 1e-3) / 1e12, "frac": flops / (gms * 1e-3) / 1e12 / pk,
+                           "max_rel_err_vs_f64": err, "stated_err_bound": res[0]["err_bound"]}
+    out["grid_5x4_chi16"] = grid
+    return out
+
+
 # ---------------------------------------------------------------- cfg4
 def run_batched_extra(args, ctx, pne, torch, dev, local_rank):
     wl = WORKLOADS["batched"]

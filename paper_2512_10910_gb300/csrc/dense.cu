@@ -27,8 +27,12 @@
 // power-of-two scale (kept exactly in a log-2 counter).  The FP64 form
 // (f64_gemm_kernel) is a plain tiled GEMM on the CUDA cores with the same
 // interface: the reference the reduced-precision forms are stated against.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 #include <algorithm>
 #include <cmath>
@@ -756,6 +760,210 @@ __global__ void grid_final_tc_kernel(const E *S, int64_t stride, const unsigned 
     (void)max_last;
 }
 
+// ---- the same site GEMM with the stages filled by the Tensor Memory Accelerator.
+// One elected thread of warp 0 issues, per stage, eight boxes of A (the running
+// tensor viewed as [set][Ku][R][Kh], each box 16 bytes of k by 128 rows) and
+// eight of B ([set][N][ldb], 16 bytes of k by BN rows) on one mbarrier with
+// the stage's byte count; a box lands as 128 (BN) consecutive 16-byte rows,
+// which is the canonical no-swizzle K-major layout with 8-row groups 128
+// bytes apart and the box's K column 2048 (16 BN) bytes from the next.  One
+// thread of warp 1 waits for a full stage, issues its four MMAs and commits
+// them to the stage's empty barrier, which the producer waits on before
+// refilling it.  Used where a 16-byte unit of k is contiguous in the running
+// tensor (Kh a multiple of the unit): the innermost box coordinate is then a
+// multiple of 16 bytes, as the copy requires.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                          uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                 ::"r"(dst), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(dst), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+                 : "memory");
+}
+
+template <typename E, int NST>
+__global__ void __launch_bounds__(kTcThreads, 2) tc_tma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                   const __grid_constant__ CUtensorMap tmB,
+                                                                   RingParams<E> p, int BN)
+{
+    constexpr int EB = (int)sizeof(E);
+    constexpr int EPU = 16 / EB;
+    constexpr int KC = kChunk / EB;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[NST], empty[NST], done;
+    __shared__ uint32_t tmem_base_sh;
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int stage_bytes = kATileBytes + BN * kChunk;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int set = blockIdx.z;
+    const int64_t m0 = (int64_t)blockIdx.x * kTcBM;
+    const int n0 = blockIdx.y * BN;
+    E *out = p.out + set * p.stride;
+    const uint32_t tcols = BN <= 32 ? 32u : (BN <= 64 ? 64u : (BN <= 128 ? 128u : 256u));
+    if (warp == 0) {
+        tmem_alloc(smem_addr(&tmem_base_sh), tcols);
+        tmem_relinquish();
+    }
+    if (tid == 32) {
+        for (int i = 0; i < NST; ++i) {
+            mbar_init(smem_addr(&full[i]), 1);
+            mbar_init(smem_addr(&empty[i]), 1);
+        }
+        mbar_init(smem_addr(&done), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+    const int nchunks = (p.K + KC - 1) / KC;
+    const uint32_t idesc = instr_desc(EB == 4 ? 2u : 1u, kTcBM, (uint32_t)BN);
+    const uint32_t stage_tx = (uint32_t)stage_bytes;
+    int failed = 0;
+    if (tid == 0) {
+        // producer
+        for (int c = 0; c < nchunks && !failed; ++c) {
+            const int s = c % NST;
+            if (c >= NST && !mbar_wait(smem_addr(&empty[s]), (uint32_t)(((c / NST) - 1) & 1))) {
+                failed = 1;
+                break;
+            }
+            const uint32_t fb = smem_addr(&full[s]);
+            mbar_expect_tx(fb, stage_tx);
+            const uint32_t sa = smem_addr(base + s * stage_bytes), sb = sa + kATileBytes;
+#pragma unroll
+            for (int cu = 0; cu < 8; ++cu) {
+                const int k = c * KC + cu * EPU;
+                const int ku = k / p.Kh, kh = k - ku * p.Kh;
+                tma_load4(sa + cu * (kTcBM * 16), &tmA, kh, (int)m0, ku, set, fb);
+                tma_load3(sb + cu * (BN * 16), &tmB, k, n0, set, fb);
+            }
+        }
+    } else if (tid == 32) {
+        // MMA issuer
+        for (int c = 0; c < nchunks; ++c) {
+            const int s = c % NST;
+            if (!mbar_wait(smem_addr(&full[s]), (uint32_t)((c / NST) & 1))) {
+                failed = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_addr(base + s * stage_bytes), sb = sa + kATileBytes;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint64_t ad = smem_desc(sa + ks * 2 * (kTcBM * 16), kTcBM * 16, 128);
+                const uint64_t bd = smem_desc(sb + ks * 2 * (BN * 16), (uint32_t)(BN * 16), 128);
+                tc_mma<EB>(tmem, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+            }
+            tc_commit(smem_addr(&empty[s]));
+        }
+        if (!failed) tc_commit(smem_addr(&done));
+    }
+    // everyone: the accumulator is complete once `done` fires
+    bool ok = __syncthreads_or(failed) == 0;
+    if (ok) ok = mbar_wait(smem_addr(&done), 0u);
+    ok = __syncthreads_and(ok) != 0;
+    tc_fence_after();
+    const float mx_in = __uint_as_float((unsigned)p.max_in[set]);
+    const int e_in = mx_in > 0.f ? ilogbf(mx_in) : 0;
+    const float sc = ldexpf(1.f, -e_in);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+        p.log2s[set] += e_in;
+        p.max_clear[set] = 0ull;
+    }
+    float mx = 0.f;
+    if (ok) {
+        constexpr int SW = 64, SP = SW + 4;
+        float *st = reinterpret_cast<float *>(base);
+        for (int c0 = 0; c0 < BN; c0 += SW) {
+#pragma unroll
+            for (int q = 0; q < SW; q += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + q), r);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) st[(warp * 32 + lane) * SP + q + j] = __uint_as_float(r[j]) * sc;
+            }
+            __syncthreads();
+            for (int i = tid; i < kTcBM * SW; i += kTcThreads) {
+                const int rr = i / SW, cc = i % SW;
+                const int64_t row = m0 + rr;
+                const int col = n0 + c0 + cc;
+                if (row < p.R && col < p.N) {
+                    const E v = round_elem<E>(st[rr * SP + cc]);
+                    out[row * p.N + col] = v;
+                    mx = fmaxf(mx, fabsf(elem_to_float<E>(v)));
+                }
+            }
+            __syncthreads();
+        }
+    } else if (tid == 0) {
+        atomicExch(p.err, 1);
+    }
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0 && mx > 0.f) atomicMax(p.max_out + set, (unsigned long long)__float_as_uint(mx));
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, tcols);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    });
+    return fn;
+}
+
+template <typename E, int NST>
+cudaError_t launch_tma_n(const RingParams<E> &p, int batch, int BN, int n_sets, cudaStream_t s, bool &used)
+{
+    used = false;
+    auto enc = tensor_map_encoder();
+    if (!enc) return cudaSuccess;
+    constexpr int EB = (int)sizeof(E);
+    const CUtensorMapDataType dt = EB == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUtensorMap ma, mb;
+    // A: [set][Ku][R][Kh], innermost first
+    const cuuint64_t adim[4] = {(cuuint64_t)p.Kh, (cuuint64_t)p.R, (cuuint64_t)p.Ku, (cuuint64_t)n_sets};
+    const cuuint64_t astr[3] = {(cuuint64_t)p.Kh * EB, (cuuint64_t)p.R * p.Kh * EB, (cuuint64_t)p.stride * EB};
+    const cuuint32_t abox[4] = {(cuuint32_t)(16 / EB), (cuuint32_t)kTcBM, 1, 1};
+    const cuuint32_t one4[4] = {1, 1, 1, 1};
+    // B: [set][N][ldb]
+    const cuuint64_t bdim[3] = {(cuuint64_t)p.ldb, (cuuint64_t)p.N, (cuuint64_t)n_sets};
+    const cuuint64_t bstr[2] = {(cuuint64_t)p.ldb * EB, (cuuint64_t)p.b_stride * EB};
+    const cuuint32_t bbox[3] = {(cuuint32_t)(16 / EB), (cuuint32_t)BN, 1};
+    if (enc(&ma, dt, 4, (void *)p.S, adim, astr, abox, one4, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS ||
+        enc(&mb, dt, 3, (void *)p.B, bdim, bstr, bbox, one4, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+            CUDA_SUCCESS)
+        return cudaSuccess;         // not encodable: the copy-loop kernel runs instead
+    const size_t smem = (size_t)NST * (kATileBytes + BN * kChunk) + 1024;
+    cudaError_t e = grant_dynamic_smem((const void *)tc_tma_gemm_kernel<E, NST>, smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((p.R + kTcBM - 1) / kTcBM), (unsigned)((p.N + BN - 1) / BN), (unsigned)batch);
+    tc_tma_gemm_kernel<E, NST><<<grid, kTcThreads, smem, s>>>(ma, mb, p, BN);
+    used = true;
+    return cudaGetLastError();
+}
+
 // stages per CTA: as many as let two CTAs share an SM (<= 113 KB each, 2 x 256
 // tensor-memory columns), so one CTA's prologue and epilogue overlap the
 // other's main loop
@@ -776,6 +984,16 @@ cudaError_t launch_ring(const RingParams<E> &p, int batch, cudaStream_t s)
     const int BN = std::min(256, ((p.N + 15) / 16) * 16);
     const int stage = kATileBytes + BN * kChunk;
     const int nst = (int)std::max<int64_t>(2, std::min<int64_t>(4, (112 * 1024) / stage));
+    constexpr int EPU = 16 / (int)sizeof(E);
+    // TMA where every 16-byte unit of k is contiguous and every stride a multiple of 16 bytes
+    if (p.Kh % EPU == 0 && (p.ldb % EPU) == 0 && (p.stride % EPU) == 0 && (p.b_stride % EPU) == 0 &&
+        p.R < (int64_t)1 << 31) {
+        bool used = false;
+        cudaError_t e = nst >= 4   ? launch_tma_n<E, 4>(p, batch, BN, batch, s, used)
+                        : nst == 3 ? launch_tma_n<E, 3>(p, batch, BN, batch, s, used)
+                                   : launch_tma_n<E, 2>(p, batch, BN, batch, s, used);
+        if (e != cudaSuccess || used) return e;
+    }
     if (nst >= 4) return launch_ring_n<E, 4>(p, batch, BN, s);
     if (nst == 3) return launch_ring_n<E, 3>(p, batch, BN, s);
     return launch_ring_n<E, 2>(p, batch, BN, s);

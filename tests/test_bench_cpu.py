@@ -52,3 +52,19 @@ def test_served_trace_is_seeded_and_poisson_like():
     kinds = {r[0] for r in r1}
     assert kinds == {"aklt", "rand3d"}
     assert all(4 <= r[3] <= 8 for r in r1)                    # orders K in 4..8
+
+
+def test_every_registered_workload_is_defined():
+    # the extras table names functions resolved only when the default run
+    # reaches it on a GPU; check here that each one exists
+    import ast
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    tree = ast.parse(src)
+    defined = {n.name for n in tree.body if isinstance(n, ast.FunctionDef)}
+    called = set()
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Tuple) and len(node.elts) == 2 and isinstance(node.elts[0], ast.Constant) \
+                and isinstance(node.elts[0].value, str) and isinstance(node.elts[1], ast.Name):
+            called.add(node.elts[1].id)
+    assert {"run_cfg3", "run_strip_extra", "run_dense_extra", "run_rank_r_extra"} <= called
+    assert called <= defined, called - defined
