@@ -49,6 +49,7 @@ constexpr int kTcThreads = 128;
 constexpr int kTcBM = 128;
 constexpr int kChunk = 128;                   // K bytes per row per stage
 constexpr int kATileBytes = kTcBM * kChunk;   // 16 KB
+constexpr int kTmaChunk = 64;                 // K bytes per row per stage of the TMA-fed kernel
 constexpr uint64_t kWaitNs = 2000000000ull;   // bounded mbarrier waits: 2 s
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -797,12 +798,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_tma_gemm_kernel(const __grid
 {
     constexpr int EB = (int)sizeof(E);
     constexpr int EPU = 16 / EB;
-    constexpr int KC = kChunk / EB;
+    constexpr int KC = kTmaChunk / EB;        // k values per stage (64 bytes of each row)
+    constexpr int UNITS = kTmaChunk / 16;     // 16-byte boxes per operand per stage
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[NST], empty[NST], done;
     __shared__ uint32_t tmem_base_sh;
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int stage_bytes = kATileBytes + BN * kChunk;
+    const int a_bytes = kTcBM * kTmaChunk;
+    const int stage_bytes = a_bytes + BN * kTmaChunk;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int set = blockIdx.z;
     const int64_t m0 = (int64_t)blockIdx.x * kTcBM;
@@ -839,9 +842,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_tma_gemm_kernel(const __grid
             }
             const uint32_t fb = smem_addr(&full[s]);
             mbar_expect_tx(fb, stage_tx);
-            const uint32_t sa = smem_addr(base + s * stage_bytes), sb = sa + kATileBytes;
+            const uint32_t sa = smem_addr(base + s * stage_bytes), sb = sa + a_bytes;
 #pragma unroll
-            for (int cu = 0; cu < 8; ++cu) {
+            for (int cu = 0; cu < UNITS; ++cu) {
                 const int k = c * KC + cu * EPU;
                 const int ku = k / p.Kh, kh = k - ku * p.Kh;
                 tma_load4(sa + cu * (kTcBM * 16), &tmA, kh, (int)m0, ku, set, fb);
@@ -857,9 +860,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_tma_gemm_kernel(const __grid
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_addr(base + s * stage_bytes), sb = sa + kATileBytes;
+            const uint32_t sa = smem_addr(base + s * stage_bytes), sb = sa + a_bytes;
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
+            for (int ks = 0; ks < UNITS / 2; ++ks) {
                 const uint64_t ad = smem_desc(sa + ks * 2 * (kTcBM * 16), kTcBM * 16, 128);
                 const uint64_t bd = smem_desc(sb + ks * 2 * (BN * 16), (uint32_t)(BN * 16), 128);
                 tc_mma<EB>(tmem, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
@@ -955,7 +958,8 @@ cudaError_t launch_tma_n(const RingParams<E> &p, int batch, int BN, int n_sets, 
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
             CUDA_SUCCESS)
         return cudaSuccess;         // not encodable: the copy-loop kernel runs instead
-    const size_t smem = (size_t)NST * (kATileBytes + BN * kChunk) + 1024;
+    // the epilogue stages the accumulator through the same shared memory: 128 x 68 floats
+    const size_t smem = std::max<size_t>((size_t)NST * (kTcBM + BN) * kTmaChunk, (size_t)kTcBM * 68 * 4) + 1024;
     cudaError_t e = grant_dynamic_smem((const void *)tc_tma_gemm_kernel<E, NST>, smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((p.R + kTcBM - 1) / kTcBM), (unsigned)((p.N + BN - 1) / BN), (unsigned)batch);
@@ -989,9 +993,13 @@ cudaError_t launch_ring(const RingParams<E> &p, int batch, cudaStream_t s)
     if (p.Kh % EPU == 0 && (p.ldb % EPU) == 0 && (p.stride % EPU) == 0 && (p.b_stride % EPU) == 0 &&
         p.R < (int64_t)1 << 31) {
         bool used = false;
-        cudaError_t e = nst >= 4   ? launch_tma_n<E, 4>(p, batch, BN, batch, s, used)
-                        : nst == 3 ? launch_tma_n<E, 3>(p, batch, BN, batch, s, used)
-                                   : launch_tma_n<E, 2>(p, batch, BN, batch, s, used);
+        // 64-byte stages: twice as many in flight in the same shared memory (two CTAs per SM)
+        const int tstage = (kTcBM + BN) * kTmaChunk;
+        const int tn = (int)std::max<int64_t>(2, std::min<int64_t>(8, (112 * 1024) / tstage));
+        cudaError_t e = tn >= 8   ? launch_tma_n<E, 8>(p, batch, BN, batch, s, used)
+                        : tn >= 6 ? launch_tma_n<E, 6>(p, batch, BN, batch, s, used)
+                        : tn >= 4 ? launch_tma_n<E, 4>(p, batch, BN, batch, s, used)
+                                  : launch_tma_n<E, 2>(p, batch, BN, batch, s, used);
         if (e != cudaSuccess || used) return e;
     }
     if (nst >= 4) return launch_ring_n<E, 4>(p, batch, BN, s);
