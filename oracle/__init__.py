@@ -26,6 +26,9 @@ Contents (each function cites the passage it follows):
                 partitions (Eq. A4).
   weights.py    weight passing (App. C) and expansions with rank-r projectors
                 onto the largest weights (Sec. V), linear and combinatorial.
+  recursive.py  recursive partitioning (Sec. IV.A): the combinatorial form
+                whose too-large sub-networks are expanded again over the
+                second-level partitions that fit inside them.
   strips.py     the infinite-lattice strip expansion (Sec. IV.C): uniform BP,
                 strip transfer-matrix eigenvalues (LAPACK / ARPACK), capped
                 patches by einsum and by row sweeps, and the per-cell sums over

@@ -31,7 +31,7 @@ __all__ = [
     "Network", "square_lattice", "cubic_lattice", "grid_graph", "with_open_legs",
     "splitmix64_uniform", "splitmix64_normal",
     "ising_tensors", "random_tensors", "aklt_tensors", "slice_open", "batched_workload",
-    "uniform_ising", "uniform_random", "uniform_product",
+    "uniform_ising", "uniform_random", "uniform_product", "square_lines", "square_block_partitions",
 ]
 
 # leg direction tags stored beside ``site_bonds`` (used by the AKLT builder)
@@ -515,3 +515,25 @@ def uniform_product(a, b, c, e) -> np.ndarray:
     """The rank-1 uniform tensor A[l,u,r,d] = a[l] b[u] c[r] e[d]: every bond
     of its lattice is independent of the others."""
     return np.einsum("i,j,k,l->ijkl", *(np.asarray(x, dtype=np.float64) for x in (a, b, c, e)))
+
+
+def square_lines(lx: int, ly: int) -> list:
+    """Every line between two columns and every line between two rows of an
+    lx-by-ly square lattice, as multi-index partitions (the first-level
+    partitions of the paper's recursive 4 x 3 example, Sec. IV.A)."""
+    return [square_line_x(lx, ly, k) for k in range(lx - 1)] + [square_line_y(lx, ly, k) for k in range(ly - 1)]
+
+
+def square_block_partitions(lx: int, ly: int, x0: int, y0: int, parts, bw: int = 3, bh: int = 3) -> list:
+    """Partitions given on a bw-by-bh square lattice placed at (x0, y0) inside
+    an lx-by-ly lattice, with bond ids mapped to the larger lattice."""
+    small = square_lattice(bw, bh, 2)
+    big = square_lattice(lx, ly, 2)
+
+    def site(s):
+        return (y0 + s // bw) * lx + x0 + s % bw
+    out = []
+    for S in parts:
+        out.append(sorted(bond_between(big, site(int(small.bond_site[b][0])), site(int(small.bond_site[b][1])))
+                          for b in S))
+    return out
