@@ -545,11 +545,11 @@ pne_status rank_terms(pne_ctx *ctx, const Geometry &g, int32_t rank, int32_t for
 // per set: c[k], abs_c[k], the signed Neumaier sum of the term values (in the
 // weighted network's scale), log_abs with the weights' log scale, and the
 // a-priori bound: FP64 rounding of nops operations per term plus, for a
-// reduced-precision contraction, term_bound[t] x |value| (bound relative to
-// each term's absolute contraction, which equals |value| for a term of
-// non-negative tensors)
+// reduced-precision contraction, bound_abs[set][term] = the contraction's
+// relative bound x |value| (relative to each term's absolute contraction,
+// which equals |value| for a term of non-negative tensors)
 void rank_results(const pne_weights *w, int form, const RankTerms &t, const std::vector<double> &vals,
-                  const std::vector<double> &term_bound, int nops, pne_result *out)
+                  const std::vector<double> &bound_abs, int nops, pne_result *out)
 {
     const int n_terms = (int)t.order.size();
     for (int set = 0; set < w->n_sets; ++set) {
@@ -568,7 +568,7 @@ void rank_results(const pne_weights *w, int form, const RankTerms &t, const std:
             comp += (std::fabs(sum) >= std::fabs(x)) ? (sum - tt) + x : (x - tt) + sum;
             sum = tt;
             asum += std::fabs(x);
-            if (!term_bound.empty()) rb += term_bound[q] * std::fabs(x);
+            if (!bound_abs.empty()) rb += bound_abs[(size_t)set * n_terms + q];
         }
         sum += comp;
         const double ls = w->log_scale[set];
@@ -585,6 +585,78 @@ void rank_results(const pne_weights *w, int form, const RankTerms &t, const std:
         r.n_terms = (uint64_t)n_terms;
         r.bp_iters = w->sweeps[set];
     }
+}
+
+// Every term network (bond kinds per term: 0 whole, 1 P range [0, rank), 2 Q
+// range [rank, d)) contracted as a grid: the restricted tensors gathered per
+// term, then the row-by-row GEMMs.  vals / bound_abs [set][term].
+pne_status grid_term_values(pne_ctx *ctx, const pne_weights *w, const std::vector<int8_t> &kind, int n_terms,
+                            int32_t rank, int32_t lx, int32_t ly, pne_dtype dtype, cudaStream_t s,
+                            std::vector<double> &vals, std::vector<double> &bound_abs)
+{
+    const Geometry &g = w->geo->full;
+    const int NB = g.n_bonds, ns = w->n_sets;
+    vals.assign((size_t)ns * n_terms, 0.0);
+    bound_abs.assign((size_t)ns * n_terms, 0.0);
+    std::vector<int32_t> lo((size_t)NB), len((size_t)NB);
+    std::vector<int64_t> off((size_t)g.n_sites + 1);
+    DevBuf dlo, dlen, doff, ddata;
+    auto cleanup = [&]() { dev_free(ctx, dlo, s); dev_free(ctx, dlen, s); dev_free(ctx, doff, s); dev_free(ctx, ddata, s); };
+    pne_status st;
+    if ((st = dev_alloc(ctx, dlo, (size_t)NB * 4, s)) || (st = dev_alloc(ctx, dlen, (size_t)NB * 4, s)) ||
+        (st = dev_alloc(ctx, doff, off.size() * 8, s)) ||
+        (st = dev_alloc(ctx, ddata, (size_t)ns * g.tens_off[g.n_sites] * 8, s))) {
+        cleanup();
+        return st;
+    }
+    for (int q = 0; q < n_terms; ++q) {
+        for (int b = 0; b < NB; ++b) {
+            const int kd = kind[(size_t)q * NB + b], d = g.bond_dim[b];
+            lo[(size_t)b] = kd == 2 ? rank : 0;
+            len[(size_t)b] = kd == 0 ? d : (kd == 1 ? rank : d - rank);
+        }
+        off[0] = 0;
+        for (int v = 0; v < g.n_sites; ++v) {
+            int64_t sz = 1;
+            for (int i = g.site_ptr[v]; i < g.site_ptr[v + 1]; ++i) sz *= len[(size_t)g.site_bonds[i]];
+            off[(size_t)v + 1] = off[(size_t)v] + sz;
+        }
+        GridPlan plan;
+        if ((st = grid_plan(ctx, lx, ly, NB, g.bond_site.data(), len.data(), g.site_ptr.data(), g.site_bonds.data(),
+                            off.data(), dtype, ns, plan)) ||
+            (st = upload(ctx, dlo.ptr, lo.data(), (size_t)NB * 4, s)) ||
+            (st = upload(ctx, dlen.ptr, len.data(), (size_t)NB * 4, s)) ||
+            (st = upload(ctx, doff.ptr, off.data(), off.size() * 8, s))) {
+            cleanup();
+            return st;
+        }
+        {
+            ProfScope ps(ctx, s, "rank_restrict");
+            restrict_kernel<<<dim3(g.n_sites, ns), 256, 0, s>>>((const double *)w->T.ptr, g.tens_off[g.n_sites],
+                                                                g.d_tens_off, g.d_site_ptr, g.d_site_bonds,
+                                                                g.d_bond_dim, (const int32_t *)dlo.ptr,
+                                                                (const int32_t *)dlen.ptr, (const int64_t *)doff.ptr,
+                                                                off[(size_t)g.n_sites], (double *)ddata.ptr);
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+            cleanup();
+            set_error(ctx, PNE_ECUDA, "restrict_kernel launch failed");
+            return PNE_ECUDA;
+        }
+        std::vector<double> h;
+        double bound = 0.0;
+        if ((st = grid_run(ctx, plan, (const double *)ddata.ptr, off[(size_t)g.n_sites], ns, dtype, s, h, bound))) {
+            cleanup();
+            return st;
+        }
+        for (int set = 0; set < ns; ++set) {
+            const double v = std::ldexp(h[2 * (size_t)set], (int)h[2 * (size_t)set + 1]);
+            vals[(size_t)set * n_terms + q] = v;
+            bound_abs[(size_t)set * n_terms + q] = dtype == PNE_F64 ? 0.0 : bound * std::fabs(v);
+        }
+    }
+    cleanup();
+    return PNE_OK;
 }
 
 }  // namespace
@@ -839,71 +911,114 @@ pne_status pne_rank_r_expand_grid(pne_ctx *ctx, const pne_weights *w, int32_t ra
     RankTerms t;
     pne_status st = rank_terms(ctx, g, rank, form, n_partitions, partition_ptr, partition_bonds, t);
     if (st) return st;
-    const int n_terms = (int)t.order.size(), NB = g.n_bonds, ns = w->n_sets;
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<double> vals((size_t)ns * n_terms), tbound((size_t)n_terms, 0.0);
-    std::vector<int32_t> lo((size_t)NB), len((size_t)NB);
-    std::vector<int64_t> off((size_t)g.n_sites + 1);
-    DevBuf dlo, dlen, doff, ddata;
-    auto cleanup = [&]() { dev_free(ctx, dlo, s); dev_free(ctx, dlen, s); dev_free(ctx, doff, s); dev_free(ctx, ddata, s); };
-    if ((st = dev_alloc(ctx, dlo, (size_t)NB * 4, s)) || (st = dev_alloc(ctx, dlen, (size_t)NB * 4, s)) ||
-        (st = dev_alloc(ctx, doff, off.size() * 8, s)) ||
-        (st = dev_alloc(ctx, ddata, (size_t)ns * g.tens_off[g.n_sites] * 8, s))) {
-        cleanup();
-        return st;
-    }
-    for (int q = 0; q < n_terms; ++q) {
-        for (int b = 0; b < NB; ++b) {
-            const int kd = t.kind[(size_t)q * NB + b], d = g.bond_dim[b];
-            lo[(size_t)b] = kd == 2 ? rank : 0;
-            len[(size_t)b] = kd == 0 ? d : (kd == 1 ? rank : d - rank);
-        }
-        off[0] = 0;
-        for (int v = 0; v < g.n_sites; ++v) {
-            int64_t sz = 1;
-            for (int i = g.site_ptr[v]; i < g.site_ptr[v + 1]; ++i) sz *= len[(size_t)g.site_bonds[i]];
-            off[(size_t)v + 1] = off[(size_t)v] + sz;
-        }
-        GridPlan plan;
-        if ((st = grid_plan(ctx, lx, ly, NB, g.bond_site.data(), len.data(), g.site_ptr.data(), g.site_bonds.data(),
-                            off.data(), dtype, ns, plan))) {
-            cleanup();
-            return st;
-        }
-        if ((st = upload(ctx, dlo.ptr, lo.data(), (size_t)NB * 4, s)) ||
-            (st = upload(ctx, dlen.ptr, len.data(), (size_t)NB * 4, s)) ||
-            (st = upload(ctx, doff.ptr, off.data(), off.size() * 8, s))) {
-            cleanup();
-            return st;
-        }
-        {
-            ProfScope ps(ctx, s, "rank_restrict");
-            restrict_kernel<<<dim3(g.n_sites, ns), 256, 0, s>>>((const double *)w->T.ptr, g.tens_off[g.n_sites],
-                                                                g.d_tens_off, g.d_site_ptr, g.d_site_bonds,
-                                                                g.d_bond_dim, (const int32_t *)dlo.ptr,
-                                                                (const int32_t *)dlen.ptr, (const int64_t *)doff.ptr,
-                                                                off[(size_t)g.n_sites], (double *)ddata.ptr);
-        }
-        if (cudaGetLastError() != cudaSuccess) {
-            cleanup();
-            set_error(ctx, PNE_ECUDA, "restrict_kernel launch failed");
-            return PNE_ECUDA;
-        }
-        std::vector<double> h;
-        double bound = 0.0;
-        if ((st = grid_run(ctx, plan, (const double *)ddata.ptr, off[(size_t)g.n_sites], ns, dtype, s, h, bound))) {
-            cleanup();
-            return st;
-        }
-        tbound[(size_t)q] = dtype == PNE_F64 ? 0.0 : bound;
-        for (int set = 0; set < ns; ++set)
-            vals[(size_t)set * n_terms + q] = std::ldexp(h[2 * (size_t)set], (int)h[2 * (size_t)set + 1]);
-    }
-    cleanup();
+    std::vector<double> vals, babs;
+    if ((st = grid_term_values(ctx, w, t.kind, (int)t.order.size(), rank, lx, ly, dtype, s, vals, babs))) return st;
     const_cast<pne_weights *>(w)->last_stream = s;
-    int lxy = std::max(lx, ly);
-    const int nops = 2 * g.n_sites + 4 * lxy + t.M + 2;
-    rank_results(w, form, t, vals, tbound, nops, out);
+    const int nops = 2 * g.n_sites + 4 * std::max(lx, ly) + t.M + 2;
+    rank_results(w, form, t, vals, babs, nops, out);
+    return PNE_OK;
+}
+
+pne_status pne_recursive_expand_grid(pne_ctx *ctx, const pne_weights *w, int32_t rank, int32_t n_partitions,
+                                     const int32_t *partition_ptr, const int32_t *partition_bonds,
+                                     int32_t n_sub_partitions, const int32_t *sub_ptr, const int32_t *sub_bonds,
+                                     int32_t max_sites, int32_t lx, int32_t ly, pne_dtype dtype, void *stream,
+                                     pne_result *out, uint64_t *n_contractions)
+{
+    HostScope hs__(ctx, "recursive_expand_grid");
+    if (!ctx || !w || !out || !partition_ptr || !partition_bonds || (n_sub_partitions > 0 && (!sub_ptr || !sub_bonds)))
+        return PNE_EINVAL;
+    auto bad = [&](const std::string &m) { set_error(ctx, PNE_EINVAL, m); return PNE_EINVAL; };
+    const Geometry &g = w->geo->full;
+    const int NB = g.n_bonds, N = g.n_sites;
+    if (dtype == PNE_F32) return bad("recursive_expand_grid takes PNE_F64, PNE_TF32 or PNE_BF16");
+    if (lx < 1 || ly < 1 || (int64_t)lx * ly != N) return bad("n_sites must be lx * ly");
+    if (max_sites < 1) return bad("max_sites must be positive");
+    if (n_partitions > 16) return bad("at most 16 first-level partitions");
+    if (n_sub_partitions < 0 || n_sub_partitions > 64) return bad("0..64 second-level partitions");
+    RankTerms t1;
+    pne_status st = rank_terms(ctx, g, rank, 1, n_partitions, partition_ptr, partition_bonds, t1);
+    if (st) return st;
+    std::vector<std::vector<int>> sub((size_t)n_sub_partitions);
+    for (int p = 0; p < n_sub_partitions; ++p) {
+        if (sub_ptr[p + 1] <= sub_ptr[p] || (p == 0 && sub_ptr[0] != 0)) return bad("malformed second-level partitions");
+        for (int i = sub_ptr[p]; i < sub_ptr[p + 1]; ++i) {
+            const int b = sub_bonds[i];
+            if (b < 0 || b >= NB) return bad("second-level partition bond out of range");
+            if (rank >= g.bond_dim[b]) return bad("rank must be below every partitioned bond's dimension");
+            sub[(size_t)p].push_back(b);
+        }
+    }
+    // every first-level subset x: the cut bonds, the components left, and
+    // either the sub-network itself or its expansion over the second-level
+    // partitions that fit inside its too-large components
+    const int n1 = (int)t1.order.size();
+    std::vector<int8_t> kind;            // every network to contract
+    std::vector<int> owner, sign2;       // its first-level term and second-level sign
+    std::vector<int> parent((size_t)N);
+    auto find = [&](int a) {
+        while (parent[(size_t)a] != a) a = parent[(size_t)a] = parent[(size_t)parent[(size_t)a]];
+        return a;
+    };
+    for (int q = 0; q < n1; ++q) {
+        const int8_t *row = t1.kind.data() + (size_t)q * NB;
+        for (int v = 0; v < N; ++v) parent[(size_t)v] = v;
+        for (int b = 0; b < NB; ++b) {
+            if (row[b] == 1) continue;
+            const int ra = find(g.bond_site[2 * b]), rb = find(g.bond_site[2 * b + 1]);
+            if (ra != rb) parent[(size_t)std::max(ra, rb)] = std::min(ra, rb);
+        }
+        std::vector<int> size((size_t)N, 0);
+        for (int v = 0; v < N; ++v) ++size[(size_t)find(v)];
+        auto big = [&](int v) { return size[(size_t)find(v)] > max_sites; };
+        std::vector<int> fit;
+        for (int p = 0; p < n_sub_partitions; ++p) {
+            bool ok = true;
+            for (int b : sub[(size_t)p]) {
+                const int s0 = g.bond_site[2 * b], s1 = g.bond_site[2 * b + 1];
+                if (row[b] == 1 || !big(s0) || find(s0) != find(s1)) { ok = false; break; }
+            }
+            if (ok) fit.push_back(p);
+        }
+        if (fit.size() > 16) return bad("more than 16 second-level partitions fit one sub-network");
+        if (fit.empty()) {
+            kind.insert(kind.end(), row, row + NB);
+            owner.push_back(q);
+            sign2.push_back(1);
+            continue;
+        }
+        for (uint32_t y = 1; y < (1u << fit.size()); ++y) {
+            std::vector<int8_t> r2(row, row + NB);
+            int k = 0;
+            for (size_t i = 0; i < fit.size(); ++i)
+                if (y >> i & 1) { ++k; for (int b : sub[(size_t)fit[i]]) r2[(size_t)b] = 1; }
+            kind.insert(kind.end(), r2.begin(), r2.end());
+            owner.push_back(q);
+            sign2.push_back(k % 2 == 1 ? 1 : -1);
+        }
+    }
+    const int nt = (int)owner.size();
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> vals, babs;
+    if ((st = grid_term_values(ctx, w, kind, nt, rank, lx, ly, dtype, s, vals, babs))) return st;
+    const_cast<pne_weights *>(w)->last_stream = s;
+    // first-level values: the second-level sums (Neumaier, in network order)
+    const int ns = w->n_sets;
+    std::vector<double> v1((size_t)ns * n1, 0.0), b1((size_t)ns * n1, 0.0), c1((size_t)ns * n1, 0.0);
+    for (int set = 0; set < ns; ++set)
+        for (int i = 0; i < nt; ++i) {
+            const size_t a = (size_t)set * n1 + owner[(size_t)i];
+            const double x = sign2[(size_t)i] * vals[(size_t)set * nt + i], tt = v1[a] + x;
+            c1[a] += (std::fabs(v1[a]) >= std::fabs(x)) ? (v1[a] - tt) + x : (x - tt) + v1[a];
+            v1[a] = tt;
+            b1[a] += babs[(size_t)set * nt + i];
+        }
+    for (size_t a = 0; a < v1.size(); ++a) v1[a] += c1[a];
+    const int nops = 2 * N + 4 * std::max(lx, ly) + t1.M + 2 + 20;
+    rank_results(w, 1, t1, v1, b1, nops, out);
+    for (int set = 0; set < ns; ++set) out[set].n_terms = (uint64_t)nt;
+    if (n_contractions) *n_contractions = (uint64_t)nt;
     return PNE_OK;
 }
 

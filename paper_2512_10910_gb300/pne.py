@@ -29,6 +29,7 @@ __all__ = [
     "Network", "PartitionOpts", "EnumOpts", "Result", "Context", "run", "network_struct",
     "pne_strip_expansion", "StripOpts", "StripResult", "PNE_STRIP_MAX_L", "PNE_STRIP_MAX_CHI",
     "pne_dense_gemm", "pne_grid_contract", "pne_rank_r_expand_grid", "pne_rank_r_expand",
+    "pne_recursive_expand_grid", "pne_weight_passing", "pne_weights_read", "pne_weights_destroy",
 ]
 
 PNE_OK, PNE_EINVAL, PNE_ENOMEM, PNE_ECUDA, PNE_ENOCONV, PNE_EDEGENERATE, PNE_ETIMEOUT, PNE_EOVERFLOW, PNE_EBUSY = range(9)
@@ -217,6 +218,11 @@ def load_library():
                                            ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, vp,
                                            ctypes.POINTER(Result)]
     lib.pne_rank_r_expand_grid.restype = ctypes.c_int
+    lib.pne_recursive_expand_grid.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int, vp, ctypes.POINTER(Result),
+                                              ctypes.POINTER(ctypes.c_uint64)]
+    lib.pne_recursive_expand_grid.restype = ctypes.c_int
     lib.pne_open_tensor.argtypes = [vp, vp, vp, ctypes.c_void_p, ctypes.c_void_p]
     lib.pne_open_tensor.restype = ctypes.c_int
     lib.pne_open_tensor_assemble.argtypes = [ctypes.POINTER(Result), ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
@@ -282,7 +288,7 @@ def exported_symbols() -> list:
              "pne_server_submit", "pne_server_poll", "pne_server_drain", "pne_server_stats", "pne_server_first_error",
              "pne_server_destroy", "pne_weight_passing", "pne_weights_read", "pne_weights_destroy",
              "pne_rank_r_expand", "pne_strip_expansion", "pne_dense_gemm", "pne_grid_contract",
-             "pne_rank_r_expand_grid"]
+             "pne_rank_r_expand_grid", "pne_recursive_expand_grid"]
     return [n for n in names if hasattr(lib, n)]
 
 
@@ -442,6 +448,29 @@ def pne_rank_r_expand_grid(ctx, w, rank, form, partitions, n_sets, lx, ly, dtype
     _check(load_library().pne_rank_r_expand_grid(ctx, w, int(rank), int(form), len(partitions), ptr.ctypes.data,
                                                  bonds.ctypes.data, int(lx), int(ly), int(dtype), stream, out), ctx)
     return [r.as_dict() for r in out]
+
+
+def _csr(partitions):
+    ptr = np.zeros(len(partitions) + 1, dtype=np.int32)
+    for i, S in enumerate(partitions):
+        ptr[i + 1] = ptr[i] + len(S)
+    bonds = (np.ascontiguousarray(np.concatenate([np.asarray(S, dtype=np.int32) for S in partitions]), dtype=np.int32)
+             if partitions else np.zeros(1, dtype=np.int32))
+    return ptr, bonds
+
+
+def pne_recursive_expand_grid(ctx, w, rank, partitions, sub_partitions, max_sites, n_sets, lx, ly, dtype,
+                              stream=None):
+    """Recursive partitioning on the weights' rank-r projectors: (results, networks contracted)."""
+    p1, b1 = _csr(partitions)
+    p2, b2 = _csr(sub_partitions)
+    out = (Result * n_sets)()
+    n = ctypes.c_uint64()
+    _check(load_library().pne_recursive_expand_grid(ctx, w, int(rank), len(partitions), p1.ctypes.data,
+                                                    b1.ctypes.data, len(sub_partitions), p2.ctypes.data,
+                                                    b2.ctypes.data, int(max_sites), int(lx), int(ly), int(dtype),
+                                                    stream, out, ctypes.byref(n)), ctx)
+    return [r.as_dict() for r in out], int(n.value)
 
 
 def pne_terms_destroy(t):
