@@ -450,7 +450,7 @@ def run_step_bench(args, wl, rank, world, local_rank):
         for name, fn in (("cfg3_ising3d_8x8x8", run_cfg3), ("cfg4_batched", run_batched_extra),
                          ("cfg5_served", run_served_comparison), ("combinatorial_3x3", run_combinatorial_extra),
                          ("rank_r_ising_sec5b", run_rank_r_extra), ("strips_infinite_ising", run_strip_extra),
-                         ("dense_blocked_chi16", run_dense_extra)):
+                         ("dense_blocked_chi16", run_dense_extra), ("recursive_4x3_chi16", run_recursive_extra)):
             if args.extras and name not in args.extras.split(","):
                 continue
             t0 = time.perf_counter()
@@ -814,6 +814,45 @@ def run_dense_extra(args, ctx, pne, torch, dev, local_rank):
                            "gemm_tflops": flops / (gms * 1e-3) / 1e12, "frac": flops / (gms * 1e-3) / 1e12 / pk,
                            "max_rel_err_vs_f64": err, "stated_err_bound": res[0]["err_bound"]}
     out["grid_5x4_chi16"] = grid
+    return out
+
+
+def run_recursive_extra(args, ctx, pne, torch, dev, local_rank):
+    """Recursive partitioning (Sec. IV.A) on the paper's 4 x 3 example: 16 x 12
+    Ising spins coarse-grained to 4 x 3 sites of bond dimension 16, eight
+    temperatures per call, rank-1 projectors of the weights; first level every
+    column and row line, second level the 3 x 3 six-line expansion on each
+    3 x 3 block, strips at most 2 wide contracted as they are.  Against the exact grid
+    contraction (FP64) and the one-level combinatorial form."""
+    bc = math.log(1 + math.sqrt(2)) / 2
+    fracs = np.linspace(0.6, 1.3, 8)
+    nets = [I.ising_blocked(4, 3, 4, bc / f) for f in fracs]
+    g = nets[0]
+    data = torch.from_numpy(np.concatenate([n.flat_data()[0] for n in nets])).to(dev)
+    nb = len(nets)
+    exact = [r["log_abs"] for r in pne.pne_grid_contract(ctx.h, g, 4, 3, pne.PNE_F64, data=data, n_batch=nb)]
+    p1 = I.square_lines(4, 3)
+    p2 = I.unique_partitions(I.square_block_partitions(4, 3, 0, 0, I.square3x3_six_lines())
+                             + I.square_block_partitions(4, 3, 1, 0, I.square3x3_six_lines()))
+    ns, keep = pne.network_struct(g, data=data, n_batch=nb)
+    w = pne.pne_weight_passing(ctx.h, ns, 0.8, 1e-10, 5000)
+    out = {"workload": "16x12 Ising coarse-grained to 4x3 (bond dimension 16), 8 temperatures 0.6..1.3 T_c: "
+                       "recursive partitioning (5 lines, then the 3x3 six-line expansion on every 3x3 block left "
+                       "whole; strips at most 2 wide contracted as they are), rank-1 projectors of the weights"}
+    try:
+        for how, fn in (("one_level_f64", lambda: (pne.pne_rank_r_expand_grid(ctx.h, w, 1, 1, p1, nb, 4, 3,
+                                                                                 pne.PNE_F64), 31)),
+                        ("recursive_f64", lambda: pne.pne_recursive_expand_grid(ctx.h, w, 1, p1, p2, 2, nb, 4, 3,
+                                                                                pne.PNE_F64)),
+                        ("recursive_tf32", lambda: pne.pne_recursive_expand_grid(ctx.h, w, 1, p1, p2, 2, nb, 4, 3,
+                                                                                 pne.PNE_TF32))):
+            ms, (res, ncon) = _timed_calls(torch, dev, fn, 2, 1)
+            errs = [abs(math.expm1(r["log_abs"] - e)) for r, e in zip(res, exact)]
+            out[how] = {"ms_per_call": ms, "contractions_per_set": ncon, "max_rel_err_vs_exact": max(errs),
+                        "rel_err_by_T_over_Tc": {f"{f:.2f}": e for f, e in zip(fracs, errs)}}
+    finally:
+        pne.pne_weights_destroy(w)
+        del keep
     return out
 
 

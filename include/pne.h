@@ -564,11 +564,13 @@ pne_status pne_rank_r_expand_grid(pne_ctx *ctx, const pne_weights *w, int32_t ra
 
 /* Recursive partitioning (Sec. IV.A) on the rank-r projectors of the weights:
  * the combinatorial form (Eq. A6) over the first-level partitions, in which
- * every sub-network whose largest connected component (sites joined by
- * bonds not cut by its partitions) has more than max_sites sites is not
- * contracted as it is but expanded again by the combinatorial form over the
- * second-level partitions that fit inside its too-large components (every
- * bond of such a partition uncut and joining two sites of one of them):
+ * every sub-network with a connected component (sites joined by bonds not
+ * cut by its partitions) too costly to contract -- on the lx x ly grid, both
+ * sides of the component's bounding box above max_side (a strip w sites wide
+ * carries w legs from row to row) -- is not contracted as it is but expanded
+ * again by the combinatorial form over the second-level partitions that fit
+ * inside its too-costly components (every bond of such a partition uncut
+ * and joining two sites of one of them):
  *     Z(P^x) ~ sum_{y != 0} (-1)^{|y|+1} Z(P^x P^y),
  * the residues of both levels neglected.  A sub-network no second-level
  * partition fits is contracted as it is.  Every network is contracted as a
@@ -581,7 +583,7 @@ pne_status pne_rank_r_expand_grid(pne_ctx *ctx, const pne_weights *w, int32_t ra
 pne_status pne_recursive_expand_grid(pne_ctx *ctx, const pne_weights *w, int32_t rank, int32_t n_partitions,
                                      const int32_t *partition_ptr, const int32_t *partition_bonds,
                                      int32_t n_sub_partitions, const int32_t *sub_ptr, const int32_t *sub_bonds,
-                                     int32_t max_sites, int32_t lx, int32_t ly, pne_dtype dtype, void *stream,
+                                     int32_t max_side, int32_t lx, int32_t ly, pne_dtype dtype, void *stream,
                                      pne_result *out, uint64_t *n_contractions);
 
 /* ---- belief propagation without device allocation ------------------------ */

@@ -6,10 +6,14 @@ Test infrastructure only (see ``oracle/__init__.py``).
   combinatorial form (Eq. A6): every non-empty subset x contributes
   (-1)^{|x|+1} Z(P^x).  The sub-network of x falls apart along the bonds of
   the partitions in x ("cut" bonds) into connected components.
-* A sub-network whose largest component has more than ``max_sites`` sites
-  (its contraction is too costly) is not contracted as it is but expanded
-  again by the combinatorial form over the second-level partitions whose
-  bonds all join sites of such a component and none of which is cut:
+* A sub-network with a component too costly to contract is not contracted
+  as it is but expanded again by the combinatorial form over the
+  second-level partitions whose bonds all join sites of such a component and
+  none of which is cut.  On a square lattice (site id = y * lx + x) the cost
+  of contracting a component grows with the shorter side of its bounding box
+  (a strip of width w carries w legs from row to row: O(chi^(2w)) for the
+  paper's blocks), so a component is too costly when both sides of its box
+  exceed ``max_side``:
       Z(P^x) ~ sum_{y != 0} (-1)^{|y|+1} Z(P^x P^y),
   the second level's residue neglected.  With one too-large component (the
   paper's 4 x 3 example, one 3 x 3 block per sub-network) this is that
@@ -54,7 +58,13 @@ def _inserts_p(proj, bonds):
     return [((int(b),), proj[int(b)][0]) for b in sorted(bonds)]
 
 
-def recursive_combinatorial(net, parts1, parts2, proj, max_sites, with_residue2=False):
+def _too_costly(C, lx, max_side):
+    xs = [v % lx for v in C]
+    ys = [v // lx for v in C]
+    return min(max(xs) - min(xs) + 1, max(ys) - min(ys) + 1) > max_side
+
+
+def recursive_combinatorial(net, parts1, parts2, proj, lx, max_side, with_residue2=False):
     """The two-level expansion.  Returns a dict: ``value`` (residues of both
     levels neglected; with ``with_residue2`` the second level's residue
     Z(P^x Q_y1 ... Q_yn), complements inserted directly, is added back to each
@@ -66,7 +76,7 @@ def recursive_combinatorial(net, parts1, parts2, proj, max_sites, with_residue2=
     for x, sign in comb_subsets(len(parts1)):
         cut = set(int(b) for p in x for b in parts1[p])
         comps = components(net, cut)
-        big = [set(C) for C in comps if len(C) > max_sites]
+        big = [set(C) for C in comps if _too_costly(C, lx, max_side)]
         sub = []
         if big:
             for S in parts2:

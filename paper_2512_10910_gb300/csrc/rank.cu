@@ -923,7 +923,7 @@ pne_status pne_rank_r_expand_grid(pne_ctx *ctx, const pne_weights *w, int32_t ra
 pne_status pne_recursive_expand_grid(pne_ctx *ctx, const pne_weights *w, int32_t rank, int32_t n_partitions,
                                      const int32_t *partition_ptr, const int32_t *partition_bonds,
                                      int32_t n_sub_partitions, const int32_t *sub_ptr, const int32_t *sub_bonds,
-                                     int32_t max_sites, int32_t lx, int32_t ly, pne_dtype dtype, void *stream,
+                                     int32_t max_side, int32_t lx, int32_t ly, pne_dtype dtype, void *stream,
                                      pne_result *out, uint64_t *n_contractions)
 {
     HostScope hs__(ctx, "recursive_expand_grid");
@@ -934,7 +934,7 @@ pne_status pne_recursive_expand_grid(pne_ctx *ctx, const pne_weights *w, int32_t
     const int NB = g.n_bonds, N = g.n_sites;
     if (dtype == PNE_F32) return bad("recursive_expand_grid takes PNE_F64, PNE_TF32 or PNE_BF16");
     if (lx < 1 || ly < 1 || (int64_t)lx * ly != N) return bad("n_sites must be lx * ly");
-    if (max_sites < 1) return bad("max_sites must be positive");
+    if (max_side < 1) return bad("max_side must be positive");
     if (n_partitions > 16) return bad("at most 16 first-level partitions");
     if (n_sub_partitions < 0 || n_sub_partitions > 64) return bad("0..64 second-level partitions");
     RankTerms t1;
@@ -969,9 +969,17 @@ pne_status pne_recursive_expand_grid(pne_ctx *ctx, const pne_weights *w, int32_t
             const int ra = find(g.bond_site[2 * b]), rb = find(g.bond_site[2 * b + 1]);
             if (ra != rb) parent[(size_t)std::max(ra, rb)] = std::min(ra, rb);
         }
-        std::vector<int> size((size_t)N, 0);
-        for (int v = 0; v < N; ++v) ++size[(size_t)find(v)];
-        auto big = [&](int v) { return size[(size_t)find(v)] > max_sites; };
+        // a component is too costly when both sides of its bounding box exceed max_side
+        std::vector<int> x0((size_t)N, INT32_MAX), x1((size_t)N, -1), y0((size_t)N, INT32_MAX), y1((size_t)N, -1);
+        for (int v = 0; v < N; ++v) {
+            const size_t r = (size_t)find(v);
+            x0[r] = std::min(x0[r], v % lx); x1[r] = std::max(x1[r], v % lx);
+            y0[r] = std::min(y0[r], v / lx); y1[r] = std::max(y1[r], v / lx);
+        }
+        auto big = [&](int v) {
+            const size_t r = (size_t)find(v);
+            return std::min(x1[r] - x0[r] + 1, y1[r] - y0[r] + 1) > max_side;
+        };
         std::vector<int> fit;
         for (int p = 0; p < n_sub_partitions; ++p) {
             bool ok = true;

@@ -31,7 +31,7 @@ __all__ = [
     "Network", "square_lattice", "cubic_lattice", "grid_graph", "with_open_legs",
     "splitmix64_uniform", "splitmix64_normal",
     "ising_tensors", "random_tensors", "aklt_tensors", "slice_open", "batched_workload",
-    "uniform_ising", "uniform_random", "uniform_product", "square_lines", "square_block_partitions",
+    "uniform_ising", "uniform_random", "uniform_product", "square_lines", "square_block_partitions", "unique_partitions",
 ]
 
 # leg direction tags stored beside ``site_bonds`` (used by the AKLT builder)
@@ -536,4 +536,16 @@ def square_block_partitions(lx: int, ly: int, x0: int, y0: int, parts, bw: int =
     for S in parts:
         out.append(sorted(bond_between(big, site(int(small.bond_site[b][0])), site(int(small.bond_site[b][1])))
                           for b in S))
+    return out
+
+
+def unique_partitions(parts) -> list:
+    """The partitions with repeated bond sets dropped (first occurrence kept):
+    overlapping blocks can place the same line twice."""
+    seen, out = set(), []
+    for S in parts:
+        key = tuple(sorted(int(b) for b in S))
+        if key not in seen:
+            seen.add(key)
+            out.append(list(key))
     return out

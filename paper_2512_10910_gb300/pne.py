@@ -459,7 +459,7 @@ def _csr(partitions):
     return ptr, bonds
 
 
-def pne_recursive_expand_grid(ctx, w, rank, partitions, sub_partitions, max_sites, n_sets, lx, ly, dtype,
+def pne_recursive_expand_grid(ctx, w, rank, partitions, sub_partitions, max_side, n_sets, lx, ly, dtype,
                               stream=None):
     """Recursive partitioning on the weights' rank-r projectors: (results, networks contracted)."""
     p1, b1 = _csr(partitions)
@@ -468,7 +468,7 @@ def pne_recursive_expand_grid(ctx, w, rank, partitions, sub_partitions, max_site
     n = ctypes.c_uint64()
     _check(load_library().pne_recursive_expand_grid(ctx, w, int(rank), len(partitions), p1.ctypes.data,
                                                     b1.ctypes.data, len(sub_partitions), p2.ctypes.data,
-                                                    b2.ctypes.data, int(max_sites), int(lx), int(ly), int(dtype),
+                                                    b2.ctypes.data, int(max_side), int(lx), int(ly), int(dtype),
                                                     stream, out, ctypes.byref(n)), ctx)
     return [r.as_dict() for r in out], int(n.value)
 

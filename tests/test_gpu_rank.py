@@ -121,26 +121,26 @@ def test_degenerate_ising_rank_two_grid_fp64_reaches_the_target(ctx):
 
 def test_recursive_partitioning_matches_oracle(ctx):
     # the paper's 4 x 3 example: every column and row line first, the 3 x 3
-    # expansion of Fig. 4 on each 3 x 3 block second, at most 6 sites per
-    # contraction; rank-1 projectors of the weights, FP64 grid contractions
+    # expansion of Fig. 4 on each 3 x 3 block second, strips at most 2 wide
+    # contracted as they are; rank-1 projectors of the weights
     from oracle import recursive as OR
     net = I.random_tensors(I.square_lattice(4, 3, 3), 5)
     p1 = I.square_lines(4, 3)
-    p2 = (I.square_block_partitions(4, 3, 0, 0, I.square3x3_six_lines())
-          + I.square_block_partitions(4, 3, 1, 0, I.square3x3_six_lines()))
+    p2 = I.unique_partitions(I.square_block_partitions(4, 3, 0, 0, I.square3x3_six_lines())
+                             + I.square_block_partitions(4, 3, 1, 0, I.square3x3_six_lines()))
     tens, S, ls, sweeps, change = OW.weight_passing(net, 0.8, 1e-11, 5000)
     wn, ls = OW.weighted_network(net, tens, S, ls)
     proj = OW.rank_r_projectors(wn, 1)
     ns, keep = pne.network_struct(net)
     w = pne.pne_weight_passing(ctx.h, ns, 0.8, 1e-11, 5000)
     try:
-        for max_sites, dt in ((6, pne.PNE_F64), (12, pne.PNE_F64), (6, pne.PNE_TF32)):
-            ref = OR.recursive_combinatorial(wn, p1, p2, proj, max_sites)
-            (res,), n = pne.pne_recursive_expand_grid(ctx.h, w, 1, p1, p2, max_sites, 1, 4, 3, dt)
+        for max_side, dt in ((2, pne.PNE_F64), (3, pne.PNE_F64), (1, pne.PNE_F64), (2, pne.PNE_TF32)):
+            ref = OR.recursive_combinatorial(wn, p1, p2, proj, 4, max_side)
+            (res,), n = pne.pne_recursive_expand_grid(ctx.h, w, 1, p1, p2, max_side, 1, 4, 3, dt)
             assert n == ref["contractions"]
             lz = math.log(abs(ref["value"])) + ls
             tol = 1e-9 if dt == pne.PNE_F64 else 1e-2
-            assert abs(res["log_abs"] - lz) <= tol, (max_sites, dt, res["log_abs"], lz)
+            assert abs(res["log_abs"] - lz) <= tol, (max_side, dt, res["log_abs"], lz)
             assert res["sign"] == (1 if ref["value"] > 0 else -1)
     finally:
         pne.pne_weights_destroy(w)
