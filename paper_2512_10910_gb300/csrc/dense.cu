@@ -36,6 +36,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -791,7 +792,31 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap *map, 
                  : "memory");
 }
 
-template <typename E, int NST>
+__device__ __forceinline__ void tma_load3_mc(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                             uint32_t bar, uint16_t mask)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+                 " [%0], [%1, {%2, %3, %4}], [%5], %6;"
+                 ::"r"(dst), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar), "h"(mask)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_commit_mc(uint32_t mbar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(mbar), "h"(mask)
+                 : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// CL CTAs on adjacent M tiles form a cluster and share the site matrix: each
+// loads 1/CL of every stage's B boxes and multicasts them to all, so the L2
+// delivers B once per cluster instead of once per CTA.  A stage is refilled
+// only after every member's MMAs on it completed (each member's commit
+// arrives on every member's empty barrier, CL arrivals per phase).
+template <typename E, int NST, int CL>
 __global__ void __launch_bounds__(kTcThreads, 2) tc_tma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                    const __grid_constant__ CUtensorMap tmB,
                                                                    RingParams<E> p, int BN)
@@ -812,6 +837,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_tma_gemm_kernel(const __grid
     const int n0 = blockIdx.y * BN;
     E *out = p.out + set * p.stride;
     const uint32_t tcols = BN <= 32 ? 32u : (BN <= 64 ? 64u : (BN <= 128 ? 128u : 256u));
+    uint32_t crank = 0;
+    if (CL > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+    const uint16_t cmask = (uint16_t)((1u << CL) - 1u);
     if (warp == 0) {
         tmem_alloc(smem_addr(&tmem_base_sh), tcols);
         tmem_relinquish();
@@ -819,13 +847,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_tma_gemm_kernel(const __grid
     if (tid == 32) {
         for (int i = 0; i < NST; ++i) {
             mbar_init(smem_addr(&full[i]), 1);
-            mbar_init(smem_addr(&empty[i]), 1);
+            mbar_init(smem_addr(&empty[i]), CL);
         }
         mbar_init(smem_addr(&done), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
+    if (CL > 1) cluster_sync_all();      // every member's barriers exist before any multicast
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
     const int nchunks = (p.K + KC - 1) / KC;
@@ -848,7 +877,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_tma_gemm_kernel(const __grid
                 const int k = c * KC + cu * EPU;
                 const int ku = k / p.Kh, kh = k - ku * p.Kh;
                 tma_load4(sa + cu * (kTcBM * 16), &tmA, kh, (int)m0, ku, set, fb);
-                tma_load3(sb + cu * (BN * 16), &tmB, k, n0, set, fb);
+                if (CL == 1)
+                    tma_load3(sb + cu * (BN * 16), &tmB, k, n0, set, fb);
+                else if (cu % CL == (int)crank)
+                    tma_load3_mc(sb + cu * (BN * 16), &tmB, k, n0, set, fb, cmask);
             }
         }
     } else if (tid == 32) {
@@ -867,7 +899,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_tma_gemm_kernel(const __grid
                 const uint64_t bd = smem_desc(sb + ks * 2 * (BN * 16), (uint32_t)(BN * 16), 128);
                 tc_mma<EB>(tmem, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
             }
-            tc_commit(smem_addr(&empty[s]));
+            if (CL == 1) tc_commit(smem_addr(&empty[s]));
+            else tc_commit_mc(smem_addr(&empty[s]), cmask);
         }
         if (!failed) tc_commit(smem_addr(&done));
     }
@@ -916,6 +949,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_tma_gemm_kernel(const __grid
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, tcols);
+    if (CL > 1) cluster_sync_all();      // no member leaves while another may still signal it
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
@@ -933,7 +967,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-template <typename E, int NST>
+template <typename E, int NST, int CL>
 cudaError_t launch_tma_n(const RingParams<E> &p, int batch, int BN, int n_sets, cudaStream_t s, bool &used)
 {
     used = false;
@@ -960,10 +994,28 @@ cudaError_t launch_tma_n(const RingParams<E> &p, int batch, int BN, int n_sets, 
         return cudaSuccess;         // not encodable: the copy-loop kernel runs instead
     // the epilogue stages the accumulator through the same shared memory: 128 x 68 floats
     const size_t smem = std::max<size_t>((size_t)NST * (kTcBM + BN) * kTmaChunk, (size_t)kTcBM * 68 * 4) + 1024;
-    cudaError_t e = grant_dynamic_smem((const void *)tc_tma_gemm_kernel<E, NST>, smem);
+    cudaError_t e = grant_dynamic_smem((const void *)tc_tma_gemm_kernel<E, NST, CL>, smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)((p.R + kTcBM - 1) / kTcBM), (unsigned)((p.N + BN - 1) / BN), (unsigned)batch);
-    tc_tma_gemm_kernel<E, NST><<<grid, kTcThreads, smem, s>>>(ma, mb, p, BN);
+    const int64_t mt = (p.R + kTcBM - 1) / kTcBM;
+    const dim3 grid((unsigned)((mt + CL - 1) / CL * CL), (unsigned)((p.N + BN - 1) / BN), (unsigned)batch);
+    if (CL == 1) {
+        tc_tma_gemm_kernel<E, NST, CL><<<grid, kTcThreads, smem, s>>>(ma, mb, p, BN);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(kTcThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, tc_tma_gemm_kernel<E, NST, CL>, ma, mb, p, BN);
+        if (e != cudaSuccess) return e;
+    }
     used = true;
     return cudaGetLastError();
 }
@@ -996,10 +1048,24 @@ cudaError_t launch_ring(const RingParams<E> &p, int batch, cudaStream_t s)
         // 64-byte stages: twice as many in flight in the same shared memory (two CTAs per SM)
         const int tstage = (kTcBM + BN) * kTmaChunk;
         const int tn = (int)std::max<int64_t>(2, std::min<int64_t>(8, (112 * 1024) / tstage));
-        cudaError_t e = tn >= 8   ? launch_tma_n<E, 8>(p, batch, BN, batch, s, used)
-                        : tn >= 6 ? launch_tma_n<E, 6>(p, batch, BN, batch, s, used)
-                        : tn >= 4 ? launch_tma_n<E, 4>(p, batch, BN, batch, s, used)
-                                  : launch_tma_n<E, 2>(p, batch, BN, batch, s, used);
+        // clusters of CL CTAs share the site matrix through multicast (PNE_TC_CLUSTER = 1, 2 or 4;
+        // default 2) when the rows fill at least two clusters
+        static const int cl_env = [] {
+            const char *v = std::getenv("PNE_TC_CLUSTER");
+            const int c = v ? std::atoi(v) : 2;
+            return (c == 1 || c == 2 || c == 4) ? c : 2;
+        }();
+        const int64_t mt = (p.R + kTcBM - 1) / kTcBM;
+        const int cl = mt >= 2 * cl_env ? cl_env : 1;
+        cudaError_t e;
+        if (cl == 4)
+            e = tn >= 8 ? launch_tma_n<E, 8, 4>(p, batch, BN, batch, s, used) : launch_tma_n<E, 4, 4>(p, batch, BN, batch, s, used);
+        else if (cl == 2)
+            e = tn >= 8 ? launch_tma_n<E, 8, 2>(p, batch, BN, batch, s, used) : launch_tma_n<E, 4, 2>(p, batch, BN, batch, s, used);
+        else
+            e = tn >= 8   ? launch_tma_n<E, 8, 1>(p, batch, BN, batch, s, used)
+                : tn >= 4 ? launch_tma_n<E, 4, 1>(p, batch, BN, batch, s, used)
+                          : launch_tma_n<E, 2, 1>(p, batch, BN, batch, s, used);
         if (e != cudaSuccess || used) return e;
     }
     if (nst >= 4) return launch_ring_n<E, 4>(p, batch, BN, s);
