@@ -543,8 +543,11 @@ pne_status pne_dense_gemm(pne_ctx *ctx, pne_dtype dtype, int32_t batch, int32_t 
  *          n_terms = 1, c[0] = 1.
  * The running tensor holds at most prod of the open vertical bonds of a row
  * times two horizontal ones; PNE_EINVAL when the batch's running tensors would
- * exceed 64 GB, or on a network that is not such a grid.  Synchronises
- * `stream`. */
+ * exceed 64 GB, or on a network that is not such a grid.  On the tensor cores,
+ * sites whose 16-byte operand units are contiguous are fed by TMA, with
+ * clusters of 2 CTAs sharing the site matrix by multicast (the environment
+ * variable PNE_TC_CLUSTER = 1, 2 or 4 sets the cluster size; results do not
+ * depend on it).  Synchronises `stream`. */
 pne_status pne_grid_contract(pne_ctx *ctx, const pne_network *net, int32_t lx, int32_t ly, pne_dtype dtype,
                              void *stream, pne_result *out);
 
