@@ -136,3 +136,23 @@ def test_grid_contract_rejects_non_grids(ctx):
     net = I.random_tensors(I.square_lattice(3, 3, 2), 1)
     with pytest.raises(pne.PneError):
         pne.pne_grid_contract(ctx.h, net, 3, 3, pne.PNE_F32)
+
+
+def test_grid_contract_large_batch(ctx):
+    # enough row tiles (5 x 4 grid of bond dimension 8, 16 tensor sets: up to
+    # 8^4 rows per set) for the persistent tensor-core form; FP64 against the
+    # oracle on two sets, TF32 / BF16 within their stated bounds of FP64 on all
+    g = I.square_lattice(5, 4, 8)
+    nets = [I.random_tensors(g, 300 + i) for i in range(16)]
+    flat = np.concatenate([n.flat_data()[0] for n in nets])
+    data = torch.from_numpy(flat).cuda()
+    r64 = pne.pne_grid_contract(ctx.h, g, 5, 4, pne.PNE_F64, data=data, n_batch=16)
+    for i in (0, 7):
+        t, ls = X.contract_sweep(nets[i])
+        e = math.log(abs(float(t))) + ls
+        assert abs(r64[i]["log_abs"] - e) < 1e-12 * abs(e)
+    for dt in (pne.PNE_TF32, pne.PNE_BF16):
+        r = pne.pne_grid_contract(ctx.h, g, 5, 4, dt, data=data, n_batch=16)
+        for a, b in zip(r, r64):
+            assert a["sign"] == b["sign"]
+            assert abs(math.expm1(a["log_abs"] - b["log_abs"])) <= a["err_bound"]
