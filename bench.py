@@ -499,11 +499,30 @@ def step_roofline(args, pne, ctx, ctypes_stream, g, sb, res, prof, prof_steps, B
             # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
             # current kernel: the 16.8 MB of float-float pair tensors read once,
             # later sweeps served from L2
-            roof.update(traffic=15.86e6, traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum per "
+            roof.update(traffic=15.84e6, traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum per "
                                                         "launch of bp_ff_cluster_kernel, this workload")
     elif fam == "contract":
         roof.update(achieved=2.0 * fma * B / (avg_ms * 1e-3) / 1e12, peak=pk_c / 1e12,
                     peak_source="measured FMA-chain kernel (pne_measure_fma_peak)", work=c_work)
+        if args.dtype == "f64" and args.workload == "random16" and mode == pne.PNE_MODE_LOOP:
+            # the step's two contract_group_kernel launches (one per running-
+            # tensor class, concurrent on side streams) read 20.4 MB from DRAM
+            # against 13.8 MB of blocked tensors touched (ncu capture)
+            roof.update(traffic=20.42e6, traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
+                                                        "two contract_group_kernel launches of a step, this workload")
+    elif fam == "gauge_block" and args.bp == "ff":
+        # gauge transform: every leg's d x d matrix applied to the site tensor,
+        # n d multiply-adds per leg (n entries), in float-float
+        work = sum(int(np.prod(g.bond_dim[g.site_bonds[g.site_ptr[v]:g.site_ptr[v + 1]]])) *
+                   int(np.sum(g.bond_dim[g.site_bonds[g.site_ptr[v]:g.site_ptr[v + 1]]]))
+                   for v in range(g.n_sites)) * B
+        roof.update(achieved=2.0 * work / (avg_ms * 1e-3) / 1e12, peak=peak_f32 / 16 / 1e12,
+                    peak_source="measured FP32 FMA-chain kernel (pne_measure_fma_peak) / 16 FP32 instructions per "
+                                "float-float multiply-add",
+                    work=f"2 flops per multiply-add; {work} multiply-adds per step (n d per leg per site)")
+        if args.workload == "random16":
+            roof.update(traffic=21.79e6, traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum per "
+                                                        "launch of block_ff_kernel, this workload")
     elif fam.startswith("enum_"):
         # the cluster search is integer work bound by issue and latency; its
         # algorithmic traffic is the cluster lists it writes (edges, sorted
@@ -516,6 +535,14 @@ def step_roofline(args, pne, ctx, ctypes_stream, g, sb, res, prof, prof_steps, B
                     peak=peak_gbs, peak_source=src,
                     work=f"{n_cl} clusters x {per_cluster} B written per search "
                          f"({launches // prof_steps} launches of {fam} per search)")
+        if args.workload == "random16":
+            # what bounds it: issue slots and the integer pipe, per launch (ncu)
+            roof.update(issue={"expand_kernel": {"issue_active_pct": 25.4, "alu_pipe_pct": 21.9,
+                                                 "dram_bytes_per_launch": 1.03e6},
+                               "expand_children_kernel": {"issue_active_pct": 12.8, "alu_pipe_pct": 8.6,
+                                                          "dram_bytes_per_launch": 0.49e6},
+                               "source": "ncu smsp__issue_active, sm__pipe_alu_cycles_active, dram__bytes_*, "
+                                         "averages over the launches of one step, this workload"})
     if roof["achieved"] is not None and roof["peak"]:
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["avg_launch_ms"] = avg_ms

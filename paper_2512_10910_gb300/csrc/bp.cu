@@ -35,7 +35,11 @@ namespace pne {
 
 namespace {
 
-constexpr int kBpWarps = 8;              // warps per block in the BP kernel
+constexpr int kBpWarps = 8;              // warps per block in the BP kernels
+constexpr int kBpClWarps = 4;            // warps per block in the cluster form
+// shared memory per block up to which the cluster form keeps its warps' site
+// tensors resident (four blocks per SM still fit in 228 KB)
+constexpr size_t kBpTensorSmem = 48 * 1024;
 constexpr long long kBarrierSpinLimit = 1ll << 25;
 
 struct BPParams {
@@ -363,6 +367,17 @@ struct ffacc {
         c = __fadd_rn(c, __fadd_rn(s.l, p.l));
     }
     __device__ __forceinline__ ff get() const { return ff_fast(h, c); }
+    // += x y: the exact product's low part goes to the compensation term
+    // without being renormalised first (12 FP32 instructions)
+    __device__ __forceinline__ void mad(ff x, ff y)
+    {
+        const float q = __fmul_rn(x.h, y.h);
+        float e = __fmaf_rn(x.h, y.h, -q);
+        e = __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, e));
+        const ff s = ff_two_sum(h, q);
+        h = s.h;
+        c = __fadd_rn(c, __fadd_rn(s.l, e));
+    }
 };
 __device__ __forceinline__ ff ff_shfl_xor(ff x, int off)
 {
@@ -448,6 +463,10 @@ struct BPFFParams {
     const int32_t *color_ptr, *color_sites;
     int smem_per_warp;            // ff entries
     int tabA, tabC;
+    // cluster form: each warp's site tensors kept in shared memory across the
+    // sweeps (t_slots per warp of slot_ff entries, slot_ff even); 0 = read
+    // them from global memory every sweep
+    int t_slots, slot_ff;
 };
 
 __device__ void site_messages_ff(const ff *__restrict__ T, int k, const int *dims, const ff *in, ff *u, ff *w,
@@ -661,42 +680,36 @@ __device__ __forceinline__ ff ldcg_ff(const ff *q)
     return {v.x, v.y};
 }
 
-// One site's outgoing messages, normalised and written to mdst; returns the
-// largest entry change (the same in every lane).  Messages are read through L2
-// (__ldcg): other blocks wrote them earlier in the same launch.
-__device__ float ff_site_update(const BPFFParams &p, int set, int v, const ff *msrc, ff *mdst, ff *in, ff *out,
-                                ff *u, ff *w, ff *x1, ff *x2, int lane)
+// Normalisation of a site's outgoing messages, LPL lanes per leg (LPL = 4
+// when every leg has dimension <= 4, else 8): unit 2-norm, the largest |entry|
+// positive (first index on ties), optional damping against the old message,
+// written to mdst; returns the largest entry change (the same in every lane).
+template <int LPL>
+__device__ __forceinline__ float ff_normalise_write(const BPFFParams &p, int l0, int k, const int *dims, const ff *msrc,
+                                                    ff *mdst, const ff *out, int lane)
 {
-    const int l0 = p.site_ptr[v], k = p.site_ptr[v + 1] - l0;
-    int dims[kMaxDeg];
-    for (int i = 0; i < kMaxDeg; ++i) dims[i] = (i < k) ? p.bond_dim[p.site_bonds[l0 + i]] : 1;
-    for (int e = lane; e < k * kMsgStride; e += 32)
-        in[e] = ldcg_ff(&msrc[(int64_t)p.inc_slot[l0 + e / kMsgStride] * kMsgStride + e % kMsgStride]);
-    __syncwarp();
-    {
-        const ff *Tv = p.T + set * p.set_stride + p.tens_off[v];
-        if (!site_messages_ff_fast(Tv, k, dims, in, u, w, x1, x2, out, lane))
-            site_messages_ff(Tv, k, dims, in, u, w, x1, x2, out, lane);
-    }
+    constexpr int LPW = 32 / LPL;
     float r = 0.f;
-    for (int j0 = 0; j0 < k; j0 += 4) {
-        const int j = j0 + (lane >> 3), a = lane & 7;
+    for (int j0 = 0; j0 < k; j0 += LPW) {
+        const int j = j0 + lane / LPL, a = lane % LPL;
         const bool live = (j < k) && (a < dims[j < k ? j : 0]);
         const ff o = live ? out[j * kMsgStride + a] : ff{0.f, 0.f};
         const ff old = live ? ldcg_ff(&msrc[(int64_t)(l0 + j) * kMsgStride + a]) : ff{0.f, 0.f};
         ff n2 = ff_mul(o, o);
-        for (int off = 4; off > 0; off >>= 1) n2 = ff_add(n2, ff_shfl_xor(n2, off));
+#pragma unroll
+        for (int off = LPL / 2; off > 0; off >>= 1) n2 = ff_add(n2, ff_shfl_xor(n2, off));
         ff big = live ? o : ff{-1.f, 0.f};
         bool has = live;
         int arg = a;
-        for (int off = 4; off > 0; off >>= 1) {
+#pragma unroll
+        for (int off = LPL / 2; off > 0; off >>= 1) {
             const ff ob = ff_shfl_xor(big, off);
             const int oa = __shfl_xor_sync(0xffffffffu, arg, off);
             const bool oh = __shfl_xor_sync(0xffffffffu, has, off);
             const bool take = oh && (!has || ff_abs_gt(ob, big) || (!ff_abs_gt(big, ob) && oa < arg));
             if (take) { big = ob; arg = oa; has = true; }
         }
-        const float oarg = __shfl_sync(0xffffffffu, o.h, (lane & ~7) | arg);
+        const float oarg = __shfl_sync(0xffffffffu, o.h, (lane & ~(LPL - 1)) | arg);
         ff nrm = ff_sqrt(n2);
         if (j < k && !(nrm.h > 0.f)) { atomicExch(p.flags + 1, 1); nrm = {1.f, 0.f}; }
         ff nv = ff_div(oarg < 0.f ? ff{-o.h, -o.l} : o, nrm);
@@ -704,18 +717,20 @@ __device__ float ff_site_update(const BPFFParams &p, int set, int v, const ff *m
             const float dm = (float)p.damping;
             ff m = ff_add(ff_mul(nv, {1.f - dm, 0.f}), ff_mul(old, {dm, 0.f}));
             ff m2 = live ? ff_mul(m, m) : ff{0.f, 0.f};
-            for (int off = 4; off > 0; off >>= 1) m2 = ff_add(m2, ff_shfl_xor(m2, off));
+#pragma unroll
+            for (int off = LPL / 2; off > 0; off >>= 1) m2 = ff_add(m2, ff_shfl_xor(m2, off));
             ff bg = live ? m : ff{-1.f, 0.f};
             bool hs = live;
             int ag = a;
-            for (int off = 4; off > 0; off >>= 1) {
+#pragma unroll
+            for (int off = LPL / 2; off > 0; off >>= 1) {
                 const ff ob = ff_shfl_xor(bg, off);
                 const int oa = __shfl_xor_sync(0xffffffffu, ag, off);
                 const bool oh = __shfl_xor_sync(0xffffffffu, hs, off);
                 const bool take = oh && (!hs || ff_abs_gt(ob, bg) || (!ff_abs_gt(bg, ob) && oa < ag));
                 if (take) { bg = ob; ag = oa; hs = true; }
             }
-            const float marg = __shfl_sync(0xffffffffu, m.h, (lane & ~7) | ag);
+            const float marg = __shfl_sync(0xffffffffu, m.h, (lane & ~(LPL - 1)) | ag);
             ff n3 = ff_sqrt(m2);
             if (j < k && !(n3.h > 0.f)) { atomicExch(p.flags + 1, 1); n3 = {1.f, 0.f}; }
             nv = ff_div(marg < 0.f ? ff{-m.h, -m.l} : m, n3);
@@ -725,13 +740,221 @@ __device__ float ff_site_update(const BPFFParams &p, int set, int v, const ff *m
             r = fmaxf(r, fabsf(__fadd_rn(__fsub_rn(nv.h, old.h), __fsub_rn(nv.l, old.l))));
         }
     }
+#pragma unroll
     for (int off = 16; off > 0; off >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
     return r;
 }
 
+// ---- sites whose legs all have dimension 4 (2 to 4 legs), two per warp.
+// Half h = lane >> 4 of the warp updates its own site; inside a half, lane
+// hl = 4 rg + cg holds rows rg RA .. rg RA + RA - 1 and columns cg RC ..
+// cg RC + RC - 1 of T[a][c] (a over the first H = K / 2 legs, c over the
+// others, last leg fastest), so each entry is read once for both halves of the
+// contraction: x1 = T w over the lane's columns and x2 = u^T T over its rows,
+// then summed over the four lanes of a row group (x1) or of a column group
+// (x2).  The same lane hl then forms output entry x = cg of leg j = rg and
+// normalises it with the other three lanes of its leg.  A site's result does
+// not depend on the other half's site (or on whether there is one).
+
+// the four values v[0..3] summed over the lanes that differ in lane bits hi
+// and lo; lane keeps the sum of v[2 bit(hi) + bit(lo)]
+__device__ __forceinline__ ff ff_reduce_scatter4(ff v0, ff v1, ff v2, ff v3, int lane, int hi, int lo)
+{
+    const bool bh = (lane & hi) != 0, bl = (lane & lo) != 0;
+    const ff k0 = ff_add(bh ? v2 : v0, ff_shfl_xor(bh ? v0 : v2, hi));
+    const ff k1 = ff_add(bh ? v3 : v1, ff_shfl_xor(bh ? v1 : v3, hi));
+    return ff_add(bl ? k1 : k0, ff_shfl_xor(bl ? k0 : k1, lo));
+}
+// v summed over the lanes that differ in lane bits hi and lo (the same in all four)
+__device__ __forceinline__ ff ff_allreduce4(ff v, int hi, int lo)
+{
+    v = ff_add(v, ff_shfl_xor(v, hi));
+    return ff_add(v, ff_shfl_xor(v, lo));
+}
+
+// largest |entry| of the four lanes of a leg (first index on ties), as in
+// ff_normalise_write; returns the lane offset (0..3) of that entry
+__device__ __forceinline__ int ff_argmax4(ff v, bool live, int a)
+{
+    ff big = live ? v : ff{-1.f, 0.f};
+    bool has = live;
+    int arg = a;
+#pragma unroll
+    for (int off = 2; off > 0; off >>= 1) {
+        const ff ob = ff_shfl_xor(big, off);
+        const int oa = __shfl_xor_sync(0xffffffffu, arg, off);
+        const bool oh = __shfl_xor_sync(0xffffffffu, has, off);
+        const bool take = oh && (!has || ff_abs_gt(ob, big) || (!ff_abs_gt(big, ob) && oa < arg));
+        if (take) { big = ob; arg = oa; has = true; }
+    }
+    return arg;
+}
+
+// Per-slot records of the cluster form, in shared memory: kSlotMeta ints
+// (first leg, pair kind, site id, the legs' incoming message slots) and the
+// site's current outgoing messages [4][4] (the entries this warp last wrote).
+constexpr int kSlotMeta = 8;
+enum { kMetaL0 = 0, kMetaKind = 1, kMetaSite = 2, kMetaInc = 3 };
+
+// every lane passes its half's site (meta, cur: the slot's records; T: its
+// tensor, 16-byte aligned; live: false for a half with no site of its own,
+// which then repeats the other half's site without writing); ws: the warp's
+// scratch, >= 128 ff.  Returns the largest message change over both sites
+// (the same in every lane).
+template <int K>
+__device__ float ff_site_pair4(const BPFFParams &p, const int *meta, ff *cur, const ff *__restrict__ T, bool live,
+                               ff *msg, ff *ws, int lane)
+{
+    constexpr int H = K / 2, A = cpow(4, H), C = cpow(4, K - H), RA = A / 4, RC = C / 4;
+    const int h = lane >> 4, hl = lane & 15, rg = hl >> 2, cg = hl & 3;
+    ff *in = ws + h * 32;             // [K][kMsgStride]
+    ff *x1 = ws + 64 + h * 16;        // [A]
+    ff *x2 = ws + 96 + h * 16;        // [C]
+    const int j = rg, x = cg;         // the lane's output entry
+    const bool mine = live && j < K;
+    const int l0 = meta[kMetaL0];
+    ff old = {0.f, 0.f};
+    if (j < K) {
+        in[j * kMsgStride + x] = ldcg_ff(&msg[(int64_t)meta[kMetaInc + j] * kMsgStride + x]);
+        old = cur[j * 4 + x];
+    }
+    __syncwarp();
+    ff w[RC];
+    if constexpr (K - H == 2) {
+        const ff b = in[H * kMsgStride + cg];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = ff_mul(b, in[(H + 1) * kMsgStride + i]);
+    } else {
+        w[0] = in[H * kMsgStride + cg];
+    }
+    ffacc p1[RA], p2[RC];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) {
+        const ff ur = (H == 2) ? ff_mul(in[rg], in[kMsgStride + r]) : in[rg];
+        const ff *row = T + (rg * RA + r) * C + cg * RC;
+        ff t[RC];
+        if constexpr (RC == 4) {
+            const float4 q0 = reinterpret_cast<const float4 *>(row)[0];
+            const float4 q1 = reinterpret_cast<const float4 *>(row)[1];
+            t[0] = {q0.x, q0.y}; t[1] = {q0.z, q0.w}; t[2] = {q1.x, q1.y}; t[3] = {q1.z, q1.w};
+        } else {
+            const float2 q0 = *reinterpret_cast<const float2 *>(row);
+            t[0] = {q0.x, q0.y};
+        }
+#pragma unroll
+        for (int i = 0; i < RC; ++i) {
+            p1[r].mad(t[i], w[i]);
+            p2[i].mad(ur, t[i]);
+        }
+    }
+    if constexpr (RA == 4) {
+        x1[4 * rg + cg] = ff_reduce_scatter4(p1[0].get(), p1[1].get(), p1[2].get(), p1[3].get(), lane, 2, 1);
+    } else {
+        const ff s1 = ff_allreduce4(p1[0].get(), 2, 1);
+        if (cg == 0) x1[rg] = s1;
+    }
+    if constexpr (RC == 4) {
+        x2[4 * cg + rg] = ff_reduce_scatter4(p2[0].get(), p2[1].get(), p2[2].get(), p2[3].get(), lane, 8, 4);
+    } else {
+        const ff s2 = ff_allreduce4(p2[0].get(), 8, 4);
+        if (rg == 0) x2[cg] = s2;
+    }
+    __syncwarp();
+    // output entry x of leg j: a one-leg half is x1 / x2 itself; in a two-leg
+    // half, the sum over the half's other leg times its message
+    ff o = {0.f, 0.f};
+    if (j < K) {
+        const bool first = j < H;
+        const ff *X = first ? x1 : x2;
+        if ((first ? H : K - H) == 1) {
+            o = X[x];
+        } else {
+            const int jj = first ? j : j - H;
+            const ff *m = in + (first ? 1 - j : H + 1 - jj) * kMsgStride;
+            ffacc acc;
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc.mad(X[jj ? 4 * y + x : 4 * x + y], m[y]);
+            o = acc.get();
+        }
+    }
+    // unit 2-norm over the leg's four lanes, largest |entry| positive
+    ff n2 = ff_mul(o, o);
+    n2 = ff_allreduce4(n2, 2, 1);
+    const int arg = ff_argmax4(o, j < K, x);
+    const float oarg = __shfl_sync(0xffffffffu, o.h, (lane & ~3) | arg);
+    ff nrm = ff_sqrt(n2);
+    if (mine && !(nrm.h > 0.f)) atomicExch(p.flags + 1, 1);
+    if (!(nrm.h > 0.f)) nrm = {1.f, 0.f};
+    ff nv = ff_div(oarg < 0.f ? ff{-o.h, -o.l} : o, nrm);
+    if (p.damping > 0.0) {
+        const float dm = (float)p.damping;
+        const ff m = ff_add(ff_mul(nv, {1.f - dm, 0.f}), ff_mul(old, {dm, 0.f}));
+        ff m2 = ff_allreduce4(ff_mul(m, m), 2, 1);
+        const int ag = ff_argmax4(m, j < K, x);
+        const float marg = __shfl_sync(0xffffffffu, m.h, (lane & ~3) | ag);
+        ff n3 = ff_sqrt(m2);
+        if (mine && !(n3.h > 0.f)) atomicExch(p.flags + 1, 1);
+        if (!(n3.h > 0.f)) n3 = {1.f, 0.f};
+        nv = ff_div(marg < 0.f ? ff{-m.h, -m.l} : m, n3);
+    }
+    float r = 0.f;
+    __syncwarp();
+    if (mine) {
+        msg[(int64_t)(l0 + j) * kMsgStride + x] = nv;
+        cur[j * 4 + x] = nv;
+        r = fabsf(__fadd_rn(__fsub_rn(nv.h, old.h), __fsub_rn(nv.l, old.l)));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, off));
+    return r;
+}
+
+// 2, 3 or 4 when every leg of v has dimension 4 (the pair form above), else 0
+__device__ __forceinline__ int ff_pair_kind(const BPFFParams &p, int v)
+{
+    const int l0 = p.site_ptr[v], k = p.site_ptr[v + 1] - l0;
+    if (k < 2 || k > 4) return 0;
+    for (int i = 0; i < k; ++i)
+        if (p.bond_dim[p.site_bonds[l0 + i]] != 4) return 0;
+    return k;
+}
+
+__device__ __forceinline__ float ff_pair_dispatch(const BPFFParams &p, int kind, const int *meta, ff *cur, const ff *T,
+                                                  bool live, ff *msg, ff *ws, int lane)
+{
+    switch (kind) {
+        case 2: return ff_site_pair4<2>(p, meta, cur, T, live, msg, ws, lane);
+        case 3: return ff_site_pair4<3>(p, meta, cur, T, live, msg, ws, lane);
+        default: return ff_site_pair4<4>(p, meta, cur, T, live, msg, ws, lane);
+    }
+}
+
+// One site's outgoing messages, normalised and written to mdst; returns the
+// largest entry change (the same in every lane).  Messages are read through L2
+// (__ldcg): other blocks wrote them earlier in the same launch.  Tv is the
+// site's tensor (in global or shared memory).
+__device__ float ff_site_update(const BPFFParams &p, int v, const ff *Tv, const ff *msrc, ff *mdst, ff *in, ff *out,
+                                ff *u, ff *w, ff *x1, ff *x2, int lane)
+{
+    const int l0 = p.site_ptr[v], k = p.site_ptr[v + 1] - l0;
+    int dims[kMaxDeg];
+    int dmax = 1;
+    for (int i = 0; i < kMaxDeg; ++i) {
+        dims[i] = (i < k) ? p.bond_dim[p.site_bonds[l0 + i]] : 1;
+        dmax = dims[i] > dmax ? dims[i] : dmax;
+    }
+    for (int e = lane; e < k * kMsgStride; e += 32)
+        in[e] = ldcg_ff(&msrc[(int64_t)p.inc_slot[l0 + e / kMsgStride] * kMsgStride + e % kMsgStride]);
+    __syncwarp();
+    if (!site_messages_ff_fast(Tv, k, dims, in, u, w, x1, x2, out, lane))
+        site_messages_ff(Tv, k, dims, in, u, w, x1, x2, out, lane);
+    return dmax <= 4 ? ff_normalise_write<4>(p, l0, k, dims, msrc, mdst, out, lane)
+                     : ff_normalise_write<8>(p, l0, k, dims, msrc, mdst, out, lane);
+}
+
 __global__ void __launch_bounds__(kBpWarps * 32, 4) bp_ff_kernel(BPFFParams p)
 {
-    extern __shared__ ff ffsmem[];
+    extern __shared__ __align__(16) ff ffsmem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     ff *ws = ffsmem + wib * p.smem_per_warp;
     ff *in = ws;
@@ -764,7 +987,8 @@ __global__ void __launch_bounds__(kBpWarps * 32, 4) bp_ff_kernel(BPFFParams p)
             if (it > 1 && __uint_as_float(__ldcg(res_prev + set)) < p.tol) continue;
             const ff *msrc = p.msg + src * msg_buf + set * msg_set;
             ff *mdst = p.msg + dst * msg_buf + set * msg_set;
-            const float r = ff_site_update(p, set, v, msrc, mdst, in, out, u, w, x1, x2, lane);
+            const float r = ff_site_update(p, v, p.T + set * p.set_stride + p.tens_off[v], msrc, mdst, in, out, u,
+                                           w, x1, x2, lane);
             if (lane == 0) atomicMax(res_cur + set, __float_as_uint(r));
             __syncwarp();
         }
@@ -802,11 +1026,20 @@ __global__ void __launch_bounds__(kBpWarps * 32, 4) bp_ff_kernel(BPFFParams p)
 // order only (in place, buffer 0).  Every block of a cluster takes the same
 // path: the loop decision depends only on the set's residual, read after a
 // cluster barrier, and the loop is bounded by max_iter.
-__global__ void __launch_bounds__(kBpWarps * 32, 4) bp_ff_cluster_kernel(BPFFParams p)
+//
+// A warp takes the sites of a colour two at a time (positions q, q + 1 of the
+// colour class, which the geometry sorts by leg count): sites whose legs all
+// have dimension 4 go through the half-warp pair form (both at once when they
+// have the same leg count), the others through the one-site form.  A warp
+// visits the same sites in the same order every sweep: with t_slots set, their
+// tensors are copied once into the warp's slots (slot_ff entries each, 16-byte
+// aligned) and read from shared memory afterwards; the pair form needs them
+// there.
+__global__ void __launch_bounds__(kBpClWarps * 32, 4) bp_ff_cluster_kernel(BPFFParams p)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
-    extern __shared__ ff ffsmem[];
+    extern __shared__ __align__(16) ff ffsmem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     ff *ws = ffsmem + wib * p.smem_per_warp;
     ff *in = ws;
@@ -817,21 +1050,86 @@ __global__ void __launch_bounds__(kBpWarps * 32, 4) bp_ff_cluster_kernel(BPFFPar
     ff *x2 = x1 + p.tabA;
     const int rank = (int)cluster.block_rank(), CL = (int)cluster.num_blocks();
     const int set = blockIdx.x / CL;
-    const int cwarp = rank * kBpWarps + wib, cwarps = CL * kBpWarps;
+    const int cwarp = rank * kBpClWarps + wib, cwarps = CL * kBpClWarps;
     const int64_t msg_set = (int64_t)p.n_legs * kMsgStride;
     ff *msg = p.msg + set * msg_set;
+    const ff *Tset = p.T + set * p.set_stride;
+    // with t_slots: [warps][t_slots][slot_ff] tensors, then [warps][t_slots][16]
+    // current messages, then [warps][t_slots][kSlotMeta] records
+    ff *tslots = nullptr, *curs = nullptr;
+    int *metas = nullptr;
+    if (p.t_slots > 0) {
+        ff *base = ffsmem + (int64_t)kBpClWarps * p.smem_per_warp;
+        tslots = base + (int64_t)wib * p.t_slots * p.slot_ff;
+        base += (int64_t)kBpClWarps * p.t_slots * p.slot_ff;
+        curs = base + (int64_t)wib * p.t_slots * 16;
+        base += (int64_t)kBpClWarps * p.t_slots * 16;
+        metas = reinterpret_cast<int *>(base) + (int64_t)wib * p.t_slots * kSlotMeta;
+        int sl = 0;
+        for (int ph = 0; ph < p.n_colors; ++ph) {
+            const int c0 = p.color_ptr[ph], nc = p.color_ptr[ph + 1] - c0;
+            for (int q = 2 * cwarp; q < nc; q += 2 * cwarps, sl += 2)
+                for (int e2 = 0; e2 < 2 && q + e2 < nc; ++e2) {
+                    const int v = p.color_sites[c0 + q + e2], l0 = p.site_ptr[v], k = p.site_ptr[v + 1] - l0;
+                    const ff *src = Tset + p.tens_off[v];
+                    const int n = (int)(p.tens_off[v + 1] - p.tens_off[v]);
+                    ff *dst = tslots + (int64_t)(sl + e2) * p.slot_ff;
+                    for (int e = lane; e < n; e += 32) dst[e] = src[e];
+                    int *m = metas + (sl + e2) * kSlotMeta;
+                    if (lane == 0) {
+                        m[kMetaL0] = l0;
+                        m[kMetaKind] = ff_pair_kind(p, v);
+                        m[kMetaSite] = v;
+                    }
+                    if (lane < 4) m[kMetaInc + lane] = lane < k ? p.inc_slot[l0 + lane] : 0;
+                    if (lane < 16 && lane / 4 < k)
+                        curs[(sl + e2) * 16 + lane] = msg[(int64_t)(l0 + lane / 4) * kMsgStride + lane % 4];
+                }
+        }
+        __syncwarp();
+    }
     for (int it = 1; it <= p.max_iter; ++it) {
         // residual slots rotate over three sweeps: the slot cleared here was
         // last read before the previous sweep's barriers
         unsigned int *res_cur = p.res + (int64_t)(it % 3) * p.n_sets + set;
         if (rank == 0 && threadIdx.x == 0) p.res[(int64_t)((it + 1) % 3) * p.n_sets + set] = 0u;
+        int sl = 0;
+        float racc = 0.f;
         for (int ph = 0; ph < p.n_colors; ++ph) {
             const int c0 = p.color_ptr[ph], nc = p.color_ptr[ph + 1] - c0;
-            for (int q = cwarp; q < nc; q += cwarps) {
-                const float r = ff_site_update(p, set, p.color_sites[c0 + q], msg, msg, in, out, u, w, x1, x2, lane);
-                if (lane == 0) atomicMax(res_cur, __float_as_uint(r));
+            for (int q = 2 * cwarp; q < nc; q += 2 * cwarps, sl += 2) {
+                const bool has_b = q + 1 < nc;
+                float r;
+                if (metas) {
+                    const int *ma = metas + sl * kSlotMeta, *mb = has_b ? ma + kSlotMeta : ma;
+                    const int ka = ma[kMetaKind], kb = has_b ? mb[kMetaKind] : 0;
+                    ff *ca = curs + sl * 16, *cb = has_b ? ca + 16 : ca;
+                    const ff *Ta = tslots + (int64_t)sl * p.slot_ff, *Tb = has_b ? Ta + p.slot_ff : Ta;
+                    if (ka > 0 && ka == kb) {
+                        const bool hi = lane >= 16;
+                        r = ff_pair_dispatch(p, ka, hi ? mb : ma, hi ? cb : ca, hi ? Tb : Ta, true, msg, ws, lane);
+                    } else {
+                        r = ka > 0 ? ff_pair_dispatch(p, ka, ma, ca, Ta, lane < 16, msg, ws, lane)
+                                   : ff_site_update(p, ma[kMetaSite], Ta, msg, msg, in, out, u, w, x1, x2, lane);
+                        if (has_b)
+                            r = fmaxf(r, kb > 0 ? ff_pair_dispatch(p, kb, mb, cb, Tb, lane < 16, msg, ws, lane)
+                                                : ff_site_update(p, mb[kMetaSite], Tb, msg, msg, in, out, u, w, x1,
+                                                                 x2, lane));
+                    }
+                } else {
+                    const int va = p.color_sites[c0 + q];
+                    r = ff_site_update(p, va, Tset + p.tens_off[va], msg, msg, in, out, u, w, x1, x2, lane);
+                    if (has_b) {
+                        const int vb = p.color_sites[c0 + q + 1];
+                        r = fmaxf(r, ff_site_update(p, vb, Tset + p.tens_off[vb], msg, msg, in, out, u, w, x1, x2,
+                                                    lane));
+                    }
+                }
+                racc = fmaxf(racc, r);
                 __syncwarp();
             }
+            // one residual word per warp and sweep, before the sweep's last barrier
+            if (ph + 1 == p.n_colors && lane == 0) atomicMax(res_cur, __float_as_uint(racc));
             cluster.sync();
         }
         const float rs = __uint_as_float(__ldcg(res_cur));
@@ -1382,14 +1680,36 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         int max_color = 0;
         for (int c = 0; c < g.n_colors; ++c) max_color = std::max(max_color, g.color_ptr[c + 1] - g.color_ptr[c]);
         int CL = 1;
-        while (CL * kBpWarps < max_color && CL < 16) CL *= 2;
-        bool cluster_ok = g.n_colors > 0 && max_color <= CL * kBpWarps * 4;
+        while (CL * kBpClWarps * 2 < max_color && CL < 16) CL *= 2;
+        bool cluster_ok = g.n_colors > 0 && max_color <= CL * kBpClWarps * 8;
+        // the cluster form's warp scratch also holds the pair form's (128 ff)
+        const int per_warp_cl = std::max(per_warp, 128);
+        const size_t smem_cl = (size_t)per_warp_cl * kBpClWarps * sizeof(double);
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute cattr[1];
+        fp.t_slots = 0;
+        fp.slot_ff = 0;
         if (cluster_ok) {
-            grant_smem(ctx, 0, bp_ff_cluster_kernel, smem);
-            cfg.blockDim = dim3(kBpWarps * 32);
-            cfg.dynamicSmemBytes = smem;
+            // slots per warp for a cluster of cl blocks (a warp takes
+            // ceil(ceil(nc / 2) / warps) pairs of sites of each colour), kept
+            // only while the block's shared memory stays within kBpTensorSmem
+            int slot_ff = 0;
+            for (int v = 0; v < g.n_sites; ++v)
+                slot_ff = std::max<int>(slot_ff, (int)(g.tens_off[v + 1] - g.tens_off[v]));
+            slot_ff = (slot_ff + 1) & ~1;
+            // per slot: the tensor, the current messages [4][4], the record
+            const size_t slot_bytes = (size_t)slot_ff * sizeof(ff) + 16 * sizeof(ff) + kSlotMeta * sizeof(int);
+            auto slots_for = [&](int cl) {
+                int n = 0;
+                for (int c = 0; c < g.n_colors; ++c) {
+                    const int pairs = (g.color_ptr[c + 1] - g.color_ptr[c] + 1) / 2;
+                    n += 2 * ((pairs + cl * kBpClWarps - 1) / (cl * kBpClWarps));
+                }
+                const size_t b = (size_t)kBpClWarps * n * slot_bytes;
+                return smem_cl + b <= kBpTensorSmem ? n : 0;
+            };
+            auto smem_for = [&](int cl) { return smem_cl + (size_t)kBpClWarps * slots_for(cl) * slot_bytes; };
+            cfg.blockDim = dim3(kBpClWarps * 32);
             cfg.stream = s;
             cattr[0].id = cudaLaunchAttributeClusterDimension;
             cattr[0].val.clusterDim.y = 1;
@@ -1397,36 +1717,44 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
             cfg.attrs = cattr;
             cfg.numAttrs = 1;
             // the largest cluster the device schedules with this kernel's
-            // resources (queried once per context, shared memory and size)
-            const std::pair<size_t, int> key{smem, CL};
-            int chosen = -1;
-            {
-                std::lock_guard<std::mutex> lk(ctx->launch_mu);
-                auto it = ctx->bp_cluster.find(key);
-                if (it != ctx->bp_cluster.end()) chosen = it->second;
-            }
-            if (chosen < 0) {
-                cudaFuncSetAttribute(bp_ff_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-                chosen = 0;
-                for (int cl = CL;;) {
+            // resources; whether (shared memory, cluster size) fits is queried
+            // once per context
+            int chosen = 0;
+            for (int cl = CL;;) {
+                const size_t sm = smem_for(cl);
+                const std::pair<size_t, int> key{sm, cl};
+                int fits = -1;
+                {
+                    std::lock_guard<std::mutex> lk(ctx->launch_mu);
+                    auto it = ctx->bp_cluster.find(key);
+                    if (it != ctx->bp_cluster.end()) fits = it->second;
+                }
+                if (fits < 0) {
+                    grant_smem(ctx, 0, bp_ff_cluster_kernel, sm);
+                    cudaFuncSetAttribute(bp_ff_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
                     cattr[0].val.clusterDim.x = cl;
                     cfg.gridDim = dim3(cl);
+                    cfg.dynamicSmemBytes = sm;
                     int ncl = 0;
-                    if (cudaOccupancyMaxActiveClusters(&ncl, (void *)bp_ff_cluster_kernel, &cfg) == cudaSuccess && ncl > 0) {
-                        chosen = cl;
-                        break;
-                    }
+                    fits = (cudaOccupancyMaxActiveClusters(&ncl, (void *)bp_ff_cluster_kernel, &cfg) == cudaSuccess &&
+                            ncl > 0) ? 1 : 0;
                     cudaGetLastError();
-                    if (cl == 1) break;
-                    cl /= 2;
-                    if (max_color > cl * kBpWarps * 4) break;
+                    std::lock_guard<std::mutex> lk(ctx->launch_mu);
+                    ctx->bp_cluster[key] = fits;
                 }
-                std::lock_guard<std::mutex> lk(ctx->launch_mu);
-                ctx->bp_cluster[key] = chosen;
+                if (fits) { chosen = cl; break; }
+                if (cl == 1) break;
+                cl /= 2;
+                if (max_color > cl * kBpClWarps * 8) break;
             }
             if (chosen > 0) {
                 CL = chosen;
                 cattr[0].val.clusterDim.x = CL;
+                cfg.dynamicSmemBytes = smem_for(CL);
+                grant_smem(ctx, 0, bp_ff_cluster_kernel, cfg.dynamicSmemBytes);
+                fp.t_slots = slots_for(CL);
+                fp.slot_ff = fp.t_slots > 0 ? slot_ff : 0;
+                fp.smem_per_warp = per_warp_cl;
             } else {
                 cluster_ok = false;
             }

@@ -383,6 +383,14 @@ pne_status finish_geometry(pne_ctx *ctx, Geometry &g, cudaStream_t s)
         g.color_sites.assign(N, 0);
         std::vector<int32_t> fill(g.color_ptr.begin(), g.color_ptr.end() - 1);
         for (int v = 0; v < N; ++v) g.color_sites[fill[col[v]]++] = v;
+        // within a colour (sites updated independently, in any order) by leg
+        // count, then id: the float-float sweeps take neighbouring entries
+        // two at a time, and sites of one leg count share a code path
+        for (int c = 0; c < nc; ++c)
+            std::stable_sort(g.color_sites.begin() + g.color_ptr[c], g.color_sites.begin() + g.color_ptr[c + 1],
+                             [&](int a, int b) {
+                                 return g.site_ptr[a + 1] - g.site_ptr[a] < g.site_ptr[b + 1] - g.site_ptr[b];
+                             });
     }
     g.site_nbr.assign(2 * g.site_bonds.size(), -1);
     for (int v = 0; v < N; ++v)

@@ -124,7 +124,7 @@ struct Geometry {
     std::vector<int64_t> tens_off;      // [n_sites+1] row-major tensor offsets
     std::vector<int32_t> blk_off;       // [n_sites][64] excitation-block offsets
     std::vector<int32_t> color_ptr;     // [n_colors+1] proper colouring of the sites (closed bonds)
-    std::vector<int32_t> color_sites;   // [n_sites] sites grouped by colour, ascending within a colour
+    std::vector<int32_t> color_sites;   // [n_sites] sites grouped by colour; within a colour by leg count, then id
     std::vector<int32_t> site_nbr;      // [n_legs][2] per leg of site_bonds: (bond, site at its other end; -1 open)
     int n_colors = 0;
     int max_deg = 0, max_dim = 0;

@@ -321,7 +321,16 @@ FF_CASES = [
     ("ising3d_ordered", lambda: I.ising_tensors(I.cubic_lattice(4, 4, 4, 2), 0.25), 8),
     ("ising2d", lambda: I.ising_tensors(I.square_lattice(4, 4, 2), 0.40), 24),
     ("bias_signed", lambda: I.random_tensors(I.square_lattice(5, 5, 3), 7, "bias:0.5"), 8),
+    # dimension-4 sites (the half-warp pair form) beside sites with a
+    # dimension-3 leg (the one-site form) in every colour class
+    ("mixed_D34", lambda: _mixed_d34(), 6),
 ]
+
+
+def _mixed_d34():
+    g = I.square_lattice(7, 6, 4)
+    g.bond_dim[::5] = 3
+    return I.random_tensors(g, 12)
 
 
 @pytest.mark.parametrize("name,make,K", FF_CASES, ids=[c[0] for c in FF_CASES])
@@ -334,6 +343,19 @@ def test_float_float_bp_matches_oracle(ctx, name, make, K):
     _check_values(ff, ref)
     assert abs(ff["log_abs"] - d64["log_abs"]) <= 1e-10
     assert ff["bp_iters"] > 0
+
+
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp64", "ff"])
+@pytest.mark.parametrize("name", ["random2d_D4", "bias_signed", "mixed_D34"])
+def test_damped_bp_reaches_the_same_fixed_point(ctx, name, arith):
+    # damping changes the path to the fixed point, not the fixed point
+    make, K = {c[0]: (c[1], c[2]) for c in FF_CASES}[name]
+    net = make()
+    ref = X.pne(net, K, E.LOOP)
+    (r,) = ctx.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64, arithmetic=arith, damping=0.3)
+    (u,) = ctx.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64, arithmetic=arith)
+    _check_values(r, ref)
+    assert r["bp_iters"] > u["bp_iters"] > 0
 
 
 # ---------------------------------------------------------------- search schedule
