@@ -932,6 +932,8 @@ def run_batched(args, wl, rank, world, local_rank, steps=None, warmup=None):
         parts.append(p); terms.append(t); datas.append(data); keep.append((ns, kp))
     batch = pne.pne_batch_create(ctx.h, terms, dtype, None, sh)
     wpb, bps, tuned = pne.pne_batch_config(batch)
+    sched = {pne.PNE_SCHED_HANDLE: "handle order", pne.PNE_SCHED_LARGEST_FIRST: "largest running tensors first"}[
+        pne.pne_batch_schedule(batch)]
     setup_s = time.time() - t0
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -978,7 +980,7 @@ def run_batched(args, wl, rank, world, local_rank, steps=None, warmup=None):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": wl["desc"], "networks": len(work), "geometry_groups": len(groups),
                       "terms_per_step": n_terms, "clusters_per_step": n_clusters,
-                      "launch_shape": {"warps_per_block": wpb, "blocks_per_sm": bps, "tuned_ms": tuned},
+                      "launch_shape": {"warps_per_block": wpb, "blocks_per_sm": bps, "schedule": sched, "tuned_ms": tuned},
                       "setup_s": setup_s, "enumeration": "per geometry, built once at setup",
                       "l2": "flushed between timed steps (256 MB write)"},
            "gpu_launches": int(sum(v[0] for v in prof.values())),

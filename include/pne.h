@@ -308,12 +308,25 @@ typedef struct {
     int32_t warps_per_block;   /* 0: autotune (with blocks_per_sm)            */
     int32_t blocks_per_sm;     /* 0: autotune                                 */
     int32_t use_graph;         /* capture and replay a CUDA graph             */
+    int32_t schedule;          /* order of the contraction items in the queue,
+                                  with a given launch shape: PNE_SCHED_HANDLE
+                                  or PNE_SCHED_LARGEST_FIRST; tuned together
+                                  with the shape when autotuning              */
 } pne_batch_opts;
 
+/* Work orders of the contraction items (the sum items always follow them).
+ * HANDLE: handle by handle, tensor set by tensor set, clusters in list order.
+ * LARGEST_FIRST: items with the largest running tensors first (stable), so the
+ * costly items do not start last and leave the tail of the launch to a few
+ * warps.  Results do not depend on the order. */
+#define PNE_SCHED_HANDLE 0
+#define PNE_SCHED_LARGEST_FIRST 1
+
 /* terms[i] must be LOOP-mode handles whose partitions stay alive as long as
- * the batch.  Autotuning times each candidate launch shape on this batch and
- * caches the winner (in memory, and in the file named by the environment
- * variable PNE_AUTOTUNE_CACHE when set).  Synchronises `stream`. */
+ * the batch.  Autotuning times each candidate (launch shape, schedule) on this
+ * batch and caches the winner (in memory, and in the file named by the
+ * environment variable PNE_AUTOTUNE_CACHE when set).  PNE_EINVAL for a given
+ * shape that does not fit or an unknown schedule.  Synchronises `stream`. */
 pne_status pne_batch_create(pne_ctx *ctx, int32_t n, pne_terms *const *terms, pne_dtype dtype,
                             const pne_batch_opts *opts, void *stream, pne_batch **out);
 /* Replay: writes sum_i pne_terms_n_results(terms[i]) results, handle-major.
@@ -322,6 +335,8 @@ pne_status pne_batch_run(pne_ctx *ctx, pne_batch *b, void *stream, pne_result *o
 int64_t pne_batch_n_results(const pne_batch *b);
 /* Chosen launch shape and its timed duration (ms) from the autotuner. */
 pne_status pne_batch_config(const pne_batch *b, int32_t *warps_per_block, int32_t *blocks_per_sm, double *tuned_ms);
+/* Chosen work order (PNE_SCHED_*). */
+pne_status pne_batch_schedule(const pne_batch *b, int32_t *schedule);
 void pne_batch_destroy(pne_batch *b);
 
 /* ---- served form: continuous batching of requests ------------------------- */

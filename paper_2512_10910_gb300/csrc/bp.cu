@@ -36,7 +36,8 @@ namespace pne {
 namespace {
 
 constexpr int kBpWarps = 8;              // warps per block in the BP kernels
-constexpr int kBpClWarps = 4;            // warps per block in the cluster form
+// warps per block of the cluster form: 4 with two sites per warp task, 8 with one
+template <int TASK> struct ClusterForm { static constexpr int kWarps = TASK == 2 ? 4 : 8; };
 // shared memory per block up to which the cluster form keeps its warps' site
 // tensors resident (four blocks per SM still fit in 228 KB)
 constexpr size_t kBpTensorSmem = 48 * 1024;
@@ -796,6 +797,20 @@ __device__ __forceinline__ int ff_argmax4(ff v, bool live, int a)
 constexpr int kSlotMeta = 8;
 enum { kMetaL0 = 0, kMetaKind = 1, kMetaSite = 2, kMetaInc = 3 };
 
+// RC consecutive pair entries from 16-byte aligned (RC = 4) or 8-byte aligned
+// (RC = 1) shared memory
+template <int RC> __device__ __forceinline__ void ff_load_row(const ff *row, ff *t);
+template <> __device__ __forceinline__ void ff_load_row<4>(const ff *row, ff *t)
+{
+    const float4 a = reinterpret_cast<const float4 *>(row)[0], b = reinterpret_cast<const float4 *>(row)[1];
+    t[0] = {a.x, a.y}; t[1] = {a.z, a.w}; t[2] = {b.x, b.y}; t[3] = {b.z, b.w};
+}
+template <> __device__ __forceinline__ void ff_load_row<1>(const ff *row, ff *t)
+{
+    const float2 a = *reinterpret_cast<const float2 *>(row);
+    t[0] = {a.x, a.y};
+}
+
 // every lane passes its half's site (meta, cur: the slot's records; T: its
 // tensor, 16-byte aligned; live: false for a half with no site of its own,
 // which then repeats the other half's site without writing); ws: the warp's
@@ -833,14 +848,7 @@ __device__ float ff_site_pair4(const BPFFParams &p, const int *meta, ff *cur, co
         const ff ur = (H == 2) ? ff_mul(in[rg], in[kMsgStride + r]) : in[rg];
         const ff *row = T + (rg * RA + r) * C + cg * RC;
         ff t[RC];
-        if constexpr (RC == 4) {
-            const float4 q0 = reinterpret_cast<const float4 *>(row)[0];
-            const float4 q1 = reinterpret_cast<const float4 *>(row)[1];
-            t[0] = {q0.x, q0.y}; t[1] = {q0.z, q0.w}; t[2] = {q1.x, q1.y}; t[3] = {q1.z, q1.w};
-        } else {
-            const float2 q0 = *reinterpret_cast<const float2 *>(row);
-            t[0] = {q0.x, q0.y};
-        }
+        ff_load_row<RC>(row, t);
 #pragma unroll
         for (int i = 0; i < RC; ++i) {
             p1[r].mad(t[i], w[i]);
@@ -1027,16 +1035,20 @@ __global__ void __launch_bounds__(kBpWarps * 32, 4) bp_ff_kernel(BPFFParams p)
 // path: the loop decision depends only on the set's residual, read after a
 // cluster barrier, and the loop is bounded by max_iter.
 //
-// A warp takes the sites of a colour two at a time (positions q, q + 1 of the
-// colour class, which the geometry sorts by leg count): sites whose legs all
-// have dimension 4 go through the half-warp pair form (both at once when they
-// have the same leg count), the others through the one-site form.  A warp
-// visits the same sites in the same order every sweep: with t_slots set, their
-// tensors are copied once into the warp's slots (slot_ff entries each, 16-byte
-// aligned) and read from shared memory afterwards; the pair form needs them
-// there.
-__global__ void __launch_bounds__(kBpClWarps * 32, 4) bp_ff_cluster_kernel(BPFFParams p)
+// TASK = 2 (networks whose sites mostly have legs of dimension 4; blocks of 4
+// warps): a warp takes the sites of a colour two at a time (positions q, q + 1
+// of the colour class, which the geometry sorts by leg count); sites whose legs
+// all have dimension 4 go through the half-warp pair form (both at once when
+// they have the same leg count), the others through the one-site form.
+// TASK = 1 (the other networks; blocks of 8 warps): one site per warp task,
+// always the one-site form.  A warp visits the same sites in the same order
+// every sweep: with t_slots set, their tensors are copied once into the warp's
+// slots (slot_ff entries each, 16-byte aligned) and read from shared memory
+// afterwards; the pair form needs them there.
+template <int TASK>
+__global__ void __launch_bounds__(ClusterForm<TASK>::kWarps * 32, 4) bp_ff_cluster_kernel(BPFFParams p)
 {
+    constexpr int kBpClWarps = ClusterForm<TASK>::kWarps;
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) ff ffsmem[];
@@ -1068,8 +1080,8 @@ __global__ void __launch_bounds__(kBpClWarps * 32, 4) bp_ff_cluster_kernel(BPFFP
         int sl = 0;
         for (int ph = 0; ph < p.n_colors; ++ph) {
             const int c0 = p.color_ptr[ph], nc = p.color_ptr[ph + 1] - c0;
-            for (int q = 2 * cwarp; q < nc; q += 2 * cwarps, sl += 2)
-                for (int e2 = 0; e2 < 2 && q + e2 < nc; ++e2) {
+            for (int q = TASK * cwarp; q < nc; q += TASK * cwarps, sl += TASK)
+                for (int e2 = 0; e2 < TASK && q + e2 < nc; ++e2) {
                     const int v = p.color_sites[c0 + q + e2], l0 = p.site_ptr[v], k = p.site_ptr[v + 1] - l0;
                     const ff *src = Tset + p.tens_off[v];
                     const int n = (int)(p.tens_off[v + 1] - p.tens_off[v]);
@@ -1097,10 +1109,14 @@ __global__ void __launch_bounds__(kBpClWarps * 32, 4) bp_ff_cluster_kernel(BPFFP
         float racc = 0.f;
         for (int ph = 0; ph < p.n_colors; ++ph) {
             const int c0 = p.color_ptr[ph], nc = p.color_ptr[ph + 1] - c0;
-            for (int q = 2 * cwarp; q < nc; q += 2 * cwarps, sl += 2) {
-                const bool has_b = q + 1 < nc;
+            for (int q = TASK * cwarp; q < nc; q += TASK * cwarps, sl += TASK) {
+                const bool has_b = TASK == 2 && q + 1 < nc;
                 float r;
-                if (metas) {
+                if constexpr (TASK == 1) {
+                    const int va = metas ? metas[sl * kSlotMeta + kMetaSite] : p.color_sites[c0 + q];
+                    const ff *Ta = metas ? tslots + (int64_t)sl * p.slot_ff : Tset + p.tens_off[va];
+                    r = ff_site_update(p, va, Ta, msg, msg, in, out, u, w, x1, x2, lane);
+                } else if (metas) {
                     const int *ma = metas + sl * kSlotMeta, *mb = has_b ? ma + kSlotMeta : ma;
                     const int ka = ma[kMetaKind], kb = has_b ? mb[kMetaKind] : 0;
                     ff *ca = curs + sl * 16, *cb = has_b ? ca + 16 : ca;
@@ -1676,12 +1692,24 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         fp.smem_per_warp = per_warp; fp.tabA = tabA; fp.tabC = tabC;
         fp.n_colors = g.n_colors; fp.color_ptr = g.d_color_ptr; fp.color_sites = g.d_color_sites;
         // one cluster per tensor set when the colour classes are small enough
-        // (at most four sites per warp and phase in a cluster of <= 16 blocks)
+        // (at most four warp tasks per warp and phase in a cluster of <= 16
+        // blocks); two sites per task when at least half of the sites take
+        // the pair form (every leg of dimension 4, 2 to 4 legs)
         int max_color = 0;
         for (int c = 0; c < g.n_colors; ++c) max_color = std::max(max_color, g.color_ptr[c + 1] - g.color_ptr[c]);
+        int n_pair = 0;
+        for (int v = 0; v < g.n_sites; ++v) {
+            const int k = g.site_ptr[v + 1] - g.site_ptr[v];
+            bool all4 = k >= 2 && k <= 4;
+            for (int i = 0; i < k && all4; ++i) all4 = g.bond_dim[g.site_bonds[g.site_ptr[v] + i]] == 4;
+            n_pair += all4 ? 1 : 0;
+        }
+        const int task = 2 * n_pair >= g.n_sites ? 2 : 1;
+        const int kBpClWarps = task == 2 ? ClusterForm<2>::kWarps : ClusterForm<1>::kWarps;
+        const void *cl_kernel = task == 2 ? (const void *)bp_ff_cluster_kernel<2> : (const void *)bp_ff_cluster_kernel<1>;
         int CL = 1;
-        while (CL * kBpClWarps * 2 < max_color && CL < 16) CL *= 2;
-        bool cluster_ok = g.n_colors > 0 && max_color <= CL * kBpClWarps * 8;
+        while (CL * kBpClWarps * task < max_color && CL < 16) CL *= 2;
+        bool cluster_ok = g.n_colors > 0 && max_color <= CL * kBpClWarps * task * 4;
         // the cluster form's warp scratch also holds the pair form's (128 ff)
         const int per_warp_cl = std::max(per_warp, 128);
         const size_t smem_cl = (size_t)per_warp_cl * kBpClWarps * sizeof(double);
@@ -1691,8 +1719,9 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         fp.slot_ff = 0;
         if (cluster_ok) {
             // slots per warp for a cluster of cl blocks (a warp takes
-            // ceil(ceil(nc / 2) / warps) pairs of sites of each colour), kept
-            // only while the block's shared memory stays within kBpTensorSmem
+            // ceil(ceil(nc / task) / warps) tasks of `task` sites of each
+            // colour), kept only while the block's shared memory stays within
+            // kBpTensorSmem
             int slot_ff = 0;
             for (int v = 0; v < g.n_sites; ++v)
                 slot_ff = std::max<int>(slot_ff, (int)(g.tens_off[v + 1] - g.tens_off[v]));
@@ -1702,8 +1731,8 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
             auto slots_for = [&](int cl) {
                 int n = 0;
                 for (int c = 0; c < g.n_colors; ++c) {
-                    const int pairs = (g.color_ptr[c + 1] - g.color_ptr[c] + 1) / 2;
-                    n += 2 * ((pairs + cl * kBpClWarps - 1) / (cl * kBpClWarps));
+                    const int tasks = (g.color_ptr[c + 1] - g.color_ptr[c] + task - 1) / task;
+                    n += task * ((tasks + cl * kBpClWarps - 1) / (cl * kBpClWarps));
                 }
                 const size_t b = (size_t)kBpClWarps * n * slot_bytes;
                 return smem_cl + b <= kBpTensorSmem ? n : 0;
@@ -1722,7 +1751,7 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
             int chosen = 0;
             for (int cl = CL;;) {
                 const size_t sm = smem_for(cl);
-                const std::pair<size_t, int> key{sm, cl};
+                const std::pair<size_t, int> key{sm, cl + 64 * task};
                 int fits = -1;
                 {
                     std::lock_guard<std::mutex> lk(ctx->launch_mu);
@@ -1730,13 +1759,13 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
                     if (it != ctx->bp_cluster.end()) fits = it->second;
                 }
                 if (fits < 0) {
-                    grant_smem(ctx, 0, bp_ff_cluster_kernel, sm);
-                    cudaFuncSetAttribute(bp_ff_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+                    grant_dynamic_smem(cl_kernel, sm);
+                    cudaFuncSetAttribute(cl_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
                     cattr[0].val.clusterDim.x = cl;
                     cfg.gridDim = dim3(cl);
                     cfg.dynamicSmemBytes = sm;
                     int ncl = 0;
-                    fits = (cudaOccupancyMaxActiveClusters(&ncl, (void *)bp_ff_cluster_kernel, &cfg) == cudaSuccess &&
+                    fits = (cudaOccupancyMaxActiveClusters(&ncl, cl_kernel, &cfg) == cudaSuccess &&
                             ncl > 0) ? 1 : 0;
                     cudaGetLastError();
                     std::lock_guard<std::mutex> lk(ctx->launch_mu);
@@ -1745,13 +1774,13 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
                 if (fits) { chosen = cl; break; }
                 if (cl == 1) break;
                 cl /= 2;
-                if (max_color > cl * kBpClWarps * 8) break;
+                if (max_color > cl * kBpClWarps * task * 4) break;
             }
             if (chosen > 0) {
                 CL = chosen;
                 cattr[0].val.clusterDim.x = CL;
                 cfg.dynamicSmemBytes = smem_for(CL);
-                grant_smem(ctx, 0, bp_ff_cluster_kernel, cfg.dynamicSmemBytes);
+                grant_dynamic_smem(cl_kernel, cfg.dynamicSmemBytes);
                 fp.t_slots = slots_for(CL);
                 fp.slot_ff = fp.t_slots > 0 ? slot_ff : 0;
                 fp.smem_per_warp = per_warp_cl;
@@ -1784,7 +1813,8 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
             ProfScope ps(ctx, s, "bp_sweeps");
             if (cluster_ok) {
                 cfg.gridDim = dim3((unsigned)(n_sets * CL));
-                fe = cudaLaunchKernelEx(&cfg, bp_ff_cluster_kernel, fp);
+                fe = task == 2 ? cudaLaunchKernelEx(&cfg, bp_ff_cluster_kernel<2>, fp)
+                               : cudaLaunchKernelEx(&cfg, bp_ff_cluster_kernel<1>, fp);
             } else {
                 fe = cudaLaunchCooperativeKernel((void *)bp_ff_kernel, dim3(nb_ff), dim3(kBpWarps * 32), fargs, smem, s);
             }

@@ -1974,7 +1974,14 @@ pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms
         for (int b = 0; b < p->n_members; ++b)
             for (int d = 0; d < G.n_desc; ++d) sum_items.push_back({g, 1, b, d, 0});
     }
+    // the two work orders (PNE_SCHED_*), one after the other on the device:
+    // handle order, then the contraction items by running-tensor size,
+    // largest first (stable); the sum items follow the contraction items in both
+    std::vector<BatchItem> largest(items);
+    std::stable_sort(largest.begin(), largest.end(),
+                     [](const BatchItem &a, const BatchItem &b) { return a.aux > b.aux; });
     items.insert(items.end(), sum_items.begin(), sum_items.end());
+    largest.insert(largest.end(), sum_items.begin(), sum_items.end());
     bp->n_items = (int64_t)items.size();
     bp->n_desc = (int64_t)descs.size();
     bp->n_partials = part_off;
@@ -1983,7 +1990,7 @@ pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms
     // counters: next (u64), done[G] (u32), need[G] (u32), status[2] (i32, 16-aligned)
     const size_t cnt_bytes = status_offset(bp->G) + 16;
     if ((st = dev_alloc(ctx, bp->groups, groups.size() * sizeof(BatchGroup), s)) ||
-        (st = dev_alloc(ctx, bp->items, std::max<size_t>(items.size(), 1) * sizeof(BatchItem), s)) ||
+        (st = dev_alloc(ctx, bp->items, std::max<size_t>(2 * items.size(), 1) * sizeof(BatchItem), s)) ||
         (st = dev_alloc(ctx, bp->descs, std::max<size_t>(descs.size(), 1) * sizeof(SumDesc), s)) ||
         (st = dev_alloc(ctx, bp->partials, std::max<int64_t>(part_off, 1) * 8, s)) ||
         (st = dev_alloc(ctx, bp->fin_start, fin_start.size() * 8, s)) ||
@@ -2001,7 +2008,12 @@ pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms
         return PNE_ENOMEM;
     }
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->groups.ptr, groups.data(), groups.size() * sizeof(BatchGroup), cudaMemcpyHostToDevice, s));
-    if (!items.empty()) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->items.ptr, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s));
+    if (!items.empty()) {
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->items.ptr, items.data(), items.size() * sizeof(BatchItem),
+                                          cudaMemcpyHostToDevice, s));
+        PNE_CUDA_TRY(ctx, cudaMemcpyAsync((BatchItem *)bp->items.ptr + items.size(), largest.data(),
+                                          largest.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s));
+    }
     if (!descs.empty()) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->descs.ptr, descs.data(), descs.size() * sizeof(SumDesc), cudaMemcpyHostToDevice, s));
     PNE_CUDA_TRY(ctx, cudaMemcpyAsync(bp->fin_start.ptr, fin_start.data(), fin_start.size() * 8, cudaMemcpyHostToDevice, s));
     // need[] sits after next and done[]
@@ -2019,7 +2031,7 @@ pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms
 
 namespace {
 template <typename T, typename L, int R>
-pne_status launch_fused(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStream_t s)
+pne_status launch_fused(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, int sched, cudaStream_t s)
 {
     auto kern = fused_batch_kernel<T, L, R>;
     const size_t smem = bp->smem_per_warp * wpb;
@@ -2034,7 +2046,8 @@ pne_status launch_fused(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStrea
         set_error(ctx, PNE_EINVAL, "batch scratch not prepared for this launch shape");
         return PNE_EINVAL;
     }
-    kern<<<bps * ctx->n_sm, wpb * 32, smem, s>>>((const BatchGroup *)bp->groups.ptr, (const BatchItem *)bp->items.ptr,
+    const BatchItem *items = (const BatchItem *)bp->items.ptr + (sched == PNE_SCHED_LARGEST_FIRST ? bp->n_items : 0);
+    kern<<<bps * ctx->n_sm, wpb * 32, smem, s>>>((const BatchGroup *)bp->groups.ptr, items,
                                                  bp->n_items, (const SumDesc *)bp->descs.ptr, (double *)bp->partials.ptr,
                                                  next, done, need, bp->xsm, glob ? bp->xmax : 0,
                                                  glob ? (T *)bp->xscratch.ptr : nullptr, status);
@@ -2078,7 +2091,7 @@ pne_status batch_prepare(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStre
     return PNE_OK;
 }
 
-pne_status batch_enqueue(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStream_t s)
+pne_status batch_enqueue(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, int sched, cudaStream_t s)
 {
     pne_status st;
     // conversions of updated partitions (each partition once)
@@ -2093,10 +2106,10 @@ pne_status batch_enqueue(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStre
     PNE_CUDA_TRY(ctx, cudaMemsetAsync(cb + status_offset(bp->G), 0, 16, s));
     {
         ProfScope ps(ctx, s, "batch_fused");
-        if (bp->dtype == PNE_F64) st = launch_fused<double, Load<double>, 0>(ctx, bp, wpb, bps, s);
-        else if (bp->dtype == PNE_BF16) st = launch_fused<float, LoadBF16, 2>(ctx, bp, wpb, bps, s);
-        else if (bp->dtype == PNE_TF32) st = launch_fused<float, Load<float>, 1>(ctx, bp, wpb, bps, s);
-        else st = launch_fused<float, Load<float>, 0>(ctx, bp, wpb, bps, s);
+        if (bp->dtype == PNE_F64) st = launch_fused<double, Load<double>, 0>(ctx, bp, wpb, bps, sched, s);
+        else if (bp->dtype == PNE_BF16) st = launch_fused<float, LoadBF16, 2>(ctx, bp, wpb, bps, sched, s);
+        else if (bp->dtype == PNE_TF32) st = launch_fused<float, Load<float>, 1>(ctx, bp, wpb, bps, sched, s);
+        else st = launch_fused<float, Load<float>, 0>(ctx, bp, wpb, bps, sched, s);
         if (st) return st;
     }
     {

@@ -1674,7 +1674,7 @@ struct pne_batch {
     pne_ctx *ctx = nullptr;
     pne::BatchPlan *plan = nullptr;
     std::vector<pne_terms *> terms;
-    int dtype = 0, wpb = 4, bps = 1;
+    int dtype = 0, wpb = 4, bps = 1, sched = PNE_SCHED_HANDLE;
     double tuned_ms = 0.0;
     bool use_graph = false;
     cudaStream_t cap = nullptr;
@@ -1686,33 +1686,40 @@ struct pne_batch {
 
 namespace {
 
-// Launch shapes found by the autotuner, by batch signature (process-wide;
-// g_tune_mu guards the map, its file and the one-time load).
-std::map<std::string, std::pair<std::pair<int, int>, double>> g_tune_cache;
+// Launch shapes and work orders found by the autotuner, by batch signature
+// (process-wide; g_tune_mu guards the map, its file and the one-time load).
+struct TuneEntry {
+    int wpb, bps, sched;
+    double ms;
+};
+std::map<std::string, TuneEntry> g_tune_cache;
 std::mutex g_tune_mu;
 bool g_tune_loaded = false;
 
+// file lines: "<key> <warps per block> <blocks per SM> <schedule> <ms>";
+// lines of any other form are skipped
 void tune_cache_load()
 {
     const char *path = std::getenv("PNE_AUTOTUNE_CACHE");
     if (!path) return;
     FILE *f = std::fopen(path, "r");
     if (!f) return;
-    char key[512];
-    int w, b;
+    char line[1024], key[512];
+    int w, b, sc;
     double ms;
-    while (std::fscanf(f, "%511s %d %d %lf", key, &w, &b, &ms) == 4) g_tune_cache[key] = {{w, b}, ms};
+    while (std::fgets(line, sizeof(line), f))
+        if (std::sscanf(line, "%511s %d %d %d %lf", key, &w, &b, &sc, &ms) == 5) g_tune_cache[key] = {w, b, sc, ms};
     std::fclose(f);
 }
 
-void tune_cache_store(const std::string &key, int w, int b, double ms)
+void tune_cache_store(const std::string &key, const TuneEntry &e)
 {
-    g_tune_cache[key] = {{w, b}, ms};
+    g_tune_cache[key] = e;
     const char *path = std::getenv("PNE_AUTOTUNE_CACHE");
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d %.6f\n", key.c_str(), w, b, ms);
+    std::fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), e.wpb, e.bps, e.sched, e.ms);
     std::fclose(f);
 }
 
@@ -1746,52 +1753,66 @@ pne_status pne_batch_create(pne_ctx *ctx, int32_t n, pne_terms *const *terms, pn
     const bool prof = ctx->prof.on;
     ctx->prof.on = false;
     if (w0 > 0 && b0 > 0) {
+        const int sc = opts->schedule;
+        if (sc != PNE_SCHED_HANDLE && sc != PNE_SCHED_LARGEST_FIRST) {
+            ctx->prof.on = prof;
+            pne_batch_destroy(b);
+            set_error(ctx, PNE_EINVAL, "unknown batch schedule");
+            return PNE_EINVAL;
+        }
         if (w0 > 32 || batch_max_blocks_per_sm(b->plan, w0) < b0) {
             ctx->prof.on = prof;
             pne_batch_destroy(b);
             set_error(ctx, PNE_EINVAL, "launch shape does not fit (shared memory or occupancy)");
             return PNE_EINVAL;
         }
-        b->wpb = w0; b->bps = b0;
+        b->wpb = w0; b->bps = b0; b->sched = sc;
     } else {
         std::unique_lock<std::mutex> tlk(g_tune_mu);
         if (!g_tune_loaded) { tune_cache_load(); g_tune_loaded = true; }
         uint64_t ncl = 0, nmem = 0;
         for (pne_terms *t : b->terms) { ncl += t->rec->n_clusters; nmem += t->part->n_members; }
-        const std::string key = "d" + std::to_string(dtype) + "_g" + std::to_string(n) + "_c" + std::to_string(ncl) +
-                                "_m" + std::to_string(nmem) + "_sm" + std::to_string(ctx->n_sm);
+        const std::string key = "v2_d" + std::to_string(dtype) + "_g" + std::to_string(n) + "_c" +
+                                std::to_string(ncl) + "_m" + std::to_string(nmem) + "_sm" + std::to_string(ctx->n_sm);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            b->wpb = it->second.first.first; b->bps = it->second.first.second; b->tuned_ms = it->second.second;
+            b->wpb = it->second.wpb; b->bps = it->second.bps; b->sched = it->second.sched; b->tuned_ms = it->second.ms;
         } else {
+            // every (warps per block, blocks per SM, work order) that fits,
+            // each run three times, the best of the last two kept
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0); cudaEventCreate(&e1);
             double best = 1e300;
             const int wcand[4] = {1, 2, 4, 8}, bcand[4] = {1, 2, 4, 8};
+            const int scand[2] = {PNE_SCHED_HANDLE, PNE_SCHED_LARGEST_FIRST};
             for (int wi = 0; wi < 4; ++wi) {
                 const int maxb = batch_max_blocks_per_sm(b->plan, wcand[wi]);
                 for (int bi = 0; bi < 4; ++bi) {
                     if (bcand[bi] > maxb) continue;
-                    double t_best = 1e300;
                     if ((st = batch_prepare(ctx, b->plan, wcand[wi], bcand[bi], s))) {
                         ctx->prof.on = prof; pne_batch_destroy(b); return st;
                     }
-                    for (int rep = 0; rep < 3; ++rep) {
-                        cudaEventRecord(e0, s);
-                        st = batch_enqueue(ctx, b->plan, wcand[wi], bcand[bi], s);
-                        cudaEventRecord(e1, s);
-                        if (st || cudaEventSynchronize(e1) != cudaSuccess) { ctx->prof.on = prof; pne_batch_destroy(b); return st ? st : PNE_ECUDA; }
-                        float ms = 0.f;
-                        cudaEventElapsedTime(&ms, e0, e1);
-                        if (rep > 0 && ms < t_best) t_best = ms;
+                    for (int sc : scand) {
+                        double t_best = 1e300;
+                        for (int rep = 0; rep < 3; ++rep) {
+                            cudaEventRecord(e0, s);
+                            st = batch_enqueue(ctx, b->plan, wcand[wi], bcand[bi], sc, s);
+                            cudaEventRecord(e1, s);
+                            if (st || cudaEventSynchronize(e1) != cudaSuccess) {
+                                ctx->prof.on = prof; pne_batch_destroy(b); return st ? st : PNE_ECUDA;
+                            }
+                            float ms = 0.f;
+                            cudaEventElapsedTime(&ms, e0, e1);
+                            if (rep > 0 && ms < t_best) t_best = ms;
+                        }
+                        if (t_best < best) { best = t_best; b->wpb = wcand[wi]; b->bps = bcand[bi]; b->sched = sc; }
                     }
-                    if (t_best < best) { best = t_best; b->wpb = wcand[wi]; b->bps = bcand[bi]; }
                 }
             }
             cudaEventDestroy(e0); cudaEventDestroy(e1);
             if (best >= 1e300) { ctx->prof.on = prof; pne_batch_destroy(b); set_error(ctx, PNE_EINVAL, "no launch shape fits"); return PNE_EINVAL; }
             b->tuned_ms = best;
-            tune_cache_store(key, b->wpb, b->bps, best);
+            tune_cache_store(key, {b->wpb, b->bps, b->sched, best});
         }
     }
     if ((st = batch_prepare(ctx, b->plan, b->wpb, b->bps, s))) { ctx->prof.on = prof; pne_batch_destroy(b); return st; }
@@ -1800,7 +1821,7 @@ pne_status pne_batch_create(pne_ctx *ctx, int32_t n, pne_terms *const *terms, pn
         cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { ctx->prof.on = prof; pne_batch_destroy(b); set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return PNE_ECUDA; }
-        st = batch_enqueue(ctx, b->plan, b->wpb, b->bps, b->cap);
+        st = batch_enqueue(ctx, b->plan, b->wpb, b->bps, b->sched, b->cap);
         e = cudaStreamEndCapture(b->cap, &b->graph);
         if (st || e != cudaSuccess) { ctx->prof.on = prof; pne_batch_destroy(b); if (!st) set_error(ctx, PNE_ECUDA, cudaGetErrorString(e)); return st ? st : PNE_ECUDA; }
         e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -1821,7 +1842,7 @@ pne_status pne_batch_run(pne_ctx *ctx, pne_batch *b, void *stream, pne_result *o
         ProfScope ps(ctx, s, "batch_graph");
         PNE_CUDA_TRY(ctx, cudaGraphLaunch(b->exec, s));
     } else {
-        pne_status st = batch_enqueue(ctx, b->plan, b->wpb, b->bps, s);
+        pne_status st = batch_enqueue(ctx, b->plan, b->wpb, b->bps, b->sched, s);
         if (st) return st;
     }
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
@@ -1857,6 +1878,13 @@ pne_status pne_batch_config(const pne_batch *b, int32_t *warps_per_block, int32_
     if (warps_per_block) *warps_per_block = b->wpb;
     if (blocks_per_sm) *blocks_per_sm = b->bps;
     if (tuned_ms) *tuned_ms = b->tuned_ms;
+    return PNE_OK;
+}
+
+pne_status pne_batch_schedule(const pne_batch *b, int32_t *schedule)
+{
+    if (!b || !schedule) return PNE_EINVAL;
+    *schedule = b->sched;
     return PNE_OK;
 }
 

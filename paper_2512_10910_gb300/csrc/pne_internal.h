@@ -463,7 +463,7 @@ struct BatchPlan;
 pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms, int dtype, cudaStream_t s,
                              BatchPlan **out);
 pne_status batch_prepare(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStream_t s);
-pne_status batch_enqueue(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, cudaStream_t s);
+pne_status batch_enqueue(pne_ctx *ctx, BatchPlan *bp, int wpb, int bps, int sched, cudaStream_t s);
 int batch_max_blocks_per_sm(BatchPlan *bp, int wpb);
 // releases the plan's buffers behind the work queued on `s` (its last stream)
 void batch_plan_destroy(pne_ctx *ctx, BatchPlan *bp, cudaStream_t s);

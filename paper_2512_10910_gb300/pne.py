@@ -24,7 +24,8 @@ __all__ = [
     "pne_contract_terms", "pne_sum", "pne_terms_n_results", "pne_terms_export",
     "pne_ctx_profile", "pne_ctx_profile_read", "pne_ctx_trace_read", "pne_terms_work", "pne_measure_fma_peak",
     "pne_bp_messages_noalloc", "pne_partition_update", "pne_batch_create", "pne_batch_run", "pne_batch_n_results", "pne_batch_config",
-    "pne_batch_destroy", "BatchOpts", "pne_server_create", "pne_server_submit", "pne_server_poll",
+    "pne_batch_schedule", "pne_batch_destroy", "BatchOpts", "PNE_SCHED_HANDLE", "PNE_SCHED_LARGEST_FIRST",
+    "pne_server_create", "pne_server_submit", "pne_server_poll",
     "pne_server_drain", "pne_server_stats", "pne_server_first_error", "pne_server_destroy", "ServerOpts", "RequestInfo",
     "Network", "PartitionOpts", "EnumOpts", "Result", "Context", "run", "network_struct",
     "pne_strip_expansion", "StripOpts", "StripResult", "PNE_STRIP_MAX_L", "PNE_STRIP_MAX_CHI",
@@ -90,7 +91,11 @@ class Result(ctypes.Structure):
 
 
 class BatchOpts(ctypes.Structure):
-    _fields_ = [("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+    _fields_ = [("warps_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("schedule", ctypes.c_int32)]
+
+
+PNE_SCHED_HANDLE, PNE_SCHED_LARGEST_FIRST = 0, 1
 
 
 class ServerOpts(ctypes.Structure):
@@ -245,6 +250,8 @@ def load_library():
     lib.pne_batch_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_double)]
     lib.pne_batch_config.restype = ctypes.c_int
+    lib.pne_batch_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.pne_batch_schedule.restype = ctypes.c_int
     lib.pne_batch_destroy.argtypes = [vp]
     lib.pne_batch_destroy.restype = None
     lib.pne_server_create.argtypes = [vp, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
@@ -284,7 +291,7 @@ def exported_symbols() -> list:
              "pne_terms_export",
              "pne_ctx_profile", "pne_ctx_profile_read", "pne_ctx_trace_read", "pne_terms_work", "pne_measure_fma_peak",
              "pne_bp_messages_noalloc", "pne_partition_update", "pne_batch_create", "pne_batch_run",
-             "pne_batch_n_results", "pne_batch_config", "pne_batch_destroy", "pne_server_create",
+             "pne_batch_n_results", "pne_batch_config", "pne_batch_schedule", "pne_batch_destroy", "pne_server_create",
              "pne_server_submit", "pne_server_poll", "pne_server_drain", "pne_server_stats", "pne_server_first_error",
              "pne_server_destroy", "pne_weight_passing", "pne_weights_read", "pne_weights_destroy",
              "pne_rank_r_expand", "pne_strip_expansion", "pne_dense_gemm", "pne_grid_contract",
@@ -541,6 +548,12 @@ def pne_batch_config(b):
     w, k, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     _check(load_library().pne_batch_config(b, ctypes.byref(w), ctypes.byref(k), ctypes.byref(ms)))
     return int(w.value), int(k.value), float(ms.value)
+
+
+def pne_batch_schedule(b) -> int:
+    v = ctypes.c_int32()
+    _check(load_library().pne_batch_schedule(b, ctypes.byref(v)))
+    return int(v.value)
 
 
 def pne_batch_destroy(b):

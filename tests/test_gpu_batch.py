@@ -63,6 +63,7 @@ def test_batch_matches_per_network_path_and_oracle(ctx, dtype):
         got = pne.pne_batch_run(ctx.h, b)
         w, k, ms = pne.pne_batch_config(b)
         assert w in (1, 2, 4, 8) and k >= 1 and ms > 0
+        assert pne.pne_batch_schedule(b) in (pne.PNE_SCHED_HANDLE, pne.PNE_SCHED_LARGEST_FIRST)
         pne.pne_batch_destroy(b)
         r = 0
         for (g, nets), t in zip(groups, terms):
@@ -88,8 +89,12 @@ def test_batch_results_identical_across_launch_shapes_and_graph(ctx):
     parts, terms, keep = _make(ctx, groups)
     try:
         runs = []
-        for opts in (pne.BatchOpts(1, 1, 1), pne.BatchOpts(2, 1, 1), pne.BatchOpts(1, 2, 0), None):
+        for opts in (pne.BatchOpts(1, 1, 1), pne.BatchOpts(2, 1, 1), pne.BatchOpts(1, 2, 0), None,
+                     pne.BatchOpts(2, 1, 1, pne.PNE_SCHED_LARGEST_FIRST),
+                     pne.BatchOpts(1, 2, 0, pne.PNE_SCHED_LARGEST_FIRST)):
             b = pne.pne_batch_create(ctx.h, terms, pne.PNE_F64, opts)
+            if opts is not None:
+                assert pne.pne_batch_schedule(b) == opts.schedule
             runs.append([(r["log_abs"], tuple(r["c"])) for r in pne.pne_batch_run(ctx.h, b)])
             runs.append([(r["log_abs"], tuple(r["c"])) for r in pne.pne_batch_run(ctx.h, b)])   # replay
             pne.pne_batch_destroy(b)
@@ -105,6 +110,9 @@ def test_batch_rejects_a_shape_that_does_not_fit(ctx):
     try:
         with pytest.raises(pne.PneError) as ei:
             pne.pne_batch_create(ctx.h, terms, pne.PNE_F64, pne.BatchOpts(32, 8, 1))
+        assert ei.value.status == pne.PNE_EINVAL
+        with pytest.raises(pne.PneError) as ei:
+            pne.pne_batch_create(ctx.h, terms, pne.PNE_F64, pne.BatchOpts(1, 1, 1, 7))
         assert ei.value.status == pne.PNE_EINVAL
     finally:
         _free(parts, terms)

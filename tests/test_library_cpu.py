@@ -172,3 +172,21 @@ def test_strip_struct_layouts_match_the_header(tmp_path):
     want = [ctypes.sizeof(O), ctypes.sizeof(R), R.log_z.offset, R.sign_z.offset, R.messages.offset,
             R.eig_change.offset, R.iters.offset, O.arithmetic.offset]
     assert got == want
+
+
+def test_batch_opts_layout_matches_the_header(tmp_path):
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "lay.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pne.h"\nint main(void){\n'
+                   'printf("%zu %zu %d %d\\n", sizeof(pne_batch_opts), offsetof(pne_batch_opts, schedule),\n'
+                   ' PNE_SCHED_HANDLE, PNE_SCHED_LARGEST_FIRST);\nreturn 0;}\n')
+    exe = tmp_path / "lay"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    B = pne.BatchOpts
+    assert got == [ctypes.sizeof(B), B.schedule.offset, pne.PNE_SCHED_HANDLE, pne.PNE_SCHED_LARGEST_FIRST]
