@@ -1704,39 +1704,46 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
             for (int i = 0; i < k && all4; ++i) all4 = g.bond_dim[g.site_bonds[g.site_ptr[v] + i]] == 4;
             n_pair += all4 ? 1 : 0;
         }
-        const int task = 2 * n_pair >= g.n_sites ? 2 : 1;
-        const int kBpClWarps = task == 2 ? ClusterForm<2>::kWarps : ClusterForm<1>::kWarps;
-        const void *cl_kernel = task == 2 ? (const void *)bp_ff_cluster_kernel<2> : (const void *)bp_ff_cluster_kernel<1>;
-        int CL = 1;
-        while (CL * kBpClWarps * task < max_color && CL < 16) CL *= 2;
-        bool cluster_ok = g.n_colors > 0 && max_color <= CL * kBpClWarps * task * 4;
         // the cluster form's warp scratch also holds the pair form's (128 ff)
         const int per_warp_cl = std::max(per_warp, 128);
+        int slot_ff = 0;
+        for (int v = 0; v < g.n_sites; ++v)
+            slot_ff = std::max<int>(slot_ff, (int)(g.tens_off[v + 1] - g.tens_off[v]));
+        slot_ff = (slot_ff + 1) & ~1;
+        // per slot: the tensor, the current messages [4][4], the record
+        const size_t slot_bytes = (size_t)slot_ff * sizeof(ff) + 16 * sizeof(ff) + kSlotMeta * sizeof(int);
+        // slots per warp for `task` sites per warp task, `warps` warps per
+        // block and a cluster of cl blocks (a warp takes ceil(ceil(nc / task) /
+        // (cl warps)) tasks of each colour), kept only while the block's shared
+        // memory stays within kBpTensorSmem
+        auto slots_of = [&](int task_, int warps, int cl) {
+            int n = 0;
+            for (int c = 0; c < g.n_colors; ++c) {
+                const int tasks = (g.color_ptr[c + 1] - g.color_ptr[c] + task_ - 1) / task_;
+                n += task_ * ((tasks + cl * warps - 1) / (cl * warps));
+            }
+            const size_t b = (size_t)per_warp_cl * warps * sizeof(double) + (size_t)warps * n * slot_bytes;
+            return b <= kBpTensorSmem ? n : 0;
+        };
+        auto cluster_for = [&](int task_, int warps) {
+            int cl = 1;
+            while (cl * warps * task_ < max_color && cl < 16) cl *= 2;
+            return cl;
+        };
+        // the pair form needs the site tensors in shared memory
+        const int task = (2 * n_pair >= g.n_sites &&
+                          slots_of(2, ClusterForm<2>::kWarps, cluster_for(2, ClusterForm<2>::kWarps)) > 0) ? 2 : 1;
+        const int kBpClWarps = task == 2 ? ClusterForm<2>::kWarps : ClusterForm<1>::kWarps;
+        const void *cl_kernel = task == 2 ? (const void *)bp_ff_cluster_kernel<2> : (const void *)bp_ff_cluster_kernel<1>;
+        int CL = cluster_for(task, kBpClWarps);
+        bool cluster_ok = g.n_colors > 0 && max_color <= CL * kBpClWarps * task * 4;
         const size_t smem_cl = (size_t)per_warp_cl * kBpClWarps * sizeof(double);
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute cattr[1];
         fp.t_slots = 0;
         fp.slot_ff = 0;
         if (cluster_ok) {
-            // slots per warp for a cluster of cl blocks (a warp takes
-            // ceil(ceil(nc / task) / warps) tasks of `task` sites of each
-            // colour), kept only while the block's shared memory stays within
-            // kBpTensorSmem
-            int slot_ff = 0;
-            for (int v = 0; v < g.n_sites; ++v)
-                slot_ff = std::max<int>(slot_ff, (int)(g.tens_off[v + 1] - g.tens_off[v]));
-            slot_ff = (slot_ff + 1) & ~1;
-            // per slot: the tensor, the current messages [4][4], the record
-            const size_t slot_bytes = (size_t)slot_ff * sizeof(ff) + 16 * sizeof(ff) + kSlotMeta * sizeof(int);
-            auto slots_for = [&](int cl) {
-                int n = 0;
-                for (int c = 0; c < g.n_colors; ++c) {
-                    const int tasks = (g.color_ptr[c + 1] - g.color_ptr[c] + task - 1) / task;
-                    n += task * ((tasks + cl * kBpClWarps - 1) / (cl * kBpClWarps));
-                }
-                const size_t b = (size_t)kBpClWarps * n * slot_bytes;
-                return smem_cl + b <= kBpTensorSmem ? n : 0;
-            };
+            auto slots_for = [&](int cl) { return slots_of(task, kBpClWarps, cl); };
             auto smem_for = [&](int cl) { return smem_cl + (size_t)kBpClWarps * slots_for(cl) * slot_bytes; };
             cfg.blockDim = dim3(kBpClWarps * 32);
             cfg.stream = s;
