@@ -37,7 +37,13 @@ namespace {
 
 constexpr int kBpWarps = 8;              // warps per block in the BP kernels
 // warps per block of the cluster form: 4 with two sites per warp task, 8 with one
-template <int TASK> struct ClusterForm { static constexpr int kWarps = TASK == 2 ? 4 : 8; };
+template <int TASK> struct ClusterForm {
+    static constexpr int kWarps = TASK == 2 ? 4 : 8;
+    // resident blocks per SM the register budget allows: 96 registers for the
+    // pair form (a few spilled) leave room on every SM for the enumeration's
+    // kernels that run beside the sweeps; at 128 the step was 1% slower
+    static constexpr int kMinBlocks = TASK == 2 ? 5 : 4;
+};
 // shared memory per block up to which the cluster form keeps its warps' site
 // tensors resident (four blocks per SM still fit in 228 KB)
 constexpr size_t kBpTensorSmem = 48 * 1024;
@@ -1046,7 +1052,7 @@ __global__ void __launch_bounds__(kBpWarps * 32, 4) bp_ff_kernel(BPFFParams p)
 // slots (slot_ff entries each, 16-byte aligned) and read from shared memory
 // afterwards; the pair form needs them there.
 template <int TASK>
-__global__ void __launch_bounds__(ClusterForm<TASK>::kWarps * 32, 4) bp_ff_cluster_kernel(BPFFParams p)
+__global__ void __launch_bounds__(ClusterForm<TASK>::kWarps * 32, ClusterForm<TASK>::kMinBlocks) bp_ff_cluster_kernel(BPFFParams p)
 {
     constexpr int kBpClWarps = ClusterForm<TASK>::kWarps;
     namespace cg = cooperative_groups;
