@@ -450,6 +450,9 @@ struct SumParams {
     const int32_t *lvl_idx[16];
     int lvl_m[16];
     double *partial;          // [members][n_desc][2]
+    unsigned int *done;       // [members] finished blocks (zero between calls)
+    double *out;              // [members][K+1][2]
+    int K;
 };
 
 constexpr int kSumThreads = 256;
@@ -491,10 +494,29 @@ __global__ void __launch_bounds__(kSumThreads) term_sum_kernel(SumParams P)
         }
         __syncthreads();
     }
+    // the member's last block to finish reduces its partials, per order in
+    // descriptor order (the same sums as finalize_kernel), and re-arms the counter
+    __shared__ int last;
     if (threadIdx.x == 0) {
         P.partial[((int64_t)b * P.n_desc + di) * 2] = sh[0][0];
         P.partial[((int64_t)b * P.n_desc + di) * 2 + 1] = sh[1][0];
+        __threadfence();
+        last = atomicAdd(P.done + b, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int k = threadIdx.x; k <= P.K; k += blockDim.x) {
+        double ss = 0.0, aa = 0.0;
+        for (int d2 = 0; d2 < P.n_desc; ++d2)
+            if (P.desc[d2].order == k) {
+                ss += __ldcg(P.partial + ((int64_t)b * P.n_desc + d2) * 2);
+                aa += __ldcg(P.partial + ((int64_t)b * P.n_desc + d2) * 2 + 1);
+            }
+        P.out[((int64_t)b * (P.K + 1) + k) * 2] = ss;
+        P.out[((int64_t)b * (P.K + 1) + k) * 2 + 1] = aa;
+    }
+    if (threadIdx.x == 0) P.done[b] = 0u;
 }
 
 // per (member, order): partials of that order in descriptor order
@@ -1526,8 +1548,49 @@ pne_status launch_contract(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s
     return PNE_OK;
 }
 
+// Small device regions gathered behind the sums' results, so that one
+// device-to-host copy brings everything the host reads after the sums.
+struct PackSegs {
+    const char *src[4];
+    int64_t off[4], bytes[4];
+    int n;
+};
+__global__ void pack_segments_kernel(PackSegs P, char *dst)
+{
+    for (int q = 0; q < P.n; ++q)
+        for (int64_t i = threadIdx.x; i < P.bytes[q]; i += blockDim.x) dst[P.off[q] + i] = P.src[q][i];
+}
+
+// per order k: the single clusters of size k, then every tuple level's terms
+// of order k, in chunks of kSumChunk (the sum order of the per-order results)
+std::vector<SumDesc> sum_descs(const EnumRecord &rec)
+{
+    std::vector<SumDesc> desc;
+    const int K = rec.K;
+    for (int k = 1; k <= K; ++k)
+        for (int64_t b0 = rec.size_start[k]; b0 < rec.size_start[k + 1]; b0 += kSumChunk)
+            desc.push_back({0, k, b0, std::min<int64_t>(b0 + kSumChunk, rec.size_start[k + 1])});
+    for (size_t l = 0; l < rec.levels.size(); ++l)
+        for (int k = 0; k <= K; ++k)
+            for (int64_t b0 = rec.levels[l].order_start[k]; b0 < rec.levels[l].order_start[k + 1]; b0 += kSumChunk)
+                desc.push_back({(int32_t)l + 1, k, b0, std::min<int64_t>(b0 + kSumChunk, rec.levels[l].order_start[k + 1])});
+    return desc;
+}
+
+pne_status sum_desc_prepare(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s)
+{
+    const std::vector<SumDesc> desc = sum_descs(rec);
+    pne_status st;
+    if (!desc.empty()) {
+        if ((st = dev_alloc(ctx, rec.sum_desc, desc.size() * sizeof(SumDesc), s))) return st;
+        if ((st = upload(ctx, rec.sum_desc.ptr, desc.data(), desc.size() * sizeof(SumDesc), s))) return st;
+    }
+    rec.n_sum_desc = (int)desc.size();
+    return PNE_OK;
+}
+
 pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, std::vector<double> &c,
-                       std::vector<double> &abs_c, int32_t *h_status)
+                       std::vector<double> &abs_c, int32_t *h_status, const std::vector<D2HCopy> &extra)
 {
     const pne_partition *p = t->part;
     const int K = t->K, B = p->n_members;
@@ -1537,30 +1600,51 @@ pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, std::ve
         std::vector<double> buf((size_t)B * (K + 1) * 2);
         PNE_CUDA_TRY(ctx, cudaMemcpyAsync(buf.data(), t->sums.ptr, buf.size() * 8, cudaMemcpyDeviceToHost, s));
         PNE_CUDA_TRY(ctx, cudaMemcpyAsync(h_status, t->status.ptr, 4, cudaMemcpyDeviceToHost, s));
+        for (const D2HCopy &x : extra)
+            PNE_CUDA_TRY(ctx, cudaMemcpyAsync(x.dst, x.src, x.bytes, cudaMemcpyDeviceToHost, s));
         PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         c.assign((size_t)B * (K + 1), 0.0); abs_c.assign((size_t)B * (K + 1), 0.0);
         for (size_t i = 0; i < c.size(); ++i) { c[i] = buf[2 * i]; abs_c[i] = buf[2 * i + 1]; }
         return PNE_OK;
     }
     const EnumRecord &rec = *t->rec;
-    for (int k = 1; k <= K; ++k)
-        for (int64_t b0 = rec.size_start[k]; b0 < rec.size_start[k + 1]; b0 += kSumChunk)
-            desc.push_back({0, k, b0, std::min<int64_t>(b0 + kSumChunk, rec.size_start[k + 1])});
     if (rec.levels.size() > 16) { set_error(ctx, PNE_EOVERFLOW, "too many tuple levels"); return PNE_EOVERFLOW; }
-    for (size_t l = 0; l < rec.levels.size(); ++l)
-        for (int k = 0; k <= K; ++k)
-            for (int64_t b0 = rec.levels[l].order_start[k]; b0 < rec.levels[l].order_start[k + 1]; b0 += kSumChunk)
-                desc.push_back({(int32_t)l + 1, k, b0, std::min<int64_t>(b0 + kSumChunk, rec.levels[l].order_start[k + 1])});
-    const int nd = (int)desc.size();
+    // the descriptors depend only on the record: built with it when it was
+    // enumerated (already on the device), else here
     DevBuf dd, part, out;
     pne_status st;
-    if ((st = dev_alloc(ctx, dd, std::max(nd, 1) * sizeof(SumDesc), s))) return st;
+    const SumDesc *d_desc = (const SumDesc *)rec.sum_desc.ptr;
+    int nd = rec.n_sum_desc;
+    if (nd < 0) {
+        desc = sum_descs(rec);
+        nd = (int)desc.size();
+        if ((st = dev_alloc(ctx, dd, std::max(nd, 1) * sizeof(SumDesc), s))) return st;
+        if (nd > 0 && (st = upload(ctx, dd.ptr, desc.data(), nd * sizeof(SumDesc), s))) return st;
+        d_desc = (const SumDesc *)dd.ptr;
+    }
+    // out: the results [B][K+1][2], then the status word and the extra
+    // regions, each at an 8-byte aligned offset
+    const int64_t res_bytes = (int64_t)B * (K + 1) * 16;
+    PackSegs segs{};
+    int64_t tail = res_bytes;
+    if (extra.size() > 3) { set_error(ctx, PNE_EINVAL, "too many read-back regions"); return PNE_EINVAL; }
+    segs.src[0] = (const char *)t->status.ptr; segs.off[0] = tail; segs.bytes[0] = 4; tail += 8;
+    segs.n = 1;
+    for (const D2HCopy &x : extra) {
+        segs.src[segs.n] = (const char *)x.src; segs.off[segs.n] = tail; segs.bytes[segs.n] = (int64_t)x.bytes;
+        tail += ((int64_t)x.bytes + 7) & ~int64_t(7);
+        ++segs.n;
+    }
     if ((st = dev_alloc(ctx, part, (size_t)B * std::max(nd, 1) * 16, s))) return st;
-    if ((st = dev_alloc(ctx, out, (size_t)B * (K + 1) * 16, s))) return st;
+    if ((st = dev_alloc(ctx, out, (size_t)tail, s))) return st;
+    if (nd > 0 && !t->sum_done.ptr) {
+        pne_terms *tm = const_cast<pne_terms *>(t);
+        if ((st = dev_alloc(ctx, tm->sum_done, (size_t)B * 4, s))) return st;
+        PNE_CUDA_TRY(ctx, cudaMemsetAsync(tm->sum_done.ptr, 0, (size_t)B * 4, s));
+    }
     if (nd > 0) {
-        if ((st = upload(ctx, dd.ptr, desc.data(), nd * sizeof(SumDesc), s))) return st;
         SumParams sp;
-        sp.desc = (const SumDesc *)dd.ptr; sp.n_desc = nd; sp.n_members = B;
+        sp.desc = d_desc; sp.n_desc = nd; sp.n_members = B;
         sp.n_clusters = (int64_t)rec.n_clusters;
         sp.w = (const double *)t->w.ptr; sp.nzc = (const int32_t *)t->nzc.ptr;
         sp.vac = (const double *)p->vac.ptr;
@@ -1570,33 +1654,31 @@ pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, std::ve
             sp.lvl_m[l] = rec.levels[l].m;
         }
         sp.partial = (double *)part.ptr;
+        sp.done = (unsigned int *)t->sum_done.ptr; sp.out = (double *)out.ptr; sp.K = K;
         if (B > 65535) { set_error(ctx, PNE_EINVAL, "too many tensor sets"); return PNE_EINVAL; }
         {
             ProfScope ps__(ctx, s, "term_sum");
             term_sum_kernel<<<dim3(nd, B), kSumThreads, 0, s>>>(sp);
         }
         PNE_CUDA_TRY(ctx, cudaGetLastError());
-        {
-            ProfScope ps__(ctx, s, "term_sum");
-            finalize_kernel<<<grid_for((int64_t)B * (K + 1), 128, ctx->n_sm), 128, 0, s>>>(
-            (const double *)part.ptr, (const SumDesc *)dd.ptr, nd, B, K, (double *)out.ptr);
-        }
-        PNE_CUDA_TRY(ctx, cudaGetLastError());
     } else {
         PNE_CUDA_TRY(ctx, cudaMemsetAsync(out.ptr, 0, (size_t)B * (K + 1) * 16, s));
     }
-    std::vector<double> buf((size_t)B * (K + 1) * 2 + 1);
-    double *hb = (double *)pinned_slot(1, buf.size() * 8);
+    pack_segments_kernel<<<1, 256, 0, s>>>(segs, (char *)out.ptr);
+    PNE_CUDA_TRY(ctx, cudaGetLastError());
+    std::vector<double> buf((size_t)tail / 8);
+    double *hb = (double *)pinned_slot(1, (size_t)tail);
     double *dst = hb ? hb : buf.data();
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dst, out.ptr, (buf.size() - 1) * 8, cudaMemcpyDeviceToHost, s));
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dst + buf.size() - 1, t->status.ptr, 4, cudaMemcpyDeviceToHost, s));
+    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dst, out.ptr, (size_t)tail, cudaMemcpyDeviceToHost, s));
     dev_free(ctx, dd, s); dev_free(ctx, part, s); dev_free(ctx, out, s);
     {
         HostScope hw__(ctx, "sync_sum");
         PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     }
-    if (hb) std::memcpy(buf.data(), hb, buf.size() * 8);
-    std::memcpy(h_status, buf.data() + buf.size() - 1, 4);
+    if (hb) std::memcpy(buf.data(), hb, (size_t)tail);
+    const char *hbytes = (const char *)buf.data();
+    std::memcpy(h_status, hbytes + segs.off[0], 4);
+    for (size_t q = 0; q < extra.size(); ++q) std::memcpy(extra[q].dst, hbytes + segs.off[q + 1], extra[q].bytes);
     c.assign((size_t)B * (K + 1), 0.0); abs_c.assign((size_t)B * (K + 1), 0.0);
     for (size_t i = 0; i < c.size(); ++i) { c[i] = buf[2 * i]; abs_c[i] = buf[2 * i + 1]; }
     return PNE_OK;

@@ -299,6 +299,7 @@ EnumRecord::~EnumRecord()
     dev_free(ctx, step_off, rs);
     dev_free(ctx, step_site, rs);
     dev_free(ctx, vgeo.storage, rs);
+    dev_free(ctx, sum_desc, rs);
 }
 
 namespace {
@@ -1120,6 +1121,7 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
                     std::lock_guard<std::mutex> lk(ctx->pool_mu);
                     ctx->stream_pool.push_back(ls);
                 }
+                if ((st = sum_desc_prepare(ctx, *rec, s))) return st;
             }
         }
         if (opts->use_cache) {
@@ -1349,6 +1351,7 @@ void pne_terms_destroy(pne_terms *t)
     dev_free(t->ctx, t->nzc, s);
     dev_free(t->ctx, t->sums, s);
     dev_free(t->ctx, t->status, s);
+    dev_free(t->ctx, t->sum_done, s);
     delete t;
 }
 
@@ -1452,9 +1455,9 @@ pne_status pne_sum(pne_ctx *ctx, const pne_terms *t, void *stream, pne_result *o
     std::vector<char> hb(vbytes + rbytes);
     char *hp = (char *)pinned_slot(2, vbytes + rbytes);
     char *dst = hp ? hp : hb.data();
-    PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dst, p->vac.ptr, vbytes, cudaMemcpyDeviceToHost, s));
-    if (rbytes) PNE_CUDA_TRY(ctx, cudaMemcpyAsync(dst + vbytes, p->rec_dev.ptr, rbytes, cudaMemcpyDeviceToHost, s));
-    pne_status st = launch_sums(ctx, t, s, c, a, &status);
+    std::vector<D2HCopy> extra{{dst, p->vac.ptr, vbytes}};
+    if (rbytes) extra.push_back({dst + vbytes, p->rec_dev.ptr, rbytes});
+    pne_status st = launch_sums(ctx, t, s, c, a, &status, extra);
     if (st) return st;
     if (hp) std::memcpy(hb.data(), hp, vbytes + rbytes);
     const double *vac = (const double *)hb.data();

@@ -82,6 +82,9 @@ int64_t *pinned_i64(pne_ctx *ctx, size_t n);
 // after every copy queued out of it has completed.  Not for use inside stream
 // capture (a captured copy would read the region when replayed).
 pne_status upload(pne_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s);
+struct EnumRecord;
+// the record's term-sum descriptors uploaded on s (LOOP mode records)
+pne_status sum_desc_prepare(pne_ctx *ctx, EnumRecord &rec, cudaStream_t s);
 // Per-thread pinned readback area `slot` of at least `bytes` (nullptr if pinned
 // memory is unavailable); read after synchronising the stream of the copies.
 // Slots: 0 partition records, 1 sums, 2 vacuum records, 3 shape records.
@@ -339,6 +342,10 @@ struct EnumRecord {
     bool comb = false;
     Geometry vgeo;
     std::vector<uint64_t> empty_by_order;       // [K+1] sub-networks with no kept bond
+    // the term-sum descriptors (per order, chunks of clusters and of each tuple
+    // level), built on the device with the record; -1: not built
+    DevBuf sum_desc;
+    int n_sum_desc = -1;
     ~EnumRecord();
 };
 
@@ -357,6 +364,7 @@ struct pne_terms {
     bool contracted = false;
     cudaStream_t last_stream = nullptr;  // stream of the last call that used the handle
     pne::DevBuf Mf, Mf32, Mf16;          // COMB: full-range blocks of the virtual geometry
+    pne::DevBuf sum_done;                // [n_members] uint32 blocks finished in the term sums (zero between calls)
 };
 
 namespace pne {
@@ -426,8 +434,16 @@ void tuples_abort(pne_ctx *ctx, TuplePrep &tp, cudaStream_t s);
 
 // contraction and sums (contract.cu)
 pne_status launch_contract(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s);
+// a device-to-host copy queued with the sums' read-back (after their kernels,
+// so that it does not sit between the contraction and the sums on the stream)
+struct D2HCopy {
+    void *dst;
+    const void *src;
+    size_t bytes;
+};
 pne_status launch_sums(pne_ctx *ctx, const pne_terms *t, cudaStream_t s,
-                       std::vector<double> &c, std::vector<double> &abs_c, int32_t *h_status);
+                       std::vector<double> &c, std::vector<double> &abs_c, int32_t *h_status,
+                       const std::vector<D2HCopy> &extra = {});
 pne_status launch_all_mode(pne_ctx *ctx, pne_terms *t, int dtype, cudaStream_t s);
 pne_status launch_plan_work(pne_ctx *ctx, const pne_terms *t, cudaStream_t s, uint64_t *fma);
 // device tables of a geometry built from its bond_site/bond_dim/site_ptr/site_bonds (pne_api.cu)
