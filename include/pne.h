@@ -125,6 +125,20 @@ typedef struct {
                             PNE_ENOCONV / PNE_EDEGENERATE / PNE_ETIMEOUT then,
                             after writing every result; non-converged sets show
                             bp_iters == 0) */
+    /* User projectors instead of BP (Eq. A2: P_b may be any projector; the
+     * identities of Eq. A3-A4 hold for every choice).  With
+     * use_user_projectors = 1, closed bond b = (s0, s1) (s0 = bond_site[b][0])
+     * takes the rank-1 projector
+     *     P_b[a0][a1] = u_b[a0] v_b[a1] / (u_b . v_b),
+     * a0 the index on s0's side, a1 on s1's, and Q_b = I - P_b.  user_u and
+     * user_v hold, for every tensor set and then every closed bond in id order,
+     * bond_dim[b] FP64 entries each ([n_batch][sum of closed bond dimensions],
+     * host memory, read during the call; open bonds take none).  No sweeps run
+     * (bp_iters = 0, residual 0, never PNE_ENOCONV); tol, max_iter and damping
+     * are ignored; |u_b . v_b| < 1e-300 or u_b = 0 gives PNE_EDEGENERATE. */
+    int32_t use_user_projectors;
+    const double *user_u;
+    const double *user_v;
 } pne_partition_opts;
 
 typedef struct {

@@ -1901,6 +1901,79 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
     return PNE_OK;
 }
 
+// user projectors: closed bond b = (s0, s1) takes u_b as the message on s1's
+// leg (the vector that arrives at s0) and v_b on s0's leg, which is the rank-1
+// projector P_b = u_b v_b^T / (u_b . v_b) of the gauge below (buffer 0)
+__global__ void user_proj_kernel(const double *u, const double *v, const int64_t *off, int64_t per_set, int n_sets,
+                                 int n_bonds, int n_legs, const int32_t *bond_site, const int32_t *bond_dim,
+                                 const int32_t *bond_leg, const int32_t *site_ptr, double *msg)
+{
+    const int64_t total = (int64_t)n_sets * n_bonds * kMsgStride;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(i % kMsgStride);
+        const int b = (int)((i / kMsgStride) % n_bonds), set = (int)(i / ((int64_t)kMsgStride * n_bonds));
+        const int s0 = bond_site[2 * b], s1 = bond_site[2 * b + 1];
+        if (s1 < 0 || a >= bond_dim[b]) continue;
+        double *base = msg + (int64_t)set * n_legs * kMsgStride;
+        const int64_t src = (int64_t)set * per_set + off[b] + a;
+        base[(int64_t)(site_ptr[s1] + bond_leg[2 * b + 1]) * kMsgStride + a] = u[src];
+        base[(int64_t)(site_ptr[s0] + bond_leg[2 * b]) * kMsgStride + a] = v[src];
+    }
+}
+
+pne_status launch_user_projectors(pne_ctx *ctx, pne_partition *p, const double *user_u, const double *user_v,
+                                  cudaStream_t s, void *rec, cudaMemcpyKind rec_kind)
+{
+    HostScope hs__(ctx, "part_user_proj");
+    const Geometry &g = p->geo->full;
+    const int n_sets = p->n_sets;
+    std::vector<int64_t> off(std::max(g.n_bonds, 1), -1);
+    int64_t per_set = 0;
+    for (int b = 0; b < g.n_bonds; ++b)
+        if (g.bond_site[2 * b + 1] >= 0) { off[b] = per_set; per_set += g.bond_dim[b]; }
+    // scratch: the record (residuals [n_sets] f64, flags[4] i32, sweeps [n_sets]
+    // i32, all zero but the gauge's degenerate flag), final buffers [n_sets]
+    // i32 (0), then the bond offsets and the two vector arrays
+    const size_t rec_bytes = (size_t)n_sets * 12 + 16;
+    const size_t head = ((rec_bytes + (size_t)n_sets * 4) + 255) & ~size_t(255);
+    const size_t off_bytes = ((size_t)off.size() * 8 + 255) & ~size_t(255);
+    const size_t vec_bytes = (size_t)n_sets * per_set * 8;
+    DevBuf scratch;
+    pne_status st = dev_alloc(ctx, scratch, head + off_bytes + 2 * std::max<size_t>(vec_bytes, 8), s);
+    if (st) return st;
+    char *base = (char *)scratch.ptr;
+    int32_t *flags = (int32_t *)(base + (size_t)n_sets * 8);
+    int32_t *finalb = (int32_t *)(base + rec_bytes);
+    int64_t *d_off = (int64_t *)(base + head);
+    double *d_u = (double *)(base + head + off_bytes), *d_v = d_u + std::max<int64_t>((int64_t)n_sets * per_set, 1);
+    auto fail = [&](pne_status e) { dev_free(ctx, scratch, s); return e; };
+    if (cudaMemsetAsync(base, 0, head, s) != cudaSuccess) return fail(PNE_ECUDA);
+    if ((st = upload(ctx, d_off, off.data(), off.size() * 8, s))) return fail(st);
+    if (vec_bytes && ((st = upload(ctx, d_u, user_u, vec_bytes, s)) || (st = upload(ctx, d_v, user_v, vec_bytes, s))))
+        return fail(st);
+    double *msg = (double *)p->msg.ptr;
+    {
+        ProfScope ps(ctx, s, "bp_init");
+        user_proj_kernel<<<grid_for((int64_t)n_sets * g.n_bonds * kMsgStride, 256, ctx->n_sm), 256, 0, s>>>(
+            d_u, d_v, d_off, per_set, n_sets, g.n_bonds, g.n_legs, g.d_bond_site, g.d_bond_dim, g.d_bond_leg,
+            g.d_site_ptr, msg);
+    }
+    if (cudaGetLastError() != cudaSuccess) return fail(PNE_ECUDA);
+    GaugeParams gp;
+    gp.n_sets = n_sets; gp.n_bonds = g.n_bonds; gp.n_legs = g.n_legs;
+    gp.bond_site = g.d_bond_site; gp.bond_dim = g.d_bond_dim; gp.bond_leg = g.d_bond_leg;
+    gp.site_ptr = g.d_site_ptr; gp.msg = msg; gp.final_buf = finalb;
+    gp.gauge = (double *)p->gauge.ptr; gp.flags = flags;
+    {
+        ProfScope ps(ctx, s, "gauge");
+        gauge_kernel<<<grid_for((int64_t)n_sets * g.n_bonds, 128, ctx->n_sm), 128, 0, s>>>(gp);
+    }
+    if (cudaGetLastError() != cudaSuccess) return fail(PNE_ECUDA);
+    if (cudaMemcpyAsync(rec, base, rec_bytes, rec_kind, s) != cudaSuccess) return fail(PNE_ECUDA);
+    dev_free(ctx, scratch, s);
+    return PNE_OK;
+}
+
 pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t *h_flag)
 {
     HostScope hs__(ctx, "part_gauge");

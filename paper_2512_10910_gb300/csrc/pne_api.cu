@@ -741,7 +741,7 @@ pne_status partition_record(pne_ctx *ctx, pne_partition *p, const char *rec)
     p->rec_pending = false;
     if (flags[0] || flags[2]) { set_error(ctx, PNE_ETIMEOUT, "grid barrier timed out in BP"); return PNE_ETIMEOUT; }
     if (flags[1] || flags[3]) { set_error(ctx, PNE_EDEGENERATE, "zero message or zero message overlap"); return PNE_EDEGENERATE; }
-    for (size_t b = 0; b < B; ++b)
+    for (size_t b = 0; b < B && !p->user_proj; ++b)
         if (p->bp_iters[b] == 0) {
             set_error(ctx, PNE_ENOCONV, "BP did not converge for tensor set " + std::to_string(b));
             return PNE_ENOCONV;
@@ -944,10 +944,22 @@ pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_p
     const int arith = opts ? opts->arithmetic : 0;
     if (arith != 0 && arith != 1) { pne_partition_destroy(p); set_error(ctx, PNE_EINVAL, "arithmetic must be 0 or 1"); return PNE_EINVAL; }
     p->arithmetic = arith;
+    const bool user = opts && opts->use_user_projectors;
+    if (user && (!opts->user_u || !opts->user_v)) {
+        pne_partition_destroy(p);
+        set_error(ctx, PNE_EINVAL, "use_user_projectors needs user_u and user_v");
+        return PNE_EINVAL;
+    }
+    p->user_proj = user;
+    // the projectors: BP sweeps to a fixed point, or the caller's vectors
+    auto projectors = [&](void *rec, cudaMemcpyKind kind) {
+        return user ? launch_user_projectors(ctx, p, opts->user_u, opts->user_v, s, rec, kind)
+                    : launch_bp(ctx, p, tol, max_iter, damping, s, rec, arith, kind);
+    };
     if (opts && opts->async_status) {
         // deferred record: kept on the device, read by the next synchronising call
         char *rd = (char *)p->rec_dev.ptr;
-        if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, rd, arith, cudaMemcpyDeviceToDevice)) ||
+        if ((st = projectors(rd, cudaMemcpyDeviceToDevice)) ||
             (st = launch_gauge(ctx, p, s, nullptr))) {
             pne_partition_destroy(p);
             return st ? st : PNE_ECUDA;
@@ -956,8 +968,7 @@ pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_p
         *out = p;
         return PNE_OK;
     }
-    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, rb, arith)) ||
-        (st = launch_gauge(ctx, p, s, nullptr))) {
+    if ((st = projectors(rb, cudaMemcpyDeviceToHost)) || (st = launch_gauge(ctx, p, s, nullptr))) {
         pne_partition_destroy(p);
         return st;
     }
@@ -972,7 +983,7 @@ pne_status pne_build_partition(pne_ctx *ctx, const pne_network *net, const pne_p
     if (flags[0] || flags[2]) { pne_partition_destroy(p); set_error(ctx, PNE_ETIMEOUT, "grid barrier timed out in BP"); return PNE_ETIMEOUT; }
     if (flags[1] || flags[3]) { pne_partition_destroy(p); set_error(ctx, PNE_EDEGENERATE, "zero message or zero message overlap"); return PNE_EDEGENERATE; }
     *out = p;
-    for (size_t b = 0; b < B; ++b)
+    for (size_t b = 0; b < B && !p->user_proj; ++b)
         if (p->bp_iters[b] == 0) {
             set_error(ctx, PNE_ENOCONV, "BP did not converge for tensor set " + std::to_string(b));
             return PNE_ENOCONV;
@@ -1507,6 +1518,16 @@ pne_status pne_partition_update(pne_ctx *ctx, pne_partition *p, const double *da
     const int arith = opts ? opts->arithmetic : p->arithmetic;
     if (arith != 0 && arith != 1) { set_error(ctx, PNE_EINVAL, "arithmetic must be 0 or 1"); return PNE_EINVAL; }
     p->arithmetic = arith;
+    const bool user = opts && opts->use_user_projectors;
+    if (user && (!opts->user_u || !opts->user_v)) {
+        set_error(ctx, PNE_EINVAL, "use_user_projectors needs user_u and user_v");
+        return PNE_EINVAL;
+    }
+    p->user_proj = user;
+    auto projectors = [&](void *rec, cudaMemcpyKind kind) {
+        return user ? launch_user_projectors(ctx, p, opts->user_u, opts->user_v, s, rec, kind)
+                    : launch_bp(ctx, p, tol, max_iter, damping, s, rec, arith, kind);
+    };
     if (opts && opts->async_status) {
         // deferred record, read by the next call that synchronises
         if (!p->rec_dev.ptr) {
@@ -1514,15 +1535,13 @@ pne_status pne_partition_update(pne_ctx *ctx, pne_partition *p, const double *da
             p->rec_dev.ptr = p->rec_own.ptr;
             p->rec_dev.bytes = p->rec_own.bytes;
         }
-        if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, p->rec_dev.ptr, arith, cudaMemcpyDeviceToDevice)) ||
-            (st = launch_gauge(ctx, p, s, nullptr)))
+        if ((st = projectors(p->rec_dev.ptr, cudaMemcpyDeviceToDevice)) || (st = launch_gauge(ctx, p, s, nullptr)))
             return st;
         p->mb32_dtype = -1;
         p->rec_pending = true;
         return PNE_OK;
     }
-    if ((st = launch_bp(ctx, p, tol, max_iter, damping, s, rb, arith)) ||
-        (st = launch_gauge(ctx, p, s, nullptr)))
+    if ((st = projectors(rb, cudaMemcpyDeviceToHost)) || (st = launch_gauge(ctx, p, s, nullptr)))
         return st;
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     std::memcpy(p->bp_iters.data(), h_iters, B * 4);
@@ -1530,7 +1549,7 @@ pne_status pne_partition_update(pne_ctx *ctx, pne_partition *p, const double *da
     p->mb32_dtype = -1;
     if (flags[0] || flags[2]) { set_error(ctx, PNE_ETIMEOUT, "grid barrier timed out in BP"); return PNE_ETIMEOUT; }
     if (flags[1] || flags[3]) { set_error(ctx, PNE_EDEGENERATE, "zero message or zero message overlap"); return PNE_EDEGENERATE; }
-    for (int b = 0; b < p->n_sets; ++b)
+    for (int b = 0; b < p->n_sets && !p->user_proj; ++b)
         if (p->bp_iters[b] == 0) { set_error(ctx, PNE_ENOCONV, "BP did not converge for tensor set " + std::to_string(b)); return PNE_ENOCONV; }
     return PNE_OK;
 }

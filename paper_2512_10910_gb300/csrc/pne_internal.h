@@ -282,6 +282,7 @@ struct pne_partition {
     pne::DevBuf Mb16;                // BF16 copy (lazy)
     int mb32_dtype = -1;
     int arithmetic = 0;              // BP sweeps: 0 FP64, 1 float-float
+    bool user_proj = false;          // projectors given by the caller (no sweeps, no convergence test)
     std::vector<int32_t> bp_iters;   // per set
     std::vector<double> bp_residual; // per set
     cudaStream_t last_stream = nullptr;
@@ -407,6 +408,11 @@ pne_status partition_settle(pne_ctx *ctx, pne_partition *p);
 // returns the BP status (ETIMEOUT, EDEGENERATE, ENOCONV or OK)
 pne_status partition_record(pne_ctx *ctx, pne_partition *p, const char *rec);
 pne_status launch_gauge(pne_ctx *ctx, pne_partition *p, cudaStream_t s, int32_t *h_flag);
+// user projectors: the caller's rank-1 projector vectors placed as the final
+// messages (no sweeps), then the gauge pairs; the convergence record (zeros,
+// the gauge's degenerate flag) copied to rec like launch_bp's
+pne_status launch_user_projectors(pne_ctx *ctx, pne_partition *p, const double *user_u, const double *user_v,
+                                  cudaStream_t s, void *rec, cudaMemcpyKind rec_kind);
 pne_status launch_convert(pne_ctx *ctx, pne_partition *p, int dtype, cudaStream_t s);
 // FP64 -> FP32 (TF32 rounding for PNE_TF32) or BF16 copy of n entries
 pne_status convert_buffer(pne_ctx *ctx, const double *src, int64_t n, int dtype, void *dst, cudaStream_t s);

@@ -27,7 +27,7 @@ __all__ = [
     "pne_batch_schedule", "pne_batch_destroy", "BatchOpts", "PNE_SCHED_HANDLE", "PNE_SCHED_LARGEST_FIRST",
     "pne_server_create", "pne_server_submit", "pne_server_poll",
     "pne_server_drain", "pne_server_stats", "pne_server_first_error", "pne_server_destroy", "ServerOpts", "RequestInfo",
-    "Network", "PartitionOpts", "EnumOpts", "Result", "Context", "run", "network_struct",
+    "Network", "PartitionOpts", "user_projector_opts", "EnumOpts", "Result", "Context", "run", "network_struct",
     "pne_strip_expansion", "StripOpts", "StripResult", "PNE_STRIP_MAX_L", "PNE_STRIP_MAX_CHI",
     "pne_dense_gemm", "pne_grid_contract", "pne_rank_r_expand_grid", "pne_rank_r_expand",
     "pne_recursive_expand_grid", "pne_weight_passing", "pne_weights_read", "pne_weights_destroy",
@@ -65,7 +65,25 @@ class Network(ctypes.Structure):
 
 class PartitionOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("damping", ctypes.c_double),
-                ("arithmetic", ctypes.c_int32), ("async_status", ctypes.c_int32)]
+                ("arithmetic", ctypes.c_int32), ("async_status", ctypes.c_int32),
+                ("use_user_projectors", ctypes.c_int32), ("user_u", ctypes.POINTER(ctypes.c_double)),
+                ("user_v", ctypes.POINTER(ctypes.c_double))]
+
+
+def user_projector_opts(u, v, **kw):
+    """PartitionOpts with user projectors P_b = u_b v_b^T / (u_b . v_b): u and v
+    are FP64 arrays laid out [tensor set][closed bonds in id order][bond_dim[b]]
+    (flattened).  Returns (opts, keep): keep holds the arrays for the call."""
+    u = np.ascontiguousarray(u, dtype=np.float64).ravel()
+    v = np.ascontiguousarray(v, dtype=np.float64).ravel()
+    if u.shape != v.shape:
+        raise ValueError("user_u and user_v must have the same length")
+    o = PartitionOpts(kw.get("tol", 1e-13), kw.get("max_iter", 10000), kw.get("damping", 0.0),
+                      kw.get("arithmetic", 0), kw.get("async_status", 0))
+    o.use_user_projectors = 1
+    o.user_u = u.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    o.user_v = v.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return o, (u, v)
 
 
 class EnumOpts(ctypes.Structure):
@@ -782,15 +800,20 @@ class Context:
 
     def expand(self, net, K, mode=PNE_MODE_LOOP, dtype=PNE_F64, data=None, n_batch=1, stream=None,
                tol=1e-13, max_iter=10000, damping=0.0, use_cache=True, allow_noconv=False,
-               export=False, arithmetic=0):
+               export=False, arithmetic=0, projectors=None):
         """One pass: partition -> enumerate -> contract -> sum.  Returns the
         list of result dicts (one per tensor set and open-index assignment);
-        with export=True also (edges, w) of the clusters."""
+        with export=True also (edges, w) of the clusters.  projectors=(u, v)
+        replaces BP by user projectors (see user_projector_opts)."""
         if isinstance(dtype, str):
             dtype = DTYPES[dtype]
         ns, keep = network_struct(net, data=data, n_batch=n_batch)
-        part, st = pne_build_partition(self.h, ns, PartitionOpts(tol, max_iter, damping, arithmetic), stream,
-                                       allow_noconv)
+        if projectors is not None:
+            popts, pkeep = user_projector_opts(*projectors, arithmetic=arithmetic)
+        else:
+            popts, pkeep = PartitionOpts(tol, max_iter, damping, arithmetic), None
+        part, st = pne_build_partition(self.h, ns, popts, stream, allow_noconv)
+        del pkeep
         try:
             terms, nc, nt = pne_enumerate_terms(self.h, part, EnumOpts(K, mode, int(use_cache)), stream)
             try:

@@ -49,7 +49,7 @@ def test_struct_layouts():
     import ctypes
     # pne_network: 2 ints, 4 pointers, data, data_off, 2 ints (LP64)
     assert ctypes.sizeof(pne.Network) == 8 + 4 * 8 + 8 + 8 + 8
-    assert ctypes.sizeof(pne.PartitionOpts) == 32
+    assert ctypes.sizeof(pne.PartitionOpts) == 56
     assert ctypes.sizeof(pne.EnumOpts) == 12
     # pne_trace_entry: name[32], kind, stream, t0_ms, t1_ms
     assert ctypes.sizeof(pne.TraceEntry) == 32 + 4 + 4 + 8 + 8
@@ -174,7 +174,7 @@ def test_strip_struct_layouts_match_the_header(tmp_path):
     assert got == want
 
 
-def test_batch_opts_layout_matches_the_header(tmp_path):
+def test_batch_and_partition_opts_layouts_match_the_header(tmp_path):
     import ctypes
     import shutil
     import subprocess
@@ -183,10 +183,13 @@ def test_batch_opts_layout_matches_the_header(tmp_path):
         pytest.skip("no C compiler")
     src = tmp_path / "lay.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pne.h"\nint main(void){\n'
-                   'printf("%zu %zu %d %d\\n", sizeof(pne_batch_opts), offsetof(pne_batch_opts, schedule),\n'
-                   ' PNE_SCHED_HANDLE, PNE_SCHED_LARGEST_FIRST);\nreturn 0;}\n')
+                   'printf("%zu %zu %d %d %zu %zu %zu %zu\\n", sizeof(pne_batch_opts),\n'
+                   ' offsetof(pne_batch_opts, schedule), PNE_SCHED_HANDLE, PNE_SCHED_LARGEST_FIRST,\n'
+                   ' sizeof(pne_partition_opts), offsetof(pne_partition_opts, use_user_projectors),\n'
+                   ' offsetof(pne_partition_opts, user_u), offsetof(pne_partition_opts, user_v));\nreturn 0;}\n')
     exe = tmp_path / "lay"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    B = pne.BatchOpts
-    assert got == [ctypes.sizeof(B), B.schedule.offset, pne.PNE_SCHED_HANDLE, pne.PNE_SCHED_LARGEST_FIRST]
+    B, P = pne.BatchOpts, pne.PartitionOpts
+    assert got == [ctypes.sizeof(B), B.schedule.offset, pne.PNE_SCHED_HANDLE, pne.PNE_SCHED_LARGEST_FIRST,
+                   ctypes.sizeof(P), P.use_user_projectors.offset, P.user_u.offset, P.user_v.offset]
