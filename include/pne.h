@@ -145,6 +145,9 @@ typedef struct {
     int32_t max_order;   /* K: keep terms with |E| <= K                      */
     int32_t mode;        /* pne_mode                                          */
     int32_t use_cache;   /* reuse a cached enumeration of the same geometry  */
+    int32_t max_cluster; /* keep only clusters of at most this many bonds
+                            (terms still up to order max_order, built from
+                            those clusters); 0 or >= max_order: no cap       */
 } pne_enum_opts;
 
 /* Result for one network (one tensor set, one open-index assignment). */

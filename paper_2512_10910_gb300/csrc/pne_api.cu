@@ -1022,8 +1022,11 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
     const Geometry &g = part->geo->closed;
     // the geometry tables may have been queued on the partition's stream
     if (part->geo->ready) PNE_CUDA_TRY(ctx, cudaStreamWaitEvent(s, part->geo->ready, 0));
+    // cluster-size cap (LOOP mode): clusters up to Kc bonds, terms up to K
+    const int Kc = (mode == PNE_MODE_LOOP && opts->max_cluster > 0 && opts->max_cluster < K) ? opts->max_cluster : K;
+    if (opts->max_cluster < 0) { set_error(ctx, PNE_EINVAL, "max_cluster must be >= 0"); return PNE_EINVAL; }
     std::string key = std::to_string(g.hash) + ":" + std::to_string(g.n_sites) + ":" + std::to_string(g.n_bonds) +
-                      ":" + std::to_string(K) + ":" + std::to_string(mode);
+                      ":" + std::to_string(K) + ":" + std::to_string(mode) + ":" + std::to_string(Kc);
     std::shared_ptr<EnumRecord> rec;
     if (opts->use_cache) {
         std::lock_guard<std::mutex> lk(ctx->cache_mu);
@@ -1064,7 +1067,12 @@ pne_status pne_enumerate_terms(pne_ctx *ctx, const pne_partition *part, const pn
             } else {
                 {
                     HostScope h1(ctx, "enum_clusters");
-                    if ((st = enumerate_clusters(ctx, g, K, mode, *rec, s))) return st;
+                    if ((st = enumerate_clusters(ctx, g, Kc, mode, *rec, s))) return st;
+                    if (Kc < K) {
+                        // no cluster is larger than Kc: the size groups Kc+1..K are empty
+                        rec->K = K;
+                        rec->size_start.resize(K + 2, rec->size_start[Kc + 1]);
+                    }
                 }
                 // the shape stage (contraction plans) and the term stage run on
                 // two streams, their host waits interleaved: each waits for its

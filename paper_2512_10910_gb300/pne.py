@@ -87,7 +87,8 @@ def user_projector_opts(u, v, **kw):
 
 
 class EnumOpts(ctypes.Structure):
-    _fields_ = [("max_order", ctypes.c_int32), ("mode", ctypes.c_int32), ("use_cache", ctypes.c_int32)]
+    _fields_ = [("max_order", ctypes.c_int32), ("mode", ctypes.c_int32), ("use_cache", ctypes.c_int32),
+                ("max_cluster", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -800,7 +801,7 @@ class Context:
 
     def expand(self, net, K, mode=PNE_MODE_LOOP, dtype=PNE_F64, data=None, n_batch=1, stream=None,
                tol=1e-13, max_iter=10000, damping=0.0, use_cache=True, allow_noconv=False,
-               export=False, arithmetic=0, projectors=None):
+               export=False, arithmetic=0, projectors=None, max_cluster=0):
         """One pass: partition -> enumerate -> contract -> sum.  Returns the
         list of result dicts (one per tensor set and open-index assignment);
         with export=True also (edges, w) of the clusters.  projectors=(u, v)
@@ -815,7 +816,7 @@ class Context:
         part, st = pne_build_partition(self.h, ns, popts, stream, allow_noconv)
         del pkeep
         try:
-            terms, nc, nt = pne_enumerate_terms(self.h, part, EnumOpts(K, mode, int(use_cache)), stream)
+            terms, nc, nt = pne_enumerate_terms(self.h, part, EnumOpts(K, mode, int(use_cache), max_cluster), stream)
             try:
                 pne_contract_terms(self.h, terms, dtype, stream)
                 res = pne_sum(self.h, terms, stream)

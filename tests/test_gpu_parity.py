@@ -358,6 +358,21 @@ def test_damped_bp_reaches_the_same_fixed_point(ctx, name, arith):
     assert r["bp_iters"] > u["bp_iters"] > 0
 
 
+@pytest.mark.parametrize("cache", [0, 1])
+@pytest.mark.parametrize("shape,D,K,mc,seed", [((6, 6), 3, 8, 4, 3), ((5, 5), 2, 10, 6, 4), ((4, 4), 4, 8, 8, 5)])
+def test_cluster_size_cap_matches_the_oracle(ctx, shape, D, K, mc, seed, cache):
+    # clusters of at most mc bonds, terms still up to order K built from them
+    net = I.random_tensors(I.square_lattice(shape[0], shape[1], D), seed)
+    cl = E.enumerate_clusters(net, mc, E.LOOP)
+    ref = X.pne(net, K, E.LOOP, clusters=cl, terms=E.enumerate_terms(net, cl, K))
+    (r,) = ctx.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64, max_cluster=mc, use_cache=bool(cache))
+    assert r["n_clusters"] == len(cl) and r["n_terms"] == ref.n_terms
+    _check_values(r, ref)
+    if mc < K:
+        (full,) = ctx.expand(net, K, pne.PNE_MODE_LOOP, pne.PNE_F64, use_cache=bool(cache))
+        assert full["n_terms"] > r["n_terms"]       # a cached record of the other cap is not reused
+
+
 # ---------------------------------------------------------------- search schedule
 @pytest.mark.parametrize("shape,D,K,limit", [((8, 8), 3, 8, 1), ((8, 8), 3, 8, 700), ((8, 8), 3, 8, 6000),
                                              ((6, 5), 2, 10, 0), ((6, 5), 2, 10, 500)])

@@ -50,7 +50,7 @@ def test_struct_layouts():
     # pne_network: 2 ints, 4 pointers, data, data_off, 2 ints (LP64)
     assert ctypes.sizeof(pne.Network) == 8 + 4 * 8 + 8 + 8 + 8
     assert ctypes.sizeof(pne.PartitionOpts) == 56
-    assert ctypes.sizeof(pne.EnumOpts) == 12
+    assert ctypes.sizeof(pne.EnumOpts) == 16
     # pne_trace_entry: name[32], kind, stream, t0_ms, t1_ms
     assert ctypes.sizeof(pne.TraceEntry) == 32 + 4 + 4 + 8 + 8
 
