@@ -499,7 +499,7 @@ def step_roofline(args, pne, ctx, ctypes_stream, g, sb, res, prof, prof_steps, B
             # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
             # current kernel: the 16.8 MB of float-float pair tensors read once,
             # later sweeps served from L2
-            roof.update(traffic=15.84e6, traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum per "
+            roof.update(traffic=15.83e6, traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum per "
                                                         "launch of bp_ff_cluster_kernel, this workload")
     elif fam == "contract":
         roof.update(achieved=2.0 * fma * B / (avg_ms * 1e-3) / 1e12, peak=pk_c / 1e12,
@@ -537,9 +537,9 @@ def step_roofline(args, pne, ctx, ctypes_stream, g, sb, res, prof, prof_steps, B
                          f"({launches // prof_steps} launches of {fam} per search)")
         if args.workload == "random16":
             # what bounds it: issue slots and the integer pipe, per launch (ncu)
-            roof.update(issue={"expand_kernel": {"issue_active_pct": 25.4, "alu_pipe_pct": 21.9,
-                                                 "dram_bytes_per_launch": 1.03e6},
-                               "expand_children_kernel": {"issue_active_pct": 12.8, "alu_pipe_pct": 8.6,
+            roof.update(issue={"expand_kernel": {"issue_active_pct": 23.4, "alu_pipe_pct": 20.9,
+                                                 "dram_bytes_per_launch": 0.77e6},
+                               "expand_children_kernel": {"issue_active_pct": 12.9, "alu_pipe_pct": 8.7,
                                                           "dram_bytes_per_launch": 0.49e6},
                                "source": "ncu smsp__issue_active, sm__pipe_alu_cycles_active, dram__bytes_*, "
                                          "averages over the launches of one step, this workload"})
