@@ -474,6 +474,7 @@ struct BPFFParams {
     // sweeps (t_slots per warp of slot_ff entries, slot_ff even); 0 = read
     // them from global memory every sweep
     int t_slots, slot_ff;
+    double *msg64;                // cluster form: the final messages in FP64, buffer 0 ([n_sets][n_legs][8])
 };
 
 __device__ void site_messages_ff(const ff *__restrict__ T, int k, const int *dims, const ff *in, ff *u, ff *w,
@@ -1163,6 +1164,13 @@ __global__ void __launch_bounds__(ClusterForm<TASK>::kWarps * 32, ClusterForm<TA
                 p.res_out[set] = (double)rs;
                 p.final_buf[set] = 0;
             }
+            // the set's messages in FP64 for the gauge (every block of the
+            // cluster wrote its share before the last barrier)
+            double *m64 = p.msg64 + set * msg_set;
+            for (int64_t i = (int64_t)rank * blockDim.x + threadIdx.x; i < msg_set; i += (int64_t)CL * blockDim.x) {
+                const ff x = ldcg_ff(msg + i);
+                m64[i] = (double)x.h + (double)x.l;
+            }
             return;
         }
     }
@@ -1697,6 +1705,7 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
         fp.flags = flags; fp.res_out = res_out; fp.bar = bar;
         fp.smem_per_warp = per_warp; fp.tabA = tabA; fp.tabC = tabC;
         fp.n_colors = g.n_colors; fp.color_ptr = g.d_color_ptr; fp.color_sites = g.d_color_sites;
+        fp.msg64 = msg;
         // one cluster per tensor set when the colour classes are small enough
         // (at most four warp tasks per warp and phase in a cluster of <= 16
         // blocks); two sites per task when at least half of the sites take
@@ -1833,7 +1842,8 @@ pne_status launch_bp(pne_ctx *ctx, pne_partition *p, double tol, int max_iter, d
             }
         }
         if (fe != cudaSuccess) { dev_free(ctx, scratch, s); PNE_CUDA_TRY(ctx, fe); }
-        {
+        if (!cluster_ok) {
+            // the cluster form writes the FP64 messages itself as it stops
             ProfScope ps(ctx, s, "bp_export");
             ff_export_kernel<<<grid_for((int64_t)n_sets * g.n_legs * kMsgStride, 256, ctx->n_sm), 256, 0, s>>>(
                 mff, msg, finalb, n_sets, (int64_t)g.n_legs * kMsgStride);
