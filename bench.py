@@ -486,8 +486,8 @@ def step_roofline(args, pne, ctx, ctypes_stream, g, sb, res, prof, prof_steps, B
     pne.pne_terms_destroy(terms)
     pne.pne_partition_destroy(part)
     pk_c = peak_f64 if args.dtype == "f64" else peak_f32
-    bp_peak = (peak_f32 / 16) if args.bp == "ff" else peak_f64
-    bp_src = ("measured FP32 FMA-chain kernel (pne_measure_fma_peak) / 16 FP32 instructions per float-float "
+    bp_peak = (peak_f32 / 12) if args.bp == "ff" else peak_f64
+    bp_src = ("measured FP32 FMA-chain kernel (pne_measure_fma_peak) / 12 FP32 instructions per float-float "
               "multiply-add" if args.bp == "ff" else "measured FP64 FMA-chain kernel (pne_measure_fma_peak)")
     bp_work = f"4 flops per tensor entry per site per sweep; {sum(iters)} sweeps over {B} sets"
     c_work = f"2 flops per plan multiply-add; {fma} multiply-adds per network"
@@ -516,8 +516,8 @@ def step_roofline(args, pne, ctx, ctypes_stream, g, sb, res, prof, prof_steps, B
         work = sum(int(np.prod(g.bond_dim[g.site_bonds[g.site_ptr[v]:g.site_ptr[v + 1]]])) *
                    int(np.sum(g.bond_dim[g.site_bonds[g.site_ptr[v]:g.site_ptr[v + 1]]]))
                    for v in range(g.n_sites)) * B
-        roof.update(achieved=2.0 * work / (avg_ms * 1e-3) / 1e12, peak=peak_f32 / 16 / 1e12,
-                    peak_source="measured FP32 FMA-chain kernel (pne_measure_fma_peak) / 16 FP32 instructions per "
+        roof.update(achieved=2.0 * work / (avg_ms * 1e-3) / 1e12, peak=peak_f32 / 12 / 1e12,
+                    peak_source="measured FP32 FMA-chain kernel (pne_measure_fma_peak) / 12 FP32 instructions per "
                                 "float-float multiply-add",
                     work=f"2 flops per multiply-add; {work} multiply-adds per step (n d per leg per site)")
         if args.workload == "random16":

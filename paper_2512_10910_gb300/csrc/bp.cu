@@ -508,7 +508,7 @@ __device__ void site_messages_ff(const ff *__restrict__ T, int k, const int *dim
             ffacc acc;
             if (a < A) {
                 const ff *row = T + (int64_t)a * C;
-                for (int c = sub; c < C; c += lpr) acc.add(ff_mul(row[c], w[c]));
+                for (int c = sub; c < C; c += lpr) acc.mad(row[c], w[c]);
             }
             ff s = acc.get();
             for (int off = lpr / 2; off > 0; off >>= 1) s = ff_add(s, ff_shfl_xor(s, off));
@@ -523,7 +523,7 @@ __device__ void site_messages_ff(const ff *__restrict__ T, int k, const int *dim
             const int c = c0 + lane % cols_per_pass;
             ffacc acc;
             if (c < C)
-                for (int a = sub; a < A; a += lpc) acc.add(ff_mul(u[a], T[(int64_t)a * C + c]));
+                for (int a = sub; a < A; a += lpc) acc.mad(u[a], T[(int64_t)a * C + c]);
             ff s = acc.get();
             for (int off = 16; off >= cols_per_pass; off >>= 1) s = ff_add(s, ff_shfl_xor(s, off));
             if (c < C && sub == 0) x2[c] = s;
@@ -628,7 +628,7 @@ __device__ void site_messages_ff_u(const ff *__restrict__ T, const ff *in, ff *u
             if (a < A) {
                 const ff *row = T + (int64_t)a * C;
 #pragma unroll 4
-                for (int c = sub; c < C; c += LPR) acc.add(ff_mul(row[c], w[c]));
+                for (int c = sub; c < C; c += LPR) acc.mad(row[c], w[c]);
             }
             ff sm = acc.get();
 #pragma unroll
@@ -645,7 +645,7 @@ __device__ void site_messages_ff_u(const ff *__restrict__ T, const ff *in, ff *u
             ffacc acc;
             if (c < C) {
 #pragma unroll 4
-                for (int a = sub; a < A; a += LPC) acc.add(ff_mul(u[a], T[(int64_t)a * C + c]));
+                for (int a = sub; a < A; a += LPC) acc.mad(u[a], T[(int64_t)a * C + c]);
             }
             ff sm = acc.get();
 #pragma unroll
@@ -1510,7 +1510,7 @@ __global__ void block_ff_kernel(BlockParams p)
                     ffacc acc;
 #pragma unroll
                     for (int a = 0; a < kMaxDim; ++a)
-                        if (a < d) acc.add(ff_mul(x[a], Gs[a * 8 + c]));
+                        if (a < d) acc.mad(x[a], Gs[a * 8 + c]);
                     nxt[base + (int64_t)c * post] = acc.get();
                 }
             }
