@@ -3,6 +3,7 @@ exports every function include/pne.h declares.  No GPU compute is issued."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2512_10910_gb300 import build as B
@@ -193,3 +194,16 @@ def test_batch_and_partition_opts_layouts_match_the_header(tmp_path):
     B, P = pne.BatchOpts, pne.PartitionOpts
     assert got == [ctypes.sizeof(B), B.schedule.offset, pne.PNE_SCHED_HANDLE, pne.PNE_SCHED_LARGEST_FIRST,
                    ctypes.sizeof(P), P.use_user_projectors.offset, P.user_u.offset, P.user_v.offset]
+
+
+def test_user_projector_options_point_at_the_callers_vectors():
+    # host-side marshalling only: flat FP64 arrays, equal lengths, flag set
+    import ctypes
+    u = np.arange(6, dtype=np.float64)
+    v = np.arange(6, 12, dtype=np.float64)
+    o, keep = pne.user_projector_opts(u, v, arithmetic=1)
+    assert o.use_user_projectors == 1 and o.arithmetic == 1
+    assert ctypes.addressof(o.user_u.contents) == keep[0].ctypes.data
+    assert [o.user_v[i] for i in range(6)] == list(v)
+    with pytest.raises(ValueError):
+        pne.user_projector_opts(u, v[:5])
