@@ -1047,9 +1047,11 @@ pne_status run_shaped(pne_ctx *ctx, const ContractParams &cp, const EnumRecord &
             PNE_CUDA_TRY(ctx, cudaStreamWaitEvent(ls, ctx->side_ev[0], 0));
         }
         {
-            // a group of lanes per cluster: 32 for large running tensors, else
-            // about one lane per two outputs of the largest step
-            const int G = xmax >= 32 ? 32 : (xmax >= 16 ? 8 : 4);
+            // a group of lanes per cluster: 32 for large running tensors, else 4
+            // (8 lanes for the 16-entry class measured 89 against 78 us on
+            // the 16x16 D = 4 step: fewer lanes per cluster keep more clusters'
+            // gathers in flight)
+            const int G = xmax >= 32 ? 32 : 4;
             const int gpb = 256 / G;
             const size_t smem2 = (size_t)gpb * 2 * xmax * sizeof(T);
             const int64_t items2 = (i1 - i0) * cp.n_members;
