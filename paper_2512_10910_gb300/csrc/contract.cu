@@ -1846,7 +1846,7 @@ __global__ void fused_batch_kernel(const BatchGroup *groups, const BatchItem *it
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int wstride = max(8 * xsm, 16 * min(xsm, 8));          // shared entries per warp
+    const int wstride = max(8 * xsm, 16 * min(xsm, 16));         // shared entries per warp
 
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     T *G0 = xscratch ? xscratch + gw * 2 * xglob * 32 + lane : nullptr;
@@ -1863,7 +1863,7 @@ __global__ void fused_batch_kernel(const BatchGroup *groups, const BatchItem *it
             if (G.shaped && !big) {
                 // groups of lanes per cluster in the warp's shared slices
                 T *W = (T *)smem_raw + (int64_t)wib * wstride;
-                if (wi.aux <= 8) batch_groups<T, L, R, 4>(G, wi, W, lane);
+                if (wi.aux <= 16) batch_groups<T, L, R, 4>(G, wi, W, lane);
                 else batch_groups<T, L, R, 8>(G, wi, W, lane);
             } else {
                 // bond dimension 2 (no running tensor) or a running tensor in
@@ -2106,9 +2106,10 @@ pne_status batch_plan_create(pne_ctx *ctx, const std::vector<pne_terms *> &terms
     PNE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const size_t elem = (dtype == PNE_F64) ? 8 : 4;
     bp->xsm = std::min(bp->xmax, kBatchSmemX);
-    // per warp: the running tensors of its lane groups (4 groups of 2 * aux
-    // entries for items up to 32 entries, 8 groups of 2 * 8 for items up to 8)
-    bp->smem_per_warp = (size_t)std::max(8 * bp->xsm, 16 * std::min(bp->xsm, 8)) * elem;
+    // per warp: the running tensors of its lane groups (8 groups of 4 lanes,
+    // 2 * aux entries each, for items up to 16 entries; 4 groups of 8 lanes for
+    // items up to 32)
+    bp->smem_per_warp = (size_t)std::max(8 * bp->xsm, 16 * std::min(bp->xsm, 16)) * elem;
     *out = bp;
     return PNE_OK;
 }
