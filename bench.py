@@ -521,7 +521,7 @@ def step_roofline(args, pne, ctx, ctypes_stream, g, sb, res, prof, prof_steps, B
                                 "float-float multiply-add",
                     work=f"2 flops per multiply-add; {work} multiply-adds per step (n d per leg per site)")
         if args.workload == "random16":
-            roof.update(traffic=21.79e6, traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum per "
+            roof.update(traffic=21.78e6, traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum per "
                                                         "launch of block_ff_kernel, this workload")
     elif fam.startswith("enum_"):
         # the cluster search is integer work bound by issue and latency; its
