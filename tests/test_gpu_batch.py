@@ -190,3 +190,32 @@ def test_full_size_batch_members_match_the_oracle(ctx):
             np.testing.assert_allclose(r["c"], ref.c, rtol=0, atol=1e-10 * scale)
     finally:
         _free(parts, terms)
+
+
+def test_batch_of_capped_enumerations_matches_the_oracle(ctx):
+    # handles whose clusters are capped below the order (max_cluster) batch
+    # like any other: terms of order <= K built from clusters of <= 4 bonds
+    groups = [(I.square_lattice(6, 6, 3), [I.random_tensors(I.square_lattice(6, 6, 3), s) for s in (81, 82)]),
+              (I.square_lattice(5, 5, 2), [I.random_tensors(I.square_lattice(5, 5, 2), 83)])]
+    parts, terms, keep = [], [], []
+    try:
+        for g, nets in groups:
+            data = np.concatenate([n.flat_data()[0] for n in nets])
+            ns, kp = pne.network_struct(g, data=data, n_batch=len(nets))
+            p, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0))
+            t, _, _ = pne.pne_enumerate_terms(ctx.h, p, pne.EnumOpts(8, 0, 1, 4))
+            parts.append(p); terms.append(t); keep.append((ns, kp))
+        b = pne.pne_batch_create(ctx.h, terms, pne.PNE_F64)
+        got = pne.pne_batch_run(ctx.h, b)
+        pne.pne_batch_destroy(b)
+        r = 0
+        for g, nets in groups:
+            for net in nets:
+                cl = E.enumerate_clusters(net, 4, E.LOOP)
+                ref = X.pne(net, 8, E.LOOP, clusters=cl, terms=E.enumerate_terms(net, cl, 8))
+                assert got[r]["n_terms"] == ref.n_terms
+                assert abs(got[r]["log_abs"] - ref.log_abs) <= 1e-10
+                np.testing.assert_allclose(got[r]["c"], ref.c, rtol=0, atol=1e-10 * np.sum(np.abs(ref.c)))
+                r += 1
+    finally:
+        _free(parts, terms)

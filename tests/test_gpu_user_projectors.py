@@ -133,3 +133,34 @@ def test_orthogonal_projector_vectors_are_degenerate(ctx):
     with pytest.raises(pne.PneError) as e:
         ctx.expand(net, 6, pne.PNE_MODE_LOOP, pne.PNE_F64, projectors=_flat(net, [uv]))
     assert e.value.status == pne.PNE_EDEGENERATE
+
+
+def test_partition_update_with_user_projectors(ctx):
+    # the handle built by BP, then updated in place with new tensors and user
+    # projectors: the enumeration built on it stays valid and the sums follow
+    # the new projectors
+    g = I.square_lattice(4, 4, 3)
+    net0, net1 = I.random_tensors(g, 71), I.random_tensors(g, 72)
+    ns, keep = pne.network_struct(net0)
+    part, _ = pne.pne_build_partition(ctx.h, ns, pne.PartitionOpts(1e-13, 10000, 0.0))
+    try:
+        terms, _, _ = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(6, pne.PNE_MODE_LOOP, 0))
+        try:
+            uv = _random_vectors(net1, 73)
+            opts, pkeep = pne.user_projector_opts(*_flat(net1, [uv]))
+            pne.pne_partition_update(ctx.h, part, net1.flat_data()[0], opts)
+            pne.pne_contract_terms(ctx.h, terms, pne.PNE_F64)
+            (r,) = pne.pne_sum(ctx.h, terms)
+            _check(r, Ex.pne(net1, 6, E.LOOP, proj=_oracle_proj(net1, uv)))
+            assert r["bp_iters"] == 0
+            # and back to BP on the same handle
+            pne.pne_partition_update(ctx.h, part, net1.flat_data()[0], pne.PartitionOpts(1e-13, 10000, 0.0))
+            pne.pne_contract_terms(ctx.h, terms, pne.PNE_F64)
+            (b,) = pne.pne_sum(ctx.h, terms)
+            _check(b, Ex.pne(net1, 6, E.LOOP))
+            assert b["bp_iters"] > 0
+            del pkeep
+        finally:
+            pne.pne_terms_destroy(terms)
+    finally:
+        pne.pne_partition_destroy(part)
