@@ -164,3 +164,33 @@ def test_partition_update_with_user_projectors(ctx):
             pne.pne_terms_destroy(terms)
     finally:
         pne.pne_partition_destroy(part)
+
+
+def test_user_projectors_with_a_deferred_record(ctx):
+    # async_status: the record (zero sweeps, the gauge's degenerate flag) is read
+    # by pne_sum; a good set of projectors sums normally, a zero overlap raises there
+    net = I.random_tensors(I.square_lattice(4, 4, 2), 91)
+    for degenerate in (False, True):
+        uv = _random_vectors(net, 92)
+        if degenerate:
+            uv[_closed(net)[2]] = (np.array([1.0, 0.0]), np.array([0.0, 1.0]))
+        opts, pkeep = pne.user_projector_opts(*_flat(net, [uv]), async_status=1)
+        ns, keep = pne.network_struct(net)
+        part, _ = pne.pne_build_partition(ctx.h, ns, opts)
+        try:
+            terms, _, _ = pne.pne_enumerate_terms(ctx.h, part, pne.EnumOpts(8, pne.PNE_MODE_LOOP, 0))
+            try:
+                pne.pne_contract_terms(ctx.h, terms, pne.PNE_F64)
+                if degenerate:
+                    with pytest.raises(pne.PneError) as e:
+                        pne.pne_sum(ctx.h, terms)
+                    assert e.value.status == pne.PNE_EDEGENERATE
+                else:
+                    (r,) = pne.pne_sum(ctx.h, terms)
+                    _check(r, Ex.pne(net, 8, E.LOOP, proj=_oracle_proj(net, uv)))
+                    assert r["bp_iters"] == 0
+            finally:
+                pne.pne_terms_destroy(terms)
+        finally:
+            pne.pne_partition_destroy(part)
+        del pkeep
